@@ -1,0 +1,197 @@
+"""FP64 CPU oracle for the line-of-sight convergence integration.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the library itself never does. It
+shares no code with the CUDA path (see rr_oracle.c for what it computes and
+which passages of Barreira et al. 2016 each function follows).
+
+Every function here takes and returns numpy arrays; fields are promoted to
+float64 before use (an FP32 input is read exactly).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over rays; no fused multiply-add
+    contraction, so x86 and Arm give the same bits)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Bundle(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("fov_x", C.c_double), ("fov_y", C.c_double),
+                ("obs", C.c_double * 3), ("chi_s", C.c_double), ("interp", C.c_int32),
+                ("periodic", C.c_int32)]
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("box", C.c_double), ("omega_m", C.c_double)]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        _lib.ora_tidal_centres.argtypes = [P, P, P]
+        _lib.ora_delta_from_tidal.argtypes = [P, P, P]
+        _lib.ora_vertex_field.argtypes = [P, P, P, P]
+        _lib.ora_trace_step.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                        P, P, P, P, C.c_int]
+        _lib.ora_ray_segments.argtypes = [P, P, C.c_long, C.c_double, C.c_double, P, C.c_long]
+        _lib.ora_ray_segments.restype = C.c_long
+        _lib.ora_ray_direction.argtypes = [P, C.c_long, P, P]
+        _lib.ora_trace_step_adjoint.argtypes = [P, P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                P, P, P, P]
+        _lib.ora_delta_from_tidal_adjoint.argtypes = [P, P, P]
+        _lib.ora_tidal_centres_adjoint.argtypes = [P, P, P]
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _bundle(b) -> _Bundle:
+    s = _Bundle()
+    s.nx, s.ny = int(b.nx), int(b.ny)
+    s.fov_x, s.fov_y = float(b.fov_x), float(b.fov_y)
+    for i in range(3):
+        s.obs[i] = float(b.obs[i])
+    s.chi_s = float(b.chi_s)
+    s.interp = int(b.interp)
+    s.periodic = 1 if b.periodic else 0
+    return s
+
+
+def _grid(g) -> _Grid:
+    s = _Grid()
+    for i in range(3):
+        s.n[i] = int(g.n[i])
+    s.box = float(g.box)
+    s.omega_m = float(g.omega_m)
+    return s
+
+
+# ---------------------------------------------------------------------------
+
+def tidal_centres(grid, phi) -> np.ndarray:
+    """d_a d_b Phi at cell centres, shape n^3 x 6 (xx, yy, zz, xy, xz, yz);
+    Eq. (tidalexample), periodic."""
+    phi = _f64(phi)
+    H = np.zeros(phi.shape + (6,), np.float64)
+    g = _grid(grid)
+    _L().ora_tidal_centres(C.byref(g), _ptr(phi), _ptr(H))
+    return H
+
+
+def delta_from_tidal(grid, H) -> np.ndarray:
+    """delta = tr(H) / (1.5 Omega_m (H0/c)^2) (comoving Poisson at a = 1)."""
+    H = _f64(H)
+    d = np.zeros(H.shape[:-1], np.float64)
+    g = _grid(grid)
+    _L().ora_delta_from_tidal(C.byref(g), _ptr(H), _ptr(d))
+    return d
+
+
+def fields(grid, phi, delta=None):
+    """(H, delta) at centres; delta derived from H when not given."""
+    H = tidal_centres(grid, phi)
+    d = delta_from_tidal(grid, H) if delta is None else _f64(delta)
+    return H, d
+
+
+def vertex_field(grid, H, delta) -> np.ndarray:
+    """Vertex values, shape n^3 x 7 (6 tidal components then delta); vertex
+    (i,j,k) at (ih, jh, kh) is the mean of the 8 cells that share it."""
+    H = _f64(H)
+    delta = _f64(delta)
+    V = np.zeros(H.shape[:-1] + (7,), np.float64)
+    g = _grid(grid)
+    _L().ora_vertex_field(C.byref(g), _ptr(H), _ptr(delta), _ptr(V))
+    return V
+
+
+class TraceResult:
+    def __init__(self, nr):
+        self.kappa = np.zeros(nr, np.float64)
+        self.kborn = np.zeros(nr, np.float64)
+        self.nseg = np.zeros(nr, np.int64)
+        self.sum_r = np.zeros(nr, np.float64)
+
+
+def trace(bundle, grid, H, delta, steps, nthreads: int = 0, result: TraceResult | None = None) -> TraceResult:
+    """Trace every ray of the bundle over the given steps (objects with chi_a,
+    chi_b, scale, a). Returns per-ray kappa, Born kappa, segment count and the
+    summed segment lengths, in rayid order (x fastest)."""
+    H = _f64(H)
+    delta = _f64(delta)
+    nr = int(bundle.nx) * int(bundle.ny)
+    res = result if result is not None else TraceResult(nr)
+    b, g = _bundle(bundle), _grid(grid)
+    for st in steps:
+        rc = _L().ora_trace_step(C.byref(b), C.byref(g), _ptr(H), _ptr(delta), float(st.chi_a),
+                                 float(st.chi_b), float(st.scale), float(st.a), _ptr(res.kappa),
+                                 _ptr(res.kborn), _ptr(res.nseg), _ptr(res.sum_r), int(nthreads))
+        if rc != 0:
+            raise ValueError("oracle: bad step interval")
+    return res
+
+
+def ray_segments(bundle, grid, rid: int, chi_a: float, chi_b: float) -> np.ndarray:
+    """Rows (chiA, chiB, cell_x, cell_y, cell_z) of one ray's segments."""
+    b, g = _bundle(bundle), _grid(grid)
+    cap = 1 << 16
+    rows = np.zeros((cap, 5), np.float64)
+    n = _L().ora_ray_segments(C.byref(b), C.byref(g), int(rid), float(chi_a), float(chi_b), _ptr(rows), cap)
+    return rows[: min(n, cap)].copy()
+
+
+def ray_direction(bundle, rid: int):
+    """(n_hat, projection weights of Eqs. n1n1 + n2n2) of one ray."""
+    b = _bundle(bundle)
+    n = np.zeros(3, np.float64)
+    w = np.zeros(6, np.float64)
+    _L().ora_ray_direction(C.byref(b), int(rid), _ptr(n), _ptr(w))
+    return n, w
+
+
+def trace_adjoint(bundle, grid, steps, dL_dkappa, dL_dkborn=None, delta_derived: bool = True):
+    """dL/dPhi at the cell centres (and dL/ddelta when delta is an independent
+    input) for L with the given per-ray derivatives."""
+    nr = int(bundle.nx) * int(bundle.ny)
+    gk = _f64(dL_dkappa).reshape(nr)
+    gb = _f64(dL_dkborn).reshape(nr) if dL_dkborn is not None else None
+    shape = tuple(int(x) for x in grid.n)
+    gH = np.zeros(shape + (6,), np.float64)
+    gd = np.zeros(shape, np.float64)
+    b, g = _bundle(bundle), _grid(grid)
+    for st in steps:
+        _L().ora_trace_step_adjoint(C.byref(b), C.byref(g), float(st.chi_a), float(st.chi_b),
+                                    float(st.scale), float(st.a), _ptr(gk), _ptr(gb), _ptr(gH), _ptr(gd))
+    if delta_derived:
+        _L().ora_delta_from_tidal_adjoint(C.byref(g), _ptr(gd), _ptr(gH))
+    gphi = np.zeros(shape, np.float64)
+    _L().ora_tidal_centres_adjoint(C.byref(g), _ptr(gH), _ptr(gphi))
+    return (gphi, None) if delta_derived else (gphi, gd)

@@ -1,0 +1,248 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the bench.
+
+This module holds none of the ray-tracing arithmetic: it only draws fields,
+describes ray bundles and lays out the per-step schedule that a caller would
+hand to the library. Everything is deterministic in the seed.
+
+Units: comoving Mpc/h for lengths; the potential is Phi/c^2 (dimensionless),
+so that the convergence is kappa = int g(chi_s, chi) Q dchi with no 1/c^2
+prefactor (Eq. kappa of Barreira et al. 2016, with Phi measured in c^2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+#: Hubble distance c/H0 in Mpc/h (H0 = 100 h km/s/Mpc).
+HUBBLE_DISTANCE = 2997.92458
+#: H0/c in h/Mpc.
+H0_OVER_C = 1.0 / HUBBLE_DISTANCE
+
+
+# ---------------------------------------------------------------------------
+# Bundles and grids
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Bundle:
+    """A light bundle: N_x x N_y rays over an opening angle Upsilon_x x Upsilon_y
+    (Sec. 2.4, Eq. txty), observer at ``obs`` in box coordinates (Sec. 2.2),
+    source at comoving distance ``chi_s``."""
+    nx: int
+    ny: int
+    fov_x: float          # radians
+    fov_y: float          # radians
+    obs: tuple            # (x, y, z) in Mpc/h
+    chi_s: float          # Mpc/h
+    interp: int = 1       # 0 = NGP (Eq. Icngp), 1 = trilinear (Eq. Icfinal)
+    periodic: bool = True
+
+    @property
+    def nrays(self) -> int:
+        return self.nx * self.ny
+
+
+@dataclass
+class Grid:
+    """Uniform cubic-cell grid of n[0] x n[1] x n[2] cells, cell size h = box/n[0]."""
+    n: tuple
+    box: float
+    omega_m: float = 0.3
+
+    @property
+    def h(self) -> float:
+        return self.box / self.n[0]
+
+    @property
+    def ncells(self) -> int:
+        return int(self.n[0]) * int(self.n[1]) * int(self.n[2])
+
+
+def deg(x: float) -> float:
+    return x * math.pi / 180.0
+
+
+# ---------------------------------------------------------------------------
+# Fields
+# ---------------------------------------------------------------------------
+
+def _kgrid(n: int, box: float):
+    k1 = 2.0 * np.pi * np.fft.fftfreq(n, d=box / n)
+    kz = 2.0 * np.pi * np.fft.rfftfreq(n, d=box / n)
+    return k1, kz
+
+
+def grf_phi(n: int, box: float, seed: int, omega_m: float = 0.3,
+            spectral_index: float = -3.0, rms_delta: float = 1.0,
+            dtype=np.float32) -> np.ndarray:
+    """Gaussian random potential Phi/c^2 on the n^3 cell centres, [ix][iy][iz]
+    with z fastest, periodic.
+
+    P_Phi(k) = A k^spectral_index for 0 < |k| <= k_Nyq = pi n / box (spherical
+    cut; the Nyquist planes are zeroed). White noise is drawn in real space with
+    numpy's PCG64(seed), transformed, shaped by sqrt(P) and transformed back, all
+    in FP64. The amplitude A makes the continuum density contrast
+    delta = -k^2 Phi / (1.5 Omega_m (H0/c)^2) (comoving Poisson equation at
+    a = 1) have the requested rms. The result is cast to ``dtype`` last.
+    """
+    import scipy.fft as sfft
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    white = rng.standard_normal((n, n, n))
+    wk = sfft.rfftn(white, workers=-1)
+    del white
+    k1, kz = _kgrid(n, box)
+    kx = k1[:, None, None]
+    ky = k1[None, :, None]
+    kzz = kz[None, None, :]
+    k2 = kx * kx + ky * ky + kzz * kzz
+    knyq = math.pi * n / box
+    shape = np.zeros_like(k2)
+    live = (k2 > 0) & (k2 <= knyq * knyq)
+    shape[live] = np.sqrt(k2[live]) ** (0.5 * spectral_index)
+    # zero the Nyquist planes so the field is exactly real-symmetric
+    if n % 2 == 0:
+        shape[n // 2, :, :] = 0.0
+        shape[:, n // 2, :] = 0.0
+        shape[:, :, -1] = 0.0
+    wk *= shape
+    phi = sfft.irfftn(wk, s=(n, n, n), workers=-1)
+    dk = sfft.irfftn(-k2 * wk, s=(n, n, n), workers=-1)
+    del wk
+    pref = 1.5 * omega_m * H0_OVER_C ** 2
+    rms = float(np.sqrt(np.mean((dk / pref) ** 2)))
+    phi *= rms_delta / rms
+    return np.ascontiguousarray(phi.astype(dtype, copy=False))
+
+
+def gaussian_phi(n: int, box: float, amp: float, sigma: float,
+                 centre=None, dtype=np.float64) -> np.ndarray:
+    """Gaussian potential A exp(-r^2 / 2 sigma^2) sampled at cell centres
+    (Eq. gaussian, Sec. 4)."""
+    h = box / n
+    c = np.full(3, box / 2.0) if centre is None else np.asarray(centre, float)
+    x = (np.arange(n) + 0.5) * h
+    dx = (x - c[0])[:, None, None]
+    dy = (x - c[1])[None, :, None]
+    dz = (x - c[2])[None, None, :]
+    r2 = dx * dx + dy * dy + dz * dz
+    return np.ascontiguousarray((amp * np.exp(-r2 / (2.0 * sigma * sigma))).astype(dtype))
+
+
+def random_field(n, seed, dtype=np.float64, scale=1.0) -> np.ndarray:
+    """White-noise field (tiny parity cases and adjoint probes)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if isinstance(n, int):
+        n = (n, n, n)
+    return np.ascontiguousarray((scale * rng.standard_normal(tuple(n))).astype(dtype))
+
+
+# ---------------------------------------------------------------------------
+# Background cosmology for the per-step schedule (flat LCDM)
+# ---------------------------------------------------------------------------
+
+def _E(z, omega_m):
+    return math.sqrt(omega_m * (1.0 + z) ** 3 + (1.0 - omega_m))
+
+
+def chi_of_z(z: float, omega_m: float = 0.3) -> float:
+    """Comoving distance c int_0^z dz/H(z) in Mpc/h (Sec. 2.2)."""
+    from scipy.integrate import quad
+    val, _ = quad(lambda zz: 1.0 / _E(zz, omega_m), 0.0, z, epsabs=0, epsrel=1e-13, limit=200)
+    return HUBBLE_DISTANCE * val
+
+
+def z_of_chi(chi: float, omega_m: float = 0.3) -> float:
+    from scipy.optimize import brentq
+    if chi <= 0:
+        return 0.0
+    return brentq(lambda z: chi_of_z(z, omega_m) - chi, 0.0, 20.0, xtol=1e-15, rtol=1e-15)
+
+
+def growth(a: float, omega_m: float = 0.3) -> float:
+    """Linear growth factor D(a) of flat LCDM, normalised to D(1) = 1:
+    D(a) propto H(a) int_0^a da' / (a' H(a'))^3."""
+    from scipy.integrate import quad
+
+    def unnorm(aa):
+        if aa <= 0:
+            return 0.0
+        e = math.sqrt(omega_m / aa ** 3 + (1.0 - omega_m))
+        val, _ = quad(lambda x: 1.0 / (x * math.sqrt(omega_m / x ** 3 + (1.0 - omega_m))) ** 3,
+                      0.0, aa, epsabs=0, epsrel=1e-12, limit=200)
+        return e * val
+
+    return unnorm(a) / unnorm(1.0)
+
+
+@dataclass
+class Step:
+    chi_a: float     # far end (the step starts here; chi decreases)
+    chi_b: float     # near end
+    scale: float     # multiplies every channel of the field for this step
+    a: float         # scale factor held constant over the step
+
+
+def step_schedule(chi_s: float, nsteps: int, omega_m: float = 0.3,
+                  rescale: bool = True) -> list:
+    """Equal-Delta-a steps between a(chi_s) and 1. Each step covers the distance
+    light travels during it, [chi_a, chi_b) with chi_a > chi_b (Sec. 2.5.2).
+    The field of a step is Phi_k = s_k Phi with s_k = D(a_k)/a_k (comoving
+    Poisson: Phi propto delta/a), a_k taken at the step's far end, when the
+    N-body code computed the field. With rescale=False every s_k = 1 and a_k = 1.
+    """
+    a_src = 1.0 / (1.0 + z_of_chi(chi_s, omega_m))
+    a_edges = np.linspace(a_src, 1.0, nsteps + 1)
+    chis = [chi_s] + [chi_of_z(1.0 / a - 1.0, omega_m) for a in a_edges[1:-1]] + [0.0]
+    steps = []
+    for k in range(nsteps):
+        ak = float(a_edges[k])
+        if rescale:
+            s = growth(ak, omega_m) / ak
+            steps.append(Step(chis[k], chis[k + 1], s, ak))
+        else:
+            steps.append(Step(chis[k], chis[k + 1], 1.0, 1.0))
+    return steps
+
+
+# ---------------------------------------------------------------------------
+# The workloads (sizes as the paper's experiments and the production setup)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    grid: Grid
+    bundle: Bundle
+    nsteps: int
+    seed: int
+    rescale: bool = False
+    notes: str = ""
+
+
+def workload(name: str) -> Workload:
+    """Named synthetic workloads.
+
+    small_64: 64^3 GRF, box 256 Mpc/h, 128x128 rays over 2x2 deg, chi_s = 256,
+        one step, observer at the centre of the z = 0 face.
+    prod_512: 512^3 FP32 GRF, box 1024 Mpc/h, 2048x2048 rays over 10x10 deg,
+        chi_s = 1000, 40 steps of equal Delta a with Phi rescaled by D(a)/a
+        (flat LCDM, Omega_m = 0.3).
+    adjoint_256: 256^3 GRF, box 512, 1024x1024 rays over 5x5 deg, chi_s = 512,
+        one step.
+    """
+    if name == "small_64":
+        g = Grid((64, 64, 64), 256.0)
+        b = Bundle(128, 128, deg(2.0), deg(2.0), (128.0, 128.0, 0.0), 256.0)
+        return Workload(name, g, b, 1, 1)
+    if name == "prod_512":
+        g = Grid((512, 512, 512), 1024.0)
+        b = Bundle(2048, 2048, deg(10.0), deg(10.0), (512.0, 512.0, 0.0), 1000.0)
+        return Workload(name, g, b, 40, 2, rescale=True)
+    if name == "adjoint_256":
+        g = Grid((256, 256, 256), 512.0)
+        b = Bundle(1024, 1024, deg(5.0), deg(5.0), (256.0, 256.0, 0.0), 512.0)
+        return Workload(name, g, b, 1, 5)
+    raise KeyError(name)
