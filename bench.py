@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the line-of-sight convergence tracer on one GB300 (or N).
+
+One benchmark step is one pass of the whole hot path over one lightcone of
+the production workload: 512^3 FP32 potential (Gaussian random field, P(k)
+propto k^-3, rms delta = 1), box 1024 Mpc/h, 2048 x 2048 rays over 10 x 10
+deg to chi_s = 1000 Mpc/h, integrated in 40 steps of equal Delta a with the
+field rescaled by D(a)/a. Per step: the tidal records of the step's footprint
+(rr_tidal_tensor), the cell-by-cell trace (rr_trace_step); then rr_finalize.
+Inputs are resident in HBM when the timed region starts; L2 is flushed
+between timed passes.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU
+oracle instead, on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = ("cell-segments/s and κ-map rays/s at 1 GB300, HBM roofline %, error vs FP64 oracle")
+UNIT = "cell-segments/s"
+# per trilinear segment the trace gathers 8 vertex records of 32 B (logical bytes)
+BYTES_PER_SEGMENT = 256
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM traffic of one trace launch from an ncu capture, valid only for the
+# kernel source it was taken on (sha256 of csrc/trace.cu). Empty until measured.
+TRACE_TRAFFIC = {}
+
+
+def _src_hash(name):
+    p = os.path.join(ROOT, "paper_1601_02012_gb300", "csrc", name)
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _config(w, nsteps):
+    return {
+        "workload": w.name,
+        "grid": list(w.grid.n),
+        "box_mpc_h": w.grid.box,
+        "rays": [w.bundle.nx, w.bundle.ny],
+        "fov_deg": round(w.bundle.fov_x * 180 / math.pi, 6),
+        "chi_s": w.bundle.chi_s,
+        "nsteps": nsteps,
+        "interp": "trilinear" if w.bundle.interp == 1 else "ngp",
+        "field": "GRF P(k)~k^-3, rms delta 1, FP32, rescaled by D(a)/a per step",
+        "l2": "flushed between timed passes (256 MiB write); per-pass working set > L2",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.dev = device_id
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.dev is not None:
+                cmd += ["-i", str(self.dev)]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _device_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or None
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_fields(grid, phi32):
+    import oracle
+    oracle.build()
+    return oracle.fields(grid, phi32.astype(np.float64))
+
+
+def _oracle_sample(bundle, grid, H, d, steps, rids, threads):
+    import oracle
+    t0 = time.perf_counter()
+    res = oracle.trace(bundle, grid, H, d, steps, nthreads=threads, rids=rids)
+    return res, time.perf_counter() - t0
+
+
+def run_reference(args, w, steps):
+    """--impl reference: the FP64 oracle on the host cores; each step traces a
+    bounded random sample of the workload's rays through all its N-body steps."""
+    threads = os.cpu_count() or 1
+    phi = synth.grf_phi_cached(w.grid.n[0], w.grid.box, w.seed)
+    H, d = _oracle_fields(w.grid, phi)
+    rng = np.random.default_rng(1234)
+    sample = 512
+    for it in range(args.warmup):
+        rids = rng.choice(w.bundle.nrays, sample, replace=False)
+        _, dt = _oracle_sample(w.bundle, w.grid, H, d, steps, rids, threads)
+        if it == 0 and dt > 0:   # size the sample for ~6 s per step
+            sample = int(min(w.bundle.nrays, max(64, sample * 6.0 / dt)))
+    times, segs = [], 0
+    for _ in range(args.steps):
+        rids = rng.choice(w.bundle.nrays, sample, replace=False)
+        res, dt = _oracle_sample(w.bundle, w.grid, H, d, steps, rids, threads)
+        times.append(dt)
+        segs += int(res.nseg.sum())
+    total = sum(times)
+    value = segs / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(w, len(steps)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} random rays of the 2048x2048 bundle per step, all {len(steps)} "
+                                   "N-body steps; tidal centres of the 512^3 grid computed once before timing"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="prod_512")
+    ap.add_argument("--fp64-dda", action="store_true", help="plain FP64 walk instead of the FP32 form")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = synth.workload(args.workload)
+    steps = synth.step_schedule(w.bundle.chi_s, w.nsteps, rescale=w.rescale) if w.nsteps > 1 else \
+        [synth.Step(w.bundle.chi_s, 0.0, 1.0, 1.0)]
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, w, steps)
+        return
+
+    import torch
+    import paper_1601_02012_gb300 as rrp
+    from paper_1601_02012_gb300 import build as rrbuild
+
+    rrbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    # each rank traces its own lightcone (its own field realisation): no data-path collective
+    seed = w.seed + 1000 * rank
+    phi_host = synth.grf_phi_cached(w.grid.n[0], w.grid.box, seed)
+    stream = torch.cuda.Stream(device=dev)
+    phi = torch.from_numpy(phi_host).to(dev)
+    rec = rrp.record_buffer(w.grid, device=dev)
+    tr = rrp.Tracer(w.bundle, fp64_dda=args.fp64_dda)
+    gd = rrp.grid_desc(w.grid)
+    bboxes = [tr.footprint(w.grid, st.chi_a, st.chi_b) for st in steps]
+    kappa = torch.empty((w.bundle.ny, w.bundle.nx), dtype=torch.float64, device=dev)
+    kborn = torch.empty_like(kappa)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    nst = len(steps)
+    ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+    ev_td = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+
+    def one_pass(src=None, timed_kernels=False):
+        rrp.rr_reset(tr.ctx, stream)
+        field = phi if src is None else src
+        for i, st in enumerate(steps):
+            if timed_kernels:
+                ev_td[i][0].record(stream)
+            rrp.rr_tidal_tensor(gd, field, None, rec, tr.where, bboxes[i], stream)
+            if timed_kernels:
+                ev_td[i][1].record(stream)
+                ev_tr[i][0].record(stream)
+            rrp.rr_trace_step(tr.ctx, gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            if timed_kernels:
+                ev_tr[i][1].record(stream)
+        rrp.rr_finalize(tr.ctx, kappa, kborn, stream)   # synchronises the stream
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_pass()
+        segs = tr.segments()
+
+        sampler = ClockSampler(_device_id(torch, dev))
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        times, trace_ms, tidal_ms = [], 0.0, 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_pass(timed_kernels=True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            trace_ms += sum(a.elapsed_time(b) for a, b in ev_tr)
+            tidal_ms += sum(a.elapsed_time(b) for a, b in ev_td)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        total_ms = sum(times)
+        if dist is not None:
+            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            s = torch.tensor([segs], dtype=torch.float64, device=dev)
+            dist.all_reduce(s)
+            segs_all = int(s.item())
+        else:
+            segs_all = segs
+
+        # end to end through the public API with host buffers: H2D of the
+        # potential from pinned memory, the pass, D2H of both maps
+        phi_pinned = torch.from_numpy(phi_host).pin_memory()
+        k_host = torch.empty(kappa.shape, dtype=torch.float64).pin_memory()
+        kb_host = torch.empty_like(k_host).pin_memory()
+        phi_dev2 = torch.empty_like(phi)
+        e2e_times = []
+        for it in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            phi_dev2.copy_(phi_pinned, non_blocking=True)
+            one_pass(src=phi_dev2)
+            k_host.copy_(kappa, non_blocking=True)
+            kb_host.copy_(kborn, non_blocking=True)
+            stream.synchronize()
+            if it >= args.warmup:
+                e2e_times.append(time.perf_counter() - t0)
+        e2e_s = sum(e2e_times)
+        if dist is not None:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+
+    if rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = _peaks()
+    per_pass_trace_s = trace_ms / args.steps / 1e3
+    achieved = segs * BYTES_PER_SEGMENT / per_pass_trace_s / 1e9
+    tidal_points = sum((b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]) for b in bboxes)
+    h = _src_hash("trace.cu")
+    traffic = TRACE_TRAFFIC.get(h)
+    value = segs_all * args.steps / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(w, nst) | {"form": "fp64 walk" if args.fp64_dda else "fp32 walk, Kahan sums",
+                                      "parallelism": f"{world} independent lightcones, one per GPU"},
+        "rays_per_s": world * w.bundle.nrays * args.steps / (total_ms / 1e3),
+        "segments_per_step": segs_all,
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": "trace_kernel<trilinear,float>",
+            "note": f"logical gather bytes: {BYTES_PER_SEGMENT} B per segment (8 vertex records) "
+                    f"x segments per launch / mean launch time; peak of {peak_kind} copy bandwidth",
+        },
+        "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps,
+                                "tidal_points_per_step": tidal_points},
+        "tidal_roofline": {"bound": "hbm", "achieved": tidal_points * 36 / (tidal_ms / args.steps / 1e3) / 1e9,
+                           "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "note": "36 B per point (4 B potential read, 32 B record written)"},
+        "e2e": {"value": segs_all * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(phi_host.nbytes),
+                "d2h_bytes_per_step": int(k_host.numel() * 8 * 2)},
+        "gpu_launches": args.steps * (2 * nst + 1),
+        "clocks": clocks,
+        "trace_src": h,
+    }
+
+    if world == 1 and not args.no_cpu_baseline:
+        # the FP64 oracle on the host cores, on a bounded sample of the same
+        # workload; the sampled rays also give the error of the GPU map
+        threads = os.cpu_count() or 1
+        H, d = _oracle_fields(w.grid, phi_host)
+        rng = np.random.default_rng(4321)
+        rids = rng.choice(w.bundle.nrays, 256, replace=False)
+        res, dt = _oracle_sample(w.bundle, w.grid, H, d, steps, rids, threads)
+        n2 = int(min(w.bundle.nrays, max(256, 256 * 12.0 / max(dt, 1e-3))))
+        rids2 = rng.choice(w.bundle.nrays, n2, replace=False)
+        res2, dt2 = _oracle_sample(w.bundle, w.grid, H, d, steps, rids2, threads)
+        line["cpu_baseline"] = {
+            "value": float(res2.nseg.sum()) / dt2, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n2} random rays of the bundle through all {nst} steps ({dt2:.1f} s); "
+                      "tidal centres of the full grid computed once outside the timing"}
+        kg = kappa.cpu().numpy().ravel()
+        kbg = kborn.cpu().numpy().ravel()
+        allr = np.concatenate([rids, rids2])
+        ko = np.concatenate([res.kappa, res2.kappa])
+        kbo = np.concatenate([res.kborn, res2.kborn])
+        rms, rmsb = math.sqrt(float(np.mean(ko ** 2))), math.sqrt(float(np.mean(kbo ** 2)))
+        line["error_vs_oracle"] = {
+            "rays": int(len(allr)),
+            "kappa_max_over_rms": float(np.abs(kg[allr] - ko).max() / rms),
+            "kborn_max_over_rms": float(np.abs(kbg[allr] - kbo).max() / rmsb),
+            "segments_per_ray_gpu": segs / w.bundle.nrays,
+            "segments_per_ray_oracle": float(np.concatenate([res.nseg, res2.nseg]).mean()),
+        }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * rr.h -- C ABI of the GB300 line-of-sight convergence tracer.
+ *
+ * The library integrates the weak-lensing convergence kappa (Eq. kappa of
+ * Barreira, Llinares, Bose & Li 2016, "RAY-RAMSES", arXiv:1601.02012) and the
+ * density-based Born convergence (first term of Eq. kappa2) cell by cell
+ * along straight rays through a periodic uniform grid (Secs. 2.4-2.6, 3.2-3.4).
+ *
+ * Conventions for every call:
+ *  - Units: lengths in comoving Mpc/h; the potential is Phi/c^2, so that
+ *    kappa = int g(chi_s, chi) Q dchi with g = (chi_s - chi) chi / chi_s.
+ *  - 3D arrays are row-major [ix][iy][iz] (z fastest), cell (i,j,k) spans
+ *    [ih, (i+1)h) x ...; vertex (i,j,k) sits at (ih, jh, kh); indices wrap
+ *    periodically (vertex n is vertex 0).
+ *  - Device pointers are caller-owned (allocated by the caller, e.g. torch);
+ *    the library never frees or reallocates them. The only memory the
+ *    library allocates itself is the per-ray state owned by an rr_ctx.
+ *  - Calls that take a stream enqueue their work on it asynchronously and
+ *    return at once, except where stated. `stream` is a cudaStream_t passed
+ *    as void* (NULL = the legacy default stream).
+ *  - Errors are returned as rr_status codes; nothing is thrown across the
+ *    ABI. Device-side failures (iteration cap, non-finite sums) are recorded
+ *    in a per-context error word and reported by rr_finalize / rr_sync_status.
+ *  - A context is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RR_OK = 0,
+    RR_ERR_ARG = -1,        /* invalid argument (null pointer, size, interval) */
+    RR_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    RR_ERR_OOM = -3,        /* device allocation failed */
+    RR_ERR_STEP_LIMIT = -4, /* a ray exceeded its per-step iteration cap */
+    RR_ERR_STATE = -5,      /* calls out of order (e.g. a gap between steps) */
+    RR_ERR_NONFINITE = -6   /* a per-ray sum became NaN or infinite */
+} rr_status;
+
+/* rr_bundle_desc.interp: how Q varies inside a cell (Sec. 2.6). */
+enum { RR_NGP = 0,          /* constant centre value, Eq. (Icngp) / (Iclensing_ngp) */
+       RR_TRILINEAR = 1 };  /* trilinear from the 8 vertices, Eq. (Icfinal) / (Iclensing) */
+
+/* rr_bundle_desc.flags */
+enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box faces */
+       RR_FP64_DDA = 2 };   /* plain form: cell walk, kernel integrals and per-step
+                               sums in FP64 (default: FP32 walk in cell-local
+                               coordinates with compensated FP32 sums) */
+
+/* rr_tidal_tensor: where the records are evaluated. */
+enum { RR_AT_VERTICES = 0,  /* mean of the 8 cells sharing each vertex (Sec. 2.7); trilinear */
+       RR_AT_CENTRES = 1 }; /* the cell-centre values themselves; NGP */
+
+/*
+ * A light bundle (Sec. 2.4): N_x x N_y rays at the angles of Eq. (txty),
+ *   theta_a = Upsilon_a / (N_a - 1) * (i_a - 1) - Upsilon_a / 2,
+ * read on the flat sky as theta = sqrt(theta_x^2 + theta_y^2),
+ * phi = atan2(theta_y, theta_x), direction n = (sin th cos ph, sin th sin ph,
+ * cos th) (Eq. raypos); N_a = 1 puts the single ray at theta_a = 0. The ray
+ * of pixel (i_x, i_y) has id (i_y - 1) N_x + (i_x - 1) (Eq. rayid, x fastest).
+ * Light travels from chi_s towards the observer, i.e. along -n.
+ */
+typedef struct {
+    int32_t nx, ny;       /* rays per side, >= 1 */
+    double fov_x, fov_y;  /* Upsilon_x, Upsilon_y in radians, [0, pi) */
+    double obs[3];        /* observer position in box coordinates, Mpc/h */
+    double chi_s;         /* comoving distance of the sources, > 0 */
+    int32_t interp;       /* RR_NGP or RR_TRILINEAR */
+    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA */
+} rr_bundle_desc;
+
+/* A uniform grid of n[0] x n[1] x n[2] cubic cells of size h = box / n[0]. */
+typedef struct {
+    int32_t n[3];         /* each in [2, 4096] */
+    double box;           /* extent along x in Mpc/h, > 0 */
+    double omega_m;       /* matter density parameter, for the Born prefactor and derived delta */
+} rr_grid_desc;
+
+typedef struct rr_ctx rr_ctx;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* rr_status_string(rr_status s);
+
+/*
+ * Create a tracing context for one bundle on the current CUDA device: device
+ * per-ray state (direction, FP64 accumulators of kappa and Born kappa, segment
+ * counter) and an error word, all zeroed. Synchronous. *out receives the
+ * handle. RR_ERR_ARG on an invalid bundle, RR_ERR_OOM if the state does not
+ * fit. Initialising the ray directions (Eq. txty, raypos) runs on the device.
+ */
+rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out);
+
+/* Free the context and its device state (synchronises the device first). */
+rr_status rr_destroy(rr_ctx* ctx);
+
+/* Zero the accumulators, the error word and the step log so that a new
+ * sequence of steps can start (asynchronous on `stream`). */
+rr_status rr_reset(rr_ctx* ctx, void* stream);
+
+/*
+ * Tidal tensor d_a d_b Phi by the central differences of Eq. (tidalexample)
+ * at the cell centres (periodic), then records at the vertices (mean of the
+ * 8 cells sharing a vertex, Sec. 2.7) or at the centres.
+ *   phi    device, n0*n1*n2 floats, Phi/c^2 at cell centres.
+ *   delta  device, n0*n1*n2 floats, or NULL: the density contrast. When NULL
+ *          it is derived from the same stencils through the comoving Poisson
+ *          equation at a = 1: delta = tr(H) / (1.5 Omega_m (H0/c)^2).
+ *   rec    device, n0*n1*n2 records of 8 floats (32 bytes, 16-byte aligned):
+ *          {Hxx, Hyy, Hzz, Hxy}, {Hxz, Hyz, delta, 0}, H in (h/Mpc)^2.
+ *   where  RR_AT_VERTICES or RR_AT_CENTRES.
+ *   bbox   NULL for the whole grid, else 6 ints {x0, x1, y0, y1, z0, z1}:
+ *          only points with x0 <= i < x1 (etc.) are written, indices taken
+ *          modulo n (x0 may be negative); x1 - x0 must lie in [1, n0].
+ * RR_ERR_ARG on a null/misaligned pointer or a bad box.
+ */
+rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                          int32_t where, const int32_t* bbox, void* stream);
+
+/*
+ * Host helper: a conservative box of vertex (or centre) indices {x0, x1, y0,
+ * y1, z0, z1} that contains every point the bundle's rays can read while
+ * tracing [chi_b, chi_a] (the footprint of one step, used to restrict
+ * rr_tidal_tensor). Pure host arithmetic, no device work.
+ */
+rr_status rr_footprint_bbox(const rr_bundle_desc* bundle, const rr_grid_desc* grid, double chi_a,
+                            double chi_b, int32_t bbox[6]);
+
+/*
+ * Advance every ray of the bundle from chi_a down to chi_b (one N-body step,
+ * Sec. 2.5.2), integrating cell by cell (Sec. 2.5.1, 2.6):
+ *   kappa      += scale * sum_cells I_c with Q = n1n1 + n2n2 (Eqs. n1n1, n2n2,
+ *                 Iclensing or Iclensing_ngp),
+ *   kappa_born += scale * sum_cells I_c with Q = 1.5 Omega_m (H0/c)^2 delta / a_step
+ *                 (first term of Eq. kappa2, a held constant over the step).
+ *   rec      records from rr_tidal_tensor (vertices for RR_TRILINEAR,
+ *            centres for RR_NGP) covering every point the step reads.
+ *   scale    multiplies every channel of the records (the field of this step
+ *            is scale * stored field).
+ * Requires chi_s >= chi_a > chi_b >= 0 and, after the first step since
+ * create/reset, chi_a equal to the previous step's chi_b (RR_ERR_STATE
+ * otherwise). The step is appended to the context's step log.
+ */
+rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a,
+                        double chi_b, double scale, double a_step, void* stream);
+
+/*
+ * Write the maps in rayid order (x fastest): kappa[ny*nx] and, if not NULL,
+ * kappa_born[ny*nx], both device FP64. Also totals the per-ray segment
+ * counters. Synchronises `stream` and returns the context's error word:
+ * RR_ERR_STEP_LIMIT or RR_ERR_NONFINITE if a device-side check failed during
+ * any step since create/reset, else RR_OK.
+ */
+rr_status rr_finalize(rr_ctx* ctx, double* kappa, double* kappa_born, void* stream);
+
+/* Synchronise `stream` and return the error word (as rr_finalize does),
+ * without writing maps. */
+rr_status rr_sync_status(rr_ctx* ctx, void* stream);
+
+/*
+ * Number of non-empty cell segments traversed by all rays since
+ * create/reset, as totalled by the last rr_finalize (host value). If
+ * per_ray is not NULL it is a device uint32[ny*nx] that receives the per-ray
+ * counts (asynchronous on `stream`).
+ */
+rr_status rr_segment_count(rr_ctx* ctx, uint64_t* total, uint32_t* per_ray, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RR_H */

@@ -54,7 +54,7 @@ def _L():
         _lib.ora_delta_from_tidal.argtypes = [P, P, P]
         _lib.ora_vertex_field.argtypes = [P, P, P, P]
         _lib.ora_trace_step.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
-                                        P, P, P, P, C.c_int]
+                                        P, P, P, P, C.c_int, P, C.c_long]
         _lib.ora_ray_segments.argtypes = [P, P, C.c_long, C.c_double, C.c_double, P, C.c_long]
         _lib.ora_ray_segments.restype = C.c_long
         _lib.ora_ray_direction.argtypes = [P, C.c_long, P, P]
@@ -141,19 +141,23 @@ class TraceResult:
         self.sum_r = np.zeros(nr, np.float64)
 
 
-def trace(bundle, grid, H, delta, steps, nthreads: int = 0, result: TraceResult | None = None) -> TraceResult:
-    """Trace every ray of the bundle over the given steps (objects with chi_a,
+def trace(bundle, grid, H, delta, steps, nthreads: int = 0, result: TraceResult | None = None,
+          rids=None) -> TraceResult:
+    """Trace the rays of the bundle over the given steps (objects with chi_a,
     chi_b, scale, a). Returns per-ray kappa, Born kappa, segment count and the
-    summed segment lengths, in rayid order (x fastest)."""
+    summed segment lengths, in rayid order (x fastest), or in the order of
+    ``rids`` when only those ray ids are traced."""
     H = _f64(H)
     delta = _f64(delta)
-    nr = int(bundle.nx) * int(bundle.ny)
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
     res = result if result is not None else TraceResult(nr)
     b, g = _bundle(bundle), _grid(grid)
     for st in steps:
         rc = _L().ora_trace_step(C.byref(b), C.byref(g), _ptr(H), _ptr(delta), float(st.chi_a),
                                  float(st.chi_b), float(st.scale), float(st.a), _ptr(res.kappa),
-                                 _ptr(res.kborn), _ptr(res.nseg), _ptr(res.sum_r), int(nthreads))
+                                 _ptr(res.kborn), _ptr(res.nseg), _ptr(res.sum_r), int(nthreads),
+                                 _ptr(ids), 0 if ids is None else len(ids))
         if rc != 0:
             raise ValueError("oracle: bad step interval")
     return res

@@ -13,7 +13,8 @@
  *   - vertex values as the mean of the 8 cells sharing the vertex
  *     (Sec. 2.7, regular-mesh vertices), evaluated on the fly;
  *   - ray directions from Eq. (txty) with theta = sqrt(tx^2 + ty^2),
- *     phi = atan2(ty, tx) (flat-sky polar reading of Eq. raypos);
+ *     phi = atan2(ty, tx), i.e. (cos phi, sin phi) = (tx, ty) / theta
+ *     (flat-sky polar reading of Eq. raypos);
  *   - the cells a ray crosses between chi_a and chi_b by merging the
  *     per-axis lists of face-crossing distances (the cell-by-cell walk of
  *     Sec. 2.5.1, written as an exact FP64 crossing list);
@@ -158,21 +159,30 @@ int ora_vertex_field(const ora_grid* g, const double* H, const double* delta, do
 /* Ray geometry: Eq. (txty), Eq. (rayid), Eq. (raypos)                       */
 /* ------------------------------------------------------------------------- */
 
-/* ix, iy are 0-based, i.e. i_x - 1 and i_y - 1 of Eq. (txty). */
-static void ray_angles(const ora_bundle* b, long ix, long iy, double* theta, double* varphi)
+/* Eq. (txty) for 0-based ix = i_x - 1, written as (2 ix - (N - 1)) U / (2 (N - 1))
+ * so that the central pixel of an odd row sits at theta_a = 0 exactly. */
+static double pixel_angle(double fov, long n, long i)
 {
-    double tx = b->nx > 1 ? b->fov_x / (double)(b->nx - 1) * (double)ix - 0.5 * b->fov_x : 0.0;
-    double ty = b->ny > 1 ? b->fov_y / (double)(b->ny - 1) * (double)iy - 0.5 * b->fov_y : 0.0;
+    return n > 1 ? (double)(2 * i - (n - 1)) * (fov / (2.0 * (double)(n - 1))) : 0.0;
+}
+
+/* theta = sqrt(tx^2 + ty^2) and the polar angle phi = atan2(ty, tx), returned as
+ * (sin phi, cos phi) = (ty, tx) / theta (phi = 0 at theta = 0). */
+static void ray_angles(const ora_bundle* b, long ix, long iy, double* theta, double* sphi, double* cphi)
+{
+    double tx = pixel_angle(b->fov_x, b->nx, ix);
+    double ty = pixel_angle(b->fov_y, b->ny, iy);
     *theta = sqrt(tx * tx + ty * ty);
-    *varphi = (*theta > 0.0) ? atan2(ty, tx) : 0.0;
+    *sphi = (*theta > 0.0) ? ty / *theta : 0.0;
+    *cphi = (*theta > 0.0) ? tx / *theta : 1.0;
 }
 
 /* Eq. (n1n1) + Eq. (n2n2): the transverse Laplacian seen by a ray with
  * direction angles (theta, phi). H = {xx, yy, zz, xy, xz, yz}. */
-static void kappa_weights(double th, double ph, double w[6])
+static void kappa_weights(double th, double sp, double cp, double w[6])
 {
-    double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
-    double s2p = sin(2.0 * ph), s2t = sin(2.0 * th);
+    double st = sin(th), ct = cos(th);
+    double s2p = 2.0 * sp * cp, s2t = sin(2.0 * th);
     /* n1n1 = sin^2(ph) xx + cos^2(ph) yy - sin(2ph) xy */
     /* n2n2 = cos^2(ph) cos^2(th) xx + sin^2(ph) cos^2(th) yy + sin^2(th) zz
      *        + sin(2ph) cos^2(th) xy - sin(ph) sin(2th) yz - cos(ph) sin(2th) xz */
@@ -298,20 +308,20 @@ static double ic_trilinear(const double Q[8], double a, double b, double c, doub
 
 /* A ray's geometry. */
 typedef struct {
-    double th, ph, st, ct, sp, cp;
+    double th, st, ct, sp, cp;
     double n[3];
     double w[6];
 } ray_geo;
 
 static void make_ray(const ora_bundle* b, long ix, long iy, ray_geo* r)
 {
-    ray_angles(b, ix, iy, &r->th, &r->ph);
-    r->st = sin(r->th); r->ct = cos(r->th); r->sp = sin(r->ph); r->cp = cos(r->ph);
+    ray_angles(b, ix, iy, &r->th, &r->sp, &r->cp);
+    r->st = sin(r->th); r->ct = cos(r->th);
     /* Eq. (raypos) */
     r->n[0] = r->st * r->cp;
     r->n[1] = r->st * r->sp;
     r->n[2] = r->ct;
-    kappa_weights(r->th, r->ph, r->w);
+    kappa_weights(r->th, r->sp, r->cp, r->w);
 }
 
 /* Callback-free walk: for each non-empty segment, evaluate the two integrands
@@ -385,18 +395,21 @@ static void cell_vertex_Q(const field_t* F, const ray_geo* r, const long cell[3]
  */
 int ora_trace_step(const ora_bundle* b, const ora_grid* g, const double* H, const double* delta,
                    double chi_a, double chi_b, double scale, double a_step,
-                   double* kappa, double* kborn, int64_t* nseg, double* sum_r, int nthreads)
+                   double* kappa, double* kborn, int64_t* nseg, double* sum_r, int nthreads,
+                   const int64_t* rids, long nrids)
 {
     if (!(chi_a > chi_b) || chi_b < 0.0) return -1;
     field_t F = {g, b, H, delta};
     const double bpref = 1.5 * g->omega_m * ORA_H0_OVER_C * ORA_H0_OVER_C / a_step;
     const double h = grid_h(g);
-    const long nr = (long)b->nx * b->ny;
+    /* all rays, or only the listed ray ids (outputs then follow the list) */
+    const long nr = rids ? nrids : (long)b->nx * b->ny;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
-    for (long rid = 0; rid < nr; ++rid) {
+    for (long slot = 0; slot < nr; ++slot) {
+        const long rid = rids ? (long)rids[slot] : slot;
         ray_geo r;
         make_ray(b, rid % b->nx, rid / b->nx, &r); /* Eq. (rayid), x fastest */
         segment_t* S;
@@ -422,10 +435,10 @@ int ora_trace_step(const ora_bundle* b, const ora_grid* g, const double* H, cons
             neu_add(&sr, sg->chiA - sg->chiB);
         }
         free(S);
-        kappa[rid] += scale * neu_val(&sk);
-        kborn[rid] += scale * neu_val(&sb);
-        if (nseg) nseg[rid] += ns;
-        if (sum_r) sum_r[rid] += neu_val(&sr);
+        kappa[slot] += scale * neu_val(&sk);
+        kborn[slot] += scale * neu_val(&sb);
+        if (nseg) nseg[slot] += ns;
+        if (sum_r) sum_r[slot] += neu_val(&sr);
     }
     return 0;
 }

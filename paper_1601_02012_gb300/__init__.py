@@ -1,0 +1,102 @@
+"""GB300-native line-of-sight convergence tracer (RAY-RAMSES hot path).
+
+The computation lives in librr.so (hand-written sm_103a CUDA behind the C ABI
+of include/rr.h). This package is a thin Python layer over it: ``_rr`` binds
+the C entry points one to one; ``Tracer`` and ``trace_kappa`` marshal torch
+tensors into them. PyTorch only provides device memory and streams.
+"""
+from __future__ import annotations
+
+from . import _rr
+from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, bundle_desc, grid_desc,
+                  rr_create, rr_destroy, rr_finalize, rr_footprint_bbox, rr_reset, rr_segment_count,
+                  rr_status_string, rr_sync_status, rr_tidal_tensor, rr_trace_step)
+
+__all__ = [
+    "Tracer", "trace_kappa", "record_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
+    "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
+    "rr_segment_count", "rr_status_string", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
+]
+
+
+def record_buffer(grid, device="cuda"):
+    """Uninitialised device buffer for n0*n1*n2 records of 8 floats."""
+    import torch
+    n = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
+    return torch.empty((n, 8), dtype=torch.float32, device=device)
+
+
+class Tracer:
+    """One ray bundle's device state (an rr_ctx) plus the calls that advance it.
+
+    bundle: object with nx, ny, fov_x, fov_y (radians), obs (3), chi_s, interp
+    (0 NGP / 1 trilinear) and periodic attributes.
+    """
+
+    def __init__(self, bundle, fp64_dda: bool = False):
+        _rr.load()
+        self.bundle = bundle
+        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda)
+        self.ctx = rr_create(self.desc)
+        self.where = RR_AT_VERTICES if int(self.desc.interp) == RR_TRILINEAR else RR_AT_CENTRES
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            rr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        rr_reset(self.ctx, stream)
+
+    def tidal(self, grid, phi, rec, delta=None, bbox=None, stream=None):
+        """rr_tidal_tensor into ``rec`` at vertices (trilinear) or centres (NGP)."""
+        rr_tidal_tensor(grid_desc(grid), phi, delta, rec, self.where, bbox, stream)
+        return rec
+
+    def footprint(self, grid, chi_a, chi_b):
+        return rr_footprint_bbox(self.desc, grid_desc(grid), chi_a, chi_b)
+
+    def step(self, grid, rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):
+        rr_trace_step(self.ctx, grid_desc(grid), rec, chi_a, chi_b, scale, a, stream)
+
+    def finalize(self, kappa=None, kborn=None, stream=None):
+        """FP64 maps [ny, nx] on the device (rayid order, x fastest)."""
+        import torch
+        ny, nx = int(self.desc.ny), int(self.desc.nx)
+        if kappa is None:
+            kappa = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+        if kborn is None:
+            kborn = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+        rr_finalize(self.ctx, kappa, kborn, stream)
+        return kappa, kborn
+
+    def segments(self, per_ray=None, stream=None) -> int:
+        return rr_segment_count(self.ctx, per_ray, stream)
+
+
+def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=True, stream=None):
+    """Trace a bundle through a sequence of steps on one potential.
+
+    phi: device float32 tensor n0 x n1 x n2 (Phi/c^2 at cell centres).
+    steps: objects with chi_a, chi_b, scale, a (the step's field is scale * Phi).
+    For each step the records are recomputed (restricted to the step's
+    footprint when ``footprint``) and the bundle is advanced; returns the FP64
+    (kappa, kappa_born) maps and the number of cell segments.
+    """
+    tr = Tracer(bundle, fp64_dda=fp64_dda)
+    try:
+        rec = record_buffer(grid, device=phi.device)
+        for st in steps:
+            bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
+            tr.tidal(grid, phi, rec, delta=delta, bbox=bbox, stream=stream)
+            tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
+        k, kb = tr.finalize(stream=stream)
+        return k, kb, tr.segments()
+    finally:
+        tr.close()

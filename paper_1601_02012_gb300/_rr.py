@@ -1,0 +1,186 @@
+"""ctypes binding of librr.so: the C ABI declared in include/rr.h, same names.
+
+Argument marshalling only -- every step of the computation runs in the CUDA
+library. Device buffers may be passed as torch tensors (their data_ptr is
+used) or as raw integer addresses. Streams may be a torch.cuda.Stream, a raw
+cudaStream_t integer, or None for the current torch stream.
+
+Importing this module does not touch the GPU; loading the library fails loudly
+if it has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librr.so")
+
+RR_OK = 0
+RR_ERR_ARG = -1
+RR_ERR_CUDA = -2
+RR_ERR_OOM = -3
+RR_ERR_STEP_LIMIT = -4
+RR_ERR_STATE = -5
+RR_ERR_NONFINITE = -6
+
+RR_NGP = 0
+RR_TRILINEAR = 1
+RR_PERIODIC = 1
+RR_FP64_DDA = 2
+RR_AT_VERTICES = 0
+RR_AT_CENTRES = 1
+
+
+class rr_bundle_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("fov_x", C.c_double), ("fov_y", C.c_double),
+                ("obs", C.c_double * 3), ("chi_s", C.c_double), ("interp", C.c_int32), ("flags", C.c_int32)]
+
+
+class rr_grid_desc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("box", C.c_double), ("omega_m", C.c_double)]
+
+
+class RRError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {rr_status_string(code)}")
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load librr.so (built in-tree by paper_1601_02012_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"librr.so is not built ({LIB_PATH}); run paper_1601_02012_gb300.build.build()")
+        lib = C.CDLL(LIB_PATH)
+        P, D, I32 = C.c_void_p, C.c_double, C.c_int32
+        sig = {
+            "rr_status_string": ([C.c_int], C.c_char_p),
+            "rr_create": ([P, C.POINTER(C.c_void_p)], C.c_int),
+            "rr_destroy": ([P], C.c_int),
+            "rr_reset": ([P, P], C.c_int),
+            "rr_tidal_tensor": ([P, P, P, P, I32, P, P], C.c_int),
+            "rr_footprint_bbox": ([P, P, D, D, P], C.c_int),
+            "rr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
+            "rr_finalize": ([P, P, P, P], C.c_int),
+            "rr_sync_status": ([P, P], C.c_int),
+            "rr_segment_count": ([P, C.POINTER(C.c_uint64), P, P], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def rr_status_string(code: int) -> str:
+    return load().rr_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str) -> int:
+    if code != RR_OK:
+        raise RRError(code, where)
+    return code
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return C.c_void_p(x)
+    return C.c_void_p(x.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return C.c_void_p(s)
+    return C.c_void_p(s.cuda_stream)
+
+
+def bundle_desc(b, fp64_dda: bool = False) -> rr_bundle_desc:
+    """rr_bundle_desc from any object with nx, ny, fov_x, fov_y, obs, chi_s,
+    interp and periodic attributes."""
+    d = rr_bundle_desc()
+    d.nx, d.ny = int(b.nx), int(b.ny)
+    d.fov_x, d.fov_y = float(b.fov_x), float(b.fov_y)
+    for i in range(3):
+        d.obs[i] = float(b.obs[i])
+    d.chi_s = float(b.chi_s)
+    d.interp = int(getattr(b, "interp", RR_TRILINEAR))
+    flags = RR_PERIODIC if getattr(b, "periodic", True) else 0
+    if fp64_dda:
+        flags |= RR_FP64_DDA
+    d.flags = flags
+    return d
+
+
+def grid_desc(g) -> rr_grid_desc:
+    d = rr_grid_desc()
+    for i in range(3):
+        d.n[i] = int(g.n[i])
+    d.box = float(g.box)
+    d.omega_m = float(getattr(g, "omega_m", 0.3))
+    return d
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------
+
+def rr_create(bundle: rr_bundle_desc) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().rr_create(C.byref(bundle), C.byref(h)), "rr_create")
+    return h
+
+
+def rr_destroy(ctx) -> None:
+    _check(load().rr_destroy(ctx), "rr_destroy")
+
+
+def rr_reset(ctx, stream=None) -> None:
+    _check(load().rr_reset(ctx, _stream(stream)), "rr_reset")
+
+
+def rr_tidal_tensor(grid: rr_grid_desc, phi, delta, rec, where: int = RR_AT_VERTICES, bbox=None,
+                    stream=None) -> None:
+    bb = None
+    if bbox is not None:
+        arr = (C.c_int32 * 6)(*[int(x) for x in bbox])
+        bb = C.cast(arr, C.c_void_p)
+    _check(load().rr_tidal_tensor(C.byref(grid), _ptr(phi), _ptr(delta), _ptr(rec), int(where), bb,
+                                  _stream(stream)), "rr_tidal_tensor")
+
+
+def rr_footprint_bbox(bundle: rr_bundle_desc, grid: rr_grid_desc, chi_a: float, chi_b: float):
+    arr = (C.c_int32 * 6)()
+    _check(load().rr_footprint_bbox(C.byref(bundle), C.byref(grid), float(chi_a), float(chi_b),
+                                    C.cast(arr, C.c_void_p)), "rr_footprint_bbox")
+    return tuple(int(x) for x in arr)
+
+
+def rr_trace_step(ctx, grid: rr_grid_desc, rec, chi_a: float, chi_b: float, scale: float = 1.0,
+                  a_step: float = 1.0, stream=None) -> None:
+    _check(load().rr_trace_step(ctx, C.byref(grid), _ptr(rec), float(chi_a), float(chi_b), float(scale),
+                                float(a_step), _stream(stream)), "rr_trace_step")
+
+
+def rr_finalize(ctx, kappa, kappa_born=None, stream=None) -> None:
+    _check(load().rr_finalize(ctx, _ptr(kappa), _ptr(kappa_born), _stream(stream)), "rr_finalize")
+
+
+def rr_sync_status(ctx, stream=None) -> int:
+    return int(load().rr_sync_status(ctx, _stream(stream)))
+
+
+def rr_segment_count(ctx, per_ray=None, stream=None) -> int:
+    tot = C.c_uint64(0)
+    _check(load().rr_segment_count(ctx, C.byref(tot), _ptr(per_ray), _stream(stream)), "rr_segment_count")
+    return int(tot.value)

@@ -1,0 +1,274 @@
+// C ABI: argument validation, contexts, stream plumbing, the step log.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+
+#include "rr_internal.h"
+
+using namespace rr;
+
+namespace {
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+rr_status check_bundle(const rr_bundle_desc* b)
+{
+    if (!b) return RR_ERR_ARG;
+    if (b->nx < 1 || b->ny < 1 || (long long)b->nx * b->ny > (1LL << 30)) return RR_ERR_ARG;
+    if (!is_finite(b->fov_x) || !is_finite(b->fov_y) || b->fov_x < 0 || b->fov_y < 0 || b->fov_x >= M_PI ||
+        b->fov_y >= M_PI)
+        return RR_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!is_finite(b->obs[a])) return RR_ERR_ARG;
+    if (!is_finite(b->chi_s) || !(b->chi_s > 0)) return RR_ERR_ARG;
+    if (b->interp != RR_NGP && b->interp != RR_TRILINEAR) return RR_ERR_ARG;
+    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA)) return RR_ERR_ARG;
+    return RR_OK;
+}
+
+rr_status check_grid(const rr_grid_desc* g)
+{
+    if (!g) return RR_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (g->n[a] < 2 || g->n[a] > 4096) return RR_ERR_ARG;
+    if (!is_finite(g->box) || !(g->box > 0)) return RR_ERR_ARG;
+    if (!is_finite(g->omega_m) || !(g->omega_m > 0)) return RR_ERR_ARG;
+    return RR_OK;
+}
+
+rr_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return RR_OK;
+    if (e == cudaErrorMemoryAllocation) return RR_ERR_OOM;
+    return RR_ERR_CUDA;
+}
+
+rr_status status_from_word(uint32_t w)
+{
+    if (w & kErrStepLimit) return RR_ERR_STEP_LIMIT;
+    if (w & kErrNonFinite) return RR_ERR_NONFINITE;
+    return RR_OK;
+}
+
+void free_state(RayState& s)
+{
+    cudaFree(s.dir);
+    cudaFree(s.kappa);
+    cudaFree(s.kborn);
+    cudaFree(s.nseg);
+    cudaFree(s.err);
+    cudaFree(s.total);
+    s = RayState{};
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rr_status_string(rr_status s)
+{
+    switch (s) {
+    case RR_OK: return "RR_OK";
+    case RR_ERR_ARG: return "RR_ERR_ARG: invalid argument";
+    case RR_ERR_CUDA: return "RR_ERR_CUDA: a CUDA runtime call failed";
+    case RR_ERR_OOM: return "RR_ERR_OOM: device allocation failed";
+    case RR_ERR_STEP_LIMIT: return "RR_ERR_STEP_LIMIT: a ray exceeded its per-step iteration cap";
+    case RR_ERR_STATE: return "RR_ERR_STATE: calls out of order";
+    case RR_ERR_NONFINITE: return "RR_ERR_NONFINITE: a per-ray sum is not finite";
+    }
+    return "unknown rr_status";
+}
+
+rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
+{
+    if (!out) return RR_ERR_ARG;
+    *out = nullptr;
+    rr_status st = check_bundle(bundle);
+    if (st != RR_OK) return st;
+    rr_ctx* ctx = new (std::nothrow) rr_ctx();
+    if (!ctx) return RR_ERR_OOM;
+    ctx->bundle = *bundle;
+    cudaGetDevice(&ctx->device);
+    const size_t nr = (size_t)bundle->nx * bundle->ny;
+    cudaError_t e = cudaSuccess;
+    RayState& s = ctx->st;
+    if (e == cudaSuccess) e = cudaMalloc(&s.dir, 3 * nr * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s.kappa, nr * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s.kborn, nr * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s.nseg, nr * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s.err, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s.total, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->host_err, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->host_total, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s.kappa, 0, nr * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(s.kborn, 0, nr * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(s.nseg, 0, nr * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(s.err, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(s.total, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = launch_init_directions(*bundle, s.dir, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_state(s);
+        if (ctx->host_err) cudaFreeHost(ctx->host_err);
+        if (ctx->host_total) cudaFreeHost(ctx->host_total);
+        delete ctx;
+        return from_cuda(e);
+    }
+    *out = ctx;
+    return RR_OK;
+}
+
+rr_status rr_destroy(rr_ctx* ctx)
+{
+    if (!ctx) return RR_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_state(ctx->st);
+    cudaFreeHost(ctx->host_err);
+    cudaFreeHost(ctx->host_total);
+    delete ctx;
+    return RR_OK;
+}
+
+rr_status rr_reset(rr_ctx* ctx, void* stream)
+{
+    if (!ctx) return RR_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nr = (size_t)ctx->bundle.nx * ctx->bundle.ny;
+    cudaError_t e = cudaMemsetAsync(ctx->st.kappa, 0, nr * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.kborn, 0, nr * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.nseg, 0, nr * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.err, 0, sizeof(uint32_t), s);
+    ctx->log.clear();
+    ctx->last_total = 0;
+    return from_cuda(e);
+}
+
+rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                          int32_t where, const int32_t* bbox, void* stream)
+{
+    rr_status st = check_grid(grid);
+    if (st != RR_OK) return st;
+    if (!phi || !rec || !aligned16(rec)) return RR_ERR_ARG;
+    if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
+    if (bbox) {
+        for (int a = 0; a < 3; ++a) {
+            const long long ext = (long long)bbox[2 * a + 1] - bbox[2 * a];
+            if (ext < 1 || ext > grid->n[a]) return RR_ERR_ARG;
+            if (bbox[2 * a] < -(1 << 20) || bbox[2 * a + 1] > (1 << 20)) return RR_ERR_ARG;
+        }
+    }
+    return from_cuda(launch_tidal(*grid, phi, delta, rec, where, bbox, (cudaStream_t)stream));
+}
+
+rr_status rr_footprint_bbox(const rr_bundle_desc* b, const rr_grid_desc* g, double chi_a, double chi_b,
+                            int32_t bbox[6])
+{
+    rr_status st = check_bundle(b);
+    if (st != RR_OK) return st;
+    st = check_grid(g);
+    if (st != RR_OK) return st;
+    if (!bbox || !is_finite(chi_a) || !is_finite(chi_b) || !(chi_a >= chi_b) || chi_b < 0) return RR_ERR_ARG;
+    // Bounds of the direction over the bundle: n_x = theta_x sinc(theta) lies in
+    // [-sin(U_x/2), sin(U_x/2)] because sinc decreases on [0, pi); n_z = cos(theta)
+    // lies in [cos(theta_max), 1].
+    const double hx = b->nx > 1 ? 0.5 * b->fov_x : 0.0, hy = b->ny > 1 ? 0.5 * b->fov_y : 0.0;
+    const double thmax = sqrt(hx * hx + hy * hy);
+    const double nlo[3] = {-sin(hx), -sin(hy), cos(thmax)};
+    const double nhi[3] = {sin(hx), sin(hy), 1.0};
+    const double h = g->box / g->n[0];
+    for (int a = 0; a < 3; ++a) {
+        const double c1 = chi_a * nlo[a], c2 = chi_b * nlo[a], c3 = chi_a * nhi[a], c4 = chi_b * nhi[a];
+        const double lo = b->obs[a] + std::min(std::min(c1, c2), std::min(c3, c4));
+        const double hi = b->obs[a] + std::max(std::max(c1, c2), std::max(c3, c4));
+        long long i0 = (long long)floor(lo / h) - 1, i1 = (long long)floor(hi / h) + 3;
+        if (i1 - i0 >= g->n[a] || i0 < -(1 << 20) || i1 > (1 << 20)) {
+            i0 = 0;
+            i1 = g->n[a];
+        }
+        bbox[2 * a] = (int32_t)i0;
+        bbox[2 * a + 1] = (int32_t)i1;
+    }
+    return RR_OK;
+}
+
+rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
+                        double scale, double a_step, void* stream)
+{
+    if (!ctx) return RR_ERR_ARG;
+    rr_status st = check_grid(grid);
+    if (st != RR_OK) return st;
+    if (!rec || !aligned16(rec)) return RR_ERR_ARG;
+    if (!is_finite(chi_a) || !is_finite(chi_b) || !is_finite(scale) || !is_finite(a_step) || !(a_step > 0)) return RR_ERR_ARG;
+    if (!(chi_a > chi_b) || chi_b < 0 || chi_a > ctx->bundle.chi_s * (1.0 + 1e-12)) return RR_ERR_ARG;
+    if (!ctx->log.empty()) {
+        const double prev = ctx->log.back().chi_b;
+        if (fabs(prev - chi_a) > 1e-12 * std::max(1.0, fabs(chi_a))) return RR_ERR_STATE;
+    }
+    const rr_bundle_desc& b = ctx->bundle;
+    TraceArgs a;
+    a.rec = reinterpret_cast<const float4*>(rec);
+    a.n0 = grid->n[0]; a.n1 = grid->n[1]; a.n2 = grid->n[2];
+    a.h = grid->box / grid->n[0];
+    a.inv_h = 1.0 / a.h;
+    a.nx = b.nx; a.ny = b.ny;
+    a.obs0 = b.obs[0]; a.obs1 = b.obs[1]; a.obs2 = b.obs[2];
+    a.chi_s = b.chi_s;
+    a.chi_a = chi_a;
+    a.chi_b = chi_b;
+    a.periodic = (b.flags & RR_PERIODIC) ? 1 : 0;
+    a.dir = ctx->st.dir;
+    a.kappa = ctx->st.kappa;
+    a.kborn = ctx->st.kborn;
+    a.nseg = ctx->st.nseg;
+    a.err = ctx->st.err;
+    a.scale = scale;
+    a.born_pref = 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step;
+    cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    ctx->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
+    return RR_OK;
+}
+
+rr_status rr_sync_status(rr_ctx* ctx, void* stream)
+{
+    if (!ctx) return RR_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->host_err, ctx->st.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return status_from_word(*ctx->host_err);
+}
+
+rr_status rr_finalize(rr_ctx* ctx, double* kappa, double* kappa_born, void* stream)
+{
+    if (!ctx || !kappa) return RR_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nr = ctx->bundle.nx * ctx->bundle.ny;
+    cudaError_t e = launch_finalize(nr, ctx->st.kappa, ctx->st.kborn, ctx->st.nseg, kappa, kappa_born,
+                                    ctx->st.total, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->host_total, ctx->st.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    rr_status st = rr_sync_status(ctx, stream);
+    ctx->last_total = *ctx->host_total;
+    return st;
+}
+
+rr_status rr_segment_count(rr_ctx* ctx, uint64_t* total, uint32_t* per_ray, void* stream)
+{
+    if (!ctx) return RR_ERR_ARG;
+    if (total) *total = ctx->last_total;
+    if (per_ray) {
+        const size_t nr = (size_t)ctx->bundle.nx * ctx->bundle.ny;
+        return from_cuda(cudaMemcpyAsync(per_ray, ctx->st.nseg, nr * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                         (cudaStream_t)stream));
+    }
+    return RR_OK;
+}
+
+}  // extern "C"

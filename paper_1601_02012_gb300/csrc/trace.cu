@@ -1,0 +1,392 @@
+// Cell-by-cell line-of-sight integration over one step (Secs. 2.5-2.6, 3.2).
+//
+// One thread owns one ray; a warp owns an 8 x 4 tile of neighbouring pixels,
+// so that its rays sit in the same or adjacent cells at every chi and the
+// record gathers of a warp mostly hit the same 128-byte lines (served by L1).
+//
+// Per ray and step:
+//  * FP64 setup: the start point obs + chi_a n (Eq. raypos), the starting
+//    cell, and (without periodic wrap) the part of [chi_b, chi_a] inside the box.
+//  * The walk runs in cell-local "mirrored" coordinates u_a in [0, 1] that
+//    grow along the motion (-n): the exit face on axis a is u_a = 1, reached
+//    after a path (1 - u_a) h / |n_a|; the smallest of the three picks the
+//    exit face (the exit-plane rule of Sec. 2.5.1, Eq. disttocross), ties go
+//    to the lowest axis. The step ends when the path reaches chi_a - chi_b.
+//  * Trilinear mode keeps the projected values of the cell's 8 vertices in
+//    registers; crossing a face keeps the 4 shared vertices and gathers the 4
+//    new ones (2 x 16-byte loads each), prefetched before the current
+//    segment's arithmetic.
+//  * Along the segment, chi = chi_A - s for s in [0, t]; the trilinear field
+//    restricted to the line is a cubic in s (the d_N of Appendix B, written
+//    about the entry point) and the lensing kernel is the quadratic
+//    g(chi_A - s); the segment integral (Eq. Iclensing) is the exact
+//    sum_N e_N J_N with J_N = int_0^t g(chi_A - s) s^(N-1) ds.
+//  * Sums over segments are compensated FP32 (Kahan); the step total is
+//    added to the ray's FP64 accumulator.
+#include <math_constants.h>
+
+#include "rr_internal.h"
+
+namespace rr {
+namespace {
+
+constexpr int WX = 8, WY = 4;     // warp tile of rays (x fastest)
+constexpr int WPX = 2, WPY = 2;   // warps per block
+constexpr int BTX = WX * WPX, BTY = WY * WPY;
+constexpr int NT = 32 * WPX * WPY;
+
+__device__ __forceinline__ int wrap_once(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+__device__ __forceinline__ int wrap_any(long long c, int n)
+{
+    long long r = c % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+struct Rec {
+    float4 a, b;
+};
+
+__device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, long long idx)
+{
+    Rec r;
+    r.a = __ldg(rec + 2 * idx);
+    r.b = __ldg(rec + 2 * idx + 1);
+    return r;
+}
+
+// Q_kappa = tr(H) - n^T H n = w . (xx, yy, zz, xy, xz, yz)
+__device__ __forceinline__ float project(const float w[6], const Rec& r)
+{
+    float q = w[0] * r.a.x;
+    q = fmaf(w[1], r.a.y, q);
+    q = fmaf(w[2], r.a.z, q);
+    q = fmaf(w[3], r.a.w, q);
+    q = fmaf(w[4], r.b.x, q);
+    q = fmaf(w[5], r.b.y, q);
+    return q;
+}
+
+// Trilinear field on the line u(s) = u0 + v s as the cubic e0 + e1 s + e2 s^2
+// + e3 s^3. q[i + 2j + 4k] is the value at the mirrored corner (i, j, k).
+__device__ __forceinline__ void line_cubic(const float q[8], float u0, float u1, float u2, float v0, float v1,
+                                           float v2, float e[4])
+{
+    float A[4], B[4];
+#pragma unroll
+    for (int jk = 0; jk < 4; ++jk) {
+        const float lo = q[2 * jk], d = q[2 * jk + 1] - lo;
+        A[jk] = fmaf(d, u0, lo);
+        B[jk] = d * v0;
+    }
+    float M0[2], M1[2], M2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float C = A[2 * k + 1] - A[2 * k], D = B[2 * k + 1] - B[2 * k];
+        M0[k] = fmaf(C, u1, A[2 * k]);
+        M1[k] = fmaf(C, v1, fmaf(D, u1, B[2 * k]));
+        M2[k] = D * v1;
+    }
+    const float E0 = M0[1] - M0[0], E1 = M1[1] - M1[0], E2 = M2[1] - M2[0];
+    e[0] = fmaf(E0, u2, M0[0]);
+    e[1] = fmaf(E0, v2, fmaf(E1, u2, M1[0]));
+    e[2] = fmaf(E1, v2, fmaf(E2, u2, M2[0]));
+    e[3] = E2 * v2;
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <class R>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) { kahan_add(s, c, x); }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// INTERP: RR_NGP or RR_TRILINEAR. R: float (compensated FP32 walk) or double
+// (plain FP64 walk).
+template <int INTERP, class R>
+__global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ix = blockIdx.x * BTX + (warp % WPX) * WX + (lane % WX);
+    const int iy = blockIdx.y * BTY + (warp / WPX) * WY + (lane / WX);
+    if (ix >= A.nx || iy >= A.ny) return;
+    const long long rid = (long long)iy * A.nx + ix;
+
+    const double nd[3] = {A.dir[3 * rid], A.dir[3 * rid + 1], A.dir[3 * rid + 2]};
+    const int nn[3] = {A.n0, A.n1, A.n2};
+
+    // Part of [chi_b, chi_a] this ray traverses (all of it with periodic wrap).
+    double hi = A.chi_a, lo = A.chi_b;
+    if (!A.periodic) {
+        const double obs[3] = {A.obs0, A.obs1, A.obs2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double ext = nn[a] * A.h;
+            if (nd[a] == 0.0) {
+                if (obs[a] < 0.0 || obs[a] > ext) hi = lo;
+            } else {
+                const double c0 = -obs[a] / nd[a], c1 = (ext - obs[a]) / nd[a];
+                hi = fmin(hi, fmax(c0, c1));
+                lo = fmax(lo, fmin(c0, c1));
+            }
+        }
+    }
+    if (!(hi > lo)) return;
+
+    // Start cell, mirrored local coordinates and the first face crossing per
+    // axis (FP64 setup).
+    const double p[3] = {fma(hi, nd[0], A.obs0), fma(hi, nd[1], A.obs1), fma(hi, nd[2], A.obs2)};
+    int c[3], sgn[3], k[3];
+    R T0[3], td[3], v[3], cu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double ua = p[a] * A.inv_h;
+        double fl = floor(ua);
+        // moving along -n: on a face with n_a > 0 the ray is entering the cell below
+        if (nd[a] > 0.0 && ua == fl) fl -= 1.0;
+        double f = ua - fl;
+        long long ci = (long long)fl;
+        if (A.periodic) {
+            ci = wrap_any(ci, nn[a]);
+        } else if (ci < 0) {
+            ci = 0; f = 0.0;
+        } else if (ci >= nn[a]) {
+            ci = nn[a] - 1; f = 1.0;
+        }
+        c[a] = (int)ci;
+        sgn[a] = nd[a] > 0.0 ? -1 : 1;
+        const double u0 = sgn[a] > 0 ? f : 1.0 - f;   // grows along the motion
+        const double va = fabs(nd[a]) * A.inv_h;
+        v[a] = (R)va;
+        k[a] = 0;
+        if (va > 0.0) {
+            // path to the k-th face crossing on this axis: T0 + k td (one rounding)
+            T0[a] = (R)((1.0 - u0) / va);
+            td[a] = (R)(1.0 / va);
+            cu[a] = (R)1;
+        } else {
+            T0[a] = (R)1e30;   // never crosses; u stays u0
+            td[a] = (R)0;
+            cu[a] = (R)u0;
+        }
+    }
+    // vertex indices of the mirrored faces 0 (entry side) and 1 (exit side)
+    int vlo[3], vhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int up = c[a] + 1 == nn[a] ? 0 : c[a] + 1;
+        vlo[a] = sgn[a] > 0 ? c[a] : up;
+        vhi[a] = sgn[a] > 0 ? up : c[a];
+    }
+    const long long sx = (long long)A.n1 * A.n2, sy = A.n2;
+
+    float w[6];
+    w[0] = (float)(nd[1] * nd[1] + nd[2] * nd[2]);
+    w[1] = (float)(nd[0] * nd[0] + nd[2] * nd[2]);
+    w[2] = (float)(nd[0] * nd[0] + nd[1] * nd[1]);
+    w[3] = (float)(-2.0 * nd[0] * nd[1]);
+    w[4] = (float)(-2.0 * nd[0] * nd[2]);
+    w[5] = (float)(-2.0 * nd[1] * nd[2]);
+
+    const R L = (R)(hi - lo);
+    const R chiA0 = (R)hi;
+    const R D0 = (R)(A.chi_s - hi);
+    const R chis = (R)A.chi_s;
+    const R ichis = (R)(1.0 / A.chi_s);
+    const int max_iter = (int)ceil((hi - lo) * (fabs(nd[0]) + fabs(nd[1]) + fabs(nd[2])) * A.inv_h) + 8;
+
+    // Field cache: projected kappa values and delta at the 8 mirrored corners
+    // (trilinear) or at the cell centre (NGP).
+    float qk[8], qb[8];
+    if (INTERP == RR_TRILINEAR) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int gx = (m & 1) ? vhi[0] : vlo[0];
+            const int gy = (m & 2) ? vhi[1] : vlo[1];
+            const int gz = (m & 4) ? vhi[2] : vlo[2];
+            const Rec r = load_rec(A.rec, gx * sx + gy * sy + gz);
+            qk[m] = project(w, r);
+            qb[m] = r.b.z;
+        }
+    } else {
+        const Rec r = load_rec(A.rec, c[0] * sx + c[1] * sy + c[2]);
+        qk[0] = project(w, r);
+        qb[0] = r.b.z;
+    }
+
+    Acc<R> sk, sb;
+    uint32_t cnt = 0;
+    R sig = 0;                       // path from the step start to the segment entry
+    R T[3] = {T0[0], T0[1], T0[2]};  // path to the next face crossing per axis
+    // Crossings closer together than the walk resolves are one crossing: a
+    // crossing within eps_rel * L of the step's end, and a segment shorter
+    // than eps_rel * (its end), are rounding slivers at an edge or corner the
+    // ray passes through; they are neither integrated nor counted. FP32: 4 ulp
+    // of the path. FP64: 2^-36, above the error the FP64 start point carries
+    // into a crossing distance (ulp(|p|) / |n_a|) for rays 1e-4 rad off an axis.
+    const R eps_rel = sizeof(R) == 4 ? (R)4.76837158203125e-07 : (R)1.4551915228366852e-11;
+    const R eps_end = L * eps_rel;
+    int iter = 0;
+    bool overflow = false;
+    while (true) {
+        // exit plane: the nearest face crossing (lowest axis on ties)
+        R tend = T[0];
+        int e = 0;
+        if (T[1] < tend) { tend = T[1]; e = 1; }
+        if (T[2] < tend) { tend = T[2]; e = 2; }
+        const bool last = !(tend < L - eps_end);
+        if (last) tend = L;
+        const R t = tend - sig;
+        // mirrored entry point of this segment
+        R u[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = fmin(fmax(fma(sig - T[a], v[a], cu[a]), (R)0), (R)1);
+
+        // Prefetch the next cell's new records before this segment's arithmetic.
+        // (register arrays are indexed only through unrolled loops, never by e)
+        int nvhi = 0, ncell = 0, ne = 1;
+        Rec nr[4];
+        if (!last) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (a == e) {
+                    nvhi = wrap_once(vhi[a] + sgn[a], nn[a]);
+                    ncell = c[a] + sgn[a];
+                    ne = nn[a];
+                }
+            if (INTERP == RR_TRILINEAR) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int pb = r & 1, qb2 = r >> 1;
+                    const int gx = e == 0 ? nvhi : (pb ? vhi[0] : vlo[0]);
+                    const int gy = e == 1 ? nvhi : (e == 0 ? (pb ? vhi[1] : vlo[1]) : (qb2 ? vhi[1] : vlo[1]));
+                    const int gz = e == 2 ? nvhi : (qb2 ? vhi[2] : vlo[2]);
+                    nr[r] = load_rec(A.rec, gx * sx + gy * sy + gz);
+                }
+            } else {
+                const int cx = e == 0 ? wrap_once(ncell, nn[0]) : c[0];
+                const int cy = e == 1 ? wrap_once(ncell, nn[1]) : c[1];
+                const int cz = e == 2 ? wrap_once(ncell, nn[2]) : c[2];
+                nr[0] = load_rec(A.rec, cx * sx + cy * sy + cz);
+            }
+        }
+
+        if (t > tend * eps_rel) {
+            // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
+            const R chiA = chiA0 - sig;
+            const R G0 = (D0 + sig) * chiA * ichis;
+            const R G1 = (2 * chiA - chis) * ichis;
+            const R G2 = -ichis;
+            if (INTERP == RR_TRILINEAR) {
+                const R t2 = t * t;
+                const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
+                const R J2 = t2 * (G0 * (R)0.5 + t * (G1 * (R)(1.0 / 3.0) + t * G2 * (R)0.25));
+                const R J3 = t2 * t * (G0 * (R)(1.0 / 3.0) + t * (G1 * (R)0.25 + t * G2 * (R)0.2));
+                const R J4 = t2 * t2 * (G0 * (R)0.25 + t * (G1 * (R)0.2 + t * G2 * (R)(1.0 / 6.0)));
+                float ek[4], eb[4];
+                const float fu0 = (float)u[0], fu1 = (float)u[1], fu2 = (float)u[2];
+                const float fv0 = (float)v[0], fv1 = (float)v[1], fv2 = (float)v[2];
+                line_cubic(qk, fu0, fu1, fu2, fv0, fv1, fv2, ek);
+                line_cubic(qb, fu0, fu1, fu2, fv0, fv1, fv2, eb);
+                sk.add((R)ek[0] * J1 + (R)ek[1] * J2 + (R)ek[2] * J3 + (R)ek[3] * J4);
+                sb.add((R)eb[0] * J1 + (R)eb[1] * J2 + (R)eb[2] * J3 + (R)eb[3] * J4);
+            } else {
+                const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
+                sk.add((R)qk[0] * J1);
+                sb.add((R)qb[0] * J1);
+            }
+            ++cnt;
+        }
+        sig = tend;
+        if (last) break;
+
+        // cross the exit face e
+        if (!A.periodic && (ncell < 0 || ncell >= ne)) break;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a == e) {
+                c[a] = wrap_once(ncell, nn[a]);
+                vlo[a] = vhi[a];
+                vhi[a] = nvhi;
+                k[a] += 1;
+                T[a] = fma((R)k[a], td[a], T0[a]);
+            }
+        if (INTERP == RR_TRILINEAR) {
+            float pk[4], pb[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                pk[r] = project(w, nr[r]);
+                pb[r] = nr[r].b.z;
+            }
+            if (e == 0) {
+                qk[0] = qk[1]; qk[2] = qk[3]; qk[4] = qk[5]; qk[6] = qk[7];
+                qk[1] = pk[0]; qk[3] = pk[1]; qk[5] = pk[2]; qk[7] = pk[3];
+                qb[0] = qb[1]; qb[2] = qb[3]; qb[4] = qb[5]; qb[6] = qb[7];
+                qb[1] = pb[0]; qb[3] = pb[1]; qb[5] = pb[2]; qb[7] = pb[3];
+            } else if (e == 1) {
+                qk[0] = qk[2]; qk[1] = qk[3]; qk[4] = qk[6]; qk[5] = qk[7];
+                qk[2] = pk[0]; qk[3] = pk[1]; qk[6] = pk[2]; qk[7] = pk[3];
+                qb[0] = qb[2]; qb[1] = qb[3]; qb[4] = qb[6]; qb[5] = qb[7];
+                qb[2] = pb[0]; qb[3] = pb[1]; qb[6] = pb[2]; qb[7] = pb[3];
+            } else {
+                qk[0] = qk[4]; qk[1] = qk[5]; qk[2] = qk[6]; qk[3] = qk[7];
+                qk[4] = pk[0]; qk[5] = pk[1]; qk[6] = pk[2]; qk[7] = pk[3];
+                qb[0] = qb[4]; qb[1] = qb[5]; qb[2] = qb[6]; qb[3] = qb[7];
+                qb[4] = pb[0]; qb[5] = pb[1]; qb[6] = pb[2]; qb[7] = pb[3];
+            }
+        } else {
+            qk[0] = project(w, nr[0]);
+            qb[0] = nr[0].b.z;
+        }
+        if (++iter > max_iter) {
+            overflow = true;
+            break;
+        }
+    }
+
+    const double vk = sk.value(), vb = sb.value();
+    if (overflow) atomicOr(A.err, kErrStepLimit);
+    if (!isfinite(vk) || !isfinite(vb)) atomicOr(A.err, kErrNonFinite);
+    A.kappa[rid] += A.scale * vk;
+    A.kborn[rid] += A.scale * A.born_pref * vb;
+    A.nseg[rid] += cnt;
+}
+
+}  // namespace
+
+cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s)
+{
+    dim3 grid((a.nx + BTX - 1) / BTX, (a.ny + BTY - 1) / BTY);
+    if (interp == RR_TRILINEAR) {
+        if (fp64_dda)
+            trace_kernel<RR_TRILINEAR, double><<<grid, NT, 0, s>>>(a);
+        else
+            trace_kernel<RR_TRILINEAR, float><<<grid, NT, 0, s>>>(a);
+    } else {
+        if (fp64_dda)
+            trace_kernel<RR_NGP, double><<<grid, NT, 0, s>>>(a);
+        else
+            trace_kernel<RR_NGP, float><<<grid, NT, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rr

@@ -230,6 +230,9 @@ def workload(name: str) -> Workload:
     prod_512: 512^3 FP32 GRF, box 1024 Mpc/h, 2048x2048 rays over 10x10 deg,
         chi_s = 1000, 40 steps of equal Delta a with Phi rescaled by D(a)/a
         (flat LCDM, Omega_m = 0.3).
+    mid_256: 256^3 GRF, box 512 (same cell size as prod_512), 1024x1024 rays
+        over 10x10 deg, chi_s = 500, 20 rescaled steps (profiling case: inputs
+        larger than L2, a few GB on the device).
     adjoint_256: 256^3 GRF, box 512, 1024x1024 rays over 5x5 deg, chi_s = 512,
         one step.
     """
@@ -241,8 +244,29 @@ def workload(name: str) -> Workload:
         g = Grid((512, 512, 512), 1024.0)
         b = Bundle(2048, 2048, deg(10.0), deg(10.0), (512.0, 512.0, 0.0), 1000.0)
         return Workload(name, g, b, 40, 2, rescale=True)
+    if name == "mid_256":
+        g = Grid((256, 256, 256), 512.0)
+        b = Bundle(1024, 1024, deg(10.0), deg(10.0), (256.0, 256.0, 0.0), 500.0)
+        return Workload(name, g, b, 20, 6, rescale=True)
     if name == "adjoint_256":
         g = Grid((256, 256, 256), 512.0)
         b = Bundle(1024, 1024, deg(5.0), deg(5.0), (256.0, 256.0, 0.0), 512.0)
         return Workload(name, g, b, 1, 5)
     raise KeyError(name)
+
+
+def grf_phi_cached(n: int, box: float, seed: int, omega_m: float = 0.3) -> np.ndarray:
+    """grf_phi (FP32) memoised on disk under $RR_CACHE (default: the system
+    temporary directory), so that repeated runs on one machine draw it once."""
+    import os
+    import tempfile
+    root = os.environ.get("RR_CACHE", os.path.join(tempfile.gettempdir(), "rr_cache"))
+    os.makedirs(root, exist_ok=True)
+    path = os.path.join(root, f"grf_n{n}_L{box:g}_s{seed}_om{omega_m:g}.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    phi = grf_phi(n, box, seed, omega_m)
+    tmp = path + f".{os.getpid()}.tmp.npy"
+    np.save(tmp, phi)
+    os.replace(tmp, path)
+    return phi
