@@ -58,8 +58,10 @@ rr_status status_from_word(uint32_t w)
 void free_state(RayState& s)
 {
     cudaFree(s.dir);
-    cudaFree(s.kappa);
-    cudaFree(s.kborn);
+    cudaFree(s.dirh);
+    cudaFree(s.dirl);
+    cudaFree(s.kacc);
+    cudaFree(s.bacc);
     cudaFree(s.nseg);
     cudaFree(s.err);
     cudaFree(s.total);
@@ -98,19 +100,21 @@ rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
     cudaError_t e = cudaSuccess;
     RayState& s = ctx->st;
     if (e == cudaSuccess) e = cudaMalloc(&s.dir, 3 * nr * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&s.kappa, nr * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&s.kborn, nr * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s.dirh, nr * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&s.dirl, nr * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&s.kacc, nr * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&s.bacc, nr * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc(&s.nseg, nr * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&s.err, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&s.total, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->host_err, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->host_total, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(s.kappa, 0, nr * sizeof(double));
-    if (e == cudaSuccess) e = cudaMemset(s.kborn, 0, nr * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(s.kacc, 0, nr * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(s.bacc, 0, nr * sizeof(float2));
     if (e == cudaSuccess) e = cudaMemset(s.nseg, 0, nr * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.err, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.total, 0, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = launch_init_directions(*bundle, s.dir, 0);
+    if (e == cudaSuccess) e = launch_init_directions(*bundle, s.dir, s.dirh, s.dirl, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_state(s);
@@ -139,8 +143,8 @@ rr_status rr_reset(rr_ctx* ctx, void* stream)
     if (!ctx) return RR_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nr = (size_t)ctx->bundle.nx * ctx->bundle.ny;
-    cudaError_t e = cudaMemsetAsync(ctx->st.kappa, 0, nr * sizeof(double), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.kborn, 0, nr * sizeof(double), s);
+    cudaError_t e = cudaMemsetAsync(ctx->st.kacc, 0, nr * sizeof(float2), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.bacc, 0, nr * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.nseg, 0, nr * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.err, 0, sizeof(uint32_t), s);
     ctx->log.clear();
@@ -215,19 +219,28 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     a.n0 = grid->n[0]; a.n1 = grid->n[1]; a.n2 = grid->n[2];
     a.h = grid->box / grid->n[0];
     a.inv_h = 1.0 / a.h;
+    a.inv_hf = (float)a.inv_h;
+    split_ff(a.inv_h, a.ihh, a.ihl);
     a.nx = b.nx; a.ny = b.ny;
     a.obs0 = b.obs[0]; a.obs1 = b.obs[1]; a.obs2 = b.obs[2];
+    for (int i = 0; i < 3; ++i) split_ff(b.obs[i], a.oh[i], a.ol[i]);
     a.chi_s = b.chi_s;
     a.chi_a = chi_a;
     a.chi_b = chi_b;
+    split_ff(chi_a, a.cah, a.cal);
+    a.Lf = (float)(chi_a - chi_b);
+    a.D0f = (float)(b.chi_s - chi_a);
+    a.inv_chi_s_f = (float)(1.0 / b.chi_s);
     a.periodic = (b.flags & RR_PERIODIC) ? 1 : 0;
     a.dir = ctx->st.dir;
-    a.kappa = ctx->st.kappa;
-    a.kborn = ctx->st.kborn;
+    a.dirh = ctx->st.dirh;
+    a.dirl = ctx->st.dirl;
+    a.kacc = ctx->st.kacc;
+    a.bacc = ctx->st.bacc;
     a.nseg = ctx->st.nseg;
     a.err = ctx->st.err;
-    a.scale = scale;
-    a.born_pref = 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step;
+    split_ff(scale, a.sch, a.scl);
+    split_ff(scale * 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step, a.bsh, a.bsl);
     cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream);
     if (e != cudaSuccess) return from_cuda(e);
     ctx->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
@@ -249,7 +262,7 @@ rr_status rr_finalize(rr_ctx* ctx, double* kappa, double* kappa_born, void* stre
     if (!ctx || !kappa) return RR_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int nr = ctx->bundle.nx * ctx->bundle.ny;
-    cudaError_t e = launch_finalize(nr, ctx->st.kappa, ctx->st.kborn, ctx->st.nseg, kappa, kappa_born,
+    cudaError_t e = launch_finalize(nr, ctx->st.kacc, ctx->st.bacc, ctx->st.nseg, kappa, kappa_born,
                                     ctx->st.total, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->host_total, ctx->st.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);

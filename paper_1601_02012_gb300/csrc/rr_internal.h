@@ -18,8 +18,10 @@ enum : uint32_t { kErrStepLimit = 1u, kErrNonFinite = 2u };
 // Per-ray state, structure of arrays, indexed by ray id (Eq. rayid).
 struct RayState {
     double* dir = nullptr;      // 3 per ray: n_hat (Eq. raypos), FP64
-    double* kappa = nullptr;    // FP64 accumulators across steps
-    double* kborn = nullptr;
+    float4* dirh = nullptr;     // n_hat rounded to FP32 (x, y, z, 0)
+    float4* dirl = nullptr;     // n_hat - dirh rounded to FP32 (float-float low parts)
+    float2* kacc = nullptr;     // kappa accumulated across steps, float-float (hi, lo)
+    float2* bacc = nullptr;     // Born kappa, float-float
     uint32_t* nseg = nullptr;   // non-empty segments since reset
     uint32_t* err = nullptr;    // device error word
     unsigned long long* total = nullptr;  // segment total written by finalize
@@ -30,32 +32,49 @@ struct StepRecord {
     double chi_a, chi_b, scale, a_step;
 };
 
-// Geometry of one step, handed to the trace kernels by value.
+// Geometry of one step, handed to the trace kernels by value. Doubles are
+// also given as float-float pairs (hi = (float)x, lo = (float)(x - hi)).
 struct TraceArgs {
     const float4* rec;          // 2 float4 per point
     int n0, n1, n2;
     double h;                   // cell size
     double inv_h;
+    float inv_hf;               // 1/h rounded to FP32
+    float ihh, ihl;             // 1/h as float-float
     int nx, ny;                 // rays
     double obs0, obs1, obs2;
+    float oh[3], ol[3];         // observer as float-float
     double chi_s, chi_a, chi_b;
+    float cah, cal;             // chi_a as float-float
+    float Lf;                   // chi_a - chi_b rounded to FP32
+    float D0f;                  // chi_s - chi_a rounded to FP32
+    float inv_chi_s_f;          // 1/chi_s rounded to FP32
     int periodic;
     const double* dir;
-    double* kappa;
-    double* kborn;
+    const float4* dirh;
+    const float4* dirl;
+    float2* kacc;
+    float2* bacc;
     uint32_t* nseg;
     uint32_t* err;
-    double scale;               // multiplies kappa and born sums
-    double born_pref;           // 1.5 Omega_m (H0/c)^2 / a_step
+    float sch, scl;             // scale (multiplies the kappa step sum), float-float
+    float bsh, bsl;             // scale * 1.5 Omega_m (H0/c)^2 / a_step, float-float
 };
 
 // Launchers (one per translation unit).
-cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, cudaStream_t s);
+cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s);
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
-cudaError_t launch_finalize(int nrays, const double* kappa, const double* kborn, const uint32_t* nseg,
+cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
                             double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s);
+
+// hi = (float)x, lo = (float)(x - hi)
+inline void split_ff(double x, float& hi, float& lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
 
 }  // namespace rr
 

@@ -4,7 +4,8 @@
 namespace rr {
 namespace {
 
-__global__ void init_directions_kernel(int nx, int ny, double fov_x, double fov_y, double* dir)
+__global__ void init_directions_kernel(int nx, int ny, double fov_x, double fov_y, double* dir, float4* dirh,
+                                       float4* dirl)
 {
     const long long rid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (rid >= (long long)nx * ny) return;
@@ -26,17 +27,20 @@ __global__ void init_directions_kernel(int nx, int ny, double fov_x, double fov_
     dir[3 * rid] = n0;
     dir[3 * rid + 1] = n1;
     dir[3 * rid + 2] = n2;
+    const float h0 = (float)n0, h1 = (float)n1, h2 = (float)n2;
+    dirh[rid] = make_float4(h0, h1, h2, 0.f);
+    dirl[rid] = make_float4((float)(n0 - (double)h0), (float)(n1 - (double)h1), (float)(n2 - (double)h2), 0.f);
 }
 
-__global__ void finalize_kernel(int nrays, const double* __restrict__ kappa, const double* __restrict__ kborn,
+__global__ void finalize_kernel(int nrays, const float2* __restrict__ kacc, const float2* __restrict__ bacc,
                                 const uint32_t* __restrict__ nseg, double* out_kappa, double* out_kborn,
                                 unsigned long long* total)
 {
     unsigned long long local = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nrays;
          i += (long long)gridDim.x * blockDim.x) {
-        if (out_kappa) out_kappa[i] = kappa[i];
-        if (out_kborn) out_kborn[i] = kborn[i];
+        if (out_kappa) out_kappa[i] = (double)kacc[i].x + (double)kacc[i].y;
+        if (out_kborn) out_kborn[i] = (double)bacc[i].x + (double)bacc[i].y;
         local += nseg[i];
     }
 #pragma unroll
@@ -46,15 +50,16 @@ __global__ void finalize_kernel(int nrays, const double* __restrict__ kappa, con
 
 }  // namespace
 
-cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, cudaStream_t s)
+cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s)
 {
     const long long nr = (long long)b.nx * b.ny;
     const int nt = 256;
-    init_directions_kernel<<<(unsigned)((nr + nt - 1) / nt), nt, 0, s>>>(b.nx, b.ny, b.fov_x, b.fov_y, dir);
+    init_directions_kernel<<<(unsigned)((nr + nt - 1) / nt), nt, 0, s>>>(b.nx, b.ny, b.fov_x, b.fov_y, dir, dirh,
+                                                                                    dirl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(int nrays, const double* kappa, const double* kborn, const uint32_t* nseg,
+cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
                             double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
@@ -67,7 +72,7 @@ cudaError_t launch_finalize(int nrays, const double* kappa, const double* kborn,
     const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    finalize_kernel<<<(unsigned)blocks, nt, 0, s>>>(nrays, kappa, kborn, nseg, out_kappa, out_kborn, total);
+    finalize_kernel<<<(unsigned)blocks, nt, 0, s>>>(nrays, kacc, bacc, nseg, out_kappa, out_kborn, total);
     return cudaGetLastError();
 }
 

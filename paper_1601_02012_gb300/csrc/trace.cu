@@ -5,24 +5,29 @@
 // record gathers of a warp mostly hit the same 128-byte lines (served by L1).
 //
 // Per ray and step:
-//  * FP64 setup: the start point obs + chi_a n (Eq. raypos), the starting
-//    cell, and (without periodic wrap) the part of [chi_b, chi_a] inside the box.
+//  * Setup: the start point obs + chi_a n (Eq. raypos) and its cell. In the
+//    FP32 form this is float-float arithmetic (chi_a, n, obs and 1/h carried
+//    as pairs of floats, ~2^-46 relative), because GB300 issues FP64 at a
+//    small fraction of the FP32 rate; the plain form uses FP64. The distances
+//    from the start point to the cell's two faces on each axis are both
+//    obtained with full relative precision.
 //  * The walk runs in cell-local "mirrored" coordinates u_a in [0, 1] that
-//    grow along the motion (-n): the exit face on axis a is u_a = 1, reached
-//    after a path (1 - u_a) h / |n_a|; the smallest of the three picks the
+//    grow along the motion (-n). The path to the k-th face crossing on axis a
+//    is T0_a + k td_a (one rounding, no drift); the nearest crossing picks the
 //    exit face (the exit-plane rule of Sec. 2.5.1, Eq. disttocross), ties go
 //    to the lowest axis. The step ends when the path reaches chi_a - chi_b.
 //  * Trilinear mode keeps the projected values of the cell's 8 vertices in
 //    registers; crossing a face keeps the 4 shared vertices and gathers the 4
-//    new ones (2 x 16-byte loads each), prefetched before the current
-//    segment's arithmetic.
+//    new ones (2 x 16-byte loads each), issued before the current segment's
+//    arithmetic.
 //  * Along the segment, chi = chi_A - s for s in [0, t]; the trilinear field
 //    restricted to the line is a cubic in s (the d_N of Appendix B, written
 //    about the entry point) and the lensing kernel is the quadratic
 //    g(chi_A - s); the segment integral (Eq. Iclensing) is the exact
 //    sum_N e_N J_N with J_N = int_0^t g(chi_A - s) s^(N-1) ds.
-//  * Sums over segments are compensated FP32 (Kahan); the step total is
-//    added to the ray's FP64 accumulator.
+//  * Sums over the segments of a step are compensated FP32 (Kahan); the step
+//    total times the step's scale is added to the ray's float-float
+//    accumulator (~48 bits).
 #include <math_constants.h>
 
 #include "rr_internal.h"
@@ -36,12 +41,6 @@ constexpr int BTX = WX * WPX, BTY = WY * WPY;
 constexpr int NT = 32 * WPX * WPY;
 
 __device__ __forceinline__ int wrap_once(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
-
-__device__ __forceinline__ int wrap_any(long long c, int n)
-{
-    long long r = c % n;
-    return (int)(r < 0 ? r + n : r);
-}
 
 struct Rec {
     float4 a, b;
@@ -94,6 +93,34 @@ __device__ __forceinline__ void line_cubic(const float q[8], float u0, float u1,
     e[3] = E2 * v2;
 }
 
+// ---- float-float helpers (error-free transformations) ----------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// acc (hi, lo) + (x_hi + x_lo) * (s_hi + s_lo)
+__device__ __forceinline__ float2 ff_mul_add(float2 acc, float xh, float xl, float sh, float sl)
+{
+    float ph, pe;
+    two_prod(xh, sh, ph, pe);
+    const float pl = pe + fmaf(xh, sl, xl * sh);
+    float s, e;
+    two_sum(acc.x, ph, s, e);
+    const float t = e + (acc.y + pl);
+    const float hi = s + t;
+    return make_float2(hi, t - (hi - s));
+}
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x)
 {
     const float y = x - c;
@@ -109,14 +136,21 @@ template <>
 struct Acc<float> {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float x) { kahan_add(s, c, x); }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    __device__ __forceinline__ bool finite() const { return isfinite(s) && isfinite(c); }
+    // the compensated sum s - c as a float-float pair
+    __device__ __forceinline__ void pair(float& hi, float& lo) const { two_sum(s, -c, hi, lo); }
 };
 
 template <>
 struct Acc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ bool finite() const { return isfinite(s); }
+    __device__ __forceinline__ void pair(float& hi, float& lo) const
+    {
+        hi = (float)s;
+        lo = (float)(s - (double)hi);
+    }
 };
 
 // INTERP: RR_NGP or RR_TRILINEAR. R: float (compensated FP32 walk) or double
@@ -124,18 +158,23 @@ struct Acc<double> {
 template <int INTERP, class R>
 __global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
 {
+    constexpr bool F64 = sizeof(R) == 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ix = blockIdx.x * BTX + (warp % WPX) * WX + (lane % WX);
     const int iy = blockIdx.y * BTY + (warp / WPX) * WY + (lane / WX);
     if (ix >= A.nx || iy >= A.ny) return;
     const long long rid = (long long)iy * A.nx + ix;
-
-    const double nd[3] = {A.dir[3 * rid], A.dir[3 * rid + 1], A.dir[3 * rid + 2]};
     const int nn[3] = {A.n0, A.n1, A.n2};
 
-    // Part of [chi_b, chi_a] this ray traverses (all of it with periodic wrap).
+    const float4 nh4 = A.dirh[rid];
+    const float nh[3] = {nh4.x, nh4.y, nh4.z};
+
+    // The part of [chi_b, chi_a] this ray traverses: all of it with periodic
+    // wrap; clipped to the box in FP64 otherwise.
+    float ch = A.cah, cl = A.cal, Lf = A.Lf, D0f = A.D0f;
     double hi = A.chi_a, lo = A.chi_b;
     if (!A.periodic) {
+        const double nd[3] = {A.dir[3 * rid], A.dir[3 * rid + 1], A.dir[3 * rid + 2]};
         const double obs[3] = {A.obs0, A.obs1, A.obs2};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -148,44 +187,92 @@ __global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
                 lo = fmax(lo, fmin(c0, c1));
             }
         }
+        if (!(hi > lo)) return;
+        ch = (float)hi;
+        cl = (float)(hi - (double)ch);
+        Lf = (float)(hi - lo);
+        D0f = (float)(A.chi_s - hi);
     }
-    if (!(hi > lo)) return;
 
-    // Start cell, mirrored local coordinates and the first face crossing per
-    // axis (FP64 setup).
-    const double p[3] = {fma(hi, nd[0], A.obs0), fma(hi, nd[1], A.obs1), fma(hi, nd[2], A.obs2)};
+    // Start cell; distances (in cells) from the start point to the lower and
+    // upper face on each axis.
     int c[3], sgn[3], k[3];
     R T0[3], td[3], v[3], cu[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double ua = p[a] * A.inv_h;
-        double fl = floor(ua);
-        // moving along -n: on a face with n_a > 0 the ray is entering the cell below
-        if (nd[a] > 0.0 && ua == fl) fl -= 1.0;
-        double f = ua - fl;
-        long long ci = (long long)fl;
-        if (A.periodic) {
-            ci = wrap_any(ci, nn[a]);
-        } else if (ci < 0) {
-            ci = 0; f = 0.0;
-        } else if (ci >= nn[a]) {
-            ci = nn[a] - 1; f = 1.0;
+        R flo, fhi;   // distance to the lower / upper face
+        long long cell;
+        if constexpr (F64) {
+            const double na = A.dir[3 * rid + a];
+            const double oa = a == 0 ? A.obs0 : (a == 1 ? A.obs1 : A.obs2);
+            const double ua = fma(hi, na, oa) * A.inv_h;
+            double fl = floor(ua);
+            double f = ua - fl, g = (fl + 1.0) - ua;
+            // exactly on a face while moving toward -a: the cell below
+            if (na > 0.0 && f == 0.0) { fl -= 1.0; f = 1.0; g = 0.0; }
+            cell = (long long)fl;
+            flo = f;
+            fhi = g;
+        } else {
+            const float4 nl4 = A.dirl[rid];
+            const float nl = a == 0 ? nl4.x : (a == 1 ? nl4.y : nl4.z);
+            // x = obs + chi n in float-float
+            float ph, pe;
+            two_prod(ch, nh[a], ph, pe);
+            const float pl = pe + fmaf(ch, nl, cl * nh[a]);
+            float xs, xe;
+            two_sum(A.oh[a], ph, xs, xe);
+            const float xl = xe + (A.ol[a] + pl);
+            // u = x / h
+            float uh, ue;
+            two_prod(xs, A.ihh, uh, ue);
+            float ul = ue + fmaf(xs, A.ihl, xl * A.ihh);
+            const float un = uh + ul;
+            ul = ul - (un - uh);
+            uh = un;
+            float fl = floorf(uh);
+            float f, g;
+            if (uh == fl && ul < 0.f) {
+                fl -= 1.f;
+                f = 1.f + ul;
+                g = -ul;
+            } else {
+                f = (uh - fl) + ul;
+                g = ((fl + 1.f) - uh) - ul;
+            }
+            // exactly on a face while moving toward -a: the cell below
+            if (nh[a] > 0.f && f == 0.f) { fl -= 1.f; f = 1.f; g = 0.f; }
+            cell = (long long)fl;
+            flo = f;
+            fhi = g;
         }
-        c[a] = (int)ci;
-        sgn[a] = nd[a] > 0.0 ? -1 : 1;
-        const double u0 = sgn[a] > 0 ? f : 1.0 - f;   // grows along the motion
-        const double va = fabs(nd[a]) * A.inv_h;
-        v[a] = (R)va;
+        int ci = (int)cell;
+        if (A.periodic) {
+            ci %= nn[a];
+            if (ci < 0) ci += nn[a];
+        } else if (ci < 0) {
+            ci = 0; flo = (R)0; fhi = (R)1;
+        } else if (ci >= nn[a]) {
+            ci = nn[a] - 1; flo = (R)1; fhi = (R)0;
+        }
+        c[a] = ci;
+        sgn[a] = nh[a] > 0.f ? -1 : 1;   // motion along a is -n_a
+        const R u0 = sgn[a] > 0 ? flo : fhi;      // mirrored: grows along the motion
+        const R e0 = sgn[a] > 0 ? fhi : flo;      // distance to the exit face
+        R va;
+        if constexpr (F64) va = (R)(fabs(A.dir[3 * rid + a]) * A.inv_h);
+        else va = fabsf(nh[a]) * A.inv_hf;
+        v[a] = va;
         k[a] = 0;
-        if (va > 0.0) {
+        if (va > (R)0) {
             // path to the k-th face crossing on this axis: T0 + k td (one rounding)
-            T0[a] = (R)((1.0 - u0) / va);
-            td[a] = (R)(1.0 / va);
+            td[a] = (R)1 / va;
+            T0[a] = e0 * td[a];
             cu[a] = (R)1;
         } else {
             T0[a] = (R)1e30;   // never crosses; u stays u0
             td[a] = (R)0;
-            cu[a] = (R)u0;
+            cu[a] = u0;
         }
     }
     // vertex indices of the mirrored faces 0 (entry side) and 1 (exit side)
@@ -199,19 +286,20 @@ __global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
     const long long sx = (long long)A.n1 * A.n2, sy = A.n2;
 
     float w[6];
-    w[0] = (float)(nd[1] * nd[1] + nd[2] * nd[2]);
-    w[1] = (float)(nd[0] * nd[0] + nd[2] * nd[2]);
-    w[2] = (float)(nd[0] * nd[0] + nd[1] * nd[1]);
-    w[3] = (float)(-2.0 * nd[0] * nd[1]);
-    w[4] = (float)(-2.0 * nd[0] * nd[2]);
-    w[5] = (float)(-2.0 * nd[1] * nd[2]);
+    w[0] = nh[1] * nh[1] + nh[2] * nh[2];
+    w[1] = nh[0] * nh[0] + nh[2] * nh[2];
+    w[2] = nh[0] * nh[0] + nh[1] * nh[1];
+    w[3] = -2.f * nh[0] * nh[1];
+    w[4] = -2.f * nh[0] * nh[2];
+    w[5] = -2.f * nh[1] * nh[2];
 
-    const R L = (R)(hi - lo);
-    const R chiA0 = (R)hi;
-    const R D0 = (R)(A.chi_s - hi);
+    const R L = F64 ? (R)(hi - lo) : (R)Lf;
+    const R chiA0 = F64 ? (R)hi : (R)ch;
+    const R D0 = F64 ? (R)(A.chi_s - hi) : (R)D0f;
     const R chis = (R)A.chi_s;
-    const R ichis = (R)(1.0 / A.chi_s);
-    const int max_iter = (int)ceil((hi - lo) * (fabs(nd[0]) + fabs(nd[1]) + fabs(nd[2])) * A.inv_h) + 8;
+    const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
+    const int max_iter =
+        (int)ceilf(Lf * (fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2])) * A.inv_hf * 1.0001f) + 8;
 
     // Field cache: projected kappa values and delta at the 8 mirrored corners
     // (trilinear) or at the cell centre (NGP).
@@ -242,7 +330,7 @@ __global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
     // ray passes through; they are neither integrated nor counted. FP32: 4 ulp
     // of the path. FP64: 2^-36, above the error the FP64 start point carries
     // into a crossing distance (ulp(|p|) / |n_a|) for rays 1e-4 rad off an axis.
-    const R eps_rel = sizeof(R) == 4 ? (R)4.76837158203125e-07 : (R)1.4551915228366852e-11;
+    const R eps_rel = F64 ? (R)1.4551915228366852e-11 : (R)4.76837158203125e-07;
     const R eps_end = L * eps_rel;
     int iter = 0;
     bool overflow = false;
@@ -362,11 +450,13 @@ __global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
         }
     }
 
-    const double vk = sk.value(), vb = sb.value();
     if (overflow) atomicOr(A.err, kErrStepLimit);
-    if (!isfinite(vk) || !isfinite(vb)) atomicOr(A.err, kErrNonFinite);
-    A.kappa[rid] += A.scale * vk;
-    A.kborn[rid] += A.scale * A.born_pref * vb;
+    if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
+    float kh, kl, bh, bl;
+    sk.pair(kh, kl);
+    sb.pair(bh, bl);
+    A.kacc[rid] = ff_mul_add(A.kacc[rid], kh, kl, A.sch, A.scl);
+    A.bacc[rid] = ff_mul_add(A.bacc[rid], bh, bl, A.bsh, A.bsl);
     A.nseg[rid] += cnt;
 }
 
