@@ -39,7 +39,8 @@ typedef enum {
     RR_ERR_OOM = -3,        /* device allocation failed */
     RR_ERR_STEP_LIMIT = -4, /* a ray exceeded its per-step iteration cap */
     RR_ERR_STATE = -5,      /* calls out of order (e.g. a gap between steps) */
-    RR_ERR_NONFINITE = -6   /* a per-ray sum became NaN or infinite */
+    RR_ERR_NONFINITE = -6,  /* a per-ray sum became NaN or infinite */
+    RR_ERR_CAPACITY = -7    /* more rays than rr_trace_step_noalloc's fixed scratch holds */
 } rr_status;
 
 /* rr_bundle_desc.interp: how Q varies inside a cell (Sec. 2.6). */
@@ -168,6 +169,39 @@ rr_status rr_sync_status(rr_ctx* ctx, void* stream);
  * counts (asynchronous on `stream`).
  */
 rr_status rr_segment_count(rr_ctx* ctx, uint64_t* total, uint32_t* per_ray, void* stream);
+
+/*
+ * One trace step that allocates nothing -- for callers that cannot let a
+ * library allocate device memory: a host framework that already owns the
+ * device memory pool through its own allocator, code that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree imply, or a plugin host that
+ * forbids driver allocations. The paper has no counterpart; it is an
+ * alternative to rr_create + rr_trace_step + rr_finalize for a single step.
+ *
+ * It traces every ray of `bundle` from chi_a down to chi_b exactly as
+ * rr_trace_step does (same kernels, same arguments and meaning) and writes
+ * kappa and (if not NULL) kappa_born, device FP64 [ny*nx] in rayid order,
+ * holding scale * the step's integrals; then it synchronises `stream` and
+ * returns the device error word as rr_finalize does.
+ *
+ * Scratch: instead of memory the library allocates, the per-ray directions,
+ * accumulators, segment counters and error word live in one fixed array in
+ * the library's device memory, sized for RR_NOALLOC_MAX_RAYS rays (about
+ * 4.8 MB). Every GPU that loads the library holds that array until the
+ * process exits. The caller still provides `rec` and the output maps. The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call reuses the same array and clears what it accumulates
+ * into at the start; calls whose work overlaps on the GPU (two streams, or
+ * two host threads, at once) race on it and must be serialised by the caller.
+ * Returns RR_ERR_CAPACITY if nx * ny > RR_NOALLOC_MAX_RAYS, RR_ERR_ARG for
+ * the argument errors rr_trace_step rejects (no step-order check: each call
+ * is independent).
+ */
+#define RR_NOALLOC_MAX_RAYS 65536
+rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const rr_grid_desc* grid, const float* rec,
+                                double chi_a, double chi_b, double scale, double a_step, double* kappa,
+                                double* kappa_born, void* stream);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,8 @@ RR_ERR_OOM = -3
 RR_ERR_STEP_LIMIT = -4
 RR_ERR_STATE = -5
 RR_ERR_NONFINITE = -6
+RR_ERR_CAPACITY = -7
+RR_NOALLOC_MAX_RAYS = 65536
 
 RR_NGP = 0
 RR_TRILINEAR = 1
@@ -69,6 +71,7 @@ def load() -> C.CDLL:
             "rr_finalize": ([P, P, P, P], C.c_int),
             "rr_sync_status": ([P, P], C.c_int),
             "rr_segment_count": ([P, C.POINTER(C.c_uint64), P, P], C.c_int),
+            "rr_trace_step_noalloc": ([P, P, P, D, D, D, D, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -184,3 +187,15 @@ def rr_segment_count(ctx, per_ray=None, stream=None) -> int:
     tot = C.c_uint64(0)
     _check(load().rr_segment_count(ctx, C.byref(tot), _ptr(per_ray), _stream(stream)), "rr_segment_count")
     return int(tot.value)
+
+
+def rr_trace_step_noalloc(bundle: rr_bundle_desc, grid: rr_grid_desc, rec, chi_a: float, chi_b: float,
+                          kappa, kappa_born=None, scale: float = 1.0, a_step: float = 1.0, stream=None) -> None:
+    """One step into the maps without any allocation by the library (its
+    scratch is a fixed device array for at most RR_NOALLOC_MAX_RAYS rays)."""
+    nr = int(bundle.nx) * int(bundle.ny)
+    if nr > RR_NOALLOC_MAX_RAYS:
+        raise RRError(RR_ERR_CAPACITY, f"rr_trace_step_noalloc: {nr} rays > {RR_NOALLOC_MAX_RAYS}")
+    _check(load().rr_trace_step_noalloc(C.byref(bundle), C.byref(grid), _ptr(rec), float(chi_a), float(chi_b),
+                                        float(scale), float(a_step), _ptr(kappa), _ptr(kappa_born),
+                                        _stream(stream)), "rr_trace_step_noalloc")

@@ -82,6 +82,7 @@ const char* rr_status_string(rr_status s)
     case RR_ERR_STEP_LIMIT: return "RR_ERR_STEP_LIMIT: a ray exceeded its per-step iteration cap";
     case RR_ERR_STATE: return "RR_ERR_STATE: calls out of order";
     case RR_ERR_NONFINITE: return "RR_ERR_NONFINITE: a per-ray sum is not finite";
+    case RR_ERR_CAPACITY: return "RR_ERR_CAPACITY: more rays than the fixed no-allocation scratch holds";
     }
     return "unknown rr_status";
 }
