@@ -89,8 +89,8 @@ const char* rr_status_string(rr_status s);
 
 /*
  * Create a tracing context for one bundle on the current CUDA device: device
- * per-ray state (direction, FP64 accumulators of kappa and Born kappa, segment
- * counter) and an error word, all zeroed. Synchronous. *out receives the
+ * per-ray state (direction, float-float accumulators of kappa and Born kappa,
+ * segment counter) and an error word, all zeroed. Synchronous. *out receives the
  * handle. RR_ERR_ARG on an invalid bundle, RR_ERR_OOM if the state does not
  * fit. Initialising the ray directions (Eq. txty, raypos) runs on the device.
  */
@@ -169,6 +169,53 @@ rr_status rr_sync_status(rr_ctx* ctx, void* stream);
  * counts (asynchronous on `stream`).
  */
 rr_status rr_segment_count(rr_ctx* ctx, uint64_t* total, uint32_t* per_ray, void* stream);
+
+/* Number of steps in the context's step log (since create/reset). */
+rr_status rr_step_count(rr_ctx* ctx, int32_t* n);
+
+/*
+ * Adjoint of logged step `step` (0-based, in call order): adds to grad_rec
+ * the gradient of L with respect to the records that step read,
+ *   grad_rec[p] += sum over rays and segments of dL/dI * dI/dq_p,
+ * where q_p is the record at point p (vertices for RR_TRILINEAR, centres for
+ * RR_NGP) and I the step's contribution to kappa (scale * Eq. Iclensing /
+ * Iclensing_ngp through Q = n1n1 + n2n2) and to kappa_born (scale * first term
+ * of Eq. kappa2). The map is linear in the records, so this is its exact
+ * transpose; it needs the geometry only, not the records.
+ *   dL_dkappa, dL_dkborn  device FP64 [ny*nx] in rayid order (either may be NULL).
+ *   grad_rec              device, n0*n1*n2 gradient records of 16 floats (64 B,
+ *                         16-byte aligned): words 0-7 hold FP32 running sums of
+ *                         the 8 record channels {Hxx,Hyy,Hzz,Hxy,Hxz,Hyz,delta,0},
+ *                         words 8-15 the accumulated rounding errors of those
+ *                         sums; the gradient of channel c is word c + word c+8.
+ *                         Accumulated with compensated atomics (the order of
+ *                         additions is not deterministic; the value is, to
+ *                         rounding).
+ */
+rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkappa, const double* dL_dkborn,
+                                float* grad_rec, void* stream);
+
+/*
+ * Transpose of rr_tidal_tensor: from gradient records (16 floats per point, as
+ * written by rr_trace_step_adjoint; at vertices or centres) to dL/dPhi at the
+ * cell centres, accumulated (+=) into dL_dphi (device,
+ * n0*n1*n2 floats). If dL_ddelta is NULL, delta is taken as derived from the
+ * potential (rr_tidal_tensor with delta == NULL) and its gradient flows into
+ * dL_dphi; otherwise dL/ddelta is accumulated into dL_ddelta.
+ */
+rr_status rr_tidal_tensor_adjoint(const rr_grid_desc* grid, const float* grad_rec, int32_t where, float* dL_dphi,
+                                  float* dL_ddelta, void* stream);
+
+/*
+ * dL/dPhi for maps traced from one potential: all logged steps must share one
+ * grid and their records must come from the same phi (each step's field being
+ * scale_k * that phi). Zeroes grad_rec (caller scratch, n0*n1*n2 gradient
+ * records of 16 floats), adds the adjoint of every logged step, then applies
+ * rr_tidal_tensor_adjoint into dL_dphi (accumulated) / dL_ddelta (NULL: delta
+ * derived from phi). RR_ERR_STATE if no step was traced or the grids differ.
+ */
+rr_status rr_trace_backward(rr_ctx* ctx, const double* dL_dkappa, const double* dL_dkborn, float* grad_rec,
+                            float* dL_dphi, float* dL_ddelta, void* stream);
 
 /*
  * One trace step that allocates nothing -- for callers that cannot let a

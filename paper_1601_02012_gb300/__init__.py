@@ -10,12 +10,14 @@ from __future__ import annotations
 from . import _rr
 from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, bundle_desc, grid_desc,
                   rr_create, rr_destroy, rr_finalize, rr_footprint_bbox, rr_reset, rr_segment_count,
-                  rr_status_string, rr_sync_status, rr_tidal_tensor, rr_trace_step)
+                  rr_status_string, rr_step_count, rr_sync_status, rr_tidal_tensor, rr_tidal_tensor_adjoint,
+                  rr_trace_backward, rr_trace_step, rr_trace_step_adjoint)
 
 __all__ = [
-    "Tracer", "trace_kappa", "record_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
+    "Tracer", "trace_kappa", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
-    "rr_segment_count", "rr_status_string", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
+    "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
+    "rr_trace_backward", "TraceKappa", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
 ]
 
 
@@ -24,6 +26,14 @@ def record_buffer(grid, device="cuda"):
     import torch
     n = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
     return torch.empty((n, 8), dtype=torch.float32, device=device)
+
+
+def grad_buffer(grid, device="cuda"):
+    """Uninitialised device buffer for n0*n1*n2 gradient records of 16 floats
+    (hi and lo words of the 8 record channels)."""
+    import torch
+    n = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
+    return torch.empty((n, 16), dtype=torch.float32, device=device)
 
 
 class Tracer:
@@ -79,6 +89,20 @@ class Tracer:
     def segments(self, per_ray=None, stream=None) -> int:
         return rr_segment_count(self.ctx, per_ray, stream)
 
+    def backward(self, grid, dkappa, dkborn=None, grad_rec=None, dphi=None, ddelta=None, stream=None):
+        """dL/dPhi (and dL/ddelta if ``ddelta`` is given: delta was an input)
+        for all logged steps, through rr_trace_backward."""
+        import torch
+        n = tuple(int(x) for x in grid.n)
+        dev = (dkappa if dkappa is not None else dkborn).device
+        if grad_rec is None:
+            grad_rec = grad_buffer(grid, device=dev)
+        if dphi is None:
+            dphi = torch.zeros(n, dtype=torch.float32, device=dev)
+        rr_trace_backward(self.ctx, dkappa.contiguous() if dkappa is not None else None,
+                          dkborn.contiguous() if dkborn is not None else None, grad_rec, dphi, ddelta, stream)
+        return dphi
+
 
 def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=True, stream=None):
     """Trace a bundle through a sequence of steps on one potential.
@@ -100,3 +124,51 @@ def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=
         return k, kb, tr.segments()
     finally:
         tr.close()
+
+
+def _make_autograd():
+    import torch
+
+    class TraceKappa(torch.autograd.Function):
+        """(kappa, kappa_born) = trace(phi) as a differentiable torch op.
+
+        forward: rr_tidal_tensor + rr_trace_step per step + rr_finalize;
+        backward: rr_trace_backward (the hand-written adjoint), giving dL/dPhi
+        for the FP32 potential. The maps are FP64, shaped [ny, nx].
+        """
+
+        @staticmethod
+        def forward(ctx, phi, grid, bundle, steps, footprint=True):
+            tr = Tracer(bundle)
+            rec = record_buffer(grid, device=phi.device)
+            for st in steps:
+                bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
+                tr.tidal(grid, phi.detach().contiguous(), rec, bbox=bbox)
+                tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a)
+            k, kb = tr.finalize()
+            ctx.tracer = tr
+            ctx.grid = grid
+            return k, kb
+
+        @staticmethod
+        def backward(ctx, gk, gb):
+            tr = ctx.tracer
+            dphi = tr.backward(ctx.grid, gk.contiguous() if gk is not None else None,
+                               gb.contiguous() if gb is not None else None)
+            tr.close()
+            return dphi, None, None, None, None
+
+    return TraceKappa
+
+
+class _Lazy:
+    _fn = None
+
+    def __getattr__(self, name):
+        if _Lazy._fn is None:
+            _Lazy._fn = _make_autograd()
+        return getattr(_Lazy._fn, name)
+
+
+#: torch.autograd.Function: TraceKappa.apply(phi, grid, bundle, steps) -> (kappa, kappa_born)
+TraceKappa = _Lazy()

@@ -72,6 +72,10 @@ def load() -> C.CDLL:
             "rr_sync_status": ([P, P], C.c_int),
             "rr_segment_count": ([P, C.POINTER(C.c_uint64), P, P], C.c_int),
             "rr_trace_step_noalloc": ([P, P, P, D, D, D, D, P, P, P], C.c_int),
+            "rr_step_count": ([P, C.POINTER(C.c_int32)], C.c_int),
+            "rr_trace_step_adjoint": ([P, I32, P, P, P, P], C.c_int),
+            "rr_tidal_tensor_adjoint": ([P, P, I32, P, P, P], C.c_int),
+            "rr_trace_backward": ([P, P, P, P, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -187,6 +191,27 @@ def rr_segment_count(ctx, per_ray=None, stream=None) -> int:
     tot = C.c_uint64(0)
     _check(load().rr_segment_count(ctx, C.byref(tot), _ptr(per_ray), _stream(stream)), "rr_segment_count")
     return int(tot.value)
+
+
+def rr_step_count(ctx) -> int:
+    n = C.c_int32(0)
+    _check(load().rr_step_count(ctx, C.byref(n)), "rr_step_count")
+    return int(n.value)
+
+
+def rr_trace_step_adjoint(ctx, step: int, dL_dkappa, dL_dkborn, grad_rec, stream=None) -> None:
+    _check(load().rr_trace_step_adjoint(ctx, int(step), _ptr(dL_dkappa), _ptr(dL_dkborn), _ptr(grad_rec),
+                                        _stream(stream)), "rr_trace_step_adjoint")
+
+
+def rr_tidal_tensor_adjoint(grid: rr_grid_desc, grad_rec, where: int, dL_dphi, dL_ddelta=None, stream=None) -> None:
+    _check(load().rr_tidal_tensor_adjoint(C.byref(grid), _ptr(grad_rec), int(where), _ptr(dL_dphi),
+                                          _ptr(dL_ddelta), _stream(stream)), "rr_tidal_tensor_adjoint")
+
+
+def rr_trace_backward(ctx, dL_dkappa, dL_dkborn, grad_rec, dL_dphi, dL_ddelta=None, stream=None) -> None:
+    _check(load().rr_trace_backward(ctx, _ptr(dL_dkappa), _ptr(dL_dkborn), _ptr(grad_rec), _ptr(dL_dphi),
+                                    _ptr(dL_ddelta), _stream(stream)), "rr_trace_backward")
 
 
 def rr_trace_step_noalloc(bundle: rr_bundle_desc, grid: rr_grid_desc, rec, chi_a: float, chi_b: float,

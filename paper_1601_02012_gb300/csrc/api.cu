@@ -14,7 +14,7 @@ namespace {
 
 bool is_finite(double x) { return std::isfinite(x); }
 
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool is_aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 rr_status check_bundle(const rr_bundle_desc* b)
 {
@@ -66,6 +66,42 @@ void free_state(RayState& s)
     cudaFree(s.err);
     cudaFree(s.total);
     s = RayState{};
+}
+
+
+// The step geometry and the context's state pointers, as the kernels take them.
+TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
+                          double scale, double a_step)
+{
+    const rr_bundle_desc& b = ctx->bundle;
+    TraceArgs a;
+    a.rec = reinterpret_cast<const float4*>(rec);
+    a.n0 = grid->n[0]; a.n1 = grid->n[1]; a.n2 = grid->n[2];
+    a.h = grid->box / grid->n[0];
+    a.inv_h = 1.0 / a.h;
+    a.inv_hf = (float)a.inv_h;
+    split_ff(a.inv_h, a.ihh, a.ihl);
+    a.nx = b.nx; a.ny = b.ny;
+    a.obs0 = b.obs[0]; a.obs1 = b.obs[1]; a.obs2 = b.obs[2];
+    for (int i = 0; i < 3; ++i) split_ff(b.obs[i], a.oh[i], a.ol[i]);
+    a.chi_s = b.chi_s;
+    a.chi_a = chi_a;
+    a.chi_b = chi_b;
+    split_ff(chi_a, a.cah, a.cal);
+    a.Lf = (float)(chi_a - chi_b);
+    a.D0f = (float)(b.chi_s - chi_a);
+    a.inv_chi_s_f = (float)(1.0 / b.chi_s);
+    a.periodic = (b.flags & RR_PERIODIC) ? 1 : 0;
+    a.dir = ctx->st.dir;
+    a.dirh = ctx->st.dirh;
+    a.dirl = ctx->st.dirl;
+    a.kacc = ctx->st.kacc;
+    a.bacc = ctx->st.bacc;
+    a.nseg = ctx->st.nseg;
+    a.err = ctx->st.err;
+    split_ff(scale, a.sch, a.scl);
+    split_ff(scale * 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step, a.bsh, a.bsl);
+    return a;
 }
 
 }  // namespace
@@ -158,7 +194,7 @@ rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const floa
 {
     rr_status st = check_grid(grid);
     if (st != RR_OK) return st;
-    if (!phi || !rec || !aligned16(rec)) return RR_ERR_ARG;
+    if (!phi || !rec || !is_aligned16(rec)) return RR_ERR_ARG;
     if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
     if (bbox) {
         for (int a = 0; a < 3; ++a) {
@@ -207,7 +243,7 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     if (!ctx) return RR_ERR_ARG;
     rr_status st = check_grid(grid);
     if (st != RR_OK) return st;
-    if (!rec || !aligned16(rec)) return RR_ERR_ARG;
+    if (!rec || !is_aligned16(rec)) return RR_ERR_ARG;
     if (!is_finite(chi_a) || !is_finite(chi_b) || !is_finite(scale) || !is_finite(a_step) || !(a_step > 0)) return RR_ERR_ARG;
     if (!(chi_a > chi_b) || chi_b < 0 || chi_a > ctx->bundle.chi_s * (1.0 + 1e-12)) return RR_ERR_ARG;
     if (!ctx->log.empty()) {
@@ -215,33 +251,7 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
         if (fabs(prev - chi_a) > 1e-12 * std::max(1.0, fabs(chi_a))) return RR_ERR_STATE;
     }
     const rr_bundle_desc& b = ctx->bundle;
-    TraceArgs a;
-    a.rec = reinterpret_cast<const float4*>(rec);
-    a.n0 = grid->n[0]; a.n1 = grid->n[1]; a.n2 = grid->n[2];
-    a.h = grid->box / grid->n[0];
-    a.inv_h = 1.0 / a.h;
-    a.inv_hf = (float)a.inv_h;
-    split_ff(a.inv_h, a.ihh, a.ihl);
-    a.nx = b.nx; a.ny = b.ny;
-    a.obs0 = b.obs[0]; a.obs1 = b.obs[1]; a.obs2 = b.obs[2];
-    for (int i = 0; i < 3; ++i) split_ff(b.obs[i], a.oh[i], a.ol[i]);
-    a.chi_s = b.chi_s;
-    a.chi_a = chi_a;
-    a.chi_b = chi_b;
-    split_ff(chi_a, a.cah, a.cal);
-    a.Lf = (float)(chi_a - chi_b);
-    a.D0f = (float)(b.chi_s - chi_a);
-    a.inv_chi_s_f = (float)(1.0 / b.chi_s);
-    a.periodic = (b.flags & RR_PERIODIC) ? 1 : 0;
-    a.dir = ctx->st.dir;
-    a.dirh = ctx->st.dirh;
-    a.dirl = ctx->st.dirl;
-    a.kacc = ctx->st.kacc;
-    a.bacc = ctx->st.bacc;
-    a.nseg = ctx->st.nseg;
-    a.err = ctx->st.err;
-    split_ff(scale, a.sch, a.scl);
-    split_ff(scale * 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step, a.bsh, a.bsl);
+    TraceArgs a = make_trace_args(ctx, grid, rec, chi_a, chi_b, scale, a_step);
     cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream);
     if (e != cudaSuccess) return from_cuda(e);
     ctx->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
@@ -283,6 +293,64 @@ rr_status rr_segment_count(rr_ctx* ctx, uint64_t* total, uint32_t* per_ray, void
                                          (cudaStream_t)stream));
     }
     return RR_OK;
+}
+
+rr_status rr_step_count(rr_ctx* ctx, int32_t* n)
+{
+    if (!ctx || !n) return RR_ERR_ARG;
+    *n = (int32_t)ctx->log.size();
+    return RR_OK;
+}
+
+rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkappa, const double* dL_dkborn,
+                                float* grad_rec, void* stream)
+{
+    if (!ctx || !grad_rec || !is_aligned16(grad_rec)) return RR_ERR_ARG;
+    if (!dL_dkappa && !dL_dkborn) return RR_ERR_ARG;
+    if (step < 0 || step >= (int32_t)ctx->log.size()) return RR_ERR_STATE;
+    const StepRecord& r = ctx->log[(size_t)step];
+    // the records pointer is not read by the adjoint (it needs geometry only)
+    TraceArgs a = make_trace_args(ctx, &r.grid, grad_rec, r.chi_a, r.chi_b, r.scale, r.a_step);
+    AdjArgs g;
+    g.dkappa = dL_dkappa;
+    g.dkborn = dL_dkborn;
+    g.grad = reinterpret_cast<float4*>(grad_rec);
+    g.kscale = r.scale;
+    g.bscale = r.scale * 1.5 * r.grid.omega_m * kH0OverC * kH0OverC / r.a_step;
+    return from_cuda(launch_trace_adjoint(a, g, ctx->bundle.interp, (ctx->bundle.flags & RR_FP64_DDA) != 0,
+                                          (cudaStream_t)stream));
+}
+
+rr_status rr_tidal_tensor_adjoint(const rr_grid_desc* grid, const float* grad_rec, int32_t where, float* dL_dphi,
+                                  float* dL_ddelta, void* stream)
+{
+    rr_status st = check_grid(grid);
+    if (st != RR_OK) return st;
+    if (!grad_rec || !is_aligned16(grad_rec) || !dL_dphi) return RR_ERR_ARG;
+    if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
+    return from_cuda(launch_tidal_adjoint(*grid, grad_rec, where, dL_dphi, dL_ddelta, (cudaStream_t)stream));
+}
+
+rr_status rr_trace_backward(rr_ctx* ctx, const double* dL_dkappa, const double* dL_dkborn, float* grad_rec,
+                            float* dL_dphi, float* dL_ddelta, void* stream)
+{
+    if (!ctx || !grad_rec || !dL_dphi) return RR_ERR_ARG;
+    if (!dL_dkappa && !dL_dkborn) return RR_ERR_ARG;
+    if (ctx->log.empty()) return RR_ERR_STATE;
+    const rr_grid_desc& g = ctx->log.front().grid;
+    for (const StepRecord& r : ctx->log)
+        if (r.grid.n[0] != g.n[0] || r.grid.n[1] != g.n[1] || r.grid.n[2] != g.n[2] || r.grid.box != g.box ||
+            r.grid.omega_m != g.omega_m)
+            return RR_ERR_STATE;
+    const size_t npts = (size_t)g.n[0] * g.n[1] * g.n[2];
+    cudaError_t e = cudaMemsetAsync(grad_rec, 0, npts * 16 * sizeof(float), (cudaStream_t)stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int32_t k = 0; k < (int32_t)ctx->log.size(); ++k) {
+        rr_status st = rr_trace_step_adjoint(ctx, k, dL_dkappa, dL_dkborn, grad_rec, stream);
+        if (st != RR_OK) return st;
+    }
+    const int where = ctx->bundle.interp == RR_TRILINEAR ? RR_AT_VERTICES : RR_AT_CENTRES;
+    return rr_tidal_tensor_adjoint(&g, grad_rec, where, dL_dphi, dL_ddelta, stream);
 }
 
 }  // extern "C"

@@ -61,11 +61,24 @@ struct TraceArgs {
     float bsh, bsl;             // scale * 1.5 Omega_m (H0/c)^2 / a_step, float-float
 };
 
+// Adjoint of one step: per-ray derivatives of the loss and the gradient
+// records (2 float4 per point, same layout as the records).
+struct AdjArgs {
+    const double* dkappa;       // dL/dkappa per ray, or NULL
+    const double* dkborn;       // dL/dkappa_born per ray, or NULL
+    float4* grad;
+    double kscale;              // the step's scale
+    double bscale;              // scale * 1.5 Omega_m (H0/c)^2 / a_step
+};
+
 // Launchers (one per translation unit).
 cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s);
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
+cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s);
+cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
+                                 cudaStream_t s);
 cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
                             double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s);
 

@@ -117,6 +117,118 @@ __global__ void __launch_bounds__(NT) tidal_kernel(TidalArgs a)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Transpose of the above: gradient records (16 floats per point: the hi and lo
+// words of 8 channels, at vertices or centres) -> dL/dPhi
+// (and dL/ddelta when delta was an independent input).
+//   vertices: gH(c) = (1/8) sum of the gradient records of the 8 vertices of c
+//             (the transpose of the 8-cell mean);
+//   delta derived from tr(H): gH_aa += gdelta / (1.5 Omega_m (H0/c)^2);
+//   dL/dPhi(m) += sum_ab (D_ab^T gH_ab)(m), and the central differences are
+//             symmetric on the periodic grid, so D_ab^T = D_ab.
+// One CTA handles 4 x 4 x 16 cells; each output cell is written by one thread.
+// ---------------------------------------------------------------------------
+
+constexpr int AX = 4, AY = 4, AZ = 16;
+
+struct TidalAdjArgs {
+    const float4* grad;
+    float* dphi;
+    float* ddelta;
+    int n0, n1, n2;
+    float ih2, iq, dinv;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(NT) tidal_adjoint_kernel(TidalAdjArgs a)
+{
+    constexpr int V = (MODE == 0) ? 1 : 0;
+    // gH is needed on the cells of the tile plus a halo of one
+    constexpr int HX = AX + 2, HY = AY + 2, HZ = AZ + 2, NH = HX * HY * HZ;
+    // gradient records: vertices c..c+1 of those cells (MODE 0) or the cells themselves
+    constexpr int GX = HX + V, GY = HY + V, GZ = HZ + V, NG = GX * GY * GZ;
+    __shared__ float sg[7][NG];
+    __shared__ float sh[6][NH];
+
+    const int cx0 = blockIdx.z * AX, cy0 = blockIdx.y * AY, cz0 = blockIdx.x * AZ;   // first output cell
+    for (int i = threadIdx.x; i < NG; i += NT) {
+        const int z = i % GZ, y = (i / GZ) % GY, x = i / (GZ * GY);
+        const int gx = wrapi(cx0 - 1 + x, a.n0), gy = wrapi(cy0 - 1 + y, a.n1), gz = wrapi(cz0 - 1 + z, a.n2);
+        const size_t p = ((size_t)gx * a.n1 + gy) * a.n2 + gz;
+        // hi + lo of each channel (see the gradient record layout in rr.h)
+        const float4 h0 = __ldg(a.grad + 4 * p), h1 = __ldg(a.grad + 4 * p + 1);
+        const float4 l0 = __ldg(a.grad + 4 * p + 2), l1 = __ldg(a.grad + 4 * p + 3);
+        sg[0][i] = h0.x + l0.x; sg[1][i] = h0.y + l0.y; sg[2][i] = h0.z + l0.z; sg[3][i] = h0.w + l0.w;
+        sg[4][i] = h1.x + l1.x; sg[5][i] = h1.y + l1.y; sg[6][i] = h1.z + l1.z;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NH; i += NT) {
+        const int z = i % HZ, y = (i / HZ) % HY, x = i / (HZ * HY);
+        float g[7];
+#pragma unroll
+        for (int ch = 0; ch < 7; ++ch) {
+            if (MODE == 0) {
+                float acc = 0.f;
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy) {
+                        const int base = ((x + dx) * GY + (y + dy)) * GZ + z;
+                        acc += sg[ch][base] + sg[ch][base + 1];
+                    }
+                g[ch] = acc * 0.125f;
+            } else {
+                g[ch] = sg[ch][(x * GY + y) * GZ + z];
+            }
+        }
+        if (!a.ddelta) {
+            const float fd = g[6] * a.dinv;
+            g[0] += fd; g[1] += fd; g[2] += fd;
+        }
+#pragma unroll
+        for (int ch = 0; ch < 6; ++ch) sh[ch][i] = g[ch];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < AX * AY * AZ; i += NT) {
+        const int z = i % AZ, y = (i / AZ) % AY, x = i / (AZ * AY);
+        constexpr int SX = HY * HZ, SY = HZ;
+        const int ci = ((x + 1) * HY + (y + 1)) * HZ + (z + 1);
+        const float* xx = sh[0] + ci;
+        const float* yy = sh[1] + ci;
+        const float* zz = sh[2] + ci;
+        const float* xy = sh[3] + ci;
+        const float* xz = sh[4] + ci;
+        const float* yz = sh[5] + ci;
+        float d = (xx[-SX] - 2.f * xx[0] + xx[SX]) * a.ih2;
+        d += (yy[-SY] - 2.f * yy[0] + yy[SY]) * a.ih2;
+        d += (zz[-1] - 2.f * zz[0] + zz[1]) * a.ih2;
+        d += ((xy[SX + SY] + xy[-SX - SY]) - (xy[SX - SY] + xy[-SX + SY])) * a.iq;
+        d += ((xz[SX + 1] + xz[-SX - 1]) - (xz[SX - 1] + xz[-SX + 1])) * a.iq;
+        d += ((yz[SY + 1] + yz[-SY - 1]) - (yz[SY - 1] + yz[-SY + 1])) * a.iq;
+        if (cx0 + x >= a.n0 || cy0 + y >= a.n1 || cz0 + z >= a.n2) continue;
+        const size_t p = ((size_t)(cx0 + x) * a.n1 + (cy0 + y)) * a.n2 + (cz0 + z);
+        a.dphi[p] += d;
+        if (a.ddelta) {
+            float gd;
+            if (MODE == 0) {
+                float acc = 0.f;
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy) {
+                        const int base = ((x + 1 + dx) * GY + (y + 1 + dy)) * GZ + (z + 1);
+                        acc += sg[6][base] + sg[6][base + 1];
+                    }
+                gd = acc * 0.125f;
+            } else {
+                gd = sg[6][((x + 1) * GY + (y + 1)) * GZ + (z + 1)];
+            }
+            a.ddelta[p] += gd;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
@@ -144,6 +256,26 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
         tidal_kernel<0><<<grid, NT, 0, s>>>(a);
     else
         tidal_kernel<1><<<grid, NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
+                                 cudaStream_t s)
+{
+    TidalAdjArgs a;
+    a.grad = reinterpret_cast<const float4*>(grad_rec);
+    a.dphi = dphi;
+    a.ddelta = ddelta;
+    a.n0 = g.n[0]; a.n1 = g.n[1]; a.n2 = g.n[2];
+    const double h = g.box / g.n[0];
+    a.ih2 = (float)(1.0 / (h * h));
+    a.iq = (float)(0.25 / (h * h));
+    a.dinv = (float)(1.0 / (1.5 * g.omega_m * kH0OverC * kH0OverC));
+    dim3 grid((a.n2 + AZ - 1) / AZ, (a.n1 + AY - 1) / AY, (a.n0 + AX - 1) / AX);
+    if (where == RR_AT_VERTICES)
+        tidal_adjoint_kernel<0><<<grid, NT, 0, s>>>(a);
+    else
+        tidal_adjoint_kernel<1><<<grid, NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
