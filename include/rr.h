@@ -218,6 +218,73 @@ rr_status rr_trace_backward(rr_ctx* ctx, const double* dL_dkappa, const double* 
                             float* dL_dphi, float* dL_ddelta, void* stream);
 
 /*
+ * Batches: many bundles (lightcones) with their own grids, fields, ray counts
+ * and source distances, traced by one persistent launch whose blocks take ray
+ * tiles of all bundles from a device work counter (a counter that only
+ * increments: no block waits on another). All bundles of a batch share
+ * `interp` and the RR_FP64_DDA flag. Each bundle has its own rr_ctx
+ * (rr_batch_context), so rr_trace_step_adjoint / rr_trace_backward work on
+ * the bundles of a batch as on single contexts.
+ *
+ * Per step: rr_batch_set_step for every bundle (host-side: checks, step log,
+ * staging of the kernel arguments in pinned host memory), then
+ * rr_batch_upload (copies the staged table to the device), rr_batch_trace
+ * (zeroes the work counter, one persistent launch), and after the last step
+ * rr_batch_finalize (maps). Upload, trace and finalize only enqueue work on
+ * `stream`, so they can be captured in a CUDA graph together with the
+ * bundles' rr_tidal_tensor calls; a replay of that graph re-reads the staged
+ * table, so restaging between replays (after the previous replay finished)
+ * changes the steps. rr_batch_sync_status synchronises and reports.
+ */
+typedef struct rr_batch rr_batch;
+
+/* n bundles; RR_ERR_ARG if n < 1 or the bundles mix interp / RR_FP64_DDA. */
+rr_status rr_batch_create(int32_t n, const rr_bundle_desc* bundles, rr_batch** out);
+rr_status rr_batch_destroy(rr_batch* b);
+rr_status rr_batch_size(rr_batch* b, int32_t* n);
+/* The context of bundle i (owned by the batch; do not destroy it). */
+rr_status rr_batch_context(rr_batch* b, int32_t i, rr_ctx** ctx);
+/* rr_reset of every bundle; clears the staged steps. */
+rr_status rr_batch_reset(rr_batch* b, void* stream);
+/* Zero every bundle's accumulators, segment counters and error word (device
+ * memsets only: the step logs and the staged steps stay), e.g. at the start of
+ * a captured graph that re-traces the same steps. */
+rr_status rr_batch_clear(rr_batch* b, void* stream);
+/* Stage one step of bundle i (arguments and checks as rr_trace_step). */
+rr_status rr_batch_set_step(rr_batch* b, int32_t i, const rr_grid_desc* grid, const float* rec, double chi_a,
+                            double chi_b, double scale, double a_step);
+/* Copy the staged table to the device. RR_ERR_STATE if a bundle has no staged step. */
+rr_status rr_batch_upload(rr_batch* b, void* stream);
+/* Trace the uploaded step of every bundle in one persistent launch. */
+rr_status rr_batch_trace(rr_batch* b, void* stream);
+/* Maps of every bundle: kappa[i], kappa_born[i] (host arrays of device FP64
+ * pointers; kappa_born may be NULL). Does not synchronise. */
+rr_status rr_batch_finalize(rr_batch* b, double* const* kappa, double* const* kappa_born, void* stream);
+/* Synchronise `stream`; *total_segments (may be NULL) = segments of all
+ * bundles since reset; returns the first non-OK error word of a bundle. */
+rr_status rr_batch_sync_status(rr_batch* b, uint64_t* total_segments, void* stream);
+/*
+ * Launch shape: a warp covers wx x (32/wx) pixels (wx in 1..32, a power of
+ * two), a block bwx x bwy warps (at most 8), each counter increment takes
+ * `chunk` tiles (1..64), blocks_per_sm persistent blocks per SM (0: as many as
+ * the occupancy calculator allows). Results do not depend on the shape.
+ */
+rr_status rr_batch_set_tuning(rr_batch* b, int32_t wx, int32_t bwx, int32_t bwy, int32_t chunk,
+                              int32_t blocks_per_sm);
+/* out = {wx, bwx, bwy, chunk, blocks_per_sm}. */
+rr_status rr_batch_get_tuning(rr_batch* b, int32_t out[5]);
+/*
+ * Autotuner: times `reps` traces of the staged step for every candidate
+ * shape (wx in {4, 8, 16, 32}; 2, 4 or 8 warps per block in several
+ * arrangements; chunk in {1, 2, 4}) with CUDA events and keeps the fastest
+ * (*best_ms = its mean time). Synchronises. The timing runs accumulate into
+ * the bundles' sums, so it clears every bundle's accumulators and counters
+ * afterwards and re-uploads the staged step: call it right after staging the
+ * first step, before tracing anything that must be kept.
+ */
+rr_status rr_batch_autotune(rr_batch* b, int32_t reps, float* best_ms, void* stream);
+
+/*
  * One trace step that allocates nothing -- for callers that cannot let a
  * library allocate device memory: a host framework that already owns the
  * device memory pool through its own allocator, code that cannot afford the

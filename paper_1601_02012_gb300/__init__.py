@@ -13,7 +13,10 @@ from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, 
                   rr_status_string, rr_step_count, rr_sync_status, rr_tidal_tensor, rr_tidal_tensor_adjoint,
                   rr_trace_backward, rr_trace_step, rr_trace_step_adjoint)
 
+from .batch import Batch  # noqa: E402
+
 __all__ = [
+    "Batch",
     "Tracer", "trace_kappa", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",

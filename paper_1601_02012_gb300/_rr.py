@@ -76,6 +76,20 @@ def load() -> C.CDLL:
             "rr_trace_step_adjoint": ([P, I32, P, P, P, P], C.c_int),
             "rr_tidal_tensor_adjoint": ([P, P, I32, P, P, P], C.c_int),
             "rr_trace_backward": ([P, P, P, P, P, P, P], C.c_int),
+            "rr_batch_create": ([I32, P, C.POINTER(C.c_void_p)], C.c_int),
+            "rr_batch_destroy": ([P], C.c_int),
+            "rr_batch_size": ([P, C.POINTER(C.c_int32)], C.c_int),
+            "rr_batch_context": ([P, I32, C.POINTER(C.c_void_p)], C.c_int),
+            "rr_batch_reset": ([P, P], C.c_int),
+            "rr_batch_clear": ([P, P], C.c_int),
+            "rr_batch_set_step": ([P, I32, P, P, D, D, D, D], C.c_int),
+            "rr_batch_upload": ([P, P], C.c_int),
+            "rr_batch_trace": ([P, P], C.c_int),
+            "rr_batch_finalize": ([P, P, P, P], C.c_int),
+            "rr_batch_sync_status": ([P, C.POINTER(C.c_uint64), P], C.c_int),
+            "rr_batch_set_tuning": ([P, I32, I32, I32, I32, I32], C.c_int),
+            "rr_batch_get_tuning": ([P, P], C.c_int),
+            "rr_batch_autotune": ([P, I32, C.POINTER(C.c_float), P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -224,3 +238,76 @@ def rr_trace_step_noalloc(bundle: rr_bundle_desc, grid: rr_grid_desc, rec, chi_a
     _check(load().rr_trace_step_noalloc(C.byref(bundle), C.byref(grid), _ptr(rec), float(chi_a), float(chi_b),
                                         float(scale), float(a_step), _ptr(kappa), _ptr(kappa_born),
                                         _stream(stream)), "rr_trace_step_noalloc")
+
+
+# ---- batches ---------------------------------------------------------------
+
+def rr_batch_create(bundles) -> C.c_void_p:
+    arr = (rr_bundle_desc * len(bundles))(*bundles)
+    h = C.c_void_p()
+    _check(load().rr_batch_create(len(bundles), C.cast(arr, C.c_void_p), C.byref(h)), "rr_batch_create")
+    return h
+
+
+def rr_batch_destroy(b) -> None:
+    _check(load().rr_batch_destroy(b), "rr_batch_destroy")
+
+
+def rr_batch_context(b, i: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().rr_batch_context(b, int(i), C.byref(h)), "rr_batch_context")
+    return h
+
+
+def rr_batch_reset(b, stream=None) -> None:
+    _check(load().rr_batch_reset(b, _stream(stream)), "rr_batch_reset")
+
+
+def rr_batch_clear(b, stream=None) -> None:
+    _check(load().rr_batch_clear(b, _stream(stream)), "rr_batch_clear")
+
+
+def rr_batch_set_step(b, i: int, grid: rr_grid_desc, rec, chi_a: float, chi_b: float, scale: float = 1.0,
+                      a_step: float = 1.0) -> None:
+    _check(load().rr_batch_set_step(b, int(i), C.byref(grid), _ptr(rec), float(chi_a), float(chi_b), float(scale),
+                                    float(a_step)), "rr_batch_set_step")
+
+
+def rr_batch_upload(b, stream=None) -> None:
+    _check(load().rr_batch_upload(b, _stream(stream)), "rr_batch_upload")
+
+
+def rr_batch_trace(b, stream=None) -> None:
+    _check(load().rr_batch_trace(b, _stream(stream)), "rr_batch_trace")
+
+
+def rr_batch_finalize(b, kappas, kborns=None, stream=None) -> None:
+    n = len(kappas)
+    ka = (C.c_void_p * n)(*[t.data_ptr() for t in kappas])
+    kb = None if kborns is None else (C.c_void_p * n)(*[t.data_ptr() for t in kborns])
+    _check(load().rr_batch_finalize(b, C.cast(ka, C.c_void_p), None if kb is None else C.cast(kb, C.c_void_p),
+                                    _stream(stream)), "rr_batch_finalize")
+
+
+def rr_batch_sync_status(b, stream=None):
+    """(status code, total segments)"""
+    tot = C.c_uint64(0)
+    code = load().rr_batch_sync_status(b, C.byref(tot), _stream(stream))
+    return int(code), int(tot.value)
+
+
+def rr_batch_set_tuning(b, wx: int, bwx: int, bwy: int, chunk: int = 1, blocks_per_sm: int = 0) -> None:
+    _check(load().rr_batch_set_tuning(b, int(wx), int(bwx), int(bwy), int(chunk), int(blocks_per_sm)),
+           "rr_batch_set_tuning")
+
+
+def rr_batch_get_tuning(b):
+    arr = (C.c_int32 * 5)()
+    _check(load().rr_batch_get_tuning(b, C.cast(arr, C.c_void_p)), "rr_batch_get_tuning")
+    return tuple(int(x) for x in arr)
+
+
+def rr_batch_autotune(b, reps: int = 3, stream=None) -> float:
+    ms = C.c_float(0)
+    _check(load().rr_batch_autotune(b, int(reps), C.byref(ms), _stream(stream)), "rr_batch_autotune")
+    return float(ms.value)

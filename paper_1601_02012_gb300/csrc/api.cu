@@ -69,6 +69,10 @@ void free_state(RayState& s)
 }
 
 
+}  // namespace
+
+namespace rr {
+
 // The step geometry and the context's state pointers, as the kernels take them.
 TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
                           double scale, double a_step)
@@ -104,7 +108,27 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     return a;
 }
 
-}  // namespace
+
+rr_status validate_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
+                        double scale, double a_step)
+{
+    if (!ctx) return RR_ERR_ARG;
+    rr_status st = check_grid(grid);
+    if (st != RR_OK) return st;
+    if (!rec || !is_aligned16(rec)) return RR_ERR_ARG;
+    if (!is_finite(chi_a) || !is_finite(chi_b) || !is_finite(scale) || !is_finite(a_step) || !(a_step > 0))
+        return RR_ERR_ARG;
+    if (!(chi_a > chi_b) || chi_b < 0 || chi_a > ctx->bundle.chi_s * (1.0 + 1e-12)) return RR_ERR_ARG;
+    if (!ctx->log.empty()) {
+        const double prev = ctx->log.back().chi_b;
+        if (fabs(prev - chi_a) > 1e-12 * std::max(1.0, fabs(chi_a))) return RR_ERR_STATE;
+    }
+    return RR_OK;
+}
+
+rr_status status_of_cuda(cudaError_t e) { return from_cuda(e); }
+
+}  // namespace rr
 
 extern "C" {
 
@@ -240,16 +264,8 @@ rr_status rr_footprint_bbox(const rr_bundle_desc* b, const rr_grid_desc* g, doub
 rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
                         double scale, double a_step, void* stream)
 {
-    if (!ctx) return RR_ERR_ARG;
-    rr_status st = check_grid(grid);
+    rr_status st = validate_step(ctx, grid, rec, chi_a, chi_b, scale, a_step);
     if (st != RR_OK) return st;
-    if (!rec || !is_aligned16(rec)) return RR_ERR_ARG;
-    if (!is_finite(chi_a) || !is_finite(chi_b) || !is_finite(scale) || !is_finite(a_step) || !(a_step > 0)) return RR_ERR_ARG;
-    if (!(chi_a > chi_b) || chi_b < 0 || chi_a > ctx->bundle.chi_s * (1.0 + 1e-12)) return RR_ERR_ARG;
-    if (!ctx->log.empty()) {
-        const double prev = ctx->log.back().chi_b;
-        if (fabs(prev - chi_a) > 1e-12 * std::max(1.0, fabs(chi_a))) return RR_ERR_STATE;
-    }
     const rr_bundle_desc& b = ctx->bundle;
     TraceArgs a = make_trace_args(ctx, grid, rec, chi_a, chi_b, scale, a_step);
     cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream);

@@ -71,16 +71,45 @@ struct AdjArgs {
     double bscale;              // scale * 1.5 Omega_m (H0/c)^2 / a_step
 };
 
+// Ray-tile shape: a warp covers wx x (32/wx) pixels, a block bwx x bwy warps.
+struct TileCfg {
+    int wx = 8, bwx = 2, bwy = 2;
+};
+
+// Arguments of the persistent batched trace (device pointers).
+struct BatchArgs {
+    const TraceArgs* cones;     // per bundle
+    const int* tile_start;      // ncones + 1 prefix offsets of the ray tiles
+    const int* tiles_x;         // tiles along x per bundle
+    int ncones;
+    int* counter;               // work counter, zeroed before each launch
+    int chunk;                  // tiles taken per counter increment
+    TileCfg tile;
+};
+
 // Launchers (one per translation unit).
 cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s);
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
+cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t);
+cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
+int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
+dim3 tile_grid(const TileCfg& t, int nx, int ny);
+bool tile_ok(const TileCfg& t);
 cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s);
 cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
                                  cudaStream_t s);
 cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
                             double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s);
+
+// The step geometry and a context's state pointers as the kernels take them.
+TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
+                          double scale, double a_step);
+// Argument and step-order checks of rr_trace_step.
+rr_status validate_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
+                        double scale, double a_step);
+rr_status status_of_cuda(cudaError_t e);
 
 // hi = (float)x, lo = (float)(x - hi)
 inline void split_ff(double x, float& hi, float& lo)

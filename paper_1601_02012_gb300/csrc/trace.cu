@@ -35,10 +35,17 @@
 namespace rr {
 namespace {
 
-constexpr int WX = 8, WY = 4;     // warp tile of rays (x fastest)
-constexpr int WPX = 2, WPY = 2;   // warps per block
-constexpr int BTX = WX * WPX, BTY = WY * WPY;
-constexpr int NT = 32 * WPX * WPY;
+constexpr int NT_MAX = 256;       // largest block the tile configurations use
+
+// Ray (ix, iy) handled by this thread in ray tile (tx, ty): a warp covers
+// wx x (32/wx) neighbouring pixels (x fastest), a block bwx x bwy warps.
+__device__ __forceinline__ void tile_ray(const TileCfg& t, int tx, int ty, int& ix, int& iy)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wy = 32 / t.wx;
+    ix = tx * (t.wx * t.bwx) + (warp % t.bwx) * t.wx + (lane % t.wx);
+    iy = ty * (wy * t.bwy) + (warp / t.bwx) * wy + (lane / t.wx);
+}
 
 __device__ __forceinline__ int wrap_once(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
@@ -304,16 +311,12 @@ __device__ __forceinline__ bool walk_setup(const TraceArgs& A, long long rid, Wa
     return true;
 }
 
-// INTERP: RR_NGP or RR_TRILINEAR. R: float (compensated FP32 walk) or double
-// (plain FP64 walk).
+// One ray over one step. INTERP: RR_NGP or RR_TRILINEAR. R: float
+// (compensated FP32 walk) or double (plain FP64 walk).
 template <int INTERP, class R>
-__global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
+__device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
     constexpr bool F64 = sizeof(R) == 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ix = blockIdx.x * BTX + (warp % WPX) * WX + (lane % WX);
-    const int iy = blockIdx.y * BTY + (warp / WPX) * WY + (lane / WX);
-    if (ix >= A.nx || iy >= A.ny) return;
     const long long rid = (long long)iy * A.nx + ix;
     const int nn[3] = {A.n0, A.n1, A.n2};
     Walk<R> W;
@@ -494,6 +497,61 @@ __global__ void __launch_bounds__(NT) trace_kernel(const TraceArgs A)
 }
 
 
+template <int INTERP, class R>
+__global__ void __launch_bounds__(NT_MAX) trace_kernel(const TraceArgs A, const TileCfg t)
+{
+    int ix, iy;
+    tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R>(A, ix, iy);
+}
+
+// Persistent work queue over the ray tiles of many bundles (lightcones): each
+// block takes `chunk` consecutive tiles from a global counter (monotonic, no
+// waiting), finds the bundle by binary search in the tile offsets, stages that
+// bundle's arguments in shared memory and traces the tile.
+template <int INTERP, class R>
+__global__ void __launch_bounds__(NT_MAX) trace_batch_kernel(const BatchArgs B)
+{
+    __shared__ TraceArgs sA;
+    __shared__ int s_item, s_cone;
+    const int total = B.tile_start[B.ncones];
+    while (true) {
+        if (threadIdx.x == 0) s_item = atomicAdd(B.counter, B.chunk);
+        __syncthreads();
+        const int item0 = s_item;
+        __syncthreads();
+        if (item0 >= total) break;
+        for (int c = 0; c < B.chunk; ++c) {
+            const int item = item0 + c;
+            if (item >= total) break;
+            if (threadIdx.x == 0) {
+                int lo = 0, hi = B.ncones - 1;   // last cone with tile_start <= item
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (B.tile_start[mid] <= item) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_cone = lo;
+            }
+            __syncthreads();
+            const int cone = s_cone;
+            {
+                const int* src = reinterpret_cast<const int*>(B.cones + cone);
+                int* dst = reinterpret_cast<int*>(&sA);
+                for (int i = threadIdx.x; i < (int)(sizeof(TraceArgs) / sizeof(int)); i += blockDim.x)
+                    dst[i] = __ldg(src + i);
+            }
+            __syncthreads();
+            const int local = item - B.tile_start[cone];
+            const int ntx = B.tiles_x[cone];
+            int ix, iy;
+            tile_ray(B.tile, local % ntx, local / ntx, ix, iy);
+            if (ix < sA.nx && iy < sA.ny) trace_ray<INTERP, R>(sA, ix, iy);
+            __syncthreads();
+        }
+    }
+}
+
 // Transpose of line_cubic: given the weights J_N of the cubic's coefficients
 // e_{N-1} in the segment integral, the weight of each corner value q[m].
 __device__ __forceinline__ void line_cubic_adjoint(const float J[4], float u0, float u1, float u2, float v0,
@@ -561,12 +619,11 @@ __device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long 
 // through Q_kappa = w . H) and gb * S (delta), with compensated 16-byte atomic
 // adds (flush_grad).
 template <int INTERP, class R>
-__global__ void __launch_bounds__(NT) trace_adjoint_kernel(const TraceArgs A, const AdjArgs B)
+__global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A, const AdjArgs B, const TileCfg tc)
 {
     constexpr bool F64 = sizeof(R) == 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ix = blockIdx.x * BTX + (warp % WPX) * WX + (lane % WX);
-    const int iy = blockIdx.y * BTY + (warp / WPX) * WY + (lane / WX);
+    int ix, iy;
+    tile_ray(tc, blockIdx.x, blockIdx.y, ix, iy);
     if (ix >= A.nx || iy >= A.ny) return;
     const long long rid = (long long)iy * A.nx + ix;
     const float gk = B.dkappa ? (float)(B.dkappa[rid] * B.kscale) : 0.f;
@@ -699,40 +756,92 @@ __global__ void __launch_bounds__(NT) trace_adjoint_kernel(const TraceArgs A, co
 
 }  // namespace
 
-cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s)
+dim3 tile_grid(const TileCfg& t, int nx, int ny)
 {
-    dim3 grid((a.nx + BTX - 1) / BTX, (a.ny + BTY - 1) / BTY);
+    const int bx = t.wx * t.bwx, by = (32 / t.wx) * t.bwy;
+    return dim3((unsigned)((nx + bx - 1) / bx), (unsigned)((ny + by - 1) / by));
+}
+
+bool tile_ok(const TileCfg& t)
+{
+    return (t.wx == 1 || t.wx == 2 || t.wx == 4 || t.wx == 8 || t.wx == 16 || t.wx == 32) && t.bwx >= 1 &&
+           t.bwy >= 1 && t.bwx * t.bwy * 32 <= NT_MAX;
+}
+
+cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t)
+{
+    if (!tile_ok(t)) return cudaErrorInvalidValue;
+    const dim3 grid = tile_grid(t, a.nx, a.ny);
+    const int nt = 32 * t.bwx * t.bwy;
     if (interp == RR_TRILINEAR) {
         if (fp64_dda)
-            trace_kernel<RR_TRILINEAR, double><<<grid, NT, 0, s>>>(a);
+            trace_kernel<RR_TRILINEAR, double><<<grid, nt, 0, s>>>(a, t);
         else
-            trace_kernel<RR_TRILINEAR, float><<<grid, NT, 0, s>>>(a);
+            trace_kernel<RR_TRILINEAR, float><<<grid, nt, 0, s>>>(a, t);
     } else {
         if (fp64_dda)
-            trace_kernel<RR_NGP, double><<<grid, NT, 0, s>>>(a);
+            trace_kernel<RR_NGP, double><<<grid, nt, 0, s>>>(a, t);
         else
-            trace_kernel<RR_NGP, float><<<grid, NT, 0, s>>>(a);
+            trace_kernel<RR_NGP, float><<<grid, nt, 0, s>>>(a, t);
     }
     return cudaGetLastError();
 }
 
+cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s)
+{
+    return launch_trace(a, interp, fp64_dda, s, TileCfg{});
+}
+
+cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s)
+{
+    if (!tile_ok(b.tile) || b.chunk < 1 || blocks < 1) return cudaErrorInvalidValue;
+    const int nt = 32 * b.tile.bwx * b.tile.bwy;
+    if (interp == RR_TRILINEAR) {
+        if (fp64_dda)
+            trace_batch_kernel<RR_TRILINEAR, double><<<blocks, nt, 0, s>>>(b);
+        else
+            trace_batch_kernel<RR_TRILINEAR, float><<<blocks, nt, 0, s>>>(b);
+    } else {
+        if (fp64_dda)
+            trace_batch_kernel<RR_NGP, double><<<blocks, nt, 0, s>>>(b);
+        else
+            trace_batch_kernel<RR_NGP, float><<<blocks, nt, 0, s>>>(b);
+    }
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t)
+{
+    const int nt = 32 * t.bwx * t.bwy;
+    int n = 0;
+    cudaError_t e;
+    if (interp == RR_TRILINEAR)
+        e = fp64_dda ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_batch_kernel<RR_TRILINEAR, double>, nt, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_batch_kernel<RR_TRILINEAR, float>, nt, 0);
+    else
+        e = fp64_dda ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_batch_kernel<RR_NGP, double>, nt, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_batch_kernel<RR_NGP, float>, nt, 0);
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
 }  // namespace rr
 
 namespace rr {
 
 cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s)
 {
-    dim3 grid((a.nx + BTX - 1) / BTX, (a.ny + BTY - 1) / BTY);
+    const TileCfg t{};
+    const dim3 grid = tile_grid(t, a.nx, a.ny);
+    const int nt = 32 * t.bwx * t.bwy;
     if (interp == RR_TRILINEAR) {
         if (fp64_dda)
-            trace_adjoint_kernel<RR_TRILINEAR, double><<<grid, NT, 0, s>>>(a, b);
+            trace_adjoint_kernel<RR_TRILINEAR, double><<<grid, nt, 0, s>>>(a, b, t);
         else
-            trace_adjoint_kernel<RR_TRILINEAR, float><<<grid, NT, 0, s>>>(a, b);
+            trace_adjoint_kernel<RR_TRILINEAR, float><<<grid, nt, 0, s>>>(a, b, t);
     } else {
         if (fp64_dda)
-            trace_adjoint_kernel<RR_NGP, double><<<grid, NT, 0, s>>>(a, b);
+            trace_adjoint_kernel<RR_NGP, double><<<grid, nt, 0, s>>>(a, b, t);
         else
-            trace_adjoint_kernel<RR_NGP, float><<<grid, NT, 0, s>>>(a, b);
+            trace_adjoint_kernel<RR_NGP, float><<<grid, nt, 0, s>>>(a, b, t);
     }
     return cudaGetLastError();
 }

@@ -270,3 +270,66 @@ def grf_phi_cached(n: int, box: float, seed: int, omega_m: float = 0.3) -> np.nd
     np.save(tmp, phi)
     os.replace(tmp, path)
     return phi
+
+
+def grf_phi_torch(n: int, box: float, seed: int, device="cuda", omega_m: float = 0.3,
+                  spectral_index: float = -3.0, rms_delta: float = 1.0):
+    """The grf_phi recipe (same spectrum, cut and normalisation) drawn and
+    transformed on a torch device: white noise from torch.Generator(seed)
+    (Philox on CUDA), FP64 FFTs, FP32 result. Deterministic for a seed on a
+    given device type; its values differ from grf_phi's (another generator)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    white = torch.randn((n, n, n), generator=gen, device=device, dtype=torch.float64)
+    wk = torch.fft.rfftn(white)
+    del white
+    k1 = 2.0 * math.pi * torch.fft.fftfreq(n, d=box / n, device=device, dtype=torch.float64)
+    kz = 2.0 * math.pi * torch.fft.rfftfreq(n, d=box / n, device=device, dtype=torch.float64)
+    k2 = k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2
+    knyq = math.pi * n / box
+    live = (k2 > 0) & (k2 <= knyq * knyq)
+    shape = torch.where(live, k2.clamp_min(1e-300) ** (0.25 * spectral_index), torch.zeros_like(k2))
+    if n % 2 == 0:
+        shape[n // 2, :, :] = 0.0
+        shape[:, n // 2, :] = 0.0
+        shape[:, :, -1] = 0.0
+    wk *= shape
+    del shape, live
+    dk = torch.fft.irfftn(-k2 * wk, s=(n, n, n))
+    pref = 1.5 * omega_m * H0_OVER_C ** 2
+    rms = float(torch.sqrt(torch.mean((dk / pref) ** 2)))
+    del dk
+    phi = torch.fft.irfftn(wk, s=(n, n, n))
+    del wk, k2
+    phi *= rms_delta / rms
+    return phi.to(torch.float32).contiguous()
+
+
+@dataclass
+class Cone:
+    """One lightcone of a batch: its grid, bundle and field seed."""
+    grid: Grid
+    bundle: Bundle
+    field_seed: int
+
+
+def batch_workload(n: int = 64, seed: int = 4, sizes=(128, 256, 512), rays=(256, 2048),
+                   fov_deg=(1.0, 10.0), chi_s=(200.0, 1000.0)) -> list:
+    """Independent lightcones of uneven sizes: grid side drawn uniformly from
+    `sizes`, box side = chi_s (observer at the centre of the z = 0 face, one
+    step from chi_s to 0), ray-grid side log-uniform in `rays` rounded to a
+    multiple of 32, field of view uniform in `fov_deg`, chi_s uniform in
+    `chi_s`; all from numpy's PCG64(seed); cone i's field seed is 1000 + i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cones = []
+    for i in range(n):
+        ng = int(rng.choice(np.asarray(sizes)))
+        side = int(round(math.exp(rng.uniform(math.log(rays[0]), math.log(rays[1]))) / 32.0)) * 32
+        side = max(32, side)
+        fov = deg(float(rng.uniform(*fov_deg)))
+        cs = float(rng.uniform(*chi_s))
+        g = Grid((ng, ng, ng), cs)
+        b = Bundle(side, side, fov, fov, (cs / 2.0, cs / 2.0, 0.0), cs)
+        cones.append(Cone(g, b, 1000 + i))
+    return cones
