@@ -95,6 +95,7 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     a.Lf = (float)(chi_a - chi_b);
     a.D0f = (float)(b.chi_s - chi_a);
     a.inv_chi_s_f = (float)(1.0 / b.chi_s);
+    a.sub_len = (float)(32.0 * a.h);
     a.periodic = (b.flags & RR_PERIODIC) ? 1 : 0;
     a.dir = ctx->st.dir;
     a.dirh = ctx->st.dirh;

@@ -124,6 +124,7 @@ extern "C" rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const r
     a.Lf = (float)(chi_a - chi_b);
     a.D0f = (float)(bundle->chi_s - chi_a);
     a.inv_chi_s_f = (float)(1.0 / bundle->chi_s);
+    a.sub_len = (float)(32.0 * a.h);
     a.periodic = (bundle->flags & RR_PERIODIC) ? 1 : 0;
     a.dir = dir;
     a.dirh = dirh;

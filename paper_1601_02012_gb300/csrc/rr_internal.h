@@ -49,6 +49,7 @@ struct TraceArgs {
     float Lf;                   // chi_a - chi_b rounded to FP32
     float D0f;                  // chi_s - chi_a rounded to FP32
     float inv_chi_s_f;          // 1/chi_s rounded to FP32
+    float sub_len;              // FP32 walk: longest sub-step (32 cell sizes)
     int periodic;
     const double* dir;
     const float4* dirh;

@@ -27,9 +27,12 @@ struct TidalArgs {
     float dinv;       // 1 / (1.5 Omega_m (H0/c)^2)
 };
 
+// i mod n; the integer division only runs for indices outside [0, n) (halo
+// points at the periodic seam, or tiles larger than a small grid).
 __device__ __forceinline__ int wrapi(int i, int n)
 {
-    int r = i % n;
+    if (i >= 0 && i < n) return i;
+    const int r = i % n;
     return r < 0 ? r + n : r;
 }
 
@@ -240,9 +243,10 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
     a.rec = reinterpret_cast<float4*>(rec);
     a.n0 = g.n[0]; a.n1 = g.n[1]; a.n2 = g.n[2];
     if (bbox) {
-        a.x0 = bbox[0]; a.ex = bbox[1] - bbox[0];
-        a.y0 = bbox[2]; a.ey = bbox[3] - bbox[2];
-        a.z0 = bbox[4]; a.ez = bbox[5] - bbox[4];
+        // the box start taken into [0, n), so that most indices need no wrap
+        a.x0 = ((bbox[0] % g.n[0]) + g.n[0]) % g.n[0]; a.ex = bbox[1] - bbox[0];
+        a.y0 = ((bbox[2] % g.n[1]) + g.n[1]) % g.n[1]; a.ey = bbox[3] - bbox[2];
+        a.z0 = ((bbox[4] % g.n[2]) + g.n[2]) % g.n[2]; a.ez = bbox[5] - bbox[4];
     } else {
         a.x0 = a.y0 = a.z0 = 0;
         a.ex = g.n[0]; a.ey = g.n[1]; a.ez = g.n[2];

@@ -171,23 +171,23 @@ struct Walk {
     int max_iter;
 };
 
-// Start point, start cell and crossing distances of ray `rid` for the step
-// [chi_b, chi_a] (see the file comment). Returns false if the ray does not
-// traverse any part of the step.
-template <class R>
-__device__ __forceinline__ bool walk_setup(const TraceArgs& A, long long rid, Walk<R>& W)
+// The part [lo, hi] of the step [chi_b, chi_a] that ray `rid` traverses: all
+// of it with periodic wrap; clipped to the box in FP64 otherwise. chi_hi is
+// also given as a float-float pair, with hi - lo and chi_s - hi in FP32.
+struct RayRange {
+    float ch, cl, Lf, D0f;
+    double hi, lo;
+};
+
+__device__ __forceinline__ bool ray_range(const TraceArgs& A, long long rid, RayRange& g)
 {
-    constexpr bool F64 = sizeof(R) == 8;
-    const int nn[3] = {A.n0, A.n1, A.n2};
-    const float4 nh4 = A.dirh[rid];
-    const float nh[3] = {nh4.x, nh4.y, nh4.z};
-    // The part of [chi_b, chi_a] this ray traverses: all of it with periodic
-    // wrap; clipped to the box in FP64 otherwise.
-    float ch = A.cah, cl = A.cal, Lf = A.Lf, D0f = A.D0f;
-    double hi = A.chi_a, lo = A.chi_b;
+    g.ch = A.cah; g.cl = A.cal; g.Lf = A.Lf; g.D0f = A.D0f;
+    g.hi = A.chi_a; g.lo = A.chi_b;
     if (!A.periodic) {
+        const int nn[3] = {A.n0, A.n1, A.n2};
         const double nd[3] = {A.dir[3 * rid], A.dir[3 * rid + 1], A.dir[3 * rid + 2]};
         const double obs[3] = {A.obs0, A.obs1, A.obs2};
+        double hi = g.hi, lo = g.lo;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double ext = nn[a] * A.h;
@@ -200,11 +200,47 @@ __device__ __forceinline__ bool walk_setup(const TraceArgs& A, long long rid, Wa
             }
         }
         if (!(hi > lo)) return false;
-        ch = (float)hi;
-        cl = (float)(hi - (double)ch);
-        Lf = (float)(hi - lo);
-        D0f = (float)(A.chi_s - hi);
+        g.hi = hi;
+        g.lo = lo;
+        g.ch = (float)hi;
+        g.cl = (float)(hi - (double)g.ch);
+        g.Lf = (float)(hi - lo);
+        g.D0f = (float)(A.chi_s - hi);
     }
+    return true;
+}
+
+// Sub-step j of nsub equal pieces of the FP32 walk: start (bh + bl) =
+// chi_hi - j dsub as a float-float pair (exact: TwoProd and TwoSum), length,
+// and chi_s - start. Consecutive sub-steps meet at the same point.
+__device__ __forceinline__ void sub_step(const RayRange& g, int j, int nsub, float dsub, float& bh, float& bl,
+                                         float& L, float& D0)
+{
+    if (nsub == 1) {
+        bh = g.ch; bl = g.cl; L = g.Lf; D0 = g.D0f;
+        return;
+    }
+    float p, pe;
+    two_prod((float)j, dsub, p, pe);
+    float s, t;
+    two_sum(g.ch, -p, s, t);
+    const float lo = t + (g.cl - pe);
+    bh = s + lo;
+    bl = lo - (bh - s);
+    L = (j == nsub - 1) ? fmaf(-(float)(nsub - 1), dsub, g.Lf) : dsub;
+    D0 = fmaf((float)j, dsub, g.D0f);
+}
+
+// Start point (bh + bl, or hi in FP64), start cell and crossing distances of
+// ray `rid` for a walk of length Lf (see the file comment).
+template <class R>
+__device__ __forceinline__ void walk_setup(const TraceArgs& A, long long rid, float ch, float cl, float Lf,
+                                           float D0f, double hi, double lo, Walk<R>& W)
+{
+    constexpr bool F64 = sizeof(R) == 8;
+    const int nn[3] = {A.n0, A.n1, A.n2};
+    const float4 nh4 = A.dirh[rid];
+    const float nh[3] = {nh4.x, nh4.y, nh4.z};
 
     // Start cell; distances (in cells) from the start point to the lower and
     // upper face on each axis.
@@ -308,7 +344,6 @@ __device__ __forceinline__ bool walk_setup(const TraceArgs& A, long long rid, Wa
     W.D0 = F64 ? (R)(A.chi_s - hi) : (R)D0f;
     W.max_iter =
         (int)ceilf(Lf * (fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2])) * A.inv_hf * 1.0001f) + 8;
-    return true;
 }
 
 // One ray over one step. INTERP: RR_NGP or RR_TRILINEAR. R: float
@@ -319,8 +354,25 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     constexpr bool F64 = sizeof(R) == 8;
     const long long rid = (long long)iy * A.nx + ix;
     const int nn[3] = {A.n0, A.n1, A.n2};
+    RayRange rg;
+    if (!ray_range(A, rid, rg)) return;
+    const R chis = (R)A.chi_s;
+    const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
+    const long long sx = (long long)A.n1 * A.n2, sy = A.n2;
+    // FP32: sub-steps of at most sub_len, so that the path variable stays small
+    const int nsub = F64 ? 1 : max(1, (int)ceilf(rg.Lf / A.sub_len));
+    const float dsub = rg.Lf / (float)nsub;
+
+    Acc<R> sk, sb;
+    uint32_t cnt = 0;
+    int iter = 0;
+    bool overflow = false;
+    int pc0 = -1, pc1 = -1, pc2 = -1;   // cell where the previous sub-step ended
+    for (int j = 0; j < nsub && !overflow; ++j) {
+    float bh, bl, Lj, D0j;
+    sub_step(rg, j, nsub, dsub, bh, bl, Lj, D0j);
     Walk<R> W;
-    if (!walk_setup<R>(A, rid, W)) return;
+    walk_setup<R>(A, rid, bh, bl, Lj, D0j, rg.hi, rg.lo, W);
     int* c = W.c;
     const int* sgn = W.sgn;
     int* k = W.k;
@@ -333,9 +385,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     const float* w = W.w;
     const R L = W.L, chiA0 = W.chiA0, D0 = W.D0;
     const int max_iter = W.max_iter;
-    const R chis = (R)A.chi_s;
-    const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
-    const long long sx = (long long)A.n1 * A.n2, sy = A.n2;
+    // a sub-step that resumes inside the previous one's last cell does not
+    // start a new cell segment
+    bool resume = j > 0 && c[0] == pc0 && c[1] == pc1 && c[2] == pc2;
+    iter = 0;
 
     // Field cache: projected kappa values and delta at the 8 mirrored corners
     // (trilinear) or at the cell centre (NGP).
@@ -356,9 +409,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         qb[0] = r.b.z;
     }
 
-    Acc<R> sk, sb;
-    uint32_t cnt = 0;
-    R sig = 0;                       // path from the step start to the segment entry
+    R sig = 0;                       // path from the sub-step start to the segment entry
     R T[3] = {T0[0], T0[1], T0[2]};  // path to the next face crossing per axis
     // Crossings closer together than the walk resolves are one crossing: a
     // crossing within eps_rel * L of the step's end, and a segment shorter
@@ -368,8 +419,6 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     // into a crossing distance (ulp(|p|) / |n_a|) for rays 1e-4 rad off an axis.
     const R eps_rel = F64 ? (R)1.4551915228366852e-11 : (R)4.76837158203125e-07;
     const R eps_end = L * eps_rel;
-    int iter = 0;
-    bool overflow = false;
     while (true) {
         // exit plane: the nearest face crossing (lowest axis on ties)
         R tend = T[0];
@@ -437,12 +486,14 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                 sk.add((R)qk[0] * J1);
                 sb.add((R)qb[0] * J1);
             }
-            ++cnt;
+            if (resume) resume = false;
+            else ++cnt;
         }
         sig = tend;
         if (last) break;
 
         // cross the exit face e
+        resume = false;
         if (!A.periodic && (ncell < 0 || ncell >= ne)) break;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -485,6 +536,8 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
             break;
         }
     }
+    pc0 = c[0]; pc1 = c[1]; pc2 = c[2];
+    }
 
     if (overflow) atomicOr(A.err, kErrStepLimit);
     if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
@@ -498,7 +551,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 
 
 template <int INTERP, class R>
-__global__ void __launch_bounds__(NT_MAX) trace_kernel(const TraceArgs A, const TileCfg t)
+__global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, const TileCfg t)
 {
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
@@ -510,7 +563,7 @@ __global__ void __launch_bounds__(NT_MAX) trace_kernel(const TraceArgs A, const 
 // waiting), finds the bundle by binary search in the tile offsets, stages that
 // bundle's arguments in shared memory and traces the tile.
 template <int INTERP, class R>
-__global__ void __launch_bounds__(NT_MAX) trace_batch_kernel(const BatchArgs B)
+__global__ void __launch_bounds__(NT_MAX, 2) trace_batch_kernel(const BatchArgs B)
 {
     __shared__ TraceArgs sA;
     __shared__ int s_item, s_cone;
@@ -630,8 +683,20 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
     const float gb = B.dkborn ? (float)(B.dkborn[rid] * B.bscale) : 0.f;
     if (gk == 0.f && gb == 0.f) return;
     const int nn[3] = {A.n0, A.n1, A.n2};
+    RayRange rg;
+    if (!ray_range(A, rid, rg)) return;
+    const R chis = (R)A.chi_s;
+    const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
+    const long long sx = (long long)A.n1 * A.n2, sy = A.n2;
+    const R eps_rel = F64 ? (R)1.4551915228366852e-11 : (R)4.76837158203125e-07;
+    const int nsub = F64 ? 1 : max(1, (int)ceilf(rg.Lf / A.sub_len));
+    const float dsub = rg.Lf / (float)nsub;
+    bool overflow = false;
+    for (int j = 0; j < nsub && !overflow; ++j) {
+    float bh, bl, Lj, D0j;
+    sub_step(rg, j, nsub, dsub, bh, bl, Lj, D0j);
     Walk<R> W;
-    if (!walk_setup<R>(A, rid, W)) return;
+    walk_setup<R>(A, rid, bh, bl, Lj, D0j, rg.hi, rg.lo, W);
     int* c = W.c;
     const int* sgn = W.sgn;
     int* k = W.k;
@@ -639,17 +704,12 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
     int* vhi = W.vhi;
     const float* w = W.w;
     const R L = W.L, chiA0 = W.chiA0, D0 = W.D0;
-    const R chis = (R)A.chi_s;
-    const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
-    const long long sx = (long long)A.n1 * A.n2, sy = A.n2;
-    const R eps_rel = F64 ? (R)1.4551915228366852e-11 : (R)4.76837158203125e-07;
     const R eps_end = L * eps_rel;
 
     float S[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     R sig = 0;
     R T[3] = {W.T0[0], W.T0[1], W.T0[2]};
     int iter = 0;
-    bool overflow = false;
     while (true) {
         R tend = T[0];
         int e = 0;
@@ -750,6 +810,7 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
         }
     } else {
         flush_grad(B.grad, c[0] * sx + c[1] * sy + c[2], S[0], gk, gb, w);
+    }
     }
     if (overflow) atomicOr(A.err, kErrStepLimit);
 }
