@@ -18,15 +18,17 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rr_oracle.c")
+_SRC_AMR = os.path.join(_HERE, "rr_oracle_amr.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP over rays; no fused multiply-add
     contraction, so x86 and Arm give the same bits)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_AMR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-o", _LIB + ".tmp", _SRC, "-lm"]
+               "-o", _LIB + ".tmp", _SRC, _SRC_AMR, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -62,6 +64,12 @@ def _L():
                                                 P, P, P, P]
         _lib.ora_delta_from_tidal_adjoint.argtypes = [P, P, P]
         _lib.ora_tidal_centres_adjoint.argtypes = [P, P, P]
+        _lib.ora_amr_vertex_weights.argtypes = [P, P, P, C.c_long]
+        _lib.ora_amr_vertex_weights.restype = C.c_long
+        _lib.ora_amr_tidal.argtypes = [P, P]
+        _lib.ora_amr_leaf_vertices.argtypes = [P, C.c_int, P, P]
+        _lib.ora_amr_trace_step.argtypes = [P, P, C.c_double, C.c_double, C.c_double, C.c_double, P, P, P, P,
+                                            C.c_long, C.c_int]
     return _lib
 
 
@@ -199,3 +207,94 @@ def trace_adjoint(bundle, grid, steps, dL_dkappa, dL_dkborn=None, delta_derived:
     gphi = np.zeros(shape, np.float64)
     _L().ora_tidal_centres_adjoint(C.byref(g), _ptr(gH), _ptr(gphi))
     return (gphi, None) if delta_derived else (gphi, gd)
+
+
+# ---------------------------------------------------------------------------
+# adaptive meshes
+# ---------------------------------------------------------------------------
+
+_AMR_LMAX = 8
+
+
+class _AmrDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("lmax", C.c_int32), ("box", C.c_double), ("omega_m", C.c_double),
+                ("octs", C.c_void_p * (_AMR_LMAX + 1)), ("noct", C.c_int64 * (_AMR_LMAX + 1)),
+                ("phi", C.c_void_p * (_AMR_LMAX + 1))]
+
+
+class _AmrBundle(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("fov_x", C.c_double), ("fov_y", C.c_double),
+                ("obs", C.c_double * 3), ("chi_s", C.c_double), ("interp", C.c_int32), ("periodic", C.c_int32)]
+
+
+class AmrHandle:
+    """Keeps the numpy arrays of a mesh alive while the oracle reads them."""
+
+    def __init__(self, mesh, phi=None):
+        phi = mesh.phi if phi is None else phi
+        self.keep = []
+        d = _AmrDesc()
+        d.n, d.lmax, d.box, d.omega_m = int(mesh.n), int(mesh.lmax), float(mesh.box), float(mesh.omega_m)
+        for l in range(mesh.lmax + 1):
+            ph = np.ascontiguousarray(phi[l], dtype=np.float64)
+            self.keep.append(ph)
+            d.phi[l] = ph.ctypes.data
+            if l >= 1:
+                oc = np.ascontiguousarray(mesh.octs[l], dtype=np.int32)
+                self.keep.append(oc)
+                d.octs[l] = oc.ctypes.data
+                d.noct[l] = len(oc)
+        self.desc = d
+
+
+def amr_vertex_weights(mesh, V):
+    """The value at finest-lattice point V as rows (level, i, j, k, weight) of leaf values."""
+    h = AmrHandle(mesh, [np.zeros(1)] * (mesh.lmax + 1) if mesh.phi is None else None)
+    v = np.ascontiguousarray(V, dtype=np.int64)
+    rows = np.zeros((64, 5))
+    n = _L().ora_amr_vertex_weights(C.byref(h.desc), _ptr(v), _ptr(rows), 64)
+    if n < 0:
+        raise ValueError(f"oracle: vertex rule failed ({n})")
+    return rows[:n].copy()
+
+
+def amr_tidal(mesh):
+    """7 channels (H xx,yy,zz,xy,xz,yz and delta) at every cell of every level."""
+    h = AmrHandle(mesh)
+    total = mesh.n ** 3 + sum(8 * len(mesh.octs[l]) for l in range(1, mesh.lmax + 1))
+    out = np.zeros((total, 7))
+    if _L().ora_amr_tidal(C.byref(h.desc), _ptr(out)) != 0:
+        raise ValueError("oracle: AMR tidal failed")
+    return out
+
+
+def amr_leaf_vertices(mesh, level, cell):
+    h = AmrHandle(mesh)
+    c = np.ascontiguousarray(cell, dtype=np.int64)
+    out = np.zeros((8, 7))
+    if _L().ora_amr_leaf_vertices(C.byref(h.desc), int(level), _ptr(c), _ptr(out)) != 0:
+        raise ValueError("oracle: AMR vertex failed")
+    return out
+
+
+def amr_trace(bundle, mesh, steps, rids=None) -> TraceResult:
+    """kappa, Born kappa and leaf-segment counts through an adaptive mesh."""
+    h = AmrHandle(mesh)
+    b = _AmrBundle()
+    b.nx, b.ny = int(bundle.nx), int(bundle.ny)
+    b.fov_x, b.fov_y = float(bundle.fov_x), float(bundle.fov_y)
+    for i in range(3):
+        b.obs[i] = float(bundle.obs[i])
+    b.chi_s = float(bundle.chi_s)
+    b.interp = int(bundle.interp)
+    b.periodic = 1 if bundle.periodic else 0
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
+    res = TraceResult(nr)
+    for st in steps:
+        rc = _L().ora_amr_trace_step(C.byref(b), C.byref(h.desc), float(st.chi_a), float(st.chi_b),
+                                     float(st.scale), float(st.a), _ptr(res.kappa), _ptr(res.kborn),
+                                     _ptr(res.nseg), _ptr(ids), 0 if ids is None else len(ids), 0)
+        if rc != 0:
+            raise ValueError(f"oracle: AMR trace failed ({rc})")
+    return res

@@ -333,3 +333,189 @@ def batch_workload(n: int = 64, seed: int = 4, sizes=(128, 256, 512), rays=(256,
         b = Bundle(side, side, fov, fov, (cs / 2.0, cs / 2.0, 0.0), cs)
         cones.append(Cone(g, b, 1000 + i))
     return cones
+
+
+# ---------------------------------------------------------------------------
+# Adaptive meshes (an octree over a periodic coarse grid)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class AmrMesh:
+    """An octree mesh: an n^3 periodic coarse grid (level 0, cell size
+    h0 = box/n) whose cells may be refined into octs of 8 children, down to
+    level lmax (cell size h0 / 2^l).
+
+    octs[l] (l = 1..lmax): int32 array (m_l, 3) of the level-(l-1) cells that
+    are refined, in level-(l-1) integer coordinates, sorted lexicographically;
+    each is the parent of the 8 level-l cells 2 (i,j,k) + (dx, dy, dz),
+    child index dx + 2 dy + 4 dz. Neighbouring leaves differ by at most one
+    level across faces, edges and corners (2:1 balance).
+    phi[l]: level 0 an (n, n, n) array, level l >= 1 an (m_l, 8) array: the
+    potential at every cell centre of that level (leaves and parents)."""
+    n: int
+    box: float
+    lmax: int
+    octs: list
+    phi: list = None
+    omega_m: float = 0.3
+
+    def h(self, level: int) -> float:
+        return self.box / self.n / (1 << level)
+
+    def nleaves(self) -> int:
+        total = self.n ** 3
+        for l in range(1, self.lmax + 1):
+            total += 7 * len(self.octs[l])
+        return total
+
+
+def _neighbours26(cells: np.ndarray, m: int) -> np.ndarray:
+    offs = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], np.int64)
+    return ((cells[:, None, :] + offs[None, :, :]) % m).reshape(-1, 3)
+
+
+def _unique_rows(a: np.ndarray) -> np.ndarray:
+    if len(a) == 0:
+        return a.reshape(0, 3).astype(np.int32)
+    return np.unique(a.astype(np.int64), axis=0).astype(np.int32)
+
+
+def amr_balance(n: int, lmax: int, flags: list) -> list:
+    """From refinement flags flags[l] (level-l cells to refine, l = 0..lmax-1)
+    build a 2:1-balanced octree: a refined level-l cell needs its parent's 26
+    neighbours refined (so its own neighbours exist), applied bottom-up; cells
+    whose parent is not refined are dropped, top-down. Returns octs[0..lmax]
+    (octs[0] unused)."""
+    fl = [_unique_rows(np.asarray(f).reshape(-1, 3)) for f in flags] + [np.zeros((0, 3), np.int32)]
+    for l in range(lmax - 1, 0, -1):
+        if len(fl[l]) == 0:
+            continue
+        parents = fl[l] // 2
+        fl[l - 1] = _unique_rows(np.concatenate([fl[l - 1], _neighbours26(parents, n << (l - 1)),
+                                                 parents]))
+    octs = [np.zeros((0, 3), np.int32)]
+    for l in range(1, lmax + 1):
+        cand = fl[l - 1]
+        if l >= 2 and len(cand):
+            # keep only cells that exist: their parent is refined
+            m = np.int64(n << (l - 2))
+            have = octs[l - 1].astype(np.int64)
+            par = (cand // 2).astype(np.int64)
+            keep = np.isin((par[:, 0] * m + par[:, 1]) * m + par[:, 2], (have[:, 0] * m + have[:, 1]) * m + have[:, 2])
+            cand = cand[keep]
+        octs.append(cand.astype(np.int32))
+    return octs
+
+
+def amr_nested_cubes(n: int, box: float, lmax: int, half_widths) -> AmrMesh:
+    """Hierarchically nested cubic refinements around the box centre (the
+    paper's Gaussian test, Sec. 4): a level-l cell is refined when its centre
+    lies within half_widths[l] (Mpc/h) of the centre along every axis."""
+    flags = []
+    c = box / 2.0
+    for l in range(lmax):
+        m = n << l
+        h = box / m
+        x = (np.arange(m) + 0.5) * h
+        inside = np.nonzero(np.abs(x - c) < half_widths[l])[0]
+        if len(inside) == 0:
+            flags.append(np.zeros((0, 3), np.int32))
+            continue
+        g = np.stack(np.meshgrid(inside, inside, inside, indexing="ij"), -1).reshape(-1, 3)
+        flags.append(g.astype(np.int32))
+    return AmrMesh(n, box, lmax, amr_balance(n, lmax, flags))
+
+
+def amr_random(n: int, box: float, lmax: int, seed: int, sigma_ln: float = 1.5, child_sigma: float = 0.5,
+               threshold: float = 8.0) -> AmrMesh:
+    """Refinement driven by a lognormal density: rho = exp(g - sigma^2/2) on
+    the coarse grid (g Gaussian, P_g propto k^-2, rms sigma_ln), passed to the
+    children by a multiplicative cascade (lognormal factors of rms child_sigma
+    normalised to mean 1 over the 8 siblings); a level-l cell is refined when
+    its mass rho (h_l/h_0)^3 exceeds `threshold` times the mean cell mass of
+    level 0; then 2:1 balanced. numpy PCG64(seed) throughout."""
+    import scipy.fft as sfft
+    rng = np.random.Generator(np.random.PCG64(seed))
+    wk = sfft.rfftn(rng.standard_normal((n, n, n)), workers=-1)
+    k1, kz = _kgrid(n, box)
+    k2 = k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2
+    shape = np.where(k2 > 0, 1.0 / np.sqrt(np.maximum(k2, 1e-300)), 0.0)
+    g = sfft.irfftn(wk * shape, s=(n, n, n), workers=-1)
+    g *= sigma_ln / g.std()
+    rho = np.exp(g - 0.5 * sigma_ln ** 2)
+    flags = []
+    cells = np.stack(np.nonzero(rho > threshold), -1).astype(np.int32)
+    rho_cells = rho[tuple(cells.T)]
+    flags.append(cells)
+    for l in range(1, lmax):
+        if len(cells) == 0:
+            flags.append(np.zeros((0, 3), np.int32))
+            continue
+        f = np.exp(child_sigma * rng.standard_normal((len(cells), 8)))
+        f /= f.mean(axis=1, keepdims=True)
+        child = (2 * cells[:, None, :] + np.array([(i & 1, (i >> 1) & 1, (i >> 2) & 1) for i in range(8)])[None])
+        rho_child = (rho_cells[:, None] * f).reshape(-1)
+        child = child.reshape(-1, 3)
+        mass = rho_child / 8.0 ** l
+        sel = mass > threshold
+        cells, rho_cells = child[sel].astype(np.int32), rho_child[sel]
+        flags.append(cells)
+    return AmrMesh(n, box, lmax, amr_balance(n, lmax, flags))
+
+
+def amr_cell_centres(mesh: AmrMesh, level: int) -> np.ndarray:
+    """Cell centres of a level: (n,n,n,3) for level 0, (m,8,3) for octs."""
+    h = mesh.h(level)
+    if level == 0:
+        x = (np.arange(mesh.n) + 0.5) * h
+        return np.stack(np.meshgrid(x, x, x, indexing="ij"), -1)
+    kids = np.array([(i & 1, (i >> 1) & 1, (i >> 2) & 1) for i in range(8)], np.float64)
+    base = 2.0 * mesh.octs[level].astype(np.float64)
+    return (base[:, None, :] + kids[None] + 0.5) * h
+
+
+def amr_sample(mesh: AmrMesh, fn) -> list:
+    """phi[l] = fn(centres) for every level (fn maps (..., 3) positions to values)."""
+    return [np.ascontiguousarray(fn(amr_cell_centres(mesh, l))) for l in range(mesh.lmax + 1)]
+
+
+def gaussian_fn(amp: float, sigma: float, centre):
+    c = np.asarray(centre, np.float64)
+
+    def f(p):
+        d = p - c
+        return amp * np.exp(-np.sum(d * d, axis=-1) / (2.0 * sigma * sigma))
+    return f
+
+
+def fourier_fn(box: float, nmodes: int, kmax: float, seed: int, spectral_index: float = -3.0,
+               omega_m: float = 0.3, rms_delta: float = 1.0):
+    """A smooth periodic random potential: sum of nmodes plane waves
+    a_k cos(k.x + p_k) with integer wave vectors (periodic in the box),
+    |k| <= kmax, a_k^2 propto |k|^spectral_index, scaled so that the
+    continuum delta = -lap(Phi)/(1.5 Om (H0/c)^2) has the requested rms."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kf = 2.0 * math.pi / box
+    mmax = int(kmax / kf)
+    ks, amps = [], []
+    while len(ks) < nmodes:
+        m = rng.integers(-mmax, mmax + 1, size=3)
+        kk = kf * m.astype(np.float64)
+        kn = float(np.sqrt(kk @ kk))
+        if kn == 0.0 or kn > kmax:
+            continue
+        ks.append(kk)
+        amps.append(kn ** (0.5 * spectral_index) * rng.standard_normal())
+    ks = np.array(ks)
+    amps = np.array(amps)
+    ph = rng.uniform(0, 2 * math.pi, nmodes)
+    pref = 1.5 * omega_m * H0_OVER_C ** 2
+    var = 0.5 * np.sum((amps * np.sum(ks * ks, axis=1) / pref) ** 2)
+    amps *= rms_delta / math.sqrt(var)
+
+    def f(p):
+        out = np.zeros(p.shape[:-1])
+        for i in range(nmodes):
+            out += amps[i] * np.cos(p @ ks[i] + ph[i])
+        return out
+    return f

@@ -1,0 +1,284 @@
+"""Pins of the oracle's adaptive-mesh part (Sec. 2.7, Sec. 3.3, Sec. 4).
+
+The vertex scheme against the weights and counts the paper prints and against
+its stated property (mass from vertices equals mass from centres), the
+interpolant's continuity across coarse-fine faces, the tidal stencils on a
+quadratic potential, the uniform limit (a fully refined level is the uniform
+oracle of twice the resolution), and the paper's Gaussian test with two nested
+refinement levels against adaptive quadrature.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _alpha(Nc, Nfv, dim):
+    f = 4.0 if dim == 2 else 8.0
+    ac = 1.0 / (Nc + sum(Nfv) / f)
+    return ac, [n / f * ac for n in Nfv]
+
+
+def test_printed_weight_examples(oracle_lib):
+    """The weights of the printed examples sum to one (Sec. 2.7), and the
+    oracle reproduces the printed 3D example: a vertex shared by seven coarse
+    cells and one fine cell (N_c = 7, N_f = 1, N_fv = 7) gets 8/63 per coarse
+    cell and 1/9 for the fine one."""
+    with open(os.path.join(GOLDEN, "amr_vertex_weights.json")) as f:
+        G = json.load(f)
+    for ex in G["two_d"].values():
+        ac, af = _alpha(ex["Nc"], ex["Nfv"], 2)
+        assert abs(ex["Nc"] * ac + sum(af) - 1.0) < 1e-15
+    ex = G["three_d"]["seven_coarse_one_fine"]
+    ac, af = _alpha(ex["Nc"], ex["Nfv"], 3)
+    assert abs(ac - 8.0 / 63.0) < 1e-15 and abs(af[0] - 1.0 / 9.0) < 1e-15
+    # one refined coarse cell (2,2,2) of a 6^3 grid: its corner (3,3,3)*h0
+    mesh = synth.AmrMesh(6, 6.0, 1, [np.zeros((0, 3), np.int32), np.array([[2, 2, 2]], np.int32)])
+    rows = oracle_lib.amr_vertex_weights(mesh, [6, 6, 6])   # finest units: h1 = h0/2
+    lv = rows[:, 0]
+    assert np.sum(lv == 0) == 7 and np.sum(lv == 1) == 1
+    assert np.allclose(rows[lv == 0, 4], 8.0 / 63.0, atol=1e-15)
+    assert abs(rows[lv == 1, 4][0] - 1.0 / 9.0) < 1e-15
+    fine = rows[lv == 1][0]
+    assert tuple(fine[1:4]) == (5.0, 5.0, 5.0)     # the child at that corner
+
+
+def _leaves(mesh):
+    """(level, i, j, k) of every leaf."""
+    out = []
+    refined = [set()] + [set() for _ in range(mesh.lmax)]
+    for l in range(1, mesh.lmax + 1):
+        refined[l - 1] = {tuple(r) for r in mesh.octs[l]}
+    for i in range(mesh.n):
+        for j in range(mesh.n):
+            for k in range(mesh.n):
+                if (i, j, k) not in refined[0]:
+                    out.append((0, i, j, k))
+    for l in range(1, mesh.lmax + 1):
+        for p in mesh.octs[l]:
+            for ch in range(8):
+                c = (2 * p[0] + (ch & 1), 2 * p[1] + ((ch >> 1) & 1), 2 * p[2] + ((ch >> 2) & 1))
+                if l == mesh.lmax or c not in refined[l]:
+                    out.append((l,) + c)
+    return out
+
+
+def _leaf_lookup(mesh, leaves):
+    return {lf: i for i, lf in enumerate(leaves)}
+
+
+def test_generated_meshes_are_balanced():
+    mesh = synth.amr_random(8, 16.0, 3, 5, threshold=3.0)
+    leaves = _leaves(mesh)
+    assert len(leaves) == mesh.nleaves()
+    L = mesh.lmax
+    level_at = {}
+    for (l, i, j, k) in leaves:
+        s = 1 << (L - l)
+        level_at[(l, i, j, k)] = l
+    # every finest-lattice cell knows its leaf level; neighbours differ by <= 1
+    M = mesh.n << L
+    lvl = np.full((M, M, M), -1, np.int8)
+    for (l, i, j, k) in leaves:
+        s = 1 << (L - l)
+        lvl[i * s:(i + 1) * s, j * s:(j + 1) * s, k * s:(k + 1) * s] = l
+    assert lvl.min() >= 0
+    for ax in range(3):
+        for sh in (1, -1):
+            assert np.abs(lvl.astype(int) - np.roll(lvl, sh, axis=ax).astype(int)).max() <= 1
+    for sx in (1, -1):
+        for sy in (1, -1):
+            for sz in (1, -1):
+                d = np.abs(lvl.astype(int) - np.roll(lvl, (sx, sy, sz), axis=(0, 1, 2)).astype(int))
+                assert d.max() <= 1
+
+
+def _corner_values(oracle_lib, mesh, leaves, field):
+    index = _leaf_lookup(mesh, leaves)
+    L = mesh.lmax
+    vals = np.zeros((len(leaves), 8))
+    cache = {}
+    for t, (l, i, j, k) in enumerate(leaves):
+        s = 1 << (L - l)
+        for c in range(8):
+            V = ((i + (c & 1)) * s, (j + ((c >> 1) & 1)) * s, (k + ((c >> 2) & 1)) * s)
+            key = tuple(v % (mesh.n << L) for v in V)
+            if key not in cache:
+                rows = oracle_lib.amr_vertex_weights(mesh, key)
+                cache[key] = sum(w * field[index[(int(r[0]), int(r[1]), int(r[2]), int(r[3]))]]
+                                 for r in rows for w in [r[4]])
+            vals[t, c] = cache[key]
+    return vals
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_mass_from_vertices_equals_mass_from_centres(oracle_lib, seed):
+    """Sec. 2.7: the total mass measured from the cell-centre values and from
+    the cell vertices (the trilinear interpolant integrates to the cell volume
+    times the mean of its 8 vertex values) agree exactly, with refinement."""
+    mesh = synth.amr_random(4, 8.0, 2, seed, threshold=1.5)
+    assert len(mesh.octs[1]) > 0 and len(mesh.octs[2]) > 0
+    leaves = _leaves(mesh)
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.5, 2.0, len(leaves))
+    vol = np.array([(mesh.h(l)) ** 3 for (l, _, _, _) in leaves])
+    vals = _corner_values(oracle_lib, mesh, leaves, rho)
+    m_centres = float(np.sum(vol * rho))
+    m_vertices = float(np.sum(vol * vals.mean(axis=1)))
+    assert abs(m_centres - m_vertices) < 1e-12 * m_centres
+
+
+def test_interpolant_continuous_across_refinement(oracle_lib):
+    """The trilinear field of a fine leaf and of the coarse leaf across a
+    coarse-fine face agree on that face (hanging vertices sit on the coarse
+    face's bilinear interpolant)."""
+    mesh = synth.amr_nested_cubes(4, 8.0, 1, [1.9])
+    leaves = _leaves(mesh)
+    index = _leaf_lookup(mesh, leaves)
+    rng = np.random.default_rng(3)
+    rho = rng.standard_normal(len(leaves))
+    vals = _corner_values(oracle_lib, mesh, leaves, rho)
+    L = mesh.lmax
+    M = mesh.n << L
+    checked = 0
+    for t, (l, i, j, k) in enumerate(leaves):
+        if l != 1:
+            continue
+        s = 1
+        for ax in range(3):
+            for side in (0, 1):
+                # neighbour across this face: which leaf?
+                c = [i, j, k]
+                c[ax] += 1 if side else -1
+                cc = tuple(x // 2 % mesh.n for x in c)
+                key = (0,) + cc
+                if key not in index:
+                    continue
+                u = rng.uniform(0, 1, 2)
+                # point on the face in finest (= level 1) units
+                p = np.array([i, j, k], float)
+                p[ax] += side
+                others = [a for a in range(3) if a != ax]
+                p[others[0]] += u[0]
+                p[others[1]] += u[1]
+
+                def tri(vs, org, h):
+                    f = (p - org) / h
+                    out = 0.0
+                    for cn in range(8):
+                        wgt = 1.0
+                        for a in range(3):
+                            bit = (cn >> a) & 1
+                            wgt *= f[a] if bit else 1 - f[a]
+                        out += wgt * vs[cn]
+                    return out
+                fine = tri(vals[t], np.array([i, j, k], float), 1.0)
+                co = index[key]
+                org = np.array(cc, float) * 2.0
+                # unwrap the coarse origin next to the fine leaf
+                for a in range(3):
+                    while org[a] - p[a] > 2.0:
+                        org[a] -= M
+                    while p[a] - org[a] > 2.0:
+                        org[a] += M
+                coarse = tri(vals[co], org, 2.0)
+                assert abs(fine - coarse) < 1e-12, (fine, coarse)
+                checked += 1
+    assert checked > 20
+
+
+def test_tidal_exact_on_quadratic_everywhere(oracle_lib):
+    """Quadratic potential on every level: the stencils are exact, and so is
+    the coarse-interpolated tidal field at refinement boundaries (trilinear
+    interpolation of a constant): H = M at every cell away from the seam."""
+    mesh = synth.amr_nested_cubes(16, 32.0, 2, [9.0, 5.2])
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((3, 3))
+    M = A + A.T
+    mesh.phi = synth.amr_sample(mesh, lambda p: 0.5 * np.einsum("...i,ij,...j->...", p, M, p))
+    H = oracle_lib.amr_tidal(mesh)
+    want = np.array([M[0, 0], M[1, 1], M[2, 2], M[0, 1], M[0, 2], M[1, 2]])
+    # level 0 cells away from the periodic seam
+    n = mesh.n
+    h0 = H[: n ** 3].reshape(n, n, n, 7)[1:-1, 1:-1, 1:-1, :6]
+    assert np.abs(h0 - want).max() < 1e-9
+    # every refined cell (the refined cubes sit in the box interior)
+    assert np.abs(H[n ** 3:, :6] - want).max() < 1e-9
+
+
+def test_uniform_limit(oracle_lib):
+    """A fully refined level reproduces the uniform oracle at twice the
+    resolution, and an unrefined mesh the uniform oracle itself."""
+    n = 6
+    box = 12.0
+    full = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 3)
+    mesh = synth.AmrMesh(n, box, 1, [np.zeros((0, 3), np.int32), full.astype(np.int32)])
+    f = synth.fourier_fn(box, 24, 2 * math.pi / box * 3, 7)
+    mesh.phi = synth.amr_sample(mesh, f)
+    b = synth.Bundle(7, 6, synth.deg(40), synth.deg(30), (5.0, 7.0, 0.0), 14.0)
+    steps = [synth.Step(14.0, 5.0, 1.1, 0.9), synth.Step(5.0, 0.0, 1.0, 1.0)]
+    ra = oracle_lib.amr_trace(b, mesh, steps)
+    g2 = synth.Grid((2 * n, 2 * n, 2 * n), box)
+    phi2 = np.zeros((2 * n,) * 3)
+    cen = synth.amr_cell_centres(mesh, 1)
+    for o, p in enumerate(mesh.octs[1]):
+        for ch in range(8):
+            phi2[2 * p[0] + (ch & 1), 2 * p[1] + ((ch >> 1) & 1), 2 * p[2] + ((ch >> 2) & 1)] = mesh.phi[1][o, ch]
+    ru = oracle_lib.trace(b, g2, *oracle_lib.fields(g2, phi2), steps)
+    assert np.abs(ra.kappa - ru.kappa).max() < 1e-12 * np.abs(ru.kappa).max()
+    assert np.abs(ra.kborn - ru.kborn).max() < 1e-12 * np.abs(ru.kborn).max()
+    assert np.array_equal(ra.nseg, ru.nseg)
+    # no refinement at all
+    mesh0 = synth.AmrMesh(n, box, 1, [np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int32)])
+    mesh0.phi = [mesh.phi[0], np.zeros((0, 8))]
+    g1 = synth.Grid((n, n, n), box)
+    r0 = oracle_lib.amr_trace(b, mesh0, steps)
+    r1 = oracle_lib.trace(b, g1, *oracle_lib.fields(g1, mesh.phi[0]), steps)
+    assert np.abs(r0.kappa - r1.kappa).max() < 1e-12 * np.abs(r1.kappa).max()
+    assert np.array_equal(r0.nseg, r1.nseg)
+
+
+def _gauss_q(p, centre, amp, sigma, nh):
+    x = p - centre
+    r2 = np.sum(x * x, axis=-1)
+    e = amp * np.exp(-r2 / (2 * sigma ** 2))
+    xn = x @ nh
+    return e * ((r2 - xn * xn) / sigma ** 4 - 2.0 / sigma ** 2)
+
+
+def test_gaussian_potential_two_refinement_levels(oracle_lib):
+    """Sec. 4 with its mesh: domain grids of 32^3 and 64^3 refined hierarchically
+    towards the centre with two cubic levels; kappa along a radial slice vs
+    adaptive quadrature: < 3% (32^3) and < 1% (64^3), zero crossings excluded."""
+    from scipy.integrate import quad
+    with open(os.path.join(GOLDEN, "gaussian_e1.json")) as f:
+        E1 = json.load(f)
+    L = E1["box"]
+    amp, sig = E1["potential"]["amp"], E1["potential"]["sigma"]
+    chis = synth.chi_of_z(E1["z_s"])
+    nr = 64
+    b = synth.Bundle(nr, 1, synth.deg(E1["fov_deg"][0]), 0.0, (L / 2, L / 2, 0.0), chis, periodic=False)
+    centre = np.full(3, L / 2)
+    exact = np.zeros(nr)
+    for rid in range(nr):
+        nh, _ = oracle_lib.ray_direction(b, rid)
+        exits = [((L if nh[a] > 0 else 0.0) - b.obs[a]) / nh[a] for a in range(3) if nh[a] != 0]
+        top = min(exits)
+        fq = lambda c: (chis - c) * c / chis * _gauss_q(np.array(b.obs) + c * nh, centre, amp, sig, nh)
+        exact[rid] = quad(fq, 0.0, top, epsabs=0, epsrel=1e-11, limit=400, points=[L / 2])[0]
+    keep = np.abs(exact) > 0.1 * np.abs(exact).max()
+    worst = {}
+    for ng, tol in ((32, E1["max_relative_error"]["32"]), (64, E1["max_relative_error"]["64"])):
+        mesh = synth.amr_nested_cubes(ng, L, 2, [0.3 * L, 0.15 * L])
+        mesh.phi = synth.amr_sample(mesh, synth.gaussian_fn(amp, sig, centre))
+        k = oracle_lib.amr_trace(b, mesh, [synth.Step(chis, 0.0, 1.0, 1.0)]).kappa
+        rel = np.abs(k - exact)[keep] / np.abs(exact[keep])
+        worst[ng] = rel.max()
+        assert rel.max() < tol, (ng, rel.max())
+    assert worst[64] < worst[32]
