@@ -285,6 +285,83 @@ rr_status rr_batch_get_tuning(rr_batch* b, int32_t out[5]);
 rr_status rr_batch_autotune(rr_batch* b, int32_t reps, float* best_ms, void* stream);
 
 /*
+ * Adaptive meshes (Secs. 2.5.1, 2.7, 3.3). A periodic n^3 coarse grid (level
+ * 0, cell size h_0 = box / n) whose cells may be refined into octs of 8
+ * children of half the size, down to level lmax <= 8, 2:1 balanced: the 26
+ * level-(l-1) neighbours of the parent of every level-l oct exist. A cell that
+ * is not refined is a leaf. Coordinates of a level-l cell are integers in
+ * [0, n 2^l); the finest lattice has side n 2^lmax <= 2^24.
+ *
+ * Cells are numbered level after level: level 0 row-major (z fastest), then
+ * for each level l >= 1 oct after oct in the order given to rr_amr_create,
+ * 8 children per oct, child (dx, dy, dz) at 8 o + dx + 2 dy + 4 dz. Leaves are
+ * numbered in the order of their cell numbers.
+ *
+ * rr_amr_create builds the mesh plan on the host and copies it to the current
+ * device (synchronous): per cell its refinement link and either its 18
+ * same-level stencil neighbours or the 8 coarser cells it interpolates from;
+ * per lattice vertex a leaf needs, its value as a weighted sum of up to 8
+ * leaves; per leaf corner the 1, 2 or 4 vertices whose mean it is.
+ *   octs[l]  (l = 1..lmax) host int32 [noct[l] x 3]: the level-(l-1) cells
+ *            refined into level-l octs, each listed once; octs[0] and
+ *            noct[0] are ignored.
+ * RR_ERR_ARG on a bad description, a parent that does not exist, a mesh that
+ * is not 2:1 balanced, or more than 2^31 - 1 cells; RR_ERR_OOM if the plan does
+ * not fit in device memory.
+ */
+typedef struct rr_amr rr_amr;
+
+typedef struct {
+    int32_t n;            /* coarse cells per side, [2, 4096] */
+    int32_t lmax;         /* finest level, [0, 8] */
+    double box;           /* extent in Mpc/h, > 0 */
+    double omega_m;       /* for the Born prefactor and the derived delta */
+} rr_amr_desc;
+
+rr_status rr_amr_create(const rr_amr_desc* desc, const int32_t* const* octs, const int64_t* noct, rr_amr** out);
+/* Free the plan (synchronises the device first). */
+rr_status rr_amr_destroy(rr_amr* mesh);
+/* Cells of all levels, leaves, and distinct lattice vertices of the plan (any may be NULL). */
+rr_status rr_amr_sizes(rr_amr* mesh, int64_t* ncells, int64_t* nleaves, int64_t* nverts);
+
+/*
+ * Leaf records from the potential at every cell centre of every level:
+ *   1. d_a d_b Phi at every cell, level by level: the central differences of
+ *      Eq. (tidalexample) with the level's own spacing when all 18 stencil
+ *      neighbours exist at that level; otherwise the coarser level's values
+ *      interpolated trilinearly to the cell centre (Sec. 3.3); delta from
+ *      tr(H) by the comoving Poisson equation at a = 1.
+ *   2. RR_AT_VERTICES: the value at each leaf corner (Sec. 2.7) -- the mean of
+ *      the 8 same-level leaves around a vertex; Eqs. (alphac3d), (alphaf3d)
+ *      at a vertex shared by coarse and fine leaves; the mean of the 2 or 4
+ *      vertices of the coarse edge or face in whose middle a corner lies.
+ *      RR_AT_CENTRES: the leaf's own cell value.
+ *   phi         device float [ncells], Phi/c^2 at cell centres in cell order.
+ *   where       RR_AT_VERTICES (for RR_TRILINEAR) or RR_AT_CENTRES (RR_NGP).
+ *   leaf_rec    device, 16-byte aligned: RR_AT_VERTICES 64 floats per leaf
+ *               (8 corners, corner dx + 2 dy + 4 dz, 8 floats each as in
+ *               rr_tidal_tensor's records); RR_AT_CENTRES 8 floats per leaf.
+ *   cell_tidal  device float [ncells x 8] or NULL: also receives step 1's
+ *               per-cell records {Hxx, Hyy, Hzz, Hxy}, {Hxz, Hyz, delta, 0}.
+ * Asynchronous on `stream` (lmax + 3 launches).
+ */
+rr_status rr_amr_tidal(rr_amr* mesh, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
+                       void* stream);
+
+/*
+ * rr_trace_step over an adaptive mesh: each ray advances leaf by leaf (the
+ * crossings of the finest lattice grouped per leaf, Sec. 2.5.1) and adds the
+ * integrals of rr_trace_step with each leaf's own cell size. `leaf_rec` from
+ * rr_amr_tidal with RR_AT_VERTICES for RR_TRILINEAR bundles, RR_AT_CENTRES for
+ * RR_NGP. Segment counts count leaf segments. RR_ERR_ARG for RR_FP64_DDA
+ * bundles (the AMR walk is the FP32 float-float form only); other checks and
+ * the step log as rr_trace_step. Steps traced this way have no adjoint:
+ * rr_trace_step_adjoint and rr_trace_backward return RR_ERR_STATE for them.
+ */
+rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* mesh, const float* leaf_rec, double chi_a, double chi_b,
+                            double scale, double a_step, void* stream);
+
+/*
  * One trace step that allocates nothing -- for callers that cannot let a
  * library allocate device memory: a host framework that already owns the
  * device memory pool through its own allocator, code that cannot afford the

@@ -14,9 +14,10 @@ from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, 
                   rr_trace_backward, rr_trace_step, rr_trace_step_adjoint)
 
 from .batch import Batch  # noqa: E402
+from ._rr import rr_amr_create, rr_amr_destroy, rr_amr_sizes, rr_amr_tidal, rr_amr_trace_step  # noqa: E402
 
 __all__ = [
-    "Batch",
+    "Batch", "AmrMesh", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal", "rr_amr_trace_step",
     "Tracer", "trace_kappa", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
@@ -92,6 +93,10 @@ class Tracer:
     def segments(self, per_ray=None, stream=None) -> int:
         return rr_segment_count(self.ctx, per_ray, stream)
 
+    def amr_step(self, mesh, leaf_rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):
+        """One step over an adaptive mesh (``AmrMesh``) from its leaf records."""
+        rr_amr_trace_step(self.ctx, mesh.handle, leaf_rec, chi_a, chi_b, scale, a, stream)
+
     def backward(self, grid, dkappa, dkborn=None, grad_rec=None, dphi=None, ddelta=None, stream=None):
         """dL/dPhi (and dL/ddelta if ``ddelta`` is given: delta was an input)
         for all logged steps, through rr_trace_backward."""
@@ -105,6 +110,46 @@ class Tracer:
         rr_trace_backward(self.ctx, dkappa.contiguous() if dkappa is not None else None,
                           dkborn.contiguous() if dkborn is not None else None, grad_rec, dphi, ddelta, stream)
         return dphi
+
+
+class AmrMesh:
+    """An adaptive mesh's device plan (an rr_amr).
+
+    n, lmax, box, omega_m: coarse cells per side, finest level, extent, Omega_m.
+    octs[l] (l = 1..lmax): [m_l, 3] integer coordinates of the level-(l-1)
+    cells refined into level-l octs. Cells are numbered level 0 row-major,
+    then per level oct after oct (in the given order) x 8 children.
+    """
+
+    def __init__(self, n, lmax, box, octs, omega_m=0.3):
+        _rr.load()
+        d = _rr.rr_amr_desc()
+        d.n, d.lmax, d.box, d.omega_m = int(n), int(lmax), float(box), float(omega_m)
+        self.desc = d
+        self.handle = rr_amr_create(d, octs)
+        self.ncells, self.nleaves, self.nverts = rr_amr_sizes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            rr_amr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def record_buffer(self, where=RR_AT_VERTICES, device="cuda"):
+        """Uninitialised leaf records: 64 floats per leaf at vertices, 8 at centres."""
+        import torch
+        per = 64 if where == RR_AT_VERTICES else 8
+        return torch.empty((self.nleaves, per), dtype=torch.float32, device=device)
+
+    def tidal(self, phi, leaf_rec, where=RR_AT_VERTICES, cell_tidal=None, stream=None):
+        """rr_amr_tidal: phi (float32 [ncells], cell order) -> leaf records."""
+        rr_amr_tidal(self.handle, phi, where, leaf_rec, cell_tidal, stream)
+        return leaf_rec
 
 
 def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=True, stream=None):

@@ -43,6 +43,10 @@ class rr_grid_desc(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("box", C.c_double), ("omega_m", C.c_double)]
 
 
+class rr_amr_desc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("lmax", C.c_int32), ("box", C.c_double), ("omega_m", C.c_double)]
+
+
 class RRError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -90,6 +94,11 @@ def load() -> C.CDLL:
             "rr_batch_set_tuning": ([P, I32, I32, I32, I32, I32], C.c_int),
             "rr_batch_get_tuning": ([P, P], C.c_int),
             "rr_batch_autotune": ([P, I32, C.POINTER(C.c_float), P], C.c_int),
+            "rr_amr_create": ([P, P, P, C.POINTER(C.c_void_p)], C.c_int),
+            "rr_amr_destroy": ([P], C.c_int),
+            "rr_amr_sizes": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+            "rr_amr_tidal": ([P, P, I32, P, P, P], C.c_int),
+            "rr_amr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -311,3 +320,46 @@ def rr_batch_autotune(b, reps: int = 3, stream=None) -> float:
     ms = C.c_float(0)
     _check(load().rr_batch_autotune(b, int(reps), C.byref(ms), _stream(stream)), "rr_batch_autotune")
     return float(ms.value)
+
+
+# ---- adaptive meshes -------------------------------------------------------
+
+def rr_amr_create(desc: rr_amr_desc, octs) -> C.c_void_p:
+    """octs[l] (l = 1..lmax): int32 array-like [m_l, 3] of the refined level-(l-1)
+    cells; octs[0] is ignored."""
+    import numpy as np
+    L = int(desc.lmax)
+    keep = []
+    ptrs = (C.c_void_p * (L + 1))()
+    counts = (C.c_int64 * (L + 1))()
+    for lv in range(1, L + 1):
+        a = np.ascontiguousarray(np.asarray(octs[lv], dtype=np.int32).reshape(-1, 3))
+        keep.append(a)
+        ptrs[lv] = a.ctypes.data if a.size else None
+        counts[lv] = a.shape[0]
+    h = C.c_void_p()
+    _check(load().rr_amr_create(C.byref(desc), C.cast(ptrs, C.c_void_p), C.cast(counts, C.c_void_p), C.byref(h)),
+           "rr_amr_create")
+    return h
+
+
+def rr_amr_destroy(mesh) -> None:
+    _check(load().rr_amr_destroy(mesh), "rr_amr_destroy")
+
+
+def rr_amr_sizes(mesh):
+    """(cells, leaves, vertices)"""
+    a, b, c = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    _check(load().rr_amr_sizes(mesh, C.byref(a), C.byref(b), C.byref(c)), "rr_amr_sizes")
+    return int(a.value), int(b.value), int(c.value)
+
+
+def rr_amr_tidal(mesh, phi, where: int, leaf_rec, cell_tidal=None, stream=None) -> None:
+    _check(load().rr_amr_tidal(mesh, _ptr(phi), int(where), _ptr(leaf_rec), _ptr(cell_tidal), _stream(stream)),
+           "rr_amr_tidal")
+
+
+def rr_amr_trace_step(ctx, mesh, leaf_rec, chi_a: float, chi_b: float, scale: float = 1.0, a_step: float = 1.0,
+                      stream=None) -> None:
+    _check(load().rr_amr_trace_step(ctx, mesh, _ptr(leaf_rec), float(chi_a), float(chi_b), float(scale),
+                                    float(a_step), _stream(stream)), "rr_amr_trace_step")

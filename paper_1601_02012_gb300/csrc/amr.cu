@@ -1,0 +1,607 @@
+// Adaptive meshes: the mesh plan (built once per mesh on the host, then kept
+// on the device) and the per-step kernels that turn the potential into
+// per-leaf records (Secs. 2.7, 3.3).
+//
+// Per step (rr_amr_tidal):
+//  1. amr_tidal_kernel, one launch per level, coarse to fine: d_a d_b Phi at
+//     every cell by the central differences of Eq. (tidalexample) when the 18
+//     same-level stencil neighbours exist, else the coarser level's values
+//     interpolated trilinearly to the cell centre (the option Sec. 3.3
+//     adopts; hence the level order); delta from tr(H) at a = 1.
+//  2. amr_vertex_kernel: the value at every distinct lattice vertex the leaf
+//     corners need, as the plan's weighted sum of up to 8 leaves (Sec. 2.7:
+//     the mean of 8 same-level leaves, or Eqs. (alphac3d), (alphaf3d)).
+//  3. amr_leafrec_kernel: per leaf corner the mean of its 1, 2 or 4 plan
+//     vertices (2 or 4: a corner in the middle of a coarse edge or face),
+//     8 corners x 8 floats = 256 bytes per leaf, read by the AMR trace kernel
+//     as one contiguous block.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "rr_internal.h"
+
+using namespace rr;
+
+namespace {
+
+// Host view of the mesh for the plan construction.
+struct AmrHost {
+    int n = 0, lmax = 0;
+    double box = 0, omega_m = 0;
+    std::vector<std::vector<int32_t>> octs;   // per level l >= 1: parent coords at level l-1
+    std::vector<int64_t> base;                // first cell number of each level (lmax + 2 entries)
+    std::vector<int32_t> refined;             // cell -> oct index at the next level, or -1
+    std::vector<int64_t> leaf_cell;           // leaf id -> cell number
+    int64_t ncells = 0;
+
+    int64_t side(int l) const { return (int64_t)n << l; }
+    static int64_t wrap(int64_t i, int64_t m)
+    {
+        const int64_t r = i % m;
+        return r < 0 ? r + m : r;
+    }
+    // cell number of (l, i, j, k) (periodic) or -1 if that cell does not exist
+    int64_t cell_at(int l, int64_t i, int64_t j, int64_t k) const
+    {
+        const int64_t m = side(l);
+        i = wrap(i, m); j = wrap(j, m); k = wrap(k, m);
+        int64_t c = ((i >> l) * n + (j >> l)) * n + (k >> l);
+        for (int lv = 1; lv <= l; ++lv) {
+            const int32_t o = refined[(size_t)c];
+            if (o < 0) return -1;
+            const int sh = l - lv;
+            c = base[(size_t)lv] + 8 * (int64_t)o + ((i >> sh) & 1) + 2 * ((j >> sh) & 1) + 4 * ((k >> sh) & 1);
+        }
+        return c;
+    }
+    // level and integer coordinates of cell number c
+    void coords(int64_t c, int& l, int64_t x[3]) const
+    {
+        l = 0;
+        while (l < lmax && c >= base[(size_t)l + 1]) ++l;
+        if (l == 0) {
+            x[0] = c / ((int64_t)n * n); x[1] = (c / n) % n; x[2] = c % n;
+            return;
+        }
+        const int64_t r = c - base[(size_t)l], o = r / 8, ch = r % 8;
+        const int32_t* p = &octs[(size_t)l][(size_t)(3 * o)];
+        x[0] = 2 * (int64_t)p[0] + (ch & 1);
+        x[1] = 2 * (int64_t)p[1] + ((ch >> 1) & 1);
+        x[2] = 2 * (int64_t)p[2] + ((ch >> 2) & 1);
+    }
+    // leaf containing the finest-lattice point V + s/2 (s in {-1, +1}^3): its
+    // cell number, level in lvl
+    int64_t leaf_near(const int64_t V[3], const int s[3], int& lvl) const
+    {
+        int64_t q[3];
+        const int64_t M = side(lmax);
+        for (int a = 0; a < 3; ++a) q[a] = wrap(s[a] > 0 ? V[a] : V[a] - 1, M);   // finest cell
+        int64_t c = ((q[0] >> lmax) * n + (q[1] >> lmax)) * n + (q[2] >> lmax);
+        int l = 0;
+        while (l < lmax) {
+            const int32_t o = refined[(size_t)c];
+            if (o < 0) break;
+            ++l;
+            const int sh = lmax - l;
+            c = base[(size_t)l] + 8 * (int64_t)o + ((q[0] >> sh) & 1) + 2 * ((q[1] >> sh) & 1) + 4 * ((q[2] >> sh) & 1);
+        }
+        lvl = l;
+        return c;
+    }
+};
+
+}  // namespace
+
+struct rr_amr {
+    AmrHost h;
+    int64_t nleaves = 0, nverts = 0;
+    int32_t* d_link = nullptr;      // per cell: leaf id, or -(first child) - 1
+    int32_t* d_stencil = nullptr;   // per cell: 18 neighbour cells (FD) or 8 coarser cells (interpolation)
+    int8_t* d_mode = nullptr;       // per cell: 0 FD, 1 interpolation
+    float* d_frac = nullptr;        // per cell: interpolation fractions (x, y, z)
+    int32_t* d_vcell = nullptr;     // per vertex: 8 leaf cells
+    float* d_vw = nullptr;          // per vertex: 8 weights
+    int32_t* d_corner = nullptr;    // per leaf corner: 4 vertex ids (-1: unused)
+    int32_t* d_leaf_cell = nullptr; // per leaf: cell number
+    float* d_H = nullptr;           // per cell: 8 floats (scratch)
+    float* d_V = nullptr;           // per vertex: 8 floats (scratch)
+};
+
+namespace {
+
+constexpr int NTA = 256;
+
+struct TidalAmrArgs {
+    const float* phi;
+    const int32_t* stencil;
+    const int8_t* mode;
+    const float* frac;
+    float* H;
+    int32_t first, count;
+    float ih2, iq, dinv;
+};
+
+__global__ void __launch_bounds__(NTA) amr_tidal_kernel(const TidalAmrArgs a)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.count) return;
+    const int c = a.first + t;
+    const int32_t* s = a.stencil + 18 * (int64_t)c;
+    float h[6];
+    if (a.mode[c] == 0) {
+        float v[18];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) v[k] = __ldg(a.phi + s[k]);
+        const float p0 = __ldg(a.phi + c);
+        // differences of neighbouring values first: exact when they are within
+        // a factor 2 of each other, so a smooth potential on a fine level keeps
+        // its FP32 precision in the second differences
+        h[0] = ((v[0] - p0) + (v[1] - p0)) * a.ih2;
+        h[1] = ((v[2] - p0) + (v[3] - p0)) * a.ih2;
+        h[2] = ((v[4] - p0) + (v[5] - p0)) * a.ih2;
+        h[3] = ((v[6] - v[8]) + (v[7] - v[9])) * a.iq;
+        h[4] = ((v[10] - v[12]) + (v[11] - v[13])) * a.iq;
+        h[5] = ((v[14] - v[16]) + (v[15] - v[17])) * a.iq;
+    } else {
+        // the coarser level was written by an earlier launch: plain loads
+        const float fx = a.frac[3 * (int64_t)c], fy = a.frac[3 * (int64_t)c + 1], fz = a.frac[3 * (int64_t)c + 2];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) h[q] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float w = ((k & 1) ? fx : 1.f - fx) * ((k & 2) ? fy : 1.f - fy) * ((k & 4) ? fz : 1.f - fz);
+            const float4 lo = reinterpret_cast<const float4*>(a.H)[2 * (int64_t)s[k]];
+            const float4 hi = reinterpret_cast<const float4*>(a.H)[2 * (int64_t)s[k] + 1];
+            h[0] = fmaf(w, lo.x, h[0]); h[1] = fmaf(w, lo.y, h[1]);
+            h[2] = fmaf(w, lo.z, h[2]); h[3] = fmaf(w, lo.w, h[3]);
+            h[4] = fmaf(w, hi.x, h[4]); h[5] = fmaf(w, hi.y, h[5]);
+        }
+    }
+    float4* out = reinterpret_cast<float4*>(a.H) + 2 * (int64_t)c;
+    out[0] = make_float4(h[0], h[1], h[2], h[3]);
+    out[1] = make_float4(h[4], h[5], (h[0] + h[1] + h[2]) * a.dinv, 0.f);
+}
+
+__global__ void __launch_bounds__(NTA) amr_vertex_kernel(const int32_t* __restrict__ vcell,
+                                                         const float* __restrict__ vw, const float* __restrict__ H,
+                                                         float* __restrict__ V, int32_t nverts)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nverts) return;
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int32_t c = __ldg(vcell + 8 * (int64_t)v + k);
+        const float w = __ldg(vw + 8 * (int64_t)v + k);
+        const float4 lo = __ldg(reinterpret_cast<const float4*>(H) + 2 * (int64_t)c);
+        const float4 hi = __ldg(reinterpret_cast<const float4*>(H) + 2 * (int64_t)c + 1);
+        acc[0] = fmaf(w, lo.x, acc[0]); acc[1] = fmaf(w, lo.y, acc[1]);
+        acc[2] = fmaf(w, lo.z, acc[2]); acc[3] = fmaf(w, lo.w, acc[3]);
+        acc[4] = fmaf(w, hi.x, acc[4]); acc[5] = fmaf(w, hi.y, acc[5]);
+        acc[6] = fmaf(w, hi.z, acc[6]);
+    }
+    float4* out = reinterpret_cast<float4*>(V) + 2 * (int64_t)v;
+    out[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    out[1] = make_float4(acc[4], acc[5], acc[6], 0.f);
+}
+
+// One thread per leaf corner: the mean of the corner's 1, 2 or 4 vertices.
+__global__ void __launch_bounds__(NTA) amr_leafrec_kernel(const int32_t* __restrict__ corner,
+                                                          const float* __restrict__ V, float* __restrict__ rec,
+                                                          int64_t ncorners)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncorners) return;
+    const int4 r = __ldg(reinterpret_cast<const int4*>(corner) + t);
+    const int ids[4] = {r.x, r.y, r.z, r.w};
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (ids[k] < 0) continue;
+        const float4 x = __ldg(reinterpret_cast<const float4*>(V) + 2 * (int64_t)ids[k]);
+        const float4 y = __ldg(reinterpret_cast<const float4*>(V) + 2 * (int64_t)ids[k] + 1);
+        a.x += x.x; a.y += x.y; a.z += x.z; a.w += x.w;
+        b.x += y.x; b.y += y.y; b.z += y.z;
+        ++cnt;
+    }
+    const float inv = cnt == 4 ? 0.25f : (cnt == 2 ? 0.5f : 1.f);
+    float4* out = reinterpret_cast<float4*>(rec) + 2 * t;
+    out[0] = make_float4(a.x * inv, a.y * inv, a.z * inv, a.w * inv);
+    out[1] = make_float4(b.x * inv, b.y * inv, b.z * inv, 0.f);
+}
+
+// One thread per leaf: its own cell record (centres, for NGP).
+__global__ void __launch_bounds__(NTA) amr_leafcentre_kernel(const int32_t* __restrict__ leaf_cell,
+                                                             const float* __restrict__ H, float* __restrict__ rec,
+                                                             int64_t nleaves)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nleaves) return;
+    const int64_t c = __ldg(leaf_cell + t);
+    float4* out = reinterpret_cast<float4*>(rec) + 2 * t;
+    out[0] = __ldg(reinterpret_cast<const float4*>(H) + 2 * c);
+    out[1] = __ldg(reinterpret_cast<const float4*>(H) + 2 * c + 1);
+}
+
+// ------------------------------------------------------------ host plan
+
+// The value at lattice vertex V (finest units) as 8 (leaf cell, weight) terms
+// when V is a corner of every leaf around it (returns 0); 1 when V lies in the
+// middle of a coarse edge or face (odd[] then marks the axes along which it is
+// off the coarse lattice, lc is the coarse level); -1 if the leaves around V
+// differ by more than one level.
+int vertex_terms(const AmrHost& h, const int64_t V[3], int32_t cells[8], float w[8], int odd[3], int& lc)
+{
+    int lv[8];
+    int64_t cc[8];
+    int lmin = 99, lmx = -1;
+    for (int o = 0; o < 8; ++o) {
+        const int s[3] = {(o & 1) ? 1 : -1, (o & 2) ? 1 : -1, (o & 4) ? 1 : -1};
+        cc[o] = h.leaf_near(V, s, lv[o]);
+        lmin = std::min(lmin, lv[o]);
+        lmx = std::max(lmx, lv[o]);
+    }
+    lc = lmin;
+    odd[0] = odd[1] = odd[2] = 0;
+    if (lmx == lmin) {
+        for (int o = 0; o < 8; ++o) { cells[o] = (int32_t)cc[o]; w[o] = 0.125f; }
+        return 0;
+    }
+    if (lmx - lmin > 1) return -1;
+    const int64_t cstep = (int64_t)1 << (h.lmax - lmin);
+    int nodd = 0;
+    for (int a = 0; a < 3; ++a) {
+        odd[a] = (AmrHost::wrap(V[a], h.side(h.lmax)) % cstep) != 0;
+        nodd += odd[a];
+    }
+    if (nodd > 0) return 1;
+    // shared by coarse and fine leaves: Eqs. (alphac3d), (alphaf3d), with
+    // N_fv of a fine leaf = its corners that touch a coarser leaf
+    const int64_t fstep = (int64_t)1 << (h.lmax - lmx);
+    int Nc = 0, nfv[8];
+    double sum_fv = 0.0;
+    for (int o = 0; o < 8; ++o) {
+        nfv[o] = 0;
+        if (lv[o] == lmin) { ++Nc; continue; }
+        int l;
+        int64_t x[3];
+        h.coords(cc[o], l, x);
+        for (int t = 0; t < 8; ++t) {
+            const int64_t W[3] = {(x[0] + (t & 1)) * fstep, (x[1] + ((t >> 1) & 1)) * fstep,
+                                  (x[2] + ((t >> 2) & 1)) * fstep};
+            bool coarser = false;
+            for (int q = 0; q < 8 && !coarser; ++q) {
+                const int s[3] = {(q & 1) ? 1 : -1, (q & 2) ? 1 : -1, (q & 4) ? 1 : -1};
+                int lq;
+                h.leaf_near(W, s, lq);
+                coarser = lq < lmx;
+            }
+            nfv[o] += coarser;
+        }
+        sum_fv += nfv[o];
+    }
+    const double ac = 1.0 / ((double)Nc + sum_fv / 8.0);
+    for (int o = 0; o < 8; ++o) {
+        cells[o] = (int32_t)cc[o];
+        w[o] = (float)(lv[o] == lmin ? ac : ac * nfv[o] / 8.0);
+    }
+    return 0;
+}
+
+struct Plan {
+    std::vector<int32_t> link, stencil, vcell, corner, leaf_cell;
+    std::vector<int8_t> mode;
+    std::vector<float> frac, vw;
+};
+
+rr_status build_plan(AmrHost& h, Plan& P, int64_t& nleaves, int64_t& nverts)
+{
+    const int L = h.lmax;
+    h.base.assign((size_t)L + 2, 0);
+    h.base[1] = (int64_t)h.n * h.n * h.n;
+    for (int l = 1; l <= L; ++l)
+        h.base[(size_t)l + 1] = h.base[(size_t)l] + 8 * (int64_t)(h.octs[(size_t)l].size() / 3);
+    h.ncells = h.base[(size_t)L + 1];
+    if (h.ncells > (int64_t)2147483647 - 8) return RR_ERR_ARG;   // cell numbers are int32 on the device
+    h.refined.assign((size_t)h.ncells, -1);
+    for (int l = 1; l <= L; ++l) {
+        const std::vector<int32_t>& o = h.octs[(size_t)l];
+        const int64_t m = (int64_t)o.size() / 3, side = h.side(l - 1);
+        for (int64_t q = 0; q < m; ++q) {
+            for (int a = 0; a < 3; ++a)
+                if (o[3 * q + a] < 0 || o[3 * q + a] >= side) return RR_ERR_ARG;
+            const int64_t c = h.cell_at(l - 1, o[3 * q], o[3 * q + 1], o[3 * q + 2]);
+            if (c < 0 || h.refined[(size_t)c] >= 0) return RR_ERR_ARG;   // missing parent, or listed twice
+            h.refined[(size_t)c] = (int32_t)q;
+        }
+    }
+    // links and leaves
+    P.link.assign((size_t)h.ncells, 0);
+    h.leaf_cell.clear();
+    for (int64_t c = 0; c < h.ncells; ++c) {
+        const int32_t o = h.refined[(size_t)c];
+        if (o >= 0) {
+            int l;
+            int64_t x[3];
+            h.coords(c, l, x);
+            P.link[(size_t)c] = -(int32_t)(h.base[(size_t)l + 1] + 8 * (int64_t)o) - 1;
+        } else {
+            P.link[(size_t)c] = (int32_t)h.leaf_cell.size();
+            h.leaf_cell.push_back(c);
+        }
+    }
+    nleaves = (int64_t)h.leaf_cell.size();
+    P.leaf_cell.assign(h.leaf_cell.begin(), h.leaf_cell.end());
+
+    // per cell: 18 same-level stencil neighbours, or 8 coarser cells to interpolate from
+    static const int offs[18][3] = {{-1, 0, 0}, {1, 0, 0},   {0, -1, 0}, {0, 1, 0},  {0, 0, -1}, {0, 0, 1},
+                                    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1},
+                                    {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    P.stencil.assign((size_t)h.ncells * 18, 0);
+    P.mode.assign((size_t)h.ncells, 0);
+    P.frac.assign((size_t)h.ncells * 3, 0.f);
+    for (int64_t c = 0; c < h.ncells; ++c) {
+        int l;
+        int64_t x[3];
+        h.coords(c, l, x);
+        bool ok = true;
+        int32_t nb[18];
+        for (int t = 0; t < 18 && ok; ++t) {
+            const int64_t q = h.cell_at(l, x[0] + offs[t][0], x[1] + offs[t][1], x[2] + offs[t][2]);
+            ok = q >= 0;
+            nb[t] = (int32_t)q;
+        }
+        if (ok) {
+            memcpy(&P.stencil[(size_t)c * 18], nb, sizeof(nb));
+            continue;
+        }
+        if (l == 0) return RR_ERR_ARG;
+        // fine centre in coarse-centre units: x / 2 - 1/4
+        P.mode[(size_t)c] = 1;
+        int64_t c0[3];
+        for (int a = 0; a < 3; ++a) {
+            if (x[a] % 2 == 0) { c0[a] = x[a] / 2 - 1; P.frac[(size_t)c * 3 + a] = 0.75f; }
+            else { c0[a] = (x[a] - 1) / 2; P.frac[(size_t)c * 3 + a] = 0.25f; }
+        }
+        for (int t = 0; t < 8; ++t) {
+            const int64_t q = h.cell_at(l - 1, c0[0] + (t & 1), c0[1] + ((t >> 1) & 1), c0[2] + ((t >> 2) & 1));
+            if (q < 0) return RR_ERR_ARG;   // not 2:1 balanced
+            P.stencil[(size_t)c * 18 + t] = (int32_t)q;
+        }
+    }
+
+    // distinct lattice vertices the leaf corners need
+    const int64_t M = h.side(L);
+    std::unordered_map<uint64_t, int32_t> vid;
+    vid.reserve((size_t)nleaves * 2 + 16);
+    P.vcell.clear();
+    P.vw.clear();
+    P.corner.assign((size_t)nleaves * 8 * 4, -1);
+    bool bad = false;
+    // id of the plan vertex at V; -2 if V is in the middle of a coarse edge or face
+    auto get_vertex = [&](const int64_t V[3]) -> int32_t {
+        const uint64_t key = ((uint64_t)AmrHost::wrap(V[0], M) * (uint64_t)M + (uint64_t)AmrHost::wrap(V[1], M)) *
+                                 (uint64_t)M + (uint64_t)AmrHost::wrap(V[2], M);
+        auto it = vid.find(key);
+        if (it != vid.end()) return it->second;
+        int32_t cells[8];
+        float w[8];
+        int odd[3], lc;
+        const int rc = vertex_terms(h, V, cells, w, odd, lc);
+        if (rc < 0) { bad = true; return -1; }
+        if (rc == 1) return -2;
+        const int32_t id = (int32_t)(P.vcell.size() / 8);
+        P.vcell.insert(P.vcell.end(), cells, cells + 8);
+        P.vw.insert(P.vw.end(), w, w + 8);
+        vid.emplace(key, id);
+        return id;
+    };
+    for (int64_t lf = 0; lf < nleaves && !bad; ++lf) {
+        int l;
+        int64_t x[3];
+        h.coords(h.leaf_cell[(size_t)lf], l, x);
+        const int64_t step = (int64_t)1 << (L - l);
+        for (int t = 0; t < 8 && !bad; ++t) {
+            const int64_t V[3] = {(x[0] + (t & 1)) * step, (x[1] + ((t >> 1) & 1)) * step,
+                                  (x[2] + ((t >> 2) & 1)) * step};
+            int32_t* slot = &P.corner[((size_t)lf * 8 + t) * 4];
+            const int32_t id = get_vertex(V);
+            if (id >= 0) {
+                slot[0] = id;
+                continue;
+            }
+            if (bad) break;
+            // middle of a coarse edge or face: the mean of its 2 or 4 coarse vertices
+            int32_t cells[8];
+            float w[8];
+            int odd[3], lc;
+            vertex_terms(h, V, cells, w, odd, lc);
+            const int nodd = odd[0] + odd[1] + odd[2];
+            if (nodd == 3) return RR_ERR_ARG;
+            const int64_t half = ((int64_t)1 << (L - lc)) / 2;
+            for (int p = 0; p < (1 << nodd); ++p) {
+                int64_t W[3] = {V[0], V[1], V[2]};
+                int bit = 0;
+                for (int a = 0; a < 3; ++a)
+                    if (odd[a]) {
+                        W[a] += ((p >> bit) & 1) ? half : -half;
+                        ++bit;
+                    }
+                const int32_t wid = get_vertex(W);
+                if (wid < 0) return RR_ERR_ARG;   // a coarse vertex in the middle of a coarser edge: not balanced
+                slot[p] = wid;
+            }
+        }
+    }
+    if (bad) return RR_ERR_ARG;
+    nverts = (int64_t)(P.vcell.size() / 8);
+    return RR_OK;
+}
+
+void free_amr(rr_amr* A)
+{
+    if (!A) return;
+    cudaFree(A->d_link);
+    cudaFree(A->d_stencil);
+    cudaFree(A->d_mode);
+    cudaFree(A->d_frac);
+    cudaFree(A->d_vcell);
+    cudaFree(A->d_vw);
+    cudaFree(A->d_corner);
+    cudaFree(A->d_leaf_cell);
+    cudaFree(A->d_H);
+    cudaFree(A->d_V);
+    delete A;
+}
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src)
+{
+    const size_t bytes = src.size() * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src.data(), bytes, cudaMemcpyHostToDevice);
+    return e;
+}
+
+unsigned blocks_for(int64_t n) { return (unsigned)((n + NTA - 1) / NTA); }
+
+}  // namespace
+
+extern "C" {
+
+rr_status rr_amr_create(const rr_amr_desc* desc, const int32_t* const* octs, const int64_t* noct, rr_amr** out)
+{
+    if (!desc || !out) return RR_ERR_ARG;
+    *out = nullptr;
+    if (desc->n < 2 || desc->n > 4096 || desc->lmax < 0 || desc->lmax > kAmrMaxLevel) return RR_ERR_ARG;
+    if (!std::isfinite(desc->box) || !(desc->box > 0) || !std::isfinite(desc->omega_m) || !(desc->omega_m > 0))
+        return RR_ERR_ARG;
+    if (((int64_t)desc->n << desc->lmax) > ((int64_t)1 << 24)) return RR_ERR_ARG;
+    if (desc->lmax > 0 && (!octs || !noct)) return RR_ERR_ARG;
+    for (int l = 1; l <= desc->lmax; ++l)
+        if (noct[l] < 0 || (noct[l] > 0 && !octs[l]) || noct[l] > ((int64_t)1 << 28)) return RR_ERR_ARG;
+    rr_amr* A = new (std::nothrow) rr_amr();
+    if (!A) return RR_ERR_OOM;
+    A->h.n = desc->n;
+    A->h.lmax = desc->lmax;
+    A->h.box = desc->box;
+    A->h.omega_m = desc->omega_m;
+    A->h.octs.assign((size_t)desc->lmax + 1, std::vector<int32_t>());
+    for (int l = 1; l <= desc->lmax; ++l) A->h.octs[(size_t)l].assign(octs[l], octs[l] + 3 * noct[l]);
+    Plan P;
+    rr_status st = build_plan(A->h, P, A->nleaves, A->nverts);
+    if (st == RR_OK) {
+        cudaError_t e = upload(&A->d_link, P.link);
+        if (e == cudaSuccess) e = upload(&A->d_stencil, P.stencil);
+        if (e == cudaSuccess) e = upload(&A->d_mode, P.mode);
+        if (e == cudaSuccess) e = upload(&A->d_frac, P.frac);
+        if (e == cudaSuccess) e = upload(&A->d_vcell, P.vcell);
+        if (e == cudaSuccess) e = upload(&A->d_vw, P.vw);
+        if (e == cudaSuccess) e = upload(&A->d_corner, P.corner);
+        if (e == cudaSuccess) e = upload(&A->d_leaf_cell, P.leaf_cell);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&A->d_H, (size_t)A->h.ncells * 8 * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc((void**)&A->d_V, (size_t)std::max<int64_t>(A->nverts, 1) * 8 * sizeof(float));
+        st = status_of_cuda(e);
+    }
+    if (st != RR_OK) {
+        free_amr(A);
+        return st;
+    }
+    std::vector<int32_t>().swap(A->h.refined);   // the tables live on the device from here on
+    *out = A;
+    return RR_OK;
+}
+
+rr_status rr_amr_destroy(rr_amr* A)
+{
+    if (!A) return RR_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_amr(A);
+    return RR_OK;
+}
+
+rr_status rr_amr_sizes(rr_amr* A, int64_t* ncells, int64_t* nleaves, int64_t* nverts)
+{
+    if (!A) return RR_ERR_ARG;
+    if (ncells) *ncells = A->h.ncells;
+    if (nleaves) *nleaves = A->nleaves;
+    if (nverts) *nverts = A->nverts;
+    return RR_OK;
+}
+
+rr_status rr_amr_tidal(rr_amr* A, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
+                       void* stream)
+{
+    if (!A || !phi || !leaf_rec || ((uintptr_t)leaf_rec & 15u)) return RR_ERR_ARG;
+    if (cell_tidal && ((uintptr_t)cell_tidal & 15u)) return RR_ERR_ARG;
+    if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const AmrHost& h = A->h;
+    float* H = cell_tidal ? cell_tidal : A->d_H;
+    const double h0 = h.box / h.n;
+    for (int l = 0; l <= h.lmax; ++l) {
+        const double hl = h0 / (double)((int64_t)1 << l);
+        TidalAmrArgs a;
+        a.phi = phi;
+        a.stencil = A->d_stencil;
+        a.mode = A->d_mode;
+        a.frac = A->d_frac;
+        a.H = H;
+        a.first = (int32_t)h.base[(size_t)l];
+        a.count = (int32_t)(h.base[(size_t)l + 1] - h.base[(size_t)l]);
+        a.ih2 = (float)(1.0 / (hl * hl));
+        a.iq = (float)(0.25 / (hl * hl));
+        a.dinv = (float)(1.0 / (1.5 * h.omega_m * kH0OverC * kH0OverC));
+        if (a.count == 0) continue;
+        amr_tidal_kernel<<<blocks_for(a.count), NTA, 0, s>>>(a);
+    }
+    if (where == RR_AT_VERTICES) {
+        if (A->nverts > 0)
+            amr_vertex_kernel<<<blocks_for(A->nverts), NTA, 0, s>>>(A->d_vcell, A->d_vw, H, A->d_V,
+                                                                    (int32_t)A->nverts);
+        amr_leafrec_kernel<<<blocks_for(A->nleaves * 8), NTA, 0, s>>>(A->d_corner, A->d_V, leaf_rec,
+                                                                      A->nleaves * 8);
+    } else {
+        amr_leafcentre_kernel<<<blocks_for(A->nleaves), NTA, 0, s>>>(A->d_leaf_cell, H, leaf_rec, A->nleaves);
+    }
+    return status_of_cuda(cudaGetLastError());
+}
+
+rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, double chi_a, double chi_b,
+                            double scale, double a_step, void* stream)
+{
+    if (!ctx || !A) return RR_ERR_ARG;
+    if (ctx->bundle.flags & RR_FP64_DDA) return RR_ERR_ARG;
+    rr_grid_desc g;   // the coarse grid: argument and step-order checks
+    g.n[0] = g.n[1] = g.n[2] = A->h.n;
+    g.box = A->h.box;
+    g.omega_m = A->h.omega_m;
+    rr_status st = validate_step(ctx, &g, leaf_rec, chi_a, chi_b, scale, a_step);
+    if (st != RR_OK) return st;
+    // the walk runs on the finest lattice: n 2^lmax cells of h_0 / 2^lmax
+    rr_grid_desc fine = g;
+    fine.n[0] = fine.n[1] = fine.n[2] = A->h.n << A->h.lmax;
+    TraceArgs a = make_trace_args(ctx, &fine, leaf_rec, chi_a, chi_b, scale, a_step);
+    // FP32 path variable: sub-steps of at most 64 finest cells (and 32 coarse ones)
+    a.sub_len = (float)(std::min(32.0, 64.0 / (double)(1 << A->h.lmax)) * (A->h.box / A->h.n));
+    AmrDevice m;
+    m.link = A->d_link;
+    m.n = A->h.n;
+    m.lmax = A->h.lmax;
+    const cudaError_t e = launch_trace_amr(a, m, ctx->bundle.interp, (cudaStream_t)stream);
+    if (e != cudaSuccess) return status_of_cuda(e);
+    StepRecord r{g, chi_a, chi_b, scale, a_step};
+    r.amr = 1;
+    ctx->log.push_back(r);
+    return RR_OK;
+}
+
+}  // extern "C"

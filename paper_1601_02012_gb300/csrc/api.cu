@@ -326,6 +326,7 @@ rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkap
     if (!dL_dkappa && !dL_dkborn) return RR_ERR_ARG;
     if (step < 0 || step >= (int32_t)ctx->log.size()) return RR_ERR_STATE;
     const StepRecord& r = ctx->log[(size_t)step];
+    if (r.amr) return RR_ERR_STATE;
     // the records pointer is not read by the adjoint (it needs geometry only)
     TraceArgs a = make_trace_args(ctx, &r.grid, grad_rec, r.chi_a, r.chi_b, r.scale, r.a_step);
     AdjArgs g;
@@ -356,7 +357,7 @@ rr_status rr_trace_backward(rr_ctx* ctx, const double* dL_dkappa, const double* 
     if (ctx->log.empty()) return RR_ERR_STATE;
     const rr_grid_desc& g = ctx->log.front().grid;
     for (const StepRecord& r : ctx->log)
-        if (r.grid.n[0] != g.n[0] || r.grid.n[1] != g.n[1] || r.grid.n[2] != g.n[2] || r.grid.box != g.box ||
+        if (r.amr || r.grid.n[0] != g.n[0] || r.grid.n[1] != g.n[1] || r.grid.n[2] != g.n[2] || r.grid.box != g.box ||
             r.grid.omega_m != g.omega_m)
             return RR_ERR_STATE;
     const size_t npts = (size_t)g.n[0] * g.n[1] * g.n[2];

@@ -30,6 +30,18 @@ struct RayState {
 struct StepRecord {
     rr_grid_desc grid;
     double chi_a, chi_b, scale, a_step;
+    int amr = 0;                // traced over an adaptive mesh (no adjoint)
+};
+
+constexpr int kAmrMaxLevel = 8;
+
+// Adaptive mesh as the trace kernel reads it. link[cell] >= 0: the cell is a
+// leaf with that id; link[cell] < 0: refined, its 8 children are the cells
+// -link - 1 + (dx + 2 dy + 4 dz).
+struct AmrDevice {
+    const int32_t* link;
+    int n;                      // coarse cells per side
+    int lmax;
 };
 
 // Geometry of one step, handed to the trace kernels by value. Doubles are
@@ -98,6 +110,7 @@ cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, in
 int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
 dim3 tile_grid(const TileCfg& t, int nx, int ny);
 bool tile_ok(const TileCfg& t);
+cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s);
 cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s);
 cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
                                  cudaStream_t s);

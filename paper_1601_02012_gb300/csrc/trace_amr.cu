@@ -1,0 +1,210 @@
+// Line-of-sight integration over an adaptive mesh (Secs. 2.5.1, 2.7, 3.3).
+//
+// The ray walks the finest lattice (side n 2^lmax) with the parametric
+// crossings of the uniform walk -- the k-th finest-face crossing on axis a at
+// path T0_a + k td_a, one rounding, float-float start point per sub-step --
+// but stops only where it leaves a leaf: a leaf of level l spans 2^(lmax - l)
+// finest cells per axis, so from the current finest cell q its exit on axis a
+// is a known number m_a of crossings ahead, and the nearest of the three exits
+// ends the segment (lowest axis on ties). After the exit the other axes catch
+// up: their crossing counters advance to the first crossing at or after the
+// exit point, which moves q along them. The leaf of q is found by descending
+// the refinement links from the coarse cell (at most lmax dependent loads).
+//
+// Inside a leaf the field is the trilinear interpolation of the leaf's 8
+// corner values (one contiguous 256-byte record) or, for NGP, the leaf's own
+// value; the segment integral is that of the uniform walk with the leaf's own
+// cell size. Consecutive segments in the same leaf (separated only by a
+// rounding sliver at an edge or corner) are one leaf segment, so the segment
+// count is the number of leaf segments.
+#include "walk.cuh"
+
+namespace rr {
+namespace {
+
+// Leaf containing the finest cell q (each in [0, n 2^lmax)): its id, or -1 if
+// the links are inconsistent; its level in lev.
+__device__ __forceinline__ int amr_locate(const AmrDevice& M, const int q[3], int& lev)
+{
+    const int L = M.lmax;
+    int v = __ldg(M.link + ((q[0] >> L) * M.n + (q[1] >> L)) * M.n + (q[2] >> L));
+    int l = 0;
+    while (v < 0 && l < L) {
+        ++l;
+        const int sh = L - l;
+        v = __ldg(M.link + (-v - 1) + ((q[0] >> sh) & 1) + 2 * ((q[1] >> sh) & 1) + 4 * ((q[2] >> sh) & 1));
+    }
+    lev = l;
+    return v < 0 ? -1 : v;
+}
+
+template <int INTERP>
+__device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevice& M, int ix, int iy)
+{
+    const long long rid = (long long)iy * A.nx + ix;
+    const int NF = A.n0;   // finest cells per side
+    RayRange rg;
+    if (!ray_range(A, rid, rg)) return;
+    const float chis = (float)A.chi_s;
+    const float ichis = A.inv_chi_s_f;
+    const int nsub = max(1, (int)ceilf(rg.Lf / A.sub_len));
+    const float dsub = rg.Lf / (float)nsub;
+    const int L = M.lmax;
+    // slivers: as in the uniform walk, 4 ulp of the path
+    const float eps_rel = 4.76837158203125e-07f;
+
+    Acc<float> sk, sb;
+    uint32_t cnt = 0;
+    bool overflow = false;
+    int prev_leaf = -1;   // leaf of the last integrated segment
+    for (int j = 0; j < nsub && !overflow; ++j) {
+        float bh, bl, Lj, D0j;
+        sub_step(rg, j, nsub, dsub, bh, bl, Lj, D0j);
+        Walk<float> W;
+        walk_setup<float>(A, rid, bh, bl, Lj, D0j, rg.hi, rg.lo, W);
+        const float Ls = W.L, chiA0 = W.chiA0, D0 = W.D0;
+        const float eps_end = Ls * eps_rel;
+        int q[3] = {W.c[0], W.c[1], W.c[2]};   // finest cell of the current point
+        int K[3] = {0, 0, 0};                   // finest-face crossings so far, per axis
+        const int flip = (W.sgn[0] < 0 ? 1 : 0) | (W.sgn[1] < 0 ? 2 : 0) | (W.sgn[2] < 0 ? 4 : 0);
+        float sig = 0.f;                        // path from the sub-step start to the segment entry
+        int iter = 0;
+        while (true) {
+            int lev;
+            const int leaf = amr_locate(M, q, lev);
+            if (leaf < 0) {
+                overflow = true;
+                break;
+            }
+            const int sh = L - lev;
+            const int span = 1 << sh;
+            const float inv_span = __int_as_float((127 - sh) << 23);   // 2^-sh
+            // crossings to the leaf's exit face (m), mirrored finest position in the
+            // leaf (jp) and path to the exit (Tx), per axis
+            int m[3], jp[3];
+            float Tx[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int pos = q[a] & (span - 1);
+                m[a] = W.sgn[a] > 0 ? span - pos : pos + 1;
+                jp[a] = W.sgn[a] > 0 ? pos : span - 1 - pos;
+                Tx[a] = W.v[a] > 0.f ? fmaf((float)(K[a] + m[a] - 1), W.td[a], W.T0[a]) : 1e30f;
+            }
+            float tend = Tx[0];
+            int e = 0;
+            if (Tx[1] < tend) { tend = Tx[1]; e = 1; }
+            if (Tx[2] < tend) { tend = Tx[2]; e = 2; }
+            const bool last = !(tend < Ls - eps_end);
+            if (last) tend = Ls;
+            const float t = tend - sig;
+
+            if (t > tend * eps_rel) {
+                float qk[8], qb[8];
+                if (INTERP == RR_TRILINEAR) {
+                    const float4* r = A.rec + 16 * (long long)leaf;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int rc = c ^ flip;
+                        Rec x;
+                        x.a = __ldg(r + 2 * rc);
+                        x.b = __ldg(r + 2 * rc + 1);
+                        qk[c] = project(W.w, x);
+                        qb[c] = x.b.z;
+                    }
+                } else {
+                    const Rec x = load_rec(A.rec, leaf);
+                    qk[0] = project(W.w, x);
+                    qb[0] = x.b.z;
+                }
+                // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
+                const float chiA = chiA0 - sig;
+                const float G0 = (D0 + sig) * chiA * ichis;
+                const float G1 = (2.f * chiA - chis) * ichis;
+                const float G2 = -ichis;
+                if (INTERP == RR_TRILINEAR) {
+                    float u[3], vl[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        vl[a] = W.v[a] * inv_span;
+                        u[a] = W.v[a] > 0.f ? fminf(fmaxf(fmaf(sig - Tx[a], vl[a], 1.f), 0.f), 1.f)
+                                            : ((float)jp[a] + W.cu[a]) * inv_span;
+                    }
+                    const float t2 = t * t;
+                    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
+                    const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
+                    const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
+                    const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
+                    float ek[4], eb[4];
+                    line_cubic(qk, u[0], u[1], u[2], vl[0], vl[1], vl[2], ek);
+                    line_cubic(qb, u[0], u[1], u[2], vl[0], vl[1], vl[2], eb);
+                    sk.add(ek[0] * J1 + ek[1] * J2 + ek[2] * J3 + ek[3] * J4);
+                    sb.add(eb[0] * J1 + eb[1] * J2 + eb[2] * J3 + eb[3] * J4);
+                } else {
+                    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
+                    sk.add(qk[0] * J1);
+                    sb.add(qb[0] * J1);
+                }
+                if (leaf != prev_leaf) ++cnt;
+                prev_leaf = leaf;
+            }
+            sig = tend;
+            if (last) break;
+
+            // leave through axis e; the other axes advance to their first
+            // crossing at or after the exit point (never past their own exit)
+            bool outside = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a == e) {
+                    K[a] += m[a];
+                    const int nq = q[a] + W.sgn[a] * m[a];
+                    outside = nq < 0 || nq >= NF;
+                    q[a] = wrap_once(nq, NF);
+                } else if (W.v[a] > 0.f) {
+                    const int kmax = K[a] + m[a] - 1;
+                    int k = (int)fminf(fmaxf(ceilf((tend - W.T0[a]) * W.v[a]), (float)K[a]), (float)kmax);
+                    while (k > K[a] && fmaf((float)(k - 1), W.td[a], W.T0[a]) >= tend) --k;
+                    while (k < kmax && fmaf((float)k, W.td[a], W.T0[a]) < tend) ++k;
+                    q[a] = wrap_once(q[a] + W.sgn[a] * (k - K[a]), NF);
+                    K[a] = k;
+                }
+            }
+            if (!A.periodic && outside) break;
+            if (++iter > W.max_iter) {
+                overflow = true;
+                break;
+            }
+        }
+    }
+
+    if (overflow) atomicOr(A.err, kErrStepLimit);
+    if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
+    float kh, kl, bh, bl;
+    sk.pair(kh, kl);
+    sb.pair(bh, bl);
+    A.kacc[rid] = ff_mul_add(A.kacc[rid], kh, kl, A.sch, A.scl);
+    A.bacc[rid] = ff_mul_add(A.bacc[rid], bh, bl, A.bsh, A.bsl);
+    A.nseg[rid] += cnt;
+}
+
+template <int INTERP>
+__global__ void __launch_bounds__(NT_MAX, 2) trace_amr_kernel(const TraceArgs A, const AmrDevice M, const TileCfg t)
+{
+    int ix, iy;
+    tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray_amr<INTERP>(A, M, ix, iy);
+}
+
+}  // namespace
+
+cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s)
+{
+    const TileCfg t;
+    const dim3 grid = tile_grid(t, a.nx, a.ny);
+    const dim3 block(32 * t.bwx * t.bwy);
+    if (interp == RR_TRILINEAR) trace_amr_kernel<RR_TRILINEAR><<<grid, block, 0, s>>>(a, m, t);
+    else trace_amr_kernel<RR_NGP><<<grid, block, 0, s>>>(a, m, t);
+    return cudaGetLastError();
+}
+
+}  // namespace rr

@@ -1,0 +1,326 @@
+// Device helpers of the cell walk shared by the uniform-grid and the
+// adaptive-mesh trace kernels: ray tiles, record loads, the projection onto
+// Q_kappa, the trilinear field on a line, float-float arithmetic, compensated
+// sums, and the per-ray, per-step walk setup (see trace.cu for the method).
+#pragma once
+
+#include <math_constants.h>
+
+#include "rr_internal.h"
+
+namespace rr {
+namespace {
+
+constexpr int NT_MAX = 256;       // largest block the tile configurations use
+
+// Ray (ix, iy) handled by this thread in ray tile (tx, ty): a warp covers
+// wx x (32/wx) neighbouring pixels (x fastest), a block bwx x bwy warps.
+__device__ __forceinline__ void tile_ray(const TileCfg& t, int tx, int ty, int& ix, int& iy)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wy = 32 / t.wx;
+    ix = tx * (t.wx * t.bwx) + (warp % t.bwx) * t.wx + (lane % t.wx);
+    iy = ty * (wy * t.bwy) + (warp / t.bwx) * wy + (lane / t.wx);
+}
+
+__device__ __forceinline__ int wrap_once(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+struct Rec {
+    float4 a, b;
+};
+
+__device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, long long idx)
+{
+    Rec r;
+    r.a = __ldg(rec + 2 * idx);
+    r.b = __ldg(rec + 2 * idx + 1);
+    return r;
+}
+
+// Q_kappa = tr(H) - n^T H n = w . (xx, yy, zz, xy, xz, yz)
+__device__ __forceinline__ float project(const float w[6], const Rec& r)
+{
+    float q = w[0] * r.a.x;
+    q = fmaf(w[1], r.a.y, q);
+    q = fmaf(w[2], r.a.z, q);
+    q = fmaf(w[3], r.a.w, q);
+    q = fmaf(w[4], r.b.x, q);
+    q = fmaf(w[5], r.b.y, q);
+    return q;
+}
+
+// Trilinear field on the line u(s) = u0 + v s as the cubic e0 + e1 s + e2 s^2
+// + e3 s^3. q[i + 2j + 4k] is the value at the mirrored corner (i, j, k).
+__device__ __forceinline__ void line_cubic(const float q[8], float u0, float u1, float u2, float v0, float v1,
+                                           float v2, float e[4])
+{
+    float A[4], B[4];
+#pragma unroll
+    for (int jk = 0; jk < 4; ++jk) {
+        const float lo = q[2 * jk], d = q[2 * jk + 1] - lo;
+        A[jk] = fmaf(d, u0, lo);
+        B[jk] = d * v0;
+    }
+    float M0[2], M1[2], M2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float C = A[2 * k + 1] - A[2 * k], D = B[2 * k + 1] - B[2 * k];
+        M0[k] = fmaf(C, u1, A[2 * k]);
+        M1[k] = fmaf(C, v1, fmaf(D, u1, B[2 * k]));
+        M2[k] = D * v1;
+    }
+    const float E0 = M0[1] - M0[0], E1 = M1[1] - M1[0], E2 = M2[1] - M2[0];
+    e[0] = fmaf(E0, u2, M0[0]);
+    e[1] = fmaf(E0, v2, fmaf(E1, u2, M1[0]));
+    e[2] = fmaf(E1, v2, fmaf(E2, u2, M2[0]));
+    e[3] = E2 * v2;
+}
+
+// ---- float-float helpers (error-free transformations) ----------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// acc (hi, lo) + (x_hi + x_lo) * (s_hi + s_lo)
+__device__ __forceinline__ float2 ff_mul_add(float2 acc, float xh, float xl, float sh, float sl)
+{
+    float ph, pe;
+    two_prod(xh, sh, ph, pe);
+    const float pl = pe + fmaf(xh, sl, xl * sh);
+    float s, e;
+    two_sum(acc.x, ph, s, e);
+    const float t = e + (acc.y + pl);
+    const float hi = s + t;
+    return make_float2(hi, t - (hi - s));
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <class R>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) { kahan_add(s, c, x); }
+    __device__ __forceinline__ bool finite() const { return isfinite(s) && isfinite(c); }
+    // the compensated sum s - c as a float-float pair
+    __device__ __forceinline__ void pair(float& hi, float& lo) const { two_sum(s, -c, hi, lo); }
+};
+
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ bool finite() const { return isfinite(s); }
+    __device__ __forceinline__ void pair(float& hi, float& lo) const
+    {
+        hi = (float)s;
+        lo = (float)(s - (double)hi);
+    }
+};
+
+// Per-ray, per-step state of the cell walk (everything the loop needs).
+template <class R>
+struct Walk {
+    int c[3], sgn[3], k[3];      // cell, motion sign per axis (+1: +axis), crossings so far
+    int vlo[3], vhi[3];          // vertex indices of the mirrored faces 0 (entry) and 1 (exit)
+    R T0[3], td[3], v[3], cu[3];
+    R L, chiA0, D0;
+    float w[6];                  // Q_kappa = w . H
+    int max_iter;
+};
+
+// The part [lo, hi] of the step [chi_b, chi_a] that ray `rid` traverses: all
+// of it with periodic wrap; clipped to the box in FP64 otherwise. chi_hi is
+// also given as a float-float pair, with hi - lo and chi_s - hi in FP32.
+struct RayRange {
+    float ch, cl, Lf, D0f;
+    double hi, lo;
+};
+
+__device__ __forceinline__ bool ray_range(const TraceArgs& A, long long rid, RayRange& g)
+{
+    g.ch = A.cah; g.cl = A.cal; g.Lf = A.Lf; g.D0f = A.D0f;
+    g.hi = A.chi_a; g.lo = A.chi_b;
+    if (!A.periodic) {
+        const int nn[3] = {A.n0, A.n1, A.n2};
+        const double nd[3] = {A.dir[3 * rid], A.dir[3 * rid + 1], A.dir[3 * rid + 2]};
+        const double obs[3] = {A.obs0, A.obs1, A.obs2};
+        double hi = g.hi, lo = g.lo;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double ext = nn[a] * A.h;
+            if (nd[a] == 0.0) {
+                if (obs[a] < 0.0 || obs[a] > ext) hi = lo;
+            } else {
+                const double c0 = -obs[a] / nd[a], c1 = (ext - obs[a]) / nd[a];
+                hi = fmin(hi, fmax(c0, c1));
+                lo = fmax(lo, fmin(c0, c1));
+            }
+        }
+        if (!(hi > lo)) return false;
+        g.hi = hi;
+        g.lo = lo;
+        g.ch = (float)hi;
+        g.cl = (float)(hi - (double)g.ch);
+        g.Lf = (float)(hi - lo);
+        g.D0f = (float)(A.chi_s - hi);
+    }
+    return true;
+}
+
+// Sub-step j of nsub equal pieces of the FP32 walk: start (bh + bl) =
+// chi_hi - j dsub as a float-float pair (exact: TwoProd and TwoSum), length,
+// and chi_s - start. Consecutive sub-steps meet at the same point.
+__device__ __forceinline__ void sub_step(const RayRange& g, int j, int nsub, float dsub, float& bh, float& bl,
+                                         float& L, float& D0)
+{
+    if (nsub == 1) {
+        bh = g.ch; bl = g.cl; L = g.Lf; D0 = g.D0f;
+        return;
+    }
+    float p, pe;
+    two_prod((float)j, dsub, p, pe);
+    float s, t;
+    two_sum(g.ch, -p, s, t);
+    const float lo = t + (g.cl - pe);
+    bh = s + lo;
+    bl = lo - (bh - s);
+    L = (j == nsub - 1) ? fmaf(-(float)(nsub - 1), dsub, g.Lf) : dsub;
+    D0 = fmaf((float)j, dsub, g.D0f);
+}
+
+// Start point (bh + bl, or hi in FP64), start cell and crossing distances of
+// ray `rid` for a walk of length Lf (see the file comment).
+template <class R>
+__device__ __forceinline__ void walk_setup(const TraceArgs& A, long long rid, float ch, float cl, float Lf,
+                                           float D0f, double hi, double lo, Walk<R>& W)
+{
+    constexpr bool F64 = sizeof(R) == 8;
+    const int nn[3] = {A.n0, A.n1, A.n2};
+    const float4 nh4 = A.dirh[rid];
+    const float nh[3] = {nh4.x, nh4.y, nh4.z};
+
+    // Start cell; distances (in cells) from the start point to the lower and
+    // upper face on each axis.
+    int* c = W.c; int* sgn = W.sgn; int* k = W.k;
+    R* T0 = W.T0; R* td = W.td; R* v = W.v; R* cu = W.cu;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R flo, fhi;   // distance to the lower / upper face
+        long long cell;
+        if constexpr (F64) {
+            const double na = A.dir[3 * rid + a];
+            const double oa = a == 0 ? A.obs0 : (a == 1 ? A.obs1 : A.obs2);
+            const double ua = fma(hi, na, oa) * A.inv_h;
+            double fl = floor(ua);
+            double f = ua - fl, g = (fl + 1.0) - ua;
+            // exactly on a face while moving toward -a: the cell below
+            if (na > 0.0 && f == 0.0) { fl -= 1.0; f = 1.0; g = 0.0; }
+            cell = (long long)fl;
+            flo = f;
+            fhi = g;
+        } else {
+            const float4 nl4 = A.dirl[rid];
+            const float nl = a == 0 ? nl4.x : (a == 1 ? nl4.y : nl4.z);
+            // x = obs + chi n in float-float
+            float ph, pe;
+            two_prod(ch, nh[a], ph, pe);
+            const float pl = pe + fmaf(ch, nl, cl * nh[a]);
+            float xs, xe;
+            two_sum(A.oh[a], ph, xs, xe);
+            const float xl = xe + (A.ol[a] + pl);
+            // u = x / h
+            float uh, ue;
+            two_prod(xs, A.ihh, uh, ue);
+            float ul = ue + fmaf(xs, A.ihl, xl * A.ihh);
+            const float un = uh + ul;
+            ul = ul - (un - uh);
+            uh = un;
+            float fl = floorf(uh);
+            float f, g;
+            if (uh == fl && ul < 0.f) {
+                fl -= 1.f;
+                f = 1.f + ul;
+                g = -ul;
+            } else {
+                f = (uh - fl) + ul;
+                g = ((fl + 1.f) - uh) - ul;
+            }
+            // exactly on a face while moving toward -a: the cell below
+            if (nh[a] > 0.f && f == 0.f) { fl -= 1.f; f = 1.f; g = 0.f; }
+            cell = (long long)fl;
+            flo = f;
+            fhi = g;
+        }
+        int ci = (int)cell;
+        if (A.periodic) {
+            ci %= nn[a];
+            if (ci < 0) ci += nn[a];
+        } else if (ci < 0) {
+            ci = 0; flo = (R)0; fhi = (R)1;
+        } else if (ci >= nn[a]) {
+            ci = nn[a] - 1; flo = (R)1; fhi = (R)0;
+        }
+        c[a] = ci;
+        sgn[a] = nh[a] > 0.f ? -1 : 1;   // motion along a is -n_a
+        const R u0 = sgn[a] > 0 ? flo : fhi;      // mirrored: grows along the motion
+        const R e0 = sgn[a] > 0 ? fhi : flo;      // distance to the exit face
+        R va;
+        if constexpr (F64) va = (R)(fabs(A.dir[3 * rid + a]) * A.inv_h);
+        else va = fabsf(nh[a]) * A.inv_hf;
+        v[a] = va;
+        k[a] = 0;
+        if (va > (R)0) {
+            // path to the k-th face crossing on this axis: T0 + k td (one rounding)
+            td[a] = (R)1 / va;
+            T0[a] = e0 * td[a];
+            cu[a] = (R)1;
+        } else {
+            T0[a] = (R)1e30;   // never crosses; u stays u0
+            td[a] = (R)0;
+            cu[a] = u0;
+        }
+    }
+    // vertex indices of the mirrored faces 0 (entry side) and 1 (exit side)
+    int* vlo = W.vlo; int* vhi = W.vhi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int up = c[a] + 1 == nn[a] ? 0 : c[a] + 1;
+        vlo[a] = sgn[a] > 0 ? c[a] : up;
+        vhi[a] = sgn[a] > 0 ? up : c[a];
+    }
+    float* w = W.w;
+    w[0] = nh[1] * nh[1] + nh[2] * nh[2];
+    w[1] = nh[0] * nh[0] + nh[2] * nh[2];
+    w[2] = nh[0] * nh[0] + nh[1] * nh[1];
+    w[3] = -2.f * nh[0] * nh[1];
+    w[4] = -2.f * nh[0] * nh[2];
+    w[5] = -2.f * nh[1] * nh[2];
+
+    W.L = F64 ? (R)(hi - lo) : (R)Lf;
+    W.chiA0 = F64 ? (R)hi : (R)ch;
+    W.D0 = F64 ? (R)(A.chi_s - hi) : (R)D0f;
+    W.max_iter =
+        (int)ceilf(Lf * (fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2])) * A.inv_hf * 1.0001f) + 8;
+}
+
+}  // namespace
+}  // namespace rr

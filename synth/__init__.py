@@ -426,14 +426,44 @@ def amr_nested_cubes(n: int, box: float, lmax: int, half_widths) -> AmrMesh:
     return AmrMesh(n, box, lmax, amr_balance(n, lmax, flags))
 
 
-def amr_random(n: int, box: float, lmax: int, seed: int, sigma_ln: float = 1.5, child_sigma: float = 0.5,
-               threshold: float = 8.0) -> AmrMesh:
-    """Refinement driven by a lognormal density: rho = exp(g - sigma^2/2) on
-    the coarse grid (g Gaussian, P_g propto k^-2, rms sigma_ln), passed to the
-    children by a multiplicative cascade (lognormal factors of rms child_sigma
-    normalised to mean 1 over the 8 siblings); a level-l cell is refined when
-    its mass rho (h_l/h_0)^3 exceeds `threshold` times the mean cell mass of
-    level 0; then 2:1 balanced. numpy PCG64(seed) throughout."""
+_KIDS = np.array([(i & 1, (i >> 1) & 1, (i >> 2) & 1) for i in range(8)], np.int64)
+
+
+def _splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) on uint64 arrays."""
+    x = x + np.uint64(0x9E3779B97F4A7C15)
+    x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return x ^ (x >> np.uint64(31))
+
+
+def _hash_normal(level: int, cells: np.ndarray, seed: int) -> np.ndarray:
+    """One standard normal per level-l cell (rows of integer coordinates), a
+    pure function of (seed, level, coordinates): SplitMix64 over the key, two
+    53-bit uniforms, Box-Muller. Independent of the order cells are visited."""
+    with np.errstate(over="ignore"):
+        h = _splitmix64(np.full(len(cells), (np.uint64(seed) << np.uint64(8)) ^ np.uint64(level), np.uint64))
+        for a in range(3):
+            h = _splitmix64(h ^ cells[:, a].astype(np.uint64))
+        h2 = _splitmix64(h ^ np.uint64(0xD1B54A32D192ED03))
+    u1 = ((h >> np.uint64(11)).astype(np.float64) + 0.5) / 9007199254740992.0
+    u2 = (h2 >> np.uint64(11)).astype(np.float64) / 9007199254740992.0
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def _cascade(level: int, parents: np.ndarray, rho_parent: np.ndarray, seed: int, child_sigma: float):
+    """Children (m, 8, 3) of level-(l-1) cells and their densities (m, 8):
+    rho_parent times lognormal factors of rms child_sigma normalised to mean 1
+    over the 8 siblings (mass conserving)."""
+    child = 2 * parents.astype(np.int64)[:, None, :] + _KIDS[None]
+    f = np.exp(child_sigma * _hash_normal(level, child.reshape(-1, 3), seed)).reshape(-1, 8)
+    f /= f.mean(axis=1, keepdims=True)
+    return child, rho_parent[:, None] * f
+
+
+def _lognormal_coarse(n: int, box: float, seed: int, sigma_ln: float) -> np.ndarray:
+    """rho = exp(g - sigma^2/2) on the n^3 grid, g Gaussian with P_g propto
+    k^-2 and rms sigma_ln (numpy PCG64(seed) white noise, FP64 FFTs)."""
     import scipy.fft as sfft
     rng = np.random.Generator(np.random.PCG64(seed))
     wk = sfft.rfftn(rng.standard_normal((n, n, n)), workers=-1)
@@ -442,25 +472,136 @@ def amr_random(n: int, box: float, lmax: int, seed: int, sigma_ln: float = 1.5, 
     shape = np.where(k2 > 0, 1.0 / np.sqrt(np.maximum(k2, 1e-300)), 0.0)
     g = sfft.irfftn(wk * shape, s=(n, n, n), workers=-1)
     g *= sigma_ln / g.std()
-    rho = np.exp(g - 0.5 * sigma_ln ** 2)
-    flags = []
-    cells = np.stack(np.nonzero(rho > threshold), -1).astype(np.int32)
+    return np.exp(g - 0.5 * sigma_ln ** 2)
+
+
+def amr_random(n: int, box: float, lmax: int, seed: int, sigma_ln: float = 1.5, child_sigma: float = 0.5,
+               threshold: float = 8.0) -> AmrMesh:
+    """Refinement driven by a lognormal density: rho = exp(g - sigma^2/2) on
+    the coarse grid (g Gaussian, P_g propto k^-2, rms sigma_ln), passed to the
+    children by a multiplicative cascade (lognormal factors of rms child_sigma,
+    a hash of the seed, level and cell, normalised to mean 1 over the 8
+    siblings); a level-l cell is refined when its mass rho (h_l/h_0)^3 exceeds
+    `threshold` times the mean cell mass of level 0; then 2:1 balanced."""
+    rho = _lognormal_coarse(n, box, seed, sigma_ln)
+    cells = np.stack(np.nonzero(rho > threshold), -1).astype(np.int64)
     rho_cells = rho[tuple(cells.T)]
-    flags.append(cells)
+    flags = [cells.astype(np.int32)]
     for l in range(1, lmax):
         if len(cells) == 0:
             flags.append(np.zeros((0, 3), np.int32))
             continue
-        f = np.exp(child_sigma * rng.standard_normal((len(cells), 8)))
-        f /= f.mean(axis=1, keepdims=True)
-        child = (2 * cells[:, None, :] + np.array([(i & 1, (i >> 1) & 1, (i >> 2) & 1) for i in range(8)])[None])
-        rho_child = (rho_cells[:, None] * f).reshape(-1)
-        child = child.reshape(-1, 3)
-        mass = rho_child / 8.0 ** l
-        sel = mass > threshold
-        cells, rho_cells = child[sel].astype(np.int32), rho_child[sel]
-        flags.append(cells)
+        child, rho_child = _cascade(l, cells, rho_cells, seed, child_sigma)
+        child, rho_child = child.reshape(-1, 3), rho_child.reshape(-1)
+        sel = rho_child / 8.0 ** l > threshold
+        cells, rho_cells = child[sel], rho_child[sel]
+        flags.append(cells.astype(np.int32))
     return AmrMesh(n, box, lmax, amr_balance(n, lmax, flags))
+
+
+def _level_keys(mesh: AmrMesh, l: int):
+    """Integer coordinates (m_l * 8, 3) of every level-l cell in cell order,
+    and their periodic keys."""
+    m = np.int64(mesh.n << l)
+    if l == 0:
+        ii = np.arange(mesh.n, dtype=np.int64)
+        c = np.stack(np.meshgrid(ii, ii, ii, indexing="ij"), -1).reshape(-1, 3)
+    else:
+        c = (2 * mesh.octs[l].astype(np.int64)[:, None, :] + _KIDS[None]).reshape(-1, 3)
+    return c, (c[:, 0] * m + c[:, 1]) * m + c[:, 2]
+
+
+def _lookup(keys_sorted, order, m, c):
+    """Cell-order index of the level cells at coordinates c (periodic), -1 where absent."""
+    c = np.mod(c, m)
+    k = (c[..., 0] * m + c[..., 1]) * m + c[..., 2]
+    pos = np.clip(np.searchsorted(keys_sorted, k), 0, len(keys_sorted) - 1)
+    hit = keys_sorted[pos] == k
+    return np.where(hit, order[pos], -1)
+
+
+def amr_density(mesh: AmrMesh, seed: int, sigma_ln: float = 1.5, child_sigma: float = 0.5) -> list:
+    """The density of amr_random(seed, sigma_ln, child_sigma) at every cell of
+    every level of the mesh: level 0 (n, n, n), level l (m_l, 8)."""
+    rho0 = _lognormal_coarse(mesh.n, mesh.box, seed, sigma_ln)
+    out = [rho0]
+    flat_prev = rho0.reshape(-1)
+    keys_prev = None
+    for l in range(1, mesh.lmax + 1):
+        par = mesh.octs[l].astype(np.int64)
+        if l == 1:
+            rp = rho0[tuple(par.T)]
+        else:
+            ks, order = keys_prev
+            idx = _lookup(ks, order, np.int64(mesh.n << (l - 1)), par)
+            rp = flat_prev[idx]
+        _, rho_l = _cascade(l, par, rp, seed, child_sigma)
+        out.append(rho_l)
+        flat_prev = rho_l.reshape(-1)
+        _, k = _level_keys(mesh, l)
+        order = np.argsort(k, kind="stable")
+        keys_prev = (k[order], order)
+    return out
+
+
+def amr_potential(mesh: AmrMesh, rho: list, omega_m: float = 0.3, sweeps: int = 8) -> list:
+    """Phi/c^2 at every cell of every level from the density (comoving Poisson
+    equation at a = 1, lap Phi = 1.5 Omega_m (H0/c)^2 delta, delta = rho /
+    mean(rho_0) - 1). Level 0: FFT solve with the eigenvalues of the 7-point
+    Laplacian. Level l >= 1: the coarser level's Phi interpolated trilinearly
+    from the 8 nearest coarser centres, then `sweeps` red-black Gauss-Seidel
+    sweeps of the 7-point equation on the cells whose 6 face neighbours exist
+    at that level (the others keep the interpolated value: Dirichlet)."""
+    import scipy.fft as sfft
+    n, box = mesh.n, mesh.box
+    pref = 1.5 * omega_m * H0_OVER_C ** 2
+    mean0 = float(rho[0].mean())
+    d0 = rho[0] / mean0 - 1.0
+    h0 = box / n
+    k1, kz = _kgrid(n, box)
+    lam = ((2.0 - 2.0 * np.cos(k1 * h0))[:, None, None] + (2.0 - 2.0 * np.cos(k1 * h0))[None, :, None]
+           + (2.0 - 2.0 * np.cos(kz * h0))[None, None, :]) / (h0 * h0)
+    dk = sfft.rfftn(d0, workers=-1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        pk = np.where(lam > 0, -pref * dk / lam, 0.0)
+    phi = [sfft.irfftn(pk, s=(n, n, n), workers=-1)]
+    prev_flat = phi[0].reshape(-1)
+    _, k0 = _level_keys(mesh, 0)
+    prev = (k0, np.arange(len(k0)))   # level 0 keys are already sorted
+    faces = np.array([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)], np.int64)
+    for l in range(1, mesh.lmax + 1):
+        c, k = _level_keys(mesh, l)
+        if len(c) == 0:
+            phi.append(np.zeros((0, 8)))
+            continue
+        m_prev = np.int64(n << (l - 1))
+        # trilinear from the coarser level: centre x/2 - 1/4 in coarse-centre units
+        lo = np.where(c % 2 == 0, c // 2 - 1, (c - 1) // 2)
+        fr = np.where(c % 2 == 0, 0.75, 0.25)
+        val = np.zeros(len(c))
+        for t in range(8):
+            d = _KIDS[t]
+            idx = _lookup(prev[0], prev[1], m_prev, lo + d[None])
+            if np.any(idx < 0):
+                raise ValueError("amr_potential: mesh is not 2:1 balanced")
+            w = np.prod(np.where(d[None] == 1, fr, 1.0 - fr), axis=1)
+            val += w * prev_flat[idx]
+        order = np.argsort(k, kind="stable")
+        ks = k[order]
+        m = np.int64(n << l)
+        nb = np.stack([_lookup(ks, order, m, c + f[None]) for f in faces], 1)
+        inner = np.all(nb >= 0, axis=1)
+        hl = box / float(m)
+        src = (hl * hl * pref) * (rho[l].reshape(-1) / mean0 - 1.0)
+        colour = (c.sum(axis=1) % 2)
+        for _ in range(sweeps):
+            for col in (0, 1):
+                sel = np.nonzero(inner & (colour == col))[0]
+                val[sel] = (val[nb[sel]].sum(axis=1) - src[sel]) / 6.0
+        phi.append(val.reshape(-1, 8))
+        prev_flat = val
+        prev = (ks, order)
+    return phi
 
 
 def amr_cell_centres(mesh: AmrMesh, level: int) -> np.ndarray:

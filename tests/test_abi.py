@@ -95,3 +95,37 @@ def test_footprint_bbox_covers_oracle_walk(rr, oracle_lib, fov, obs, chi_a, chi_
             for a in range(3):
                 c = int(r[2 + a])
                 assert inside[a][c % n] and inside[a][(c + 1) % n], (rid, a, c, bbox)
+
+
+def test_amr_plan_validation_is_host_side(rr):
+    """rr_amr_create rejects bad descriptions and meshes that are not 2:1
+    balanced while building its plan on the host, before any device work."""
+    lib = rr.load()
+    h = C.c_void_p()
+
+    def create(n, lmax, octs, box=8.0):
+        d = rr.rr_amr_desc()
+        d.n, d.lmax, d.box, d.omega_m = n, lmax, box, 0.3
+        keep = [np.ascontiguousarray(np.asarray(o, np.int32).reshape(-1, 3)) for o in octs]
+        ptrs = (C.c_void_p * (lmax + 1))()
+        counts = (C.c_int64 * (lmax + 1))()
+        for lv in range(1, lmax + 1):
+            ptrs[lv] = keep[lv].ctypes.data if keep[lv].size else None
+            counts[lv] = keep[lv].shape[0]
+        return lib.rr_amr_create(C.byref(d), C.cast(ptrs, C.c_void_p), C.cast(counts, C.c_void_p), C.byref(h))
+
+    empty = np.zeros((0, 3))
+    assert create(1, 0, [empty]) == rr.RR_ERR_ARG                          # n < 2
+    assert create(4, 9, [empty] * 10) == rr.RR_ERR_ARG                     # lmax > 8
+    assert create(4, 0, [empty], box=0.0) == rr.RR_ERR_ARG                 # box
+    assert create(4, 1, [empty, [[4, 0, 0]]]) == rr.RR_ERR_ARG             # parent outside the grid
+    assert create(4, 1, [empty, [[1, 1, 1], [1, 1, 1]]]) == rr.RR_ERR_ARG  # refined twice
+    # a level-2 oct whose level-1 parent does not exist
+    assert create(4, 2, [empty, [[1, 1, 1]], [[0, 0, 0]]]) == rr.RR_ERR_ARG
+    # a level-2 oct next to unrefined coarse cells: not 2:1 balanced
+    assert create(4, 2, [empty, [[1, 1, 1]], [[2, 2, 2]]]) == rr.RR_ERR_ARG
+    assert lib.rr_amr_create(None, None, None, C.byref(h)) == rr.RR_ERR_ARG
+    assert lib.rr_amr_destroy(None) == rr.RR_ERR_ARG
+    assert lib.rr_amr_sizes(None, None, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_amr_tidal(None, C.c_void_p(16), 0, C.c_void_p(16), None, None) == rr.RR_ERR_ARG
+    assert lib.rr_amr_trace_step(None, None, C.c_void_p(16), 1.0, 0.0, 1.0, 1.0, None) == rr.RR_ERR_ARG
