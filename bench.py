@@ -337,6 +337,163 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def _amr_config(w, mesh, nsteps):
+    return {
+        "workload": w.name, "coarse_grid": w.n, "box_mpc_h": w.box, "levels": w.lmax,
+        "octs_per_level": [len(mesh.octs[l]) for l in range(1, w.lmax + 1)], "leaves": mesh.nleaves(),
+        "rays": [w.bundle.nx, w.bundle.ny], "fov_deg": round(w.bundle.fov_x * 180 / math.pi, 6),
+        "chi_s": w.bundle.chi_s, "nsteps": nsteps, "interp": "trilinear",
+        "field": "lognormal density (sigma_ln 1.5, hashed cascade 0.5), refine where mass > 8x mean, "
+                 "2:1 balanced; Phi: 7-point FFT Poisson on level 0, trilinear prolongation + 8 red-black "
+                 "Gauss-Seidel sweeps per level; FP32; rescaled by D(a)/a per step",
+        "l2": "flushed between timed passes (256 MiB write); leaf records > L2",
+    }
+
+
+def run_amr(args, name):
+    """The adaptive-mesh workload: per step rr_amr_tidal over the whole mesh
+    (per-level stencils, vertex weights, 256-byte leaf records) and
+    rr_amr_trace_step (leaf-by-leaf walk); then rr_finalize."""
+    import torch
+    import paper_1601_02012_gb300 as rrp
+    from paper_1601_02012_gb300 import build as rrbuild
+
+    rrbuild.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = synth.amr_workload(name)
+    steps = synth.step_schedule(w.bundle.chi_s, w.nsteps, rescale=w.rescale)
+    t0 = time.perf_counter()
+    mesh, flat = synth.amr_workload_mesh(w)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gm = rrp.AmrMesh(w.n, w.lmax, w.box, mesh.octs, mesh.omega_m)
+    t_plan = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    phi = torch.from_numpy(flat).to(dev)
+    rec = gm.record_buffer(rrp.RR_AT_VERTICES, device=dev)
+    tr = rrp.Tracer(w.bundle)
+    kappa = torch.empty((w.bundle.ny, w.bundle.nx), dtype=torch.float64, device=dev)
+    kborn = torch.empty_like(kappa)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    nst = len(steps)
+    ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+    ev_td = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+
+    def one_pass(src=None, timed_kernels=False):
+        rrp.rr_reset(tr.ctx, stream)
+        field = phi if src is None else src
+        for i, st in enumerate(steps):
+            if timed_kernels:
+                ev_td[i][0].record(stream)
+            gm.tidal(field, rec, rrp.RR_AT_VERTICES, None, stream)
+            if timed_kernels:
+                ev_td[i][1].record(stream)
+                ev_tr[i][0].record(stream)
+            tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            if timed_kernels:
+                ev_tr[i][1].record(stream)
+        rrp.rr_finalize(tr.ctx, kappa, kborn, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_pass()
+        segs = tr.segments()
+        sampler = ClockSampler(_device_id(torch, dev))
+        torch.cuda.synchronize()
+        sampler.start()
+        times, trace_ms, tidal_ms = [], 0.0, 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_pass(timed_kernels=True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            trace_ms += sum(a.elapsed_time(b) for a, b in ev_tr)
+            tidal_ms += sum(a.elapsed_time(b) for a, b in ev_td)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        phi_pinned = torch.from_numpy(flat).pin_memory()
+        k_host = torch.empty(kappa.shape, dtype=torch.float64).pin_memory()
+        kb_host = torch.empty_like(k_host).pin_memory()
+        phi_dev2 = torch.empty_like(phi)
+        e2e = []
+        for it in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            phi_dev2.copy_(phi_pinned, non_blocking=True)
+            one_pass(src=phi_dev2)
+            k_host.copy_(kappa, non_blocking=True)
+            kb_host.copy_(kborn, non_blocking=True)
+            stream.synchronize()
+            if it >= args.warmup:
+                e2e.append(time.perf_counter() - t0)
+
+    peaks, peak_kind = _peaks()
+    total_ms = sum(times)
+    per_pass_trace_s = trace_ms / args.steps / 1e3
+    achieved = segs * BYTES_PER_SEGMENT / per_pass_trace_s / 1e9
+    per_pass_tidal_s = tidal_ms / args.steps / 1e3
+    line = {
+        "metric": METRIC, "value": segs * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _amr_config(w, mesh, nst) | {"form": "fp32 float-float walk on the finest lattice, Kahan sums"},
+        "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
+        "segments_per_step": segs,
+        "setup_s": {"mesh_and_potential": t_gen, "plan": t_plan},
+        "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps},
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "trace_amr_kernel<trilinear>",
+            "note": f"logical gather bytes: {BYTES_PER_SEGMENT} B per leaf segment (the leaf's 8 corner "
+                    f"records) x leaf segments / trace time; peak of {peak_kind} copy bandwidth"},
+        "tidal_per_pass": {"launches": nst * (w.lmax + 3), "ms": tidal_ms / args.steps,
+                           "leaf_records_gbs": nst * gm.nleaves * 256 / per_pass_tidal_s / 1e9},
+        "e2e": {"value": segs * args.steps / sum(e2e), "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes),
+                "d2h_bytes_per_step": int(k_host.numel() * 8 * 2)},
+        "gpu_launches": args.steps * (nst * (w.lmax + 4) + 1),
+        "clocks": clocks,
+        "trace_src": _src_hash("trace_amr.cu"),
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rng = np.random.default_rng(99)
+        rids = rng.choice(w.bundle.nrays, 24, replace=False)
+        t0 = time.perf_counter()
+        res = oracle.amr_trace(w.bundle, mesh, steps, rids=rids)
+        dt = time.perf_counter() - t0
+        n2 = int(min(w.bundle.nrays, max(24, 24 * 15.0 / max(dt, 1e-3))))
+        rids2 = rng.choice(w.bundle.nrays, n2, replace=False)
+        t0 = time.perf_counter()
+        res2 = oracle.amr_trace(w.bundle, mesh, steps, rids=rids2)
+        dt2 = time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": float(res2.nseg.sum()) / dt2, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n2} random rays of the bundle through all {nst} steps ({dt2:.1f} s); the AMR oracle "
+                      "is single-threaded (its memoised tidal field is shared)"}
+        kg = kappa.cpu().numpy().ravel()
+        kbg = kborn.cpu().numpy().ravel()
+        allr = np.concatenate([rids, rids2])
+        ko = np.concatenate([res.kappa, res2.kappa])
+        kbo = np.concatenate([res.kborn, res2.kborn])
+        rms, rmsb = math.sqrt(float(np.mean(ko ** 2))), math.sqrt(float(np.mean(kbo ** 2)))
+        line["error_vs_oracle"] = {
+            "rays": int(len(allr)),
+            "kappa_max_over_rms": float(np.abs(kg[allr] - ko).max() / rms),
+            "kborn_max_over_rms": float(np.abs(kbg[allr] - kbo).max() / rmsb),
+            "segments_per_ray_gpu": segs / w.bundle.nrays,
+            "segments_per_ray_oracle": float(np.concatenate([res.nseg, res2.nseg]).mean()),
+        }
+    tr.close()
+    gm.close()
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
@@ -358,6 +515,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload.startswith("amr_"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the production "
+                              "uniform workload; the AMR line carries its own oracle sample"}))
+            return
+        if rank == 0:
+            run_amr(args, args.workload)
+        return
     if args.workload == "batch64":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the production "

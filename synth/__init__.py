@@ -660,3 +660,76 @@ def fourier_fn(box: float, nmodes: int, kmax: float, seed: int, spectral_index: 
             out += amps[i] * np.cos(p @ ks[i] + ph[i])
         return out
     return f
+
+
+# ---------------------------------------------------------------------------
+# Adaptive-mesh workloads
+# ---------------------------------------------------------------------------
+
+@dataclass
+class AmrWorkload:
+    name: str
+    n: int
+    box: float
+    lmax: int
+    seed: int
+    sigma_ln: float
+    child_sigma: float
+    threshold: float
+    bundle: Bundle
+    nsteps: int
+    rescale: bool = True
+
+
+def amr_workload(name: str) -> AmrWorkload:
+    """Named adaptive-mesh workloads (lognormal density, sigma_ln = 1.5, cascade
+    child_sigma = 0.5, refinement where the cell mass exceeds 8x the mean,
+    Phi by amr_potential; equal-Delta-a steps with Phi rescaled by D(a)/a).
+
+    amr_256: 256^3 coarse grid, box 512 Mpc/h, up to 4 extra levels (about
+        21.7M leaves), 4096 x 4096 rays over 5 x 5 deg to chi_s = 500, 32 steps.
+    amr_128: 128^3 coarse grid, box 256, up to 4 levels, 1024 x 1024 rays over
+        5 x 5 deg to chi_s = 250, 8 steps (profiling case: leaf records larger
+        than L2, about 1 GB on the device).
+    """
+    if name == "amr_256":
+        b = Bundle(4096, 4096, deg(5.0), deg(5.0), (256.0, 256.0, 0.0), 500.0)
+        return AmrWorkload(name, 256, 512.0, 4, 8, 1.5, 0.5, 8.0, b, 32)
+    if name == "amr_128":
+        b = Bundle(1024, 1024, deg(5.0), deg(5.0), (128.0, 128.0, 0.0), 250.0)
+        return AmrWorkload(name, 128, 256.0, 4, 9, 1.5, 0.5, 8.0, b, 8)
+    raise KeyError(name)
+
+
+def amr_workload_mesh(w: AmrWorkload, omega_m: float = 0.3):
+    """(mesh with FP64 phi per level, flat FP32 phi in cell order) of an
+    adaptive-mesh workload, memoised on disk under $RR_CACHE like
+    grf_phi_cached."""
+    import os
+    import tempfile
+    root = os.environ.get("RR_CACHE", os.path.join(tempfile.gettempdir(), "rr_cache"))
+    os.makedirs(root, exist_ok=True)
+    path = os.path.join(root, f"amr_{w.n}_L{w.box:g}_l{w.lmax}_s{w.seed}_t{w.threshold:g}_v2.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        octs = [np.zeros((0, 3), np.int32)] + [z[f"octs{l}"] for l in range(1, w.lmax + 1)]
+        mesh = AmrMesh(w.n, w.box, w.lmax, octs, omega_m=omega_m)
+        flat = z["phi"]
+    else:
+        mesh = amr_random(w.n, w.box, w.lmax, w.seed, w.sigma_ln, w.child_sigma, w.threshold)
+        mesh.omega_m = omega_m
+        rho = amr_density(mesh, w.seed, w.sigma_ln, w.child_sigma)
+        phi = amr_potential(mesh, rho, omega_m)
+        flat = np.concatenate([np.asarray(p, np.float64).reshape(-1) for p in phi]).astype(np.float32)
+        tmp = path + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, phi=flat, **{f"octs{l}": mesh.octs[l] for l in range(1, w.lmax + 1)})
+        os.replace(tmp, path)
+    # per-level FP64 copies of the FP32 values (what both sides read)
+    parts, off = [], 0
+    sizes = [w.n ** 3] + [8 * len(mesh.octs[l]) for l in range(1, w.lmax + 1)]
+    for l, sz in enumerate(sizes):
+        p = flat[off:off + sz].astype(np.float64)
+        parts.append(p.reshape(w.n, w.n, w.n) if l == 0 else p.reshape(-1, 8))
+        off += sz
+    mesh.phi = parts
+    return mesh, flat
