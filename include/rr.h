@@ -298,10 +298,11 @@ rr_status rr_batch_autotune(rr_batch* b, int32_t reps, float* best_ms, void* str
  * numbered in the order of their cell numbers.
  *
  * rr_amr_create builds the mesh plan on the host and copies it to the current
- * device (synchronous): per cell its refinement link and either its 18
- * same-level stencil neighbours or the 8 coarser cells it interpolates from;
- * per lattice vertex a leaf needs, its value as a weighted sum of up to 8
- * leaves; per leaf corner the 1, 2 or 4 vertices whose mean it is.
+ * device (synchronous; the host part runs on all hardware threads): per cell
+ * its refinement link and either its 18 same-level stencil neighbours or the 8
+ * coarser cells it interpolates from; per lattice vertex a leaf needs, its
+ * value as a weighted sum of up to 8 leaves; per leaf corner the 1, 2 or 4
+ * vertices whose mean it is.
  *   octs[l]  (l = 1..lmax) host int32 [noct[l] x 3]: the level-(l-1) cells
  *            refined into level-l octs, each listed once; octs[0] and
  *            noct[0] are ignored.
@@ -321,7 +322,9 @@ typedef struct {
 rr_status rr_amr_create(const rr_amr_desc* desc, const int32_t* const* octs, const int64_t* noct, rr_amr** out);
 /* Free the plan (synchronises the device first). */
 rr_status rr_amr_destroy(rr_amr* mesh);
-/* Cells of all levels, leaves, and distinct lattice vertices of the plan (any may be NULL). */
+/* Cells of all levels, leaves, and vertex slots of the plan (one per leaf: the
+ * leaf's lower corner, which owns the lattice vertex there unless it is hanging)
+ * (any may be NULL). */
 rr_status rr_amr_sizes(rr_amr* mesh, int64_t* ncells, int64_t* nleaves, int64_t* nverts);
 
 /*
@@ -343,10 +346,15 @@ rr_status rr_amr_sizes(rr_amr* mesh, int64_t* ncells, int64_t* nleaves, int64_t*
  *               rr_tidal_tensor's records); RR_AT_CENTRES 8 floats per leaf.
  *   cell_tidal  device float [ncells x 8] or NULL: also receives step 1's
  *               per-cell records {Hxx, Hyy, Hzz, Hxy}, {Hxz, Hyz, delta, 0}.
+ *   bbox        NULL for the whole mesh, else 6 ints {x0, x1, y0, y1, z0, z1}
+ *               of coarse cells (as rr_footprint_bbox gives them for the
+ *               coarse grid, indices modulo n, x1 - x0 in [1, n]): only the
+ *               records of leaves inside that box are written (and the cell
+ *               and vertex values they need, within lmax + 3 coarse cells).
  * Asynchronous on `stream` (lmax + 3 launches).
  */
 rr_status rr_amr_tidal(rr_amr* mesh, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
-                       void* stream);
+                       const int32_t* bbox, void* stream);
 
 /*
  * rr_trace_step over an adaptive mesh: each ray advances leaf by leaf (the

@@ -146,10 +146,23 @@ class AmrMesh:
         per = 64 if where == RR_AT_VERTICES else 8
         return torch.empty((self.nleaves, per), dtype=torch.float32, device=device)
 
-    def tidal(self, phi, leaf_rec, where=RR_AT_VERTICES, cell_tidal=None, stream=None):
-        """rr_amr_tidal: phi (float32 [ncells], cell order) -> leaf records."""
-        rr_amr_tidal(self.handle, phi, where, leaf_rec, cell_tidal, stream)
+    def tidal(self, phi, leaf_rec, where=RR_AT_VERTICES, cell_tidal=None, bbox=None, stream=None):
+        """rr_amr_tidal: phi (float32 [ncells], cell order) -> leaf records
+        (of the leaves in ``bbox``, a coarse-cell box, or of all)."""
+        rr_amr_tidal(self.handle, phi, where, leaf_rec, cell_tidal, bbox, stream)
         return leaf_rec
+
+    def coarse_grid(self):
+        """rr_grid_desc of the coarse grid (for rr_footprint_bbox)."""
+        d = _rr.rr_grid_desc()
+        for i in range(3):
+            d.n[i] = int(self.desc.n)
+        d.box, d.omega_m = float(self.desc.box), float(self.desc.omega_m)
+        return d
+
+    def footprint(self, tracer, chi_a, chi_b):
+        """Coarse-cell box of the leaves a step of ``tracer``'s bundle can read."""
+        return rr_footprint_bbox(tracer.desc, self.coarse_grid(), chi_a, chi_b)
 
 
 def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=True, stream=None):

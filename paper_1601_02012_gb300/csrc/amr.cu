@@ -19,9 +19,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
-#include <unordered_map>
+#include <thread>
 #include <vector>
 
 #include "rr_internal.h"
@@ -109,29 +110,78 @@ struct rr_amr {
     float* d_vw = nullptr;          // per vertex: 8 weights
     int32_t* d_corner = nullptr;    // per leaf corner: 4 vertex ids (-1: unused)
     int32_t* d_leaf_cell = nullptr; // per leaf: cell number
+    int32_t* d_coarse = nullptr;    // per cell: its level-0 ancestor (cell number)
     float* d_H = nullptr;           // per cell: 8 floats (scratch)
     float* d_V = nullptr;           // per vertex: 8 floats (scratch)
+    // per level, the first cell number / leaf id whose coarse x is >= i (n + 1
+    // entries), when every level's cells are ordered by coarse x (octs listed
+    // in lexicographic order); footprint launches then cover x-slabs only
+    bool x_sorted = false;
+    std::vector<std::vector<int64_t>> cell_x, leaf_x;
 };
 
 namespace {
 
 constexpr int NTA = 256;
 
+// A box of coarse cells {x0, x0 + wx) x ... (periodic), or all of them.
+struct AmrBox {
+    int n, all;
+    int x0, wx, y0, wy, z0, wz;
+};
+
+__device__ __forceinline__ bool in_range(int i, int x0, int w, int m, int n)
+{
+    if (w + 2 * m >= n) return true;
+    int d = (i - x0 + m) % n;
+    if (d < 0) d += n;
+    return d < w + 2 * m;
+}
+
+// Is coarse cell c0 within `margin` coarse cells of the box?
+__device__ __forceinline__ bool in_box(const AmrBox& b, int c0, int margin)
+{
+    if (b.all) return true;
+    const int i = c0 / (b.n * b.n), j = (c0 / b.n) % b.n, k = c0 % b.n;
+    return in_range(i, b.x0, b.wx, margin, b.n) && in_range(j, b.y0, b.wy, margin, b.n) &&
+           in_range(k, b.z0, b.wz, margin, b.n);
+}
+
+// Up to kMaxRanges index ranges [start, start + len) covered by one launch;
+// pre[] holds their prefix sums (thread t serves range r with pre[r] <= t < pre[r + 1]).
+constexpr int kMaxRanges = 2 * (kAmrMaxLevel + 1);
+struct Ranges {
+    int n;
+    int64_t start[kMaxRanges];
+    int64_t pre[kMaxRanges + 1];
+};
+
+__device__ __forceinline__ int64_t range_at(const Ranges& R, int64_t t)
+{
+    int r = 0;
+    while (r + 1 < R.n && t >= R.pre[r + 1]) ++r;
+    return R.start[r] + (t - R.pre[r]);
+}
+
 struct TidalAmrArgs {
     const float* phi;
     const int32_t* stencil;
     const int8_t* mode;
     const float* frac;
+    const int32_t* coarse;
     float* H;
-    int32_t first, count;
+    Ranges cells;
     float ih2, iq, dinv;
+    AmrBox box;
+    int margin;
 };
 
 __global__ void __launch_bounds__(NTA) amr_tidal_kernel(const TidalAmrArgs a)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.count) return;
-    const int c = a.first + t;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.cells.pre[a.cells.n]) return;
+    const int c = (int)range_at(a.cells, t);
+    if (!in_box(a.box, __ldg(a.coarse + c), a.margin)) return;
     const int32_t* s = a.stencil + 18 * (int64_t)c;
     float h[6];
     if (a.mode[c] == 0) {
@@ -168,12 +218,17 @@ __global__ void __launch_bounds__(NTA) amr_tidal_kernel(const TidalAmrArgs a)
     out[1] = make_float4(h[4], h[5], (h[0] + h[1] + h[2]) * a.dinv, 0.f);
 }
 
+// One thread per vertex slot (slot v belongs to leaf v, owner of its lower corner).
 __global__ void __launch_bounds__(NTA) amr_vertex_kernel(const int32_t* __restrict__ vcell,
                                                          const float* __restrict__ vw, const float* __restrict__ H,
-                                                         float* __restrict__ V, int32_t nverts)
+                                                         float* __restrict__ V, const Ranges slots,
+                                                         const int32_t* __restrict__ leaf_cell,
+                                                         const int32_t* __restrict__ coarse, const AmrBox box)
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nverts) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= slots.pre[slots.n]) return;
+    const int v = (int)range_at(slots, t);
+    if (!in_box(box, __ldg(coarse + __ldg(leaf_cell + v)), 2)) return;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -194,10 +249,13 @@ __global__ void __launch_bounds__(NTA) amr_vertex_kernel(const int32_t* __restri
 // One thread per leaf corner: the mean of the corner's 1, 2 or 4 vertices.
 __global__ void __launch_bounds__(NTA) amr_leafrec_kernel(const int32_t* __restrict__ corner,
                                                           const float* __restrict__ V, float* __restrict__ rec,
-                                                          int64_t ncorners)
+                                                          const Ranges corners, const int32_t* __restrict__ leaf_cell,
+                                                          const int32_t* __restrict__ coarse, const AmrBox box)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncorners) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= corners.pre[corners.n]) return;
+    const int64_t t = range_at(corners, i);
+    if (!in_box(box, __ldg(coarse + __ldg(leaf_cell + t / 8)), 0)) return;
     const int4 r = __ldg(reinterpret_cast<const int4*>(corner) + t);
     const int ids[4] = {r.x, r.y, r.z, r.w};
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -220,17 +278,50 @@ __global__ void __launch_bounds__(NTA) amr_leafrec_kernel(const int32_t* __restr
 // One thread per leaf: its own cell record (centres, for NGP).
 __global__ void __launch_bounds__(NTA) amr_leafcentre_kernel(const int32_t* __restrict__ leaf_cell,
                                                              const float* __restrict__ H, float* __restrict__ rec,
-                                                             int64_t nleaves)
+                                                             const Ranges leaves, const int32_t* __restrict__ coarse,
+                                                             const AmrBox box)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nleaves) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= leaves.pre[leaves.n]) return;
+    const int64_t t = range_at(leaves, i);
     const int64_t c = __ldg(leaf_cell + t);
+    if (!in_box(box, __ldg(coarse + c), 0)) return;
     float4* out = reinterpret_cast<float4*>(rec) + 2 * t;
     out[0] = __ldg(reinterpret_cast<const float4*>(H) + 2 * c);
     out[1] = __ldg(reinterpret_cast<const float4*>(H) + 2 * c + 1);
 }
 
 // ------------------------------------------------------------ host plan
+
+// f(begin, end) over [0, n) in chunks on all hardware threads (serial when
+// n is small or no thread can be started).
+template <class F>
+void parallel_for(int64_t n, F&& f)
+{
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 128u));
+    constexpr int64_t kChunk = 4096;
+    if (nt == 1 || n < 4 * kChunk) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    auto work = [&]() {
+        for (;;) {
+            const int64_t b = next.fetch_add(kChunk);
+            if (b >= n) break;
+            f(b, std::min(n, b + kChunk));
+        }
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (unsigned t = 1; t < nt; ++t) pool.emplace_back(work);
+    } catch (...) {
+        // fewer threads: the ones started and this one share the work
+    }
+    work();
+    for (std::thread& t : pool) t.join();
+}
 
 // The value at lattice vertex V (finest units) as 8 (leaf cell, weight) terms
 // when V is a corner of every leaf around it (returns 0); 1 when V lies in the
@@ -296,7 +387,7 @@ int vertex_terms(const AmrHost& h, const int64_t V[3], int32_t cells[8], float w
 }
 
 struct Plan {
-    std::vector<int32_t> link, stencil, vcell, corner, leaf_cell;
+    std::vector<int32_t> link, stencil, vcell, corner, leaf_cell, coarse;
     std::vector<int8_t> mode;
     std::vector<float> frac, vw;
 };
@@ -339,6 +430,15 @@ rr_status build_plan(AmrHost& h, Plan& P, int64_t& nleaves, int64_t& nverts)
     }
     nleaves = (int64_t)h.leaf_cell.size();
     P.leaf_cell.assign(h.leaf_cell.begin(), h.leaf_cell.end());
+    P.coarse.assign((size_t)h.ncells, 0);
+    parallel_for(h.ncells, [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c) {
+            int l;
+            int64_t x[3];
+            h.coords(c, l, x);
+            P.coarse[(size_t)c] = (int32_t)((((x[0] >> l) * h.n) + (x[1] >> l)) * h.n + (x[2] >> l));
+        }
+    });
 
     // per cell: 18 same-level stencil neighbours, or 8 coarser cells to interpolate from
     static const int offs[18][3] = {{-1, 0, 0}, {1, 0, 0},   {0, -1, 0}, {0, 1, 0},  {0, 0, -1}, {0, 0, 1},
@@ -347,101 +447,137 @@ rr_status build_plan(AmrHost& h, Plan& P, int64_t& nleaves, int64_t& nverts)
     P.stencil.assign((size_t)h.ncells * 18, 0);
     P.mode.assign((size_t)h.ncells, 0);
     P.frac.assign((size_t)h.ncells * 3, 0.f);
-    for (int64_t c = 0; c < h.ncells; ++c) {
-        int l;
-        int64_t x[3];
-        h.coords(c, l, x);
-        bool ok = true;
-        int32_t nb[18];
-        for (int t = 0; t < 18 && ok; ++t) {
-            const int64_t q = h.cell_at(l, x[0] + offs[t][0], x[1] + offs[t][1], x[2] + offs[t][2]);
-            ok = q >= 0;
-            nb[t] = (int32_t)q;
-        }
-        if (ok) {
-            memcpy(&P.stencil[(size_t)c * 18], nb, sizeof(nb));
-            continue;
-        }
-        if (l == 0) return RR_ERR_ARG;
-        // fine centre in coarse-centre units: x / 2 - 1/4
-        P.mode[(size_t)c] = 1;
-        int64_t c0[3];
-        for (int a = 0; a < 3; ++a) {
-            if (x[a] % 2 == 0) { c0[a] = x[a] / 2 - 1; P.frac[(size_t)c * 3 + a] = 0.75f; }
-            else { c0[a] = (x[a] - 1) / 2; P.frac[(size_t)c * 3 + a] = 0.25f; }
-        }
-        for (int t = 0; t < 8; ++t) {
-            const int64_t q = h.cell_at(l - 1, c0[0] + (t & 1), c0[1] + ((t >> 1) & 1), c0[2] + ((t >> 2) & 1));
-            if (q < 0) return RR_ERR_ARG;   // not 2:1 balanced
-            P.stencil[(size_t)c * 18 + t] = (int32_t)q;
-        }
-    }
-
-    // distinct lattice vertices the leaf corners need
-    const int64_t M = h.side(L);
-    std::unordered_map<uint64_t, int32_t> vid;
-    vid.reserve((size_t)nleaves * 2 + 16);
-    P.vcell.clear();
-    P.vw.clear();
-    P.corner.assign((size_t)nleaves * 8 * 4, -1);
-    bool bad = false;
-    // id of the plan vertex at V; -2 if V is in the middle of a coarse edge or face
-    auto get_vertex = [&](const int64_t V[3]) -> int32_t {
-        const uint64_t key = ((uint64_t)AmrHost::wrap(V[0], M) * (uint64_t)M + (uint64_t)AmrHost::wrap(V[1], M)) *
-                                 (uint64_t)M + (uint64_t)AmrHost::wrap(V[2], M);
-        auto it = vid.find(key);
-        if (it != vid.end()) return it->second;
-        int32_t cells[8];
-        float w[8];
-        int odd[3], lc;
-        const int rc = vertex_terms(h, V, cells, w, odd, lc);
-        if (rc < 0) { bad = true; return -1; }
-        if (rc == 1) return -2;
-        const int32_t id = (int32_t)(P.vcell.size() / 8);
-        P.vcell.insert(P.vcell.end(), cells, cells + 8);
-        P.vw.insert(P.vw.end(), w, w + 8);
-        vid.emplace(key, id);
-        return id;
-    };
-    for (int64_t lf = 0; lf < nleaves && !bad; ++lf) {
-        int l;
-        int64_t x[3];
-        h.coords(h.leaf_cell[(size_t)lf], l, x);
-        const int64_t step = (int64_t)1 << (L - l);
-        for (int t = 0; t < 8 && !bad; ++t) {
-            const int64_t V[3] = {(x[0] + (t & 1)) * step, (x[1] + ((t >> 1) & 1)) * step,
-                                  (x[2] + ((t >> 2) & 1)) * step};
-            int32_t* slot = &P.corner[((size_t)lf * 8 + t) * 4];
-            const int32_t id = get_vertex(V);
-            if (id >= 0) {
-                slot[0] = id;
+    std::atomic<int> bad{0};
+    parallel_for(h.ncells, [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c) {
+            int l;
+            int64_t x[3];
+            h.coords(c, l, x);
+            bool ok = true;
+            int32_t nb[18];
+            for (int t = 0; t < 18 && ok; ++t) {
+                const int64_t q = h.cell_at(l, x[0] + offs[t][0], x[1] + offs[t][1], x[2] + offs[t][2]);
+                ok = q >= 0;
+                nb[t] = (int32_t)q;
+            }
+            if (ok) {
+                memcpy(&P.stencil[(size_t)c * 18], nb, sizeof(nb));
                 continue;
             }
-            if (bad) break;
-            // middle of a coarse edge or face: the mean of its 2 or 4 coarse vertices
+            if (l == 0) {
+                bad = 1;
+                continue;
+            }
+            // fine centre in coarse-centre units: x / 2 - 1/4
+            P.mode[(size_t)c] = 1;
+            int64_t lo[3];
+            for (int a = 0; a < 3; ++a) {
+                if (x[a] % 2 == 0) { lo[a] = x[a] / 2 - 1; P.frac[(size_t)c * 3 + a] = 0.75f; }
+                else { lo[a] = (x[a] - 1) / 2; P.frac[(size_t)c * 3 + a] = 0.25f; }
+            }
+            for (int t = 0; t < 8; ++t) {
+                const int64_t q = h.cell_at(l - 1, lo[0] + (t & 1), lo[1] + ((t >> 1) & 1), lo[2] + ((t >> 2) & 1));
+                if (q < 0) bad = 1;   // not 2:1 balanced
+                P.stencil[(size_t)c * 18 + t] = (int32_t)q;
+            }
+        }
+    });
+    if (bad) return RR_ERR_ARG;
+
+    // Vertices. A lattice point V that is a corner of every leaf around it is
+    // owned by the leaf just above it (the leaf containing V + (1/2, 1/2, 1/2)
+    // finest cells), of which it is the lower corner; so the plan keeps one
+    // vertex slot per leaf, for its lower corner, with zero weights when that
+    // corner is hanging. Every other leaf corner lies in the middle of a
+    // coarser leaf's edge or face and takes the mean of that edge's or face's
+    // coarse vertices.
+    const int64_t M = h.side(L);
+    nverts = nleaves;
+    P.vcell.assign((size_t)nleaves * 8, 0);
+    P.vw.assign((size_t)nleaves * 8, 0.f);
+    P.corner.assign((size_t)nleaves * 8 * 4, -1);
+    std::vector<uint8_t> is_vertex((size_t)nleaves, 0);
+    auto lower_corner = [&](int64_t leaf, int64_t V[3]) {
+        int l;
+        int64_t x[3];
+        h.coords(h.leaf_cell[(size_t)leaf], l, x);
+        for (int a = 0; a < 3; ++a) V[a] = x[a] << (L - l);
+    };
+    parallel_for(nleaves, [&](int64_t b, int64_t e) {
+        for (int64_t lf = b; lf < e; ++lf) {
+            int64_t V[3];
+            lower_corner(lf, V);
             int32_t cells[8];
             float w[8];
             int odd[3], lc;
-            vertex_terms(h, V, cells, w, odd, lc);
-            const int nodd = odd[0] + odd[1] + odd[2];
-            if (nodd == 3) return RR_ERR_ARG;
-            const int64_t half = ((int64_t)1 << (L - lc)) / 2;
-            for (int p = 0; p < (1 << nodd); ++p) {
-                int64_t W[3] = {V[0], V[1], V[2]};
-                int bit = 0;
-                for (int a = 0; a < 3; ++a)
-                    if (odd[a]) {
-                        W[a] += ((p >> bit) & 1) ? half : -half;
-                        ++bit;
-                    }
-                const int32_t wid = get_vertex(W);
-                if (wid < 0) return RR_ERR_ARG;   // a coarse vertex in the middle of a coarser edge: not balanced
-                slot[p] = wid;
+            const int rc = vertex_terms(h, V, cells, w, odd, lc);
+            if (rc < 0) {
+                bad = 1;
+                continue;
+            }
+            if (rc == 0) {
+                memcpy(&P.vcell[(size_t)lf * 8], cells, sizeof(cells));
+                memcpy(&P.vw[(size_t)lf * 8], w, sizeof(w));
+                is_vertex[(size_t)lf] = 1;
+            } else {
+                for (int k = 0; k < 8; ++k) P.vcell[(size_t)lf * 8 + k] = (int32_t)h.leaf_cell[(size_t)lf];
             }
         }
-    }
+    });
     if (bad) return RR_ERR_ARG;
-    nverts = (int64_t)(P.vcell.size() / 8);
+    // slot of the plan vertex at V, or -1 if V is not one
+    auto vertex_at = [&](const int64_t V[3]) -> int32_t {
+        static const int up[3] = {1, 1, 1};
+        int lv;
+        const int32_t owner = P.link[(size_t)h.leaf_near(V, up, lv)];
+        int64_t W[3];
+        lower_corner(owner, W);
+        for (int a = 0; a < 3; ++a)
+            if (W[a] != AmrHost::wrap(V[a], M)) return -1;
+        return is_vertex[(size_t)owner] ? owner : -1;
+    };
+    parallel_for(nleaves, [&](int64_t b, int64_t e) {
+        for (int64_t lf = b; lf < e; ++lf) {
+            int l;
+            int64_t x[3];
+            h.coords(h.leaf_cell[(size_t)lf], l, x);
+            const int64_t step = (int64_t)1 << (L - l);
+            for (int t = 0; t < 8; ++t) {
+                const int64_t V[3] = {(x[0] + (t & 1)) * step, (x[1] + ((t >> 1) & 1)) * step,
+                                      (x[2] + ((t >> 2) & 1)) * step};
+                int32_t* slot = &P.corner[((size_t)lf * 8 + t) * 4];
+                const int32_t id = vertex_at(V);
+                if (id >= 0) {
+                    slot[0] = id;
+                    continue;
+                }
+                // middle of a coarse edge or face: the mean of its 2 or 4 coarse vertices
+                int32_t cells[8];
+                float w[8];
+                int odd[3], lc;
+                const int nodd_rc = vertex_terms(h, V, cells, w, odd, lc);
+                const int nodd = odd[0] + odd[1] + odd[2];
+                if (nodd_rc != 1 || nodd == 3) {
+                    bad = 1;
+                    break;
+                }
+                const int64_t half = ((int64_t)1 << (L - lc)) / 2;
+                for (int p = 0; p < (1 << nodd); ++p) {
+                    int64_t W[3] = {V[0], V[1], V[2]};
+                    int bit = 0;
+                    for (int a = 0; a < 3; ++a)
+                        if (odd[a]) {
+                            W[a] += ((p >> bit) & 1) ? half : -half;
+                            ++bit;
+                        }
+                    const int32_t wid = vertex_at(W);
+                    if (wid < 0) bad = 1;   // a coarse vertex in the middle of a coarser edge: not balanced
+                    slot[p] = wid;
+                }
+            }
+        }
+    });
+    if (bad) return RR_ERR_ARG;
     return RR_OK;
 }
 
@@ -456,6 +592,7 @@ void free_amr(rr_amr* A)
     cudaFree(A->d_vw);
     cudaFree(A->d_corner);
     cudaFree(A->d_leaf_cell);
+    cudaFree(A->d_coarse);
     cudaFree(A->d_H);
     cudaFree(A->d_V);
     delete A;
@@ -471,6 +608,76 @@ cudaError_t upload(T** dst, const std::vector<T>& src)
 }
 
 unsigned blocks_for(int64_t n) { return (unsigned)((n + NTA - 1) / NTA); }
+
+// Per level, the first cell number and the first leaf id whose coarse x is >= i.
+void build_x_tables(rr_amr* A, const Plan& P)
+{
+    const AmrHost& h = A->h;
+    const int n = h.n, L = h.lmax;
+    const int64_t nn = (int64_t)n * n;
+    A->cell_x.assign((size_t)L + 1, std::vector<int64_t>());
+    A->leaf_x.assign((size_t)L + 1, std::vector<int64_t>());
+    A->x_sorted = true;
+    // first index of each x in [first, last) of a sequence whose x never decreases
+    auto table = [&](int64_t first, int64_t last, auto x_of, std::vector<int64_t>& tab) {
+        std::vector<int64_t> cnt((size_t)n, 0);
+        int prev = 0;
+        for (int64_t i = first; i < last; ++i) {
+            const int x = x_of(i);
+            if (x < prev) return false;
+            ++cnt[(size_t)x];
+            prev = x;
+        }
+        tab.assign((size_t)n + 1, first);
+        for (int i = 0; i < n; ++i) tab[(size_t)i + 1] = tab[(size_t)i] + cnt[(size_t)i];
+        return true;
+    };
+    for (int l = 0; l <= L && A->x_sorted; ++l) {
+        const int64_t c0 = h.base[(size_t)l], c1 = h.base[(size_t)l + 1];
+        const int64_t f0 = std::lower_bound(h.leaf_cell.begin(), h.leaf_cell.end(), c0) - h.leaf_cell.begin();
+        const int64_t f1 = std::lower_bound(h.leaf_cell.begin(), h.leaf_cell.end(), c1) - h.leaf_cell.begin();
+        A->x_sorted = table(c0, c1, [&](int64_t c) { return (int)(P.coarse[(size_t)c] / nn); }, A->cell_x[(size_t)l]) &&
+                      table(f0, f1, [&](int64_t f) { return (int)(P.coarse[(size_t)h.leaf_cell[(size_t)f]] / nn); },
+                            A->leaf_x[(size_t)l]);
+    }
+}
+
+// Add the part of table `tab` (n + 1 entries: first index with coarse x >= i)
+// for x in [lo, lo + w) (periodic), times `mult`, to R.
+void add_x_ranges(Ranges& R, const std::vector<int64_t>& tab, int lo, int w, int n, int64_t mult)
+{
+    auto push = [&](int64_t a, int64_t b) {
+        if (b <= a || R.n >= kMaxRanges) return;
+        R.start[R.n] = a * mult;
+        R.pre[R.n + 1] = R.pre[R.n] + (b - a) * mult;
+        ++R.n;
+    };
+    if (w >= n) {
+        push(tab[0], tab[(size_t)n]);
+        return;
+    }
+    lo = (int)AmrHost::wrap(lo, n);
+    const int hi = lo + w;
+    if (hi <= n) {
+        push(tab[(size_t)lo], tab[(size_t)hi]);
+    } else {
+        push(tab[(size_t)lo], tab[(size_t)n]);
+        push(tab[0], tab[(size_t)(hi - n)]);
+    }
+}
+
+Ranges one_range(int64_t start, int64_t len)
+{
+    Ranges R;
+    R.n = 0;
+    R.pre[0] = 0;
+    if (len > 0) {
+        R.n = 1;
+        R.start[0] = start;
+        R.pre[1] = len;
+    }
+    return R;
+}
 
 }  // namespace
 
@@ -506,6 +713,7 @@ rr_status rr_amr_create(const rr_amr_desc* desc, const int32_t* const* octs, con
         if (e == cudaSuccess) e = upload(&A->d_vw, P.vw);
         if (e == cudaSuccess) e = upload(&A->d_corner, P.corner);
         if (e == cudaSuccess) e = upload(&A->d_leaf_cell, P.leaf_cell);
+        if (e == cudaSuccess) e = upload(&A->d_coarse, P.coarse);
         if (e == cudaSuccess) e = cudaMalloc((void**)&A->d_H, (size_t)A->h.ncells * 8 * sizeof(float));
         if (e == cudaSuccess)
             e = cudaMalloc((void**)&A->d_V, (size_t)std::max<int64_t>(A->nverts, 1) * 8 * sizeof(float));
@@ -515,6 +723,7 @@ rr_status rr_amr_create(const rr_amr_desc* desc, const int32_t* const* octs, con
         free_amr(A);
         return st;
     }
+    build_x_tables(A, P);
     std::vector<int32_t>().swap(A->h.refined);   // the tables live on the device from here on
     *out = A;
     return RR_OK;
@@ -538,15 +747,49 @@ rr_status rr_amr_sizes(rr_amr* A, int64_t* ncells, int64_t* nleaves, int64_t* nv
 }
 
 rr_status rr_amr_tidal(rr_amr* A, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
-                       void* stream)
+                       const int32_t* bbox, void* stream)
 {
     if (!A || !phi || !leaf_rec || ((uintptr_t)leaf_rec & 15u)) return RR_ERR_ARG;
     if (cell_tidal && ((uintptr_t)cell_tidal & 15u)) return RR_ERR_ARG;
     if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
     const AmrHost& h = A->h;
+    AmrBox box;
+    box.n = h.n;
+    box.all = bbox ? 0 : 1;
+    box.x0 = box.y0 = box.z0 = 0;
+    box.wx = box.wy = box.wz = h.n;
+    if (bbox) {
+        for (int a = 0; a < 3; ++a) {
+            const int64_t w = (int64_t)bbox[2 * a + 1] - bbox[2 * a];
+            if (w < 1 || w > h.n) return RR_ERR_ARG;
+        }
+        box.x0 = (int)AmrHost::wrap(bbox[0], h.n); box.wx = bbox[1] - bbox[0];
+        box.y0 = (int)AmrHost::wrap(bbox[2], h.n); box.wy = bbox[3] - bbox[2];
+        box.z0 = (int)AmrHost::wrap(bbox[4], h.n); box.wz = bbox[5] - bbox[4];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
     float* H = cell_tidal ? cell_tidal : A->d_H;
     const double h0 = h.box / h.n;
+    // index ranges of the cells / leaves a launch covers: x-slabs of the box
+    // (plus the launch's margin) when the levels are ordered by coarse x
+    const bool slabs = bbox && A->x_sorted;
+    auto level_cells = [&](int l, int margin) {
+        if (!slabs) return one_range(h.base[(size_t)l], h.base[(size_t)l + 1] - h.base[(size_t)l]);
+        Ranges R;
+        R.n = 0;
+        R.pre[0] = 0;
+        add_x_ranges(R, A->cell_x[(size_t)l], box.x0 - margin, box.wx + 2 * margin, h.n, 1);
+        return R;
+    };
+    auto all_leaves = [&](int margin, int64_t mult) {
+        if (!slabs) return one_range(0, A->nleaves * mult);
+        Ranges R;
+        R.n = 0;
+        R.pre[0] = 0;
+        for (int l = 0; l <= h.lmax; ++l)
+            add_x_ranges(R, A->leaf_x[(size_t)l], box.x0 - margin, box.wx + 2 * margin, h.n, mult);
+        return R;
+    };
     for (int l = 0; l <= h.lmax; ++l) {
         const double hl = h0 / (double)((int64_t)1 << l);
         TidalAmrArgs a;
@@ -554,23 +797,34 @@ rr_status rr_amr_tidal(rr_amr* A, const float* phi, int32_t where, float* leaf_r
         a.stencil = A->d_stencil;
         a.mode = A->d_mode;
         a.frac = A->d_frac;
+        a.coarse = A->d_coarse;
         a.H = H;
-        a.first = (int32_t)h.base[(size_t)l];
-        a.count = (int32_t)(h.base[(size_t)l + 1] - h.base[(size_t)l]);
         a.ih2 = (float)(1.0 / (hl * hl));
         a.iq = (float)(0.25 / (hl * hl));
         a.dinv = (float)(1.0 / (1.5 * h.omega_m * kH0OverC * kH0OverC));
-        if (a.count == 0) continue;
-        amr_tidal_kernel<<<blocks_for(a.count), NTA, 0, s>>>(a);
+        a.box = box;
+        // vertices read leaves up to 3 coarse cells outside the box; an
+        // interpolated cell reads the coarser level one coarse cell further out
+        a.margin = 3 + h.lmax - l;
+        a.cells = level_cells(l, a.margin);
+        const int64_t cnt = a.cells.pre[a.cells.n];
+        if (cnt == 0) continue;
+        amr_tidal_kernel<<<blocks_for(cnt), NTA, 0, s>>>(a);
     }
     if (where == RR_AT_VERTICES) {
-        if (A->nverts > 0)
-            amr_vertex_kernel<<<blocks_for(A->nverts), NTA, 0, s>>>(A->d_vcell, A->d_vw, H, A->d_V,
-                                                                    (int32_t)A->nverts);
-        amr_leafrec_kernel<<<blocks_for(A->nleaves * 8), NTA, 0, s>>>(A->d_corner, A->d_V, leaf_rec,
-                                                                      A->nleaves * 8);
+        const Ranges slots = all_leaves(2, 1);
+        if (slots.pre[slots.n] > 0)
+            amr_vertex_kernel<<<blocks_for(slots.pre[slots.n]), NTA, 0, s>>>(A->d_vcell, A->d_vw, H, A->d_V, slots,
+                                                                             A->d_leaf_cell, A->d_coarse, box);
+        const Ranges corners = all_leaves(0, 8);
+        if (corners.pre[corners.n] > 0)
+            amr_leafrec_kernel<<<blocks_for(corners.pre[corners.n]), NTA, 0, s>>>(
+                A->d_corner, A->d_V, leaf_rec, corners, A->d_leaf_cell, A->d_coarse, box);
     } else {
-        amr_leafcentre_kernel<<<blocks_for(A->nleaves), NTA, 0, s>>>(A->d_leaf_cell, H, leaf_rec, A->nleaves);
+        const Ranges leaves = all_leaves(0, 1);
+        if (leaves.pre[leaves.n] > 0)
+            amr_leafcentre_kernel<<<blocks_for(leaves.pre[leaves.n]), NTA, 0, s>>>(A->d_leaf_cell, H, leaf_rec,
+                                                                                   leaves, A->d_coarse, box);
     }
     return status_of_cuda(cudaGetLastError());
 }

@@ -50,6 +50,8 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     const int nsub = F64 ? 1 : max(1, (int)ceilf(rg.Lf / A.sub_len));
     const float dsub = rg.Lf / (float)nsub;
 
+    // per-step sums of (kappa, Born kappa): packed Kahan pairs (FP32) or FP64
+    Acc2 s2;
     Acc<R> sk, sb;
     uint32_t cnt = 0;
     int iter = 0;
@@ -77,9 +79,9 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     bool resume = j > 0 && c[0] == pc0 && c[1] == pc1 && c[2] == pc2;
     iter = 0;
 
-    // Field cache: projected kappa values and delta at the 8 mirrored corners
+    // Field cache: (projected kappa value, delta) at the 8 mirrored corners
     // (trilinear) or at the cell centre (NGP).
-    float qk[8], qb[8];
+    float2 q2[8];
     if (INTERP == RR_TRILINEAR) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -87,13 +89,11 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
             const int gy = (m & 2) ? vhi[1] : vlo[1];
             const int gz = (m & 4) ? vhi[2] : vlo[2];
             const Rec r = load_rec(A.rec, gx * sx + gy * sy + gz);
-            qk[m] = project(w, r);
-            qb[m] = r.b.z;
+            q2[m] = make_float2(project(w, r), r.b.z);
         }
     } else {
         const Rec r = load_rec(A.rec, c[0] * sx + c[1] * sy + c[2]);
-        qk[0] = project(w, r);
-        qb[0] = r.b.z;
+        q2[0] = make_float2(project(w, r), r.b.z);
     }
 
     R sig = 0;                       // path from the sub-step start to the segment entry
@@ -161,17 +161,27 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                 const R J2 = t2 * (G0 * (R)0.5 + t * (G1 * (R)(1.0 / 3.0) + t * G2 * (R)0.25));
                 const R J3 = t2 * t * (G0 * (R)(1.0 / 3.0) + t * (G1 * (R)0.25 + t * G2 * (R)0.2));
                 const R J4 = t2 * t2 * (G0 * (R)0.25 + t * (G1 * (R)0.2 + t * G2 * (R)(1.0 / 6.0)));
-                float ek[4], eb[4];
-                const float fu0 = (float)u[0], fu1 = (float)u[1], fu2 = (float)u[2];
-                const float fv0 = (float)v[0], fv1 = (float)v[1], fv2 = (float)v[2];
-                line_cubic(qk, fu0, fu1, fu2, fv0, fv1, fv2, ek);
-                line_cubic(qb, fu0, fu1, fu2, fv0, fv1, fv2, eb);
-                sk.add((R)ek[0] * J1 + (R)ek[1] * J2 + (R)ek[2] * J3 + (R)ek[3] * J4);
-                sb.add((R)eb[0] * J1 + (R)eb[1] * J2 + (R)eb[2] * J3 + (R)eb[3] * J4);
+                float2 e2[4];
+                line_cubic2(q2, bc2((float)u[0]), bc2((float)u[1]), bc2((float)u[2]), bc2((float)v[0]),
+                            bc2((float)v[1]), bc2((float)v[2]), e2);
+                if constexpr (F64) {
+                    sk.add((R)e2[0].x * J1 + (R)e2[1].x * J2 + (R)e2[2].x * J3 + (R)e2[3].x * J4);
+                    sb.add((R)e2[0].y * J1 + (R)e2[1].y * J2 + (R)e2[2].y * J3 + (R)e2[3].y * J4);
+                } else {
+                    float2 x = __fmul2_rn(e2[0], bc2(J1));
+                    x = __ffma2_rn(e2[1], bc2(J2), x);
+                    x = __ffma2_rn(e2[2], bc2(J3), x);
+                    x = __ffma2_rn(e2[3], bc2(J4), x);
+                    s2.add(x);
+                }
             } else {
                 const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
-                sk.add((R)qk[0] * J1);
-                sb.add((R)qb[0] * J1);
+                if constexpr (F64) {
+                    sk.add((R)q2[0].x * J1);
+                    sb.add((R)q2[0].y * J1);
+                } else {
+                    s2.add(__fmul2_rn(q2[0], bc2(J1)));
+                }
             }
             if (resume) resume = false;
             else ++cnt;
@@ -189,34 +199,25 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                 vlo[a] = vhi[a];
                 vhi[a] = nvhi;
                 k[a] += 1;
-                T[a] = fma((R)k[a], td[a], T0[a]);
+                if constexpr (F64) T[a] = fma((R)k[a], td[a], T0[a]);
+                else T[a] = fmaf(i2f_exact(k[a]), td[a], T0[a]);
             }
         if (INTERP == RR_TRILINEAR) {
-            float pk[4], pb[4];
+            float2 p2[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                pk[r] = project(w, nr[r]);
-                pb[r] = nr[r].b.z;
-            }
+            for (int r = 0; r < 4; ++r) p2[r] = make_float2(project(w, nr[r]), nr[r].b.z);
             if (e == 0) {
-                qk[0] = qk[1]; qk[2] = qk[3]; qk[4] = qk[5]; qk[6] = qk[7];
-                qk[1] = pk[0]; qk[3] = pk[1]; qk[5] = pk[2]; qk[7] = pk[3];
-                qb[0] = qb[1]; qb[2] = qb[3]; qb[4] = qb[5]; qb[6] = qb[7];
-                qb[1] = pb[0]; qb[3] = pb[1]; qb[5] = pb[2]; qb[7] = pb[3];
+                q2[0] = q2[1]; q2[2] = q2[3]; q2[4] = q2[5]; q2[6] = q2[7];
+                q2[1] = p2[0]; q2[3] = p2[1]; q2[5] = p2[2]; q2[7] = p2[3];
             } else if (e == 1) {
-                qk[0] = qk[2]; qk[1] = qk[3]; qk[4] = qk[6]; qk[5] = qk[7];
-                qk[2] = pk[0]; qk[3] = pk[1]; qk[6] = pk[2]; qk[7] = pk[3];
-                qb[0] = qb[2]; qb[1] = qb[3]; qb[4] = qb[6]; qb[5] = qb[7];
-                qb[2] = pb[0]; qb[3] = pb[1]; qb[6] = pb[2]; qb[7] = pb[3];
+                q2[0] = q2[2]; q2[1] = q2[3]; q2[4] = q2[6]; q2[5] = q2[7];
+                q2[2] = p2[0]; q2[3] = p2[1]; q2[6] = p2[2]; q2[7] = p2[3];
             } else {
-                qk[0] = qk[4]; qk[1] = qk[5]; qk[2] = qk[6]; qk[3] = qk[7];
-                qk[4] = pk[0]; qk[5] = pk[1]; qk[6] = pk[2]; qk[7] = pk[3];
-                qb[0] = qb[4]; qb[1] = qb[5]; qb[2] = qb[6]; qb[3] = qb[7];
-                qb[4] = pb[0]; qb[5] = pb[1]; qb[6] = pb[2]; qb[7] = pb[3];
+                q2[0] = q2[4]; q2[1] = q2[5]; q2[2] = q2[6]; q2[3] = q2[7];
+                q2[4] = p2[0]; q2[5] = p2[1]; q2[6] = p2[2]; q2[7] = p2[3];
             }
         } else {
-            qk[0] = project(w, nr[0]);
-            qb[0] = nr[0].b.z;
+            q2[0] = make_float2(project(w, nr[0]), nr[0].b.z);
         }
         if (++iter > max_iter) {
             overflow = true;
@@ -226,6 +227,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     pc0 = c[0]; pc1 = c[1]; pc2 = c[2];
     }
 
+    if constexpr (!F64) {
+        sk.s = s2.s.x; sk.c = s2.c.x;
+        sb.s = s2.s.y; sb.c = s2.c.y;
+    }
     if (overflow) atomicOr(A.err, kErrStepLimit);
     if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
     float kh, kl, bh, bl;

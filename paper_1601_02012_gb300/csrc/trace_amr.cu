@@ -53,7 +53,7 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     // slivers: as in the uniform walk, 4 ulp of the path
     const float eps_rel = 4.76837158203125e-07f;
 
-    Acc<float> sk, sb;
+    Acc2 s2;   // (kappa, Born kappa) Kahan pairs
     uint32_t cnt = 0;
     bool overflow = false;
     int prev_leaf = -1;   // leaf of the last integrated segment
@@ -65,7 +65,7 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
         const float Ls = W.L, chiA0 = W.chiA0, D0 = W.D0;
         const float eps_end = Ls * eps_rel;
         int q[3] = {W.c[0], W.c[1], W.c[2]};   // finest cell of the current point
-        int K[3] = {0, 0, 0};                   // finest-face crossings so far, per axis
+        float K[3] = {0.f, 0.f, 0.f};           // finest-face crossings so far, per axis (exact integers)
         const int flip = (W.sgn[0] < 0 ? 1 : 0) | (W.sgn[1] < 0 ? 2 : 0) | (W.sgn[2] < 0 ? 4 : 0);
         float sig = 0.f;                        // path from the sub-step start to the segment entry
         int iter = 0;
@@ -82,13 +82,14 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
             // crossings to the leaf's exit face (m), mirrored finest position in the
             // leaf (jp) and path to the exit (Tx), per axis
             int m[3], jp[3];
-            float Tx[3];
+            float mf[3], Tx[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int pos = q[a] & (span - 1);
                 m[a] = W.sgn[a] > 0 ? span - pos : pos + 1;
                 jp[a] = W.sgn[a] > 0 ? pos : span - 1 - pos;
-                Tx[a] = W.v[a] > 0.f ? fmaf((float)(K[a] + m[a] - 1), W.td[a], W.T0[a]) : 1e30f;
+                mf[a] = i2f_exact(m[a]);
+                Tx[a] = W.v[a] > 0.f ? fmaf(K[a] + (mf[a] - 1.f), W.td[a], W.T0[a]) : 1e30f;
             }
             float tend = Tx[0];
             int e = 0;
@@ -99,7 +100,7 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
             const float t = tend - sig;
 
             if (t > tend * eps_rel) {
-                float qk[8], qb[8];
+                float2 q2[8];   // (Q_kappa, delta) at the mirrored corners, or the leaf's own value
                 if (INTERP == RR_TRILINEAR) {
                     const float4* r = A.rec + 16 * (long long)leaf;
 #pragma unroll
@@ -108,13 +109,11 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                         Rec x;
                         x.a = __ldg(r + 2 * rc);
                         x.b = __ldg(r + 2 * rc + 1);
-                        qk[c] = project(W.w, x);
-                        qb[c] = x.b.z;
+                        q2[c] = make_float2(project(W.w, x), x.b.z);
                     }
                 } else {
                     const Rec x = load_rec(A.rec, leaf);
-                    qk[0] = project(W.w, x);
-                    qb[0] = x.b.z;
+                    q2[0] = make_float2(project(W.w, x), x.b.z);
                 }
                 // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
                 const float chiA = chiA0 - sig;
@@ -127,22 +126,23 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                     for (int a = 0; a < 3; ++a) {
                         vl[a] = W.v[a] * inv_span;
                         u[a] = W.v[a] > 0.f ? fminf(fmaxf(fmaf(sig - Tx[a], vl[a], 1.f), 0.f), 1.f)
-                                            : ((float)jp[a] + W.cu[a]) * inv_span;
+                                            : (i2f_exact(jp[a]) + W.cu[a]) * inv_span;
                     }
                     const float t2 = t * t;
                     const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
                     const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
                     const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
                     const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
-                    float ek[4], eb[4];
-                    line_cubic(qk, u[0], u[1], u[2], vl[0], vl[1], vl[2], ek);
-                    line_cubic(qb, u[0], u[1], u[2], vl[0], vl[1], vl[2], eb);
-                    sk.add(ek[0] * J1 + ek[1] * J2 + ek[2] * J3 + ek[3] * J4);
-                    sb.add(eb[0] * J1 + eb[1] * J2 + eb[2] * J3 + eb[3] * J4);
+                    float2 e2[4];
+                    line_cubic2(q2, bc2(u[0]), bc2(u[1]), bc2(u[2]), bc2(vl[0]), bc2(vl[1]), bc2(vl[2]), e2);
+                    float2 x = __fmul2_rn(e2[0], bc2(J1));
+                    x = __ffma2_rn(e2[1], bc2(J2), x);
+                    x = __ffma2_rn(e2[2], bc2(J3), x);
+                    x = __ffma2_rn(e2[3], bc2(J4), x);
+                    s2.add(x);
                 } else {
                     const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
-                    sk.add(qk[0] * J1);
-                    sb.add(qb[0] * J1);
+                    s2.add(__fmul2_rn(q2[0], bc2(J1)));
                 }
                 if (leaf != prev_leaf) ++cnt;
                 prev_leaf = leaf;
@@ -156,16 +156,17 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 if (a == e) {
-                    K[a] += m[a];
+                    K[a] += mf[a];
                     const int nq = q[a] + W.sgn[a] * m[a];
                     outside = nq < 0 || nq >= NF;
                     q[a] = wrap_once(nq, NF);
                 } else if (W.v[a] > 0.f) {
-                    const int kmax = K[a] + m[a] - 1;
-                    int k = (int)fminf(fmaxf(ceilf((tend - W.T0[a]) * W.v[a]), (float)K[a]), (float)kmax);
-                    while (k > K[a] && fmaf((float)(k - 1), W.td[a], W.T0[a]) >= tend) --k;
-                    while (k < kmax && fmaf((float)k, W.td[a], W.T0[a]) < tend) ++k;
-                    q[a] = wrap_once(q[a] + W.sgn[a] * (k - K[a]), NF);
+                    // counters are exact integers in float: the first crossing at or after tend
+                    const float kmax = K[a] + (mf[a] - 1.f);
+                    float k = fminf(fmaxf(ceilf((tend - W.T0[a]) * W.v[a]), K[a]), kmax);
+                    while (k > K[a] && fmaf(k - 1.f, W.td[a], W.T0[a]) >= tend) k -= 1.f;
+                    while (k < kmax && fmaf(k, W.td[a], W.T0[a]) < tend) k += 1.f;
+                    q[a] = wrap_once(q[a] + W.sgn[a] * f2i_exact(k - K[a]), NF);
                     K[a] = k;
                 }
             }
@@ -178,10 +179,10 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     }
 
     if (overflow) atomicOr(A.err, kErrStepLimit);
-    if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
+    if (!s2.finite()) atomicOr(A.err, kErrNonFinite);
     float kh, kl, bh, bl;
-    sk.pair(kh, kl);
-    sb.pair(bh, bl);
+    two_sum(s2.s.x, -s2.c.x, kh, kl);
+    two_sum(s2.s.y, -s2.c.y, bh, bl);
     A.kacc[rid] = ff_mul_add(A.kacc[rid], kh, kl, A.sch, A.scl);
     A.bacc[rid] = ff_mul_add(A.bacc[rid], bh, bl, A.bsh, A.bsl);
     A.nseg[rid] += cnt;

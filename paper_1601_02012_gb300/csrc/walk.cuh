@@ -104,6 +104,61 @@ __device__ __forceinline__ float2 ff_mul_add(float2 acc, float xh, float xl, flo
     return make_float2(hi, t - (hi - s));
 }
 
+// ---- (kappa, delta) pairs on the packed FP32 pipe (FFMA2 / FADD2 / FMUL2) ---
+// Each packed operation rounds each lane exactly as its scalar counterpart.
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+// a - b as fma(b, -1, a): one rounding, the same result as a scalar subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// line_cubic on the pair channels: q[m] = (Q_kappa, delta) at mirrored corner m
+__device__ __forceinline__ void line_cubic2(const float2 q[8], float2 u0, float2 u1, float2 u2, float2 v0,
+                                            float2 v1, float2 v2, float2 e[4])
+{
+    float2 A[4], B[4];
+#pragma unroll
+    for (int jk = 0; jk < 4; ++jk) {
+        const float2 lo = q[2 * jk], d = sub2(q[2 * jk + 1], lo);
+        A[jk] = __ffma2_rn(d, u0, lo);
+        B[jk] = __fmul2_rn(d, v0);
+    }
+    float2 M0[2], M1[2], M2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float2 C = sub2(A[2 * k + 1], A[2 * k]), D = sub2(B[2 * k + 1], B[2 * k]);
+        M0[k] = __ffma2_rn(C, u1, A[2 * k]);
+        M1[k] = __ffma2_rn(C, v1, __ffma2_rn(D, u1, B[2 * k]));
+        M2[k] = __fmul2_rn(D, v1);
+    }
+    const float2 E0 = sub2(M0[1], M0[0]), E1 = sub2(M1[1], M1[0]), E2 = sub2(M2[1], M2[0]);
+    e[0] = __ffma2_rn(E0, u2, M0[0]);
+    e[1] = __ffma2_rn(E0, v2, __ffma2_rn(E1, u2, M1[0]));
+    e[2] = __ffma2_rn(E1, v2, __ffma2_rn(E2, u2, M2[0]));
+    e[3] = __fmul2_rn(E2, v2);
+}
+
+// Kahan sums of both channels at once
+struct Acc2 {
+    float2 s = {0.f, 0.f}, c = {0.f, 0.f};
+    __device__ __forceinline__ void add(float2 x)
+    {
+        const float2 y = sub2(x, c);
+        const float2 t = __fadd2_rn(s, y);
+        c = sub2(sub2(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ bool finite() const
+    {
+        return isfinite(s.x) && isfinite(c.x) && isfinite(s.y) && isfinite(c.y);
+    }
+};
+
+// float of an integer in [0, 2^23) and back, exact, on the FP32/integer pipes
+// (the bit pattern of 2^23 + i), instead of the conversion unit
+__device__ __forceinline__ float i2f_exact(int i) { return __int_as_float(0x4B000000 | i) - 8388608.f; }
+__device__ __forceinline__ int f2i_exact(float f) { return __float_as_int(f + 8388608.f) - 0x4B000000; }
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x)
 {
     const float y = x - c;

@@ -127,5 +127,5 @@ def test_amr_plan_validation_is_host_side(rr):
     assert lib.rr_amr_create(None, None, None, C.byref(h)) == rr.RR_ERR_ARG
     assert lib.rr_amr_destroy(None) == rr.RR_ERR_ARG
     assert lib.rr_amr_sizes(None, None, None, None) == rr.RR_ERR_ARG
-    assert lib.rr_amr_tidal(None, C.c_void_p(16), 0, C.c_void_p(16), None, None) == rr.RR_ERR_ARG
+    assert lib.rr_amr_tidal(None, C.c_void_p(16), 0, C.c_void_p(16), None, None, None) == rr.RR_ERR_ARG
     assert lib.rr_amr_trace_step(None, None, C.c_void_p(16), 1.0, 0.0, 1.0, 1.0, None) == rr.RR_ERR_ARG

@@ -278,3 +278,71 @@ def test_errors_and_no_adjoint(rrp):
     with pytest.raises(rrp.RRError):
         gm.tidal(torch.zeros(4, device="cuda"), rec, 7)
     gm.close()
+
+
+def _shuffled(mesh, seed):
+    """The same mesh with the octs of every level listed in a random order
+    (and the potential rows with them): another cell numbering."""
+    rng = np.random.default_rng(seed)
+    octs, phi = [mesh.octs[0]], [mesh.phi[0]]
+    for l in range(1, mesh.lmax + 1):
+        perm = rng.permutation(len(mesh.octs[l]))
+        octs.append(np.ascontiguousarray(mesh.octs[l][perm]))
+        phi.append(np.ascontiguousarray(mesh.phi[l][perm]))
+    out = synth.AmrMesh(mesh.n, mesh.box, mesh.lmax, octs, phi, mesh.omega_m)
+    return out
+
+
+@pytest.mark.parametrize("interp", [1, 0])
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_footprint_records_give_the_same_maps(rrp, interp, shuffle):
+    """Records of only the leaves in each step's coarse footprint box (the
+    rest left as NaN) give the same maps, bit for bit, as records of the
+    whole mesh: the walk reads nothing outside the box. With the octs listed
+    out of order (no x-slab launches; another cell numbering) the maps are
+    the same bits again."""
+    import torch
+    mesh = synth.amr_random(16, 32.0, 2, 6, threshold=1.5, child_sigma=0.8)
+    mesh.phi = synth.amr_sample(mesh, synth.fourier_fn(32.0, 40, 2 * math.pi / 32.0 * 6, 17))
+    _round_phi(mesh)
+    reference = None
+    if shuffle:
+        b0 = synth.Bundle(21, 18, synth.deg(8), synth.deg(6), (16.0, 15.0, 0.5), 30.0, interp=interp)
+        st0 = [synth.Step(30.0, 20.0, 1.2, 0.7), synth.Step(20.0, 10.0, 1.1, 0.85), synth.Step(10.0, 0.0, 1.0, 1.0)]
+        reference = _trace_gpu(rrp, mesh, b0, st0)
+        mesh = _shuffled(mesh, 23)
+    b = synth.Bundle(21, 18, synth.deg(8), synth.deg(6), (16.0, 15.0, 0.5), 30.0, interp=interp)
+    steps = [synth.Step(30.0, 20.0, 1.2, 0.7), synth.Step(20.0, 10.0, 1.1, 0.85), synth.Step(10.0, 0.0, 1.0, 1.0)]
+    where = rrp.RR_AT_VERTICES if interp == 1 else rrp.RR_AT_CENTRES
+    gm = _gpu_mesh(rrp, mesh)
+    phi = torch.from_numpy(_flat_phi(mesh)).cuda()
+    full = gm.record_buffer(where)
+    gm.tidal(phi, full, where)
+    maps = []
+    for use_box in (False, True):
+        tr = rrp.Tracer(b)
+        rec = gm.record_buffer(where)
+        written = 0
+        for st in steps:
+            if use_box:
+                bb = gm.footprint(tr, st.chi_a, st.chi_b)
+                assert any(bb[2 * a + 1] - bb[2 * a] < 16 for a in range(3))
+                rec.fill_(float("nan"))
+                gm.tidal(phi, rec, where, bbox=bb)
+                ok = ~torch.isnan(rec).any(dim=1)
+                written += int(ok.sum())
+                assert torch.equal(rec[ok], full[ok])
+            else:
+                rec.copy_(full)
+            tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a)
+        k, kb = tr.finalize()
+        maps.append((k.cpu().numpy(), kb.cpu().numpy(), tr.segments()))
+        tr.close()
+        if use_box:
+            assert 0 < written < len(steps) * gm.nleaves
+    assert np.array_equal(maps[0][0], maps[1][0]) and np.array_equal(maps[0][1], maps[1][1])
+    assert maps[0][2] == maps[1][2]
+    if reference is not None:
+        assert np.array_equal(reference[0], maps[0][0].ravel()) and np.array_equal(reference[1], maps[0][1].ravel())
+        assert reference[2] == maps[0][2]
+    gm.close()
