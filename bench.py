@@ -41,14 +41,38 @@ BYTES_PER_SEGMENT = 256
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic of one trace launch from an ncu capture, valid only for the
-# kernel source it was taken on (sha256 of csrc/trace.cu). Empty until measured.
+# kernel source it was taken on (sha256 of csrc/trace.cu + csrc/walk.cuh).
 TRACE_TRAFFIC = {}
 
 
-def _src_hash(name):
-    p = os.path.join(ROOT, "paper_1601_02012_gb300", "csrc", name)
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def _src_hash(*names):
+    """sha256 (16 hex digits) of the kernel sources, in the given order."""
+    hsh = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_1601_02012_gb300", "csrc", name), "rb") as f:
+            hsh.update(f.read())
+    return hsh.hexdigest()[:16]
+
+
+def rank_seed(base_seed, rank):
+    """Field seed of a rank: every rank traces its own lightcone (its own field
+    realisation), so the ranks share no data and need no collective."""
+    return base_seed + 1000 * rank
+
+
+def combine_over_ranks(dist, device, total_ms, segs, e2e_s):
+    """Whole-job figures from the ranks' own: the slowest rank's timed and
+    end-to-end seconds (the job ends when it does) and the sum of the ranks'
+    segments. `dist` is torch.distributed (or None for one rank); `device`
+    holds the reduction tensors (the rank's GPU under NCCL, CPU under gloo)."""
+    if dist is None:
+        return total_ms, segs, e2e_s
+    import torch
+    t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(segs)], dtype=torch.float64, device=device)
+    dist.all_reduce(n)
+    return float(t[0].item()), int(n[0].item()), float(t[1].item())
 
 
 def _peaks():
@@ -474,7 +498,7 @@ def run_amr(args, name):
                 "d2h_bytes_per_step": int(k_host.numel() * 8 * 2)},
         "gpu_launches": args.steps * (nst * (w.lmax + 4) + 1),
         "clocks": clocks,
-        "trace_src": _src_hash("trace_amr.cu"),
+        "trace_src": _src_hash("trace_amr.cu", "walk.cuh"),
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -573,7 +597,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     # each rank traces its own lightcone (its own field realisation): no data-path collective
-    seed = w.seed + 1000 * rank
+    seed = rank_seed(w.seed, rank)
     phi_host = synth.grf_phi_cached(w.grid.n[0], w.grid.box, seed)
     stream = torch.cuda.Stream(device=dev)
     phi = torch.from_numpy(phi_host).to(dev)
@@ -625,17 +649,10 @@ def main():
             trace_ms += sum(a.elapsed_time(b) for a, b in ev_tr)
             tidal_ms += sum(a.elapsed_time(b) for a, b in ev_td)
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         clocks = sampler.stop()
         total_ms = sum(times)
-        if dist is not None:
-            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-            s = torch.tensor([segs], dtype=torch.float64, device=dev)
-            dist.all_reduce(s)
-            segs_all = int(s.item())
-        else:
-            segs_all = segs
 
         # the tidal kernel on the whole grid (its HBM roofline; not part of a pass)
         full_ms = []
@@ -689,10 +706,7 @@ def main():
             if it >= args.warmup:
                 e2e_times.append(time.perf_counter() - t0)
         e2e_s = sum(e2e_times)
-        if dist is not None:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        total_ms, segs_all, e2e_s = combine_over_ranks(dist, dev, total_ms, segs, e2e_s)
 
     if rank != 0:
         dist.barrier()
@@ -703,7 +717,7 @@ def main():
     per_pass_trace_s = trace_ms / args.steps / 1e3
     achieved = segs * BYTES_PER_SEGMENT / per_pass_trace_s / 1e9
     tidal_points = sum((b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]) for b in bboxes)
-    h = _src_hash("trace.cu")
+    h = _src_hash("trace.cu", "walk.cuh")
     traffic = TRACE_TRAFFIC.get(h)
     value = segs_all * args.steps / (total_ms / 1e3)
     line = {

@@ -1,26 +1,31 @@
 // Tidal tensor and vertex records (Sec. 3.3, Eq. tidalexample; Sec. 2.7).
 //
-// One CTA produces a 4 x 4 x 32 tile of records (z fastest). It stages the
-// potential of the tile plus a halo of two cells in shared memory, evaluates
-// the six central-difference second derivatives at every cell centre the tile
-// needs, and then either averages the 8 cells around each vertex or copies
-// the centre values. Reads are 4 B per point from HBM (halo re-reads hit L2),
-// writes 32 B per point as contiguous float4 runs: the kernel is bound by HBM
-// bandwidth, 36 algorithmic bytes per point.
+// One CTA owns a TY x TZ column of output points (z fastest, one warp per
+// z-row) and marches along x through a chunk of planes. Per plane it keeps
+// three planes of the potential (with a two-cell halo in y and z) in a shared
+// ring, evaluates the six central-difference second derivatives at the cell
+// centres of the current plane, and for records at vertices adds the 2 x 2
+// centres around each vertex in that plane; a vertex's record is the mean of
+// that sum and the previous plane's (kept in registers), i.e. of the 8 cells
+// around it. The next potential plane is loaded into registers while the
+// current one is processed. HBM traffic per point: the potential read about
+// 1.4 times (halo re-reads of neighbouring columns hit L2) and the 32-byte
+// record written once, as 1 KiB runs per warp: 36 algorithmic bytes per point.
 #include "rr_internal.h"
 
 namespace rr {
 namespace {
 
-constexpr int TX = 4, TY = 4, TZ = 32;
-constexpr int NT = 256;
+constexpr int TY = 8, TZ = 32;       // output points per CTA and plane
+constexpr int NT = TY * TZ;          // one thread per output point
+constexpr int XCHUNK = 32;           // planes per CTA
 
 struct TidalArgs {
     const float* phi;
     const float* delta;
     float4* rec;
     int n0, n1, n2;
-    int x0, y0, z0;   // first point of the box (may be negative; wrapped)
+    int x0, y0, z0;   // first point of the box (wrapped into [0, n))
     int ex, ey, ez;   // box extents
     float ih2;        // 1/h^2
     float iq;         // 1/(4 h^2)
@@ -38,88 +43,109 @@ __device__ __forceinline__ int wrapi(int i, int n)
 
 // MODE 0: records at vertices; MODE 1: records at centres.
 template <int MODE>
-__global__ void __launch_bounds__(NT) tidal_kernel(TidalArgs a)
+__global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
 {
-    constexpr int V = (MODE == 0) ? 1 : 0;           // extra cell below each point
-    constexpr int CX = TX + V, CY = TY + V, CZ = TZ + V;
-    constexpr int PX = CX + 2, PY = CY + 2, PZ = CZ + 2;
-    constexpr int NC = CX * CY * CZ;
-    __shared__ float sphi[PX * PY * PZ];
-    __shared__ float sH[7][NC];
+    constexpr int V = (MODE == 0) ? 1 : 0;           // extra centre row below each output row
+    constexpr int CY = TY + V, CZ = TZ + V;          // centres per plane
+    constexpr int PY = CY + 2, PZ = CZ + 2;          // potential per plane (halo 1 around the centres)
+    constexpr int NP = PY * PZ, NC = CY * CZ;
+    constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane
+    __shared__ float ring[3][NP];
+    __shared__ float sH[MODE == 0 ? 7 : 1][MODE == 0 ? NC : 1];
 
-    const int px0 = blockIdx.z * TX, py0 = blockIdx.y * TY, pz0 = blockIdx.x * TZ;  // box-relative
-    const int cx0 = a.x0 + px0 - V, cy0 = a.y0 + py0 - V, cz0 = a.z0 + pz0 - V;     // first cell
+    const int ty = threadIdx.x / TZ, tz = threadIdx.x % TZ;
+    const int py0 = blockIdx.y * TY, pz0 = blockIdx.x * TZ;            // box-relative
+    const int xb = blockIdx.z * XCHUNK, xe = min(xb + XCHUNK, a.ex);   // output planes [xb, xe)
+    const int cy0 = a.y0 + py0 - V, cz0 = a.z0 + pz0 - V;              // first centre of the column
+    const int c_first = a.x0 + xb - V, c_last = a.x0 + xe - 1;         // centre planes (global, unwrapped)
 
-    for (int i = threadIdx.x; i < PX * PY * PZ; i += NT) {
-        const int z = i % PZ, y = (i / PZ) % PY, x = i / (PZ * PY);
-        const int gx = wrapi(cx0 - 1 + x, a.n0), gy = wrapi(cy0 - 1 + y, a.n1), gz = wrapi(cz0 - 1 + z, a.n2);
-        sphi[i] = __ldg(a.phi + ((size_t)gx * a.n1 + gy) * a.n2 + gz);
+    // potential plane gx into registers / into a ring slot
+    int poff[LP];
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+        const int i = threadIdx.x + k * NT;
+        const int y = i / PZ, z = i % PZ;
+        poff[k] = i < NP ? wrapi(cy0 - 1 + y, a.n1) * a.n2 + wrapi(cz0 - 1 + z, a.n2) : -1;
     }
-    __syncthreads();
-
-    for (int i = threadIdx.x; i < NC; i += NT) {
-        const int z = i % CZ, y = (i / CZ) % CY, x = i / (CZ * CY);
-        const float* c = sphi + ((x + 1) * PY + (y + 1)) * PZ + (z + 1);
-        constexpr int SX = PY * PZ, SY = PZ;
-        const float p0 = c[0];
-        // Eq. (tidalexample): (Phi_- - 2 Phi_0 + Phi_+)/h^2 and (Phi_++ + Phi_-- - Phi_+- - Phi_-+)/(4h^2)
-        const float hxx = (c[-SX] - 2.f * p0 + c[SX]) * a.ih2;
-        const float hyy = (c[-SY] - 2.f * p0 + c[SY]) * a.ih2;
-        const float hzz = (c[-1] - 2.f * p0 + c[1]) * a.ih2;
-        const float hxy = ((c[SX + SY] + c[-SX - SY]) - (c[SX - SY] + c[-SX + SY])) * a.iq;
-        const float hxz = ((c[SX + 1] + c[-SX - 1]) - (c[SX - 1] + c[-SX + 1])) * a.iq;
-        const float hyz = ((c[SY + 1] + c[-SY - 1]) - (c[SY - 1] + c[-SY + 1])) * a.iq;
-        float d;
-        if (a.delta) {
-            const int gx = wrapi(cx0 + x, a.n0), gy = wrapi(cy0 + y, a.n1), gz = wrapi(cz0 + z, a.n2);
-            d = __ldg(a.delta + ((size_t)gx * a.n1 + gy) * a.n2 + gz);
-        } else {
-            d = (hxx + hyy + hzz) * a.dinv;
+    auto fetch = [&](int gx, float r[LP]) {
+        const size_t base = (size_t)wrapi(gx, a.n0) * a.n1 * a.n2;
+#pragma unroll
+        for (int k = 0; k < LP; ++k) r[k] = poff[k] >= 0 ? __ldg(a.phi + base + poff[k]) : 0.f;
+    };
+    auto put = [&](int slot, const float r[LP]) {
+#pragma unroll
+        for (int k = 0; k < LP; ++k) {
+            const int i = threadIdx.x + k * NT;
+            if (i < NP) ring[slot][i] = r[k];
         }
-        sH[0][i] = hxx; sH[1][i] = hyy; sH[2][i] = hzz;
-        sH[3][i] = hxy; sH[4][i] = hxz; sH[5][i] = hyz;
-        sH[6][i] = d;
+    };
+    {
+        float r[LP];
+        fetch(c_first - 1, r); put(0, r);
+        fetch(c_first, r); put(1, r);
+        fetch(c_first + 1, r); put(2, r);
     }
     __syncthreads();
 
-    // Output: 2 float4 per point, flattened so that consecutive threads write
-    // consecutive 16-byte words (z-fastest runs of 32 points = 1 KiB).
-    for (int f = threadIdx.x; f < TX * TY * TZ * 2; f += NT) {
-        const int half = f & 1, p = f >> 1;
-        const int z = p % TZ, y = (p / TZ) % TY, x = p / (TZ * TY);
-        if (px0 + x >= a.ex || py0 + y >= a.ey || pz0 + z >= a.ez) continue;
-        const int ch0 = half ? 4 : 0;
-        const int nch = half ? 3 : 4;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (MODE == 0) {
-            // vertex (x, y, z) of the tile is shared by tile cells x..x+1, y..y+1, z..z+1
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (k < nch) {
-                    const float* s = sH[ch0 + k];
-                    float acc = 0.f;
-#pragma unroll
-                    for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-                        for (int dy = 0; dy < 2; ++dy) {
-                            const int base = ((x + dx) * CY + (y + dy)) * CZ + z;
-                            acc += s[base] + s[base + 1];
-                        }
-                    v[k] = acc * 0.125f;
-                }
+    const bool out_yz = py0 + ty < a.ey && pz0 + tz < a.ez;
+    const size_t out_yz_off = out_yz ? (size_t)wrapi(a.y0 + py0 + ty, a.n1) * a.n2 + wrapi(a.z0 + pz0 + tz, a.n2) : 0;
+    float prev[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // 2 x 2 centre sum of the previous plane
+    for (int c = c_first; c <= c_last; ++c) {
+        const int s0 = (c - c_first) % 3, s1 = (c - c_first + 1) % 3, s2 = (c - c_first + 2) % 3;
+        const float* P0 = ring[s0];   // plane c - 1
+        const float* P1 = ring[s1];   // plane c
+        const float* P2 = ring[s2];   // plane c + 1
+        float nxt[LP];
+        if (c < c_last) fetch(c + 2, nxt);   // the plane after next, while this one is processed
+
+        // second derivatives at the centres of plane c (differences of neighbours first)
+        float h[7];
+        for (int i = threadIdx.x; i < NC; i += NT) {
+            const int y = i / CZ, z = i % CZ;
+            const int o = (y + 1) * PZ + (z + 1);
+            const float p0 = P1[o];
+            h[0] = ((P0[o] - p0) + (P2[o] - p0)) * a.ih2;
+            h[1] = ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) * a.ih2;
+            h[2] = ((P1[o - 1] - p0) + (P1[o + 1] - p0)) * a.ih2;
+            h[3] = ((P2[o + PZ] - P2[o - PZ]) + (P0[o - PZ] - P0[o + PZ])) * a.iq;
+            h[4] = ((P2[o + 1] - P2[o - 1]) + (P0[o - 1] - P0[o + 1])) * a.iq;
+            h[5] = ((P1[o + PZ + 1] - P1[o + PZ - 1]) + (P1[o - PZ - 1] - P1[o - PZ + 1])) * a.iq;
+            if (a.delta) {
+                const int gx = wrapi(c, a.n0), gy = wrapi(cy0 + y, a.n1), gz = wrapi(cz0 + z, a.n2);
+                h[6] = __ldg(a.delta + ((size_t)gx * a.n1 + gy) * a.n2 + gz);
+            } else {
+                h[6] = (h[0] + h[1] + h[2]) * a.dinv;
             }
-        } else {
-            const int ci = (x * CY + y) * CZ + z;
+            if (MODE == 0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k < nch) v[k] = sH[ch0 + k][ci];
+                for (int q = 0; q < 7; ++q) sH[q][i] = h[q];
+            }
         }
-        const int gx = wrapi(a.x0 + px0 + x, a.n0), gy = wrapi(a.y0 + py0 + y, a.n1),
-                  gz = wrapi(a.z0 + pz0 + z, a.n2);
-        a.rec[2 * (((size_t)gx * a.n1 + gy) * a.n2 + gz) + half] = make_float4(v[0], v[1], v[2], v[3]);
+        if (MODE == 0) {
+            __syncthreads();
+            float b[7];
+            const int o = ty * CZ + tz;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) b[q] = (sH[q][o] + sH[q][o + 1]) + (sH[q][o + CZ] + sH[q][o + CZ + 1]);
+            if (c > c_first && out_yz) {
+                float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
+                r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
+                                   (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
+                r[1] = make_float4((prev[4] + b[4]) * 0.125f, (prev[5] + b[5]) * 0.125f,
+                                   (prev[6] + b[6]) * 0.125f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 7; ++q) prev[q] = b[q];
+        } else if (out_yz) {
+            float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
+            r[0] = make_float4(h[0], h[1], h[2], h[3]);
+            r[1] = make_float4(h[4], h[5], h[6], 0.f);
+        }
+        __syncthreads();   // every read of plane c - 1 (and of sH) is done
+        if (c < c_last) put(s0, nxt);
+        __syncthreads();
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // Transpose of the above: gradient records (16 floats per point: the hi and lo
@@ -255,7 +281,7 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
     a.ih2 = (float)(1.0 / (h * h));
     a.iq = (float)(0.25 / (h * h));
     a.dinv = (float)(1.0 / (1.5 * g.omega_m * kH0OverC * kH0OverC));
-    dim3 grid((a.ez + TZ - 1) / TZ, (a.ey + TY - 1) / TY, (a.ex + TX - 1) / TX);
+    dim3 grid((a.ez + TZ - 1) / TZ, (a.ey + TY - 1) / TY, (a.ex + XCHUNK - 1) / XCHUNK);
     if (where == RR_AT_VERTICES)
         tidal_kernel<0><<<grid, NT, 0, s>>>(a);
     else

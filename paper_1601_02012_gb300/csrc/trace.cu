@@ -297,216 +297,6 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_batch_kernel(const BatchArgs 
     }
 }
 
-// Transpose of line_cubic: given the weights J_N of the cubic's coefficients
-// e_{N-1} in the segment integral, the weight of each corner value q[m].
-__device__ __forceinline__ void line_cubic_adjoint(const float J[4], float u0, float u1, float u2, float v0,
-                                                   float v1, float v2, float W[8])
-{
-    const float E0 = J[0] * u2 + J[1] * v2;
-    const float E1 = J[1] * u2 + J[2] * v2;
-    const float E2 = J[2] * u2 + J[3] * v2;
-    const float M0[2] = {J[0] - E0, E0};
-    const float M1[2] = {J[1] - E1, E1};
-    const float M2[2] = {J[2] - E2, E2};
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-        const float C = fmaf(M0[kk], u1, M1[kk] * v1);
-        const float D = fmaf(M1[kk], u1, M2[kk] * v1);
-        const float A0 = M0[kk] - C, A1 = C;
-        const float B0 = M1[kk] - D, B1 = D;
-        // x-step for the pairs jk = 2 kk (j = 0) and 2 kk + 1 (j = 1)
-        const float d0 = fmaf(A0, u0, B0 * v0);
-        const float d1 = fmaf(A1, u0, B1 * v0);
-        W[4 * kk + 0] = A0 - d0;
-        W[4 * kk + 1] = d0;
-        W[4 * kk + 2] = A1 - d1;
-        W[4 * kk + 3] = d1;
-    }
-}
-
-// Rounding error of the FP32 sum old + x (TwoSum), per component.
-__device__ __forceinline__ float4 sum_error(float4 o, float4 x)
-{
-    float4 e;
-    float s, t;
-    two_sum(o.x, x.x, s, t); e.x = t;
-    two_sum(o.y, x.y, s, t); e.y = t;
-    two_sum(o.z, x.z, s, t); e.z = t;
-    two_sum(o.w, x.w, s, t); e.w = t;
-    return e;
-}
-
-// Add S * (gk w, gb) to the gradient record of point idx. A gradient record
-// is 16 floats: the FP32 running sums of the 8 channels (hi) and the exact
-// rounding errors of those sums (lo): the atomic add returns the value it
-// added to, TwoSum of (old, x) gives the error of that addition, and the
-// error is itself accumulated. hi + lo is then accurate even where thousands
-// of contributions of both signs cancel.
-__device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long idx, float S, float gk, float gb,
-                                           const float* w)
-{
-    if (S == 0.f) return;
-    const float a = gk * S;
-    const float4 x0 = make_float4(a * w[0], a * w[1], a * w[2], a * w[3]);
-    const float4 x1 = make_float4(a * w[4], a * w[5], gb * S, 0.f);
-    float4* p = grad + 4 * idx;
-    const float4 o0 = atomicAdd(p, x0);
-    const float4 o1 = atomicAdd(p + 1, x1);
-    atomicAdd(p + 2, sum_error(o0, x0));
-    atomicAdd(p + 3, sum_error(o1, x1));
-}
-
-// Adjoint of one step: replays the walk and, for every point the ray's
-// segments read (the 8 vertices of each cell, or its centre), accumulates
-// dI/dq of the segment integrals (the transpose of the forward map) while the
-// point stays in the ray's current cell; a point is flushed into the
-// gradient records once per residency, as gk * S * w (the six tidal channels
-// through Q_kappa = w . H) and gb * S (delta), with compensated 16-byte atomic
-// adds (flush_grad).
-template <int INTERP, class R>
-__global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A, const AdjArgs B, const TileCfg tc)
-{
-    constexpr bool F64 = sizeof(R) == 8;
-    int ix, iy;
-    tile_ray(tc, blockIdx.x, blockIdx.y, ix, iy);
-    if (ix >= A.nx || iy >= A.ny) return;
-    const long long rid = (long long)iy * A.nx + ix;
-    const float gk = B.dkappa ? (float)(B.dkappa[rid] * B.kscale) : 0.f;
-    const float gb = B.dkborn ? (float)(B.dkborn[rid] * B.bscale) : 0.f;
-    if (gk == 0.f && gb == 0.f) return;
-    const int nn[3] = {A.n0, A.n1, A.n2};
-    RayRange rg;
-    if (!ray_range(A, rid, rg)) return;
-    const R chis = (R)A.chi_s;
-    const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
-    const long long sx = (long long)A.n1 * A.n2, sy = A.n2;
-    const R eps_rel = F64 ? (R)1.4551915228366852e-11 : (R)4.76837158203125e-07;
-    const int nsub = F64 ? 1 : max(1, (int)ceilf(rg.Lf / A.sub_len));
-    const float dsub = rg.Lf / (float)nsub;
-    bool overflow = false;
-    for (int j = 0; j < nsub && !overflow; ++j) {
-    float bh, bl, Lj, D0j;
-    sub_step(rg, j, nsub, dsub, bh, bl, Lj, D0j);
-    Walk<R> W;
-    walk_setup<R>(A, rid, bh, bl, Lj, D0j, rg.hi, rg.lo, W);
-    int* c = W.c;
-    const int* sgn = W.sgn;
-    int* k = W.k;
-    int* vlo = W.vlo;
-    int* vhi = W.vhi;
-    const float* w = W.w;
-    const R L = W.L, chiA0 = W.chiA0, D0 = W.D0;
-    const R eps_end = L * eps_rel;
-
-    float S[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    R sig = 0;
-    R T[3] = {W.T0[0], W.T0[1], W.T0[2]};
-    int iter = 0;
-    while (true) {
-        R tend = T[0];
-        int e = 0;
-        if (T[1] < tend) { tend = T[1]; e = 1; }
-        if (T[2] < tend) { tend = T[2]; e = 2; }
-        const bool last = !(tend < L - eps_end);
-        if (last) tend = L;
-        const R t = tend - sig;
-        if (t > tend * eps_rel) {
-            R u[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) u[a] = fmin(fmax(fma(sig - T[a], W.v[a], W.cu[a]), (R)0), (R)1);
-            const R chiA = chiA0 - sig;
-            const R G0 = (D0 + sig) * chiA * ichis;
-            const R G1 = (2 * chiA - chis) * ichis;
-            const R G2 = -ichis;
-            const R t2 = t * t;
-            const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
-            if (INTERP == RR_TRILINEAR) {
-                const float J[4] = {(float)J1,
-                                    (float)(t2 * (G0 * (R)0.5 + t * (G1 * (R)(1.0 / 3.0) + t * G2 * (R)0.25))),
-                                    (float)(t2 * t * (G0 * (R)(1.0 / 3.0) + t * (G1 * (R)0.25 + t * G2 * (R)0.2))),
-                                    (float)(t2 * t2 * (G0 * (R)0.25 + t * (G1 * (R)0.2 + t * G2 * (R)(1.0 / 6.0))))};
-                float Wm[8];
-                line_cubic_adjoint(J, (float)u[0], (float)u[1], (float)u[2], (float)W.v[0], (float)W.v[1],
-                                   (float)W.v[2], Wm);
-#pragma unroll
-                for (int m = 0; m < 8; ++m) S[m] += Wm[m];
-            } else {
-                S[0] += (float)J1;
-            }
-        }
-        sig = tend;
-        if (last) break;
-
-        int nvhi = 0, ncell = 0, ne = 1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (a == e) {
-                nvhi = wrap_once(vhi[a] + sgn[a], nn[a]);
-                ncell = c[a] + sgn[a];
-                ne = nn[a];
-            }
-        if (INTERP == RR_TRILINEAR) {
-            // the 4 corners on the entry face along e leave the ray's cell
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int pb = r & 1, qb2 = r >> 1;
-                const int m = e == 0 ? 2 * r : (e == 1 ? pb + 4 * qb2 : r);
-                const int gx = e == 0 ? vlo[0] : (pb ? vhi[0] : vlo[0]);
-                const int gy = e == 1 ? vlo[1] : (e == 0 ? (pb ? vhi[1] : vlo[1]) : (qb2 ? vhi[1] : vlo[1]));
-                const int gz = e == 2 ? vlo[2] : (qb2 ? vhi[2] : vlo[2]);
-                float Sm = 0.f;
-#pragma unroll
-                for (int mm = 0; mm < 8; ++mm)
-                    if (mm == m) Sm = S[mm];
-                flush_grad(B.grad, gx * sx + gy * sy + gz, Sm, gk, gb, w);
-            }
-            if (e == 0) {
-                S[0] = S[1]; S[2] = S[3]; S[4] = S[5]; S[6] = S[7];
-                S[1] = 0.f; S[3] = 0.f; S[5] = 0.f; S[7] = 0.f;
-            } else if (e == 1) {
-                S[0] = S[2]; S[1] = S[3]; S[4] = S[6]; S[5] = S[7];
-                S[2] = 0.f; S[3] = 0.f; S[6] = 0.f; S[7] = 0.f;
-            } else {
-                S[0] = S[4]; S[1] = S[5]; S[2] = S[6]; S[3] = S[7];
-                S[4] = 0.f; S[5] = 0.f; S[6] = 0.f; S[7] = 0.f;
-            }
-        } else {
-            flush_grad(B.grad, c[0] * sx + c[1] * sy + c[2], S[0], gk, gb, w);
-            S[0] = 0.f;
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (a == e) {
-                c[a] = wrap_once(ncell, nn[a]);
-                vlo[a] = vhi[a];
-                vhi[a] = nvhi;
-                k[a] += 1;
-                T[a] = fma((R)k[a], W.td[a], W.T0[a]);
-            }
-        // the ray left the box (no wrap): the corners still pending are
-        // flushed below
-        if (!A.periodic && (ncell < 0 || ncell >= ne)) break;
-        if (++iter > W.max_iter) {
-            overflow = true;
-            break;
-        }
-    }
-    // flush everything still pending
-    if (INTERP == RR_TRILINEAR) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int gx = (m & 1) ? vhi[0] : vlo[0];
-            const int gy = (m & 2) ? vhi[1] : vlo[1];
-            const int gz = (m & 4) ? vhi[2] : vlo[2];
-            flush_grad(B.grad, gx * sx + gy * sy + gz, S[m], gk, gb, w);
-        }
-    } else {
-        flush_grad(B.grad, c[0] * sx + c[1] * sy + c[2], S[0], gk, gb, w);
-    }
-    }
-    if (overflow) atomicOr(A.err, kErrStepLimit);
-}
-
 }  // namespace
 
 dim3 tile_grid(const TileCfg& t, int nx, int ny)
@@ -578,25 +368,3 @@ int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t)
 }
 }  // namespace rr
 
-namespace rr {
-
-cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s)
-{
-    const TileCfg t{};
-    const dim3 grid = tile_grid(t, a.nx, a.ny);
-    const int nt = 32 * t.bwx * t.bwy;
-    if (interp == RR_TRILINEAR) {
-        if (fp64_dda)
-            trace_adjoint_kernel<RR_TRILINEAR, double><<<grid, nt, 0, s>>>(a, b, t);
-        else
-            trace_adjoint_kernel<RR_TRILINEAR, float><<<grid, nt, 0, s>>>(a, b, t);
-    } else {
-        if (fp64_dda)
-            trace_adjoint_kernel<RR_NGP, double><<<grid, nt, 0, s>>>(a, b, t);
-        else
-            trace_adjoint_kernel<RR_NGP, float><<<grid, nt, 0, s>>>(a, b, t);
-    }
-    return cudaGetLastError();
-}
-
-}  // namespace rr
