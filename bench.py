@@ -40,9 +40,11 @@ UNIT = "cell-segments/s"
 BYTES_PER_SEGMENT = 256
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM traffic of one trace launch from an ncu capture, valid only for the
-# kernel source it was taken on (sha256 of csrc/trace.cu + csrc/walk.cuh).
-TRACE_TRAFFIC = {}
+# DRAM bytes (read + write) of one production trace launch from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), valid
+# only for the kernel source it was taken on (sha256 of csrc/trace.cu +
+# csrc/walk.cuh).
+TRACE_TRAFFIC = {"d70576c606850ba8": 275_722_880}
 
 
 def _src_hash(*names):
@@ -733,7 +735,10 @@ def main():
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "kernel": "trace_kernel<trilinear,float>",
             "note": f"logical gather bytes: {BYTES_PER_SEGMENT} B per segment (8 vertex records) "
-                    f"x segments per launch / mean launch time; peak of {peak_kind} copy bandwidth",
+                    f"x segments per launch / mean launch time; peak of {peak_kind} copy bandwidth; "
+                    "traffic: DRAM bytes read + written per launch (ncu, production workload), "
+                    "null when the kernel source differs from the captured one",
+            "algorithmic_bytes_per_launch": segs * BYTES_PER_SEGMENT / nst,
         },
         "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps,
                                 "tidal_points_per_step": tidal_points},
@@ -781,6 +786,27 @@ def main():
             "kborn_max_over_rms": float(np.abs(kbg[allr] - kbo).max() / rmsb),
             "segments_per_ray_gpu": segs / w.bundle.nrays,
             "segments_per_ray_oracle": float(np.concatenate([res.nseg, res2.nseg]).mean()),
+        }
+        # map statistics: a contiguous patch of the map (its centre quarter per
+        # side) traced by the oracle through all steps, P(ell) and PDF vs the GPU's
+        from paper_1601_02012_gb300 import mapstats
+        px = min(512, w.bundle.nx)
+        py = min(512, w.bundle.ny)
+        x0, y0 = (w.bundle.nx - px) // 2, (w.bundle.ny - py) // 2
+        iy, ix = np.meshgrid(np.arange(y0, y0 + py), np.arange(x0, x0 + px), indexing="ij")
+        prids = (iy * w.bundle.nx + ix).ravel()
+        t0 = time.perf_counter()
+        pres, _ = _oracle_sample(w.bundle, w.grid, H, d, steps, prids, threads)
+        dtp = time.perf_counter() - t0
+        fx = w.bundle.fov_x * (px - 1) / max(w.bundle.nx - 1, 1)
+        fy = w.bundle.fov_y * (py - 1) / max(w.bundle.ny - 1, 1)
+        line["map_statistics"] = {
+            "patch": f"{px}x{py} rays at the map centre ({fx * 180 / math.pi:.3f} x {fy * 180 / math.pi:.3f} deg), "
+                     f"all {nst} steps, oracle {dtp:.1f} s",
+            "kappa": mapstats.compare(kg[prids].reshape(py, px), pres.kappa.reshape(py, px), fx, fy),
+            "kborn": mapstats.compare(kbg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
+            "definition": "P(ell): 20 log bins of ell = 2 pi m / Upsilon, largest relative bin difference; "
+                          "PDF: 100 bins over +-5 sigma of the oracle map, L1 distance",
         }
     print(json.dumps(line), flush=True)
     if dist is not None:

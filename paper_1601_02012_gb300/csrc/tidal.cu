@@ -11,6 +11,8 @@
 // current one is processed. HBM traffic per point: the potential read about
 // 1.4 times (halo re-reads of neighbouring columns hit L2) and the 32-byte
 // record written once, as 1 KiB runs per warp: 36 algorithmic bytes per point.
+#include <algorithm>
+
 #include "rr_internal.h"
 
 namespace rr {
@@ -18,7 +20,7 @@ namespace {
 
 constexpr int TY = 8, TZ = 32;       // output points per CTA and plane
 constexpr int NT = TY * TZ;          // one thread per output point
-constexpr int XCHUNK = 32;           // planes per CTA
+constexpr int XCHUNK_MAX = 32;       // planes per CTA, at most
 
 struct TidalArgs {
     const float* phi;
@@ -30,6 +32,7 @@ struct TidalArgs {
     float ih2;        // 1/h^2
     float iq;         // 1/(4 h^2)
     float dinv;       // 1 / (1.5 Omega_m (H0/c)^2)
+    int xchunk;       // planes per CTA
 };
 
 // i mod n; the integer division only runs for indices outside [0, n) (halo
@@ -51,11 +54,12 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
     constexpr int NP = PY * PZ, NC = CY * CZ;
     constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane
     __shared__ float ring[3][NP];
-    __shared__ float sH[MODE == 0 ? 7 : 1][MODE == 0 ? NC : 1];
+    constexpr int HC = MODE == 0 ? 7 : 1, HN = MODE == 0 ? NC : 1;
+    __shared__ float sH[HC][HN];   // centre values of the current plane (vertices only)
 
     const int ty = threadIdx.x / TZ, tz = threadIdx.x % TZ;
     const int py0 = blockIdx.y * TY, pz0 = blockIdx.x * TZ;            // box-relative
-    const int xb = blockIdx.z * XCHUNK, xe = min(xb + XCHUNK, a.ex);   // output planes [xb, xe)
+    const int xb = blockIdx.z * a.xchunk, xe = min(xb + a.xchunk, a.ex);   // output planes [xb, xe)
     const int cy0 = a.y0 + py0 - V, cz0 = a.z0 + pz0 - V;              // first centre of the column
     const int c_first = a.x0 + xb - V, c_last = a.x0 + xe - 1;         // centre planes (global, unwrapped)
 
@@ -116,17 +120,20 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
             } else {
                 h[6] = (h[0] + h[1] + h[2]) * a.dinv;
             }
-            if (MODE == 0) {
+            if constexpr (MODE == 0) {
 #pragma unroll
                 for (int q = 0; q < 7; ++q) sH[q][i] = h[q];
             }
         }
-        if (MODE == 0) {
-            __syncthreads();
+        // every read of plane c - 1 is done (and, for vertices, plane c's centres are in sH)
+        __syncthreads();
+        if (c < c_last) put(s0, nxt);
+        if constexpr (MODE == 0) {
+            const float (*H)[HN] = sH;
             float b[7];
             const int o = ty * CZ + tz;
 #pragma unroll
-            for (int q = 0; q < 7; ++q) b[q] = (sH[q][o] + sH[q][o + 1]) + (sH[q][o + CZ] + sH[q][o + CZ + 1]);
+            for (int q = 0; q < 7; ++q) b[q] = (H[q][o] + H[q][o + 1]) + (H[q][o + CZ] + H[q][o + CZ + 1]);
             if (c > c_first && out_yz) {
                 float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
                 r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
@@ -141,9 +148,7 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
             r[0] = make_float4(h[0], h[1], h[2], h[3]);
             r[1] = make_float4(h[4], h[5], h[6], 0.f);
         }
-        __syncthreads();   // every read of plane c - 1 (and of sH) is done
-        if (c < c_last) put(s0, nxt);
-        __syncthreads();
+        __syncthreads();   // plane c + 2 is in the ring and every read of sH is done
     }
 }
 
@@ -281,7 +286,18 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
     a.ih2 = (float)(1.0 / (h * h));
     a.iq = (float)(0.25 / (h * h));
     a.dinv = (float)(1.0 / (1.5 * g.omega_m * kH0OverC * kH0OverC));
-    dim3 grid((a.ez + TZ - 1) / TZ, (a.ey + TY - 1) / TY, (a.ex + XCHUNK - 1) / XCHUNK);
+    // planes per CTA: long marches on big boxes; short ones when the box has
+    // few y-z tiles, so that every SM still gets a couple of CTAs
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 152;
+    }
+    const long long tiles_yz = (long long)((a.ez + TZ - 1) / TZ) * ((a.ey + TY - 1) / TY);
+    const long long want = (long long)a.ex * tiles_yz / (2LL * nsm);
+    a.xchunk = (int)std::max(2LL, std::min((long long)XCHUNK_MAX, want));
+    dim3 grid((a.ez + TZ - 1) / TZ, (a.ey + TY - 1) / TY, (a.ex + a.xchunk - 1) / a.xchunk);
     if (where == RR_AT_VERTICES)
         tidal_kernel<0><<<grid, NT, 0, s>>>(a);
     else

@@ -59,45 +59,75 @@ __device__ __forceinline__ float4 sum_error(float4 o, float4 x)
 // Neighbouring rays of a warp are far closer together than a cell, so they
 // usually cross the same faces in the same iteration and flush the same
 // point together. When all 32 lanes flush one point, their contributions are
-// summed across the warp first (compensated: TwoSum at every butterfly step,
-// the errors carried alongside) and one lane issues the atomics; otherwise
-// every lane adds its own.
+// summed across the warp first by a reduce-scatter butterfly (each of the
+// first three exchanges halves the channels a lane keeps: 4 + 2 + 1 + 1 + 1
+// shuffles instead of 5 per channel), compensated (TwoSum at every addition,
+// the errors carried alongside), after which lane 4c holds the total of
+// channel c and adds it with scalar atomics; otherwise every lane adds its own.
+__device__ __forceinline__ void warp_pair_add(float& x, float& e, float ox, float oe)
+{
+    float sum, err;
+    two_sum(x, ox, sum, err);
+    x = sum;
+    e += oe + err;
+}
+
 __device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long idx, float S, float gk, float gb,
                                            const float* w)
 {
     const float a = gk * S;
-    float x[7] = {a * w[0], a * w[1], a * w[2], a * w[3], a * w[4], a * w[5], gb * S};
-    float e[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const unsigned active = __activemask();
-    bool leader = true;
     if (active == 0xffffffffu && __match_any_sync(active, idx) == active) {
+        constexpr unsigned FULL = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        float x[8] = {a * w[0], a * w[1], a * w[2], a * w[3], a * w[4], a * w[5], gb * S, 0.f};
+        float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // xor 16: keep channels 4 b4 .. 4 b4 + 3
+        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+        float k4[4], f4[4];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-            for (int c = 0; c < 7; ++c) {
-                const float ox = __shfl_xor_sync(0xffffffffu, x[c], off);
-                const float oe = __shfl_xor_sync(0xffffffffu, e[c], off);
-                float sum, err;
-                two_sum(x[c], ox, sum, err);
-                x[c] = sum;
-                e[c] += oe + err;
-            }
+        for (int i = 0; i < 4; ++i) {
+            const float sx = b4 ? x[i] : x[4 + i], se = b4 ? e[i] : e[4 + i];
+            k4[i] = b4 ? x[4 + i] : x[i];
+            f4[i] = b4 ? e[4 + i] : e[i];
+            warp_pair_add(k4[i], f4[i], __shfl_xor_sync(FULL, sx, 16), __shfl_xor_sync(FULL, se, 16));
         }
-        leader = (threadIdx.x & 31) == 0;
-    }
-    if (!leader) return;
-    if (x[0] == 0.f && x[1] == 0.f && x[2] == 0.f && x[3] == 0.f && x[4] == 0.f && x[5] == 0.f && x[6] == 0.f)
+        // xor 8: keep 2 of the 4
+        float k2[2], f2[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float sx = b3 ? k4[i] : k4[2 + i], se = b3 ? f4[i] : f4[2 + i];
+            k2[i] = b3 ? k4[2 + i] : k4[i];
+            f2[i] = b3 ? f4[2 + i] : f4[i];
+            warp_pair_add(k2[i], f2[i], __shfl_xor_sync(FULL, sx, 8), __shfl_xor_sync(FULL, se, 8));
+        }
+        // xor 4: keep 1 of the 2
+        float v = b2 ? k2[1] : k2[0], ve = b2 ? f2[1] : f2[0];
+        {
+            const float sx = b2 ? k2[0] : k2[1], se = b2 ? f2[0] : f2[1];
+            warp_pair_add(v, ve, __shfl_xor_sync(FULL, sx, 4), __shfl_xor_sync(FULL, se, 4));
+        }
+        // xor 2, xor 1: the whole warp's total of channel (lane >> 2)
+        warp_pair_add(v, ve, __shfl_xor_sync(FULL, v, 2), __shfl_xor_sync(FULL, ve, 2));
+        warp_pair_add(v, ve, __shfl_xor_sync(FULL, v, 1), __shfl_xor_sync(FULL, ve, 1));
+        const int ch = lane >> 2;
+        if ((lane & 3) == 0 && ch < 7 && v != 0.f) {
+            float* p = reinterpret_cast<float*>(grad + 4 * idx);
+            const float old = atomicAdd(p + ch, v);
+            float sum, err;
+            two_sum(old, v, sum, err);
+            atomicAdd(p + 8 + ch, err + ve);
+        }
         return;
-    const float4 x0 = make_float4(x[0], x[1], x[2], x[3]);
-    const float4 x1 = make_float4(x[4], x[5], x[6], 0.f);
+    }
+    if (S == 0.f) return;
+    const float4 x0 = make_float4(a * w[0], a * w[1], a * w[2], a * w[3]);
+    const float4 x1 = make_float4(a * w[4], a * w[5], gb * S, 0.f);
     float4* p = grad + 4 * idx;
     const float4 o0 = atomicAdd(p, x0);
     const float4 o1 = atomicAdd(p + 1, x1);
-    float4 r0 = sum_error(o0, x0), r1 = sum_error(o1, x1);
-    r0.x += e[0]; r0.y += e[1]; r0.z += e[2]; r0.w += e[3];
-    r1.x += e[4]; r1.y += e[5]; r1.z += e[6];
-    atomicAdd(p + 2, r0);
-    atomicAdd(p + 3, r1);
+    atomicAdd(p + 2, sum_error(o0, x0));
+    atomicAdd(p + 3, sum_error(o1, x1));
 }
 
 // Adjoint of one step: replays the walk and, for every point the ray's

@@ -123,6 +123,12 @@ def test_small_64_workload(rrpkg, oracle_lib, interp, fp64_dda):
     assert_map(k, o.kappa)
     assert_map(kb, o.kborn, what="kborn")
     assert abs(nseg - int(o.nseg.sum())) <= 1e-4 * o.nseg.sum()
+    # the map statistics: P(ell) bins and the one-point PDF
+    from paper_1601_02012_gb300 import mapstats
+    shape = (w.bundle.ny, w.bundle.nx)
+    for got, want in ((k, o.kappa), (kb, o.kborn)):
+        st = mapstats.compare(got.reshape(shape), want.reshape(shape), w.bundle.fov_x, w.bundle.fov_y)
+        assert st["pl_max_rel"] <= 1e-4 and st["pdf_l1"] <= 1e-3, st
 
 
 @pytest.mark.parametrize("interp", [1, 0])
