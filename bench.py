@@ -40,11 +40,11 @@ UNIT = "cell-segments/s"
 BYTES_PER_SEGMENT = 256
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) of one production trace launch from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), valid
-# only for the kernel source it was taken on (sha256 of csrc/trace.cu +
-# csrc/walk.cuh).
-TRACE_TRAFFIC = {"d70576c606850ba8": 275_722_880}
+# DRAM bytes (read + write) of one trace launch from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), per
+# (kernel source, workload): valid only for the source it was taken on (sha256
+# of csrc/trace.cu + csrc/walk.cuh) and for that workload.
+TRACE_TRAFFIC = {("d70576c606850ba8", "prod_512"): 275_722_880}
 
 
 def _src_hash(*names):
@@ -720,7 +720,7 @@ def main():
     achieved = segs * BYTES_PER_SEGMENT / per_pass_trace_s / 1e9
     tidal_points = sum((b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]) for b in bboxes)
     h = _src_hash("trace.cu", "walk.cuh")
-    traffic = TRACE_TRAFFIC.get(h)
+    traffic = TRACE_TRAFFIC.get((h, w.name))
     value = segs_all * args.steps / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -807,6 +807,20 @@ def main():
             "kborn": mapstats.compare(kbg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
             "definition": "P(ell): 20 log bins of ell = 2 pi m / Upsilon, largest relative bin difference; "
                           "PDF: 100 bins over +-5 sigma of the oracle map, L1 distance",
+        }
+        # the same statistics for the FP32 walk without compensated sums (one pass)
+        trp = rrp.Tracer(w.bundle, plain_sums=True)
+        with torch.cuda.stream(stream):
+            for i, st in enumerate(steps):
+                rrp.rr_tidal_tensor(gd, phi, None, rec, trp.where, bboxes[i], stream)
+                rrp.rr_trace_step(trp.ctx, gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            kp, kbp = trp.finalize(stream=stream)
+        trp.close()
+        kpg, kbpg = kp.cpu().numpy().ravel(), kbp.cpu().numpy().ravel()
+        line["map_statistics"]["plain_fp32_sums"] = {
+            "kappa": mapstats.compare(kpg[prids].reshape(py, px), pres.kappa.reshape(py, px), fx, fy),
+            "kborn": mapstats.compare(kbpg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
+            "note": "the same pass with uncompensated FP32 sums within and across steps (RR_PLAIN_SUMS)",
         }
     print(json.dumps(line), flush=True)
     if dist is not None:

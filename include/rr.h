@@ -49,9 +49,13 @@ enum { RR_NGP = 0,          /* constant centre value, Eq. (Icngp) / (Iclensing_n
 
 /* rr_bundle_desc.flags */
 enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box faces */
-       RR_FP64_DDA = 2 };   /* plain form: cell walk, kernel integrals and per-step
+       RR_FP64_DDA = 2,     /* plain form: cell walk, kernel integrals and per-step
                                sums in FP64 (default: FP32 walk in cell-local
                                coordinates with compensated FP32 sums) */
+       RR_PLAIN_SUMS = 4 }; /* the FP32 walk with uncompensated FP32 sums, within and
+                               across steps: only to measure what the compensation
+                               buys (rr_create / rr_trace_step only; not with
+                               RR_FP64_DDA, batches, AMR or the no-allocation call) */
 
 /* rr_tidal_tensor: where the records are evaluated. */
 enum { RR_AT_VERTICES = 0,  /* mean of the 8 cells sharing each vertex (Sec. 2.7); trilinear */
@@ -72,7 +76,7 @@ typedef struct {
     double obs[3];        /* observer position in box coordinates, Mpc/h */
     double chi_s;         /* comoving distance of the sources, > 0 */
     int32_t interp;       /* RR_NGP or RR_TRILINEAR */
-    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA */
+    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS */
 } rr_bundle_desc;
 
 /* A uniform grid of n[0] x n[1] x n[2] cubic cells of size h = box / n[0]. */

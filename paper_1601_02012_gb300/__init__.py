@@ -44,13 +44,14 @@ class Tracer:
     """One ray bundle's device state (an rr_ctx) plus the calls that advance it.
 
     bundle: object with nx, ny, fov_x, fov_y (radians), obs (3), chi_s, interp
-    (0 NGP / 1 trilinear) and periodic attributes.
+    (0 NGP / 1 trilinear) and periodic attributes. fp64_dda: the plain FP64
+    walk; plain_sums: the FP32 walk without compensated sums (for comparison).
     """
 
-    def __init__(self, bundle, fp64_dda: bool = False):
+    def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False):
         _rr.load()
         self.bundle = bundle
-        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda)
+        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums)
         self.ctx = rr_create(self.desc)
         self.where = RR_AT_VERTICES if int(self.desc.interp) == RR_TRILINEAR else RR_AT_CENTRES
 

@@ -30,6 +30,7 @@ RR_NGP = 0
 RR_TRILINEAR = 1
 RR_PERIODIC = 1
 RR_FP64_DDA = 2
+RR_PLAIN_SUMS = 4
 RR_AT_VERTICES = 0
 RR_AT_CENTRES = 1
 
@@ -135,7 +136,7 @@ def _stream(s):
     return C.c_void_p(s.cuda_stream)
 
 
-def bundle_desc(b, fp64_dda: bool = False) -> rr_bundle_desc:
+def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False) -> rr_bundle_desc:
     """rr_bundle_desc from any object with nx, ny, fov_x, fov_y, obs, chi_s,
     interp and periodic attributes."""
     d = rr_bundle_desc()
@@ -148,6 +149,8 @@ def bundle_desc(b, fp64_dda: bool = False) -> rr_bundle_desc:
     flags = RR_PERIODIC if getattr(b, "periodic", True) else 0
     if fp64_dda:
         flags |= RR_FP64_DDA
+    if plain_sums:
+        flags |= RR_PLAIN_SUMS
     d.flags = flags
     return d
 

@@ -27,7 +27,8 @@ rr_status check_bundle(const rr_bundle_desc* b)
         if (!is_finite(b->obs[a])) return RR_ERR_ARG;
     if (!is_finite(b->chi_s) || !(b->chi_s > 0)) return RR_ERR_ARG;
     if (b->interp != RR_NGP && b->interp != RR_TRILINEAR) return RR_ERR_ARG;
-    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA)) return RR_ERR_ARG;
+    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS)) return RR_ERR_ARG;
+    if ((b->flags & RR_PLAIN_SUMS) && (b->flags & RR_FP64_DDA)) return RR_ERR_ARG;
     return RR_OK;
 }
 
@@ -269,7 +270,8 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     if (st != RR_OK) return st;
     const rr_bundle_desc& b = ctx->bundle;
     TraceArgs a = make_trace_args(ctx, grid, rec, chi_a, chi_b, scale, a_step);
-    cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream);
+    cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{},
+                                 (b.flags & RR_PLAIN_SUMS) != 0);
     if (e != cudaSuccess) return from_cuda(e);
     ctx->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
     return RR_OK;

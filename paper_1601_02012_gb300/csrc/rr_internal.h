@@ -105,7 +105,8 @@ cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4*
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
-cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t);
+cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
+                         bool plain_sums = false);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
 int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
 dim3 tile_grid(const TileCfg& t, int nx, int ny);

@@ -34,8 +34,9 @@ namespace rr {
 namespace {
 
 // One ray over one step. INTERP: RR_NGP or RR_TRILINEAR. R: float
-// (compensated FP32 walk) or double (plain FP64 walk).
-template <int INTERP, class R>
+// (compensated FP32 walk) or double (plain FP64 walk). PLAIN (FP32 only):
+// uncompensated FP32 sums within and across steps, for comparison.
+template <int INTERP, class R, bool PLAIN = false>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
     constexpr bool F64 = sizeof(R) == 8;
@@ -172,13 +173,16 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                     x = __ffma2_rn(e2[1], bc2(J2), x);
                     x = __ffma2_rn(e2[2], bc2(J3), x);
                     x = __ffma2_rn(e2[3], bc2(J4), x);
-                    s2.add(x);
+                    if constexpr (PLAIN) s2.s = __fadd2_rn(s2.s, x);
+                    else s2.add(x);
                 }
             } else {
                 const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
                 if constexpr (F64) {
                     sk.add((R)q2[0].x * J1);
                     sb.add((R)q2[0].y * J1);
+                } else if constexpr (PLAIN) {
+                    s2.s = __ffma2_rn(q2[0], bc2(J1), s2.s);
                 } else {
                     s2.add(__fmul2_rn(q2[0], bc2(J1)));
                 }
@@ -233,6 +237,13 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     }
     if (overflow) atomicOr(A.err, kErrStepLimit);
     if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
+    if constexpr (PLAIN) {
+        // plain FP32 across steps too: the high word only
+        A.kacc[rid] = make_float2(fmaf(sk.s, A.sch, A.kacc[rid].x), 0.f);
+        A.bacc[rid] = make_float2(fmaf(sb.s, A.bsh, A.bacc[rid].x), 0.f);
+        A.nseg[rid] += cnt;
+        return;
+    }
     float kh, kl, bh, bl;
     sk.pair(kh, kl);
     sb.pair(bh, bl);
@@ -242,12 +253,12 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 }
 
 
-template <int INTERP, class R>
+template <int INTERP, class R, bool PLAIN = false>
 __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, const TileCfg t)
 {
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
-    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R>(A, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, PLAIN>(A, ix, iy);
 }
 
 // Persistent work queue over the ray tiles of many bundles (lightcones): each
@@ -311,11 +322,17 @@ bool tile_ok(const TileCfg& t)
            t.bwy >= 1 && t.bwx * t.bwy * 32 <= NT_MAX;
 }
 
-cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t)
+cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
+                         bool plain_sums)
 {
     if (!tile_ok(t)) return cudaErrorInvalidValue;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const int nt = 32 * t.bwx * t.bwy;
+    if (plain_sums && !fp64_dda) {
+        if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, true><<<grid, nt, 0, s>>>(a, t);
+        else trace_kernel<RR_NGP, float, true><<<grid, nt, 0, s>>>(a, t);
+        return cudaGetLastError();
+    }
     if (interp == RR_TRILINEAR) {
         if (fp64_dda)
             trace_kernel<RR_TRILINEAR, double><<<grid, nt, 0, s>>>(a, t);

@@ -232,3 +232,30 @@ def test_prod_512_sampled(rrpkg, oracle_lib):
     assert np.abs(kb[rids] - o.kborn).max() <= TOL * rmsb
     mean_seg = nseg / w.bundle.nrays
     assert abs(mean_seg - o.nseg.mean()) <= 0.02 * o.nseg.mean()
+
+
+def test_plain_sums_form(rrpkg, oracle_lib):
+    """RR_PLAIN_SUMS (the FP32 walk with uncompensated sums, a comparison form)
+    traces the same segments; its maps stay close to the oracle's, and the
+    compensated default is at least as close on a long one-step cone."""
+    import torch
+    g = synth.Grid((64, 64, 64), 64.0)
+    b = synth.Bundle(48, 40, synth.deg(12), synth.deg(10), (32.0, 32.0, 0.0), 600.0)
+    phi = synth.grf_phi(64, 64.0, 21)
+    steps = [synth.Step(600.0, 0.0, 1.0, 1.0)]
+    o = run_oracle(oracle_lib, phi, g, b, steps)
+    ph = torch.from_numpy(np.ascontiguousarray(phi, np.float32)).cuda()
+    errs = {}
+    for plain in (False, True):
+        tr = rrpkg.Tracer(b, plain_sums=plain)
+        rec = rrpkg.record_buffer(g)
+        tr.tidal(g, ph, rec)
+        tr.step(g, rec, 600.0, 0.0)
+        k, kb = tr.finalize()
+        errs[plain] = (map_errors(k.cpu().numpy(), o.kappa)[0], map_errors(kb.cpu().numpy(), o.kborn)[0],
+                       tr.segments())
+        tr.close()
+    assert errs[False][2] == errs[True][2]
+    assert errs[False][0] <= TOL and errs[False][1] <= TOL
+    assert errs[True][0] <= 1e-3 and errs[True][1] <= 1e-3
+    assert errs[False][0] <= errs[True][0] * 1.01 + 1e-7
