@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), per
 # (kernel source, workload): valid only for the source it was taken on (sha256
 # of csrc/trace.cu + csrc/walk.cuh) and for that workload.
-TRACE_TRAFFIC = {("d70576c606850ba8", "prod_512"): 275_722_880}
+TRACE_TRAFFIC = {("85bb554c18edd692", "prod_512"): 275_786_880}
 
 
 def _src_hash(*names):
