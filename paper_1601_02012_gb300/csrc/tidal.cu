@@ -1,16 +1,18 @@
 // Tidal tensor and vertex records (Sec. 3.3, Eq. tidalexample; Sec. 2.7).
 //
-// One CTA owns a TY x TZ column of output points (z fastest, one warp per
-// z-row) and marches along x through a chunk of planes. Per plane it keeps
-// three planes of the potential (with a two-cell halo in y and z) in a shared
-// ring, evaluates the six central-difference second derivatives at the cell
-// centres of the current plane, and for records at vertices adds the 2 x 2
-// centres around each vertex in that plane; a vertex's record is the mean of
-// that sum and the previous plane's (kept in registers), i.e. of the 8 cells
-// around it. The next potential plane is loaded into registers while the
-// current one is processed. HBM traffic per point: the potential read about
-// 1.4 times (halo re-reads of neighbouring columns hit L2) and the 32-byte
-// record written once, as 1 KiB runs per warp: 36 algorithmic bytes per point.
+// One CTA of 8 warps owns an 8 (y) x 32 (z) block of cell centres, one warp
+// per z-row, one thread per centre, and marches along x through a chunk of
+// planes. Per plane it keeps three planes of the potential (with a one-cell
+// halo) in a shared ring, and every thread evaluates the six central-difference
+// second derivatives at its own centre. For records at vertices, vertex (y, z)
+// of the plane is the upper corner of centres (y-1..y, z-1..z): the z pair is
+// summed with a warp shuffle, the y pair through shared memory, and the
+// record is the mean of that 2 x 2 sum and the previous plane's (kept in
+// registers) -- the 8 cells around the vertex. The first centre row and column
+// of the block are the halo of its 7 x 31 vertices. The next potential plane is
+// loaded into registers while the current one is processed. HBM traffic per
+// point: the potential read about 1.5 times (halo re-reads hit L2) and the
+// 32-byte record written once: 36 algorithmic bytes per point.
 #include <algorithm>
 
 #include "rr_internal.h"
@@ -18,8 +20,8 @@
 namespace rr {
 namespace {
 
-constexpr int TY = 8, TZ = 32;       // output points per CTA and plane
-constexpr int NT = TY * TZ;          // one thread per output point
+constexpr int TY = 8, TZ = 32;       // centres per CTA and plane
+constexpr int NT = TY * TZ;          // one thread per centre
 constexpr int XCHUNK_MAX = 32;       // planes per CTA, at most
 
 struct TidalArgs {
@@ -44,24 +46,24 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return r < 0 ? r + n : r;
 }
 
-// MODE 0: records at vertices; MODE 1: records at centres.
+// MODE 0: records at vertices (7 x 31 per CTA and plane); MODE 1: records at
+// centres (8 x 32).
 template <int MODE>
 __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
 {
-    constexpr int V = (MODE == 0) ? 1 : 0;           // extra centre row below each output row
-    constexpr int CY = TY + V, CZ = TZ + V;          // centres per plane
-    constexpr int PY = CY + 2, PZ = CZ + 2;          // potential per plane (halo 1 around the centres)
-    constexpr int NP = PY * PZ, NC = CY * CZ;
+    constexpr int V = (MODE == 0) ? 1 : 0;
+    constexpr int OY = TY - V, OZ = TZ - V;          // output points per CTA and plane
+    constexpr int PY = TY + 2, PZ = TZ + 2;          // potential per plane (halo 1 around the centres)
+    constexpr int NP = PY * PZ;
     constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane
     __shared__ float ring[3][NP];
-    constexpr int HC = MODE == 0 ? 7 : 1, HN = MODE == 0 ? NC : 1;
-    __shared__ float sH[HC][HN];   // centre values of the current plane (vertices only)
+    __shared__ float sP[MODE == 0 ? 7 : 1][MODE == 0 ? NT : 1];   // z-pair sums of every centre
 
     const int ty = threadIdx.x / TZ, tz = threadIdx.x % TZ;
-    const int py0 = blockIdx.y * TY, pz0 = blockIdx.x * TZ;            // box-relative
+    const int py0 = blockIdx.y * OY, pz0 = blockIdx.x * OZ;               // box-relative first output
     const int xb = blockIdx.z * a.xchunk, xe = min(xb + a.xchunk, a.ex);   // output planes [xb, xe)
-    const int cy0 = a.y0 + py0 - V, cz0 = a.z0 + pz0 - V;              // first centre of the column
-    const int c_first = a.x0 + xb - V, c_last = a.x0 + xe - 1;         // centre planes (global, unwrapped)
+    const int cy0 = a.y0 + py0 - V, cz0 = a.z0 + pz0 - V;                 // centre (0, 0) of the block
+    const int c_first = a.x0 + xb - V, c_last = a.x0 + xe - 1;            // centre planes (unwrapped)
 
     // potential plane gx into registers / into a ring slot
     int poff[LP];
@@ -91,8 +93,11 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
     }
     __syncthreads();
 
-    const bool out_yz = py0 + ty < a.ey && pz0 + tz < a.ez;
-    const size_t out_yz_off = out_yz ? (size_t)wrapi(a.y0 + py0 + ty, a.n1) * a.n2 + wrapi(a.z0 + pz0 + tz, a.n2) : 0;
+    const int oy = py0 + ty - V, oz = pz0 + tz - V;   // this thread's output point (box-relative)
+    const bool out_yz = ty >= V && tz >= V && oy < a.ey && oz < a.ez;
+    const size_t out_yz_off = out_yz ? (size_t)wrapi(a.y0 + oy, a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2) : 0;
+    const int o = (ty + 1) * PZ + (tz + 1);          // own centre in the ring
+    const size_t d_yz = (size_t)wrapi(cy0 + ty, a.n1) * a.n2 + wrapi(cz0 + tz, a.n2);
     float prev[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // 2 x 2 centre sum of the previous plane
     for (int c = c_first; c <= c_last; ++c) {
         const int s0 = (c - c_first) % 3, s1 = (c - c_first + 1) % 3, s2 = (c - c_first + 2) % 3;
@@ -102,53 +107,51 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
         float nxt[LP];
         if (c < c_last) fetch(c + 2, nxt);   // the plane after next, while this one is processed
 
-        // second derivatives at the centres of plane c (differences of neighbours first)
+        // second derivatives at this thread's centre (differences of neighbours first)
         float h[7];
-        for (int i = threadIdx.x; i < NC; i += NT) {
-            const int y = i / CZ, z = i % CZ;
-            const int o = (y + 1) * PZ + (z + 1);
-            const float p0 = P1[o];
-            h[0] = ((P0[o] - p0) + (P2[o] - p0)) * a.ih2;
-            h[1] = ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) * a.ih2;
-            h[2] = ((P1[o - 1] - p0) + (P1[o + 1] - p0)) * a.ih2;
-            h[3] = ((P2[o + PZ] - P2[o - PZ]) + (P0[o - PZ] - P0[o + PZ])) * a.iq;
-            h[4] = ((P2[o + 1] - P2[o - 1]) + (P0[o - 1] - P0[o + 1])) * a.iq;
-            h[5] = ((P1[o + PZ + 1] - P1[o + PZ - 1]) + (P1[o - PZ - 1] - P1[o - PZ + 1])) * a.iq;
-            if (a.delta) {
-                const int gx = wrapi(c, a.n0), gy = wrapi(cy0 + y, a.n1), gz = wrapi(cz0 + z, a.n2);
-                h[6] = __ldg(a.delta + ((size_t)gx * a.n1 + gy) * a.n2 + gz);
-            } else {
-                h[6] = (h[0] + h[1] + h[2]) * a.dinv;
-            }
-            if constexpr (MODE == 0) {
+        const float p0 = P1[o];
+        h[0] = ((P0[o] - p0) + (P2[o] - p0)) * a.ih2;
+        h[1] = ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) * a.ih2;
+        h[2] = ((P1[o - 1] - p0) + (P1[o + 1] - p0)) * a.ih2;
+        h[3] = ((P2[o + PZ] - P2[o - PZ]) + (P0[o - PZ] - P0[o + PZ])) * a.iq;
+        h[4] = ((P2[o + 1] - P2[o - 1]) + (P0[o - 1] - P0[o + 1])) * a.iq;
+        h[5] = ((P1[o + PZ + 1] - P1[o + PZ - 1]) + (P1[o - PZ - 1] - P1[o - PZ + 1])) * a.iq;
+        if (a.delta) h[6] = __ldg(a.delta + (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + d_yz);
+        else h[6] = (h[0] + h[1] + h[2]) * a.dinv;
+
+        float pz[7];
+        if constexpr (MODE == 0) {
+            // z pair: this centre and the one below it in z (the lane to the left)
 #pragma unroll
-                for (int q = 0; q < 7; ++q) sH[q][i] = h[q];
+            for (int q = 0; q < 7; ++q) pz[q] = h[q] + __shfl_up_sync(0xffffffffu, h[q], 1);
+            if (ty < TY - 1) {
+#pragma unroll
+                for (int q = 0; q < 7; ++q) sP[q][threadIdx.x] = pz[q];
             }
         }
-        // every read of plane c - 1 is done (and, for vertices, plane c's centres are in sH)
-        __syncthreads();
+        __syncthreads();   // every read of plane c - 1 is done; the z pairs are shared
         if (c < c_last) put(s0, nxt);
         if constexpr (MODE == 0) {
-            const float (*H)[HN] = sH;
-            float b[7];
-            const int o = ty * CZ + tz;
+            if (ty >= 1) {
+                float b[7];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) b[q] = (H[q][o] + H[q][o + 1]) + (H[q][o + CZ] + H[q][o + CZ + 1]);
-            if (c > c_first && out_yz) {
-                float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
-                r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
-                                   (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
-                r[1] = make_float4((prev[4] + b[4]) * 0.125f, (prev[5] + b[5]) * 0.125f,
-                                   (prev[6] + b[6]) * 0.125f, 0.f);
+                for (int q = 0; q < 7; ++q) b[q] = pz[q] + sP[q][threadIdx.x - TZ];
+                if (c > c_first && out_yz) {
+                    float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
+                    r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
+                                       (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
+                    r[1] = make_float4((prev[4] + b[4]) * 0.125f, (prev[5] + b[5]) * 0.125f,
+                                       (prev[6] + b[6]) * 0.125f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < 7; ++q) prev[q] = b[q];
             }
-#pragma unroll
-            for (int q = 0; q < 7; ++q) prev[q] = b[q];
         } else if (out_yz) {
             float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
             r[0] = make_float4(h[0], h[1], h[2], h[3]);
             r[1] = make_float4(h[4], h[5], h[6], 0.f);
         }
-        __syncthreads();   // plane c + 2 is in the ring and every read of sH is done
+        __syncthreads();   // plane c + 2 is in the ring and every read of sP is done
     }
 }
 
@@ -294,10 +297,11 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             nsm = 152;
     }
-    const long long tiles_yz = (long long)((a.ez + TZ - 1) / TZ) * ((a.ey + TY - 1) / TY);
+    const int oy = where == RR_AT_VERTICES ? TY - 1 : TY, oz = where == RR_AT_VERTICES ? TZ - 1 : TZ;
+    const long long tiles_yz = (long long)((a.ez + oz - 1) / oz) * ((a.ey + oy - 1) / oy);
     const long long want = (long long)a.ex * tiles_yz / (2LL * nsm);
     a.xchunk = (int)std::max(2LL, std::min((long long)XCHUNK_MAX, want));
-    dim3 grid((a.ez + TZ - 1) / TZ, (a.ey + TY - 1) / TY, (a.ex + a.xchunk - 1) / a.xchunk);
+    dim3 grid((a.ez + oz - 1) / oz, (a.ey + oy - 1) / oy, (a.ex + a.xchunk - 1) / a.xchunk);
     if (where == RR_AT_VERTICES)
         tidal_kernel<0><<<grid, NT, 0, s>>>(a);
     else
