@@ -56,8 +56,8 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
     constexpr int PY = TY + 2, PZ = TZ + 2;          // potential per plane (halo 1 around the centres)
     constexpr int NP = PY * PZ;
     constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane
-    __shared__ float ring[3][NP];
-    __shared__ float sP[MODE == 0 ? 7 : 1][MODE == 0 ? NT : 1];   // z-pair sums of every centre
+    __shared__ float ring[4][NP];   // potential planes c - 1, c, c + 1 and the one arriving (c + 2)
+    __shared__ float sP[2][MODE == 0 ? 7 : 1][MODE == 0 ? NT : 1];   // z-pair sums of every centre, by plane parity
 
     const int ty = threadIdx.x / TZ, tz = threadIdx.x % TZ;
     const int py0 = blockIdx.y * OY, pz0 = blockIdx.x * OZ;               // box-relative first output
@@ -85,11 +85,15 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
             if (i < NP) ring[slot][i] = r[k];
         }
     };
+    // ring slot of plane p
+    auto slot = [&](int p) { return (p - (c_first - 1)) & 3; };
+    float nxt[LP];   // the plane two ahead of the current one, on its way to the ring
     {
         float r[LP];
         fetch(c_first - 1, r); put(0, r);
         fetch(c_first, r); put(1, r);
         fetch(c_first + 1, r); put(2, r);
+        fetch(c_first + 2, nxt);
     }
     __syncthreads();
 
@@ -100,12 +104,15 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
     const size_t d_yz = (size_t)wrapi(cy0 + ty, a.n1) * a.n2 + wrapi(cz0 + tz, a.n2);
     float prev[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // 2 x 2 centre sum of the previous plane
     for (int c = c_first; c <= c_last; ++c) {
-        const int s0 = (c - c_first) % 3, s1 = (c - c_first + 1) % 3, s2 = (c - c_first + 2) % 3;
-        const float* P0 = ring[s0];   // plane c - 1
-        const float* P1 = ring[s1];   // plane c
-        const float* P2 = ring[s2];   // plane c + 1
-        float nxt[LP];
-        if (c < c_last) fetch(c + 2, nxt);   // the plane after next, while this one is processed
+        const float* P0 = ring[slot(c - 1)];
+        const float* P1 = ring[slot(c)];
+        const float* P2 = ring[slot(c + 1)];
+        // plane c + 2 goes into the slot of plane c - 2 (read last iteration,
+        // before its barrier); plane c + 3 is fetched into registers, a whole
+        // plane of work ahead of its use
+        float nxt2[LP];
+        if (c + 3 <= c_last + 1) fetch(c + 3, nxt2);
+        if (c + 2 <= c_last + 1) put(slot(c + 2), nxt);
 
         // second derivatives at this thread's centre (differences of neighbours first)
         float h[7];
@@ -126,16 +133,17 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
             for (int q = 0; q < 7; ++q) pz[q] = h[q] + __shfl_up_sync(0xffffffffu, h[q], 1);
             if (ty < TY - 1) {
 #pragma unroll
-                for (int q = 0; q < 7; ++q) sP[q][threadIdx.x] = pz[q];
+                for (int q = 0; q < 7; ++q) sP[(c - c_first) & 1][q][threadIdx.x] = pz[q];
             }
         }
-        __syncthreads();   // every read of plane c - 1 is done; the z pairs are shared
-        if (c < c_last) put(s0, nxt);
+        // plane c + 2 is in the ring and the z pairs of plane c are shared; the
+        // next iteration writes the other sP buffer and a ring slot not read here
+        __syncthreads();
         if constexpr (MODE == 0) {
             if (ty >= 1) {
                 float b[7];
 #pragma unroll
-                for (int q = 0; q < 7; ++q) b[q] = pz[q] + sP[q][threadIdx.x - TZ];
+                for (int q = 0; q < 7; ++q) b[q] = pz[q] + sP[(c - c_first) & 1][q][threadIdx.x - TZ];
                 if (c > c_first && out_yz) {
                     float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
                     r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
@@ -151,7 +159,8 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
             r[0] = make_float4(h[0], h[1], h[2], h[3]);
             r[1] = make_float4(h[4], h[5], h[6], 0.f);
         }
-        __syncthreads();   // plane c + 2 is in the ring and every read of sP is done
+#pragma unroll
+        for (int k = 0; k < LP; ++k) nxt[k] = nxt2[k];
     }
 }
 
