@@ -295,23 +295,25 @@ def _shuffled(mesh, seed):
 
 @pytest.mark.parametrize("interp", [1, 0])
 @pytest.mark.parametrize("shuffle", [False, True])
-def test_footprint_records_give_the_same_maps(rrp, interp, shuffle):
+@pytest.mark.parametrize("obs", [(16.0, 15.0, 0.5), (0.7, 31.2, 30.0)])
+def test_footprint_records_give_the_same_maps(rrp, interp, shuffle, obs):
     """Records of only the leaves in each step's coarse footprint box (the
     rest left as NaN) give the same maps, bit for bit, as records of the
     whole mesh: the walk reads nothing outside the box. With the octs listed
     out of order (no x-slab launches; another cell numbering) the maps are
-    the same bits again."""
+    the same bits again. The second observer sits at a corner of the periodic
+    box, so the boxes wrap through the seams (two x-slab ranges per level)."""
     import torch
     mesh = synth.amr_random(16, 32.0, 2, 6, threshold=1.5, child_sigma=0.8)
     mesh.phi = synth.amr_sample(mesh, synth.fourier_fn(32.0, 40, 2 * math.pi / 32.0 * 6, 17))
     _round_phi(mesh)
     reference = None
     if shuffle:
-        b0 = synth.Bundle(21, 18, synth.deg(8), synth.deg(6), (16.0, 15.0, 0.5), 30.0, interp=interp)
+        b0 = synth.Bundle(21, 18, synth.deg(8), synth.deg(6), obs, 30.0, interp=interp)
         st0 = [synth.Step(30.0, 20.0, 1.2, 0.7), synth.Step(20.0, 10.0, 1.1, 0.85), synth.Step(10.0, 0.0, 1.0, 1.0)]
         reference = _trace_gpu(rrp, mesh, b0, st0)
         mesh = _shuffled(mesh, 23)
-    b = synth.Bundle(21, 18, synth.deg(8), synth.deg(6), (16.0, 15.0, 0.5), 30.0, interp=interp)
+    b = synth.Bundle(21, 18, synth.deg(8), synth.deg(6), obs, 30.0, interp=interp)
     steps = [synth.Step(30.0, 20.0, 1.2, 0.7), synth.Step(20.0, 10.0, 1.1, 0.85), synth.Step(10.0, 0.0, 1.0, 1.0)]
     where = rrp.RR_AT_VERTICES if interp == 1 else rrp.RR_AT_CENTRES
     gm = _gpu_mesh(rrp, mesh)
