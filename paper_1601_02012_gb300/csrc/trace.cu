@@ -151,40 +151,34 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         }
 
         if (t > tend * eps_rel) {
-            // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
-            const R chiA = chiA0 - sig;
-            const R G0 = (D0 + sig) * chiA * ichis;
-            const R G1 = (2 * chiA - chis) * ichis;
-            const R G2 = -ichis;
-            if (INTERP == RR_TRILINEAR) {
+            if constexpr (!F64) {
+                float G0, G1, G2;
+                kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
+                const float2 x = INTERP == RR_TRILINEAR
+                                     ? segment_trilinear(q2, u[0], u[1], u[2], v[0], v[1], v[2], t, G0, G1, G2)
+                                     : segment_ngp(q2[0], t, G0, G1, G2);
+                if constexpr (PLAIN) s2.s = __fadd2_rn(s2.s, x);
+                else s2.add(x);
+            } else {
+                // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
+                const R chiA = chiA0 - sig;
+                const R G0 = (D0 + sig) * chiA * ichis;
+                const R G1 = (2 * chiA - chis) * ichis;
+                const R G2 = -ichis;
                 const R t2 = t * t;
                 const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
-                const R J2 = t2 * (G0 * (R)0.5 + t * (G1 * (R)(1.0 / 3.0) + t * G2 * (R)0.25));
-                const R J3 = t2 * t * (G0 * (R)(1.0 / 3.0) + t * (G1 * (R)0.25 + t * G2 * (R)0.2));
-                const R J4 = t2 * t2 * (G0 * (R)0.25 + t * (G1 * (R)0.2 + t * G2 * (R)(1.0 / 6.0)));
-                float2 e2[4];
-                line_cubic2(q2, bc2((float)u[0]), bc2((float)u[1]), bc2((float)u[2]), bc2((float)v[0]),
-                            bc2((float)v[1]), bc2((float)v[2]), e2);
-                if constexpr (F64) {
+                if (INTERP == RR_TRILINEAR) {
+                    const R J2 = t2 * (G0 * (R)0.5 + t * (G1 * (R)(1.0 / 3.0) + t * G2 * (R)0.25));
+                    const R J3 = t2 * t * (G0 * (R)(1.0 / 3.0) + t * (G1 * (R)0.25 + t * G2 * (R)0.2));
+                    const R J4 = t2 * t2 * (G0 * (R)0.25 + t * (G1 * (R)0.2 + t * G2 * (R)(1.0 / 6.0)));
+                    float2 e2[4];
+                    line_cubic2(q2, bc2((float)u[0]), bc2((float)u[1]), bc2((float)u[2]), bc2((float)v[0]),
+                                bc2((float)v[1]), bc2((float)v[2]), e2);
                     sk.add((R)e2[0].x * J1 + (R)e2[1].x * J2 + (R)e2[2].x * J3 + (R)e2[3].x * J4);
                     sb.add((R)e2[0].y * J1 + (R)e2[1].y * J2 + (R)e2[2].y * J3 + (R)e2[3].y * J4);
                 } else {
-                    float2 x = __fmul2_rn(e2[0], bc2(J1));
-                    x = __ffma2_rn(e2[1], bc2(J2), x);
-                    x = __ffma2_rn(e2[2], bc2(J3), x);
-                    x = __ffma2_rn(e2[3], bc2(J4), x);
-                    if constexpr (PLAIN) s2.s = __fadd2_rn(s2.s, x);
-                    else s2.add(x);
-                }
-            } else {
-                const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
-                if constexpr (F64) {
                     sk.add((R)q2[0].x * J1);
                     sb.add((R)q2[0].y * J1);
-                } else if constexpr (PLAIN) {
-                    s2.s = __ffma2_rn(q2[0], bc2(J1), s2.s);
-                } else {
-                    s2.add(__fmul2_rn(q2[0], bc2(J1)));
                 }
             }
             if (resume) resume = false;

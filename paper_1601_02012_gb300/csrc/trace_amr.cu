@@ -115,11 +115,8 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                     const Rec x = load_rec(A.rec, leaf);
                     q2[0] = make_float2(project(W.w, x), x.b.z);
                 }
-                // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
-                const float chiA = chiA0 - sig;
-                const float G0 = (D0 + sig) * chiA * ichis;
-                const float G1 = (2.f * chiA - chis) * ichis;
-                const float G2 = -ichis;
+                float G0, G1, G2;
+                kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
                 if (INTERP == RR_TRILINEAR) {
                     float u[3], vl[3];
 #pragma unroll
@@ -128,21 +125,9 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                         u[a] = W.v[a] > 0.f ? fminf(fmaxf(fmaf(sig - Tx[a], vl[a], 1.f), 0.f), 1.f)
                                             : (i2f_exact(jp[a]) + W.cu[a]) * inv_span;
                     }
-                    const float t2 = t * t;
-                    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
-                    const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
-                    const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
-                    const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
-                    float2 e2[4];
-                    line_cubic2(q2, bc2(u[0]), bc2(u[1]), bc2(u[2]), bc2(vl[0]), bc2(vl[1]), bc2(vl[2]), e2);
-                    float2 x = __fmul2_rn(e2[0], bc2(J1));
-                    x = __ffma2_rn(e2[1], bc2(J2), x);
-                    x = __ffma2_rn(e2[2], bc2(J3), x);
-                    x = __ffma2_rn(e2[3], bc2(J4), x);
-                    s2.add(x);
+                    s2.add(segment_trilinear(q2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
                 } else {
-                    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
-                    s2.add(__fmul2_rn(q2[0], bc2(J1)));
+                    s2.add(segment_ngp(q2[0], t, G0, G1, G2));
                 }
                 if (leaf != prev_leaf) ++cnt;
                 prev_leaf = leaf;

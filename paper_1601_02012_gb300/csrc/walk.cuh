@@ -154,6 +154,45 @@ struct Acc2 {
     }
 };
 
+// The segment integrals of the FP32 walk, (kappa, Born) as one pair. The
+// segment starts at path sig of the sub-step (chi_A = chiA0 - sig, chi_s -
+// chi_A = D0 + sig) and has length t; along it the lensing kernel is
+// g(chi_A - s) = G0 + G1 s + G2 s^2.
+//  trilinear: the field on the line is the cubic e_0..e_3 of line_cubic2
+//             (corners q, mirrored entry point u, rates v) and the integral is
+//             sum_N e_{N-1} J_N with J_N = int_0^t g s^(N-1) ds (Eq. Iclensing);
+//  NGP:       the constant value times J_1 (Eq. Iclensing_ngp).
+__device__ __forceinline__ void kernel_coeffs(float t, float sig, float chiA0, float D0, float chis, float ichis,
+                                              float& G0, float& G1, float& G2)
+{
+    const float chiA = chiA0 - sig;
+    G0 = (D0 + sig) * chiA * ichis;
+    G1 = (2.f * chiA - chis) * ichis;
+    G2 = -ichis;
+}
+
+__device__ __forceinline__ float2 segment_trilinear(const float2 q[8], float u0, float u1, float u2, float v0,
+                                                    float v1, float v2, float t, float G0, float G1, float G2)
+{
+    const float t2 = t * t;
+    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
+    const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
+    const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
+    const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
+    float2 e2[4];
+    line_cubic2(q, bc2(u0), bc2(u1), bc2(u2), bc2(v0), bc2(v1), bc2(v2), e2);
+    float2 x = __fmul2_rn(e2[0], bc2(J1));
+    x = __ffma2_rn(e2[1], bc2(J2), x);
+    x = __ffma2_rn(e2[2], bc2(J3), x);
+    return __ffma2_rn(e2[3], bc2(J4), x);
+}
+
+__device__ __forceinline__ float2 segment_ngp(float2 q, float t, float G0, float G1, float G2)
+{
+    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
+    return __fmul2_rn(q, bc2(J1));
+}
+
 // float of an integer in [0, 2^23) and back, exact, on the FP32/integer pipes
 // (the bit pattern of 2^23 + i), instead of the conversion unit
 __device__ __forceinline__ float i2f_exact(int i) { return __int_as_float(0x4B000000 | i) - 8388608.f; }
