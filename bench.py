@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), per
 # (kernel source, workload): valid only for the source it was taken on (sha256
 # of csrc/trace.cu + csrc/walk.cuh) and for that workload.
-TRACE_TRAFFIC = {("85bb554c18edd692", "prod_512"): 275_786_880}
+TRACE_TRAFFIC = {("e21e1884dfbb2b63", "prod_512"): 275_083_392}
 
 
 def _src_hash(*names):
@@ -541,6 +541,77 @@ def run_amr(args, name):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
+def _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, nck=8):
+    """Time kappa maps for nck source distances (the step boundaries nearest
+    to chi_s j / nck): one moments pass with snapshots vs one ordinary pass per
+    source distance; the maps of the two agree to the stated difference."""
+    nst = len(steps)
+    picks = sorted({min(range(nst), key=lambda i: abs(steps[i].chi_a - w.bundle.chi_s * j / nck))
+                    for j in range(1, nck + 1)})
+    ny, nx = w.bundle.ny, w.bundle.nx
+    trm = rrp.Tracer(w.bundle, moments=True)
+    snaps = {i: torch.empty((4, ny, nx), dtype=torch.float64, device=phi.device) for i in picks if i > 0}
+    m_end = torch.empty((4, ny, nx), dtype=torch.float64, device=phi.device)
+
+    def moments_pass():
+        rrp.rr_reset(trm.ctx, stream)
+        for i, st in enumerate(steps):
+            if i in snaps:
+                trm.moments(snaps[i], stream)
+            rrp.rr_tidal_tensor(gd, phi, None, rec, trm.where, bboxes[i], stream)
+            rrp.rr_trace_step(trm.ctx, gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+        trm.moments(m_end, stream)
+
+    # one ordinary context per source distance (bundle with chi_s = chi_k)
+    ctxs = {}
+    for i in picks:
+        bi = rrp.bundle_desc(w.bundle)
+        bi.chi_s = steps[i].chi_a
+        ctxs[i] = rrp.rr_create(bi)
+    where = rrp.RR_AT_VERTICES if w.bundle.interp == 1 else rrp.RR_AT_CENTRES
+    maps = {i: torch.empty((ny, nx), dtype=torch.float64, device=phi.device) for i in picks}
+
+    def ordinary_passes():
+        for i in picks:
+            rrp.rr_reset(ctxs[i], stream)
+            for j in range(i, nst):
+                st = steps[j]
+                rrp.rr_tidal_tensor(gd, phi, None, rec, where, bboxes[j], stream)
+                rrp.rr_trace_step(ctxs[i], gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            rrp.rr_finalize(ctxs[i], maps[i], None, stream)
+
+    def timed(fn):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    with torch.cuda.stream(stream):
+        moments_pass()
+        t_mom = timed(moments_pass)
+        ordinary_passes()
+        t_ord = timed(ordinary_passes)
+        worst = 0.0
+        for i in picks:
+            k, _ = rrp.source_kappa(m_end, snaps.get(i), steps[i].chi_a, stream)
+            ref = maps[i]
+            rms = float(torch.sqrt(torch.mean(ref * ref)))
+            worst = max(worst, float((k - ref).abs().max()) / rms)
+    trm.close()
+    for c in ctxs.values():
+        rrp.rr_destroy(c)
+    return {"source_chi": [round(steps[i].chi_a, 3) for i in picks], "moments_pass_ms": t_mom,
+            "ordinary_passes_ms": t_ord, "speedup": t_ord / t_mom,
+            "max_over_rms_vs_ordinary": worst,
+            "note": "one pass in the moments form with a snapshot at each source distance, against one "
+                    "ordinary pass per source distance (each from its chi_s down to 0, contexts created "
+                    "before the timing); CUDA events, L2 flushed before each"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -710,6 +781,13 @@ def main():
         e2e_s = sum(e2e_times)
         total_ms, segs_all, e2e_s = combine_over_ranks(dist, dev, total_ms, segs, e2e_s)
 
+        # kappa for several source distances from one pass (Eqs. Isources,
+        # Isources1): the moments form with snapshots at step boundaries, against
+        # one ordinary pass per source distance
+        sources = None
+        if world == 1:
+            sources = _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush)
+
     if rank != 0:
         dist.barrier()
         dist.destroy_process_group()
@@ -754,6 +832,7 @@ def main():
         "e2e": {"value": segs_all * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(phi_host.nbytes),
                 "d2h_bytes_per_step": int(k_host.numel() * 8 * 2)},
+        "source_redshifts": sources,
         "gpu_launches": args.steps * (2 * nst + 1),
         "clocks": clocks,
         "trace_src": h,

@@ -52,10 +52,16 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
        RR_FP64_DDA = 2,     /* plain form: cell walk, kernel integrals and per-step
                                sums in FP64 (default: FP32 walk in cell-local
                                coordinates with compensated FP32 sums) */
-       RR_PLAIN_SUMS = 4 }; /* the FP32 walk with uncompensated FP32 sums, within and
+       RR_PLAIN_SUMS = 4,   /* the FP32 walk with uncompensated FP32 sums, within and
                                across steps: only to measure what the compensation
                                buys (rr_create / rr_trace_step only; not with
                                RR_FP64_DDA, batches, AMR or the no-allocation call) */
+       RR_SOURCE_MOMENTS = 8 }; /* rays accumulate the two moments of Eq. (Isources),
+                               A = int chi Q dchi and B = int chi^2 Q dchi (for kappa
+                               and Born kappa) instead of kappa itself, so that kappa
+                               for any source distance chi_k <= chi_s follows from one
+                               pass (rr_moments, rr_source_kappa); FP32 walk with
+                               compensated sums; rr_create / rr_trace_step only */
 
 /* rr_tidal_tensor: where the records are evaluated. */
 enum { RR_AT_VERTICES = 0,  /* mean of the 8 cells sharing each vertex (Sec. 2.7); trilinear */
@@ -76,7 +82,7 @@ typedef struct {
     double obs[3];        /* observer position in box coordinates, Mpc/h */
     double chi_s;         /* comoving distance of the sources, > 0 */
     int32_t interp;       /* RR_NGP or RR_TRILINEAR */
-    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS */
+    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS */
 } rr_bundle_desc;
 
 /* A uniform grid of n[0] x n[1] x n[2] cubic cells of size h = box / n[0]. */
@@ -161,6 +167,32 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
  * any step since create/reset, else RR_OK.
  */
 rr_status rr_finalize(rr_ctx* ctx, double* kappa, double* kappa_born, void* stream);
+
+/*
+ * Source-redshift moments (contexts created with RR_SOURCE_MOMENTS; Eqs.
+ * Isources, Isources1). kappa(chi_s) = int_0^chi_s (chi - chi^2/chi_s) Q dchi =
+ * A(chi_s) - B(chi_s)/chi_s with A(X) = int_0^X chi Q dchi and B(X) = int_0^X
+ * chi^2 Q dchi, where chi_s appears only as the upper limit and in the factor
+ * of B. Rays integrate from the sources towards the observer, so the moments
+ * accumulated down to chi_k are the parts above chi_k: A(chi_k) = A_end -
+ * A_k with A_k taken once the steps down to chi_k are traced (same for B).
+ * rr_finalize of such a context writes kappa for the context's own chi_s.
+ */
+
+/* The moments accumulated since create/reset: out = device FP64 [4][ny*nx],
+ * rows A_kappa, B_kappa, A_born, B_born in rayid order, each summed over the
+ * traced steps as scale * int chi^k Q dchi (Born: with the prefactor of Eq.
+ * kappa2). Asynchronous. RR_ERR_STATE for a context without RR_SOURCE_MOMENTS. */
+rr_status rr_moments(rr_ctx* ctx, double* out, void* stream);
+
+/* kappa and Born kappa for sources at chi_k from two moment snapshots of
+ * rr_moments: m_end after the last step (down to the observer), m_k after the
+ * steps down to chi_k (NULL when chi_k is the context's chi_s: nothing traced
+ * above it); kappa = (A_end - A_k) - (B_end - B_k) / chi_k per channel.
+ * nrays entries per row; kappa_born may be NULL. Asynchronous; RR_ERR_ARG on
+ * null pointers, nrays < 1 or chi_k <= 0. */
+rr_status rr_source_kappa(const double* m_end, const double* m_k, int64_t nrays, double chi_k, double* kappa,
+                          double* kappa_born, void* stream);
 
 /* Synchronise `stream` and return the error word (as rr_finalize does),
  * without writing maps. */

@@ -17,7 +17,7 @@ from .batch import Batch  # noqa: E402
 from ._rr import rr_amr_create, rr_amr_destroy, rr_amr_sizes, rr_amr_tidal, rr_amr_trace_step  # noqa: E402
 
 __all__ = [
-    "Batch", "AmrMesh", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal", "rr_amr_trace_step",
+    "Batch", "AmrMesh", "source_kappa", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal", "rr_amr_trace_step",
     "Tracer", "trace_kappa", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
@@ -45,13 +45,15 @@ class Tracer:
 
     bundle: object with nx, ny, fov_x, fov_y (radians), obs (3), chi_s, interp
     (0 NGP / 1 trilinear) and periodic attributes. fp64_dda: the plain FP64
-    walk; plain_sums: the FP32 walk without compensated sums (for comparison).
+    walk; plain_sums: the FP32 walk without compensated sums (for comparison);
+    moments: accumulate the source-redshift moments of Eq. (Isources) (see
+    ``moments()`` and ``source_kappa``).
     """
 
-    def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False):
+    def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False):
         _rr.load()
         self.bundle = bundle
-        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums)
+        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums, moments=moments)
         self.ctx = rr_create(self.desc)
         self.where = RR_AT_VERTICES if int(self.desc.interp) == RR_TRILINEAR else RR_AT_CENTRES
 
@@ -94,6 +96,16 @@ class Tracer:
     def segments(self, per_ray=None, stream=None) -> int:
         return rr_segment_count(self.ctx, per_ray, stream)
 
+    def moments(self, out=None, stream=None):
+        """Snapshot of the moments so far: FP64 [4, ny, nx] on the device, rows
+        A_kappa, B_kappa, A_born, B_born (contexts created with moments=True)."""
+        import torch
+        ny, nx = int(self.desc.ny), int(self.desc.nx)
+        if out is None:
+            out = torch.empty((4, ny, nx), dtype=torch.float64, device="cuda")
+        _rr.rr_moments(self.ctx, out, stream)
+        return out
+
     def amr_step(self, mesh, leaf_rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):
         """One step over an adaptive mesh (``AmrMesh``) from its leaf records."""
         rr_amr_trace_step(self.ctx, mesh.handle, leaf_rec, chi_a, chi_b, scale, a, stream)
@@ -111,6 +123,18 @@ class Tracer:
         rr_trace_backward(self.ctx, dkappa.contiguous() if dkappa is not None else None,
                           dkborn.contiguous() if dkborn is not None else None, grad_rec, dphi, ddelta, stream)
         return dphi
+
+
+def source_kappa(m_end, m_k, chi_k, stream=None):
+    """kappa and Born kappa [ny, nx] for sources at chi_k from two moment
+    snapshots (``Tracer.moments``): m_end after the last step, m_k after the
+    steps down to chi_k (None when chi_k is the bundle's chi_s)."""
+    import torch
+    ny, nx = int(m_end.shape[1]), int(m_end.shape[2])
+    k = torch.empty((ny, nx), dtype=torch.float64, device=m_end.device)
+    kb = torch.empty_like(k)
+    _rr.rr_source_kappa(m_end, m_k, ny * nx, chi_k, k, kb, stream)
+    return k, kb
 
 
 class AmrMesh:

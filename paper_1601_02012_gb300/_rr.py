@@ -31,6 +31,7 @@ RR_TRILINEAR = 1
 RR_PERIODIC = 1
 RR_FP64_DDA = 2
 RR_PLAIN_SUMS = 4
+RR_SOURCE_MOMENTS = 8
 RR_AT_VERTICES = 0
 RR_AT_CENTRES = 1
 
@@ -95,6 +96,8 @@ def load() -> C.CDLL:
             "rr_batch_set_tuning": ([P, I32, I32, I32, I32, I32], C.c_int),
             "rr_batch_get_tuning": ([P, P], C.c_int),
             "rr_batch_autotune": ([P, I32, C.POINTER(C.c_float), P], C.c_int),
+            "rr_moments": ([P, P, P], C.c_int),
+            "rr_source_kappa": ([P, P, C.c_int64, D, P, P, P], C.c_int),
             "rr_amr_create": ([P, P, P, C.POINTER(C.c_void_p)], C.c_int),
             "rr_amr_destroy": ([P], C.c_int),
             "rr_amr_sizes": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
@@ -136,7 +139,7 @@ def _stream(s):
     return C.c_void_p(s.cuda_stream)
 
 
-def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False) -> rr_bundle_desc:
+def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False) -> rr_bundle_desc:
     """rr_bundle_desc from any object with nx, ny, fov_x, fov_y, obs, chi_s,
     interp and periodic attributes."""
     d = rr_bundle_desc()
@@ -151,6 +154,8 @@ def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False) -> rr_bundl
         flags |= RR_FP64_DDA
     if plain_sums:
         flags |= RR_PLAIN_SUMS
+    if moments:
+        flags |= RR_SOURCE_MOMENTS
     d.flags = flags
     return d
 
@@ -217,6 +222,16 @@ def rr_segment_count(ctx, per_ray=None, stream=None) -> int:
     tot = C.c_uint64(0)
     _check(load().rr_segment_count(ctx, C.byref(tot), _ptr(per_ray), _stream(stream)), "rr_segment_count")
     return int(tot.value)
+
+
+def rr_moments(ctx, out, stream=None) -> None:
+    """out: device FP64 [4, ny*nx] (A_kappa, B_kappa, A_born, B_born)."""
+    _check(load().rr_moments(ctx, _ptr(out), _stream(stream)), "rr_moments")
+
+
+def rr_source_kappa(m_end, m_k, nrays: int, chi_k: float, kappa, kappa_born=None, stream=None) -> None:
+    _check(load().rr_source_kappa(_ptr(m_end), _ptr(m_k), int(nrays), float(chi_k), _ptr(kappa), _ptr(kappa_born),
+                                  _stream(stream)), "rr_source_kappa")
 
 
 def rr_step_count(ctx) -> int:

@@ -27,8 +27,9 @@ rr_status check_bundle(const rr_bundle_desc* b)
         if (!is_finite(b->obs[a])) return RR_ERR_ARG;
     if (!is_finite(b->chi_s) || !(b->chi_s > 0)) return RR_ERR_ARG;
     if (b->interp != RR_NGP && b->interp != RR_TRILINEAR) return RR_ERR_ARG;
-    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS)) return RR_ERR_ARG;
-    if ((b->flags & RR_PLAIN_SUMS) && (b->flags & RR_FP64_DDA)) return RR_ERR_ARG;
+    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS)) return RR_ERR_ARG;
+    if ((b->flags & RR_PLAIN_SUMS) && (b->flags & (RR_FP64_DDA | RR_SOURCE_MOMENTS))) return RR_ERR_ARG;
+    if ((b->flags & RR_SOURCE_MOMENTS) && (b->flags & RR_FP64_DDA)) return RR_ERR_ARG;
     return RR_OK;
 }
 
@@ -63,6 +64,8 @@ void free_state(RayState& s)
     cudaFree(s.dirl);
     cudaFree(s.kacc);
     cudaFree(s.bacc);
+    cudaFree(s.kmom);
+    cudaFree(s.bmom);
     cudaFree(s.nseg);
     cudaFree(s.err);
     cudaFree(s.total);
@@ -103,6 +106,8 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     a.dirl = ctx->st.dirl;
     a.kacc = ctx->st.kacc;
     a.bacc = ctx->st.bacc;
+    a.kmom = ctx->st.kmom;
+    a.bmom = ctx->st.bmom;
     a.nseg = ctx->st.nseg;
     a.err = ctx->st.err;
     split_ff(scale, a.sch, a.scl);
@@ -174,6 +179,12 @@ rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->host_total, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(s.kacc, 0, nr * sizeof(float2));
     if (e == cudaSuccess) e = cudaMemset(s.bacc, 0, nr * sizeof(float2));
+    if (bundle->flags & RR_SOURCE_MOMENTS) {
+        if (e == cudaSuccess) e = cudaMalloc(&s.kmom, nr * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&s.bmom, nr * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemset(s.kmom, 0, nr * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemset(s.bmom, 0, nr * sizeof(float2));
+    }
     if (e == cudaSuccess) e = cudaMemset(s.nseg, 0, nr * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.err, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.total, 0, sizeof(unsigned long long));
@@ -208,6 +219,8 @@ rr_status rr_reset(rr_ctx* ctx, void* stream)
     const size_t nr = (size_t)ctx->bundle.nx * ctx->bundle.ny;
     cudaError_t e = cudaMemsetAsync(ctx->st.kacc, 0, nr * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.bacc, 0, nr * sizeof(float2), s);
+    if (e == cudaSuccess && ctx->st.kmom) e = cudaMemsetAsync(ctx->st.kmom, 0, nr * sizeof(float2), s);
+    if (e == cudaSuccess && ctx->st.bmom) e = cudaMemsetAsync(ctx->st.bmom, 0, nr * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.nseg, 0, nr * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.err, 0, sizeof(uint32_t), s);
     ctx->log.clear();
@@ -270,8 +283,8 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     if (st != RR_OK) return st;
     const rr_bundle_desc& b = ctx->bundle;
     TraceArgs a = make_trace_args(ctx, grid, rec, chi_a, chi_b, scale, a_step);
-    cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{},
-                                 (b.flags & RR_PLAIN_SUMS) != 0);
+    const int form = (b.flags & RR_SOURCE_MOMENTS) ? kFormMoments : ((b.flags & RR_PLAIN_SUMS) ? kFormPlain : kFormKahan);
+    cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{}, form);
     if (e != cudaSuccess) return from_cuda(e);
     ctx->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
     return RR_OK;
@@ -293,7 +306,7 @@ rr_status rr_finalize(rr_ctx* ctx, double* kappa, double* kappa_born, void* stre
     cudaStream_t s = (cudaStream_t)stream;
     const int nr = ctx->bundle.nx * ctx->bundle.ny;
     cudaError_t e = launch_finalize(nr, ctx->st.kacc, ctx->st.bacc, ctx->st.nseg, kappa, kappa_born,
-                                    ctx->st.total, s);
+                                    ctx->st.total, s, ctx->st.kmom, ctx->st.bmom, ctx->bundle.chi_s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->host_total, ctx->st.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return from_cuda(e);
@@ -314,6 +327,23 @@ rr_status rr_segment_count(rr_ctx* ctx, uint64_t* total, uint32_t* per_ray, void
     return RR_OK;
 }
 
+rr_status rr_moments(rr_ctx* ctx, double* out, void* stream)
+{
+    if (!ctx || !out) return RR_ERR_ARG;
+    if (!ctx->st.kmom) return RR_ERR_STATE;
+    const int nr = ctx->bundle.nx * ctx->bundle.ny;
+    return from_cuda(launch_moments(nr, ctx->st.kacc, ctx->st.kmom, ctx->st.bacc, ctx->st.bmom, out,
+                                    (cudaStream_t)stream));
+}
+
+rr_status rr_source_kappa(const double* m_end, const double* m_k, int64_t nrays, double chi_k, double* kappa,
+                          double* kappa_born, void* stream)
+{
+    if (!m_end || !kappa || nrays < 1 || !is_finite(chi_k) || !(chi_k > 0)) return RR_ERR_ARG;
+    return from_cuda(launch_source_kappa(m_end, m_k, (long long)nrays, chi_k, kappa, kappa_born,
+                                         (cudaStream_t)stream));
+}
+
 rr_status rr_step_count(rr_ctx* ctx, int32_t* n)
 {
     if (!ctx || !n) return RR_ERR_ARG;
@@ -328,7 +358,7 @@ rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkap
     if (!dL_dkappa && !dL_dkborn) return RR_ERR_ARG;
     if (step < 0 || step >= (int32_t)ctx->log.size()) return RR_ERR_STATE;
     const StepRecord& r = ctx->log[(size_t)step];
-    if (r.amr) return RR_ERR_STATE;
+    if (r.amr || (ctx->bundle.flags & RR_SOURCE_MOMENTS)) return RR_ERR_STATE;
     // the records pointer is not read by the adjoint (it needs geometry only)
     TraceArgs a = make_trace_args(ctx, &r.grid, grad_rec, r.chi_a, r.chi_b, r.scale, r.a_step);
     AdjArgs g;

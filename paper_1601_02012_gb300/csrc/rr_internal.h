@@ -20,8 +20,10 @@ struct RayState {
     double* dir = nullptr;      // 3 per ray: n_hat (Eq. raypos), FP64
     float4* dirh = nullptr;     // n_hat rounded to FP32 (x, y, z, 0)
     float4* dirl = nullptr;     // n_hat - dirh rounded to FP32 (float-float low parts)
-    float2* kacc = nullptr;     // kappa accumulated across steps, float-float (hi, lo)
-    float2* bacc = nullptr;     // Born kappa, float-float
+    float2* kacc = nullptr;     // kappa accumulated across steps, float-float (hi, lo); A moment (moments form)
+    float2* bacc = nullptr;     // Born kappa, float-float; Born A moment (moments form)
+    float2* kmom = nullptr;     // moments form only: B moment of kappa, float-float
+    float2* bmom = nullptr;     // moments form only: B moment of Born kappa
     uint32_t* nseg = nullptr;   // non-empty segments since reset
     uint32_t* err = nullptr;    // device error word
     unsigned long long* total = nullptr;  // segment total written by finalize
@@ -68,6 +70,8 @@ struct TraceArgs {
     const float4* dirl;
     float2* kacc;
     float2* bacc;
+    float2* kmom;               // B moments (moments form), else unused
+    float2* bmom;
     uint32_t* nseg;
     uint32_t* err;
     float sch, scl;             // scale (multiplies the kappa step sum), float-float
@@ -105,8 +109,10 @@ cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4*
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
+// Forms of the FP32 walk's sums.
+enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2 };
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
-                         bool plain_sums = false);
+                         int form = kFormKahan);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
 int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
 dim3 tile_grid(const TileCfg& t, int nx, int ny);
@@ -116,7 +122,12 @@ cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int inter
 cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
                                  cudaStream_t s);
 cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
-                            double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s);
+                            double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s,
+                            const float2* kmom = nullptr, const float2* bmom = nullptr, double chi_s = 0.0);
+cudaError_t launch_moments(int nrays, const float2* kacc, const float2* kmom, const float2* bacc, const float2* bmom,
+                           double* out, cudaStream_t s);
+cudaError_t launch_source_kappa(const double* m_end, const double* m_k, long long nrays, double chi_k, double* kappa,
+                                double* kborn, cudaStream_t s);
 
 // The step geometry and a context's state pointers as the kernels take them.
 TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,

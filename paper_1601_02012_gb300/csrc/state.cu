@@ -1,4 +1,5 @@
-// Ray directions (Eq. txty, Eq. raypos) and the finalize pass (maps in rayid order).
+// Ray directions (Eq. txty, Eq. raypos), the finalize pass (maps in rayid order)
+// and the source-redshift moments (Eqs. Isources, Isources1).
 #include "rr_internal.h"
 
 namespace rr {
@@ -32,15 +33,20 @@ __global__ void init_directions_kernel(int nx, int ny, double fov_x, double fov_
     dirl[rid] = make_float4((float)(n0 - (double)h0), (float)(n1 - (double)h1), (float)(n2 - (double)h2), 0.f);
 }
 
+__device__ __forceinline__ double ff(float2 v) { return (double)v.x + (double)v.y; }
+
+// Maps from the accumulators; for the moments form (kmom, bmom not null)
+// kappa = A - B / chi_s per channel (Eq. Isources).
 __global__ void finalize_kernel(int nrays, const float2* __restrict__ kacc, const float2* __restrict__ bacc,
                                 const uint32_t* __restrict__ nseg, double* out_kappa, double* out_kborn,
-                                unsigned long long* total)
+                                unsigned long long* total, const float2* __restrict__ kmom,
+                                const float2* __restrict__ bmom, double inv_chi_s)
 {
     unsigned long long local = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nrays;
          i += (long long)gridDim.x * blockDim.x) {
-        if (out_kappa) out_kappa[i] = (double)kacc[i].x + (double)kacc[i].y;
-        if (out_kborn) out_kborn[i] = (double)bacc[i].x + (double)bacc[i].y;
+        if (out_kappa) out_kappa[i] = kmom ? ff(kacc[i]) - ff(kmom[i]) * inv_chi_s : ff(kacc[i]);
+        if (out_kborn) out_kborn[i] = bmom ? ff(bacc[i]) - ff(bmom[i]) * inv_chi_s : ff(bacc[i]);
         local += nseg[i];
     }
 #pragma unroll
@@ -48,7 +54,53 @@ __global__ void finalize_kernel(int nrays, const float2* __restrict__ kacc, cons
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(total, local);
 }
 
+// The four moments (A_kappa, B_kappa, A_born, B_born) as FP64 rows.
+__global__ void moments_kernel(int nrays, const float2* __restrict__ kacc, const float2* __restrict__ kmom,
+                               const float2* __restrict__ bacc, const float2* __restrict__ bmom, double* out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrays) return;
+    out[i] = ff(kacc[i]);
+    out[nrays + i] = ff(kmom[i]);
+    out[2LL * nrays + i] = ff(bacc[i]);
+    out[3LL * nrays + i] = ff(bmom[i]);
+}
+
+// kappa for sources at chi_k from the moments at the end and at chi_k
+// (Eqs. Isources, Isources1): A(chi_k) = A_end - A_k, B(chi_k) = B_end - B_k.
+__global__ void source_kappa_kernel(const double* __restrict__ m_end, const double* __restrict__ m_k,
+                                    long long nrays, double inv_chi_k, double* kappa, double* kborn)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrays) return;
+    double a = m_end[i], b = m_end[nrays + i], ab = m_end[2 * nrays + i], bb = m_end[3 * nrays + i];
+    if (m_k) {
+        a -= m_k[i];
+        b -= m_k[nrays + i];
+        ab -= m_k[2 * nrays + i];
+        bb -= m_k[3 * nrays + i];
+    }
+    kappa[i] = a - b * inv_chi_k;
+    if (kborn) kborn[i] = ab - bb * inv_chi_k;
+}
+
 }  // namespace
+
+cudaError_t launch_moments(int nrays, const float2* kacc, const float2* kmom, const float2* bacc, const float2* bmom,
+                           double* out, cudaStream_t s)
+{
+    const int nt = 256;
+    moments_kernel<<<(unsigned)(((long long)nrays + nt - 1) / nt), nt, 0, s>>>(nrays, kacc, kmom, bacc, bmom, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_kappa(const double* m_end, const double* m_k, long long nrays, double chi_k, double* kappa,
+                                double* kborn, cudaStream_t s)
+{
+    const int nt = 256;
+    source_kappa_kernel<<<(unsigned)((nrays + nt - 1) / nt), nt, 0, s>>>(m_end, m_k, nrays, 1.0 / chi_k, kappa, kborn);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s)
 {
@@ -60,7 +112,8 @@ cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4*
 }
 
 cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
-                            double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s)
+                            double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s,
+                            const float2* kmom, const float2* bmom, double chi_s)
 {
     cudaError_t e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -72,7 +125,8 @@ cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, c
     const long long cap = (long long)(sms > 0 ? sms : 1) * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    finalize_kernel<<<(unsigned)blocks, nt, 0, s>>>(nrays, kacc, bacc, nseg, out_kappa, out_kborn, total);
+    finalize_kernel<<<(unsigned)blocks, nt, 0, s>>>(nrays, kacc, bacc, nseg, out_kappa, out_kborn, total, kmom, bmom,
+                                                    (kmom && chi_s > 0) ? 1.0 / chi_s : 0.0);
     return cudaGetLastError();
 }
 

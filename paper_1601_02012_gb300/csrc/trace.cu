@@ -34,9 +34,12 @@ namespace rr {
 namespace {
 
 // One ray over one step. INTERP: RR_NGP or RR_TRILINEAR. R: float
-// (compensated FP32 walk) or double (plain FP64 walk). PLAIN (FP32 only):
-// uncompensated FP32 sums within and across steps, for comparison.
-template <int INTERP, class R, bool PLAIN = false>
+// (compensated FP32 walk) or double (plain FP64 walk). FORM (FP32 only):
+// kFormKahan (default), kFormPlain (uncompensated FP32 sums within and across
+// steps, for comparison) or kFormMoments (the moments A = int chi Q and
+// B = int chi^2 Q of Eq. Isources instead of kappa: the kernel g becomes chi
+// and chi^2, i.e. (G0, G1, G2) = (chi_A, -1, 0) and (chi_A^2, -2 chi_A, 1)).
+template <int INTERP, class R, int FORM = kFormKahan>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
     constexpr bool F64 = sizeof(R) == 8;
@@ -53,6 +56,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 
     // per-step sums of (kappa, Born kappa): packed Kahan pairs (FP32) or FP64
     Acc2 s2;
+    Acc2 s2m;   // moments form: the B moments
     Acc<R> sk, sb;
     uint32_t cnt = 0;
     int iter = 0;
@@ -151,13 +155,24 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         }
 
         if (t > tend * eps_rel) {
-            if constexpr (!F64) {
+            if constexpr (!F64 && FORM == kFormMoments) {
+                const float chiA = chiA0 - sig;
+                if (INTERP == RR_TRILINEAR) {
+                    float2 e2[4];
+                    line_cubic2(q2, bc2(u[0]), bc2(u[1]), bc2(u[2]), bc2(v[0]), bc2(v[1]), bc2(v[2]), e2);
+                    s2.add(dot_kernel(e2, t, chiA, -1.f, 0.f));
+                    s2m.add(dot_kernel(e2, t, chiA * chiA, -2.f * chiA, 1.f));
+                } else {
+                    s2.add(segment_ngp(q2[0], t, chiA, -1.f, 0.f));
+                    s2m.add(segment_ngp(q2[0], t, chiA * chiA, -2.f * chiA, 1.f));
+                }
+            } else if constexpr (!F64) {
                 float G0, G1, G2;
                 kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
                 const float2 x = INTERP == RR_TRILINEAR
                                      ? segment_trilinear(q2, u[0], u[1], u[2], v[0], v[1], v[2], t, G0, G1, G2)
                                      : segment_ngp(q2[0], t, G0, G1, G2);
-                if constexpr (PLAIN) s2.s = __fadd2_rn(s2.s, x);
+                if constexpr (FORM == kFormPlain) s2.s = __fadd2_rn(s2.s, x);
                 else s2.add(x);
             } else {
                 // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
@@ -231,7 +246,15 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     }
     if (overflow) atomicOr(A.err, kErrStepLimit);
     if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
-    if constexpr (PLAIN) {
+    if constexpr (FORM == kFormMoments) {
+        float mh, ml;
+        if (!s2m.finite()) atomicOr(A.err, kErrNonFinite);
+        two_sum(s2m.s.x, -s2m.c.x, mh, ml);
+        A.kmom[rid] = ff_mul_add(A.kmom[rid], mh, ml, A.sch, A.scl);
+        two_sum(s2m.s.y, -s2m.c.y, mh, ml);
+        A.bmom[rid] = ff_mul_add(A.bmom[rid], mh, ml, A.bsh, A.bsl);
+    }
+    if constexpr (FORM == kFormPlain) {
         // plain FP32 across steps too: the high word only
         A.kacc[rid] = make_float2(fmaf(sk.s, A.sch, A.kacc[rid].x), 0.f);
         A.bacc[rid] = make_float2(fmaf(sb.s, A.bsh, A.bacc[rid].x), 0.f);
@@ -247,12 +270,12 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 }
 
 
-template <int INTERP, class R, bool PLAIN = false>
+template <int INTERP, class R, int FORM = kFormKahan>
 __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, const TileCfg t)
 {
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
-    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, PLAIN>(A, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM>(A, ix, iy);
 }
 
 // Persistent work queue over the ray tiles of many bundles (lightcones): each
@@ -317,14 +340,19 @@ bool tile_ok(const TileCfg& t)
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
-                         bool plain_sums)
+                         int form)
 {
     if (!tile_ok(t)) return cudaErrorInvalidValue;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const int nt = 32 * t.bwx * t.bwy;
-    if (plain_sums && !fp64_dda) {
-        if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, true><<<grid, nt, 0, s>>>(a, t);
-        else trace_kernel<RR_NGP, float, true><<<grid, nt, 0, s>>>(a, t);
+    if (form == kFormPlain && !fp64_dda) {
+        if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, kFormPlain><<<grid, nt, 0, s>>>(a, t);
+        else trace_kernel<RR_NGP, float, kFormPlain><<<grid, nt, 0, s>>>(a, t);
+        return cudaGetLastError();
+    }
+    if (form == kFormMoments && !fp64_dda) {
+        if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
+        else trace_kernel<RR_NGP, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
         return cudaGetLastError();
     }
     if (interp == RR_TRILINEAR) {

@@ -171,20 +171,27 @@ __device__ __forceinline__ void kernel_coeffs(float t, float sig, float chiA0, f
     G2 = -ichis;
 }
 
-__device__ __forceinline__ float2 segment_trilinear(const float2 q[8], float u0, float u1, float u2, float v0,
-                                                    float v1, float v2, float t, float G0, float G1, float G2)
+// sum_N e_{N-1} J_N for the cubic e (pair channels) and the quadratic kernel
+// G0 + G1 s + G2 s^2 over [0, t]
+__device__ __forceinline__ float2 dot_kernel(const float2 e2[4], float t, float G0, float G1, float G2)
 {
     const float t2 = t * t;
     const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
     const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
     const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
     const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
-    float2 e2[4];
-    line_cubic2(q, bc2(u0), bc2(u1), bc2(u2), bc2(v0), bc2(v1), bc2(v2), e2);
     float2 x = __fmul2_rn(e2[0], bc2(J1));
     x = __ffma2_rn(e2[1], bc2(J2), x);
     x = __ffma2_rn(e2[2], bc2(J3), x);
     return __ffma2_rn(e2[3], bc2(J4), x);
+}
+
+__device__ __forceinline__ float2 segment_trilinear(const float2 q[8], float u0, float u1, float u2, float v0,
+                                                    float v1, float v2, float t, float G0, float G1, float G2)
+{
+    float2 e2[4];
+    line_cubic2(q, bc2(u0), bc2(u1), bc2(u2), bc2(v0), bc2(v1), bc2(v2), e2);
+    return dot_kernel(e2, t, G0, G1, G2);
 }
 
 __device__ __forceinline__ float2 segment_ngp(float2 q, float t, float G0, float G1, float G2)

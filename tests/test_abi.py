@@ -129,3 +129,16 @@ def test_amr_plan_validation_is_host_side(rr):
     assert lib.rr_amr_sizes(None, None, None, None) == rr.RR_ERR_ARG
     assert lib.rr_amr_tidal(None, C.c_void_p(16), 0, C.c_void_p(16), None, None, None) == rr.RR_ERR_ARG
     assert lib.rr_amr_trace_step(None, None, C.c_void_p(16), 1.0, 0.0, 1.0, 1.0, None) == rr.RR_ERR_ARG
+
+
+def test_source_kappa_validation_is_host_side(rr):
+    lib = rr.load()
+    assert lib.rr_source_kappa(None, None, 4, 1.0, C.c_void_p(16), None, None) == rr.RR_ERR_ARG
+    assert lib.rr_source_kappa(C.c_void_p(16), None, 0, 1.0, C.c_void_p(16), None, None) == rr.RR_ERR_ARG
+    assert lib.rr_source_kappa(C.c_void_p(16), None, 4, 0.0, C.c_void_p(16), None, None) == rr.RR_ERR_ARG
+    assert lib.rr_moments(None, C.c_void_p(16), None) == rr.RR_ERR_ARG
+    good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
+    h = C.c_void_p()
+    for flags in (rr.RR_SOURCE_MOMENTS | rr.RR_FP64_DDA, rr.RR_SOURCE_MOMENTS | rr.RR_PLAIN_SUMS, 16):
+        good.flags = flags
+        assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG

@@ -64,9 +64,12 @@ def run_oracle(oracle_lib, phi, grid, bundle, steps, delta=None, rids=None):
 
 @pytest.mark.parametrize("where", ["vertices", "centres"])
 @pytest.mark.parametrize("with_delta", [False, True])
-def test_tidal_records(rrpkg, oracle_lib, where, with_delta):
+@pytest.mark.parametrize("shape", [(24, 20, 40), (2, 3, 5), (5, 2, 33)])
+def test_tidal_records(rrpkg, oracle_lib, where, with_delta, shape):
+    """Every record of the grid against the oracle's stencils and vertex means;
+    also grids smaller than a CTA's 8 x 32 block (indices wrap several times)."""
     import torch
-    g = synth.Grid((24, 20, 40), 48.0)
+    g = synth.Grid(shape, 2.0 * shape[0])
     phi = synth.random_field(g.n, 7, np.float32)
     delta = synth.random_field(g.n, 8, np.float32) if with_delta else None
     H, d = oracle_lib.fields(g, phi.astype(np.float64), None if delta is None else delta.astype(np.float64))
