@@ -57,6 +57,8 @@ def _L():
         _lib.ora_vertex_field.argtypes = [P, P, P, P]
         _lib.ora_trace_step.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
                                         P, P, P, P, C.c_int, P, C.c_long]
+        _lib.ora_trace_step_shear.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P, P, C.c_int, P,
+                                              C.c_long]
         _lib.ora_ray_segments.argtypes = [P, P, C.c_long, C.c_double, C.c_double, P, C.c_long]
         _lib.ora_ray_segments.restype = C.c_long
         _lib.ora_ray_direction.argtypes = [P, C.c_long, P, P]
@@ -169,6 +171,24 @@ def trace(bundle, grid, H, delta, steps, nthreads: int = 0, result: TraceResult 
         if rc != 0:
             raise ValueError("oracle: bad step interval")
     return res
+
+
+def trace_shear(bundle, grid, H, steps, nthreads: int = 0, rids=None):
+    """The shear (gamma1, gamma2) of the bundle over the given steps (Eqs.
+    gamma1, gamma2), per ray in rayid order or in the order of ``rids``."""
+    H = _f64(H)
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
+    g1 = np.zeros(nr, np.float64)
+    g2 = np.zeros(nr, np.float64)
+    b, g = _bundle(bundle), _grid(grid)
+    for st in steps:
+        rc = _L().ora_trace_step_shear(C.byref(b), C.byref(g), _ptr(H), float(st.chi_a), float(st.chi_b),
+                                       float(st.scale), _ptr(g1), _ptr(g2), int(nthreads), _ptr(ids),
+                                       0 if ids is None else len(ids))
+        if rc != 0:
+            raise ValueError("oracle: bad step interval")
+    return g1, g2
 
 
 def ray_segments(bundle, grid, rid: int, chi_a: float, chi_b: float) -> np.ndarray:

@@ -23,6 +23,8 @@
  *     alpha_i of Eq. (trilinear_coef) and the d_N of Appendix B;
  *   - the density-based Born convergence, the first term of Eq. (kappa2),
  *     with a held constant over the step;
+ *   - the shear (Eqs. gamma1, gamma2) by the same walk and integrals with
+ *     Q = n1n1 - n2n2 and Q = 2 n1n2 (Eq. n1n2 in its orthonormal reading);
  *   - Neumaier-compensated per-ray sums;
  *   - the exact adjoint of all of the above (the transpose of a linear map),
  *     built segment by segment from unit-vector evaluations of the same
@@ -140,7 +142,7 @@ static void vertex_value(const ora_grid* g, const double* H, const double* delta
             for (int dk = -1; dk <= 0; ++dk) {
                 size_t ci = cell_index(g, vi + di, vj + dj, vk + dk);
                 for (int c = 0; c < 6; ++c) out[c] += H[6 * ci + c];
-                out[6] += delta[ci];
+                if (delta) out[6] += delta[ci];
             }
     for (int c = 0; c < 7; ++c) out[c] *= 0.125;
 }
@@ -192,6 +194,37 @@ static void kappa_weights(double th, double sp, double cp, double w[6])
     w[3] = -s2p + s2p * ct * ct;
     w[4] = -cp * s2t;
     w[5] = -sp * s2t;
+}
+
+/* Shear (Eqs. gamma1, gamma2). gamma1 takes Q = n1n1 - n2n2 with the printed
+ * Eqs. (n1n1), (n2n2). gamma2 takes Q = 2 n1n2; the printed Eq. (n1n2) equals
+ * e_phi^T H e_theta / sin(theta) for the orthonormal e_phi = (-sin ph, cos ph,
+ * 0), e_theta = (cos th cos ph, cos th sin ph, -sin th) that Eqs. (n1n1),
+ * (n2n2) use, and diverges at theta -> 0; the reading taken is the orthonormal
+ * one, Eq. (n1n2) times sin(theta):
+ *   n1n2 = cos th [cos ph sin ph (yy - xx) + (cos^2 ph - sin^2 ph) xy]
+ *          + sin th (sin ph xz - cos ph yz). */
+static void gamma1_weights(double th, double sp, double cp, double w[6])
+{
+    double st = sin(th), ct = cos(th);
+    double s2p = 2.0 * sp * cp, s2t = sin(2.0 * th);
+    w[0] = sp * sp - cp * cp * ct * ct;
+    w[1] = cp * cp - sp * sp * ct * ct;
+    w[2] = -st * st;
+    w[3] = -s2p - s2p * ct * ct;
+    w[4] = cp * s2t;
+    w[5] = sp * s2t;
+}
+
+static void gamma2_weights(double th, double sp, double cp, double w[6])
+{
+    double st = sin(th), ct = cos(th);
+    w[0] = -2.0 * ct * cp * sp;
+    w[1] = 2.0 * ct * cp * sp;
+    w[2] = 0.0;
+    w[3] = 2.0 * ct * (cp * cp - sp * sp);
+    w[4] = 2.0 * st * sp;
+    w[5] = -2.0 * st * cp;
 }
 
 static double project(const double w[6], const double* Hc)
@@ -310,7 +343,9 @@ static double ic_trilinear(const double Q[8], double a, double b, double c, doub
 typedef struct {
     double th, st, ct, sp, cp;
     double n[3];
-    double w[6];
+    double w[6];      /* Q weights of the first channel: kappa, or gamma1 */
+    double w2[6];     /* second channel when it is a shear: gamma2 */
+    int shear;        /* 0: (kappa, Born); 1: (gamma1, gamma2) */
 } ray_geo;
 
 static void make_ray(const ora_bundle* b, long ix, long iy, ray_geo* r)
@@ -322,6 +357,15 @@ static void make_ray(const ora_bundle* b, long ix, long iy, ray_geo* r)
     r->n[1] = r->st * r->sp;
     r->n[2] = r->ct;
     kappa_weights(r->th, r->sp, r->cp, r->w);
+    r->shear = 0;
+}
+
+static void make_shear_ray(const ora_bundle* b, long ix, long iy, ray_geo* r)
+{
+    make_ray(b, ix, iy, r);
+    gamma1_weights(r->th, r->sp, r->cp, r->w);
+    gamma2_weights(r->th, r->sp, r->cp, r->w2);
+    r->shear = 1;
 }
 
 /* Callback-free walk: for each non-empty segment, evaluate the two integrands
@@ -383,7 +427,7 @@ static void cell_vertex_Q(const field_t* F, const ray_geo* r, const long cell[3]
         vertex_value(F->g, F->H, F->delta, cell[0] + (v & 1), cell[1] + ((v >> 1) & 1),
                      cell[2] + ((v >> 2) & 1), val);
         Qk[v] = project(r->w, val);
-        Qb[v] = bpref * val[6];
+        Qb[v] = r->shear ? project(r->w2, val) : bpref * val[6];
     }
 }
 
@@ -393,10 +437,34 @@ static void cell_vertex_Q(const field_t* F, const ray_geo* r, const long cell[3]
  * (first term of Eq. kappa2, a constant during the step).
  * kappa, kborn, sum_r are accumulated (+=); nseg is accumulated.
  */
+static int trace_step(const ora_bundle* b, const ora_grid* g, const double* H, const double* delta,
+                      double chi_a, double chi_b, double scale, double a_step,
+                      double* kappa, double* kborn, int64_t* nseg, double* sum_r, int nthreads,
+                      const int64_t* rids, long nrids, int shear);
+
 int ora_trace_step(const ora_bundle* b, const ora_grid* g, const double* H, const double* delta,
                    double chi_a, double chi_b, double scale, double a_step,
                    double* kappa, double* kborn, int64_t* nseg, double* sum_r, int nthreads,
                    const int64_t* rids, long nrids)
+{
+    return trace_step(b, g, H, delta, chi_a, chi_b, scale, a_step, kappa, kborn, nseg, sum_r, nthreads, rids,
+                      nrids, 0);
+}
+
+/* The shear (Eqs. gamma1, gamma2) of one step: gamma1 and gamma2 are
+ * accumulated like kappa, with Q = n1n1 - n2n2 and Q = 2 n1n2 (see
+ * gamma2_weights for the reading of Eq. n1n2). */
+int ora_trace_step_shear(const ora_bundle* b, const ora_grid* g, const double* H, double chi_a, double chi_b,
+                         double scale, double* gamma1, double* gamma2, int nthreads, const int64_t* rids,
+                         long nrids)
+{
+    return trace_step(b, g, H, NULL, chi_a, chi_b, scale, 1.0, gamma1, gamma2, NULL, NULL, nthreads, rids, nrids, 1);
+}
+
+static int trace_step(const ora_bundle* b, const ora_grid* g, const double* H, const double* delta,
+                      double chi_a, double chi_b, double scale, double a_step,
+                      double* kappa, double* kborn, int64_t* nseg, double* sum_r, int nthreads,
+                      const int64_t* rids, long nrids, int shear)
 {
     if (!(chi_a > chi_b) || chi_b < 0.0) return -1;
     field_t F = {g, b, H, delta};
@@ -411,7 +479,8 @@ int ora_trace_step(const ora_bundle* b, const ora_grid* g, const double* H, cons
     for (long slot = 0; slot < nr; ++slot) {
         const long rid = rids ? (long)rids[slot] : slot;
         ray_geo r;
-        make_ray(b, rid % b->nx, rid / b->nx, &r); /* Eq. (rayid), x fastest */
+        if (shear) make_shear_ray(b, rid % b->nx, rid / b->nx, &r);
+        else make_ray(b, rid % b->nx, rid / b->nx, &r); /* Eq. (rayid), x fastest */
         segment_t* S;
         long ns = walk(&F, &r, chi_a, chi_b, &S);
         neu_t sk = {0, 0}, sb = {0, 0}, sr = {0, 0};
@@ -421,7 +490,7 @@ int ora_trace_step(const ora_bundle* b, const ora_grid* g, const double* H, cons
             if (b->interp == 0) {
                 size_t ci = cell_index(g, sg->cell[0], sg->cell[1], sg->cell[2]);
                 double qk = project(r.w, H + 6 * ci);
-                double qb = bpref * delta[ci];
+                double qb = shear ? project(r.w2, H + 6 * ci) : bpref * delta[ci];
                 ik = ic_ngp(qk, sg->chiA, sg->chiB, b->chi_s);
                 ib = ic_ngp(qb, sg->chiA, sg->chiB, b->chi_s);
             } else {
