@@ -612,6 +612,51 @@ def _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush,
                     "before the timing); CUDA events, L2 flushed before each"}
 
 
+def _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, kappa_trace_ms, reps=3):
+    """Time the trace kernels of a pass in the shear form (kappa, Born kappa,
+    gamma1 and gamma2 of Eqs. gamma1, gamma2 in one walk) against those of the
+    default form (kappa_trace_ms, per pass); the shear form's kappa is checked
+    against the default form's."""
+    nst = len(steps)
+    trs = rrp.Tracer(w.bundle, shear=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+    ny, nx = w.bundle.ny, w.bundle.nx
+    k = torch.empty((ny, nx), dtype=torch.float64, device=phi.device)
+    kb = torch.empty_like(k)
+
+    def shear_pass(timed_kernels):
+        rrp.rr_reset(trs.ctx, stream)
+        for i, st in enumerate(steps):
+            rrp.rr_tidal_tensor(gd, phi, None, rec, trs.where, bboxes[i], stream)
+            if timed_kernels:
+                ev[i][0].record(stream)
+            rrp.rr_trace_step(trs.ctx, gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            if timed_kernels:
+                ev[i][1].record(stream)
+        rrp.rr_finalize(trs.ctx, k, kb, stream)
+
+    with torch.cuda.stream(stream):
+        shear_pass(False)
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            shear_pass(True)
+            ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        segs = trs.segments()
+        g1, g2 = trs.shear(stream=stream)
+        torch.cuda.synchronize()
+        rms_g = [float(torch.sqrt(torch.mean(x * x))) for x in (g1, g2)]
+    trs.close()
+    t = sum(ms) / reps
+    return {"trace_ms_per_pass": t, "kappa_only_trace_ms_per_pass": kappa_trace_ms,
+            "cost_vs_kappa_only": t / kappa_trace_ms, "segments_per_s": segs / (t / 1e3),
+            "gather_gbs": segs * BYTES_PER_SEGMENT / (t / 1e3) / 1e9,
+            "rms_gamma1": rms_g[0], "rms_gamma2": rms_g[1], "kappa": k, "kborn": kb,
+            "note": "trace kernels of one pass in the shear form (kappa, Born kappa, gamma1, gamma2 "
+                    "in one walk), CUDA events per launch, L2 flushed before each pass, mean of "
+                    f"{reps} passes; the default form's per-pass trace time beside it"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -785,8 +830,17 @@ def main():
         # Isources1): the moments form with snapshots at step boundaries, against
         # one ordinary pass per source distance
         sources = None
+        shear = None
         if world == 1:
             sources = _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush)
+            # the shear in the same walk (Eqs. gamma1, gamma2)
+            shear = _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush,
+                                trace_ms / args.steps)
+            one_pass()
+            ks, kbs = shear.pop("kappa"), shear.pop("kborn")
+            rms = float(torch.sqrt(torch.mean(kappa * kappa)))
+            shear["kappa_max_over_rms_vs_default_form"] = float((ks - kappa).abs().max()) / rms
+            del ks, kbs
 
     if rank != 0:
         dist.barrier()
@@ -833,6 +887,7 @@ def main():
                 "h2d_bytes_per_step": int(phi_host.nbytes),
                 "d2h_bytes_per_step": int(k_host.numel() * 8 * 2)},
         "source_redshifts": sources,
+        "shear": shear,
         "gpu_launches": args.steps * (2 * nst + 1),
         "clocks": clocks,
         "trace_src": h,

@@ -56,12 +56,17 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
                                across steps: only to measure what the compensation
                                buys (rr_create / rr_trace_step only; not with
                                RR_FP64_DDA, batches, AMR or the no-allocation call) */
-       RR_SOURCE_MOMENTS = 8 }; /* rays accumulate the two moments of Eq. (Isources),
+       RR_SOURCE_MOMENTS = 8,   /* rays accumulate the two moments of Eq. (Isources),
                                A = int chi Q dchi and B = int chi^2 Q dchi (for kappa
                                and Born kappa) instead of kappa itself, so that kappa
                                for any source distance chi_k <= chi_s follows from one
                                pass (rr_moments, rr_source_kappa); FP32 walk with
                                compensated sums; rr_create / rr_trace_step only */
+       RR_SHEAR = 16 };     /* rays also accumulate the shear gamma1, gamma2 (Eqs.
+                               gamma1, gamma2) in the same walk as kappa (rr_shear);
+                               FP32 walk with compensated sums; rr_create /
+                               rr_trace_step only; not with RR_FP64_DDA,
+                               RR_PLAIN_SUMS or RR_SOURCE_MOMENTS */
 
 /* rr_tidal_tensor: where the records are evaluated. */
 enum { RR_AT_VERTICES = 0,  /* mean of the 8 cells sharing each vertex (Sec. 2.7); trilinear */
@@ -82,7 +87,7 @@ typedef struct {
     double obs[3];        /* observer position in box coordinates, Mpc/h */
     double chi_s;         /* comoving distance of the sources, > 0 */
     int32_t interp;       /* RR_NGP or RR_TRILINEAR */
-    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS */
+    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR */
 } rr_bundle_desc;
 
 /* A uniform grid of n[0] x n[1] x n[2] cubic cells of size h = box / n[0]. */
@@ -193,6 +198,21 @@ rr_status rr_moments(rr_ctx* ctx, double* out, void* stream);
  * null pointers, nrays < 1 or chi_k <= 0. */
 rr_status rr_source_kappa(const double* m_end, const double* m_k, int64_t nrays, double chi_k, double* kappa,
                           double* kappa_born, void* stream);
+
+/*
+ * Shear (contexts created with RR_SHEAR; Eqs. gamma1, gamma2, Sec. 3.4). Per
+ * ray, in the transverse frame e_phi = (-sin phi, cos phi, 0), e_theta =
+ * (cos theta cos phi, cos theta sin phi, -sin theta) of its direction (phi = 0
+ * for the ray along the z axis), the walk integrates the lensing kernel times
+ * Q1 = e_phi.H.e_phi - e_theta.H.e_theta (gamma1) and Q2 = 2 e_phi.H.e_theta
+ * (gamma2, Eq. n1n2 read in that orthonormal frame), H the tidal tensor of the
+ * records, with the field and kernel integrals of kappa (NGP or trilinear).
+ * gamma1 and gamma2 = device FP64 [ny*nx] each, rayid order, summed over the
+ * steps since create/reset with each step's scale (the kappa sum's factor).
+ * Asynchronous; RR_ERR_ARG on null pointers, RR_ERR_STATE for a context
+ * without RR_SHEAR.
+ */
+rr_status rr_shear(rr_ctx* ctx, double* gamma1, double* gamma2, void* stream);
 
 /* Synchronise `stream` and return the error word (as rr_finalize does),
  * without writing maps. */

@@ -15,10 +15,12 @@ from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, 
 
 from .batch import Batch  # noqa: E402
 from ._rr import rr_amr_create, rr_amr_destroy, rr_amr_sizes, rr_amr_tidal, rr_amr_trace_step  # noqa: E402
+from ._rr import RR_SHEAR, rr_shear  # noqa: E402
 
 __all__ = [
-    "Batch", "AmrMesh", "source_kappa", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal", "rr_amr_trace_step",
-    "Tracer", "trace_kappa", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
+    "Batch", "AmrMesh", "source_kappa", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal",
+    "rr_amr_trace_step", "RR_SHEAR", "rr_shear",
+    "Tracer", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
     "rr_trace_backward", "TraceKappa", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
@@ -47,13 +49,15 @@ class Tracer:
     (0 NGP / 1 trilinear) and periodic attributes. fp64_dda: the plain FP64
     walk; plain_sums: the FP32 walk without compensated sums (for comparison);
     moments: accumulate the source-redshift moments of Eq. (Isources) (see
-    ``moments()`` and ``source_kappa``).
+    ``moments()`` and ``source_kappa``); shear: also accumulate the shear
+    (gamma1, gamma2) of Eqs. gamma1, gamma2 in the same walk (see ``shear()``).
     """
 
-    def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False):
+    def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False,
+                 shear: bool = False):
         _rr.load()
         self.bundle = bundle
-        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums, moments=moments)
+        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums, moments=moments, shear=shear)
         self.ctx = rr_create(self.desc)
         self.where = RR_AT_VERTICES if int(self.desc.interp) == RR_TRILINEAR else RR_AT_CENTRES
 
@@ -105,6 +109,18 @@ class Tracer:
             out = torch.empty((4, ny, nx), dtype=torch.float64, device="cuda")
         _rr.rr_moments(self.ctx, out, stream)
         return out
+
+    def shear(self, gamma1=None, gamma2=None, stream=None):
+        """The shear maps so far: FP64 (gamma1, gamma2), each [ny, nx] on the
+        device (contexts created with shear=True)."""
+        import torch
+        ny, nx = int(self.desc.ny), int(self.desc.nx)
+        if gamma1 is None:
+            gamma1 = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+        if gamma2 is None:
+            gamma2 = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+        _rr.rr_shear(self.ctx, gamma1, gamma2, stream)
+        return gamma1, gamma2
 
     def amr_step(self, mesh, leaf_rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):
         """One step over an adaptive mesh (``AmrMesh``) from its leaf records."""
@@ -208,6 +224,24 @@ def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=
             tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
         k, kb = tr.finalize(stream=stream)
         return k, kb, tr.segments()
+    finally:
+        tr.close()
+
+
+def trace_shear(phi, grid, bundle, steps, delta=None, footprint=True, stream=None):
+    """As ``trace_kappa``, with the shear of Eqs. gamma1, gamma2 accumulated in
+    the same walk: returns the FP64 maps (kappa, kappa_born, gamma1, gamma2),
+    each [ny, nx], and the number of cell segments."""
+    tr = Tracer(bundle, shear=True)
+    try:
+        rec = record_buffer(grid, device=phi.device)
+        for st in steps:
+            bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
+            tr.tidal(grid, phi, rec, delta=delta, bbox=bbox, stream=stream)
+            tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
+        k, kb = tr.finalize(stream=stream)
+        g1, g2 = tr.shear(stream=stream)
+        return k, kb, g1, g2, tr.segments()
     finally:
         tr.close()
 

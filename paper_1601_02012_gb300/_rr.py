@@ -32,6 +32,7 @@ RR_PERIODIC = 1
 RR_FP64_DDA = 2
 RR_PLAIN_SUMS = 4
 RR_SOURCE_MOMENTS = 8
+RR_SHEAR = 16
 RR_AT_VERTICES = 0
 RR_AT_CENTRES = 1
 
@@ -97,6 +98,7 @@ def load() -> C.CDLL:
             "rr_batch_get_tuning": ([P, P], C.c_int),
             "rr_batch_autotune": ([P, I32, C.POINTER(C.c_float), P], C.c_int),
             "rr_moments": ([P, P, P], C.c_int),
+            "rr_shear": ([P, P, P, P], C.c_int),
             "rr_source_kappa": ([P, P, C.c_int64, D, P, P, P], C.c_int),
             "rr_amr_create": ([P, P, P, C.POINTER(C.c_void_p)], C.c_int),
             "rr_amr_destroy": ([P], C.c_int),
@@ -139,7 +141,8 @@ def _stream(s):
     return C.c_void_p(s.cuda_stream)
 
 
-def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False) -> rr_bundle_desc:
+def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False,
+                shear: bool = False) -> rr_bundle_desc:
     """rr_bundle_desc from any object with nx, ny, fov_x, fov_y, obs, chi_s,
     interp and periodic attributes."""
     d = rr_bundle_desc()
@@ -156,6 +159,8 @@ def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bo
         flags |= RR_PLAIN_SUMS
     if moments:
         flags |= RR_SOURCE_MOMENTS
+    if shear:
+        flags |= RR_SHEAR
     d.flags = flags
     return d
 
@@ -227,6 +232,11 @@ def rr_segment_count(ctx, per_ray=None, stream=None) -> int:
 def rr_moments(ctx, out, stream=None) -> None:
     """out: device FP64 [4, ny*nx] (A_kappa, B_kappa, A_born, B_born)."""
     _check(load().rr_moments(ctx, _ptr(out), _stream(stream)), "rr_moments")
+
+
+def rr_shear(ctx, gamma1, gamma2, stream=None) -> None:
+    """gamma1, gamma2: device FP64 [ny*nx] each."""
+    _check(load().rr_shear(ctx, _ptr(gamma1), _ptr(gamma2), _stream(stream)), "rr_shear")
 
 
 def rr_source_kappa(m_end, m_k, nrays: int, chi_k: float, kappa, kappa_born=None, stream=None) -> None:

@@ -27,9 +27,10 @@ rr_status check_bundle(const rr_bundle_desc* b)
         if (!is_finite(b->obs[a])) return RR_ERR_ARG;
     if (!is_finite(b->chi_s) || !(b->chi_s > 0)) return RR_ERR_ARG;
     if (b->interp != RR_NGP && b->interp != RR_TRILINEAR) return RR_ERR_ARG;
-    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS)) return RR_ERR_ARG;
+    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR)) return RR_ERR_ARG;
     if ((b->flags & RR_PLAIN_SUMS) && (b->flags & (RR_FP64_DDA | RR_SOURCE_MOMENTS))) return RR_ERR_ARG;
     if ((b->flags & RR_SOURCE_MOMENTS) && (b->flags & RR_FP64_DDA)) return RR_ERR_ARG;
+    if ((b->flags & RR_SHEAR) && (b->flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS))) return RR_ERR_ARG;
     return RR_OK;
 }
 
@@ -66,6 +67,8 @@ void free_state(RayState& s)
     cudaFree(s.bacc);
     cudaFree(s.kmom);
     cudaFree(s.bmom);
+    cudaFree(s.g1acc);
+    cudaFree(s.g2acc);
     cudaFree(s.nseg);
     cudaFree(s.err);
     cudaFree(s.total);
@@ -108,6 +111,8 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     a.bacc = ctx->st.bacc;
     a.kmom = ctx->st.kmom;
     a.bmom = ctx->st.bmom;
+    a.g1acc = ctx->st.g1acc;
+    a.g2acc = ctx->st.g2acc;
     a.nseg = ctx->st.nseg;
     a.err = ctx->st.err;
     split_ff(scale, a.sch, a.scl);
@@ -185,6 +190,12 @@ rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
         if (e == cudaSuccess) e = cudaMemset(s.kmom, 0, nr * sizeof(float2));
         if (e == cudaSuccess) e = cudaMemset(s.bmom, 0, nr * sizeof(float2));
     }
+    if (bundle->flags & RR_SHEAR) {
+        if (e == cudaSuccess) e = cudaMalloc(&s.g1acc, nr * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&s.g2acc, nr * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemset(s.g1acc, 0, nr * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemset(s.g2acc, 0, nr * sizeof(float2));
+    }
     if (e == cudaSuccess) e = cudaMemset(s.nseg, 0, nr * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.err, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.total, 0, sizeof(unsigned long long));
@@ -221,6 +232,8 @@ rr_status rr_reset(rr_ctx* ctx, void* stream)
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.bacc, 0, nr * sizeof(float2), s);
     if (e == cudaSuccess && ctx->st.kmom) e = cudaMemsetAsync(ctx->st.kmom, 0, nr * sizeof(float2), s);
     if (e == cudaSuccess && ctx->st.bmom) e = cudaMemsetAsync(ctx->st.bmom, 0, nr * sizeof(float2), s);
+    if (e == cudaSuccess && ctx->st.g1acc) e = cudaMemsetAsync(ctx->st.g1acc, 0, nr * sizeof(float2), s);
+    if (e == cudaSuccess && ctx->st.g2acc) e = cudaMemsetAsync(ctx->st.g2acc, 0, nr * sizeof(float2), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.nseg, 0, nr * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->st.err, 0, sizeof(uint32_t), s);
     ctx->log.clear();
@@ -283,7 +296,10 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     if (st != RR_OK) return st;
     const rr_bundle_desc& b = ctx->bundle;
     TraceArgs a = make_trace_args(ctx, grid, rec, chi_a, chi_b, scale, a_step);
-    const int form = (b.flags & RR_SOURCE_MOMENTS) ? kFormMoments : ((b.flags & RR_PLAIN_SUMS) ? kFormPlain : kFormKahan);
+    const int form = (b.flags & RR_SOURCE_MOMENTS) ? kFormMoments
+                     : (b.flags & RR_PLAIN_SUMS)   ? kFormPlain
+                     : (b.flags & RR_SHEAR)        ? kFormShear
+                                                   : kFormKahan;
     cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{}, form);
     if (e != cudaSuccess) return from_cuda(e);
     ctx->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
@@ -334,6 +350,14 @@ rr_status rr_moments(rr_ctx* ctx, double* out, void* stream)
     const int nr = ctx->bundle.nx * ctx->bundle.ny;
     return from_cuda(launch_moments(nr, ctx->st.kacc, ctx->st.kmom, ctx->st.bacc, ctx->st.bmom, out,
                                     (cudaStream_t)stream));
+}
+
+rr_status rr_shear(rr_ctx* ctx, double* gamma1, double* gamma2, void* stream)
+{
+    if (!ctx || !gamma1 || !gamma2) return RR_ERR_ARG;
+    if (!ctx->st.g1acc) return RR_ERR_STATE;
+    const int nr = ctx->bundle.nx * ctx->bundle.ny;
+    return from_cuda(launch_shear_out(nr, ctx->st.g1acc, ctx->st.g2acc, gamma1, gamma2, (cudaStream_t)stream));
 }
 
 rr_status rr_source_kappa(const double* m_end, const double* m_k, int64_t nrays, double chi_k, double* kappa,

@@ -133,6 +133,8 @@ extern "C" rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const r
     a.bacc = bacc;
     a.kmom = nullptr;
     a.bmom = nullptr;
+    a.g1acc = nullptr;
+    a.g2acc = nullptr;
     a.nseg = nseg;
     a.err = err;
     split_ff(scale, a.sch, a.scl);

@@ -24,6 +24,8 @@ struct RayState {
     float2* bacc = nullptr;     // Born kappa, float-float; Born A moment (moments form)
     float2* kmom = nullptr;     // moments form only: B moment of kappa, float-float
     float2* bmom = nullptr;     // moments form only: B moment of Born kappa
+    float2* g1acc = nullptr;    // shear form only: gamma1, float-float
+    float2* g2acc = nullptr;    // shear form only: gamma2, float-float
     uint32_t* nseg = nullptr;   // non-empty segments since reset
     uint32_t* err = nullptr;    // device error word
     unsigned long long* total = nullptr;  // segment total written by finalize
@@ -72,6 +74,8 @@ struct TraceArgs {
     float2* bacc;
     float2* kmom;               // B moments (moments form), else unused
     float2* bmom;
+    float2* g1acc;              // gamma1, gamma2 (shear form), else unused
+    float2* g2acc;
     uint32_t* nseg;
     uint32_t* err;
     float sch, scl;             // scale (multiplies the kappa step sum), float-float
@@ -110,7 +114,7 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
                          const int32_t* bbox, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
 // Forms of the FP32 walk's sums.
-enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2 };
+enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2, kFormShear = 3 };
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
                          int form = kFormKahan);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
@@ -126,6 +130,8 @@ cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, c
                             const float2* kmom = nullptr, const float2* bmom = nullptr, double chi_s = 0.0);
 cudaError_t launch_moments(int nrays, const float2* kacc, const float2* kmom, const float2* bacc, const float2* bmom,
                            double* out, cudaStream_t s);
+cudaError_t launch_shear_out(int nrays, const float2* g1acc, const float2* g2acc, double* gamma1, double* gamma2,
+                             cudaStream_t s);
 cudaError_t launch_source_kappa(const double* m_end, const double* m_k, long long nrays, double chi_k, double* kappa,
                                 double* kborn, cudaStream_t s);
 

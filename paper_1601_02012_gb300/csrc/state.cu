@@ -1,5 +1,5 @@
-// Ray directions (Eq. txty, Eq. raypos), the finalize pass (maps in rayid order)
-// and the source-redshift moments (Eqs. Isources, Isources1).
+// Ray directions (Eq. txty, Eq. raypos), the finalize pass (maps in rayid order),
+// the source-redshift moments (Eqs. Isources, Isources1) and the shear maps.
 #include "rr_internal.h"
 
 namespace rr {
@@ -66,6 +66,16 @@ __global__ void moments_kernel(int nrays, const float2* __restrict__ kacc, const
     out[3LL * nrays + i] = ff(bmom[i]);
 }
 
+// The shear maps from their float-float accumulators.
+__global__ void shear_out_kernel(int nrays, const float2* __restrict__ g1acc, const float2* __restrict__ g2acc,
+                                 double* gamma1, double* gamma2)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrays) return;
+    gamma1[i] = ff(g1acc[i]);
+    gamma2[i] = ff(g2acc[i]);
+}
+
 // kappa for sources at chi_k from the moments at the end and at chi_k
 // (Eqs. Isources, Isources1): A(chi_k) = A_end - A_k, B(chi_k) = B_end - B_k.
 __global__ void source_kappa_kernel(const double* __restrict__ m_end, const double* __restrict__ m_k,
@@ -91,6 +101,14 @@ cudaError_t launch_moments(int nrays, const float2* kacc, const float2* kmom, co
 {
     const int nt = 256;
     moments_kernel<<<(unsigned)(((long long)nrays + nt - 1) / nt), nt, 0, s>>>(nrays, kacc, kmom, bacc, bmom, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shear_out(int nrays, const float2* g1acc, const float2* g2acc, double* gamma1, double* gamma2,
+                             cudaStream_t s)
+{
+    const int nt = 256;
+    shear_out_kernel<<<(unsigned)(((long long)nrays + nt - 1) / nt), nt, 0, s>>>(nrays, g1acc, g2acc, gamma1, gamma2);
     return cudaGetLastError();
 }
 

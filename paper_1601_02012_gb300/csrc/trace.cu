@@ -30,19 +30,43 @@
 //    accumulator (~48 bits).
 #include "walk.cuh"
 
+#ifndef SHEAR_NREG
+#define SHEAR_NREG 168
+#endif
+
 namespace rr {
 namespace {
+
+// Crossing face e of the mirrored cell: the 4 corners on the exit side become
+// the entry side and the 4 new corner values p come in on the exit side.
+__device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], int e)
+{
+    if (e == 0) {
+        q[0] = q[1]; q[2] = q[3]; q[4] = q[5]; q[6] = q[7];
+        q[1] = p[0]; q[3] = p[1]; q[5] = p[2]; q[7] = p[3];
+    } else if (e == 1) {
+        q[0] = q[2]; q[1] = q[3]; q[4] = q[6]; q[5] = q[7];
+        q[2] = p[0]; q[3] = p[1]; q[6] = p[2]; q[7] = p[3];
+    } else {
+        q[0] = q[4]; q[1] = q[5]; q[2] = q[6]; q[3] = q[7];
+        q[4] = p[0]; q[5] = p[1]; q[6] = p[2]; q[7] = p[3];
+    }
+}
 
 // One ray over one step. INTERP: RR_NGP or RR_TRILINEAR. R: float
 // (compensated FP32 walk) or double (plain FP64 walk). FORM (FP32 only):
 // kFormKahan (default), kFormPlain (uncompensated FP32 sums within and across
-// steps, for comparison) or kFormMoments (the moments A = int chi Q and
+// steps, for comparison), kFormMoments (the moments A = int chi Q and
 // B = int chi^2 Q of Eq. Isources instead of kappa: the kernel g becomes chi
-// and chi^2, i.e. (G0, G1, G2) = (chi_A, -1, 0) and (chi_A^2, -2 chi_A, 1)).
+// and chi^2, i.e. (G0, G1, G2) = (chi_A, -1, 0) and (chi_A^2, -2 chi_A, 1)) or
+// kFormShear (kappa and Born kappa, and the shear pair (gamma1, gamma2) of Eqs.
+// gamma1, gamma2 from a second projection of the same records, carried as a
+// second packed pair through the same segments).
 template <int INTERP, class R, int FORM = kFormKahan>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
     constexpr bool F64 = sizeof(R) == 8;
+    constexpr bool SH = !F64 && FORM == kFormShear;
     const long long rid = (long long)iy * A.nx + ix;
     const int nn[3] = {A.n0, A.n1, A.n2};
     RayRange rg;
@@ -56,7 +80,9 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 
     // per-step sums of (kappa, Born kappa): packed Kahan pairs (FP32) or FP64
     Acc2 s2;
-    Acc2 s2m;   // moments form: the B moments
+    Acc2 s2m;   // moments form: the B moments; shear form: (gamma1, gamma2)
+    float w1[6], w2[6];   // shear form: the Q weights of gamma1, gamma2
+    if constexpr (SH) shear_weights(A.dirh[rid], w1, w2);
     Acc<R> sk, sb;
     uint32_t cnt = 0;
     int iter = 0;
@@ -85,8 +111,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     iter = 0;
 
     // Field cache: (projected kappa value, delta) at the 8 mirrored corners
-    // (trilinear) or at the cell centre (NGP).
+    // (trilinear) or at the cell centre (NGP); the shear form also keeps
+    // (gamma1, gamma2) values there.
     float2 q2[8];
+    float2 g2[SH ? 8 : 1];
     if (INTERP == RR_TRILINEAR) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -95,10 +123,12 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
             const int gz = (m & 4) ? vhi[2] : vlo[2];
             const Rec r = load_rec(A.rec, gx * sx + gy * sy + gz);
             q2[m] = make_float2(project(w, r), r.b.z);
+            if constexpr (SH) g2[m] = make_float2(project(w1, r), project(w2, r));
         }
     } else {
         const Rec r = load_rec(A.rec, c[0] * sx + c[1] * sy + c[2]);
         q2[0] = make_float2(project(w, r), r.b.z);
+        if constexpr (SH) g2[0] = make_float2(project(w1, r), project(w2, r));
     }
 
     R sig = 0;                       // path from the sub-step start to the segment entry
@@ -174,6 +204,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                                      : segment_ngp(q2[0], t, G0, G1, G2);
                 if constexpr (FORM == kFormPlain) s2.s = __fadd2_rn(s2.s, x);
                 else s2.add(x);
+                if constexpr (SH)
+                    s2m.add(INTERP == RR_TRILINEAR
+                                ? segment_trilinear(g2, u[0], u[1], u[2], v[0], v[1], v[2], t, G0, G1, G2)
+                                : segment_ngp(g2[0], t, G0, G1, G2));
             } else {
                 // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
                 const R chiA = chiA0 - sig;
@@ -219,18 +253,15 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
             float2 p2[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) p2[r] = make_float2(project(w, nr[r]), nr[r].b.z);
-            if (e == 0) {
-                q2[0] = q2[1]; q2[2] = q2[3]; q2[4] = q2[5]; q2[6] = q2[7];
-                q2[1] = p2[0]; q2[3] = p2[1]; q2[5] = p2[2]; q2[7] = p2[3];
-            } else if (e == 1) {
-                q2[0] = q2[2]; q2[1] = q2[3]; q2[4] = q2[6]; q2[5] = q2[7];
-                q2[2] = p2[0]; q2[3] = p2[1]; q2[6] = p2[2]; q2[7] = p2[3];
-            } else {
-                q2[0] = q2[4]; q2[1] = q2[5]; q2[2] = q2[6]; q2[3] = q2[7];
-                q2[4] = p2[0]; q2[5] = p2[1]; q2[6] = p2[2]; q2[7] = p2[3];
+            shift_corners(q2, p2, e);
+            if constexpr (SH) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) p2[r] = make_float2(project(w1, nr[r]), project(w2, nr[r]));
+                shift_corners(g2, p2, e);
             }
         } else {
             q2[0] = make_float2(project(w, nr[0]), nr[0].b.z);
+            if constexpr (SH) g2[0] = make_float2(project(w1, nr[0]), project(w2, nr[0]));
         }
         if (++iter > max_iter) {
             overflow = true;
@@ -246,6 +277,14 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     }
     if (overflow) atomicOr(A.err, kErrStepLimit);
     if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
+    if constexpr (SH) {
+        float gh, gl;
+        if (!s2m.finite()) atomicOr(A.err, kErrNonFinite);
+        two_sum(s2m.s.x, -s2m.c.x, gh, gl);
+        A.g1acc[rid] = ff_mul_add(A.g1acc[rid], gh, gl, A.sch, A.scl);
+        two_sum(s2m.s.y, -s2m.c.y, gh, gl);
+        A.g2acc[rid] = ff_mul_add(A.g2acc[rid], gh, gl, A.sch, A.scl);
+    }
     if constexpr (FORM == kFormMoments) {
         float mh, ml;
         if (!s2m.finite()) atomicOr(A.err, kErrNonFinite);
@@ -276,6 +315,17 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, con
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
     if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM>(A, ix, iy);
+}
+
+// The shear form carries a second field cache and accumulator pair: it gets
+// more registers per thread than the 128 of two resident 256-thread blocks.
+template <int INTERP>
+__global__ void __maxnreg__(SHEAR_NREG) trace_shear_kernel(const TraceArgs A,
+                                                            const TileCfg t)
+{
+    int ix, iy;
+    tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, float, kFormShear>(A, ix, iy);
 }
 
 // Persistent work queue over the ray tiles of many bundles (lightcones): each
@@ -353,6 +403,11 @@ cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStre
     if (form == kFormMoments && !fp64_dda) {
         if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
         else trace_kernel<RR_NGP, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
+        return cudaGetLastError();
+    }
+    if (form == kFormShear && !fp64_dda) {
+        if (interp == RR_TRILINEAR) trace_shear_kernel<RR_TRILINEAR><<<grid, nt, 0, s>>>(a, t);
+        else trace_shear_kernel<RR_NGP><<<grid, nt, 0, s>>>(a, t);
         return cudaGetLastError();
     }
     if (interp == RR_TRILINEAR) {

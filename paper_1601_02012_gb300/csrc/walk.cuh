@@ -200,6 +200,37 @@ __device__ __forceinline__ float2 segment_ngp(float2 q, float t, float G0, float
     return __fmul2_rn(q, bc2(J1));
 }
 
+// Q weights of the shear (Eqs. gamma1, gamma2) for the direction n = (sin th
+// cos ph, sin th sin ph, cos th): with the transverse frame e_phi = (-sin ph,
+// cos ph, 0), e_theta = (cos th cos ph, cos th sin ph, -sin th) (ph = 0 on the
+// z axis), gamma1 takes Q = e_phi.H.e_phi - e_theta.H.e_theta = w1 . H and
+// gamma2 Q = 2 e_phi.H.e_theta = w2 . H, H = (xx, yy, zz, xy, xz, yz).
+// sin th = |(n_x, n_y)| and (cos ph, sin ph) = (n_x, n_y) / sin th keep full
+// relative precision however close the ray is to the axis.
+__device__ __forceinline__ void shear_weights(float4 n, float w1[6], float w2[6])
+{
+    const float st = sqrtf(fmaf(n.x, n.x, n.y * n.y));
+    float cp = 1.f, sp = 0.f;
+    if (st > 0.f) {
+        cp = n.x / st;
+        sp = n.y / st;
+    }
+    const float fx = -sp, fy = cp;                          // e_phi
+    const float tx = n.z * cp, ty = n.z * sp, tz = -st;     // e_theta
+    w1[0] = fx * fx - tx * tx;
+    w1[1] = fy * fy - ty * ty;
+    w1[2] = -tz * tz;
+    w1[3] = 2.f * (fx * fy - tx * ty);
+    w1[4] = -2.f * tx * tz;
+    w1[5] = -2.f * ty * tz;
+    w2[0] = 2.f * fx * tx;
+    w2[1] = 2.f * fy * ty;
+    w2[2] = 0.f;
+    w2[3] = 2.f * (fx * ty + fy * tx);
+    w2[4] = 2.f * fx * tz;
+    w2[5] = 2.f * fy * tz;
+}
+
 // float of an integer in [0, 2^23) and back, exact, on the FP32/integer pipes
 // (the bit pattern of 2^23 + i), instead of the conversion unit
 __device__ __forceinline__ float i2f_exact(int i) { return __int_as_float(0x4B000000 | i) - 8388608.f; }

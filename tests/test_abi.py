@@ -139,6 +139,16 @@ def test_source_kappa_validation_is_host_side(rr):
     assert lib.rr_moments(None, C.c_void_p(16), None) == rr.RR_ERR_ARG
     good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
     h = C.c_void_p()
-    for flags in (rr.RR_SOURCE_MOMENTS | rr.RR_FP64_DDA, rr.RR_SOURCE_MOMENTS | rr.RR_PLAIN_SUMS, 16):
+    for flags in (rr.RR_SOURCE_MOMENTS | rr.RR_FP64_DDA, rr.RR_SOURCE_MOMENTS | rr.RR_PLAIN_SUMS, 32):
         good.flags = flags
+        assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG
+
+
+def test_shear_validation_is_host_side(rr):
+    lib = rr.load()
+    assert lib.rr_shear(None, C.c_void_p(16), C.c_void_p(16), None) == rr.RR_ERR_ARG
+    good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
+    h = C.c_void_p()
+    for other in (rr.RR_FP64_DDA, rr.RR_PLAIN_SUMS, rr.RR_SOURCE_MOMENTS):
+        good.flags = rr.RR_SHEAR | other
         assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG
