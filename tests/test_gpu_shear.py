@@ -104,9 +104,12 @@ def test_shear_form_keeps_kappa(rrp):
 
 def test_gaussian_lens_shear(rrp, oracle_lib):
     """Sec. 4 (the Gaussian lens, trilinear, 40 x 40 deg, z_s = 0.95) on a
-    128 x 128 map at 64^3: gamma1 and gamma2 match the oracle, and gamma2 on the
-    map's two mirror lines (the central row and column) vanishes to FP32
-    rounding of the symmetric field."""
+    129 x 129 map at 64^3. The shear of a lens axisymmetric about the central
+    ray is tangential, i.e. pure gamma1 in the polar frame: gamma2 is only the
+    cubic mesh's anisotropy (~1e-3 of gamma1), so its errors are measured in
+    units of the shear's own scale, rms(gamma1). gamma2 vanishes to FP32
+    rounding on the map's four mirror lines (central row and column, both
+    diagonals), which are symmetry planes of the lens and of the mesh."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "gaussian_e1.json")) as f:
@@ -120,16 +123,20 @@ def test_gaussian_lens_shear(rrp, oracle_lib):
     steps = [synth.Step(E1["gamma1_chi_max"], 0.0, 1.0, 1.0)]
     got = _gpu(rrp, phi, g, b, steps)
     want = _oracle(oracle_lib, phi, g, b, steps)
-    for x, y, what in zip(got[:4], want, ("kappa", "kborn", "gamma1", "gamma2")):
+    for x, y, what in zip(got[:3], want[:3], ("kappa", "kborn", "gamma1")):
         if what == "kborn":
             continue   # no density here
         e_inf, e_2 = _err(x, y)
         assert e_inf <= TOL and e_2 <= TOL, (what, e_inf, e_2)
+    rms1 = math.sqrt(float(np.mean(want[2] ** 2)))
+    assert np.abs(got[3] - want[3]).max() <= TOL * rms1
+    assert np.abs(want[3]).max() <= 2e-3 * np.abs(want[2]).max()
     g1 = got[2].reshape(nr, nr)
     g2 = got[3].reshape(nr, nr)
     peak = np.abs(g1).max()
-    assert np.abs(g2[nr // 2, :]).max() <= 1e-5 * peak
-    assert np.abs(g2[:, nr // 2]).max() <= 1e-5 * peak
+    i = np.arange(nr)
+    for line in (g2[nr // 2, :], g2[:, nr // 2], g2[i, i], g2[i, nr - 1 - i]):
+        assert np.abs(line).max() <= 1e-5 * peak
 
 
 def test_shear_at_production_size_sampled(rrp, oracle_lib):
