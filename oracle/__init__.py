@@ -59,6 +59,9 @@ def _L():
                                         P, P, P, P, C.c_int, P, C.c_long]
         _lib.ora_trace_step_shear.argtypes = [P, P, P, C.c_double, C.c_double, C.c_double, P, P, C.c_int, P,
                                               C.c_long]
+        _lib.ora_fields_grad.argtypes = [P, P, P]
+        _lib.ora_trace_step_method_a.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                 P, P, C.c_int, P, C.c_long]
         _lib.ora_ray_segments.argtypes = [P, P, C.c_long, C.c_double, C.c_double, P, C.c_long]
         _lib.ora_ray_segments.restype = C.c_long
         _lib.ora_ray_direction.argtypes = [P, C.c_long, P, P]
@@ -189,6 +192,36 @@ def trace_shear(bundle, grid, H, steps, nthreads: int = 0, rids=None):
         if rc != 0:
             raise ValueError("oracle: bad step interval")
     return g1, g2
+
+
+def fields_grad(grid, phi) -> np.ndarray:
+    """d_a Phi at cell centres, [n0, n1, n2, 3], central differences."""
+    g = _grid(grid)
+    phi = _f64(phi)
+    G = np.zeros(tuple(int(x) for x in grid.n) + (3,), np.float64)
+    _L().ora_fields_grad(C.byref(g), _ptr(phi), _ptr(G))
+    return G
+
+
+def trace_method_a(bundle, grid, G, delta, steps, nthreads: int = 0, rids=None):
+    """Method A (Eq. kappa2) over the given steps: (kgrad, kborn) per ray, in
+    rayid order or in the order of ``rids``; kgrad holds the gradient integral
+    and the steps' surface terms, kborn the density term, and the Method A
+    convergence is their sum."""
+    G = _f64(G)
+    d = _f64(delta)
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
+    kg = np.zeros(nr, np.float64)
+    kb = np.zeros(nr, np.float64)
+    b, g = _bundle(bundle), _grid(grid)
+    for st in steps:
+        rc = _L().ora_trace_step_method_a(C.byref(b), C.byref(g), _ptr(G), _ptr(d), float(st.chi_a),
+                                          float(st.chi_b), float(st.scale), float(st.a), _ptr(kg), _ptr(kb),
+                                          int(nthreads), _ptr(ids), 0 if ids is None else len(ids))
+        if rc != 0:
+            raise ValueError("oracle: bad step interval")
+    return kg, kb
 
 
 def ray_segments(bundle, grid, rid: int, chi_a: float, chi_b: float) -> np.ndarray:

@@ -25,6 +25,10 @@
  *     with a held constant over the step;
  *   - the shear (Eqs. gamma1, gamma2) by the same walk and integrals with
  *     Q = n1n1 - n2n2 and Q = 2 n1n2 (Eq. n1n2 in its orthonormal reading);
+ *   - Method A (Eq. kappa2): d_a Phi at centres by central differences,
+ *     the integral of (1 - 2 chi/chi_s) n.grad(Phi) by Eq. (Icfinal) with
+ *     that kernel, and each step's surface term g n.grad(Phi) at the ends of
+ *     the traced interval (Eq. 2nterm);
  *   - Neumaier-compensated per-ray sums;
  *   - the exact adjoint of all of the above (the transpose of a linear map),
  *     built segment by segment from unit-vector evaluations of the same
@@ -141,7 +145,8 @@ static void vertex_value(const ora_grid* g, const double* H, const double* delta
         for (int dj = -1; dj <= 0; ++dj)
             for (int dk = -1; dk <= 0; ++dk) {
                 size_t ci = cell_index(g, vi + di, vj + dj, vk + dk);
-                for (int c = 0; c < 6; ++c) out[c] += H[6 * ci + c];
+                if (H)
+                    for (int c = 0; c < 6; ++c) out[c] += H[6 * ci + c];
                 if (delta) out[6] += delta[ci];
             }
     for (int c = 0; c < 7; ++c) out[c] *= 0.125;
@@ -296,12 +301,12 @@ static double ic_ngp(double Qc, double chiA, double chiB, double chis)
     return Qc / chis * (0.5 * chis * (chiA * chiA - chiB * chiB) - (chiA * chiA * chiA - chiB * chiB * chiB) / 3.0);
 }
 
-/* Eq. (Iclensing) for the trilinear field given by the vertex values
- * Q[0..7] = Q_1..Q_8 at P_1..P_8, P_{1 + i + 2j + 4k} = P_1 + (i, j, k) h.
- * (a, b, c) = A - P_1; st, ct, sp, cp are the ray's sin/cos of theta, phi. */
-static double ic_trilinear(const double Q[8], double a, double b, double c, double h,
-                           double st, double ct, double sp, double cp,
-                           double chiA, double chiB, double chis)
+/* The d_N of Eq. (Qcompact) (Appendix B) for the trilinear field of the
+ * vertex values Q[0..7] = Q_1..Q_8 at P_1..P_8, P_{1 + i + 2j + 4k} = P_1 +
+ * (i, j, k) h, along the ray from A, (a, b, c) = A - P_1; st, ct, sp, cp are
+ * the ray's sin/cos of theta, phi. */
+static void dn_coeffs(const double Q[8], double a, double b, double c, double h,
+                      double st, double ct, double sp, double cp, double d[4])
 {
     /* Eq. (trilinear_coef) */
     double al1 = Q[0];
@@ -315,7 +320,6 @@ static double ic_trilinear(const double Q[8], double a, double b, double c, doub
     double h2 = h * h, h3 = h2 * h;
     double nx = st * cp, ny = st * sp, nz = ct;
     /* Appendix B, the d_N of Eq. (Qcompact) */
-    double d[4];
     d[0] = al1 + (al2 * a + al3 * b + al4 * c) / h + (al5 * a * b + al6 * b * c + al7 * a * c) / h2
            + al8 * a * b * c / h3;
     d[1] = (al2 * nx + al3 * ny + al4 * nz) / h
@@ -324,6 +328,17 @@ static double ic_trilinear(const double Q[8], double a, double b, double c, doub
     d[2] = (al5 * nx * ny + al7 * nx * nz + al6 * ny * nz) / h2
            + (al8 * a * ny * nz + al8 * b * nx * nz + al8 * c * nx * ny) / h3;
     d[3] = al8 / h3 * nx * ny * nz;
+}
+
+/* Eq. (Iclensing) for the trilinear field given by the vertex values
+ * Q[0..7] = Q_1..Q_8 at P_1..P_8, P_{1 + i + 2j + 4k} = P_1 + (i, j, k) h.
+ * (a, b, c) = A - P_1; st, ct, sp, cp are the ray's sin/cos of theta, phi. */
+static double ic_trilinear(const double Q[8], double a, double b, double c, double h,
+                           double st, double ct, double sp, double cp,
+                           double chiA, double chiB, double chis)
+{
+    double d[4];
+    dn_coeffs(Q, a, b, c, h, st, ct, sp, cp, d);
     /* Eq. (Iclensing), R = chi_B - chi_A */
     double R = chiB - chiA;
     double sum = 0.0;
@@ -508,6 +523,140 @@ static int trace_step(const ora_bundle* b, const ora_grid* g, const double* H, c
         kborn[slot] += scale * neu_val(&sb);
         if (nseg) nseg[slot] += ns;
         if (sum_r) sum_r[slot] += neu_val(&sr);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Method A (Sec. 3.5, Eq. kappa2): the gradient and surface terms           */
+/* ------------------------------------------------------------------------- */
+
+/* d_a Phi at cell centres by central differences, (Phi_{+1} - Phi_{-1}) / (2h)
+ * along each axis, periodic indexing (the field whose negative is the force
+ * of the N-body code). G: 3 per cell, (x, y, z). */
+int ora_fields_grad(const ora_grid* g, const double* phi, double* G)
+{
+    const double ih = 1.0 / grid_h(g);
+    for (long i = 0; i < g->n[0]; ++i)
+        for (long j = 0; j < g->n[1]; ++j)
+            for (long k = 0; k < g->n[2]; ++k) {
+                double* out = G + 3 * cell_index(g, i, j, k);
+                out[0] = 0.5 * ih * (phi[cell_index(g, i + 1, j, k)] - phi[cell_index(g, i - 1, j, k)]);
+                out[1] = 0.5 * ih * (phi[cell_index(g, i, j + 1, k)] - phi[cell_index(g, i, j - 1, k)]);
+                out[2] = 0.5 * ih * (phi[cell_index(g, i, j, k + 1)] - phi[cell_index(g, i, j, k - 1)]);
+            }
+    return 0;
+}
+
+/* Q = n . grad Phi (the radial derivative of Eq. kappa2) at vertex (vi, vj,
+ * vk): the mean of the 8 cells sharing it (Sec. 2.7). */
+static double vertex_radial_grad(const ora_grid* g, const double* G, const double n[3], long vi, long vj, long vk)
+{
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int di = -1; di <= 0; ++di)
+        for (int dj = -1; dj <= 0; ++dj)
+            for (int dk = -1; dk <= 0; ++dk) {
+                const double* gc = G + 3 * cell_index(g, vi + di, vj + dj, vk + dk);
+                for (int a = 0; a < 3; ++a) v[a] += gc[a];
+            }
+    return 0.125 * (n[0] * v[0] + n[1] * v[1] + n[2] * v[2]);
+}
+
+/* Eq. (Icfinal) with the kernel K = d g / d chi = 1 - 2 chi / chi_s: with
+ * R = chi_B - chi_A, int_{chi_B}^{chi_A} K (chi - chi_A)^{N-1} dchi =
+ * -(1 - 2 chi_A / chi_s) R^N / N + (2 / chi_s) R^{N+1} / (N + 1). */
+static double ic_dg_trilinear(const double d[4], double chiA, double chiB, double chis)
+{
+    double R = chiB - chiA;
+    double sum = 0.0;
+    for (int N = 1; N <= 4; ++N) {
+        double RN = pow(R, N);
+        sum += d[N - 1] * (-(1.0 - 2.0 * chiA / chis) * RN / N + 2.0 / chis * RN * R / (N + 1));
+    }
+    return sum;
+}
+
+/* Eq. (Icngp) with K = 1 - 2 chi / chi_s: Q_c [(chi_A - chi_B) - (chi_A^2 - chi_B^2) / chi_s] */
+static double ic_dg_ngp(double Qc, double chiA, double chiB, double chis)
+{
+    return Qc * ((chiA - chiB) - (chiA * chiA - chiB * chiB) / chis);
+}
+
+static double lensing_g(double chi, double chis) { return (chis - chi) * chi / chis; }
+
+/*
+ * Method A's step terms for every ray: the second term of Eq. (kappa2),
+ * int K n.grad(Phi) dchi with K = 1 - 2 chi / chi_s, and the step's part of
+ * the surface term, g n.grad(Phi) evaluated at the start (chi_i) and the end
+ * (chi_f) of the part of the ray traced in the step (Eq. 2nterm), entering
+ * with a minus sign: kgrad += scale * (sum of cell integrals - [g Q](chi_i)
+ * + [g Q](chi_f)). The first term (density, Born) is accumulated into kborn as
+ * in ora_trace_step; the full Method A convergence is kgrad + kborn (the
+ * d/dt term is dropped, as in the paper). The field at the two end points:
+ * trilinear, the cubic of Eq. (Qcompact) of the first (last) cell at its own
+ * start (at the end point); NGP, that cell's centre value.
+ */
+int ora_trace_step_method_a(const ora_bundle* b, const ora_grid* g, const double* G, const double* delta,
+                            double chi_a, double chi_b, double scale, double a_step,
+                            double* kgrad, double* kborn, int nthreads, const int64_t* rids, long nrids)
+{
+    if (!(chi_a > chi_b) || chi_b < 0.0) return -1;
+    field_t F = {g, b, NULL, delta};
+    const double bpref = 1.5 * g->omega_m * ORA_H0_OVER_C * ORA_H0_OVER_C / a_step;
+    const double h = grid_h(g);
+    const double chis = b->chi_s;
+    const long nr = rids ? nrids : (long)b->nx * b->ny;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (long slot = 0; slot < nr; ++slot) {
+        const long rid = rids ? (long)rids[slot] : slot;
+        ray_geo r;
+        make_ray(b, rid % b->nx, rid / b->nx, &r);
+        segment_t* S;
+        long ns = walk(&F, &r, chi_a, chi_b, &S);
+        neu_t sg_sum = {0, 0}, sb = {0, 0};
+        double q_start = 0.0, q_end = 0.0;
+        for (long s = 0; s < ns; ++s) {
+            const segment_t* sg = &S[s];
+            double ig, ib;
+            if (b->interp == 0) {
+                size_t ci = cell_index(g, sg->cell[0], sg->cell[1], sg->cell[2]);
+                const double* gc = G + 3 * ci;
+                double qc = r.n[0] * gc[0] + r.n[1] * gc[1] + r.n[2] * gc[2];
+                ig = ic_dg_ngp(qc, sg->chiA, sg->chiB, chis);
+                ib = ic_ngp(bpref * delta[ci], sg->chiA, sg->chiB, chis);
+                if (s == 0) q_start = qc;
+                if (s == ns - 1) q_end = qc;
+            } else {
+                double Qg[8], Qb[8], d[4];
+                for (int v = 0; v < 8; ++v) {
+                    long vi = sg->cell[0] + (v & 1), vj = sg->cell[1] + ((v >> 1) & 1), vk = sg->cell[2] + ((v >> 2) & 1);
+                    Qg[v] = vertex_radial_grad(g, G, r.n, vi, vj, vk);
+                    double val[7];
+                    vertex_value(g, NULL, delta, vi, vj, vk, val);
+                    Qb[v] = bpref * val[6];
+                }
+                dn_coeffs(Qg, sg->a, sg->b, sg->c, h, r.st, r.ct, r.sp, r.cp, d);
+                ig = ic_dg_trilinear(d, sg->chiA, sg->chiB, chis);
+                ib = ic_trilinear(Qb, sg->a, sg->b, sg->c, h, r.st, r.ct, r.sp, r.cp, sg->chiA, sg->chiB, chis);
+                if (s == 0) q_start = d[0];
+                if (s == ns - 1) {
+                    double R = S[ns - 1].chiB - sg->chiA;
+                    q_end = d[0] + R * (d[1] + R * (d[2] + R * d[3]));
+                }
+            }
+            neu_add(&sg_sum, ig);
+            neu_add(&sb, ib);
+        }
+        if (ns > 0) {
+            neu_add(&sg_sum, -lensing_g(S[0].chiA, chis) * q_start);
+            neu_add(&sg_sum, lensing_g(S[ns - 1].chiB, chis) * q_end);
+        }
+        free(S);
+        kgrad[slot] += scale * neu_val(&sg_sum);
+        kborn[slot] += scale * neu_val(&sb);
     }
     return 0;
 }
