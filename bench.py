@@ -657,6 +657,63 @@ def _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, kappa
                     f"{reps} passes; the default form's per-pass trace time beside it"}
 
 
+def _method_a_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, kappa_pass_ms, kappa, reps=3):
+    """Time a pass by Method A (Eq. kappa2: gradient records of 16 B per point
+    instead of the 32 B tidal records, the kernel dg/dchi and the surface
+    terms) against a pass by Method B (kappa_pass_ms); its kappa map is
+    compared with Method B's."""
+    nst = len(steps)
+    tra = rrp.Tracer(w.bundle, method_a=True)
+    reca = tra.record_buffer(w.grid, device=phi.device)
+    ev_r = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+    ev_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+    k = torch.empty_like(kappa)
+    kb = torch.empty_like(kappa)
+
+    def pass_a(timed):
+        rrp.rr_reset(tra.ctx, stream)
+        for i, st in enumerate(steps):
+            if timed:
+                ev_r[i][0].record(stream)
+            rrp.rr_gradient_records(gd, phi, None, reca, tra.where, bboxes[i], stream)
+            if timed:
+                ev_r[i][1].record(stream)
+                ev_t[i][0].record(stream)
+            rrp.rr_trace_step(tra.ctx, gd, reca, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            if timed:
+                ev_t[i][1].record(stream)
+        rrp.rr_finalize(tra.ctx, k, kb, stream)
+
+    with torch.cuda.stream(stream):
+        pass_a(False)
+        tot, rec_ms, tr_ms = [], 0.0, 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pass_a(True)
+            e1.record(stream)
+            e1.synchronize()
+            tot.append(e0.elapsed_time(e1))
+            rec_ms += sum(a.elapsed_time(b) for a, b in ev_r)
+            tr_ms += sum(a.elapsed_time(b) for a, b in ev_t)
+        segs = tra.segments()
+        rms = float(torch.sqrt(torch.mean(kappa * kappa)))
+        diff = float((k - kappa).abs().max()) / rms
+    tra.close()
+    del reca
+    t = sum(tot) / reps
+    return {"ms_per_pass": t, "method_b_ms_per_pass": kappa_pass_ms, "speedup_vs_method_b": kappa_pass_ms / t,
+            "trace_ms_per_pass": tr_ms / reps, "records_ms_per_pass": rec_ms / reps,
+            "segments_per_s": segs / (t / 1e3),
+            "gather_gbs": segs * 128 / (tr_ms / reps / 1e3) / 1e9,
+            "kappa_max_over_rms_vs_method_b": diff,
+            "note": "one pass by Method A (gradient records over each step's footprint, the walk with "
+                    "kernel dg/dchi and the per-step surface terms, finalize), CUDA events, L2 flushed "
+                    f"before each pass, mean of {reps}; 128 logical gather bytes per segment (8 x 16 B); "
+                    "the map differs from Method B's by the discretisation of the two formulations"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -831,6 +888,7 @@ def main():
         # one ordinary pass per source distance
         sources = None
         shear = None
+        method_a = None
         if world == 1:
             sources = _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush)
             # the shear in the same walk (Eqs. gamma1, gamma2)
@@ -841,6 +899,9 @@ def main():
             rms = float(torch.sqrt(torch.mean(kappa * kappa)))
             shear["kappa_max_over_rms_vs_default_form"] = float((ks - kappa).abs().max()) / rms
             del ks, kbs
+            # Method A (Eq. kappa2) in the same configuration
+            method_a = _method_a_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush,
+                                      total_ms / args.steps, kappa)
 
     if rank != 0:
         dist.barrier()
@@ -888,6 +949,7 @@ def main():
                 "d2h_bytes_per_step": int(k_host.numel() * 8 * 2)},
         "source_redshifts": sources,
         "shear": shear,
+        "method_a": method_a,
         "gpu_launches": args.steps * (2 * nst + 1),
         "clocks": clocks,
         "trace_src": h,

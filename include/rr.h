@@ -62,11 +62,21 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
                                for any source distance chi_k <= chi_s follows from one
                                pass (rr_moments, rr_source_kappa); FP32 walk with
                                compensated sums; rr_create / rr_trace_step only */
-       RR_SHEAR = 16 };     /* rays also accumulate the shear gamma1, gamma2 (Eqs.
+       RR_SHEAR = 16,       /* rays also accumulate the shear gamma1, gamma2 (Eqs.
                                gamma1, gamma2) in the same walk as kappa (rr_shear);
                                FP32 walk with compensated sums; rr_create /
                                rr_trace_step only; not with RR_FP64_DDA,
                                RR_PLAIN_SUMS or RR_SOURCE_MOMENTS */
+       RR_METHOD_A = 32 };  /* Method A (Eq. kappa2): rr_trace_step reads gradient
+                               records (rr_gradient_records) and accumulates the
+                               density term (kappa_born) and, separately, the
+                               integral of (1 - 2 chi/chi_s) n.grad(Phi) plus each
+                               step's surface term g n.grad(Phi) |_end - |_start
+                               of the traced interval (Eq. 2nterm); rr_finalize
+                               writes kappa = the sum of the three terms and
+                               kappa_born = the density term. FP32 walk with
+                               compensated sums; rr_create / rr_trace_step only;
+                               no adjoint; not with the other optional flags */
 
 /* rr_tidal_tensor: where the records are evaluated. */
 enum { RR_AT_VERTICES = 0,  /* mean of the 8 cells sharing each vertex (Sec. 2.7); trilinear */
@@ -87,7 +97,8 @@ typedef struct {
     double obs[3];        /* observer position in box coordinates, Mpc/h */
     double chi_s;         /* comoving distance of the sources, > 0 */
     int32_t interp;       /* RR_NGP or RR_TRILINEAR */
-    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR */
+    int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR |
+                             RR_METHOD_A */
 } rr_bundle_desc;
 
 /* A uniform grid of n[0] x n[1] x n[2] cubic cells of size h = box / n[0]. */
@@ -138,6 +149,19 @@ rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const floa
                           int32_t where, const int32_t* bbox, void* stream);
 
 /*
+ * Gradient records of Method A (Eq. kappa2, Sec. 3.5): d_a Phi by central
+ * differences (Phi_{+1} - Phi_{-1}) / (2h) at the cell centres (periodic),
+ * then records at the vertices (mean of the 8 cells, Sec. 2.7) or at the
+ * centres. Arguments as for rr_tidal_tensor, except
+ *   rec    device, n0*n1*n2 records of 4 floats (16 bytes, 16-byte aligned):
+ *          {d_x Phi, d_y Phi, d_z Phi, delta}, grad Phi in h/Mpc; delta given,
+ *          or (NULL) derived from the 7-point Laplacian as rr_tidal_tensor does.
+ * These are the records rr_trace_step reads for an RR_METHOD_A context.
+ */
+rr_status rr_gradient_records(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                              int32_t where, const int32_t* bbox, void* stream);
+
+/*
  * Host helper: a conservative box of vertex (or centre) indices {x0, x1, y0,
  * y1, z0, z1} that contains every point the bundle's rays can read while
  * tracing [chi_b, chi_a] (the footprint of one step, used to restrict
@@ -154,7 +178,9 @@ rr_status rr_footprint_bbox(const rr_bundle_desc* bundle, const rr_grid_desc* gr
  *   kappa_born += scale * sum_cells I_c with Q = 1.5 Omega_m (H0/c)^2 delta / a_step
  *                 (first term of Eq. kappa2, a held constant over the step).
  *   rec      records from rr_tidal_tensor (vertices for RR_TRILINEAR,
- *            centres for RR_NGP) covering every point the step reads.
+ *            centres for RR_NGP) covering every point the step reads; for
+ *            an RR_METHOD_A context, records from rr_gradient_records (the
+ *            kappa channel then follows Method A, see RR_METHOD_A).
  *   scale    multiplies every channel of the records (the field of this step
  *            is scale * stored field).
  * Requires chi_s >= chi_a > chi_b >= 0 and, after the first step since

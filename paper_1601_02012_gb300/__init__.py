@@ -16,15 +16,25 @@ from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, 
 from .batch import Batch  # noqa: E402
 from ._rr import rr_amr_create, rr_amr_destroy, rr_amr_sizes, rr_amr_tidal, rr_amr_trace_step  # noqa: E402
 from ._rr import RR_SHEAR, rr_shear  # noqa: E402
+from ._rr import RR_METHOD_A, rr_gradient_records  # noqa: E402
 
 __all__ = [
     "Batch", "AmrMesh", "source_kappa", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal",
-    "rr_amr_trace_step", "RR_SHEAR", "rr_shear",
+    "rr_amr_trace_step", "RR_SHEAR", "rr_shear", "RR_METHOD_A", "rr_gradient_records", "trace_method_a",
+    "gradient_buffer",
     "Tracer", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
     "rr_trace_backward", "TraceKappa", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
 ]
+
+
+def gradient_buffer(grid, device="cuda"):
+    """Uninitialised device buffer for n0*n1*n2 gradient records of 4 floats
+    (Method A)."""
+    import torch
+    n = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
+    return torch.empty((n, 4), dtype=torch.float32, device=device)
 
 
 def record_buffer(grid, device="cuda"):
@@ -50,14 +60,18 @@ class Tracer:
     walk; plain_sums: the FP32 walk without compensated sums (for comparison);
     moments: accumulate the source-redshift moments of Eq. (Isources) (see
     ``moments()`` and ``source_kappa``); shear: also accumulate the shear
-    (gamma1, gamma2) of Eqs. gamma1, gamma2 in the same walk (see ``shear()``).
+    (gamma1, gamma2) of Eqs. gamma1, gamma2 in the same walk (see ``shear()``);
+    method_a: kappa by Method A (Eq. kappa2) from gradient records
+    (``tidal`` then writes those, 4 floats per point).
     """
 
     def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False,
-                 shear: bool = False):
+                 shear: bool = False, method_a: bool = False):
         _rr.load()
         self.bundle = bundle
-        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums, moments=moments, shear=shear)
+        self.method_a = bool(method_a)
+        self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums, moments=moments, shear=shear,
+                                method_a=method_a)
         self.ctx = rr_create(self.desc)
         self.where = RR_AT_VERTICES if int(self.desc.interp) == RR_TRILINEAR else RR_AT_CENTRES
 
@@ -76,9 +90,18 @@ class Tracer:
         rr_reset(self.ctx, stream)
 
     def tidal(self, grid, phi, rec, delta=None, bbox=None, stream=None):
-        """rr_tidal_tensor into ``rec`` at vertices (trilinear) or centres (NGP)."""
-        rr_tidal_tensor(grid_desc(grid), phi, delta, rec, self.where, bbox, stream)
+        """The records this context traces, into ``rec``, at vertices
+        (trilinear) or centres (NGP): rr_tidal_tensor, or rr_gradient_records
+        for Method A."""
+        if self.method_a:
+            _rr.rr_gradient_records(grid_desc(grid), phi, delta, rec, self.where, bbox, stream)
+        else:
+            rr_tidal_tensor(grid_desc(grid), phi, delta, rec, self.where, bbox, stream)
         return rec
+
+    def record_buffer(self, grid, device="cuda"):
+        """An uninitialised record buffer of the kind this context traces."""
+        return gradient_buffer(grid, device) if self.method_a else record_buffer(grid, device)
 
     def footprint(self, grid, chi_a, chi_b):
         return rr_footprint_bbox(self.desc, grid_desc(grid), chi_a, chi_b)
@@ -218,6 +241,24 @@ def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=
     tr = Tracer(bundle, fp64_dda=fp64_dda)
     try:
         rec = record_buffer(grid, device=phi.device)
+        for st in steps:
+            bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
+            tr.tidal(grid, phi, rec, delta=delta, bbox=bbox, stream=stream)
+            tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
+        k, kb = tr.finalize(stream=stream)
+        return k, kb, tr.segments()
+    finally:
+        tr.close()
+
+
+def trace_method_a(phi, grid, bundle, steps, delta=None, footprint=True, stream=None):
+    """As ``trace_kappa``, by Method A (Eq. kappa2): the records are the
+    gradient records, and the returned kappa holds the density term, the
+    integral of (1 - 2 chi/chi_s) n.grad(Phi) and the steps' surface terms;
+    kappa_born is the density term alone."""
+    tr = Tracer(bundle, method_a=True)
+    try:
+        rec = tr.record_buffer(grid, device=phi.device)
         for st in steps:
             bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
             tr.tidal(grid, phi, rec, delta=delta, bbox=bbox, stream=stream)

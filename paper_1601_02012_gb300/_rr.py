@@ -33,6 +33,7 @@ RR_FP64_DDA = 2
 RR_PLAIN_SUMS = 4
 RR_SOURCE_MOMENTS = 8
 RR_SHEAR = 16
+RR_METHOD_A = 32
 RR_AT_VERTICES = 0
 RR_AT_CENTRES = 1
 
@@ -99,6 +100,7 @@ def load() -> C.CDLL:
             "rr_batch_autotune": ([P, I32, C.POINTER(C.c_float), P], C.c_int),
             "rr_moments": ([P, P, P], C.c_int),
             "rr_shear": ([P, P, P, P], C.c_int),
+            "rr_gradient_records": ([P, P, P, P, C.c_int32, P, P], C.c_int),
             "rr_source_kappa": ([P, P, C.c_int64, D, P, P, P], C.c_int),
             "rr_amr_create": ([P, P, P, C.POINTER(C.c_void_p)], C.c_int),
             "rr_amr_destroy": ([P], C.c_int),
@@ -142,7 +144,7 @@ def _stream(s):
 
 
 def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False,
-                shear: bool = False) -> rr_bundle_desc:
+                shear: bool = False, method_a: bool = False) -> rr_bundle_desc:
     """rr_bundle_desc from any object with nx, ny, fov_x, fov_y, obs, chi_s,
     interp and periodic attributes."""
     d = rr_bundle_desc()
@@ -161,6 +163,8 @@ def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bo
         flags |= RR_SOURCE_MOMENTS
     if shear:
         flags |= RR_SHEAR
+    if method_a:
+        flags |= RR_METHOD_A
     d.flags = flags
     return d
 
@@ -253,6 +257,17 @@ def rr_step_count(ctx) -> int:
 def rr_trace_step_adjoint(ctx, step: int, dL_dkappa, dL_dkborn, grad_rec, stream=None) -> None:
     _check(load().rr_trace_step_adjoint(ctx, int(step), _ptr(dL_dkappa), _ptr(dL_dkborn), _ptr(grad_rec),
                                         _stream(stream)), "rr_trace_step_adjoint")
+
+
+def rr_gradient_records(grid: rr_grid_desc, phi, delta, rec, where: int = RR_AT_VERTICES, bbox=None,
+                        stream=None) -> None:
+    """rec: 4 floats per point {d_x Phi, d_y Phi, d_z Phi, delta} (Method A)."""
+    bb = None
+    if bbox is not None:
+        arr = (C.c_int32 * 6)(*[int(x) for x in bbox])
+        bb = C.cast(arr, C.c_void_p)
+    _check(load().rr_gradient_records(C.byref(grid), _ptr(phi), _ptr(delta), _ptr(rec), int(where), bb,
+                                      _stream(stream)), "rr_gradient_records")
 
 
 def rr_tidal_tensor_adjoint(grid: rr_grid_desc, grad_rec, where: int, dL_dphi, dL_ddelta=None, stream=None) -> None:

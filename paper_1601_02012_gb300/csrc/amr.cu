@@ -833,7 +833,8 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, doubl
                             double scale, double a_step, void* stream)
 {
     if (!ctx || !A) return RR_ERR_ARG;
-    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR)) return RR_ERR_ARG;
+    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A))
+        return RR_ERR_ARG;
     rr_grid_desc g;   // the coarse grid: argument and step-order checks
     g.n[0] = g.n[1] = g.n[2] = A->h.n;
     g.box = A->h.box;

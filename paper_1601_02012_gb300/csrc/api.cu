@@ -27,10 +27,13 @@ rr_status check_bundle(const rr_bundle_desc* b)
         if (!is_finite(b->obs[a])) return RR_ERR_ARG;
     if (!is_finite(b->chi_s) || !(b->chi_s > 0)) return RR_ERR_ARG;
     if (b->interp != RR_NGP && b->interp != RR_TRILINEAR) return RR_ERR_ARG;
-    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR)) return RR_ERR_ARG;
+    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A))
+        return RR_ERR_ARG;
     if ((b->flags & RR_PLAIN_SUMS) && (b->flags & (RR_FP64_DDA | RR_SOURCE_MOMENTS))) return RR_ERR_ARG;
     if ((b->flags & RR_SOURCE_MOMENTS) && (b->flags & RR_FP64_DDA)) return RR_ERR_ARG;
     if ((b->flags & RR_SHEAR) && (b->flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS))) return RR_ERR_ARG;
+    if ((b->flags & RR_METHOD_A) && (b->flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR)))
+        return RR_ERR_ARG;
     return RR_OK;
 }
 
@@ -241,8 +244,8 @@ rr_status rr_reset(rr_ctx* ctx, void* stream)
     return from_cuda(e);
 }
 
-rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
-                          int32_t where, const int32_t* bbox, void* stream)
+static rr_status point_records(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                               int32_t where, const int32_t* bbox, void* stream, int kind)
 {
     rr_status st = check_grid(grid);
     if (st != RR_OK) return st;
@@ -255,7 +258,19 @@ rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const floa
             if (bbox[2 * a] < -(1 << 20) || bbox[2 * a + 1] > (1 << 20)) return RR_ERR_ARG;
         }
     }
-    return from_cuda(launch_tidal(*grid, phi, delta, rec, where, bbox, (cudaStream_t)stream));
+    return from_cuda(launch_tidal(*grid, phi, delta, rec, where, bbox, (cudaStream_t)stream, kind));
+}
+
+rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                          int32_t where, const int32_t* bbox, void* stream)
+{
+    return point_records(grid, phi, delta, rec, where, bbox, stream, 0);
+}
+
+rr_status rr_gradient_records(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                              int32_t where, const int32_t* bbox, void* stream)
+{
+    return point_records(grid, phi, delta, rec, where, bbox, stream, 1);
 }
 
 rr_status rr_footprint_bbox(const rr_bundle_desc* b, const rr_grid_desc* g, double chi_a, double chi_b,
@@ -299,6 +314,7 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     const int form = (b.flags & RR_SOURCE_MOMENTS) ? kFormMoments
                      : (b.flags & RR_PLAIN_SUMS)   ? kFormPlain
                      : (b.flags & RR_SHEAR)        ? kFormShear
+                     : (b.flags & RR_METHOD_A)     ? kFormMethodA
                                                    : kFormKahan;
     cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{}, form);
     if (e != cudaSuccess) return from_cuda(e);
@@ -322,7 +338,8 @@ rr_status rr_finalize(rr_ctx* ctx, double* kappa, double* kappa_born, void* stre
     cudaStream_t s = (cudaStream_t)stream;
     const int nr = ctx->bundle.nx * ctx->bundle.ny;
     cudaError_t e = launch_finalize(nr, ctx->st.kacc, ctx->st.bacc, ctx->st.nseg, kappa, kappa_born,
-                                    ctx->st.total, s, ctx->st.kmom, ctx->st.bmom, ctx->bundle.chi_s);
+                                    ctx->st.total, s, ctx->st.kmom, ctx->st.bmom, ctx->bundle.chi_s,
+                                    (ctx->bundle.flags & RR_METHOD_A) != 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->host_total, ctx->st.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return from_cuda(e);
@@ -382,7 +399,7 @@ rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkap
     if (!dL_dkappa && !dL_dkborn) return RR_ERR_ARG;
     if (step < 0 || step >= (int32_t)ctx->log.size()) return RR_ERR_STATE;
     const StepRecord& r = ctx->log[(size_t)step];
-    if (r.amr || (ctx->bundle.flags & RR_SOURCE_MOMENTS)) return RR_ERR_STATE;
+    if (r.amr || (ctx->bundle.flags & (RR_SOURCE_MOMENTS | RR_METHOD_A))) return RR_ERR_STATE;
     // the records pointer is not read by the adjoint (it needs geometry only)
     TraceArgs a = make_trace_args(ctx, &r.grid, grad_rec, r.chi_a, r.chi_b, r.scale, r.a_step);
     AdjArgs g;

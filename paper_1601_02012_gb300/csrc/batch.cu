@@ -84,7 +84,7 @@ rr_status rr_batch_create(int32_t n, const rr_bundle_desc* bundles, rr_batch** o
     for (int i = 0; i < n; ++i) {
         if (bundles[i].interp != bundles[0].interp) return RR_ERR_ARG;
         if ((bundles[i].flags & RR_FP64_DDA) != (bundles[0].flags & RR_FP64_DDA)) return RR_ERR_ARG;
-        if (bundles[i].flags & (RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR)) return RR_ERR_ARG;
+        if (bundles[i].flags & (RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A)) return RR_ERR_ARG;
     }
     rr_batch* b = new (std::nothrow) rr_batch();
     if (!b) return RR_ERR_OOM;

@@ -110,11 +110,12 @@ struct BatchArgs {
 
 // Launchers (one per translation unit).
 cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s);
+// kind 0: tidal records (2 float4 per point); kind 1: gradient records (1 float4)
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
-                         const int32_t* bbox, cudaStream_t s);
+                         const int32_t* bbox, cudaStream_t s, int kind = 0);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
 // Forms of the FP32 walk's sums.
-enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2, kFormShear = 3 };
+enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2, kFormShear = 3, kFormMethodA = 4 };
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
                          int form = kFormKahan);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
@@ -127,7 +128,8 @@ cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, i
                                  cudaStream_t s);
 cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
                             double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s,
-                            const float2* kmom = nullptr, const float2* bmom = nullptr, double chi_s = 0.0);
+                            const float2* kmom = nullptr, const float2* bmom = nullptr, double chi_s = 0.0,
+                            bool add_born = false);
 cudaError_t launch_moments(int nrays, const float2* kacc, const float2* kmom, const float2* bacc, const float2* bmom,
                            double* out, cudaStream_t s);
 cudaError_t launch_shear_out(int nrays, const float2* g1acc, const float2* g2acc, double* gamma1, double* gamma2,

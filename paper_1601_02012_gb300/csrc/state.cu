@@ -36,16 +36,19 @@ __global__ void init_directions_kernel(int nx, int ny, double fov_x, double fov_
 __device__ __forceinline__ double ff(float2 v) { return (double)v.x + (double)v.y; }
 
 // Maps from the accumulators; for the moments form (kmom, bmom not null)
-// kappa = A - B / chi_s per channel (Eq. Isources).
+// kappa = A - B / chi_s per channel (Eq. Isources); for Method A (add_born)
+// kappa = the gradient and surface terms plus the density term (Eq. kappa2).
 __global__ void finalize_kernel(int nrays, const float2* __restrict__ kacc, const float2* __restrict__ bacc,
                                 const uint32_t* __restrict__ nseg, double* out_kappa, double* out_kborn,
                                 unsigned long long* total, const float2* __restrict__ kmom,
-                                const float2* __restrict__ bmom, double inv_chi_s)
+                                const float2* __restrict__ bmom, double inv_chi_s, int add_born)
 {
     unsigned long long local = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nrays;
          i += (long long)gridDim.x * blockDim.x) {
-        if (out_kappa) out_kappa[i] = kmom ? ff(kacc[i]) - ff(kmom[i]) * inv_chi_s : ff(kacc[i]);
+        if (out_kappa)
+            out_kappa[i] = kmom ? ff(kacc[i]) - ff(kmom[i]) * inv_chi_s
+                                : (add_born ? ff(kacc[i]) + ff(bacc[i]) : ff(kacc[i]));
         if (out_kborn) out_kborn[i] = bmom ? ff(bacc[i]) - ff(bmom[i]) * inv_chi_s : ff(bacc[i]);
         local += nseg[i];
     }
@@ -131,7 +134,7 @@ cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4*
 
 cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
                             double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s,
-                            const float2* kmom, const float2* bmom, double chi_s)
+                            const float2* kmom, const float2* bmom, double chi_s, bool add_born)
 {
     cudaError_t e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
@@ -144,7 +147,7 @@ cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, c
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     finalize_kernel<<<(unsigned)blocks, nt, 0, s>>>(nrays, kacc, bacc, nseg, out_kappa, out_kborn, total, kmom, bmom,
-                                                    (kmom && chi_s > 0) ? 1.0 / chi_s : 0.0);
+                                                    (kmom && chi_s > 0) ? 1.0 / chi_s : 0.0, add_born ? 1 : 0);
     return cudaGetLastError();
 }
 

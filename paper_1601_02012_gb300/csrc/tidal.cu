@@ -1,4 +1,5 @@
-// Tidal tensor and vertex records (Sec. 3.3, Eq. tidalexample; Sec. 2.7).
+// Tidal tensor and vertex records (Sec. 3.3, Eq. tidalexample; Sec. 2.7), and
+// the gradient records of Method A (Eq. kappa2).
 //
 // One CTA of 8 warps owns an 8 (y) x 32 (z) block of cell centres, one warp
 // per z-row, one thread per centre, and marches along x through a chunk of
@@ -12,7 +13,9 @@
 // of the block are the halo of its 7 x 31 vertices. The next potential plane is
 // loaded into registers while the current one is processed. HBM traffic per
 // point: the potential read about 1.5 times (halo re-reads hit L2) and the
-// 32-byte record written once: 36 algorithmic bytes per point.
+// 32-byte record written once: 36 algorithmic bytes per point. The gradient
+// records (KIND 1) take the same march with the three central first
+// differences and delta instead: one 16-byte record, 20 bytes per point.
 #include <algorithm>
 
 #include "rr_internal.h"
@@ -34,6 +37,7 @@ struct TidalArgs {
     float ih2;        // 1/h^2
     float iq;         // 1/(4 h^2)
     float dinv;       // 1 / (1.5 Omega_m (H0/c)^2)
+    float ih2h;       // 1/(2h), gradient records
     int xchunk;       // planes per CTA
 };
 
@@ -47,17 +51,20 @@ __device__ __forceinline__ int wrapi(int i, int n)
 }
 
 // MODE 0: records at vertices (7 x 31 per CTA and plane); MODE 1: records at
-// centres (8 x 32).
-template <int MODE>
+// centres (8 x 32). KIND 0: tidal records, 7 channels {Hxx, Hyy, Hzz, Hxy,
+// Hxz, Hyz, delta} in 2 float4; KIND 1: gradient records, 4 channels
+// {d_x Phi, d_y Phi, d_z Phi, delta} in 1 float4.
+template <int MODE, int KIND>
 __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
 {
     constexpr int V = (MODE == 0) ? 1 : 0;
+    constexpr int NC = KIND == 0 ? 7 : 4;            // channels
     constexpr int OY = TY - V, OZ = TZ - V;          // output points per CTA and plane
     constexpr int PY = TY + 2, PZ = TZ + 2;          // potential per plane (halo 1 around the centres)
     constexpr int NP = PY * PZ;
     constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane
     __shared__ float ring[4][NP];   // potential planes c - 1, c, c + 1 and the one arriving (c + 2)
-    __shared__ float sP[2][MODE == 0 ? 7 : 1][MODE == 0 ? NT : 1];   // z-pair sums of every centre, by plane parity
+    __shared__ float sP[2][MODE == 0 ? NC : 1][MODE == 0 ? NT : 1];   // z-pair sums of every centre, by plane parity
 
     const int ty = threadIdx.x / TZ, tz = threadIdx.x % TZ;
     const int py0 = blockIdx.y * OY, pz0 = blockIdx.x * OZ;               // box-relative first output
@@ -102,7 +109,9 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
     const size_t out_yz_off = out_yz ? (size_t)wrapi(a.y0 + oy, a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2) : 0;
     const int o = (ty + 1) * PZ + (tz + 1);          // own centre in the ring
     const size_t d_yz = (size_t)wrapi(cy0 + ty, a.n1) * a.n2 + wrapi(cz0 + tz, a.n2);
-    float prev[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // 2 x 2 centre sum of the previous plane
+    float prev[NC];   // 2 x 2 centre sum of the previous plane
+#pragma unroll
+    for (int q = 0; q < NC; ++q) prev[q] = 0.f;
     for (int c = c_first; c <= c_last; ++c) {
         const float* P0 = ring[slot(c - 1)];
         const float* P1 = ring[slot(c)];
@@ -114,26 +123,41 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
         if (c + 3 <= c_last + 1) fetch(c + 3, nxt2);
         if (c + 2 <= c_last + 1) put(slot(c + 2), nxt);
 
-        // second derivatives at this thread's centre (differences of neighbours first)
-        float h[7];
+        float h[NC];
         const float p0 = P1[o];
-        h[0] = ((P0[o] - p0) + (P2[o] - p0)) * a.ih2;
-        h[1] = ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) * a.ih2;
-        h[2] = ((P1[o - 1] - p0) + (P1[o + 1] - p0)) * a.ih2;
-        h[3] = ((P2[o + PZ] - P2[o - PZ]) + (P0[o - PZ] - P0[o + PZ])) * a.iq;
-        h[4] = ((P2[o + 1] - P2[o - 1]) + (P0[o - 1] - P0[o + 1])) * a.iq;
-        h[5] = ((P1[o + PZ + 1] - P1[o + PZ - 1]) + (P1[o - PZ - 1] - P1[o - PZ + 1])) * a.iq;
-        if (a.delta) h[6] = __ldg(a.delta + (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + d_yz);
-        else h[6] = (h[0] + h[1] + h[2]) * a.dinv;
+        if constexpr (KIND == 0) {
+            // second derivatives at this thread's centre (differences of neighbours first)
+            h[0] = ((P0[o] - p0) + (P2[o] - p0)) * a.ih2;
+            h[1] = ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) * a.ih2;
+            h[2] = ((P1[o - 1] - p0) + (P1[o + 1] - p0)) * a.ih2;
+            h[3] = ((P2[o + PZ] - P2[o - PZ]) + (P0[o - PZ] - P0[o + PZ])) * a.iq;
+            h[4] = ((P2[o + 1] - P2[o - 1]) + (P0[o - 1] - P0[o + 1])) * a.iq;
+            h[5] = ((P1[o + PZ + 1] - P1[o + PZ - 1]) + (P1[o - PZ - 1] - P1[o - PZ + 1])) * a.iq;
+            if (a.delta) h[6] = __ldg(a.delta + (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + d_yz);
+            else h[6] = (h[0] + h[1] + h[2]) * a.dinv;
+        } else {
+            // central first differences, and delta (given, or from the 7-point
+            // Laplacian, the trace of the stencils above)
+            h[0] = (P2[o] - P0[o]) * a.ih2h;
+            h[1] = (P1[o + PZ] - P1[o - PZ]) * a.ih2h;
+            h[2] = (P1[o + 1] - P1[o - 1]) * a.ih2h;
+            if (a.delta) {
+                h[3] = __ldg(a.delta + (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + d_yz);
+            } else {
+                const float lap = (((P0[o] - p0) + (P2[o] - p0)) + ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) +
+                                   ((P1[o - 1] - p0) + (P1[o + 1] - p0))) * a.ih2;
+                h[3] = lap * a.dinv;
+            }
+        }
 
-        float pz[7];
+        float pz[NC];
         if constexpr (MODE == 0) {
             // z pair: this centre and the one below it in z (the lane to the left)
 #pragma unroll
-            for (int q = 0; q < 7; ++q) pz[q] = h[q] + __shfl_up_sync(0xffffffffu, h[q], 1);
+            for (int q = 0; q < NC; ++q) pz[q] = h[q] + __shfl_up_sync(0xffffffffu, h[q], 1);
             if (ty < TY - 1) {
 #pragma unroll
-                for (int q = 0; q < 7; ++q) sP[(c - c_first) & 1][q][threadIdx.x] = pz[q];
+                for (int q = 0; q < NC; ++q) sP[(c - c_first) & 1][q][threadIdx.x] = pz[q];
             }
         }
         // plane c + 2 is in the ring and the z pairs of plane c are shared; the
@@ -141,23 +165,34 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
         __syncthreads();
         if constexpr (MODE == 0) {
             if (ty >= 1) {
-                float b[7];
+                float b[NC];
 #pragma unroll
-                for (int q = 0; q < 7; ++q) b[q] = pz[q] + sP[(c - c_first) & 1][q][threadIdx.x - TZ];
+                for (int q = 0; q < NC; ++q) b[q] = pz[q] + sP[(c - c_first) & 1][q][threadIdx.x - TZ];
                 if (c > c_first && out_yz) {
-                    float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
-                    r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
-                                       (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
-                    r[1] = make_float4((prev[4] + b[4]) * 0.125f, (prev[5] + b[5]) * 0.125f,
-                                       (prev[6] + b[6]) * 0.125f, 0.f);
+                    const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off;
+                    if constexpr (KIND == 0) {
+                        float4* r = a.rec + 2 * pt;
+                        r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
+                                           (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
+                        r[1] = make_float4((prev[4] + b[4]) * 0.125f, (prev[5] + b[5]) * 0.125f,
+                                           (prev[6] + b[6]) * 0.125f, 0.f);
+                    } else {
+                        a.rec[pt] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
+                                                (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
+                    }
                 }
 #pragma unroll
-                for (int q = 0; q < 7; ++q) prev[q] = b[q];
+                for (int q = 0; q < NC; ++q) prev[q] = b[q];
             }
         } else if (out_yz) {
-            float4* r = a.rec + 2 * ((size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off);
-            r[0] = make_float4(h[0], h[1], h[2], h[3]);
-            r[1] = make_float4(h[4], h[5], h[6], 0.f);
+            const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off;
+            if constexpr (KIND == 0) {
+                float4* r = a.rec + 2 * pt;
+                r[0] = make_float4(h[0], h[1], h[2], h[3]);
+                r[1] = make_float4(h[4], h[5], h[6], 0.f);
+            } else {
+                a.rec[pt] = make_float4(h[0], h[1], h[2], h[3]);
+            }
         }
 #pragma unroll
         for (int k = 0; k < LP; ++k) nxt[k] = nxt2[k];
@@ -278,7 +313,7 @@ __global__ void __launch_bounds__(NT) tidal_adjoint_kernel(TidalAdjArgs a)
 }  // namespace
 
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
-                         const int32_t* bbox, cudaStream_t s)
+                         const int32_t* bbox, cudaStream_t s, int kind)
 {
     TidalArgs a;
     a.phi = phi;
@@ -298,6 +333,7 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
     a.ih2 = (float)(1.0 / (h * h));
     a.iq = (float)(0.25 / (h * h));
     a.dinv = (float)(1.0 / (1.5 * g.omega_m * kH0OverC * kH0OverC));
+    a.ih2h = (float)(0.5 / h);
     // planes per CTA: long marches on big boxes; short ones when the box has
     // few y-z tiles, so that every SM still gets a couple of CTAs
     static int nsm = 0;
@@ -311,10 +347,13 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
     const long long want = (long long)a.ex * tiles_yz / (2LL * nsm);
     a.xchunk = (int)std::max(2LL, std::min((long long)XCHUNK_MAX, want));
     dim3 grid((a.ez + oz - 1) / oz, (a.ey + oy - 1) / oy, (a.ex + a.xchunk - 1) / a.xchunk);
-    if (where == RR_AT_VERTICES)
-        tidal_kernel<0><<<grid, NT, 0, s>>>(a);
-    else
-        tidal_kernel<1><<<grid, NT, 0, s>>>(a);
+    if (kind == 0) {
+        if (where == RR_AT_VERTICES) tidal_kernel<0, 0><<<grid, NT, 0, s>>>(a);
+        else tidal_kernel<1, 0><<<grid, NT, 0, s>>>(a);
+    } else {
+        if (where == RR_AT_VERTICES) tidal_kernel<0, 1><<<grid, NT, 0, s>>>(a);
+        else tidal_kernel<1, 1><<<grid, NT, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

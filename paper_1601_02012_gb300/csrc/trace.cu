@@ -28,6 +28,8 @@
 //  * Sums over the segments of a step are compensated FP32 (Kahan); the step
 //    total times the step's scale is added to the ray's float-float
 //    accumulator (~48 bits).
+#include <type_traits>
+
 #include "walk.cuh"
 
 namespace rr {
@@ -57,12 +59,19 @@ __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], in
 // and chi^2, i.e. (G0, G1, G2) = (chi_A, -1, 0) and (chi_A^2, -2 chi_A, 1)) or
 // kFormShear (kappa and Born kappa, and the shear pair (gamma1, gamma2) of Eqs.
 // gamma1, gamma2 from a second projection of the same records, carried as a
-// second packed pair through the same segments).
+// second packed pair through the same segments) or kFormMethodA (Method A,
+// Eq. kappa2, on gradient records {grad Phi, delta}: the first channel
+// integrates n . grad Phi with the kernel dg/dchi and adds the step's surface
+// terms -g n.grad Phi at the start and +g n.grad Phi at the end of the traced
+// interval (Eq. 2nterm); the second is the Born term as in the other forms).
 template <int INTERP, class R, int FORM = kFormKahan>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
     constexpr bool F64 = sizeof(R) == 8;
     constexpr bool SH = !F64 && FORM == kFormShear;
+    constexpr bool MA = !F64 && FORM == kFormMethodA;
+    // one record per point: 2 float4 of the tidal tensor, or 1 gradient float4
+    using PR = typename std::conditional<MA, float4, Rec>::type;
     const long long rid = (long long)iy * A.nx + ix;
     const int nn[3] = {A.n0, A.n1, A.n2};
     RayRange rg;
@@ -79,6 +88,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     Acc2 s2m;   // moments form: the B moments; shear form: (gamma1, gamma2)
     float w1[6], w2[6];   // shear form: the Q weights of gamma1, gamma2
     if constexpr (SH) shear_weights(A.dirh[rid], w1, w2);
+    float4 nd;            // Method A: the direction, for n . grad Phi
+    if constexpr (MA) nd = A.dirh[rid];
+    // Method A: n . grad Phi and g at the start and at the end of the interval
+    float qa = 0.f, ga = 0.f, qb = 0.f, gb = 0.f;
     Acc<R> sk, sb;
     uint32_t cnt = 0;
     int iter = 0;
@@ -101,6 +114,15 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     const float* w = W.w;
     const R L = W.L, chiA0 = W.chiA0, D0 = W.D0;
     const int max_iter = W.max_iter;
+    auto fetch = [&](long long i) -> PR {
+        if constexpr (MA) return load_grad_rec(A.rec, i);
+        else return load_rec(A.rec, i);
+    };
+    // (the channel pair the walk integrates) of a record
+    auto pair = [&](const PR& r) -> float2 {
+        if constexpr (MA) return radial_pair(nd, r);
+        else return make_float2(project(w, r), r.b.z);
+    };
     // a sub-step that resumes inside the previous one's last cell does not
     // start a new cell segment
     bool resume = j > 0 && c[0] == pc0 && c[1] == pc1 && c[2] == pc2;
@@ -117,13 +139,13 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
             const int gx = (m & 1) ? vhi[0] : vlo[0];
             const int gy = (m & 2) ? vhi[1] : vlo[1];
             const int gz = (m & 4) ? vhi[2] : vlo[2];
-            const Rec r = load_rec(A.rec, gx * sx + gy * sy + gz);
-            q2[m] = make_float2(project(w, r), r.b.z);
+            const PR r = fetch(gx * sx + gy * sy + gz);
+            q2[m] = pair(r);
             if constexpr (SH) g2[m] = make_float2(project(w1, r), project(w2, r));
         }
     } else {
-        const Rec r = load_rec(A.rec, c[0] * sx + c[1] * sy + c[2]);
-        q2[0] = make_float2(project(w, r), r.b.z);
+        const PR r = fetch(c[0] * sx + c[1] * sy + c[2]);
+        q2[0] = pair(r);
         if constexpr (SH) g2[0] = make_float2(project(w1, r), project(w2, r));
     }
 
@@ -154,7 +176,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         // Prefetch the next cell's new records before this segment's arithmetic.
         // (register arrays are indexed only through unrolled loops, never by e)
         int nvhi = 0, ncell = 0, ne = 1;
-        Rec nr[4];
+        PR nr[4];
         if (!last) {
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -170,13 +192,36 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                     const int gx = e == 0 ? nvhi : (pb ? vhi[0] : vlo[0]);
                     const int gy = e == 1 ? nvhi : (e == 0 ? (pb ? vhi[1] : vlo[1]) : (qb2 ? vhi[1] : vlo[1]));
                     const int gz = e == 2 ? nvhi : (qb2 ? vhi[2] : vlo[2]);
-                    nr[r] = load_rec(A.rec, gx * sx + gy * sy + gz);
+                    nr[r] = fetch(gx * sx + gy * sy + gz);
                 }
             } else {
                 const int cx = e == 0 ? wrap_once(ncell, nn[0]) : c[0];
                 const int cy = e == 1 ? wrap_once(ncell, nn[1]) : c[1];
                 const int cz = e == 2 ? wrap_once(ncell, nn[2]) : c[2];
-                nr[0] = load_rec(A.rec, cx * sx + cy * sy + cz);
+                nr[0] = fetch(cx * sx + cy * sy + cz);
+            }
+        }
+        if constexpr (MA) {
+            // the surface terms of Eq. (2nterm): n . grad Phi and g at the start
+            // of the traced interval (the first segment's entry) and at its end
+            // (the exit of the segment that ends the interval: the last one,
+            // or, without wrap, the one leaving the box)
+            if (j == 0 && iter == 0) {
+                qa = INTERP == RR_TRILINEAR ? trilinear_x(q2, u[0], u[1], u[2]) : q2[0].x;
+                ga = D0 * chiA0 * ichis;
+            }
+            if (last || (!A.periodic && (ncell < 0 || ncell >= ne))) {
+                if (INTERP == RR_TRILINEAR) {
+                    float ue[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) ue[a] = fminf(fmaxf(fmaf(t, v[a], u[a]), 0.f), 1.f);
+                    qb = trilinear_x(q2, ue[0], ue[1], ue[2]);
+                } else {
+                    qb = q2[0].x;
+                }
+                float G0, G1, G2;
+                kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
+                gb = fmaf(t, fmaf(t, G2, G1), G0);
             }
         }
 
@@ -192,6 +237,12 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                     s2.add(segment_ngp(q2[0], t, chiA, -1.f, 0.f));
                     s2m.add(segment_ngp(q2[0], t, chiA * chiA, -2.f * chiA, 1.f));
                 }
+            } else if constexpr (MA) {
+                float G0, G1, G2;
+                kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
+                s2.add(INTERP == RR_TRILINEAR
+                           ? segment_trilinear_a(q2, u[0], u[1], u[2], v[0], v[1], v[2], t, G0, G1, G2)
+                           : segment_ngp_a(q2[0], t, G0, G1, G2));
             } else if constexpr (!F64) {
                 float G0, G1, G2;
                 kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
@@ -248,7 +299,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         if (INTERP == RR_TRILINEAR) {
             float2 p2[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) p2[r] = make_float2(project(w, nr[r]), nr[r].b.z);
+            for (int r = 0; r < 4; ++r) p2[r] = pair(nr[r]);
             shift_corners(q2, p2, e);
             if constexpr (SH) {
 #pragma unroll
@@ -256,7 +307,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                 shift_corners(g2, p2, e);
             }
         } else {
-            q2[0] = make_float2(project(w, nr[0]), nr[0].b.z);
+            q2[0] = pair(nr[0]);
             if constexpr (SH) g2[0] = make_float2(project(w1, nr[0]), project(w2, nr[0]));
         }
         if (++iter > max_iter) {
@@ -267,6 +318,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     pc0 = c[0]; pc1 = c[1]; pc2 = c[2];
     }
 
+    if constexpr (MA) {
+        s2.add(make_float2(-ga * qa, 0.f));
+        s2.add(make_float2(gb * qb, 0.f));
+    }
     if constexpr (!F64) {
         sk.s = s2.s.x; sk.c = s2.c.x;
         sb.s = s2.s.y; sb.c = s2.c.y;
@@ -388,6 +443,11 @@ cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStre
     if (form == kFormMoments && !fp64_dda) {
         if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
         else trace_kernel<RR_NGP, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
+        return cudaGetLastError();
+    }
+    if (form == kFormMethodA && !fp64_dda) {
+        if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, kFormMethodA><<<grid, nt, 0, s>>>(a, t);
+        else trace_kernel<RR_NGP, float, kFormMethodA><<<grid, nt, 0, s>>>(a, t);
         return cudaGetLastError();
     }
     if (form == kFormShear && !fp64_dda) {

@@ -37,6 +37,19 @@ __device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, long lon
     return r;
 }
 
+// A gradient record of Method A: one float4 {d_x Phi, d_y Phi, d_z Phi, delta}
+// per point.
+__device__ __forceinline__ float4 load_grad_rec(const float4* __restrict__ rec, long long idx)
+{
+    return __ldg(rec + idx);
+}
+
+// (n . grad Phi, delta) of a gradient record for the direction n
+__device__ __forceinline__ float2 radial_pair(float4 n, float4 r)
+{
+    return make_float2(fmaf(n.x, r.x, fmaf(n.y, r.y, n.z * r.z)), r.w);
+}
+
 // Q_kappa = tr(H) - n^T H n = w . (xx, yy, zz, xy, xz, yz)
 __device__ __forceinline__ float project(const float w[6], const Rec& r)
 {
@@ -192,6 +205,54 @@ __device__ __forceinline__ float2 segment_trilinear(const float2 q[8], float u0,
     float2 e2[4];
     line_cubic2(q, bc2(u0), bc2(u1), bc2(u2), bc2(v0), bc2(v1), bc2(v2), e2);
     return dot_kernel(e2, t, G0, G1, G2);
+}
+
+// Method A (Eq. kappa2): the pair (n . grad Phi, delta) with two kernels, the
+// first channel with K = dg/dchi = 1 - 2 chi/chi_s, i.e. K(chi_A - s) = -G1 -
+// 2 G2 s, the second (Born) with g itself: sum_N e_{N-1} (L_N, J_N), L_N =
+// int_0^t K s^(N-1) ds.
+__device__ __forceinline__ float2 dot_kernel_a(const float2 e2[4], float t, float G0, float G1, float G2)
+{
+    const float t2 = t * t;
+    const float K0 = -G1, K1 = -2.f * G2;
+    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
+    const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
+    const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
+    const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
+    const float L1 = t * (K0 + t * K1 * 0.5f);
+    const float L2 = t2 * (K0 * 0.5f + t * K1 * (1.f / 3.f));
+    const float L3 = t2 * t * (K0 * (1.f / 3.f) + t * K1 * 0.25f);
+    const float L4 = t2 * t2 * (K0 * 0.25f + t * K1 * 0.2f);
+    float2 x = __fmul2_rn(e2[0], make_float2(L1, J1));
+    x = __ffma2_rn(e2[1], make_float2(L2, J2), x);
+    x = __ffma2_rn(e2[2], make_float2(L3, J3), x);
+    return __ffma2_rn(e2[3], make_float2(L4, J4), x);
+}
+
+__device__ __forceinline__ float2 segment_trilinear_a(const float2 q[8], float u0, float u1, float u2, float v0,
+                                                      float v1, float v2, float t, float G0, float G1, float G2)
+{
+    float2 e2[4];
+    line_cubic2(q, bc2(u0), bc2(u1), bc2(u2), bc2(v0), bc2(v1), bc2(v2), e2);
+    return dot_kernel_a(e2, t, G0, G1, G2);
+}
+
+__device__ __forceinline__ float2 segment_ngp_a(float2 q, float t, float G0, float G1, float G2)
+{
+    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
+    const float L1 = t * (-G1 - t * G2);
+    return __fmul2_rn(q, make_float2(L1, J1));
+}
+
+// First channel of the trilinear field of the mirrored corners q at the
+// mirrored point u (the constant term of the line cubic there).
+__device__ __forceinline__ float trilinear_x(const float2 q[8], float u0, float u1, float u2)
+{
+    float a[4];
+#pragma unroll
+    for (int jk = 0; jk < 4; ++jk) a[jk] = fmaf(q[2 * jk + 1].x - q[2 * jk].x, u0, q[2 * jk].x);
+    const float b0 = fmaf(a[1] - a[0], u1, a[0]), b1 = fmaf(a[3] - a[2], u1, a[2]);
+    return fmaf(b1 - b0, u2, b0);
 }
 
 __device__ __forceinline__ float2 segment_ngp(float2 q, float t, float G0, float G1, float G2)

@@ -139,8 +139,21 @@ def test_source_kappa_validation_is_host_side(rr):
     assert lib.rr_moments(None, C.c_void_p(16), None) == rr.RR_ERR_ARG
     good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
     h = C.c_void_p()
-    for flags in (rr.RR_SOURCE_MOMENTS | rr.RR_FP64_DDA, rr.RR_SOURCE_MOMENTS | rr.RR_PLAIN_SUMS, 32):
+    for flags in (rr.RR_SOURCE_MOMENTS | rr.RR_FP64_DDA, rr.RR_SOURCE_MOMENTS | rr.RR_PLAIN_SUMS, 64):
         good.flags = flags
+        assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG
+
+
+def test_method_a_validation_is_host_side(rr):
+    lib = rr.load()
+    g = rr.grid_desc(synth.Grid((8, 8, 8), 16.0))
+    assert lib.rr_gradient_records(C.byref(g), None, None, C.c_void_p(16), 0, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_gradient_records(C.byref(g), C.c_void_p(16), None, C.c_void_p(8), 0, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_gradient_records(C.byref(g), C.c_void_p(16), None, C.c_void_p(16), 2, None, None) == rr.RR_ERR_ARG
+    good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
+    h = C.c_void_p()
+    for other in (rr.RR_FP64_DDA, rr.RR_PLAIN_SUMS, rr.RR_SOURCE_MOMENTS, rr.RR_SHEAR):
+        good.flags = rr.RR_METHOD_A | other
         assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG
 
 
