@@ -62,6 +62,8 @@ def _L():
         _lib.ora_fields_grad.argtypes = [P, P, P]
         _lib.ora_trace_step_method_a.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, C.c_double,
                                                  P, P, C.c_int, P, C.c_long]
+        _lib.ora_trace_step_kq.argtypes = [P, P, P, P, C.c_double, C.c_double, C.c_double, P, P, P, C.c_int, P,
+                                           C.c_long]
         _lib.ora_ray_segments.argtypes = [P, P, C.c_long, C.c_double, C.c_double, P, C.c_long]
         _lib.ora_ray_segments.restype = C.c_long
         _lib.ora_ray_direction.argtypes = [P, C.c_long, P, P]
@@ -222,6 +224,27 @@ def trace_method_a(bundle, grid, G, delta, steps, nthreads: int = 0, rids=None):
         if rc != 0:
             raise ValueError("oracle: bad step interval")
     return kg, kb
+
+
+def trace_kq(bundle, grid, Q1, Q2, kernels, steps, nthreads: int = 0, rids=None):
+    """Two generic integrals int K_c(chi) Q_c dchi per ray over the given steps
+    (each step's field is st.scale * Q_c); kernels = (k0, k1, k2) per channel,
+    K_c = k0 + k1 chi + k2 chi^2; Q2 may be None. Returns (I1, I2)."""
+    Q1 = _f64(Q1)
+    Q2 = None if Q2 is None else _f64(Q2)
+    k = np.ascontiguousarray(np.asarray(kernels, np.float64).reshape(6))
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
+    o1 = np.zeros(nr, np.float64)
+    o2 = np.zeros(nr, np.float64)
+    b, g = _bundle(bundle), _grid(grid)
+    for st in steps:
+        rc = _L().ora_trace_step_kq(C.byref(b), C.byref(g), _ptr(Q1), _ptr(Q2), float(st.chi_a), float(st.chi_b),
+                                    float(st.scale), _ptr(k), _ptr(o1), _ptr(o2), int(nthreads), _ptr(ids),
+                                    0 if ids is None else len(ids))
+        if rc != 0:
+            raise ValueError("oracle: bad step interval")
+    return o1, o2
 
 
 def ray_segments(bundle, grid, rid: int, chi_a: float, chi_b: float) -> np.ndarray:

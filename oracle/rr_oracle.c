@@ -25,6 +25,8 @@
  *     with a held constant over the step;
  *   - the shear (Eqs. gamma1, gamma2) by the same walk and integrals with
  *     Q = n1n1 - n2n2 and Q = 2 n1n2 (Eq. n1n2 in its orthonormal reading);
+ *   - generic integrals int K Q dchi of two scalar fields with quadratic
+ *     kernels K(chi) (Eqs. Ic, Icngp, Icfinal; the ISW integral of Sec. 6);
  *   - Method A (Eq. kappa2): d_a Phi at centres by central differences,
  *     the integral of (1 - 2 chi/chi_s) n.grad(Phi) by Eq. (Icfinal) with
  *     that kernel, and each step's surface term g n.grad(Phi) at the ends of
@@ -657,6 +659,104 @@ int ora_trace_step_method_a(const ora_bundle* b, const ora_grid* g, const double
         free(S);
         kgrad[slot] += scale * neu_val(&sg_sum);
         kborn[slot] += scale * neu_val(&sb);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Generic integrals I = int K(chi) Q dchi (Eqs. Ic, Icngp, Icfinal; Sec. 6)   */
+/* ------------------------------------------------------------------------- */
+
+/* Value of a scalar field at vertex (vi, vj, vk): the mean of the 8 cells
+ * sharing it (Sec. 2.7). */
+static double vertex_scalar(const ora_grid* g, const double* F, long vi, long vj, long vk)
+{
+    double v = 0.0;
+    for (int di = -1; di <= 0; ++di)
+        for (int dj = -1; dj <= 0; ++dj)
+            for (int dk = -1; dk <= 0; ++dk) v += F[cell_index(g, vi + di, vj + dj, vk + dk)];
+    return 0.125 * v;
+}
+
+/* Eq. (Icfinal) with a quadratic kernel K(chi) = k0 + k1 chi + k2 chi^2.
+ * About chi_A, K = c0 + c1 s + c2 s^2 with s = chi - chi_A, c0 = K(chi_A),
+ * c1 = k1 + 2 k2 chi_A, c2 = k2, and with R = chi_B - chi_A
+ * int_{chi_B}^{chi_A} K s^{N-1} dchi = -(c0 R^N / N + c1 R^{N+1} / (N+1) + c2 R^{N+2} / (N+2)). */
+static double ic_poly_trilinear(const double d[4], const double k[3], double chiA, double chiB)
+{
+    const double c0 = k[0] + chiA * (k[1] + chiA * k[2]), c1 = k[1] + 2.0 * k[2] * chiA, c2 = k[2];
+    const double R = chiB - chiA;
+    double sum = 0.0;
+    for (int N = 1; N <= 4; ++N) {
+        double RN = pow(R, N);
+        sum -= d[N - 1] * (c0 * RN / N + c1 * RN * R / (N + 1) + c2 * RN * R * R / (N + 2));
+    }
+    return sum;
+}
+
+/* Eq. (Icngp) with the same kernel: Q_c [P(chi_A) - P(chi_B)], P' = K. */
+static double ic_poly_ngp(double Qc, const double k[3], double chiA, double chiB)
+{
+    double PA = chiA * (k[0] + chiA * (k[1] / 2.0 + chiA * k[2] / 3.0));
+    double PB = chiB * (k[0] + chiB * (k[1] / 2.0 + chiB * k[2] / 3.0));
+    return Qc * (PA - PB);
+}
+
+/*
+ * Two generic line-of-sight integrals per ray over one step: out_c +=
+ * scale * sum over the crossed cells of int K_c(chi) Q_c dchi, with Q_c a
+ * scalar field at cell centres (Q2 may be NULL: zero), taken at the centre
+ * (NGP) or trilinear from the vertex means (Sec. 2.7), and K_c(chi) = k[3c] +
+ * k[3c+1] chi + k[3c+2] chi^2. With Q = (Phi_curr - Phi_prev) / dt this is the
+ * ISW integral of Sec. 6; with Q = delta and K = the lensing kernel, the
+ * density term of Eq. (kappa2).
+ */
+int ora_trace_step_kq(const ora_bundle* b, const ora_grid* g, const double* Q1, const double* Q2,
+                      double chi_a, double chi_b, double scale, const double* k, double* out1, double* out2,
+                      int nthreads, const int64_t* rids, long nrids)
+{
+    if (!(chi_a > chi_b) || chi_b < 0.0) return -1;
+    field_t F = {g, b, NULL, NULL};
+    const double h = grid_h(g);
+    const long nr = rids ? nrids : (long)b->nx * b->ny;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (long slot = 0; slot < nr; ++slot) {
+        const long rid = rids ? (long)rids[slot] : slot;
+        ray_geo r;
+        make_ray(b, rid % b->nx, rid / b->nx, &r);
+        segment_t* S;
+        long ns = walk(&F, &r, chi_a, chi_b, &S);
+        neu_t s1 = {0, 0}, s2 = {0, 0};
+        for (long s = 0; s < ns; ++s) {
+            const segment_t* sg = &S[s];
+            double i1, i2 = 0.0;
+            if (b->interp == 0) {
+                size_t ci = cell_index(g, sg->cell[0], sg->cell[1], sg->cell[2]);
+                i1 = ic_poly_ngp(Q1[ci], k, sg->chiA, sg->chiB);
+                if (Q2) i2 = ic_poly_ngp(Q2[ci], k + 3, sg->chiA, sg->chiB);
+            } else {
+                double V1[8], V2[8], d[4];
+                for (int v = 0; v < 8; ++v) {
+                    long vi = sg->cell[0] + (v & 1), vj = sg->cell[1] + ((v >> 1) & 1), vk = sg->cell[2] + ((v >> 2) & 1);
+                    V1[v] = vertex_scalar(g, Q1, vi, vj, vk);
+                    V2[v] = Q2 ? vertex_scalar(g, Q2, vi, vj, vk) : 0.0;
+                }
+                dn_coeffs(V1, sg->a, sg->b, sg->c, h, r.st, r.ct, r.sp, r.cp, d);
+                i1 = ic_poly_trilinear(d, k, sg->chiA, sg->chiB);
+                if (Q2) {
+                    dn_coeffs(V2, sg->a, sg->b, sg->c, h, r.st, r.ct, r.sp, r.cp, d);
+                    i2 = ic_poly_trilinear(d, k + 3, sg->chiA, sg->chiB);
+                }
+            }
+            neu_add(&s1, i1);
+            neu_add(&s2, i2);
+        }
+        free(S);
+        out1[slot] += scale * neu_val(&s1);
+        out2[slot] += scale * neu_val(&s2);
     }
     return 0;
 }
