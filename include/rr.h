@@ -67,7 +67,7 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
                                FP32 walk with compensated sums; rr_create /
                                rr_trace_step only; not with RR_FP64_DDA,
                                RR_PLAIN_SUMS or RR_SOURCE_MOMENTS */
-       RR_METHOD_A = 32 };  /* Method A (Eq. kappa2): rr_trace_step reads gradient
+       RR_METHOD_A = 32,    /* Method A (Eq. kappa2): rr_trace_step reads gradient
                                records (rr_gradient_records) and accumulates the
                                density term (kappa_born) and, separately, the
                                integral of (1 - 2 chi/chi_s) n.grad(Phi) plus each
@@ -76,6 +76,14 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
                                writes kappa = the sum of the three terms and
                                kappa_born = the density term. FP32 walk with
                                compensated sums; rr_create / rr_trace_step only;
+                               no adjoint; not with the other optional flags */
+       RR_GENERIC = 64 };   /* generic integrals (Eqs. Ic, Icngp, Icfinal): rr_trace_step
+                               reads scalar-pair records (rr_scalar_records) and
+                               accumulates int K_c(chi) Q_c dchi for the two channels,
+                               K_c quadratic in chi (rr_set_kernels; default: the
+                               lensing kernel g for both); rr_finalize writes channel
+                               0 into kappa and channel 1 into kappa_born. FP32 walk
+                               with compensated sums; rr_create / rr_trace_step only;
                                no adjoint; not with the other optional flags */
 
 /* rr_tidal_tensor: where the records are evaluated. */
@@ -98,7 +106,7 @@ typedef struct {
     double chi_s;         /* comoving distance of the sources, > 0 */
     int32_t interp;       /* RR_NGP or RR_TRILINEAR */
     int32_t flags;        /* RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR |
-                             RR_METHOD_A */
+                             RR_METHOD_A | RR_GENERIC */
 } rr_bundle_desc;
 
 /* A uniform grid of n[0] x n[1] x n[2] cubic cells of size h = box / n[0]. */
@@ -160,6 +168,48 @@ rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const floa
  */
 rr_status rr_gradient_records(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
                               int32_t where, const int32_t* bbox, void* stream);
+
+/*
+ * Scalar-pair records of the generic integrals (RR_GENERIC; Eqs. Ic, Icngp,
+ * Icfinal, Sec. 2.6): writes channel `channel` (0 or 1) of each point's
+ * float2 record, leaving the other channel as it was.
+ *   field       device, n0*n1*n2 floats at cell centres.
+ *   field_prev  device, n0*n1*n2 floats, or NULL. When given, the channel is
+ *               the finite-difference time derivative (field - field_prev) *
+ *               inv_dt (the ISW integrand of Sec. 6 for a potential); else the
+ *               field itself.
+ *   rec         device, n0*n1*n2 records of 2 floats (8 bytes; 16-byte aligned
+ *               base), at the vertices (mean of the 8 cells sharing a vertex,
+ *               Sec. 2.7) or at the centres (where).
+ *   bbox        as for rr_tidal_tensor.
+ * RR_ERR_ARG on a null/misaligned pointer, a channel other than 0/1, a
+ * non-finite inv_dt or a bad box.
+ */
+rr_status rr_scalar_records(const rr_grid_desc* grid, const float* field, const float* field_prev, double inv_dt,
+                            int32_t channel, float* rec, int32_t where, const int32_t* bbox, void* stream);
+
+/*
+ * Kernels of an RR_GENERIC context, used by the steps traced after the call:
+ * K_c(chi) = k[3c] + k[3c+1] chi + k[3c+2] chi^2 for channel c = 0, 1 (chi in
+ * Mpc/h; the lensing kernel g(chi_s, chi) is {0, 1, -1/chi_s}, its derivative
+ * dg/dchi {1, -2/chi_s, 0}, a plain line integral {1, 0, 0}). Host-side only.
+ * RR_ERR_ARG on a null pointer or a non-finite coefficient, RR_ERR_STATE for
+ * a context without RR_GENERIC.
+ */
+rr_status rr_set_kernels(rr_ctx* ctx, const double k[6]);
+
+/*
+ * Move the observer (box coordinates, Mpc/h) for the steps traced after the
+ * call, keeping the ray directions: the tiling of Sec. 2.2, where each box of
+ * a tile is traced from the observer's position relative to that box's origin
+ * (with RR_PERIODIC off a ray is then traced only while it is inside the box),
+ * or the re-use of one box with a relocated observer (Sec. 6). The next step
+ * may start at any chi_a <= chi_s (the continuity check with the previous step
+ * is waived once); the step log keeps each step's observer, so the adjoint
+ * replays every step from the observer it was traced from. Host-side only.
+ * RR_ERR_ARG on a null pointer or a non-finite coordinate.
+ */
+rr_status rr_set_observer(rr_ctx* ctx, const double obs[3]);
 
 /*
  * Host helper: a conservative box of vertex (or centre) indices {x0, x1, y0,

@@ -17,16 +17,25 @@ from .batch import Batch  # noqa: E402
 from ._rr import rr_amr_create, rr_amr_destroy, rr_amr_sizes, rr_amr_tidal, rr_amr_trace_step  # noqa: E402
 from ._rr import RR_SHEAR, rr_shear  # noqa: E402
 from ._rr import RR_METHOD_A, rr_gradient_records  # noqa: E402
+from ._rr import RR_GENERIC, rr_scalar_records, rr_set_kernels, rr_set_observer  # noqa: E402
 
 __all__ = [
     "Batch", "AmrMesh", "source_kappa", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal",
     "rr_amr_trace_step", "RR_SHEAR", "rr_shear", "RR_METHOD_A", "rr_gradient_records", "trace_method_a",
-    "gradient_buffer",
+    "gradient_buffer", "RR_GENERIC", "rr_scalar_records", "rr_set_kernels", "rr_set_observer", "scalar_buffer",
+    "trace_tiles",
     "Tracer", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
     "rr_trace_backward", "TraceKappa", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
 ]
+
+
+def scalar_buffer(grid, device="cuda"):
+    """Zeroed device buffer for n0*n1*n2 scalar-pair records (generic form)."""
+    import torch
+    n = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
+    return torch.zeros((n, 2), dtype=torch.float32, device=device)
 
 
 def gradient_buffer(grid, device="cuda"):
@@ -62,16 +71,19 @@ class Tracer:
     ``moments()`` and ``source_kappa``); shear: also accumulate the shear
     (gamma1, gamma2) of Eqs. gamma1, gamma2 in the same walk (see ``shear()``);
     method_a: kappa by Method A (Eq. kappa2) from gradient records
-    (``tidal`` then writes those, 4 floats per point).
+    (``tidal`` then writes those, 4 floats per point); generic: two generic
+    integrals int K_c Q_c dchi from scalar-pair records (see ``scalars``,
+    ``set_kernels``).
     """
 
     def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False,
-                 shear: bool = False, method_a: bool = False):
+                 shear: bool = False, method_a: bool = False, generic: bool = False):
         _rr.load()
         self.bundle = bundle
         self.method_a = bool(method_a)
+        self.generic = bool(generic)
         self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums, moments=moments, shear=shear,
-                                method_a=method_a)
+                                method_a=method_a, generic=generic)
         self.ctx = rr_create(self.desc)
         self.where = RR_AT_VERTICES if int(self.desc.interp) == RR_TRILINEAR else RR_AT_CENTRES
 
@@ -101,7 +113,23 @@ class Tracer:
 
     def record_buffer(self, grid, device="cuda"):
         """An uninitialised record buffer of the kind this context traces."""
+        if self.generic:
+            return scalar_buffer(grid, device)
         return gradient_buffer(grid, device) if self.method_a else record_buffer(grid, device)
+
+    def scalars(self, grid, field, rec, channel=0, field_prev=None, inv_dt=1.0, bbox=None, stream=None):
+        """rr_scalar_records: channel ``channel`` of the scalar-pair records."""
+        _rr.rr_scalar_records(grid_desc(grid), field, field_prev, inv_dt, channel, rec, self.where, bbox, stream)
+        return rec
+
+    def set_kernels(self, kernels):
+        """(k0, k1, k2) per channel: K_c(chi) = k0 + k1 chi + k2 chi^2."""
+        _rr.rr_set_kernels(self.ctx, kernels)
+
+    def set_observer(self, obs):
+        """Move the observer for the following steps (box tiling, Sec. 2.2)."""
+        _rr.rr_set_observer(self.ctx, obs)
+        self.desc.obs[0], self.desc.obs[1], self.desc.obs[2] = (float(x) for x in obs)
 
     def footprint(self, grid, chi_a, chi_b):
         return rr_footprint_bbox(self.desc, grid_desc(grid), chi_a, chi_b)
@@ -263,6 +291,31 @@ def trace_method_a(phi, grid, bundle, steps, delta=None, footprint=True, stream=
             bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
             tr.tidal(grid, phi, rec, delta=delta, bbox=bbox, stream=stream)
             tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
+        k, kb = tr.finalize(stream=stream)
+        return k, kb, tr.segments()
+    finally:
+        tr.close()
+
+
+def trace_tiles(tiles, bundle, steps, footprint=True, stream=None):
+    """Trace one bundle through a tile of boxes (Sec. 2.2): ``tiles`` is a list
+    of (phi, grid, obs) with the observer's position relative to each box's
+    origin; each box is traced over all ``steps`` from its own observer, and
+    without wrap (the bundle's periodic flag is ignored) a ray contributes only
+    while it is inside that box. Returns the FP64 (kappa, kappa_born) maps of
+    the whole tile and the number of cell segments."""
+    import copy
+    b = copy.copy(bundle)
+    b.periodic = False
+    tr = Tracer(b)
+    try:
+        for phi, grid, obs in tiles:
+            rec = record_buffer(grid, device=phi.device)
+            tr.set_observer(obs)
+            for st in steps:
+                bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
+                tr.tidal(grid, phi, rec, bbox=bbox, stream=stream)
+                tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
         k, kb = tr.finalize(stream=stream)
         return k, kb, tr.segments()
     finally:

@@ -13,6 +13,8 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+import numpy as np
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librr.so")
 
@@ -34,6 +36,7 @@ RR_PLAIN_SUMS = 4
 RR_SOURCE_MOMENTS = 8
 RR_SHEAR = 16
 RR_METHOD_A = 32
+RR_GENERIC = 64
 RR_AT_VERTICES = 0
 RR_AT_CENTRES = 1
 
@@ -101,6 +104,9 @@ def load() -> C.CDLL:
             "rr_moments": ([P, P, P], C.c_int),
             "rr_shear": ([P, P, P, P], C.c_int),
             "rr_gradient_records": ([P, P, P, P, C.c_int32, P, P], C.c_int),
+            "rr_scalar_records": ([P, P, P, D, C.c_int32, P, C.c_int32, P, P], C.c_int),
+            "rr_set_kernels": ([P, P], C.c_int),
+            "rr_set_observer": ([P, P], C.c_int),
             "rr_source_kappa": ([P, P, C.c_int64, D, P, P, P], C.c_int),
             "rr_amr_create": ([P, P, P, C.POINTER(C.c_void_p)], C.c_int),
             "rr_amr_destroy": ([P], C.c_int),
@@ -144,7 +150,7 @@ def _stream(s):
 
 
 def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False,
-                shear: bool = False, method_a: bool = False) -> rr_bundle_desc:
+                shear: bool = False, method_a: bool = False, generic: bool = False) -> rr_bundle_desc:
     """rr_bundle_desc from any object with nx, ny, fov_x, fov_y, obs, chi_s,
     interp and periodic attributes."""
     d = rr_bundle_desc()
@@ -165,6 +171,8 @@ def bundle_desc(b, fp64_dda: bool = False, plain_sums: bool = False, moments: bo
         flags |= RR_SHEAR
     if method_a:
         flags |= RR_METHOD_A
+    if generic:
+        flags |= RR_GENERIC
     d.flags = flags
     return d
 
@@ -268,6 +276,28 @@ def rr_gradient_records(grid: rr_grid_desc, phi, delta, rec, where: int = RR_AT_
         bb = C.cast(arr, C.c_void_p)
     _check(load().rr_gradient_records(C.byref(grid), _ptr(phi), _ptr(delta), _ptr(rec), int(where), bb,
                                       _stream(stream)), "rr_gradient_records")
+
+
+def rr_scalar_records(grid: rr_grid_desc, field, field_prev, inv_dt: float, channel: int, rec,
+                      where: int = RR_AT_VERTICES, bbox=None, stream=None) -> None:
+    """Channel ``channel`` of the float2 records: field, or (field - field_prev) * inv_dt."""
+    bb = None
+    if bbox is not None:
+        arr = (C.c_int32 * 6)(*[int(x) for x in bbox])
+        bb = C.cast(arr, C.c_void_p)
+    _check(load().rr_scalar_records(C.byref(grid), _ptr(field), _ptr(field_prev), float(inv_dt), int(channel),
+                                    _ptr(rec), int(where), bb, _stream(stream)), "rr_scalar_records")
+
+
+def rr_set_kernels(ctx, kernels) -> None:
+    """kernels: (k0, k1, k2) per channel, K_c(chi) = k0 + k1 chi + k2 chi^2."""
+    k = (C.c_double * 6)(*[float(x) for x in np.asarray(kernels, dtype=np.float64).reshape(6)])
+    _check(load().rr_set_kernels(ctx, C.cast(k, C.c_void_p)), "rr_set_kernels")
+
+
+def rr_set_observer(ctx, obs) -> None:
+    o = (C.c_double * 3)(*[float(x) for x in obs])
+    _check(load().rr_set_observer(ctx, C.cast(o, C.c_void_p)), "rr_set_observer")
 
 
 def rr_tidal_tensor_adjoint(grid: rr_grid_desc, grad_rec, where: int, dL_dphi, dL_ddelta=None, stream=None) -> None:

@@ -27,12 +27,16 @@ rr_status check_bundle(const rr_bundle_desc* b)
         if (!is_finite(b->obs[a])) return RR_ERR_ARG;
     if (!is_finite(b->chi_s) || !(b->chi_s > 0)) return RR_ERR_ARG;
     if (b->interp != RR_NGP && b->interp != RR_TRILINEAR) return RR_ERR_ARG;
-    if (b->flags & ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A))
+    if (b->flags &
+        ~(RR_PERIODIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A | RR_GENERIC))
         return RR_ERR_ARG;
     if ((b->flags & RR_PLAIN_SUMS) && (b->flags & (RR_FP64_DDA | RR_SOURCE_MOMENTS))) return RR_ERR_ARG;
     if ((b->flags & RR_SOURCE_MOMENTS) && (b->flags & RR_FP64_DDA)) return RR_ERR_ARG;
     if ((b->flags & RR_SHEAR) && (b->flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS))) return RR_ERR_ARG;
     if ((b->flags & RR_METHOD_A) && (b->flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR)))
+        return RR_ERR_ARG;
+    if ((b->flags & RR_GENERIC) &&
+        (b->flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A)))
         return RR_ERR_ARG;
     return RR_OK;
 }
@@ -85,9 +89,10 @@ namespace rr {
 
 // The step geometry and the context's state pointers, as the kernels take them.
 TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
-                          double scale, double a_step)
+                          double scale, double a_step, const double* obs)
 {
     const rr_bundle_desc& b = ctx->bundle;
+    if (!obs) obs = b.obs;
     TraceArgs a;
     a.rec = reinterpret_cast<const float4*>(rec);
     a.n0 = grid->n[0]; a.n1 = grid->n[1]; a.n2 = grid->n[2];
@@ -96,8 +101,8 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     a.inv_hf = (float)a.inv_h;
     split_ff(a.inv_h, a.ihh, a.ihl);
     a.nx = b.nx; a.ny = b.ny;
-    a.obs0 = b.obs[0]; a.obs1 = b.obs[1]; a.obs2 = b.obs[2];
-    for (int i = 0; i < 3; ++i) split_ff(b.obs[i], a.oh[i], a.ol[i]);
+    a.obs0 = obs[0]; a.obs1 = obs[1]; a.obs2 = obs[2];
+    for (int i = 0; i < 3; ++i) split_ff(obs[i], a.oh[i], a.ol[i]);
     a.chi_s = b.chi_s;
     a.chi_a = chi_a;
     a.chi_b = chi_b;
@@ -119,8 +124,23 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     a.nseg = ctx->st.nseg;
     a.err = ctx->st.err;
     split_ff(scale, a.sch, a.scl);
-    split_ff(scale * 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step, a.bsh, a.bsl);
+    if (b.flags & RR_GENERIC) {
+        // both channels are plain integrals times the step's scale
+        a.bsh = a.sch;
+        a.bsl = a.scl;
+    } else {
+        split_ff(scale * 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step, a.bsh, a.bsl);
+    }
+    for (int i = 0; i < 6; ++i) a.kq[i] = (float)ctx->kq[i];
     return a;
+}
+
+StepRecord make_step_record(const rr_ctx* ctx, const rr_grid_desc* grid, double chi_a, double chi_b, double scale,
+                            double a_step)
+{
+    StepRecord r{*grid, chi_a, chi_b, scale, a_step};
+    for (int i = 0; i < 3; ++i) r.obs[i] = ctx->bundle.obs[i];
+    return r;
 }
 
 
@@ -134,7 +154,7 @@ rr_status validate_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     if (!is_finite(chi_a) || !is_finite(chi_b) || !is_finite(scale) || !is_finite(a_step) || !(a_step > 0))
         return RR_ERR_ARG;
     if (!(chi_a > chi_b) || chi_b < 0 || chi_a > ctx->bundle.chi_s * (1.0 + 1e-12)) return RR_ERR_ARG;
-    if (!ctx->log.empty()) {
+    if (!ctx->log.empty() && !ctx->relocated) {
         const double prev = ctx->log.back().chi_b;
         if (fabs(prev - chi_a) > 1e-12 * std::max(1.0, fabs(chi_a))) return RR_ERR_STATE;
     }
@@ -171,6 +191,12 @@ rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
     rr_ctx* ctx = new (std::nothrow) rr_ctx();
     if (!ctx) return RR_ERR_OOM;
     ctx->bundle = *bundle;
+    // generic form: both kernels start as the lensing kernel g = chi - chi^2 / chi_s
+    for (int c = 0; c < 2; ++c) {
+        ctx->kq[3 * c] = 0.0;
+        ctx->kq[3 * c + 1] = 1.0;
+        ctx->kq[3 * c + 2] = -1.0 / bundle->chi_s;
+    }
     cudaGetDevice(&ctx->device);
     const size_t nr = (size_t)bundle->nx * bundle->ny;
     cudaError_t e = cudaSuccess;
@@ -267,6 +293,45 @@ rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const floa
     return point_records(grid, phi, delta, rec, where, bbox, stream, 0);
 }
 
+rr_status rr_scalar_records(const rr_grid_desc* grid, const float* field, const float* field_prev, double inv_dt,
+                            int32_t channel, float* rec, int32_t where, const int32_t* bbox, void* stream)
+{
+    rr_status st = check_grid(grid);
+    if (st != RR_OK) return st;
+    if (!field || !rec || !is_aligned16(rec) || (channel != 0 && channel != 1) || !is_finite(inv_dt))
+        return RR_ERR_ARG;
+    if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
+    if (bbox) {
+        for (int a = 0; a < 3; ++a) {
+            const long long ext = (long long)bbox[2 * a + 1] - bbox[2 * a];
+            if (ext < 1 || ext > grid->n[a]) return RR_ERR_ARG;
+            if (bbox[2 * a] < -(1 << 20) || bbox[2 * a + 1] > (1 << 20)) return RR_ERR_ARG;
+        }
+    }
+    return from_cuda(launch_scalar_records(*grid, field, field_prev, (float)inv_dt, channel, rec, where, bbox,
+                                           (cudaStream_t)stream));
+}
+
+rr_status rr_set_kernels(rr_ctx* ctx, const double k[6])
+{
+    if (!ctx || !k) return RR_ERR_ARG;
+    if (!(ctx->bundle.flags & RR_GENERIC)) return RR_ERR_STATE;
+    for (int i = 0; i < 6; ++i)
+        if (!is_finite(k[i])) return RR_ERR_ARG;
+    for (int i = 0; i < 6; ++i) ctx->kq[i] = k[i];
+    return RR_OK;
+}
+
+rr_status rr_set_observer(rr_ctx* ctx, const double obs[3])
+{
+    if (!ctx || !obs) return RR_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (!is_finite(obs[i])) return RR_ERR_ARG;
+    for (int i = 0; i < 3; ++i) ctx->bundle.obs[i] = obs[i];
+    ctx->relocated = true;
+    return RR_OK;
+}
+
 rr_status rr_gradient_records(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
                               int32_t where, const int32_t* bbox, void* stream)
 {
@@ -315,10 +380,12 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
                      : (b.flags & RR_PLAIN_SUMS)   ? kFormPlain
                      : (b.flags & RR_SHEAR)        ? kFormShear
                      : (b.flags & RR_METHOD_A)     ? kFormMethodA
+                     : (b.flags & RR_GENERIC)      ? kFormGeneric
                                                    : kFormKahan;
     cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{}, form);
     if (e != cudaSuccess) return from_cuda(e);
-    ctx->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
+    ctx->log.push_back(make_step_record(ctx, grid, chi_a, chi_b, scale, a_step));
+    ctx->relocated = false;
     return RR_OK;
 }
 
@@ -399,9 +466,10 @@ rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkap
     if (!dL_dkappa && !dL_dkborn) return RR_ERR_ARG;
     if (step < 0 || step >= (int32_t)ctx->log.size()) return RR_ERR_STATE;
     const StepRecord& r = ctx->log[(size_t)step];
-    if (r.amr || (ctx->bundle.flags & (RR_SOURCE_MOMENTS | RR_METHOD_A))) return RR_ERR_STATE;
-    // the records pointer is not read by the adjoint (it needs geometry only)
-    TraceArgs a = make_trace_args(ctx, &r.grid, grad_rec, r.chi_a, r.chi_b, r.scale, r.a_step);
+    if (r.amr || (ctx->bundle.flags & (RR_SOURCE_MOMENTS | RR_METHOD_A | RR_GENERIC))) return RR_ERR_STATE;
+    // the records pointer is not read by the adjoint (it needs geometry only);
+    // the step is replayed from the observer it was traced from
+    TraceArgs a = make_trace_args(ctx, &r.grid, grad_rec, r.chi_a, r.chi_b, r.scale, r.a_step, r.obs);
     AdjArgs g;
     g.dkappa = dL_dkappa;
     g.dkborn = dL_dkborn;

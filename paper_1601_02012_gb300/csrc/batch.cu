@@ -84,7 +84,8 @@ rr_status rr_batch_create(int32_t n, const rr_bundle_desc* bundles, rr_batch** o
     for (int i = 0; i < n; ++i) {
         if (bundles[i].interp != bundles[0].interp) return RR_ERR_ARG;
         if ((bundles[i].flags & RR_FP64_DDA) != (bundles[0].flags & RR_FP64_DDA)) return RR_ERR_ARG;
-        if (bundles[i].flags & (RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A)) return RR_ERR_ARG;
+        if (bundles[i].flags & (RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A | RR_GENERIC))
+            return RR_ERR_ARG;
     }
     rr_batch* b = new (std::nothrow) rr_batch();
     if (!b) return RR_ERR_OOM;
@@ -174,7 +175,7 @@ rr_status rr_batch_set_step(rr_batch* b, int32_t i, const rr_grid_desc* grid, co
     rr_status st = validate_step(c, grid, rec, chi_a, chi_b, scale, a_step);
     if (st != RR_OK) return st;
     b->h_args[i] = make_trace_args(c, grid, rec, chi_a, chi_b, scale, a_step);
-    c->log.push_back(StepRecord{*grid, chi_a, chi_b, scale, a_step});
+    c->log.push_back(make_step_record(c, grid, chi_a, chi_b, scale, a_step));
     b->staged[(size_t)i] = true;
     return RR_OK;
 }

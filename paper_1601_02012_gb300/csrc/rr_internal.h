@@ -35,6 +35,7 @@ struct StepRecord {
     rr_grid_desc grid;
     double chi_a, chi_b, scale, a_step;
     int amr = 0;                // traced over an adaptive mesh (no adjoint)
+    double obs[3] = {0, 0, 0};  // the observer the step was traced from
 };
 
 constexpr int kAmrMaxLevel = 8;
@@ -76,6 +77,7 @@ struct TraceArgs {
     float2* bmom;
     float2* g1acc;              // gamma1, gamma2 (shear form), else unused
     float2* g2acc;
+    float kq[6];                // generic form: K_c(chi) = kq[3c] + kq[3c+1] chi + kq[3c+2] chi^2
     uint32_t* nseg;
     uint32_t* err;
     float sch, scl;             // scale (multiplies the kappa step sum), float-float
@@ -115,7 +117,7 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
                          const int32_t* bbox, cudaStream_t s, int kind = 0);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
 // Forms of the FP32 walk's sums.
-enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2, kFormShear = 3, kFormMethodA = 4 };
+enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2, kFormShear = 3, kFormMethodA = 4, kFormGeneric = 5 };
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
                          int form = kFormKahan);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
@@ -134,12 +136,20 @@ cudaError_t launch_moments(int nrays, const float2* kacc, const float2* kmom, co
                            double* out, cudaStream_t s);
 cudaError_t launch_shear_out(int nrays, const float2* g1acc, const float2* g2acc, double* gamma1, double* gamma2,
                              cudaStream_t s);
+// Scalar-pair records of the generic form: channel `channel` (0 or 1) of the
+// float2 records = field, or (field - prev) * inv_dt, at vertices or centres.
+cudaError_t launch_scalar_records(const rr_grid_desc& g, const float* field, const float* prev, float inv_dt,
+                                  int channel, float* rec, int where, const int32_t* bbox, cudaStream_t s);
 cudaError_t launch_source_kappa(const double* m_end, const double* m_k, long long nrays, double chi_k, double* kappa,
                                 double* kborn, cudaStream_t s);
 
 // The step geometry and a context's state pointers as the kernels take them.
+// (obs: the observer to trace from; NULL: the context's current one)
 TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
-                          double scale, double a_step);
+                          double scale, double a_step, const double* obs = nullptr);
+// The log entry of a step traced now from the context's current observer.
+StepRecord make_step_record(const rr_ctx* ctx, const rr_grid_desc* grid, double chi_a, double chi_b, double scale,
+                            double a_step);
 // Argument and step-order checks of rr_trace_step.
 rr_status validate_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
                         double scale, double a_step);
@@ -162,4 +172,6 @@ struct rr_ctx {
     unsigned long long last_total = 0;
     uint32_t* host_err = nullptr;             // pinned
     unsigned long long* host_total = nullptr; // pinned
+    bool relocated = false;                   // observer moved since the last step: no continuity check
+    double kq[6] = {0, 1, 0, 0, 1, 0};        // generic form kernels (set at create and by rr_set_kernels)
 };

@@ -310,7 +310,58 @@ __global__ void __launch_bounds__(NT) tidal_adjoint_kernel(TidalAdjArgs a)
     }
 }
 
+// Scalar-pair records (generic form): channel ch of the float2 record of each
+// point = Q or its 8-cell vertex mean (Sec. 2.7), with Q = field, or (field -
+// prev) * inv_dt (a finite-difference time derivative, e.g. of the potential
+// for the ISW integral). One thread per point of the box, z fastest.
+template <int MODE>
+__global__ void scalar_records_kernel(const float* __restrict__ field, const float* __restrict__ prev, float inv_dt,
+                                      int ch, float* __restrict__ rec, int n0, int n1, int n2, int x0, int y0,
+                                      int z0, int ex, int ey, int ez)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)ex * ey * ez) return;
+    const int z = (int)(i % ez), y = (int)((i / ez) % ey), x = (int)(i / ((long long)ez * ey));
+    const int px = wrapi(x0 + x, n0), py = wrapi(y0 + y, n1), pz = wrapi(z0 + z, n2);
+    auto q = [&](int cx, int cy, int cz) {
+        const size_t c = ((size_t)cx * n1 + cy) * n2 + cz;
+        const float f = __ldg(field + c);
+        return prev ? (f - __ldg(prev + c)) * inv_dt : f;
+    };
+    float v;
+    if (MODE == 0) {
+        const int xm = wrapi(px - 1, n0), ym = wrapi(py - 1, n1), zm = wrapi(pz - 1, n2);
+        v = ((q(xm, ym, zm) + q(xm, ym, pz)) + (q(xm, py, zm) + q(xm, py, pz))) +
+            ((q(px, ym, zm) + q(px, ym, pz)) + (q(px, py, zm) + q(px, py, pz)));
+        v *= 0.125f;
+    } else {
+        v = q(px, py, pz);
+    }
+    rec[2 * (((size_t)px * n1 + py) * n2 + pz) + ch] = v;
+}
+
 }  // namespace
+
+cudaError_t launch_scalar_records(const rr_grid_desc& g, const float* field, const float* prev, float inv_dt,
+                                  int channel, float* rec, int where, const int32_t* bbox, cudaStream_t s)
+{
+    int x0 = 0, y0 = 0, z0 = 0, ex = g.n[0], ey = g.n[1], ez = g.n[2];
+    if (bbox) {
+        x0 = ((bbox[0] % g.n[0]) + g.n[0]) % g.n[0]; ex = bbox[1] - bbox[0];
+        y0 = ((bbox[2] % g.n[1]) + g.n[1]) % g.n[1]; ey = bbox[3] - bbox[2];
+        z0 = ((bbox[4] % g.n[2]) + g.n[2]) % g.n[2]; ez = bbox[5] - bbox[4];
+    }
+    const long long npts = (long long)ex * ey * ez;
+    const int nt = 256;
+    const unsigned blocks = (unsigned)((npts + nt - 1) / nt);
+    if (where == RR_AT_VERTICES)
+        scalar_records_kernel<0><<<blocks, nt, 0, s>>>(field, prev, inv_dt, channel, rec, g.n[0], g.n[1], g.n[2], x0,
+                                                       y0, z0, ex, ey, ez);
+    else
+        scalar_records_kernel<1><<<blocks, nt, 0, s>>>(field, prev, inv_dt, channel, rec, g.n[0], g.n[1], g.n[2], x0,
+                                                       y0, z0, ex, ey, ez);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s, int kind)

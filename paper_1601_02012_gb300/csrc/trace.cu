@@ -63,15 +63,19 @@ __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], in
 // Eq. kappa2, on gradient records {grad Phi, delta}: the first channel
 // integrates n . grad Phi with the kernel dg/dchi and adds the step's surface
 // terms -g n.grad Phi at the start and +g n.grad Phi at the end of the traced
-// interval (Eq. 2nterm); the second is the Born term as in the other forms).
+// interval (Eq. 2nterm); the second is the Born term as in the other forms) or
+// kFormGeneric (two scalar fields from float2 records, each with its own
+// quadratic kernel K(chi): the generic integrals of Eqs. Ic, Icfinal).
 template <int INTERP, class R, int FORM = kFormKahan>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
     constexpr bool F64 = sizeof(R) == 8;
     constexpr bool SH = !F64 && FORM == kFormShear;
     constexpr bool MA = !F64 && FORM == kFormMethodA;
-    // one record per point: 2 float4 of the tidal tensor, or 1 gradient float4
-    using PR = typename std::conditional<MA, float4, Rec>::type;
+    constexpr bool GEN = !F64 && FORM == kFormGeneric;
+    // one record per point: 2 float4 of the tidal tensor, 1 gradient float4
+    // (Method A) or a float2 scalar pair (generic form)
+    using PR = typename std::conditional<MA, float4, typename std::conditional<GEN, float2, Rec>::type>::type;
     const long long rid = (long long)iy * A.nx + ix;
     const int nn[3] = {A.n0, A.n1, A.n2};
     RayRange rg;
@@ -116,11 +120,13 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     const int max_iter = W.max_iter;
     auto fetch = [&](long long i) -> PR {
         if constexpr (MA) return load_grad_rec(A.rec, i);
+        else if constexpr (GEN) return __ldg(reinterpret_cast<const float2*>(A.rec) + i);
         else return load_rec(A.rec, i);
     };
     // (the channel pair the walk integrates) of a record
     auto pair = [&](const PR& r) -> float2 {
         if constexpr (MA) return radial_pair(nd, r);
+        else if constexpr (GEN) return r;
         else return make_float2(project(w, r), r.b.z);
     };
     // a sub-step that resumes inside the previous one's last cell does not
@@ -236,6 +242,24 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                 } else {
                     s2.add(segment_ngp(q2[0], t, chiA, -1.f, 0.f));
                     s2m.add(segment_ngp(q2[0], t, chiA * chiA, -2.f * chiA, 1.f));
+                }
+            } else if constexpr (GEN) {
+                // each channel's kernel about the entry point: K(chi_A - s) =
+                // K(chi_A) - K'(chi_A) s + k2 s^2
+                const float chiA = chiA0 - sig;
+                const float2 G0 = make_float2(fmaf(chiA, fmaf(chiA, A.kq[2], A.kq[1]), A.kq[0]),
+                                              fmaf(chiA, fmaf(chiA, A.kq[5], A.kq[4]), A.kq[3]));
+                const float2 G1 = make_float2(-fmaf(2.f * A.kq[2], chiA, A.kq[1]), -fmaf(2.f * A.kq[5], chiA, A.kq[4]));
+                const float2 G2 = make_float2(A.kq[2], A.kq[5]);
+                if (INTERP == RR_TRILINEAR) {
+                    float2 e2[4];
+                    line_cubic2(q2, bc2(u[0]), bc2(u[1]), bc2(u[2]), bc2(v[0]), bc2(v[1]), bc2(v[2]), e2);
+                    s2.add(dot_kernel_pair(e2, t, G0, G1, G2));
+                } else {
+                    const float2 tt = bc2(t);
+                    const float2 J1 = __fmul2_rn(tt, __ffma2_rn(tt, __ffma2_rn(tt, __fmul2_rn(G2, bc2(1.f / 3.f)),
+                                                                              __fmul2_rn(G1, bc2(0.5f))), G0));
+                    s2.add(__fmul2_rn(q2[0], J1));
                 }
             } else if constexpr (MA) {
                 float G0, G1, G2;
@@ -443,6 +467,11 @@ cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStre
     if (form == kFormMoments && !fp64_dda) {
         if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
         else trace_kernel<RR_NGP, float, kFormMoments><<<grid, nt, 0, s>>>(a, t);
+        return cudaGetLastError();
+    }
+    if (form == kFormGeneric && !fp64_dda) {
+        if (interp == RR_TRILINEAR) trace_kernel<RR_TRILINEAR, float, kFormGeneric><<<grid, nt, 0, s>>>(a, t);
+        else trace_kernel<RR_NGP, float, kFormGeneric><<<grid, nt, 0, s>>>(a, t);
         return cudaGetLastError();
     }
     if (form == kFormMethodA && !fp64_dda) {

@@ -244,6 +244,24 @@ __device__ __forceinline__ float2 segment_ngp_a(float2 q, float t, float G0, flo
     return __fmul2_rn(q, make_float2(L1, J1));
 }
 
+// Two channels with their own quadratic kernels, K_c(chi_A - s) = G0c + G1c s
+// + G2c s^2 (the generic form): sum_N e_{N-1} (J_N(x), J_N(y)).
+__device__ __forceinline__ float2 dot_kernel_pair(const float2 e2[4], float t, float2 G0, float2 G1, float2 G2)
+{
+    const float2 t1 = bc2(t), t2 = bc2(t * t);
+    const float2 t3 = __fmul2_rn(t2, t1), t4 = __fmul2_rn(t2, t2);
+    // J_N = t^N (G0 / N + t (G1 / (N+1) + t G2 / (N+2)))
+    auto J = [&](float2 tn, float a, float b, float c) {
+        const float2 in = __ffma2_rn(t1, __ffma2_rn(t1, __fmul2_rn(G2, bc2(c)), __fmul2_rn(G1, bc2(b))),
+                                     __fmul2_rn(G0, bc2(a)));
+        return __fmul2_rn(tn, in);
+    };
+    float2 x = __fmul2_rn(e2[0], J(t1, 1.f, 0.5f, 1.f / 3.f));
+    x = __ffma2_rn(e2[1], J(t2, 0.5f, 1.f / 3.f, 0.25f), x);
+    x = __ffma2_rn(e2[2], J(t3, 1.f / 3.f, 0.25f, 0.2f), x);
+    return __ffma2_rn(e2[3], J(t4, 0.25f, 0.2f, 1.f / 6.f), x);
+}
+
 // First channel of the trilinear field of the mirrored corners q at the
 // mirrored point u (the constant term of the line cubic there).
 __device__ __forceinline__ float trilinear_x(const float2 q[8], float u0, float u1, float u2)

@@ -51,7 +51,7 @@ def test_argument_validation_is_host_side(rr):
     good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
     h = C.c_void_p()
     assert lib.rr_create(None, C.byref(h)) == rr.RR_ERR_ARG
-    for field, val in (("nx", 0), ("fov_x", -0.1), ("fov_y", 4.0), ("chi_s", 0.0), ("interp", 7), ("flags", 64)):
+    for field, val in (("nx", 0), ("fov_x", -0.1), ("fov_y", 4.0), ("chi_s", 0.0), ("interp", 7), ("flags", 128)):
         bad = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
         setattr(bad, field, val)
         assert lib.rr_create(C.byref(bad), C.byref(h)) == rr.RR_ERR_ARG, field
@@ -139,7 +139,7 @@ def test_source_kappa_validation_is_host_side(rr):
     assert lib.rr_moments(None, C.c_void_p(16), None) == rr.RR_ERR_ARG
     good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
     h = C.c_void_p()
-    for flags in (rr.RR_SOURCE_MOMENTS | rr.RR_FP64_DDA, rr.RR_SOURCE_MOMENTS | rr.RR_PLAIN_SUMS, 64):
+    for flags in (rr.RR_SOURCE_MOMENTS | rr.RR_FP64_DDA, rr.RR_SOURCE_MOMENTS | rr.RR_PLAIN_SUMS, 128):
         good.flags = flags
         assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG
 
@@ -154,6 +154,23 @@ def test_method_a_validation_is_host_side(rr):
     h = C.c_void_p()
     for other in (rr.RR_FP64_DDA, rr.RR_PLAIN_SUMS, rr.RR_SOURCE_MOMENTS, rr.RR_SHEAR):
         good.flags = rr.RR_METHOD_A | other
+        assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG
+
+
+def test_generic_and_relocation_validation_is_host_side(rr):
+    lib = rr.load()
+    g = rr.grid_desc(synth.Grid((8, 8, 8), 16.0))
+    f = C.c_void_p(16)
+    assert lib.rr_scalar_records(C.byref(g), None, None, 1.0, 0, f, 0, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_scalar_records(C.byref(g), f, None, 1.0, 2, f, 0, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_scalar_records(C.byref(g), f, None, float("inf"), 0, f, 0, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_scalar_records(C.byref(g), f, None, 1.0, 0, C.c_void_p(8), 0, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_set_kernels(None, f) == rr.RR_ERR_ARG
+    assert lib.rr_set_observer(None, f) == rr.RR_ERR_ARG
+    good = rr.bundle_desc(synth.Bundle(4, 4, 0.1, 0.1, (1, 1, 0), 10.0))
+    h = C.c_void_p()
+    for other in (rr.RR_FP64_DDA, rr.RR_PLAIN_SUMS, rr.RR_SOURCE_MOMENTS, rr.RR_SHEAR, rr.RR_METHOD_A):
+        good.flags = rr.RR_GENERIC | other
         assert lib.rr_create(C.byref(good), C.byref(h)) == rr.RR_ERR_ARG
 
 
