@@ -718,6 +718,55 @@ def _method_a_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, kappa_p
                     "the density term with a = 1 (delta derived from the scaled potential)"}
 
 
+def _generic_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, kappa_pass_ms, reps=3):
+    """Time a pass of the generic form (two scalar fields with their own
+    quadratic kernels, Eqs. Ic, Icfinal) set up as the ISW integral of Sec. 6:
+    channel 0 integrates (Phi_a - Phi_b) / dt between each step's potential and
+    the previous step's, channel 1 the potential with the lensing kernel.
+    Scalar-pair records are 8 B per point."""
+    nst = len(steps)
+    trg = rrp.Tracer(w.bundle, generic=True)
+    trg.set_kernels(((2.0, 0.0, 0.0), (0.0, 1.0, -1.0 / w.bundle.chi_s)))
+    recg = trg.record_buffer(w.grid, device=phi.device)
+    prev = torch.empty_like(phi)
+    cur = torch.empty_like(phi)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+    o1 = torch.empty((w.bundle.ny, w.bundle.nx), dtype=torch.float64, device=phi.device)
+    o2 = torch.empty_like(o1)
+
+    def pass_g(timed):
+        rrp.rr_reset(trg.ctx, stream)
+        for i, st in enumerate(steps):
+            sp = steps[i - 1].scale if i > 0 else st.scale
+            torch.mul(phi, sp, out=prev)
+            torch.mul(phi, st.scale, out=cur)
+            if timed:
+                ev[i][0].record(stream)
+            rrp.rr_scalar_records(gd, cur, prev, 100.0, 0, recg, trg.where, bboxes[i], stream)
+            rrp.rr_scalar_records(gd, cur, None, 1.0, 1, recg, trg.where, bboxes[i], stream)
+            rrp.rr_trace_step(trg.ctx, gd, recg, st.chi_a, st.chi_b, 1.0, st.a, stream)
+            if timed:
+                ev[i][1].record(stream)
+        rrp.rr_finalize(trg.ctx, o1, o2, stream)
+
+    with torch.cuda.stream(stream):
+        pass_g(False)
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            pass_g(True)
+            torch.cuda.synchronize()
+            ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        segs = trg.segments()
+    trg.close()
+    del recg, prev, cur
+    t = sum(ms) / reps
+    return {"ms_per_pass": t, "method_b_ms_per_pass": kappa_pass_ms, "segments_per_s": segs / (t / 1e3),
+            "note": "records (2 channels) and trace kernels of one pass of the generic form set up as the "
+                    "ISW integral (channel 0: (Phi_a - Phi_prev) / dt with K = 2; channel 1: Phi with K = g), "
+                    f"CUDA events per step, L2 flushed before each pass, mean of {reps}"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -893,6 +942,7 @@ def main():
         sources = None
         shear = None
         method_a = None
+        generic = None
         if world == 1:
             sources = _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush)
             # the shear in the same walk (Eqs. gamma1, gamma2)
@@ -906,6 +956,8 @@ def main():
             # Method A (Eq. kappa2) in the same configuration
             method_a = _method_a_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush,
                                       total_ms / args.steps, kappa)
+            # generic K.Q integrals (the ISW set-up of Sec. 6)
+            generic = _generic_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, total_ms / args.steps)
 
     if rank != 0:
         dist.barrier()
@@ -954,6 +1006,7 @@ def main():
         "source_redshifts": sources,
         "shear": shear,
         "method_a": method_a,
+        "generic_isw": generic,
         "gpu_launches": args.steps * (2 * nst + 1),
         "clocks": clocks,
         "trace_src": h,
