@@ -47,8 +47,8 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     if (!ray_range(A, rid, rg)) return;
     const float chis = (float)A.chi_s;
     const float ichis = A.inv_chi_s_f;
-    const int nsub = max(1, (int)ceilf(rg.Lf / A.sub_len));
-    const float dsub = rg.Lf / (float)nsub;
+    const int nsub = max(1, f2i_signed(fminf(ceilf(rg.Lf / A.sub_len), 4194303.f)));
+    const float dsub = rg.Lf / i2f_exact(nsub);
     const int L = M.lmax;
     // slivers: as in the uniform walk, 4 ulp of the path
     const float eps_rel = 4.76837158203125e-07f;
@@ -59,9 +59,9 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     int prev_leaf = -1;   // leaf of the last integrated segment
     for (int j = 0; j < nsub && !overflow; ++j) {
         float bh, bl, Lj, D0j;
-        sub_step(rg, j, nsub, dsub, bh, bl, Lj, D0j);
+        sub_step<true>(rg, j, nsub, dsub, bh, bl, Lj, D0j);
         Walk<float> W;
-        walk_setup<float>(A, rid, bh, bl, Lj, D0j, rg.hi, rg.lo, W);
+        walk_setup<float, true>(A, rid, bh, bl, Lj, D0j, rg.hi, rg.lo, W);
         const float Ls = W.L, chiA0 = W.chiA0, D0 = W.D0;
         const float eps_end = Ls * eps_rel;
         int q[3] = {W.c[0], W.c[1], W.c[2]};   // finest cell of the current point

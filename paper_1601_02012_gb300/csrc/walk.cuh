@@ -314,6 +314,12 @@ __device__ __forceinline__ void shear_weights(float4 n, float w1[6], float w2[6]
 // (the bit pattern of 2^23 + i), instead of the conversion unit
 __device__ __forceinline__ float i2f_exact(int i) { return __int_as_float(0x4B000000 | i) - 8388608.f; }
 __device__ __forceinline__ int f2i_exact(float f) { return __float_as_int(f + 8388608.f) - 0x4B000000; }
+// a float holding an integer of either sign to int: exact through the bit
+// pattern of 1.5 * 2^23 + f for |f| < 2^22, the conversion unit otherwise
+__device__ __forceinline__ int f2i_signed(float f)
+{
+    return fabsf(f) < 4194304.f ? __float_as_int(f + 12582912.f) - 0x4B400000 : (int)f;
+}
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x)
 {
@@ -399,7 +405,11 @@ __device__ __forceinline__ bool ray_range(const TraceArgs& A, long long rid, Ray
 
 // Sub-step j of nsub equal pieces of the FP32 walk: start (bh + bl) =
 // chi_hi - j dsub as a float-float pair (exact: TwoProd and TwoSum), length,
-// and chi_s - start. Consecutive sub-steps meet at the same point.
+// and chi_s - start. Consecutive sub-steps meet at the same point. EXACT:
+// integers become floats through the exact bit pattern instead of the
+// conversion unit (same values; measured faster in the adaptive-mesh walk,
+// slower in the uniform one, where the conversions are rare).
+template <bool EXACT = false>
 __device__ __forceinline__ void sub_step(const RayRange& g, int j, int nsub, float dsub, float& bh, float& bl,
                                          float& L, float& D0)
 {
@@ -408,19 +418,22 @@ __device__ __forceinline__ void sub_step(const RayRange& g, int j, int nsub, flo
         return;
     }
     float p, pe;
-    two_prod((float)j, dsub, p, pe);
+    const float fj = EXACT ? i2f_exact(j) : (float)j;
+    two_prod(fj, dsub, p, pe);
     float s, t;
     two_sum(g.ch, -p, s, t);
     const float lo = t + (g.cl - pe);
     bh = s + lo;
     bl = lo - (bh - s);
-    L = (j == nsub - 1) ? fmaf(-(float)(nsub - 1), dsub, g.Lf) : dsub;
-    D0 = fmaf((float)j, dsub, g.D0f);
+    L = (j == nsub - 1) ? fmaf(-(EXACT ? i2f_exact(nsub - 1) : (float)(nsub - 1)), dsub, g.Lf) : dsub;
+    D0 = fmaf(fj, dsub, g.D0f);
 }
 
 // Start point (bh + bl, or hi in FP64), start cell and crossing distances of
-// ray `rid` for a walk of length Lf (see the file comment).
-template <class R>
+// ray `rid` for a walk of length Lf (see the file comment). EXACT: as for
+// sub_step (the start cell through the exact bit pattern, the periodic wrap
+// only for cells outside [0, n)).
+template <class R, bool EXACT = false>
 __device__ __forceinline__ void walk_setup(const TraceArgs& A, long long rid, float ch, float cl, float Lf,
                                            float D0f, double hi, double lo, Walk<R>& W)
 {
@@ -477,14 +490,17 @@ __device__ __forceinline__ void walk_setup(const TraceArgs& A, long long rid, fl
             }
             // exactly on a face while moving toward -a: the cell below
             if (nh[a] > 0.f && f == 0.f) { fl -= 1.f; f = 1.f; g = 0.f; }
-            cell = (long long)fl;
+            if constexpr (EXACT) cell = f2i_signed(fl);
+            else cell = (long long)fl;
             flo = f;
             fhi = g;
         }
         int ci = (int)cell;
         if (A.periodic) {
-            ci %= nn[a];
-            if (ci < 0) ci += nn[a];
+            if (!EXACT || (unsigned)ci >= (unsigned)nn[a]) {
+                ci %= nn[a];
+                if (ci < 0) ci += nn[a];
+            }
         } else if (ci < 0) {
             ci = 0; flo = (R)0; fhi = (R)1;
         } else if (ci >= nn[a]) {
@@ -529,8 +545,9 @@ __device__ __forceinline__ void walk_setup(const TraceArgs& A, long long rid, fl
     W.L = F64 ? (R)(hi - lo) : (R)Lf;
     W.chiA0 = F64 ? (R)hi : (R)ch;
     W.D0 = F64 ? (R)(A.chi_s - hi) : (R)D0f;
-    W.max_iter =
-        (int)ceilf(Lf * (fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2])) * A.inv_hf * 1.0001f) + 8;
+    const float cap = ceilf(Lf * (fabsf(nh[0]) + fabsf(nh[1]) + fabsf(nh[2])) * A.inv_hf * 1.0001f);
+    if constexpr (EXACT) W.max_iter = cap < 4194304.f ? f2i_signed(cap) + 8 : 0x3fffffff;
+    else W.max_iter = (int)cap + 8;
 }
 
 }  // namespace
