@@ -70,8 +70,9 @@ __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], in
 // cell's two vertex planes per axis (entry and exit side) instead of vertex
 // indices, so that a record's offset is two additions (6.5 % faster on the
 // production workload; 32-bit offsets measured slower, the walk then spills).
-// The persistent batch kernel, which also holds its staged arguments, keeps
-// vertex indices (plane offsets measured 2.6 % slower there).
+// Only the default form uses them: the persistent batch kernel, which also
+// holds its staged arguments, and the forms with more per-segment state
+// (moments, shear, Method A, generic) measured 1.5-4 % slower with them.
 template <int INTERP, class R, int FORM = kFormKahan, bool PLANES = true>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, con
 {
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
-    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM>(A, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM, FORM == kFormKahan>(A, ix, iy);
 }
 
 // Persistent work queue over the ray tiles of many bundles (lightcones): each
