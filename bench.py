@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), per
 # (kernel source, workload): valid only for the source it was taken on (sha256
 # of csrc/trace.cu + csrc/walk.cuh) and for that workload.
-TRACE_TRAFFIC = {("e3a2be46dd18a4ec", "prod_512"): 274_823_424}
+TRACE_TRAFFIC = {("e3309eba94146260", "prod_512"): 274_965_760}
 
 
 def _src_hash(*names):
