@@ -75,6 +75,7 @@ def _L():
         _lib.ora_amr_vertex_weights.restype = C.c_long
         _lib.ora_amr_tidal.argtypes = [P, P]
         _lib.ora_amr_leaf_vertices.argtypes = [P, C.c_int, P, P]
+        _lib.ora_amr_trace_step_shear.argtypes = [P, P, C.c_double, C.c_double, C.c_double, P, P, P, C.c_long]
         _lib.ora_amr_trace_step.argtypes = [P, P, C.c_double, C.c_double, C.c_double, C.c_double, P, P, P, P,
                                             C.c_long, C.c_int]
     return _lib
@@ -351,6 +352,36 @@ def amr_leaf_vertices(mesh, level, cell):
     if _L().ora_amr_leaf_vertices(C.byref(h.desc), int(level), _ptr(c), _ptr(out)) != 0:
         raise ValueError("oracle: AMR vertex failed")
     return out
+
+
+def _amr_bundle(bundle):
+    b = _AmrBundle()
+    b.nx, b.ny = int(bundle.nx), int(bundle.ny)
+    b.fov_x, b.fov_y = float(bundle.fov_x), float(bundle.fov_y)
+    for i in range(3):
+        b.obs[i] = float(bundle.obs[i])
+    b.chi_s = float(bundle.chi_s)
+    b.interp = int(bundle.interp)
+    b.periodic = 1 if bundle.periodic else 0
+    return b
+
+
+def amr_trace_shear(bundle, mesh, steps, rids=None):
+    """The shear (gamma1, gamma2) of Eqs. gamma1, gamma2 through an adaptive
+    mesh, per ray in rayid order or in the order of ``rids``."""
+    h = AmrHandle(mesh)
+    b = _amr_bundle(bundle)
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
+    g1 = np.zeros(nr, np.float64)
+    g2 = np.zeros(nr, np.float64)
+    for st in steps:
+        rc = _L().ora_amr_trace_step_shear(C.byref(b), C.byref(h.desc), float(st.chi_a), float(st.chi_b),
+                                           float(st.scale), _ptr(g1), _ptr(g2), _ptr(ids),
+                                           0 if ids is None else len(ids))
+        if rc != 0:
+            raise ValueError(f"oracle: AMR trace failed ({rc})")
+    return g1, g2
 
 
 def amr_trace(bundle, mesh, steps, rids=None) -> TraceResult:

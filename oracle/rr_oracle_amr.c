@@ -26,7 +26,10 @@
  *   - the walk: every face of the finest lattice crossed by the ray, merged
  *     over the three axes; consecutive pieces in the same leaf form one leaf
  *     segment; per leaf segment the integrals of rr_oracle.c with the leaf's
- *     own size h.
+ *     own size h;
+ *   - the shear (Eqs. gamma1, gamma2) by the same walk with the weights of
+ *     rr_oracle.c's shear (printed Eqs. n1n1 - n2n2; Eq. n1n2 read in the
+ *     orthonormal frame).
  */
 #include <math.h>
 #include <stdint.h>
@@ -482,11 +485,32 @@ static void neu_add_a(neu_a* s, double x)
 /*
  * One step [chi_b, chi_a] for the listed rays (or all rays when rids is NULL):
  * kappa, kborn += scale * (integrals); nseg += leaf segments. Outputs follow
- * the list order (or rayid order).
+ * the list order (or rayid order). shear: the two channels are the shear
+ * gamma1, gamma2 (Eqs. gamma1, gamma2) instead: Q = n1n1 - n2n2 from the
+ * printed Eqs. (n1n1), (n2n2), and Q = 2 n1n2 with Eq. (n1n2) in its
+ * orthonormal reading (the printed form times sin theta).
  */
+static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
+                     double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids, long nrids,
+                     int shear);
+
 int ora_amr_trace_step(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
                        double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids,
                        long nrids, int nthreads)
+{
+    (void)nthreads;
+    return amr_trace(b, d, chi_a, chi_b, scale, a_step, kappa, kborn, nseg, rids, nrids, 0);
+}
+
+int ora_amr_trace_step_shear(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b,
+                             double scale, double* gamma1, double* gamma2, const int64_t* rids, long nrids)
+{
+    return amr_trace(b, d, chi_a, chi_b, scale, 1.0, gamma1, gamma2, NULL, rids, nrids, 1);
+}
+
+static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
+                     double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids, long nrids,
+                     int shear)
 {
     if (!(chi_a > chi_b) || chi_b < 0.0) return -1;
     amr_t A;
@@ -496,7 +520,6 @@ int ora_amr_trace_step(const ora_amr_bundle* b, const ora_amr_desc* d, double ch
     const double hf = h0 / (double)((int64_t)1 << d->lmax);
     const long nr = rids ? nrids : (long)b->nx * b->ny;
     int err = 0;
-    (void)nthreads;
     /* single thread: the memoised tidal field is shared */
     for (long slot = 0; slot < nr && !err; ++slot) {
         const long rid = rids ? (long)rids[slot] : slot;
@@ -510,6 +533,22 @@ int ora_amr_trace_step(const ora_amr_bundle* b, const ora_amr_desc* d, double ch
         double s2p = 2.0 * sp * cp, s2t = sin(2.0 * th);
         double w[6] = {sp * sp + cp * cp * ct * ct, cp * cp + sp * sp * ct * ct, st * st, -s2p + s2p * ct * ct,
                        -cp * s2t, -sp * s2t};
+        double w2[6] = {0, 0, 0, 0, 0, 0};
+        if (shear) {
+            /* Eqs. (n1n1) - (n2n2) */
+            w[0] = sp * sp - cp * cp * ct * ct;
+            w[1] = cp * cp - sp * sp * ct * ct;
+            w[2] = -st * st;
+            w[3] = -s2p - s2p * ct * ct;
+            w[4] = cp * s2t;
+            w[5] = sp * s2t;
+            /* 2 n1n2, Eq. (n1n2) times sin theta */
+            w2[0] = -2.0 * ct * cp * sp;
+            w2[1] = 2.0 * ct * cp * sp;
+            w2[3] = 2.0 * ct * (cp * cp - sp * sp);
+            w2[4] = 2.0 * st * sp;
+            w2[5] = -2.0 * st * cp;
+        }
         double lo = chi_b, hi = chi_a;
         if (!b->periodic) {
             for (int a = 0; a < 3; ++a) {
@@ -579,10 +618,13 @@ int ora_amr_trace_step(const ora_amr_bundle* b, const ora_amr_desc* d, double ch
                     if (b->interp == 0) {
                         double H[7];
                         if (tidal_at(&A, cur_l, cur_c[0], cur_c[1], cur_c[2], H) != 0) { err = 1; break; }
-                        double qk = 0;
-                        for (int q = 0; q < 6; ++q) qk += w[q] * H[q];
+                        double qk = 0, q2 = 0;
+                        for (int q = 0; q < 6; ++q) {
+                            qk += w[q] * H[q];
+                            q2 += w2[q] * H[q];
+                        }
                         ik = ic_ngp_a(qk, segA, segB, b->chi_s);
-                        ib = ic_ngp_a(bpref * H[6], segA, segB, b->chi_s);
+                        ib = ic_ngp_a(shear ? q2 : bpref * H[6], segA, segB, b->chi_s);
                     } else {
                         double Qk[8], Qb[8];
                         const int64_t step = (int64_t)1 << (d->lmax - cur_l);
@@ -592,8 +634,12 @@ int ora_amr_trace_step(const ora_amr_bundle* b, const ora_amr_desc* d, double ch
                             double val[7];
                             if (vertex_value(&A, V, val) != 0) { err = 1; break; }
                             Qk[t] = 0;
-                            for (int q = 0; q < 6; ++q) Qk[t] += w[q] * val[q];
-                            Qb[t] = bpref * val[6];
+                            double q2 = 0;
+                            for (int q = 0; q < 6; ++q) {
+                                Qk[t] += w[q] * val[q];
+                                q2 += w2[q] * val[q];
+                            }
+                            Qb[t] = shear ? q2 : bpref * val[6];
                         }
                         if (err) break;
                         double P1[3] = {(double)ucell[0] * hl, (double)ucell[1] * hl, (double)ucell[2] * hl};
