@@ -65,8 +65,8 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
        RR_SHEAR = 16,       /* rays also accumulate the shear gamma1, gamma2 (Eqs.
                                gamma1, gamma2) in the same walk as kappa (rr_shear);
                                FP32 walk with compensated sums; rr_create /
-                               rr_trace_step only; not with RR_FP64_DDA,
-                               RR_PLAIN_SUMS or RR_SOURCE_MOMENTS */
+                               rr_trace_step / rr_amr_trace_step; not with
+                               RR_FP64_DDA, RR_PLAIN_SUMS or RR_SOURCE_MOMENTS */
        RR_METHOD_A = 32,    /* Method A (Eq. kappa2): rr_trace_step reads gradient
                                records (rr_gradient_records) and accumulates the
                                density term (kappa_born) and, separately, the
@@ -493,9 +493,11 @@ rr_status rr_amr_tidal(rr_amr* mesh, const float* phi, int32_t where, float* lea
  * crossings of the finest lattice grouped per leaf, Sec. 2.5.1) and adds the
  * integrals of rr_trace_step with each leaf's own cell size. `leaf_rec` from
  * rr_amr_tidal with RR_AT_VERTICES for RR_TRILINEAR bundles, RR_AT_CENTRES for
- * RR_NGP. Segment counts count leaf segments. RR_ERR_ARG for RR_FP64_DDA
- * bundles (the AMR walk is the FP32 float-float form only); other checks and
- * the step log as rr_trace_step. Steps traced this way have no adjoint:
+ * RR_NGP. Segment counts count leaf segments. An RR_SHEAR context also
+ * accumulates the shear (rr_shear). RR_ERR_ARG for RR_FP64_DDA bundles (the
+ * AMR walk is the FP32 float-float form only) and for the other optional
+ * forms (RR_PLAIN_SUMS, RR_SOURCE_MOMENTS, RR_METHOD_A, RR_GENERIC); other
+ * checks and the step log as rr_trace_step. Steps traced this way have no adjoint:
  * rr_trace_step_adjoint and rr_trace_backward return RR_ERR_STATE for them.
  */
 rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* mesh, const float* leaf_rec, double chi_a, double chi_b,

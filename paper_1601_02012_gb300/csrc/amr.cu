@@ -833,7 +833,7 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, doubl
                             double scale, double a_step, void* stream)
 {
     if (!ctx || !A) return RR_ERR_ARG;
-    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_SHEAR | RR_METHOD_A | RR_GENERIC))
+    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_METHOD_A | RR_GENERIC))
         return RR_ERR_ARG;
     rr_grid_desc g;   // the coarse grid: argument and step-order checks
     g.n[0] = g.n[1] = g.n[2] = A->h.n;
@@ -851,7 +851,8 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, doubl
     m.link = A->d_link;
     m.n = A->h.n;
     m.lmax = A->h.lmax;
-    const cudaError_t e = launch_trace_amr(a, m, ctx->bundle.interp, (cudaStream_t)stream);
+    const cudaError_t e =
+        launch_trace_amr(a, m, ctx->bundle.interp, (cudaStream_t)stream, (ctx->bundle.flags & RR_SHEAR) != 0);
     if (e != cudaSuccess) return status_of_cuda(e);
     StepRecord r = make_step_record(ctx, &g, chi_a, chi_b, scale, a_step);
     r.amr = 1;

@@ -16,7 +16,9 @@
 // value; the segment integral is that of the uniform walk with the leaf's own
 // cell size. Consecutive segments in the same leaf (separated only by a
 // rounding sliver at an edge or corner) are one leaf segment, so the segment
-// count is the number of leaf segments.
+// count is the number of leaf segments. SH: also the shear (gamma1, gamma2) of
+// Eqs. gamma1, gamma2, a second projection of the same corner records carried
+// through the same segment integrals.
 #include "walk.cuh"
 
 namespace rr {
@@ -38,7 +40,7 @@ __device__ __forceinline__ int amr_locate(const AmrDevice& M, const int q[3], in
     return v < 0 ? -1 : v;
 }
 
-template <int INTERP>
+template <int INTERP, bool SH>
 __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevice& M, int ix, int iy)
 {
     const long long rid = (long long)iy * A.nx + ix;
@@ -54,6 +56,9 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     const float eps_rel = 4.76837158203125e-07f;
 
     Acc2 s2;   // (kappa, Born kappa) Kahan pairs
+    Acc2 sg;   // (gamma1, gamma2), shear only
+    float w1[6], w2[6];
+    if constexpr (SH) shear_weights(A.dirh[rid], w1, w2);
     uint32_t cnt = 0;
     bool overflow = false;
     int prev_leaf = -1;   // leaf of the last integrated segment
@@ -101,6 +106,7 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
 
             if (t > tend * eps_rel) {
                 float2 q2[8];   // (Q_kappa, delta) at the mirrored corners, or the leaf's own value
+                float2 g2[SH ? 8 : 1];   // (Q_gamma1, Q_gamma2) there
                 if (INTERP == RR_TRILINEAR) {
                     const float4* r = A.rec + 16 * (long long)leaf;
 #pragma unroll
@@ -110,10 +116,12 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                         x.a = __ldg(r + 2 * rc);
                         x.b = __ldg(r + 2 * rc + 1);
                         q2[c] = make_float2(project(W.w, x), x.b.z);
+                        if constexpr (SH) g2[c] = make_float2(project(w1, x), project(w2, x));
                     }
                 } else {
                     const Rec x = load_rec(A.rec, leaf);
                     q2[0] = make_float2(project(W.w, x), x.b.z);
+                    if constexpr (SH) g2[0] = make_float2(project(w1, x), project(w2, x));
                 }
                 float G0, G1, G2;
                 kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
@@ -126,8 +134,11 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                                             : (i2f_exact(jp[a]) + W.cu[a]) * inv_span;
                     }
                     s2.add(segment_trilinear(q2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
+                    if constexpr (SH)
+                        sg.add(segment_trilinear(g2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
                 } else {
                     s2.add(segment_ngp(q2[0], t, G0, G1, G2));
+                    if constexpr (SH) sg.add(segment_ngp(g2[0], t, G0, G1, G2));
                 }
                 if (leaf != prev_leaf) ++cnt;
                 prev_leaf = leaf;
@@ -171,25 +182,38 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     A.kacc[rid] = ff_mul_add(A.kacc[rid], kh, kl, A.sch, A.scl);
     A.bacc[rid] = ff_mul_add(A.bacc[rid], bh, bl, A.bsh, A.bsl);
     A.nseg[rid] += cnt;
+    if constexpr (SH) {
+        if (!sg.finite()) atomicOr(A.err, kErrNonFinite);
+        float gh, gl;
+        two_sum(sg.s.x, -sg.c.x, gh, gl);
+        A.g1acc[rid] = ff_mul_add(A.g1acc[rid], gh, gl, A.sch, A.scl);
+        two_sum(sg.s.y, -sg.c.y, gh, gl);
+        A.g2acc[rid] = ff_mul_add(A.g2acc[rid], gh, gl, A.sch, A.scl);
+    }
 }
 
-template <int INTERP>
+template <int INTERP, bool SH>
 __global__ void __launch_bounds__(NT_MAX, 2) trace_amr_kernel(const TraceArgs A, const AmrDevice M, const TileCfg t)
 {
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
-    if (ix < A.nx && iy < A.ny) trace_ray_amr<INTERP>(A, M, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray_amr<INTERP, SH>(A, M, ix, iy);
 }
 
 }  // namespace
 
-cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s)
+cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, bool shear)
 {
     const TileCfg t;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const dim3 block(32 * t.bwx * t.bwy);
-    if (interp == RR_TRILINEAR) trace_amr_kernel<RR_TRILINEAR><<<grid, block, 0, s>>>(a, m, t);
-    else trace_amr_kernel<RR_NGP><<<grid, block, 0, s>>>(a, m, t);
+    if (shear) {
+        if (interp == RR_TRILINEAR) trace_amr_kernel<RR_TRILINEAR, true><<<grid, block, 0, s>>>(a, m, t);
+        else trace_amr_kernel<RR_NGP, true><<<grid, block, 0, s>>>(a, m, t);
+    } else {
+        if (interp == RR_TRILINEAR) trace_amr_kernel<RR_TRILINEAR, false><<<grid, block, 0, s>>>(a, m, t);
+        else trace_amr_kernel<RR_NGP, false><<<grid, block, 0, s>>>(a, m, t);
+    }
     return cudaGetLastError();
 }
 

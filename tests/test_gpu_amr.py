@@ -348,3 +348,55 @@ def test_footprint_records_give_the_same_maps(rrp, interp, shuffle, obs):
         assert np.array_equal(reference[0], maps[0][0].ravel()) and np.array_equal(reference[1], maps[0][1].ravel())
         assert reference[2] == maps[0][2]
     gm.close()
+
+
+# ---------------------------------------------------------------------------
+# the shear (RR_SHEAR) through the adaptive mesh
+# ---------------------------------------------------------------------------
+
+def _trace_gpu_shear(rrp, mesh, bundle, steps):
+    import torch
+    gm = _gpu_mesh(rrp, mesh)
+    where = rrp.RR_AT_VERTICES if bundle.interp == 1 else rrp.RR_AT_CENTRES
+    rec = gm.record_buffer(where)
+    gm.tidal(torch.from_numpy(_flat_phi(mesh)).cuda(), rec, where)
+    tr = rrp.Tracer(bundle, shear=True)
+    for st in steps:
+        tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a)
+    k, kb = tr.finalize()
+    g1, g2 = tr.shear()
+    out = [x.cpu().numpy().ravel() for x in (k, kb, g1, g2)]
+    tr.close()
+    gm.close()
+    return out
+
+
+@pytest.mark.parametrize("interp", [1, 0])
+def test_shear_random_mesh_vs_oracle(rrp, oracle_lib, interp):
+    """gamma1, gamma2 (Eqs. gamma1, gamma2) over three refinement levels and
+    two steps, with kappa and Born kappa of the same walk unchanged."""
+    mesh = _random_mesh()
+    b = synth.Bundle(23, 17, synth.deg(30), synth.deg(22), (3.1, 12.7, 0.4), 40.0, interp=interp)
+    steps = [synth.Step(40.0, 17.0, 1.1, 0.8), synth.Step(17.0, 0.0, 0.95, 1.0)]
+    k, kb, g1, g2 = _trace_gpu_shear(rrp, mesh, b, steps)
+    o = oracle_lib.amr_trace(b, mesh, steps)
+    w1, w2 = oracle_lib.amr_trace_shear(b, mesh, steps)
+    _assert_map(k, o.kappa)
+    _assert_map(kb, o.kborn, what="kborn")
+    _assert_map(g1, w1, what="gamma1")
+    _assert_map(g2, w2, what="gamma2")
+
+
+def test_shear_nested_gaussian_vs_oracle(rrp, oracle_lib):
+    """Sec. 4's mesh (two refined cubes towards the lens): the shear of the
+    axisymmetric lens is tangential, so gamma2 is only the mesh's anisotropy;
+    its errors are measured in units of rms(gamma1)."""
+    L = 32.0
+    mesh = _gauss_mesh(16, L)
+    b = synth.Bundle(31, 31, synth.deg(20), synth.deg(20), (L / 2, L / 2, 0.0), 60.0, periodic=False)
+    steps = [synth.Step(60.0, 0.0, 1.0, 1.0)]
+    _, _, g1, g2 = _trace_gpu_shear(rrp, mesh, b, steps)
+    w1, w2 = oracle_lib.amr_trace_shear(b, mesh, steps)
+    _assert_map(g1, w1, what="gamma1")
+    rms1 = math.sqrt(float(np.mean(w1 ** 2)))
+    assert np.abs(g2 - w2).max() <= TOL * rms1
