@@ -469,6 +469,30 @@ def run_amr(args, name):
             if it >= args.warmup:
                 e2e.append(time.perf_counter() - t0)
 
+        # the shear through the same mesh (RR_SHEAR in the AMR walk)
+        trs = rrp.Tracer(w.bundle, shear=True)
+        ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+
+        def shear_pass(timed):
+            rrp.rr_reset(trs.ctx, stream)
+            for i, st in enumerate(steps):
+                gm.tidal(phi, rec, rrp.RR_AT_VERTICES, None, bboxes[i], stream)
+                if timed:
+                    ev_s[i][0].record(stream)
+                trs.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+                if timed:
+                    ev_s[i][1].record(stream)
+            rrp.rr_finalize(trs.ctx, kappa, kborn, stream)
+
+        shear_pass(False)
+        sh_ms = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            shear_pass(True)
+            torch.cuda.synchronize()
+            sh_ms.append(sum(a.elapsed_time(b) for a, b in ev_s))
+        trs.close()
+
     peaks, peak_kind = _peaks()
     total_ms = sum(times)
     per_pass_trace_s = trace_ms / args.steps / 1e3
@@ -482,6 +506,11 @@ def run_amr(args, name):
         "segments_per_step": segs,
         "setup_s": {"mesh_and_potential": t_gen, "plan": t_plan},
         "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps},
+        "shear": {"trace_ms_per_pass": sum(sh_ms) / len(sh_ms),
+                  "kappa_only_trace_ms_per_pass": trace_ms / args.steps,
+                  "cost_vs_kappa_only": (sum(sh_ms) / len(sh_ms)) / (trace_ms / args.steps),
+                  "note": "trace kernels of one pass in the shear form (kappa, Born kappa, gamma1, gamma2 in "
+                          "one AMR walk), CUDA events per launch, L2 flushed before each pass, mean of 2"},
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "trace_amr_kernel<trilinear>",
