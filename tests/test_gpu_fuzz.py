@@ -45,7 +45,8 @@ def _case(seed):
     b = synth.Bundle(nx, ny, fov[0], fov[1], obs, chis, interp=interp, periodic=periodic)
     nst = int(rng.integers(1, 5))
     edges = np.sort(rng.uniform(0.0, chis, size=nst - 1))[::-1]
-    edges = [chis] + list(edges) + [float(rng.uniform(0, 0.2) * chis)]
+    edges = [chis] + list(edges)
+    edges.append(float(rng.uniform(0, 0.2) * edges[-1]))   # the last step ends short of the observer
     steps = [synth.Step(float(edges[i]), float(edges[i + 1]), float(rng.uniform(0.5, 1.5)),
                         float(rng.uniform(0.5, 1.0))) for i in range(nst)]
     phi = synth.random_field(n, 2000 + seed, np.float32)
