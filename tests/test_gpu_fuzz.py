@@ -103,7 +103,7 @@ def _oracle(oracle_lib, form, g, b, steps, phi, kern):
     return out
 
 
-@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("seed", range(40))
 def test_random_cases_all_forms(rrp, oracle_lib, seed):
     g, b, steps, phi = _case(seed)
     for form in FORMS:
