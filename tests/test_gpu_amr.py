@@ -400,3 +400,37 @@ def test_shear_nested_gaussian_vs_oracle(rrp, oracle_lib):
     _assert_map(g1, w1, what="gamma1")
     rms1 = math.sqrt(float(np.mean(w1 ** 2)))
     assert np.abs(g2 - w2).max() <= TOL * rms1
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_meshes_and_bundles(rrp, oracle_lib, seed):
+    """Seeded sweep: random refinement (1-3 levels), random bundles (ragged,
+    up to 50 deg, observers inside or outside the box, periodic or bounded),
+    uneven steps; kappa, Born kappa and the shear against the oracle."""
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.choice([6, 8]))
+    box = float(rng.uniform(8.0, 20.0))
+    mesh = synth.amr_random(n, box, int(rng.integers(1, 4)), 40 + seed, threshold=float(rng.uniform(1.0, 1.6)),
+                            child_sigma=0.8)
+    f = synth.fourier_fn(box, 30, 2 * math.pi / box * 4, 60 + seed)
+    mesh.phi = synth.amr_sample(mesh, f)
+    _round_phi(mesh)
+    periodic = bool(rng.integers(0, 2))
+    obs = tuple(float(x) for x in rng.uniform(-0.2, 1.2, size=3) * box)
+    if not periodic:
+        obs = (obs[0], obs[1], float(rng.uniform(-0.4, 0.1) * box))
+    chis = float(rng.uniform(0.8, 2.5) * box)
+    b = synth.Bundle(int(rng.integers(1, 24)), int(rng.integers(1, 24)), synth.deg(float(rng.uniform(2, 50))),
+                     synth.deg(float(rng.uniform(2, 50))), obs, chis, interp=int(rng.integers(0, 2)),
+                     periodic=periodic)
+    mid = float(rng.uniform(0.3, 0.7) * chis)
+    steps = [synth.Step(chis, mid, float(rng.uniform(0.6, 1.4)), 0.9),
+             synth.Step(mid, float(rng.uniform(0.0, 0.1) * chis), float(rng.uniform(0.6, 1.4)), 1.0)]
+    k, kb, g1, g2 = _trace_gpu_shear(rrp, mesh, b, steps)
+    o = oracle_lib.amr_trace(b, mesh, steps)
+    w1, w2 = oracle_lib.amr_trace_shear(b, mesh, steps)
+    for got, want, what in ((k, o.kappa, "kappa"), (kb, o.kborn, "kborn"), (g1, w1, "gamma1"), (g2, w2, "gamma2")):
+        if not np.any(want):
+            assert np.abs(got).max() == 0.0, what
+            continue
+        _assert_map(got, want, what=what)
