@@ -76,6 +76,8 @@ def _L():
         _lib.ora_amr_tidal.argtypes = [P, P]
         _lib.ora_amr_leaf_vertices.argtypes = [P, C.c_int, P, P]
         _lib.ora_amr_trace_step_shear.argtypes = [P, P, C.c_double, C.c_double, C.c_double, P, P, P, C.c_long]
+        _lib.ora_amr_trace_step_method_a.argtypes = [P, P, C.c_double, C.c_double, C.c_double, C.c_double, P, P, P,
+                                                     C.c_long]
         _lib.ora_amr_trace_step.argtypes = [P, P, C.c_double, C.c_double, C.c_double, C.c_double, P, P, P, P,
                                             C.c_long, C.c_int]
     return _lib
@@ -382,6 +384,24 @@ def amr_trace_shear(bundle, mesh, steps, rids=None):
         if rc != 0:
             raise ValueError(f"oracle: AMR trace failed ({rc})")
     return g1, g2
+
+
+def amr_trace_method_a(bundle, mesh, steps, rids=None):
+    """Method A (Eq. kappa2) through an adaptive mesh: (kgrad, kborn) per ray;
+    the Method A convergence is their sum."""
+    h = AmrHandle(mesh)
+    b = _amr_bundle(bundle)
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
+    kg = np.zeros(nr, np.float64)
+    kb = np.zeros(nr, np.float64)
+    for st in steps:
+        rc = _L().ora_amr_trace_step_method_a(C.byref(b), C.byref(h.desc), float(st.chi_a), float(st.chi_b),
+                                              float(st.scale), float(st.a), _ptr(kg), _ptr(kb), _ptr(ids),
+                                              0 if ids is None else len(ids))
+        if rc != 0:
+            raise ValueError(f"oracle: AMR trace failed ({rc})")
+    return kg, kb
 
 
 def amr_trace(bundle, mesh, steps, rids=None) -> TraceResult:

@@ -29,7 +29,12 @@
  *     own size h;
  *   - the shear (Eqs. gamma1, gamma2) by the same walk with the weights of
  *     rr_oracle.c's shear (printed Eqs. n1n1 - n2n2; Eq. n1n2 read in the
- *     orthonormal frame).
+ *     orthonormal frame);
+ *   - Method A (Eq. kappa2): d_a Phi per cell by central differences (the
+ *     coarse level's interpolated where the same-level stencil is incomplete,
+ *     as for the tidal tensor), vertex values by the same rules, the integral
+ *     of (1 - 2 chi/chi_s) n.grad(Phi) per leaf segment and the step's
+ *     surface terms at the ends of the traced interval (Eq. 2nterm).
  */
 #include <math.h>
 #include <stdint.h>
@@ -61,6 +66,7 @@ typedef struct {
     int64_t* keys[AMR_LMAX + 1];
     double* H[AMR_LMAX + 1];   /* 7 channels per cell of each level */
     int64_t ncell[AMR_LMAX + 1];
+    int grad;                  /* channels 0-2 hold d_a Phi instead of d_a d_a Phi (Method A) */
 } amr_t;
 
 /* ---------------------------------------------------------------- lookup */
@@ -172,6 +178,16 @@ static int tidal_fd(const amr_t* A, int l, int64_t i, int64_t j, int64_t k, doub
     out[3] = (v[6] + v[7] - v[8] - v[9]) * q;
     out[4] = (v[10] + v[11] - v[12] - v[13]) * q;
     out[5] = (v[14] + v[15] - v[16] - v[17]) * q;
+    if (A->grad) {
+        /* Method A: the central first differences, with delta from the
+         * Laplacian of the second differences (as for the tidal tensor) */
+        const double lap = out[0] + out[1] + out[2];
+        out[0] = 0.5 * (v[1] - v[0]) / h;
+        out[1] = 0.5 * (v[3] - v[2]) / h;
+        out[2] = 0.5 * (v[5] - v[4]) / h;
+        out[3] = out[4] = 0.0;
+        out[5] = lap;   /* moved to channel 6 by tidal_at */
+    }
     return 1;
 }
 
@@ -184,7 +200,11 @@ static int tidal_at(amr_t* A, int l, int64_t i, int64_t j, int64_t k, double out
         for (int c = 0; c < 7; ++c) out[c] = memo[c];
         return 0;
     }
-    if (!tidal_fd(A, l, i, j, k, out)) {
+    const double pref = 1.5 * A->d->omega_m * ORA_H0_OVER_C_A * ORA_H0_OVER_C_A;
+    double delta;   /* Method A: delta of the cell */
+    if (tidal_fd(A, l, i, j, k, out)) {
+        delta = out[5] / pref;   /* (grad mode: channel 5 holds the Laplacian) */
+    } else {
         /* coarse d_a d_b Phi interpolated to the fine centre (Sec. 3.3):
          * fine centre in coarse units = i/2 - 1/4 */
         int64_t c0[3];
@@ -194,6 +214,7 @@ static int tidal_at(amr_t* A, int l, int64_t i, int64_t j, int64_t k, double out
             if (ii[a] % 2 == 0) { c0[a] = ii[a] / 2 - 1; f[a] = 0.75; }
             else { c0[a] = (ii[a] - 1) / 2; f[a] = 0.25; }
         }
+        double lap = 0.0;
         for (int c = 0; c < 6; ++c) out[c] = 0.0;
         for (int t = 0; t < 8; ++t) {
             const int dx = t & 1, dy = (t >> 1) & 1, dz = (t >> 2) & 1;
@@ -201,10 +222,17 @@ static int tidal_at(amr_t* A, int l, int64_t i, int64_t j, int64_t k, double out
             if (tidal_at(A, l - 1, c0[0] + dx, c0[1] + dy, c0[2] + dz, hc) != 0) return -1;
             const double wgt = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
             for (int c = 0; c < 6; ++c) out[c] += wgt * hc[c];
+            lap += wgt * hc[6];
         }
+        delta = lap;   /* Method A: the coarse delta interpolated like the gradient */
     }
-    /* delta from the comoving Poisson equation at a = 1 */
-    out[6] = (out[0] + out[1] + out[2]) / (1.5 * A->d->omega_m * ORA_H0_OVER_C_A * ORA_H0_OVER_C_A);
+    if (A->grad) {
+        out[5] = 0.0;
+        out[6] = delta;
+    } else {
+        /* delta from the comoving Poisson equation at a = 1 */
+        out[6] = (out[0] + out[1] + out[2]) / pref;
+    }
     for (int c = 0; c < 7; ++c) memo[c] = out[c];
     memo[7] = 1.0;
     return 0;
@@ -440,8 +468,10 @@ static double ic_ngp_a(double Qc, double chiA, double chiB, double chis)
 }
 
 /* Eq. (Iclensing) with the alpha of Eq. (trilinear_coef) and the d_N of App. B */
-static double ic_tri_a(const double Q[8], double a, double b, double c, double h, double nx, double ny,
-                       double nz, double chiA, double chiB, double chis)
+/* the d_N of Eq. (Qcompact) (Appendix B) for the trilinear field of the
+ * corner values Q along the ray from A = P_1 + (a, b, c) */
+static void dn_a(const double Q[8], double a, double b, double c, double h, double nx, double ny, double nz,
+                 double d[4])
 {
     double al1 = Q[0], al2 = Q[1] - Q[0], al3 = Q[2] - Q[0], al4 = Q[4] - Q[0];
     double al5 = Q[3] - Q[2] - Q[1] + Q[0];
@@ -449,7 +479,6 @@ static double ic_tri_a(const double Q[8], double a, double b, double c, double h
     double al7 = Q[5] - Q[4] - Q[1] + Q[0];
     double al8 = Q[7] - Q[6] - Q[5] - Q[3] + Q[1] + Q[4] + Q[2] - Q[0];
     double h2 = h * h, h3 = h2 * h;
-    double d[4];
     d[0] = al1 + (al2 * a + al3 * b + al4 * c) / h + (al5 * a * b + al6 * b * c + al7 * a * c) / h2
            + al8 * a * b * c / h3;
     d[1] = (al2 * nx + al3 * ny + al4 * nz) / h
@@ -458,6 +487,13 @@ static double ic_tri_a(const double Q[8], double a, double b, double c, double h
     d[2] = (al5 * nx * ny + al7 * nx * nz + al6 * ny * nz) / h2
            + (al8 * a * ny * nz + al8 * b * nx * nz + al8 * c * nx * ny) / h3;
     d[3] = al8 / h3 * nx * ny * nz;
+}
+
+static double ic_tri_a(const double Q[8], double a, double b, double c, double h, double nx, double ny,
+                       double nz, double chiA, double chiB, double chis)
+{
+    double d[4];
+    dn_a(Q, a, b, c, h, nx, ny, nz, d);
     double R = chiB - chiA, sum = 0.0;
     for (int N = 1; N <= 4; ++N) {
         double RN = pow(R, N);
@@ -465,6 +501,18 @@ static double ic_tri_a(const double Q[8], double a, double b, double c, double h
                            + RN * R * R / (N + 2));
     }
     return sum / chis;
+}
+
+/* Method A (Eq. kappa2): Eq. (Icfinal) with K = dg/dchi = 1 - 2 chi/chi_s
+ * for the cubic d_N; R = chi_B - chi_A */
+static double ic_dg_tri_a(const double d[4], double chiA, double chiB, double chis)
+{
+    double R = chiB - chiA, sum = 0.0;
+    for (int N = 1; N <= 4; ++N) {
+        double RN = pow(R, N);
+        sum += d[N - 1] * (-(1.0 - 2.0 * chiA / chis) * RN / N + 2.0 / chis * RN * R / (N + 1));
+    }
+    return sum;
 }
 
 static double pixel_angle_a(double fov, long n, long i)
@@ -492,7 +540,7 @@ static void neu_add_a(neu_a* s, double x)
  */
 static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
                      double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids, long nrids,
-                     int shear);
+                     int mode);
 
 int ora_amr_trace_step(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
                        double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids,
@@ -508,13 +556,28 @@ int ora_amr_trace_step_shear(const ora_amr_bundle* b, const ora_amr_desc* d, dou
     return amr_trace(b, d, chi_a, chi_b, scale, 1.0, gamma1, gamma2, NULL, rids, nrids, 1);
 }
 
+/* Method A (Eq. kappa2) through the adaptive mesh: kgrad += scale * (the
+ * leaf-segment integrals of (1 - 2 chi/chi_s) n.grad(Phi) - [g n.grad(Phi)]
+ * at the start + [g n.grad(Phi)] at the end of the traced interval), kborn +=
+ * the density term; d_a Phi per cell by central differences where the
+ * same-level stencil is complete, else the coarse level's interpolated (the
+ * rule of Sec. 3.3 for the tidal tensor), vertex values by the Sec. 2.7 rules. */
+int ora_amr_trace_step_method_a(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b,
+                                double scale, double a_step, double* kgrad, double* kborn, const int64_t* rids,
+                                long nrids)
+{
+    return amr_trace(b, d, chi_a, chi_b, scale, a_step, kgrad, kborn, NULL, rids, nrids, 2);
+}
+
 static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
                      double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids, long nrids,
-                     int shear)
+                     int mode)
 {
+    const int shear = mode == 1, method_a = mode == 2;
     if (!(chi_a > chi_b) || chi_b < 0.0) return -1;
     amr_t A;
     if (amr_init(&A, d) != 0) return -10;
+    A.grad = method_a;
     const double bpref = 1.5 * d->omega_m * ORA_H0_OVER_C_A * ORA_H0_OVER_C_A / a_step;
     const double h0 = d->box / d->n;
     const double hf = h0 / (double)((int64_t)1 << d->lmax);
@@ -564,6 +627,8 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
         }
         neu_a sk = {0, 0}, sb = {0, 0};
         long count = 0;
+        /* Method A: n.grad(Phi) and chi at the start and the end of the interval */
+        double q_start = 0.0, chi_start = 0.0, q_end = 0.0, chi_end = 0.0;
         if (hi > lo) {
             /* every finest-lattice face crossing in (lo, hi) */
             long cap = 2;
@@ -623,7 +688,15 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
                             qk += w[q] * H[q];
                             q2 += w2[q] * H[q];
                         }
-                        ik = ic_ngp_a(qk, segA, segB, b->chi_s);
+                        if (method_a) {
+                            const double qg = n[0] * H[0] + n[1] * H[1] + n[2] * H[2];
+                            ik = qg * ((segA - segB) - (segA * segA - segB * segB) / b->chi_s);
+                            if (count == 0) { q_start = qg; chi_start = segA; }
+                            q_end = qg;
+                            chi_end = segB;
+                        } else {
+                            ik = ic_ngp_a(qk, segA, segB, b->chi_s);
+                        }
                         ib = ic_ngp_a(shear ? q2 : bpref * H[6], segA, segB, b->chi_s);
                     } else {
                         double Qk[8], Qb[8];
@@ -639,6 +712,7 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
                                 Qk[t] += w[q] * val[q];
                                 q2 += w2[q] * val[q];
                             }
+                            if (method_a) Qk[t] = n[0] * val[0] + n[1] * val[1] + n[2] * val[2];
                             Qb[t] = shear ? q2 : bpref * val[6];
                         }
                         if (err) break;
@@ -646,7 +720,17 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
                         double aa = b->obs[0] + segA * n[0] - P1[0];
                         double bb = b->obs[1] + segA * n[1] - P1[1];
                         double cc = b->obs[2] + segA * n[2] - P1[2];
-                        ik = ic_tri_a(Qk, aa, bb, cc, hl, n[0], n[1], n[2], segA, segB, b->chi_s);
+                        if (method_a) {
+                            double dq[4];
+                            dn_a(Qk, aa, bb, cc, hl, n[0], n[1], n[2], dq);
+                            ik = ic_dg_tri_a(dq, segA, segB, b->chi_s);
+                            if (count == 0) { q_start = dq[0]; chi_start = segA; }
+                            const double R = segB - segA;
+                            q_end = dq[0] + R * (dq[1] + R * (dq[2] + R * dq[3]));
+                            chi_end = segB;
+                        } else {
+                            ik = ic_tri_a(Qk, aa, bb, cc, hl, n[0], n[1], n[2], segA, segB, b->chi_s);
+                        }
                         ib = ic_tri_a(Qb, aa, bb, cc, hl, n[0], n[1], n[2], segA, segB, b->chi_s);
                     }
                     neu_add_a(&sk, ik);
@@ -663,6 +747,11 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
                 }
             }
             free(Lst);
+        }
+        if (method_a && count > 0) {
+            /* the step's surface terms (Eq. 2nterm) */
+            neu_add_a(&sk, -(b->chi_s - chi_start) * chi_start / b->chi_s * q_start);
+            neu_add_a(&sk, (b->chi_s - chi_end) * chi_end / b->chi_s * q_end);
         }
         kappa[slot] += scale * (sk.sum + sk.comp);
         kborn[slot] += scale * (sb.sum + sb.comp);
