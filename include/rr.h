@@ -75,7 +75,8 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
                                of the traced interval (Eq. 2nterm); rr_finalize
                                writes kappa = the sum of the three terms and
                                kappa_born = the density term. FP32 walk with
-                               compensated sums; rr_create / rr_trace_step only;
+                               compensated sums; rr_create / rr_trace_step /
+                               rr_amr_trace_step (records of rr_amr_gradient);
                                no adjoint; not with the other optional flags */
        RR_GENERIC = 64 };   /* generic integrals (Eqs. Ic, Icngp, Icfinal): rr_trace_step
                                reads scalar-pair records (rr_scalar_records) and
@@ -489,15 +490,29 @@ rr_status rr_amr_tidal(rr_amr* mesh, const float* phi, int32_t where, float* lea
                        const int32_t* bbox, void* stream);
 
 /*
+ * The records of Method A (Eq. kappa2) over the adaptive mesh, in the layout
+ * and with the arguments of rr_amr_tidal: per cell of every level d_a Phi by
+ * central differences where the same-level stencil of rr_amr_tidal is
+ * complete, else the coarser level's gradient interpolated trilinearly to the
+ * cell centre (the Sec. 3.3 rule), and delta as rr_amr_tidal derives it; the
+ * 8 channels hold {d_x Phi, d_y Phi, d_z Phi, 0}, {0, 0, delta, 0}, and the
+ * vertex values and leaf records follow from them as for the tidal records.
+ * These are the records rr_amr_trace_step reads for an RR_METHOD_A context.
+ */
+rr_status rr_amr_gradient(rr_amr* mesh, const float* phi, int32_t where, float* leaf_rec, float* cell_grad,
+                          const int32_t* bbox, void* stream);
+
+/*
  * rr_trace_step over an adaptive mesh: each ray advances leaf by leaf (the
  * crossings of the finest lattice grouped per leaf, Sec. 2.5.1) and adds the
  * integrals of rr_trace_step with each leaf's own cell size. `leaf_rec` from
  * rr_amr_tidal with RR_AT_VERTICES for RR_TRILINEAR bundles, RR_AT_CENTRES for
  * RR_NGP. Segment counts count leaf segments. An RR_SHEAR context also
- * accumulates the shear (rr_shear). RR_ERR_ARG for RR_FP64_DDA bundles (the
- * AMR walk is the FP32 float-float form only) and for the other optional
- * forms (RR_PLAIN_SUMS, RR_SOURCE_MOMENTS, RR_METHOD_A, RR_GENERIC); other
- * checks and the step log as rr_trace_step. Steps traced this way have no adjoint:
+ * accumulates the shear (rr_shear); an RR_METHOD_A context reads the records
+ * of rr_amr_gradient and follows Method A as rr_trace_step does. RR_ERR_ARG
+ * for RR_FP64_DDA bundles (the AMR walk is the FP32 float-float form only) and
+ * for RR_PLAIN_SUMS, RR_SOURCE_MOMENTS and RR_GENERIC; other checks and the
+ * step log as rr_trace_step. Steps traced this way have no adjoint:
  * rr_trace_step_adjoint and rr_trace_backward return RR_ERR_STATE for them.
  */
 rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* mesh, const float* leaf_rec, double chi_a, double chi_b,

@@ -244,6 +244,12 @@ class AmrMesh:
         rr_amr_tidal(self.handle, phi, where, leaf_rec, cell_tidal, bbox, stream)
         return leaf_rec
 
+    def gradient(self, phi, leaf_rec, where=RR_AT_VERTICES, cell_grad=None, bbox=None, stream=None):
+        """rr_amr_gradient: the Method A records ({grad Phi, 0}, {0, 0, delta,
+        0} in the layout of the tidal records) of the leaves in ``bbox`` or of all."""
+        _rr.rr_amr_gradient(self.handle, phi, where, leaf_rec, cell_grad, bbox, stream)
+        return leaf_rec
+
     def coarse_grid(self):
         """rr_grid_desc of the coarse grid (for rr_footprint_bbox)."""
         d = _rr.rr_grid_desc()

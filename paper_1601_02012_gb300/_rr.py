@@ -112,6 +112,7 @@ def load() -> C.CDLL:
             "rr_amr_destroy": ([P], C.c_int),
             "rr_amr_sizes": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
             "rr_amr_tidal": ([P, P, I32, P, P, P, P], C.c_int),
+            "rr_amr_gradient": ([P, P, I32, P, P, P, P], C.c_int),
             "rr_amr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -434,6 +435,15 @@ def rr_amr_tidal(mesh, phi, where: int, leaf_rec, cell_tidal=None, bbox=None, st
         bb = C.cast(arr, C.c_void_p)
     _check(load().rr_amr_tidal(mesh, _ptr(phi), int(where), _ptr(leaf_rec), _ptr(cell_tidal), bb,
                                _stream(stream)), "rr_amr_tidal")
+
+
+def rr_amr_gradient(mesh, phi, where: int, leaf_rec, cell_grad=None, bbox=None, stream=None) -> None:
+    bb = None
+    if bbox is not None:
+        arr = (C.c_int32 * 6)(*[int(x) for x in bbox])
+        bb = C.cast(arr, C.c_void_p)
+    _check(load().rr_amr_gradient(mesh, _ptr(phi), int(where), _ptr(leaf_rec), _ptr(cell_grad), bb,
+                                  _stream(stream)), "rr_amr_gradient")
 
 
 def rr_amr_trace_step(ctx, mesh, leaf_rec, chi_a: float, chi_b: float, scale: float = 1.0, a_step: float = 1.0,

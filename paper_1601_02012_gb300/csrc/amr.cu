@@ -172,8 +172,10 @@ struct TidalAmrArgs {
     float* H;
     Ranges cells;
     float ih2, iq, dinv;
+    float ih2h;   // 1/(2h): gradient mode
     AmrBox box;
     int margin;
+    int grad;     // Method A: {d_x Phi, d_y Phi, d_z Phi, 0}, {0, 0, delta, 0} in the same 8 channels
 };
 
 __global__ void __launch_bounds__(NTA) amr_tidal_kernel(const TidalAmrArgs a)
@@ -198,6 +200,29 @@ __global__ void __launch_bounds__(NTA) amr_tidal_kernel(const TidalAmrArgs a)
         h[3] = ((v[6] - v[8]) + (v[7] - v[9])) * a.iq;
         h[4] = ((v[10] - v[12]) + (v[11] - v[13])) * a.iq;
         h[5] = ((v[14] - v[16]) + (v[15] - v[17])) * a.iq;
+        if (a.grad) {
+            // central first differences (x-, x+, y-, y+, z-, z+ are stencil entries 0-5)
+            float4* out = reinterpret_cast<float4*>(a.H) + 2 * (int64_t)c;
+            out[0] = make_float4((v[1] - v[0]) * a.ih2h, (v[3] - v[2]) * a.ih2h, (v[5] - v[4]) * a.ih2h, 0.f);
+            out[1] = make_float4(0.f, 0.f, (h[0] + h[1] + h[2]) * a.dinv, 0.f);
+            return;
+        }
+    } else if (a.grad) {
+        // the coarser level's gradient and delta interpolated (Sec. 3.3's rule)
+        const float fx = a.frac[3 * (int64_t)c], fy = a.frac[3 * (int64_t)c + 1], fz = a.frac[3 * (int64_t)c + 2];
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float w = ((k & 1) ? fx : 1.f - fx) * ((k & 2) ? fy : 1.f - fy) * ((k & 4) ? fz : 1.f - fz);
+            const float4 lo = reinterpret_cast<const float4*>(a.H)[2 * (int64_t)s[k]];
+            const float4 hi = reinterpret_cast<const float4*>(a.H)[2 * (int64_t)s[k] + 1];
+            g[0] = fmaf(w, lo.x, g[0]); g[1] = fmaf(w, lo.y, g[1]);
+            g[2] = fmaf(w, lo.z, g[2]); g[3] = fmaf(w, hi.z, g[3]);
+        }
+        float4* out = reinterpret_cast<float4*>(a.H) + 2 * (int64_t)c;
+        out[0] = make_float4(g[0], g[1], g[2], 0.f);
+        out[1] = make_float4(0.f, 0.f, g[3], 0.f);
+        return;
     } else {
         // the coarser level was written by an earlier launch: plain loads
         const float fx = a.frac[3 * (int64_t)c], fy = a.frac[3 * (int64_t)c + 1], fz = a.frac[3 * (int64_t)c + 2];
@@ -746,8 +771,8 @@ rr_status rr_amr_sizes(rr_amr* A, int64_t* ncells, int64_t* nleaves, int64_t* nv
     return RR_OK;
 }
 
-rr_status rr_amr_tidal(rr_amr* A, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
-                       const int32_t* bbox, void* stream)
+static rr_status amr_records(rr_amr* A, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
+                              const int32_t* bbox, void* stream, int grad)
 {
     if (!A || !phi || !leaf_rec || ((uintptr_t)leaf_rec & 15u)) return RR_ERR_ARG;
     if (cell_tidal && ((uintptr_t)cell_tidal & 15u)) return RR_ERR_ARG;
@@ -802,6 +827,8 @@ rr_status rr_amr_tidal(rr_amr* A, const float* phi, int32_t where, float* leaf_r
         a.ih2 = (float)(1.0 / (hl * hl));
         a.iq = (float)(0.25 / (hl * hl));
         a.dinv = (float)(1.0 / (1.5 * h.omega_m * kH0OverC * kH0OverC));
+        a.ih2h = (float)(0.5 / hl);
+        a.grad = grad;
         a.box = box;
         // vertices read leaves up to 3 coarse cells outside the box; an
         // interpolated cell reads the coarser level one coarse cell further out
@@ -829,12 +856,23 @@ rr_status rr_amr_tidal(rr_amr* A, const float* phi, int32_t where, float* leaf_r
     return status_of_cuda(cudaGetLastError());
 }
 
+rr_status rr_amr_tidal(rr_amr* A, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
+                       const int32_t* bbox, void* stream)
+{
+    return amr_records(A, phi, where, leaf_rec, cell_tidal, bbox, stream, 0);
+}
+
+rr_status rr_amr_gradient(rr_amr* A, const float* phi, int32_t where, float* leaf_rec, float* cell_grad,
+                          const int32_t* bbox, void* stream)
+{
+    return amr_records(A, phi, where, leaf_rec, cell_grad, bbox, stream, 1);
+}
+
 rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, double chi_a, double chi_b,
                             double scale, double a_step, void* stream)
 {
     if (!ctx || !A) return RR_ERR_ARG;
-    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_METHOD_A | RR_GENERIC))
-        return RR_ERR_ARG;
+    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_GENERIC)) return RR_ERR_ARG;
     rr_grid_desc g;   // the coarse grid: argument and step-order checks
     g.n[0] = g.n[1] = g.n[2] = A->h.n;
     g.box = A->h.box;
@@ -852,7 +890,9 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, doubl
     m.n = A->h.n;
     m.lmax = A->h.lmax;
     const cudaError_t e =
-        launch_trace_amr(a, m, ctx->bundle.interp, (cudaStream_t)stream, (ctx->bundle.flags & RR_SHEAR) != 0);
+        launch_trace_amr(a, m, ctx->bundle.interp, (cudaStream_t)stream,
+                         (ctx->bundle.flags & RR_SHEAR) ? kFormShear
+                                                        : ((ctx->bundle.flags & RR_METHOD_A) ? kFormMethodA : kFormKahan));
     if (e != cudaSuccess) return status_of_cuda(e);
     StepRecord r = make_step_record(ctx, &g, chi_a, chi_b, scale, a_step);
     r.amr = 1;

@@ -124,8 +124,8 @@ cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, in
 int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
 dim3 tile_grid(const TileCfg& t, int nx, int ny);
 bool tile_ok(const TileCfg& t);
-// shear: also the shear (gamma1, gamma2) into g1acc, g2acc
-cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, bool shear = false);
+// form: kFormKahan, kFormShear (also gamma1, gamma2 into g1acc, g2acc) or kFormMethodA
+cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, int form = 0);
 cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s);
 cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
                                  cudaStream_t s);

@@ -16,9 +16,12 @@
 // value; the segment integral is that of the uniform walk with the leaf's own
 // cell size. Consecutive segments in the same leaf (separated only by a
 // rounding sliver at an edge or corner) are one leaf segment, so the segment
-// count is the number of leaf segments. SH: also the shear (gamma1, gamma2) of
-// Eqs. gamma1, gamma2, a second projection of the same corner records carried
-// through the same segment integrals.
+// count is the number of leaf segments. FORM kFormShear: also the shear
+// (gamma1, gamma2) of Eqs. gamma1, gamma2, a second projection of the same
+// corner records carried through the same segment integrals. kFormMethodA:
+// Method A (Eq. kappa2) on gradient records (rr_amr_gradient): n . grad Phi
+// with the kernel dg/dchi, the density term with g, and the step's surface
+// terms at the two ends of the traced interval (Eq. 2nterm).
 #include "walk.cuh"
 
 namespace rr {
@@ -40,9 +43,11 @@ __device__ __forceinline__ int amr_locate(const AmrDevice& M, const int q[3], in
     return v < 0 ? -1 : v;
 }
 
-template <int INTERP, bool SH>
+template <int INTERP, int FORM>
 __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevice& M, int ix, int iy)
 {
+    constexpr bool SH = FORM == kFormShear;
+    constexpr bool MA = FORM == kFormMethodA;
     const long long rid = (long long)iy * A.nx + ix;
     const int NF = A.n0;   // finest cells per side
     RayRange rg;
@@ -59,6 +64,9 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     Acc2 sg;   // (gamma1, gamma2), shear only
     float w1[6], w2[6];
     if constexpr (SH) shear_weights(A.dirh[rid], w1, w2);
+    float4 nd;   // Method A: the direction
+    if constexpr (MA) nd = A.dirh[rid];
+    float qa = 0.f, ga = 0.f, qb = 0.f, gb = 0.f;   // Method A: n . grad Phi and g at the two ends
     uint32_t cnt = 0;
     bool overflow = false;
     int prev_leaf = -1;   // leaf of the last integrated segment
@@ -103,8 +111,24 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
             const bool last = !(tend < Ls - eps_end);
             if (last) tend = Ls;
             const float t = tend - sig;
+            const bool integrate = t > tend * eps_rel;
+            // Method A: the first piece of the interval and the one that ends it
+            // (the last, or the one leaving a bounded box) give the surface terms
+            bool first = false, ends = false;
+            if constexpr (MA) {
+                first = j == 0 && iter == 0;
+                ends = last;
+                if (!A.periodic && !last) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        if (a == e) {
+                            const int nq = q[a] + W.sgn[a] * m[a];
+                            ends = nq < 0 || nq >= NF;
+                        }
+                }
+            }
 
-            if (t > tend * eps_rel) {
+            if (integrate || first || ends) {
                 float2 q2[8];   // (Q_kappa, delta) at the mirrored corners, or the leaf's own value
                 float2 g2[SH ? 8 : 1];   // (Q_gamma1, Q_gamma2) there
                 if (INTERP == RR_TRILINEAR) {
@@ -115,12 +139,13 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                         Rec x;
                         x.a = __ldg(r + 2 * rc);
                         x.b = __ldg(r + 2 * rc + 1);
-                        q2[c] = make_float2(project(W.w, x), x.b.z);
+                        q2[c] = MA ? radial_pair(nd, x.a) : make_float2(project(W.w, x), x.b.z);
+                        if constexpr (MA) q2[c].y = x.b.z;
                         if constexpr (SH) g2[c] = make_float2(project(w1, x), project(w2, x));
                     }
                 } else {
                     const Rec x = load_rec(A.rec, leaf);
-                    q2[0] = make_float2(project(W.w, x), x.b.z);
+                    q2[0] = MA ? make_float2(radial_pair(nd, x.a).x, x.b.z) : make_float2(project(W.w, x), x.b.z);
                     if constexpr (SH) g2[0] = make_float2(project(w1, x), project(w2, x));
                 }
                 float G0, G1, G2;
@@ -133,15 +158,48 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                         u[a] = W.v[a] > 0.f ? fminf(fmaxf(fmaf(sig - Tx[a], vl[a], 1.f), 0.f), 1.f)
                                             : (i2f_exact(jp[a]) + W.cu[a]) * inv_span;
                     }
-                    s2.add(segment_trilinear(q2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
-                    if constexpr (SH)
-                        sg.add(segment_trilinear(g2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
+                    if (integrate) {
+                        if constexpr (MA)
+                            s2.add(segment_trilinear_a(q2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
+                        else
+                            s2.add(segment_trilinear(q2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
+                        if constexpr (SH)
+                            sg.add(segment_trilinear(g2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
+                    }
+                    if constexpr (MA) {
+                        if (first) {
+                            qa = trilinear_x(q2, u[0], u[1], u[2]);
+                            ga = D0 * chiA0 * ichis;
+                        }
+                        if (ends) {
+                            float ue[3];
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) ue[a] = fminf(fmaxf(fmaf(t, vl[a], u[a]), 0.f), 1.f);
+                            qb = trilinear_x(q2, ue[0], ue[1], ue[2]);
+                            gb = fmaf(t, fmaf(t, G2, G1), G0);
+                        }
+                    }
                 } else {
-                    s2.add(segment_ngp(q2[0], t, G0, G1, G2));
-                    if constexpr (SH) sg.add(segment_ngp(g2[0], t, G0, G1, G2));
+                    if (integrate) {
+                        if constexpr (MA) s2.add(segment_ngp_a(q2[0], t, G0, G1, G2));
+                        else s2.add(segment_ngp(q2[0], t, G0, G1, G2));
+                        if constexpr (SH) sg.add(segment_ngp(g2[0], t, G0, G1, G2));
+                    }
+                    if constexpr (MA) {
+                        if (first) {
+                            qa = q2[0].x;
+                            ga = D0 * chiA0 * ichis;
+                        }
+                        if (ends) {
+                            qb = q2[0].x;
+                            gb = fmaf(t, fmaf(t, G2, G1), G0);
+                        }
+                    }
                 }
-                if (leaf != prev_leaf) ++cnt;
-                prev_leaf = leaf;
+                if (integrate) {
+                    if (leaf != prev_leaf) ++cnt;
+                    prev_leaf = leaf;
+                }
             }
             sig = tend;
             if (last) break;
@@ -174,6 +232,10 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
         }
     }
 
+    if constexpr (MA) {
+        s2.add(make_float2(-ga * qa, 0.f));
+        s2.add(make_float2(gb * qb, 0.f));
+    }
     if (overflow) atomicOr(A.err, kErrStepLimit);
     if (!s2.finite()) atomicOr(A.err, kErrNonFinite);
     float kh, kl, bh, bl;
@@ -192,27 +254,31 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     }
 }
 
-template <int INTERP, bool SH>
+template <int INTERP, int FORM>
 __global__ void __launch_bounds__(NT_MAX, 2) trace_amr_kernel(const TraceArgs A, const AmrDevice M, const TileCfg t)
 {
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
-    if (ix < A.nx && iy < A.ny) trace_ray_amr<INTERP, SH>(A, M, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray_amr<INTERP, FORM>(A, M, ix, iy);
 }
 
 }  // namespace
 
-cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, bool shear)
+cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, int form)
 {
     const TileCfg t;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const dim3 block(32 * t.bwx * t.bwy);
-    if (shear) {
-        if (interp == RR_TRILINEAR) trace_amr_kernel<RR_TRILINEAR, true><<<grid, block, 0, s>>>(a, m, t);
-        else trace_amr_kernel<RR_NGP, true><<<grid, block, 0, s>>>(a, m, t);
+    const bool tri = interp == RR_TRILINEAR;
+    if (form == kFormShear) {
+        if (tri) trace_amr_kernel<RR_TRILINEAR, kFormShear><<<grid, block, 0, s>>>(a, m, t);
+        else trace_amr_kernel<RR_NGP, kFormShear><<<grid, block, 0, s>>>(a, m, t);
+    } else if (form == kFormMethodA) {
+        if (tri) trace_amr_kernel<RR_TRILINEAR, kFormMethodA><<<grid, block, 0, s>>>(a, m, t);
+        else trace_amr_kernel<RR_NGP, kFormMethodA><<<grid, block, 0, s>>>(a, m, t);
     } else {
-        if (interp == RR_TRILINEAR) trace_amr_kernel<RR_TRILINEAR, false><<<grid, block, 0, s>>>(a, m, t);
-        else trace_amr_kernel<RR_NGP, false><<<grid, block, 0, s>>>(a, m, t);
+        if (tri) trace_amr_kernel<RR_TRILINEAR, kFormKahan><<<grid, block, 0, s>>>(a, m, t);
+        else trace_amr_kernel<RR_NGP, kFormKahan><<<grid, block, 0, s>>>(a, m, t);
     }
     return cudaGetLastError();
 }

@@ -402,11 +402,56 @@ def test_shear_nested_gaussian_vs_oracle(rrp, oracle_lib):
     assert np.abs(g2 - w2).max() <= TOL * rms1
 
 
+def _trace_gpu_method_a(rrp, mesh, bundle, steps):
+    import torch
+    gm = _gpu_mesh(rrp, mesh)
+    where = rrp.RR_AT_VERTICES if bundle.interp == 1 else rrp.RR_AT_CENTRES
+    rec = gm.record_buffer(where)
+    gm.gradient(torch.from_numpy(_flat_phi(mesh)).cuda(), rec, where)
+    tr = rrp.Tracer(bundle, method_a=True)
+    for st in steps:
+        tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a)
+    k, kb = tr.finalize()
+    out = [x.cpu().numpy().ravel() for x in (k, kb)]
+    tr.close()
+    gm.close()
+    return out
+
+
+@pytest.mark.parametrize("interp", [1, 0])
+def test_method_a_random_mesh_vs_oracle(rrp, oracle_lib, interp):
+    """Method A (Eq. kappa2) over three refinement levels and two steps with
+    different scales (the surface terms do not telescope): kappa (all three
+    terms) and the density term."""
+    mesh = _random_mesh()
+    b = synth.Bundle(23, 17, synth.deg(30), synth.deg(22), (3.1, 12.7, 0.4), 40.0, interp=interp)
+    steps = [synth.Step(40.0, 17.0, 1.1, 0.8), synth.Step(17.0, 0.0, 0.95, 1.0)]
+    k, kb = _trace_gpu_method_a(rrp, mesh, b, steps)
+    kg, kbo = oracle_lib.amr_trace_method_a(b, mesh, steps)
+    _assert_map(k, kg + kbo)
+    _assert_map(kb, kbo, what="kborn")
+
+
+@pytest.mark.parametrize("interp", [1, 0])
+def test_method_a_nested_gaussian_vs_oracle(rrp, oracle_lib, interp):
+    """Sec. 4's mesh, bounded box, the observer on its face: the rays enter
+    and leave the box, so the surface terms sit on the box faces."""
+    L = 32.0
+    mesh = _gauss_mesh(16, L)
+    b = synth.Bundle(31, 9, synth.deg(20), synth.deg(6), (L / 2, L / 2, 0.0), 60.0, interp=interp,
+                     periodic=False)
+    steps = [synth.Step(60.0, 20.0, 0.9, 1.0), synth.Step(20.0, 0.0, 1.0, 1.0)]
+    k, kb = _trace_gpu_method_a(rrp, mesh, b, steps)
+    kg, kbo = oracle_lib.amr_trace_method_a(b, mesh, steps)
+    _assert_map(k, kg + kbo)
+    _assert_map(kb, kbo, what="kborn")
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_meshes_and_bundles(rrp, oracle_lib, seed):
     """Seeded sweep: random refinement (1-3 levels), random bundles (ragged,
     up to 50 deg, observers inside or outside the box, periodic or bounded),
-    uneven steps; kappa, Born kappa and the shear against the oracle."""
+    uneven steps; kappa, Born kappa, the shear and Method A against the oracle."""
     rng = np.random.default_rng(500 + seed)
     n = int(rng.choice([6, 8]))
     box = float(rng.uniform(8.0, 20.0))
@@ -429,7 +474,10 @@ def test_random_meshes_and_bundles(rrp, oracle_lib, seed):
     k, kb, g1, g2 = _trace_gpu_shear(rrp, mesh, b, steps)
     o = oracle_lib.amr_trace(b, mesh, steps)
     w1, w2 = oracle_lib.amr_trace_shear(b, mesh, steps)
-    for got, want, what in ((k, o.kappa, "kappa"), (kb, o.kborn, "kborn"), (g1, w1, "gamma1"), (g2, w2, "gamma2")):
+    ka, kba = _trace_gpu_method_a(rrp, mesh, b, steps)
+    wg, wb = oracle_lib.amr_trace_method_a(b, mesh, steps)
+    for got, want, what in ((k, o.kappa, "kappa"), (kb, o.kborn, "kborn"), (g1, w1, "gamma1"), (g2, w2, "gamma2"),
+                            (ka, wg + wb, "kappa A"), (kba, wb, "kborn A")):
         if not np.any(want):
             assert np.abs(got).max() == 0.0, what
             continue
