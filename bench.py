@@ -493,6 +493,30 @@ def run_amr(args, name):
             sh_ms.append(sum(a.elapsed_time(b) for a, b in ev_s))
         trs.close()
 
+        # Method A through the same mesh (rr_amr_gradient records, RR_METHOD_A walk)
+        tra = rrp.Tracer(w.bundle, method_a=True)
+        ev_a = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+
+        def method_a_pass(timed):
+            rrp.rr_reset(tra.ctx, stream)
+            for i, st in enumerate(steps):
+                if timed:
+                    ev_a[i][0].record(stream)
+                gm.gradient(phi, rec, rrp.RR_AT_VERTICES, None, bboxes[i], stream)
+                tra.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, 1.0, stream)
+                if timed:
+                    ev_a[i][1].record(stream)
+            rrp.rr_finalize(tra.ctx, kappa, kborn, stream)
+
+        method_a_pass(False)
+        ma_ms = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            method_a_pass(True)
+            torch.cuda.synchronize()
+            ma_ms.append(sum(a.elapsed_time(b) for a, b in ev_a))
+        tra.close()
+
     peaks, peak_kind = _peaks()
     total_ms = sum(times)
     per_pass_trace_s = trace_ms / args.steps / 1e3
@@ -511,6 +535,9 @@ def run_amr(args, name):
                   "cost_vs_kappa_only": (sum(sh_ms) / len(sh_ms)) / (trace_ms / args.steps),
                   "note": "trace kernels of one pass in the shear form (kappa, Born kappa, gamma1, gamma2 in "
                           "one AMR walk), CUDA events per launch, L2 flushed before each pass, mean of 2"},
+        "method_a": {"ms_per_pass": sum(ma_ms) / len(ma_ms), "method_b_ms_per_pass": total_ms / args.steps,
+                     "note": "records (rr_amr_gradient over each step's footprint) and the Method A AMR walk "
+                             "of one pass, CUDA events per step, L2 flushed before each pass, mean of 2"},
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "trace_amr_kernel<trilinear>",
