@@ -76,6 +76,7 @@ def _L():
         _lib.ora_amr_tidal.argtypes = [P, P]
         _lib.ora_amr_leaf_vertices.argtypes = [P, C.c_int, P, P]
         _lib.ora_amr_trace_step_shear.argtypes = [P, P, C.c_double, C.c_double, C.c_double, P, P, P, C.c_long]
+        _lib.ora_amr_trace_step_kq.argtypes = [P, P, C.c_double, C.c_double, C.c_double, P, P, P, C.c_long]
         _lib.ora_amr_trace_step_method_a.argtypes = [P, P, C.c_double, C.c_double, C.c_double, C.c_double, P, P, P,
                                                      C.c_long]
         _lib.ora_amr_trace_step.argtypes = [P, P, C.c_double, C.c_double, C.c_double, C.c_double, P, P, P, P,
@@ -384,6 +385,30 @@ def amr_trace_shear(bundle, mesh, steps, rids=None):
         if rc != 0:
             raise ValueError(f"oracle: AMR trace failed ({rc})")
     return g1, g2
+
+
+def amr_trace_kq(bundle, mesh, Q1, Q2, kernels, steps, rids=None):
+    """Two generic integrals int K_c(chi) Q_c dchi through an adaptive mesh;
+    Q_c per level as mesh.phi is (level 0: n^3, level l: octs x 8), Q2 may be
+    None; each step's field is st.scale * Q_c. Returns (I1, I2)."""
+    b = _amr_bundle(bundle)
+    ids = None if rids is None else np.ascontiguousarray(rids, dtype=np.int64)
+    nr = int(bundle.nx) * int(bundle.ny) if ids is None else len(ids)
+    ker = np.asarray(kernels, np.float64).reshape(2, 3)
+    outs = []
+    for Q, k in ((Q1, ker[0]), (Q2, ker[1])):
+        o = np.zeros(nr, np.float64)
+        if Q is not None:
+            h = AmrHandle(mesh, Q)
+            kk = np.ascontiguousarray(k)
+            for st in steps:
+                rc = _L().ora_amr_trace_step_kq(C.byref(b), C.byref(h.desc), float(st.chi_a), float(st.chi_b),
+                                                float(st.scale), _ptr(kk), _ptr(o), _ptr(ids),
+                                                0 if ids is None else len(ids))
+                if rc != 0:
+                    raise ValueError(f"oracle: AMR trace failed ({rc})")
+        outs.append(o)
+    return outs[0], outs[1]
 
 
 def amr_trace_method_a(bundle, mesh, steps, rids=None):

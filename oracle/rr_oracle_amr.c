@@ -34,7 +34,9 @@
  *     coarse level's interpolated where the same-level stencil is incomplete,
  *     as for the tidal tensor), vertex values by the same rules, the integral
  *     of (1 - 2 chi/chi_s) n.grad(Phi) per leaf segment and the step's
- *     surface terms at the ends of the traced interval (Eq. 2nterm).
+ *     surface terms at the ends of the traced interval (Eq. 2nterm);
+ *   - generic integrals int K(chi) Q dchi of a scalar field with a quadratic
+ *     kernel (Eqs. Ic, Icngp, Icfinal), its vertex values by the same rules.
  */
 #include <math.h>
 #include <stdint.h>
@@ -67,6 +69,7 @@ typedef struct {
     double* H[AMR_LMAX + 1];   /* 7 channels per cell of each level */
     int64_t ncell[AMR_LMAX + 1];
     int grad;                  /* channels 0-2 hold d_a Phi instead of d_a d_a Phi (Method A) */
+    int scalar;                /* channel 0 holds the cell value itself (generic integrals) */
 } amr_t;
 
 /* ---------------------------------------------------------------- lookup */
@@ -198,6 +201,14 @@ static int tidal_at(amr_t* A, int l, int64_t i, int64_t j, int64_t k, double out
     double* memo = A->H[l] + 8 * idx;
     if (memo[7] == 1.0) {
         for (int c = 0; c < 7; ++c) out[c] = memo[c];
+        return 0;
+    }
+    if (A->scalar) {
+        /* generic integrals: the field's own cell value */
+        for (int c = 0; c < 7; ++c) out[c] = 0.0;
+        out[0] = phi_at(A, l, idx);
+        for (int c = 0; c < 7; ++c) memo[c] = out[c];
+        memo[7] = 1.0;
         return 0;
     }
     const double pref = 1.5 * A->d->omega_m * ORA_H0_OVER_C_A * ORA_H0_OVER_C_A;
@@ -540,20 +551,20 @@ static void neu_add_a(neu_a* s, double x)
  */
 static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
                      double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids, long nrids,
-                     int mode);
+                     int mode, const double* kq);
 
 int ora_amr_trace_step(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
                        double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids,
                        long nrids, int nthreads)
 {
     (void)nthreads;
-    return amr_trace(b, d, chi_a, chi_b, scale, a_step, kappa, kborn, nseg, rids, nrids, 0);
+    return amr_trace(b, d, chi_a, chi_b, scale, a_step, kappa, kborn, nseg, rids, nrids, 0, NULL);
 }
 
 int ora_amr_trace_step_shear(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b,
                              double scale, double* gamma1, double* gamma2, const int64_t* rids, long nrids)
 {
-    return amr_trace(b, d, chi_a, chi_b, scale, 1.0, gamma1, gamma2, NULL, rids, nrids, 1);
+    return amr_trace(b, d, chi_a, chi_b, scale, 1.0, gamma1, gamma2, NULL, rids, nrids, 1, NULL);
 }
 
 /* Method A (Eq. kappa2) through the adaptive mesh: kgrad += scale * (the
@@ -566,18 +577,33 @@ int ora_amr_trace_step_method_a(const ora_amr_bundle* b, const ora_amr_desc* d, 
                                 double scale, double a_step, double* kgrad, double* kborn, const int64_t* rids,
                                 long nrids)
 {
-    return amr_trace(b, d, chi_a, chi_b, scale, a_step, kgrad, kborn, NULL, rids, nrids, 2);
+    return amr_trace(b, d, chi_a, chi_b, scale, a_step, kgrad, kborn, NULL, rids, nrids, 2, NULL);
+}
+
+/* A generic integral int K(chi) Q dchi through the adaptive mesh (Eqs. Ic,
+ * Icngp, Icfinal): Q is the scalar field given in place of the potential
+ * (its cell values; vertex values by the Sec. 2.7 rules), K(chi) = k[0] +
+ * k[1] chi + k[2] chi^2; out += scale * (leaf-segment integrals). */
+int ora_amr_trace_step_kq(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
+                          const double* k, double* out, const int64_t* rids, long nrids)
+{
+    const long nr = rids ? nrids : (long)b->nx * b->ny;
+    double* unused = (double*)calloc((size_t)(nr > 0 ? nr : 1), sizeof(double));
+    int rc = amr_trace(b, d, chi_a, chi_b, scale, 1.0, out, unused, NULL, rids, nrids, 3, k);
+    free(unused);
+    return rc;
 }
 
 static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_a, double chi_b, double scale,
                      double a_step, double* kappa, double* kborn, int64_t* nseg, const int64_t* rids, long nrids,
-                     int mode)
+                     int mode, const double* kq)
 {
-    const int shear = mode == 1, method_a = mode == 2;
+    const int shear = mode == 1, method_a = mode == 2, generic = mode == 3;
     if (!(chi_a > chi_b) || chi_b < 0.0) return -1;
     amr_t A;
     if (amr_init(&A, d) != 0) return -10;
     A.grad = method_a;
+    A.scalar = generic;
     const double bpref = 1.5 * d->omega_m * ORA_H0_OVER_C_A * ORA_H0_OVER_C_A / a_step;
     const double h0 = d->box / d->n;
     const double hf = h0 / (double)((int64_t)1 << d->lmax);
@@ -688,7 +714,10 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
                             qk += w[q] * H[q];
                             q2 += w2[q] * H[q];
                         }
-                        if (method_a) {
+                        if (generic) {
+                            ik = H[0] * (segA * (kq[0] + segA * (kq[1] / 2.0 + segA * kq[2] / 3.0))
+                                         - segB * (kq[0] + segB * (kq[1] / 2.0 + segB * kq[2] / 3.0)));
+                        } else if (method_a) {
                             const double qg = n[0] * H[0] + n[1] * H[1] + n[2] * H[2];
                             ik = qg * ((segA - segB) - (segA * segA - segB * segB) / b->chi_s);
                             if (count == 0) { q_start = qg; chi_start = segA; }
@@ -713,6 +742,7 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
                                 q2 += w2[q] * val[q];
                             }
                             if (method_a) Qk[t] = n[0] * val[0] + n[1] * val[1] + n[2] * val[2];
+                            if (generic) Qk[t] = val[0];
                             Qb[t] = shear ? q2 : bpref * val[6];
                         }
                         if (err) break;
@@ -720,7 +750,18 @@ static int amr_trace(const ora_amr_bundle* b, const ora_amr_desc* d, double chi_
                         double aa = b->obs[0] + segA * n[0] - P1[0];
                         double bb = b->obs[1] + segA * n[1] - P1[1];
                         double cc = b->obs[2] + segA * n[2] - P1[2];
-                        if (method_a) {
+                        if (generic) {
+                            double dq[4];
+                            dn_a(Qk, aa, bb, cc, hl, n[0], n[1], n[2], dq);
+                            /* K about chi_A: c0 + c1 s + c2 s^2, s = chi - chi_A in [R, 0] */
+                            const double c0 = kq[0] + segA * (kq[1] + segA * kq[2]), c1 = kq[1] + 2.0 * kq[2] * segA;
+                            const double R = segB - segA;
+                            ik = 0.0;
+                            for (int N = 1; N <= 4; ++N) {
+                                const double RN = pow(R, N);
+                                ik -= dq[N - 1] * (c0 * RN / N + c1 * RN * R / (N + 1) + kq[2] * RN * R * R / (N + 2));
+                            }
+                        } else if (method_a) {
                             double dq[4];
                             dn_a(Qk, aa, bb, cc, hl, n[0], n[1], n[2], dq);
                             ik = ic_dg_tri_a(dq, segA, segB, b->chi_s);
