@@ -84,8 +84,9 @@ enum { RR_PERIODIC = 1,     /* wrap cell indices; else a ray stops at the box fa
                                K_c quadratic in chi (rr_set_kernels; default: the
                                lensing kernel g for both); rr_finalize writes channel
                                0 into kappa and channel 1 into kappa_born. FP32 walk
-                               with compensated sums; rr_create / rr_trace_step only;
-                               no adjoint; not with the other optional flags */
+                               with compensated sums; rr_create / rr_trace_step /
+                               rr_amr_trace_step (records of rr_amr_scalars); no
+                               adjoint; not with the other optional flags */
 
 /* rr_tidal_tensor: where the records are evaluated. */
 enum { RR_AT_VERTICES = 0,  /* mean of the 8 cells sharing each vertex (Sec. 2.7); trilinear */
@@ -503,16 +504,31 @@ rr_status rr_amr_gradient(rr_amr* mesh, const float* phi, int32_t where, float* 
                           const int32_t* bbox, void* stream);
 
 /*
+ * The records of the generic integrals (RR_GENERIC; Eqs. Ic, Icngp, Icfinal)
+ * over the adaptive mesh, in the layout and with the box and output arguments
+ * of rr_amr_tidal: per cell Q0 and Q1, each its field's cell value or, when
+ * its prev is given, (field - prev) * inv_dt (the ISW integrand of Sec. 6 for
+ * a potential); the 8 channels hold {Q0, Q1, 0, 0}, {0, 0, 0, 0}, and vertex
+ * values and leaf records follow as for the tidal records. field0: device,
+ * one float per cell in cell order (as phi); field1 may be NULL (Q1 = 0).
+ * RR_ERR_ARG on a null field0, a non-finite inv_dt or as rr_amr_tidal.
+ */
+rr_status rr_amr_scalars(rr_amr* mesh, const float* field0, const float* prev0, double inv_dt0, const float* field1,
+                         const float* prev1, double inv_dt1, int32_t where, float* leaf_rec, float* cell_buf,
+                         const int32_t* bbox, void* stream);
+
+/*
  * rr_trace_step over an adaptive mesh: each ray advances leaf by leaf (the
  * crossings of the finest lattice grouped per leaf, Sec. 2.5.1) and adds the
  * integrals of rr_trace_step with each leaf's own cell size. `leaf_rec` from
  * rr_amr_tidal with RR_AT_VERTICES for RR_TRILINEAR bundles, RR_AT_CENTRES for
  * RR_NGP. Segment counts count leaf segments. An RR_SHEAR context also
  * accumulates the shear (rr_shear); an RR_METHOD_A context reads the records
- * of rr_amr_gradient and follows Method A as rr_trace_step does. RR_ERR_ARG
- * for RR_FP64_DDA bundles (the AMR walk is the FP32 float-float form only) and
- * for RR_PLAIN_SUMS, RR_SOURCE_MOMENTS and RR_GENERIC; other checks and the
- * step log as rr_trace_step. Steps traced this way have no adjoint:
+ * of rr_amr_gradient and follows Method A as rr_trace_step does; an
+ * RR_GENERIC context reads the records of rr_amr_scalars. RR_ERR_ARG for
+ * RR_FP64_DDA bundles (the AMR walk is the FP32 float-float form only) and for
+ * RR_PLAIN_SUMS and RR_SOURCE_MOMENTS; other checks and the step log as
+ * rr_trace_step. Steps traced this way have no adjoint:
  * rr_trace_step_adjoint and rr_trace_backward return RR_ERR_STATE for them.
  */
 rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* mesh, const float* leaf_rec, double chi_a, double chi_b,

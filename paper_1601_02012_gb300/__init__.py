@@ -250,6 +250,14 @@ class AmrMesh:
         _rr.rr_amr_gradient(self.handle, phi, where, leaf_rec, cell_grad, bbox, stream)
         return leaf_rec
 
+    def scalars(self, field0, leaf_rec, where=RR_AT_VERTICES, prev0=None, inv_dt0=1.0, field1=None, prev1=None,
+                inv_dt1=1.0, cell_buf=None, bbox=None, stream=None):
+        """rr_amr_scalars: the records of the generic integrals, channel c the
+        field (cell order) or (field - prev) * inv_dt; field1 None: zero."""
+        _rr.rr_amr_scalars(self.handle, field0, prev0, inv_dt0, field1, prev1, inv_dt1, where, leaf_rec, cell_buf,
+                           bbox, stream)
+        return leaf_rec
+
     def coarse_grid(self):
         """rr_grid_desc of the coarse grid (for rr_footprint_bbox)."""
         d = _rr.rr_grid_desc()

@@ -113,6 +113,7 @@ def load() -> C.CDLL:
             "rr_amr_sizes": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
             "rr_amr_tidal": ([P, P, I32, P, P, P, P], C.c_int),
             "rr_amr_gradient": ([P, P, I32, P, P, P, P], C.c_int),
+            "rr_amr_scalars": ([P, P, P, D, P, P, D, I32, P, P, P, P], C.c_int),
             "rr_amr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -444,6 +445,17 @@ def rr_amr_gradient(mesh, phi, where: int, leaf_rec, cell_grad=None, bbox=None, 
         bb = C.cast(arr, C.c_void_p)
     _check(load().rr_amr_gradient(mesh, _ptr(phi), int(where), _ptr(leaf_rec), _ptr(cell_grad), bb,
                                   _stream(stream)), "rr_amr_gradient")
+
+
+def rr_amr_scalars(mesh, field0, prev0, inv_dt0: float, field1, prev1, inv_dt1: float, where: int, leaf_rec,
+                   cell_buf=None, bbox=None, stream=None) -> None:
+    bb = None
+    if bbox is not None:
+        arr = (C.c_int32 * 6)(*[int(x) for x in bbox])
+        bb = C.cast(arr, C.c_void_p)
+    _check(load().rr_amr_scalars(mesh, _ptr(field0), _ptr(prev0), float(inv_dt0), _ptr(field1), _ptr(prev1),
+                                 float(inv_dt1), int(where), _ptr(leaf_rec), _ptr(cell_buf), bb, _stream(stream)),
+           "rr_amr_scalars")
 
 
 def rr_amr_trace_step(ctx, mesh, leaf_rec, chi_a: float, chi_b: float, scale: float = 1.0, a_step: float = 1.0,

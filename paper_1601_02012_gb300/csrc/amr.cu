@@ -176,6 +176,13 @@ struct TidalAmrArgs {
     AmrBox box;
     int margin;
     int grad;     // Method A: {d_x Phi, d_y Phi, d_z Phi, 0}, {0, 0, delta, 0} in the same 8 channels
+    // generic integrals: {Q0, Q1, 0, 0}, {0, 0, 0, 0} with Q_c = field_c or (field_c - prev_c) * idt_c
+    const float* f0;
+    const float* p0;
+    const float* f1;
+    const float* p1;
+    float idt0, idt1;
+    int scalar;
 };
 
 __global__ void __launch_bounds__(NTA) amr_tidal_kernel(const TidalAmrArgs a)
@@ -184,6 +191,19 @@ __global__ void __launch_bounds__(NTA) amr_tidal_kernel(const TidalAmrArgs a)
     if (t >= a.cells.pre[a.cells.n]) return;
     const int c = (int)range_at(a.cells, t);
     if (!in_box(a.box, __ldg(a.coarse + c), a.margin)) return;
+    if (a.scalar) {
+        // the cell values themselves (no stencil, no fallback)
+        float q0 = __ldg(a.f0 + c), q1 = 0.f;
+        if (a.p0) q0 = (q0 - __ldg(a.p0 + c)) * a.idt0;
+        if (a.f1) {
+            q1 = __ldg(a.f1 + c);
+            if (a.p1) q1 = (q1 - __ldg(a.p1 + c)) * a.idt1;
+        }
+        float4* out = reinterpret_cast<float4*>(a.H) + 2 * (int64_t)c;
+        out[0] = make_float4(q0, q1, 0.f, 0.f);
+        out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     const int32_t* s = a.stencil + 18 * (int64_t)c;
     float h[6];
     if (a.mode[c] == 0) {
@@ -771,8 +791,16 @@ rr_status rr_amr_sizes(rr_amr* A, int64_t* ncells, int64_t* nleaves, int64_t* nv
     return RR_OK;
 }
 
+struct ScalarIn {
+    const float* f0 = nullptr;
+    const float* p0 = nullptr;
+    const float* f1 = nullptr;
+    const float* p1 = nullptr;
+    float idt0 = 1.f, idt1 = 1.f;
+};
+
 static rr_status amr_records(rr_amr* A, const float* phi, int32_t where, float* leaf_rec, float* cell_tidal,
-                              const int32_t* bbox, void* stream, int grad)
+                              const int32_t* bbox, void* stream, int grad, const ScalarIn* sc = nullptr)
 {
     if (!A || !phi || !leaf_rec || ((uintptr_t)leaf_rec & 15u)) return RR_ERR_ARG;
     if (cell_tidal && ((uintptr_t)cell_tidal & 15u)) return RR_ERR_ARG;
@@ -829,6 +857,13 @@ static rr_status amr_records(rr_amr* A, const float* phi, int32_t where, float* 
         a.dinv = (float)(1.0 / (1.5 * h.omega_m * kH0OverC * kH0OverC));
         a.ih2h = (float)(0.5 / hl);
         a.grad = grad;
+        a.scalar = sc ? 1 : 0;
+        a.f0 = sc ? sc->f0 : nullptr;
+        a.p0 = sc ? sc->p0 : nullptr;
+        a.f1 = sc ? sc->f1 : nullptr;
+        a.p1 = sc ? sc->p1 : nullptr;
+        a.idt0 = sc ? sc->idt0 : 1.f;
+        a.idt1 = sc ? sc->idt1 : 1.f;
         a.box = box;
         // vertices read leaves up to 3 coarse cells outside the box; an
         // interpolated cell reads the coarser level one coarse cell further out
@@ -868,11 +903,26 @@ rr_status rr_amr_gradient(rr_amr* A, const float* phi, int32_t where, float* lea
     return amr_records(A, phi, where, leaf_rec, cell_grad, bbox, stream, 1);
 }
 
+rr_status rr_amr_scalars(rr_amr* A, const float* field0, const float* prev0, double inv_dt0, const float* field1,
+                         const float* prev1, double inv_dt1, int32_t where, float* leaf_rec, float* cell_buf,
+                         const int32_t* bbox, void* stream)
+{
+    if (!field0 || !std::isfinite(inv_dt0) || !std::isfinite(inv_dt1)) return RR_ERR_ARG;
+    ScalarIn sc;
+    sc.f0 = field0;
+    sc.p0 = prev0;
+    sc.f1 = field1;
+    sc.p1 = field1 ? prev1 : nullptr;
+    sc.idt0 = (float)inv_dt0;
+    sc.idt1 = (float)inv_dt1;
+    return amr_records(A, field0, where, leaf_rec, cell_buf, bbox, stream, 0, &sc);
+}
+
 rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, double chi_a, double chi_b,
                             double scale, double a_step, void* stream)
 {
     if (!ctx || !A) return RR_ERR_ARG;
-    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS | RR_GENERIC)) return RR_ERR_ARG;
+    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS)) return RR_ERR_ARG;
     rr_grid_desc g;   // the coarse grid: argument and step-order checks
     g.n[0] = g.n[1] = g.n[2] = A->h.n;
     g.box = A->h.box;
@@ -891,8 +941,10 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, doubl
     m.lmax = A->h.lmax;
     const cudaError_t e =
         launch_trace_amr(a, m, ctx->bundle.interp, (cudaStream_t)stream,
-                         (ctx->bundle.flags & RR_SHEAR) ? kFormShear
-                                                        : ((ctx->bundle.flags & RR_METHOD_A) ? kFormMethodA : kFormKahan));
+                         (ctx->bundle.flags & RR_SHEAR)      ? kFormShear
+                         : (ctx->bundle.flags & RR_METHOD_A) ? kFormMethodA
+                         : (ctx->bundle.flags & RR_GENERIC)  ? kFormGeneric
+                                                             : kFormKahan);
     if (e != cudaSuccess) return status_of_cuda(e);
     StepRecord r = make_step_record(ctx, &g, chi_a, chi_b, scale, a_step);
     r.amr = 1;

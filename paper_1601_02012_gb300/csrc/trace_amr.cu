@@ -21,7 +21,8 @@
 // corner records carried through the same segment integrals. kFormMethodA:
 // Method A (Eq. kappa2) on gradient records (rr_amr_gradient): n . grad Phi
 // with the kernel dg/dchi, the density term with g, and the step's surface
-// terms at the two ends of the traced interval (Eq. 2nterm).
+// terms at the two ends of the traced interval (Eq. 2nterm). kFormGeneric: two
+// scalar channels (rr_amr_scalars records) with their own quadratic kernels.
 #include "walk.cuh"
 
 namespace rr {
@@ -48,6 +49,7 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
 {
     constexpr bool SH = FORM == kFormShear;
     constexpr bool MA = FORM == kFormMethodA;
+    constexpr bool GEN = FORM == kFormGeneric;
     const long long rid = (long long)iy * A.nx + ix;
     const int NF = A.n0;   // finest cells per side
     RayRange rg;
@@ -141,15 +143,26 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                         x.b = __ldg(r + 2 * rc + 1);
                         q2[c] = MA ? radial_pair(nd, x.a) : make_float2(project(W.w, x), x.b.z);
                         if constexpr (MA) q2[c].y = x.b.z;
+                        if constexpr (GEN) q2[c] = make_float2(x.a.x, x.a.y);
                         if constexpr (SH) g2[c] = make_float2(project(w1, x), project(w2, x));
                     }
                 } else {
                     const Rec x = load_rec(A.rec, leaf);
                     q2[0] = MA ? make_float2(radial_pair(nd, x.a).x, x.b.z) : make_float2(project(W.w, x), x.b.z);
+                    if constexpr (GEN) q2[0] = make_float2(x.a.x, x.a.y);
                     if constexpr (SH) g2[0] = make_float2(project(w1, x), project(w2, x));
                 }
                 float G0, G1, G2;
                 kernel_coeffs(t, sig, chiA0, D0, chis, ichis, G0, G1, G2);
+                // generic form: each channel's kernel about the entry point
+                float2 K0, K1, K2;
+                if constexpr (GEN) {
+                    const float chiA = chiA0 - sig;
+                    K0 = make_float2(fmaf(chiA, fmaf(chiA, A.kq[2], A.kq[1]), A.kq[0]),
+                                     fmaf(chiA, fmaf(chiA, A.kq[5], A.kq[4]), A.kq[3]));
+                    K1 = make_float2(-fmaf(2.f * A.kq[2], chiA, A.kq[1]), -fmaf(2.f * A.kq[5], chiA, A.kq[4]));
+                    K2 = make_float2(A.kq[2], A.kq[5]);
+                }
                 if (INTERP == RR_TRILINEAR) {
                     float u[3], vl[3];
 #pragma unroll
@@ -159,7 +172,11 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                                             : (i2f_exact(jp[a]) + W.cu[a]) * inv_span;
                     }
                     if (integrate) {
-                        if constexpr (MA)
+                        if constexpr (GEN) {
+                            float2 e2[4];
+                            line_cubic2(q2, bc2(u[0]), bc2(u[1]), bc2(u[2]), bc2(vl[0]), bc2(vl[1]), bc2(vl[2]), e2);
+                            s2.add(dot_kernel_pair(e2, t, K0, K1, K2));
+                        } else if constexpr (MA)
                             s2.add(segment_trilinear_a(q2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
                         else
                             s2.add(segment_trilinear(q2, u[0], u[1], u[2], vl[0], vl[1], vl[2], t, G0, G1, G2));
@@ -181,7 +198,13 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                     }
                 } else {
                     if (integrate) {
-                        if constexpr (MA) s2.add(segment_ngp_a(q2[0], t, G0, G1, G2));
+                        if constexpr (GEN) {
+                            const float2 tt = bc2(t);
+                            const float2 J1 = __fmul2_rn(
+                                tt, __ffma2_rn(tt, __ffma2_rn(tt, __fmul2_rn(K2, bc2(1.f / 3.f)), __fmul2_rn(K1, bc2(0.5f))),
+                                               K0));
+                            s2.add(__fmul2_rn(q2[0], J1));
+                        } else if constexpr (MA) s2.add(segment_ngp_a(q2[0], t, G0, G1, G2));
                         else s2.add(segment_ngp(q2[0], t, G0, G1, G2));
                         if constexpr (SH) sg.add(segment_ngp(g2[0], t, G0, G1, G2));
                     }
@@ -273,6 +296,9 @@ cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp,
     if (form == kFormShear) {
         if (tri) trace_amr_kernel<RR_TRILINEAR, kFormShear><<<grid, block, 0, s>>>(a, m, t);
         else trace_amr_kernel<RR_NGP, kFormShear><<<grid, block, 0, s>>>(a, m, t);
+    } else if (form == kFormGeneric) {
+        if (tri) trace_amr_kernel<RR_TRILINEAR, kFormGeneric><<<grid, block, 0, s>>>(a, m, t);
+        else trace_amr_kernel<RR_NGP, kFormGeneric><<<grid, block, 0, s>>>(a, m, t);
     } else if (form == kFormMethodA) {
         if (tri) trace_amr_kernel<RR_TRILINEAR, kFormMethodA><<<grid, block, 0, s>>>(a, m, t);
         else trace_amr_kernel<RR_NGP, kFormMethodA><<<grid, block, 0, s>>>(a, m, t);

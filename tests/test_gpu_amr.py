@@ -447,6 +447,43 @@ def test_method_a_nested_gaussian_vs_oracle(rrp, oracle_lib, interp):
     _assert_map(kb, kbo, what="kborn")
 
 
+def _flat(levels):
+    return np.concatenate([np.asarray(q, np.float64).reshape(-1) for q in levels]).astype(np.float32)
+
+
+@pytest.mark.parametrize("interp", [1, 0])
+def test_generic_integrals_random_mesh_vs_oracle(rrp, oracle_lib, interp):
+    """Generic integrals (RR_GENERIC) over three refinement levels: channel 0
+    a finite-difference time derivative (the ISW integrand of Sec. 6) of two
+    fields, channel 1 a field with the lensing kernel, two steps."""
+    import torch
+    mesh = _random_mesh()
+    cur = [np.asarray(p, np.float32).astype(np.float64) for p in mesh.phi]
+    prev = [np.asarray(0.9 * p + 0.01, np.float32).astype(np.float64) for p in mesh.phi]
+    inv_dt = 20.0
+    b = synth.Bundle(23, 17, synth.deg(30), synth.deg(22), (3.1, 12.7, 0.4), 40.0, interp=interp)
+    steps = [synth.Step(40.0, 17.0, 1.1, 1.0), synth.Step(17.0, 0.0, 0.95, 1.0)]
+    ker = ((2.0, 0.01, 0.0), (0.0, 1.0, -1.0 / 40.0))
+    gm = _gpu_mesh(rrp, mesh)
+    where = rrp.RR_AT_VERTICES if interp == 1 else rrp.RR_AT_CENTRES
+    rec = gm.record_buffer(where)
+    fc, fp = torch.from_numpy(_flat(cur)).cuda(), torch.from_numpy(_flat(prev)).cuda()
+    gm.scalars(fc, rec, where, prev0=fp, inv_dt0=inv_dt, field1=fc)
+    tr = rrp.Tracer(b, generic=True)
+    tr.set_kernels(ker)
+    for st in steps:
+        tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a)
+    o1, o2 = tr.finalize()
+    got = [x.cpu().numpy().ravel() for x in (o1, o2)]
+    tr.close()
+    gm.close()
+    q = [(np.asarray(c, np.float32).astype(np.float64) - np.asarray(p_, np.float32).astype(np.float64)) * inv_dt
+         for c, p_ in zip(cur, prev)]
+    want = oracle_lib.amr_trace_kq(b, mesh, q, cur, ker, steps)
+    _assert_map(got[0], want[0], what="isw")
+    _assert_map(got[1], want[1], what="channel 1")
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_meshes_and_bundles(rrp, oracle_lib, seed):
     """Seeded sweep: random refinement (1-3 levels), random bundles (ragged,
