@@ -517,6 +517,38 @@ def run_amr(args, name):
             ma_ms.append(sum(a.elapsed_time(b) for a, b in ev_a))
         tra.close()
 
+        # generic integrals through the same mesh, as the ISW set-up of Sec. 6
+        # (channel 0: (Phi_a - Phi_prev) / dt with K = 2; channel 1: Phi with K = g)
+        trg = rrp.Tracer(w.bundle, generic=True)
+        trg.set_kernels(((2.0, 0.0, 0.0), (0.0, 1.0, -1.0 / w.bundle.chi_s)))
+        cur_g = torch.empty_like(phi)
+        prev_g = torch.empty_like(phi)
+        ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+
+        def generic_pass(timed):
+            rrp.rr_reset(trg.ctx, stream)
+            for i, st in enumerate(steps):
+                torch.mul(phi, steps[i - 1].scale if i > 0 else st.scale, out=prev_g)
+                torch.mul(phi, st.scale, out=cur_g)
+                if timed:
+                    ev_g[i][0].record(stream)
+                gm.scalars(cur_g, rec, rrp.RR_AT_VERTICES, prev0=prev_g, inv_dt0=100.0, field1=cur_g,
+                           bbox=bboxes[i], stream=stream)
+                trg.amr_step(gm, rec, st.chi_a, st.chi_b, 1.0, st.a, stream)
+                if timed:
+                    ev_g[i][1].record(stream)
+            rrp.rr_finalize(trg.ctx, kappa, kborn, stream)
+
+        generic_pass(False)
+        gen_ms = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            generic_pass(True)
+            torch.cuda.synchronize()
+            gen_ms.append(sum(a.elapsed_time(b) for a, b in ev_g))
+        trg.close()
+        del cur_g, prev_g
+
     peaks, peak_kind = _peaks()
     total_ms = sum(times)
     per_pass_trace_s = trace_ms / args.steps / 1e3
@@ -538,6 +570,9 @@ def run_amr(args, name):
         "method_a": {"ms_per_pass": sum(ma_ms) / len(ma_ms), "method_b_ms_per_pass": total_ms / args.steps,
                      "note": "records (rr_amr_gradient over each step's footprint) and the Method A AMR walk "
                              "of one pass, CUDA events per step, L2 flushed before each pass, mean of 2"},
+        "generic_isw": {"ms_per_pass": sum(gen_ms) / len(gen_ms), "method_b_ms_per_pass": total_ms / args.steps,
+                        "note": "records (rr_amr_scalars, two channels, over each step's footprint) and the "
+                                "generic AMR walk set up as the ISW integral, CUDA events per step, mean of 2"},
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "trace_amr_kernel<trilinear>",
