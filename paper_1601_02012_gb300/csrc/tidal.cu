@@ -1,21 +1,24 @@
 // Tidal tensor and vertex records (Sec. 3.3, Eq. tidalexample; Sec. 2.7), and
 // the gradient records of Method A (Eq. kappa2).
 //
-// One CTA of 8 warps owns an 8 (y) x 32 (z) block of cell centres, one warp
-// per z-row, one thread per centre, and marches along x through a chunk of
-// planes. Per plane it keeps three planes of the potential (with a one-cell
-// halo) in a shared ring, and every thread evaluates the six central-difference
-// second derivatives at its own centre. For records at vertices, vertex (y, z)
-// of the plane is the upper corner of centres (y-1..y, z-1..z): the z pair is
-// summed with a warp shuffle, the y pair through shared memory, and the
-// record is the mean of that 2 x 2 sum and the previous plane's (kept in
-// registers) -- the 8 cells around the vertex. The first centre row and column
-// of the block are the halo of its 7 x 31 vertices. The next potential plane is
-// loaded into registers while the current one is processed. HBM traffic per
-// point: the potential read about 1.5 times (halo re-reads hit L2) and the
-// 32-byte record written once: 36 algorithmic bytes per point. The gradient
-// records (KIND 1) take the same march with the three central first
-// differences and delta instead: one 16-byte record, 20 bytes per point.
+// One CTA of 8 warps owns a 16 (y) x 32 (z) block of cell centres, each warp
+// two y-rows, each thread the two centres of its lane in them, and marches
+// along x through a chunk of planes. Per plane it keeps three planes of the
+// potential (with a one-cell halo) in a shared ring, and every thread
+// evaluates the six central-difference second derivatives at its two centres
+// (whose stencils share their middle rows: 28 shared-memory reads instead of
+// 2 x 19). For records at vertices, vertex (y, z) of the plane is the upper
+// corner of centres (y-1..y, z-1..z): the z pair is summed with a warp
+// shuffle, the y pair in registers (the vertex between a thread's two rows)
+// or through shared memory (the vertex between two warps), and the record is
+// the mean of that 2 x 2 sum and the previous plane's (kept in registers) --
+// the 8 cells around the vertex. The first centre row and column of the block
+// are the halo of its 15 x 31 vertices. The next potential plane is loaded
+// into registers while the current one is processed. HBM traffic per point:
+// the potential read about 1.2 times (halo re-reads hit L2) and the 32-byte
+// record written once: 36 algorithmic bytes per point. The gradient records
+// (KIND 1) take the same march with the three central first differences and
+// delta instead: one 16-byte record, 20 bytes per point.
 #include <algorithm>
 
 #include "rr_internal.h"
@@ -23,8 +26,8 @@
 namespace rr {
 namespace {
 
-constexpr int TY = 8, TZ = 32;       // centres per CTA and plane
-constexpr int NT = TY * TZ;          // one thread per centre
+constexpr int TY = 16, TZ = 32;      // centres per CTA and plane
+constexpr int NT = 256;              // 8 warps, two y-rows of 32 centres each
 constexpr int XCHUNK_MAX = 32;       // planes per CTA, at most
 
 struct TidalArgs {
@@ -50,12 +53,51 @@ __device__ __forceinline__ int wrapi(int i, int n)
     return r < 0 ? r + n : r;
 }
 
-// MODE 0: records at vertices (7 x 31 per CTA and plane); MODE 1: records at
-// centres (8 x 32). KIND 0: tidal records, 7 channels {Hxx, Hyy, Hzz, Hxy,
+// The channels of one centre from the three potential planes (P0, P1, P2 =
+// planes x-1, x, x+1) read at the offsets of its stencil: KIND 0: the six
+// second differences of Eq. (tidalexample) and delta; KIND 1: the three
+// central first differences and delta. Differences of neighbours first.
+template <int KIND>
+__device__ __forceinline__ void centre_channels(float p0, float x0m, float x0p, float ym, float yp, float zm,
+                                                float zp, float xyA, float xyB, float xzA, float xzB, float yzA,
+                                                float yzB, float dlt, bool has_delta, const TidalArgs& a,
+                                                float* h)
+{
+    // x0m / x0p: P0 and P2 at the centre; ym / yp, zm / zp: P1 neighbours;
+    // xyA = P2[y+1] - P2[y-1], xyB = P0[y-1] - P0[y+1] (and so on)
+    if constexpr (KIND == 0) {
+        h[0] = ((x0m - p0) + (x0p - p0)) * a.ih2;
+        h[1] = ((ym - p0) + (yp - p0)) * a.ih2;
+        h[2] = ((zm - p0) + (zp - p0)) * a.ih2;
+        h[3] = (xyA + xyB) * a.iq;
+        h[4] = (xzA + xzB) * a.iq;
+        h[5] = (yzA + yzB) * a.iq;
+        h[6] = has_delta ? dlt : (h[0] + h[1] + h[2]) * a.dinv;
+    } else {
+        h[0] = (x0p - x0m) * a.ih2h;
+        h[1] = (yp - ym) * a.ih2h;
+        h[2] = (zp - zm) * a.ih2h;
+        if (has_delta) {
+            h[3] = dlt;
+        } else {
+            const float lap = (((x0m - p0) + (x0p - p0)) + ((ym - p0) + (yp - p0)) + ((zm - p0) + (zp - p0))) * a.ih2;
+            h[3] = lap * a.dinv;
+        }
+    }
+}
+
+// MODE 0: records at vertices (15 x 31 per CTA and plane); MODE 1: records at
+// centres (16 x 32). KIND 0: tidal records, 7 channels {Hxx, Hyy, Hzz, Hxy,
 // Hxz, Hyz, delta} in 2 float4; KIND 1: gradient records, 4 channels
-// {d_x Phi, d_y Phi, d_z Phi, delta} in 1 float4.
+// {d_x Phi, d_y Phi, d_z Phi, delta} in 1 float4. Each thread owns the two
+// centres (2 w, z) and (2 w + 1, z) of its warp w, lane z: the two stencils
+// share their middle rows, so 28 shared-memory reads serve two centres (19 for
+// one alone), and the vertex between the two rows sums its y pair in
+// registers.
+// (4 resident CTAs per SM: 64 registers; uncapped, 69 registers left 3 and
+// measured 9 % slower on a 512^3 grid)
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
+__global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
 {
     constexpr int V = (MODE == 0) ? 1 : 0;
     constexpr int NC = KIND == 0 ? 7 : 4;            // channels
@@ -63,10 +105,12 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
     constexpr int PY = TY + 2, PZ = TZ + 2;          // potential per plane (halo 1 around the centres)
     constexpr int NP = PY * PZ;
     constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane
+    constexpr int NW = NT / 32;                      // warps
     __shared__ float ring[4][NP];   // potential planes c - 1, c, c + 1 and the one arriving (c + 2)
-    __shared__ float sP[2][MODE == 0 ? NC : 1][MODE == 0 ? NT : 1];   // z-pair sums of every centre, by plane parity
+    __shared__ float sP[2][MODE == 0 ? NC : 1][MODE == 0 ? NT : 1];   // z-pair sums of each warp's second row
 
-    const int ty = threadIdx.x / TZ, tz = threadIdx.x % TZ;
+    const int w = threadIdx.x / 32, tz = threadIdx.x % 32;
+    const int r0 = 2 * w;                                                  // this thread's first centre row
     const int py0 = blockIdx.y * OY, pz0 = blockIdx.x * OZ;               // box-relative first output
     const int xb = blockIdx.z * a.xchunk, xe = min(xb + a.xchunk, a.ex);   // output planes [xb, xe)
     const int cy0 = a.y0 + py0 - V, cz0 = a.z0 + pz0 - V;                 // centre (0, 0) of the block
@@ -104,14 +148,29 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
     }
     __syncthreads();
 
-    const int oy = py0 + ty - V, oz = pz0 + tz - V;   // this thread's output point (box-relative)
-    const bool out_yz = ty >= V && tz >= V && oy < a.ey && oz < a.ez;
-    const size_t out_yz_off = out_yz ? (size_t)wrapi(a.y0 + oy, a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2) : 0;
-    const int o = (ty + 1) * PZ + (tz + 1);          // own centre in the ring
-    const size_t d_yz = (size_t)wrapi(cy0 + ty, a.n1) * a.n2 + wrapi(cz0 + tz, a.n2);
-    float prev[NC];   // 2 x 2 centre sum of the previous plane
+    // outputs: centre rows r0 and r0 + 1 (MODE 1), or the vertices on rows r0
+    // and r0 + 1 (MODE 0: vertex row r is the upper corner of centre rows
+    // r - 1 and r; row 0 and column 0 are the halo)
+    const int oz = pz0 + tz - V;
+    const bool oz_ok = tz >= V && oz < a.ez;
+    int oy[2];
+    bool out_ok[2];
+    size_t out_off[2];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) prev[q] = 0.f;
+    for (int k = 0; k < 2; ++k) {
+        oy[k] = py0 + r0 + k - V;
+        out_ok[k] = oz_ok && (r0 + k) >= V && oy[k] < a.ey;
+        out_off[k] = out_ok[k] ? (size_t)wrapi(a.y0 + oy[k], a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2) : 0;
+    }
+    const int o = (r0 + 1) * PZ + (tz + 1);          // first centre in the ring
+    size_t d_yz[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) d_yz[k] = (size_t)wrapi(cy0 + r0 + k, a.n1) * a.n2 + wrapi(cz0 + tz, a.n2);
+    float prev[2][NC];   // 2 x 2 centre sums of the previous plane, per output row
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) prev[k][q] = 0.f;
     for (int c = c_first; c <= c_last; ++c) {
         const float* P0 = ring[slot(c - 1)];
         const float* P1 = ring[slot(c)];
@@ -123,75 +182,86 @@ __global__ void __launch_bounds__(NT) tidal_kernel(const TidalArgs a)
         if (c + 3 <= c_last + 1) fetch(c + 3, nxt2);
         if (c + 2 <= c_last + 1) put(slot(c + 2), nxt);
 
-        float h[NC];
-        const float p0 = P1[o];
-        if constexpr (KIND == 0) {
-            // second derivatives at this thread's centre (differences of neighbours first)
-            h[0] = ((P0[o] - p0) + (P2[o] - p0)) * a.ih2;
-            h[1] = ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) * a.ih2;
-            h[2] = ((P1[o - 1] - p0) + (P1[o + 1] - p0)) * a.ih2;
-            h[3] = ((P2[o + PZ] - P2[o - PZ]) + (P0[o - PZ] - P0[o + PZ])) * a.iq;
-            h[4] = ((P2[o + 1] - P2[o - 1]) + (P0[o - 1] - P0[o + 1])) * a.iq;
-            h[5] = ((P1[o + PZ + 1] - P1[o + PZ - 1]) + (P1[o - PZ - 1] - P1[o - PZ + 1])) * a.iq;
-            if (a.delta) h[6] = __ldg(a.delta + (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + d_yz);
-            else h[6] = (h[0] + h[1] + h[2]) * a.dinv;
-        } else {
-            // central first differences, and delta (given, or from the 7-point
-            // Laplacian, the trace of the stencils above)
-            h[0] = (P2[o] - P0[o]) * a.ih2h;
-            h[1] = (P1[o + PZ] - P1[o - PZ]) * a.ih2h;
-            h[2] = (P1[o + 1] - P1[o - 1]) * a.ih2h;
-            if (a.delta) {
-                h[3] = __ldg(a.delta + (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + d_yz);
-            } else {
-                const float lap = (((P0[o] - p0) + (P2[o] - p0)) + ((P1[o - PZ] - p0) + (P1[o + PZ] - p0)) +
-                                   ((P1[o - 1] - p0) + (P1[o + 1] - p0))) * a.ih2;
-                h[3] = lap * a.dinv;
-            }
+        // the two stencils: rows r0 - 1 .. r0 + 2 of P1 at z - 1 .. z + 1, rows
+        // r0 - 1 .. r0 + 2 of P0 and P2 at z, rows r0, r0 + 1 of P0 and P2 at z +- 1
+        const int om = o - PZ, o1 = o + PZ, op = o + 2 * PZ;
+        const float a_m0 = P1[om - 1], a_m1 = P1[om], a_m2 = P1[om + 1];
+        const float a_00 = P1[o - 1], a_01 = P1[o], a_02 = P1[o + 1];
+        const float a_10 = P1[o1 - 1], a_11 = P1[o1], a_12 = P1[o1 + 1];
+        const float a_p0 = P1[op - 1], a_p1 = P1[op], a_p2 = P1[op + 1];
+        const float b_m = P0[om], b_0 = P0[o], b_1 = P0[o1], b_p = P0[op];
+        const float b_0m = P0[o - 1], b_0p = P0[o + 1], b_1m = P0[o1 - 1], b_1p = P0[o1 + 1];
+        const float c_m = P2[om], c_0 = P2[o], c_1 = P2[o1], c_p = P2[op];
+        const float c_0m = P2[o - 1], c_0p = P2[o + 1], c_1m = P2[o1 - 1], c_1p = P2[o1 + 1];
+        float dl[2] = {0.f, 0.f};
+        if (a.delta) {
+            const size_t base = (size_t)wrapi(c, a.n0) * a.n1 * a.n2;
+            dl[0] = __ldg(a.delta + base + d_yz[0]);
+            dl[1] = __ldg(a.delta + base + d_yz[1]);
         }
+        float h[2][NC];
+        // centre (r0, z): y neighbours rows r0 -+ 1
+        centre_channels<KIND>(a_01, b_0, c_0, a_m1, a_11, a_00, a_02, c_1 - c_m, b_m - b_1, c_0p - c_0m, b_0m - b_0p,
+                              a_12 - a_10, a_m0 - a_m2, dl[0], a.delta != nullptr, a, h[0]);
+        // centre (r0 + 1, z): y neighbours rows r0, r0 + 2
+        centre_channels<KIND>(a_11, b_1, c_1, a_01, a_p1, a_10, a_12, c_p - c_0, b_0 - b_p, c_1p - c_1m, b_1m - b_1p,
+                              a_p2 - a_p0, a_00 - a_02, dl[1], a.delta != nullptr, a, h[1]);
 
-        float pz[NC];
+        float pz[2][NC];
         if constexpr (MODE == 0) {
-            // z pair: this centre and the one below it in z (the lane to the left)
+            // z pairs: each centre and the one below it in z (the lane to the left)
 #pragma unroll
-            for (int q = 0; q < NC; ++q) pz[q] = h[q] + __shfl_up_sync(0xffffffffu, h[q], 1);
-            if (ty < TY - 1) {
+            for (int k = 0; k < 2; ++k)
 #pragma unroll
-                for (int q = 0; q < NC; ++q) sP[(c - c_first) & 1][q][threadIdx.x] = pz[q];
+                for (int q = 0; q < NC; ++q) pz[k][q] = h[k][q] + __shfl_up_sync(0xffffffffu, h[k][q], 1);
+            if (w < NW - 1) {
+#pragma unroll
+                for (int q = 0; q < NC; ++q) sP[(c - c_first) & 1][q][threadIdx.x] = pz[1][q];
             }
         }
-        // plane c + 2 is in the ring and the z pairs of plane c are shared; the
-        // next iteration writes the other sP buffer and a ring slot not read here
+        // plane c + 2 is in the ring and the second-row z pairs of plane c are
+        // shared; the next iteration writes the other sP buffer and a ring slot
+        // not read here
         __syncthreads();
         if constexpr (MODE == 0) {
-            if (ty >= 1) {
-                float b[NC];
+            // vertex row r0 + 1: centre rows r0 and r0 + 1 (this thread); vertex
+            // row r0: centre rows r0 - 1 (the warp above's second row) and r0
+            float b[2][NC];
 #pragma unroll
-                for (int q = 0; q < NC; ++q) b[q] = pz[q] + sP[(c - c_first) & 1][q][threadIdx.x - TZ];
-                if (c > c_first && out_yz) {
-                    const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off;
+            for (int q = 0; q < NC; ++q) {
+                b[1][q] = pz[0][q] + pz[1][q];
+                b[0][q] = w >= 1 ? pz[0][q] + sP[(c - c_first) & 1][q][threadIdx.x - 32] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (c > c_first && out_ok[k]) {
+                    const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_off[k];
                     if constexpr (KIND == 0) {
                         float4* r = a.rec + 2 * pt;
-                        r[0] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
-                                           (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
-                        r[1] = make_float4((prev[4] + b[4]) * 0.125f, (prev[5] + b[5]) * 0.125f,
-                                           (prev[6] + b[6]) * 0.125f, 0.f);
+                        r[0] = make_float4((prev[k][0] + b[k][0]) * 0.125f, (prev[k][1] + b[k][1]) * 0.125f,
+                                           (prev[k][2] + b[k][2]) * 0.125f, (prev[k][3] + b[k][3]) * 0.125f);
+                        r[1] = make_float4((prev[k][4] + b[k][4]) * 0.125f, (prev[k][5] + b[k][5]) * 0.125f,
+                                           (prev[k][6] + b[k][6]) * 0.125f, 0.f);
                     } else {
-                        a.rec[pt] = make_float4((prev[0] + b[0]) * 0.125f, (prev[1] + b[1]) * 0.125f,
-                                                (prev[2] + b[2]) * 0.125f, (prev[3] + b[3]) * 0.125f);
+                        a.rec[pt] = make_float4((prev[k][0] + b[k][0]) * 0.125f, (prev[k][1] + b[k][1]) * 0.125f,
+                                                (prev[k][2] + b[k][2]) * 0.125f, (prev[k][3] + b[k][3]) * 0.125f);
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < NC; ++q) prev[q] = b[q];
+                for (int q = 0; q < NC; ++q) prev[k][q] = b[k][q];
             }
-        } else if (out_yz) {
-            const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_yz_off;
-            if constexpr (KIND == 0) {
-                float4* r = a.rec + 2 * pt;
-                r[0] = make_float4(h[0], h[1], h[2], h[3]);
-                r[1] = make_float4(h[4], h[5], h[6], 0.f);
-            } else {
-                a.rec[pt] = make_float4(h[0], h[1], h[2], h[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!out_ok[k]) continue;
+                const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_off[k];
+                if constexpr (KIND == 0) {
+                    float4* r = a.rec + 2 * pt;
+                    r[0] = make_float4(h[k][0], h[k][1], h[k][2], h[k][3]);
+                    r[1] = make_float4(h[k][4], h[k][5], h[k][6], 0.f);
+                } else {
+                    a.rec[pt] = make_float4(h[k][0], h[k][1], h[k][2], h[k][3]);
+                }
             }
         }
 #pragma unroll
