@@ -61,17 +61,11 @@ __device__ __forceinline__ float4 sum_error(float4 o, float4 x)
 // point together. When all 32 lanes flush one point, their contributions are
 // summed across the warp first by a reduce-scatter butterfly (each of the
 // first three exchanges halves the channels a lane keeps: 4 + 2 + 1 + 1 + 1
-// shuffles instead of 5 per channel), compensated (TwoSum at every addition,
-// the errors carried alongside), after which lane 4c holds the total of
-// channel c and adds it with scalar atomics; otherwise every lane adds its own.
-__device__ __forceinline__ void warp_pair_add(float& x, float& e, float ox, float oe)
-{
-    float sum, err;
-    two_sum(x, ox, sum, err);
-    x = sum;
-    e += oe + err;
-}
-
+// shuffles instead of 5 per channel), after which lane 4c holds the total of
+// channel c and adds it with a compensated scalar atomic; otherwise every lane
+// adds its own. The 32-term warp sums are plain FP32 (a relative error of a
+// few ulp per flush); the compensation guards the long chains of additions
+// into one record, where thousands of contributions of both signs meet.
 __device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long idx, float S, float gk, float gb,
                                            const float* w)
 {
@@ -80,43 +74,33 @@ __device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long 
     if (active == 0xffffffffu && __match_any_sync(active, idx) == active) {
         constexpr unsigned FULL = 0xffffffffu;
         const int lane = threadIdx.x & 31;
-        float x[8] = {a * w[0], a * w[1], a * w[2], a * w[3], a * w[4], a * w[5], gb * S, 0.f};
-        float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float x[8] = {a * w[0], a * w[1], a * w[2], a * w[3], a * w[4], a * w[5], gb * S, 0.f};
         // xor 16: keep channels 4 b4 .. 4 b4 + 3
         const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-        float k4[4], f4[4];
+        float k4[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float sx = b4 ? x[i] : x[4 + i], se = b4 ? e[i] : e[4 + i];
-            k4[i] = b4 ? x[4 + i] : x[i];
-            f4[i] = b4 ? e[4 + i] : e[i];
-            warp_pair_add(k4[i], f4[i], __shfl_xor_sync(FULL, sx, 16), __shfl_xor_sync(FULL, se, 16));
+            const float sx = b4 ? x[i] : x[4 + i];
+            k4[i] = (b4 ? x[4 + i] : x[i]) + __shfl_xor_sync(FULL, sx, 16);
         }
         // xor 8: keep 2 of the 4
-        float k2[2], f2[2];
+        float k2[2];
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            const float sx = b3 ? k4[i] : k4[2 + i], se = b3 ? f4[i] : f4[2 + i];
-            k2[i] = b3 ? k4[2 + i] : k4[i];
-            f2[i] = b3 ? f4[2 + i] : f4[i];
-            warp_pair_add(k2[i], f2[i], __shfl_xor_sync(FULL, sx, 8), __shfl_xor_sync(FULL, se, 8));
+            const float sx = b3 ? k4[i] : k4[2 + i];
+            k2[i] = (b3 ? k4[2 + i] : k4[i]) + __shfl_xor_sync(FULL, sx, 8);
         }
-        // xor 4: keep 1 of the 2
-        float v = b2 ? k2[1] : k2[0], ve = b2 ? f2[1] : f2[0];
-        {
-            const float sx = b2 ? k2[0] : k2[1], se = b2 ? f2[0] : f2[1];
-            warp_pair_add(v, ve, __shfl_xor_sync(FULL, sx, 4), __shfl_xor_sync(FULL, se, 4));
-        }
-        // xor 2, xor 1: the whole warp's total of channel (lane >> 2)
-        warp_pair_add(v, ve, __shfl_xor_sync(FULL, v, 2), __shfl_xor_sync(FULL, ve, 2));
-        warp_pair_add(v, ve, __shfl_xor_sync(FULL, v, 1), __shfl_xor_sync(FULL, ve, 1));
+        // xor 4: keep 1 of the 2; xor 2, xor 1: the whole warp's total of channel (lane >> 2)
+        float v = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(FULL, b2 ? k2[0] : k2[1], 4);
+        v += __shfl_xor_sync(FULL, v, 2);
+        v += __shfl_xor_sync(FULL, v, 1);
         const int ch = lane >> 2;
         if ((lane & 3) == 0 && ch < 7 && v != 0.f) {
             float* p = reinterpret_cast<float*>(grad + 4 * idx);
             const float old = atomicAdd(p + ch, v);
             float sum, err;
             two_sum(old, v, sum, err);
-            atomicAdd(p + 8 + ch, err + ve);
+            atomicAdd(p + 8 + ch, err);
         }
         return;
     }
