@@ -105,6 +105,13 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     const int nn[3] = {A.n0, A.n1, A.n2};
     RayRange rg;
     if (!ray_range(A, rid, rg)) return;
+    prefetch_l2(A.kacc + rid);
+    prefetch_l2(A.bacc + rid);
+    prefetch_l2(A.nseg + rid);
+    if constexpr (SH) {
+        prefetch_l2(A.g1acc + rid);
+        prefetch_l2(A.g2acc + rid);
+    }
     const R chis = (R)A.chi_s;
     const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
     const long long sx = (long long)A.n1 * A.n2, sy = A.n2;

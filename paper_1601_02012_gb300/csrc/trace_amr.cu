@@ -54,6 +54,13 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     const int NF = A.n0;   // finest cells per side
     RayRange rg;
     if (!ray_range(A, rid, rg)) return;
+    prefetch_l2(A.kacc + rid);
+    prefetch_l2(A.bacc + rid);
+    prefetch_l2(A.nseg + rid);
+    if constexpr (SH) {
+        prefetch_l2(A.g1acc + rid);
+        prefetch_l2(A.g2acc + rid);
+    }
     const float chis = (float)A.chi_s;
     const float ichis = A.inv_chi_s_f;
     const int nsub = max(1, f2i_signed(fminf(ceilf(rg.Lf / A.sub_len), 4194303.f)));

@@ -23,6 +23,13 @@ __device__ __forceinline__ void tile_ray(const TileCfg& t, int tx, int ty, int& 
     iy = ty * (wy * t.bwy) + (warp / t.bwx) * wy + (lane / t.wx);
 }
 
+// starts moving the line holding p into L2; the per-ray accumulators are
+// read and written once, after the walk, so their fetch overlaps the walk
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
+}
+
 __device__ __forceinline__ int wrap_once(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
 struct Rec {
