@@ -214,6 +214,27 @@ rr_status rr_set_kernels(rr_ctx* ctx, const double k[6]);
 rr_status rr_set_observer(rr_ctx* ctx, const double obs[3]);
 
 /*
+ * Copy, from host memory into the same positions of a device array, the cells
+ * of a cell-centred field (the potential Phi, delta, a scalar channel) that a
+ * boxed rr_tidal_tensor, rr_gradient_records or rr_scalar_records call reads:
+ * the box widened by 2 cells on each side (the stencils of Eq. (tidalexample)
+ * and the 8-cell vertex mean of Sec. 2.7 reach 2 cells below a vertex box and
+ * 1 above), indices modulo n. A step of the walk reads records only inside its
+ * footprint (rr_footprint_bbox), so streaming each step's footprint replaces
+ * copying the whole field. Cells outside the widened box are left as they were.
+ *   host   host, n0*n1*n2 floats in the grid's [ix][iy][iz] order (z fastest);
+ *          page-locked for a copy that is asynchronous to the host.
+ *   dev    device, n0*n1*n2 floats, same order.
+ *   bbox   6 ints as for rr_tidal_tensor, or NULL for the whole field.
+ *   bytes  out (may be NULL): the bytes the call enqueued.
+ * At most 8 three-dimensional copies (the wrapped pieces of the box) are
+ * enqueued on `stream`; the call does not wait for them.
+ * RR_ERR_ARG on a null pointer or a bad box; RR_ERR_CUDA if a copy is refused.
+ */
+rr_status rr_upload_box(const rr_grid_desc* grid, const float* host, float* dev, const int32_t* bbox,
+                        int64_t* bytes, void* stream);
+
+/*
  * Host helper: a conservative box of vertex (or centre) indices {x0, x1, y0,
  * y1, z0, z1} that contains every point the bundle's rays can read while
  * tracing [chi_b, chi_a] (the footprint of one step, used to restrict

@@ -18,12 +18,13 @@ from ._rr import rr_amr_create, rr_amr_destroy, rr_amr_sizes, rr_amr_tidal, rr_a
 from ._rr import RR_SHEAR, rr_shear  # noqa: E402
 from ._rr import RR_METHOD_A, rr_gradient_records  # noqa: E402
 from ._rr import RR_GENERIC, rr_scalar_records, rr_set_kernels, rr_set_observer  # noqa: E402
+from ._rr import rr_upload_box  # noqa: E402
 
 __all__ = [
     "Batch", "AmrMesh", "source_kappa", "rr_amr_create", "rr_amr_destroy", "rr_amr_sizes", "rr_amr_tidal",
     "rr_amr_trace_step", "RR_SHEAR", "rr_shear", "RR_METHOD_A", "rr_gradient_records", "trace_method_a",
     "gradient_buffer", "RR_GENERIC", "rr_scalar_records", "rr_set_kernels", "rr_set_observer", "scalar_buffer",
-    "trace_tiles",
+    "trace_tiles", "rr_upload_box",
     "Tracer", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
@@ -172,6 +173,47 @@ class Tracer:
             gamma2 = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
         _rr.rr_shear(self.ctx, gamma1, gamma2, stream)
         return gamma1, gamma2
+
+    def trace_streamed(self, grid, phi_host, steps, rec, bufs, stream, copy_stream, bboxes=None, delta_host=None,
+                       delta_bufs=None):
+        """The steps of a pass with the potential streamed from host memory.
+
+        phi_host: page-locked host tensor of n0*n1*n2 floats; bufs: two device
+        arrays of the same size; steps: objects with chi_a, chi_b, scale, a.
+        For each step rr_upload_box copies the step's footprint (plus the
+        stencil reach) into one of the two buffers on ``copy_stream`` while the
+        step before computes from the other one; ``stream`` waits for each
+        copy before the step's records, and a copy into a buffer waits until
+        the records made from it two steps earlier are done. Only the cells a
+        step reads are moved, so the maps equal those of the same steps on the
+        whole field. delta_host / delta_bufs: the same for a given density
+        contrast. Returns the bytes copied."""
+        import torch
+        if self.generic:
+            raise ValueError("trace_streamed: the generic form takes its fields through scalars()")
+        g = grid_desc(grid)
+        if bboxes is None:
+            bboxes = [self.footprint(grid, st.chi_a, st.chi_b) for st in steps]
+        released = [None, None]
+        total = 0
+        for i, st in enumerate(steps):
+            slot = i % 2
+            if released[slot] is not None:
+                copy_stream.wait_event(released[slot])
+            total += rr_upload_box(g, phi_host, bufs[slot], bboxes[i], copy_stream)
+            delta = None
+            if delta_host is not None:
+                total += rr_upload_box(g, delta_host, delta_bufs[slot], bboxes[i], copy_stream)
+                delta = delta_bufs[slot]
+            copied = torch.cuda.Event()
+            copied.record(copy_stream)
+            stream.wait_event(copied)
+            self.tidal(grid, bufs[slot], rec, delta=delta, bbox=bboxes[i], stream=stream)
+            done = torch.cuda.Event()
+            done.record(stream)
+            released[slot] = done
+            self.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+        return total
 
     def amr_step(self, mesh, leaf_rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):
         """One step over an adaptive mesh (``AmrMesh``) from its leaf records."""

@@ -78,6 +78,7 @@ def load() -> C.CDLL:
             "rr_reset": ([P, P], C.c_int),
             "rr_tidal_tensor": ([P, P, P, P, I32, P, P], C.c_int),
             "rr_footprint_bbox": ([P, P, D, D, P], C.c_int),
+            "rr_upload_box": ([P, P, P, P, C.POINTER(C.c_int64), P], C.c_int),
             "rr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
             "rr_finalize": ([P, P, P, P], C.c_int),
             "rr_sync_status": ([P, P], C.c_int),
@@ -221,6 +222,20 @@ def rr_footprint_bbox(bundle: rr_bundle_desc, grid: rr_grid_desc, chi_a: float, 
     _check(load().rr_footprint_bbox(C.byref(bundle), C.byref(grid), float(chi_a), float(chi_b),
                                     C.cast(arr, C.c_void_p)), "rr_footprint_bbox")
     return tuple(int(x) for x in arr)
+
+
+def rr_upload_box(grid: rr_grid_desc, host, dev, bbox=None, stream=None) -> int:
+    """Copy the cells a boxed record call reads (the box widened by 2 cells,
+    modulo n) from the host array ``host`` into the device array ``dev``;
+    returns the bytes enqueued."""
+    bb = None
+    if bbox is not None:
+        arr = (C.c_int32 * 6)(*[int(x) for x in bbox])
+        bb = C.cast(arr, C.c_void_p)
+    nbytes = C.c_int64(0)
+    _check(load().rr_upload_box(C.byref(grid), _ptr(host), _ptr(dev), bb, C.byref(nbytes), _stream(stream)),
+           "rr_upload_box")
+    return int(nbytes.value)
 
 
 def rr_trace_step(ctx, grid: rr_grid_desc, rec, chi_a: float, chi_b: float, scale: float = 1.0,

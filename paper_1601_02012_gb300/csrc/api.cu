@@ -312,6 +312,60 @@ rr_status rr_scalar_records(const rr_grid_desc* grid, const float* field, const 
                                            (cudaStream_t)stream));
 }
 
+rr_status rr_upload_box(const rr_grid_desc* grid, const float* host, float* dev, const int32_t* bbox,
+                        int64_t* bytes, void* stream)
+{
+    rr_status st = check_grid(grid);
+    if (st != RR_OK) return st;
+    if (!host || !dev) return RR_ERR_ARG;
+    const int* n = grid->n;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (!bbox) {
+        const size_t all = sizeof(float) * (size_t)n[0] * n[1] * n[2];
+        if (bytes) *bytes = (int64_t)all;
+        return from_cuda(cudaMemcpyAsync(dev, host, all, cudaMemcpyHostToDevice, s));
+    }
+    // per axis: the widened range as at most two runs of indices in [0, n)
+    int r0[3][2], rw[3][2], nr[3];
+    for (int a = 0; a < 3; ++a) {
+        const long long ext = (long long)bbox[2 * a + 1] - bbox[2 * a];
+        if (ext < 1 || ext > n[a]) return RR_ERR_ARG;
+        if (bbox[2 * a] < -(1 << 20) || bbox[2 * a + 1] > (1 << 20)) return RR_ERR_ARG;
+        const long long w = ext + 4;
+        if (w >= n[a]) {
+            nr[a] = 1; r0[a][0] = 0; rw[a][0] = n[a];
+            continue;
+        }
+        const int lo = (int)(((long long)bbox[2 * a] - 2) % n[a] + n[a]) % n[a];
+        if (lo + w <= n[a]) {
+            nr[a] = 1; r0[a][0] = lo; rw[a][0] = (int)w;
+        } else {
+            nr[a] = 2;
+            r0[a][0] = lo; rw[a][0] = n[a] - lo;
+            r0[a][1] = 0;  rw[a][1] = (int)(lo + w - n[a]);
+        }
+    }
+    const size_t pitch = sizeof(float) * (size_t)n[2];
+    int64_t total = 0;
+    for (int i = 0; i < nr[0]; ++i)
+        for (int j = 0; j < nr[1]; ++j)
+            for (int k = 0; k < nr[2]; ++k) {
+                cudaMemcpy3DParms p;
+                memset(&p, 0, sizeof(p));
+                p.srcPtr = make_cudaPitchedPtr(const_cast<float*>(host), pitch, n[2], n[1]);
+                p.dstPtr = make_cudaPitchedPtr(dev, pitch, n[2], n[1]);
+                p.srcPos = make_cudaPos(sizeof(float) * (size_t)r0[2][k], r0[1][j], r0[0][i]);
+                p.dstPos = p.srcPos;
+                p.extent = make_cudaExtent(sizeof(float) * (size_t)rw[2][k], rw[1][j], rw[0][i]);
+                p.kind = cudaMemcpyHostToDevice;
+                const cudaError_t e = cudaMemcpy3DAsync(&p, s);
+                if (e != cudaSuccess) return from_cuda(e);
+                total += (int64_t)sizeof(float) * rw[2][k] * rw[1][j] * rw[0][i];
+            }
+    if (bytes) *bytes = total;
+    return RR_OK;
+}
+
 rr_status rr_set_kernels(rr_ctx* ctx, const double k[6])
 {
     if (!ctx || !k) return RR_ERR_ARG;

@@ -71,6 +71,22 @@ def test_argument_validation_is_host_side(rr):
     assert lib.rr_footprint_bbox(C.byref(good), C.byref(g), 1.0, 2.0, C.cast(out, C.c_void_p)) == rr.RR_ERR_ARG
 
 
+def test_upload_box_validation_is_host_side(rr):
+    lib = rr.load()
+    g = rr.grid_desc(synth.Grid((8, 8, 8), 16.0))
+    gbad = rr.grid_desc(synth.Grid((8, 8, 5000), 16.0))
+    nb = C.c_int64(-1)
+    p = C.c_void_p(16)
+    assert lib.rr_upload_box(None, p, p, None, C.byref(nb), None) == rr.RR_ERR_ARG
+    assert lib.rr_upload_box(C.byref(gbad), p, p, None, C.byref(nb), None) == rr.RR_ERR_ARG
+    assert lib.rr_upload_box(C.byref(g), None, p, None, C.byref(nb), None) == rr.RR_ERR_ARG
+    assert lib.rr_upload_box(C.byref(g), p, None, None, C.byref(nb), None) == rr.RR_ERR_ARG
+    for box in ((0, 9, 0, 8, 0, 8), (0, 8, 3, 3, 0, 8), (0, 8, 0, 8, 5, 4), (-(1 << 21), -(1 << 21) + 2, 0, 8, 0, 8)):
+        bb = (C.c_int32 * 6)(*box)
+        assert lib.rr_upload_box(C.byref(g), p, p, C.cast(bb, C.c_void_p), C.byref(nb), None) == rr.RR_ERR_ARG, box
+    assert nb.value == -1   # nothing reported for a refused call
+
+
 @pytest.mark.parametrize("fov,obs,chi_a,chi_b", [
     (10.0, (32.0, 32.0, 0.0), 60.0, 40.0),
     (40.0, (2.0, 60.0, 0.0), 30.0, 0.0),
