@@ -119,6 +119,12 @@ class ClockSampler:
             if self.dev is not None:
                 cmd += ["-i", str(self.dev)]
             self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+            # the timed region starts once the sampler is running (its first line written)
+            t_end = time.perf_counter() + 3.0
+            while time.perf_counter() < t_end and self.proc.poll() is None:
+                if os.fstat(self.file.fileno()).st_size > 0:
+                    break
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -187,8 +193,8 @@ def run_reference(args, w, steps):
     for it in range(args.warmup):
         rids = rng.choice(w.bundle.nrays, sample, replace=False)
         _, dt = _oracle_sample(w.bundle, w.grid, H, d, steps, rids, threads)
-        if it == 0 and dt > 0:   # size the sample for ~6 s per step
-            sample = int(min(w.bundle.nrays, max(64, sample * 6.0 / dt)))
+        if it == 0 and dt > 0:   # size the sample for ~3 s per step
+            sample = int(min(w.bundle.nrays, max(64, sample * 3.0 / dt)))
     times, segs = [], 0
     for _ in range(args.steps):
         rids = rng.choice(w.bundle.nrays, sample, replace=False)
@@ -864,7 +870,7 @@ def _generic_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, kappa_pa
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="prod_512")
