@@ -187,13 +187,19 @@ class Tracer:
         the records made from it two steps earlier are done. Only the cells a
         step reads are moved, so the maps equal those of the same steps on the
         whole field. delta_host / delta_bufs: the same for a given density
-        contrast. Returns the bytes copied."""
+        contrast. The host arrays must stay unchanged until ``stream`` has
+        passed the last step. Returns the bytes copied."""
         import torch
         if self.generic:
             raise ValueError("trace_streamed: the generic form takes its fields through scalars()")
         g = grid_desc(grid)
         if bboxes is None:
             bboxes = [self.footprint(grid, st.chi_a, st.chi_b) for st in steps]
+        # the buffers may still be read by work already queued on `stream`
+        # (a previous pass): the first copies wait for it
+        queued = torch.cuda.Event()
+        queued.record(stream)
+        copy_stream.wait_event(queued)
         released = [None, None]
         total = 0
         for i, st in enumerate(steps):

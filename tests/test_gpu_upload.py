@@ -168,3 +168,30 @@ def test_streamed_pass_with_delta(rrpkg):
     finally:
         tr.close()
     assert torch.equal(k1, k2) and torch.equal(kb1, kb2)
+
+
+def test_back_to_back_streamed_passes_share_buffers(rrpkg):
+    """Two passes of two fields through the same two device buffers, queued
+    without a host synchronisation between them: the second pass's first
+    copies wait for the first pass's steps, so each map is its field's."""
+    import torch
+    rrp = rrpkg
+    grid, bundle, steps, phi_a = _pass_case(1)
+    phi_b = (synth.grf_phi(64, 128.0, seed=12) * 0.5).astype(np.float32)
+    ref = [rrp.trace_kappa(torch.from_numpy(p).cuda(), grid, bundle, steps)[:2] for p in (phi_a, phi_b)]
+    trs = [rrp.Tracer(bundle), rrp.Tracer(bundle)]
+    try:
+        stream, copy_stream = torch.cuda.Stream(), torch.cuda.Stream()
+        bufs = [torch.full(phi_a.shape, float("nan"), dtype=torch.float32, device="cuda") for _ in range(2)]
+        rec = trs[0].record_buffer(grid)
+        hosts = [torch.from_numpy(p).pin_memory() for p in (phi_a, phi_b)]
+        for tr, host in zip(trs, hosts):
+            tr.reset(stream)
+            tr.trace_streamed(grid, host, steps, rec, bufs, stream, copy_stream)
+        maps = [tr.finalize(stream=stream) for tr in trs]
+        torch.cuda.synchronize()
+    finally:
+        for tr in trs:
+            tr.close()
+    for (k1, kb1), (k2, kb2) in zip(ref, maps):
+        assert torch.equal(k1, k2) and torch.equal(kb1, kb2)
