@@ -66,8 +66,25 @@ __device__ __forceinline__ float4 sum_error(float4 o, float4 x)
 // adds its own. The 32-term warp sums are plain FP32 (a relative error of a
 // few ulp per flush); the compensation guards the long chains of additions
 // into one record, where thousands of contributions of both signs meet.
-__device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long idx, float S, float gk, float gb,
-                                           const float* w)
+// A flush whose compensation is still to be made: the atomic add of v into
+// *p returned old; the rounding error of old + v goes into p[8].
+struct PendingAdd {
+    float* p;
+    float old, v;
+};
+
+__device__ __forceinline__ void finish_add(const PendingAdd& d)
+{
+    float sum, err;
+    two_sum(d.old, d.v, sum, err);
+    atomicAdd(d.p + 8, err);
+}
+
+// First half of a flush: returns true when it left a compensation pending in
+// `pend` (the warp-summed path), so that several flushes' atomics can be in
+// flight before their returned values are needed.
+__device__ __forceinline__ bool flush_grad_begin(float4* __restrict__ grad, long long idx, float S, float gk,
+                                                 float gb, const float* w, PendingAdd& pend)
 {
     const float a = gk * S;
     const unsigned active = __activemask();
@@ -96,15 +113,15 @@ __device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long 
         v += __shfl_xor_sync(FULL, v, 1);
         const int ch = lane >> 2;
         if ((lane & 3) == 0 && ch < 7 && v != 0.f) {
-            float* p = reinterpret_cast<float*>(grad + 4 * idx);
-            const float old = atomicAdd(p + ch, v);
-            float sum, err;
-            two_sum(old, v, sum, err);
-            atomicAdd(p + 8 + ch, err);
+            float* p = reinterpret_cast<float*>(grad + 4 * idx) + ch;
+            pend.p = p;
+            pend.v = v;
+            pend.old = atomicAdd(p, v);
+            return true;
         }
-        return;
+        return false;
     }
-    if (S == 0.f) return;
+    if (S == 0.f) return false;
     const float4 x0 = make_float4(a * w[0], a * w[1], a * w[2], a * w[3]);
     const float4 x1 = make_float4(a * w[4], a * w[5], gb * S, 0.f);
     float4* p = grad + 4 * idx;
@@ -112,6 +129,14 @@ __device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long 
     const float4 o1 = atomicAdd(p + 1, x1);
     atomicAdd(p + 2, sum_error(o0, x0));
     atomicAdd(p + 3, sum_error(o1, x1));
+    return false;
+}
+
+__device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long idx, float S, float gk, float gb,
+                                           const float* w)
+{
+    PendingAdd d;
+    if (flush_grad_begin(grad, idx, S, gk, gb, w, d)) finish_add(d);
 }
 
 // Adjoint of one step: replays the walk and, for every point the ray's
@@ -204,7 +229,10 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
                 ne = nn[a];
             }
         if (INTERP == RR_TRILINEAR) {
-            // the 4 corners on the entry face along e leave the ray's cell
+            // the 4 corners on the entry face along e leave the ray's cell;
+            // their four atomics are issued before any returned value is used
+            PendingAdd pend[4];
+            bool pending[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int pb = r & 1, qb2 = r >> 1;
@@ -216,8 +244,11 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
 #pragma unroll
                 for (int mm = 0; mm < 8; ++mm)
                     if (mm == m) Sm = S[mm];
-                flush_grad(B.grad, gx * sx + gy * sy + gz, Sm, gk, gb, w);
+                pending[r] = flush_grad_begin(B.grad, gx * sx + gy * sy + gz, Sm, gk, gb, w, pend[r]);
             }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (pending[r]) finish_add(pend[r]);
             if (e == 0) {
                 S[0] = S[1]; S[2] = S[3]; S[4] = S[5]; S[6] = S[7];
                 S[1] = 0.f; S[3] = 0.f; S[5] = 0.f; S[7] = 0.f;
