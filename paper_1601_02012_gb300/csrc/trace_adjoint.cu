@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
     R sig = 0;
     R T[3] = {W.T0[0], W.T0[1], W.T0[2]};
     int iter = 0;
+    PendingAdd pend[4];
+    bool pending[4] = {false, false, false, false};
     while (true) {
         R tend = T[0];
         int e = 0;
@@ -231,8 +233,11 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
         if (INTERP == RR_TRILINEAR) {
             // the 4 corners on the entry face along e leave the ray's cell;
             // their four atomics are issued before any returned value is used
-            PendingAdd pend[4];
-            bool pending[4];
+            // the previous crossing's compensations, whose atomics have had this
+            // segment's arithmetic to return
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (pending[r]) finish_add(pend[r]);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int pb = r & 1, qb2 = r >> 1;
@@ -246,9 +251,6 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
                     if (mm == m) Sm = S[mm];
                 pending[r] = flush_grad_begin(B.grad, gx * sx + gy * sy + gz, Sm, gk, gb, w, pend[r]);
             }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (pending[r]) finish_add(pend[r]);
             if (e == 0) {
                 S[0] = S[1]; S[2] = S[3]; S[4] = S[5]; S[6] = S[7];
                 S[1] = 0.f; S[3] = 0.f; S[5] = 0.f; S[7] = 0.f;
@@ -280,6 +282,9 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
             break;
         }
     }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (pending[r]) finish_add(pend[r]);
     // flush everything still pending
     if (INTERP == RR_TRILINEAR) {
 #pragma unroll
