@@ -30,10 +30,17 @@ namespace {
 
 // Leaf containing the finest cell q (each in [0, n 2^lmax)): its id, or -1 if
 // the links are inconsistent; its level in lev.
-__device__ __forceinline__ int amr_locate(const AmrDevice& M, const int q[3], int& lev)
+__device__ __forceinline__ int coarse_link(const AmrDevice& M, const int q[3])
 {
     const int L = M.lmax;
-    int v = __ldg(M.link + ((q[0] >> L) * M.n + (q[1] >> L)) * M.n + (q[2] >> L));
+    return __ldg(M.link + ((q[0] >> L) * M.n + (q[1] >> L)) * M.n + (q[2] >> L));
+}
+
+// The leaf holding finest cell q, descending from its coarse cell's link
+// value v (coarse_link).
+__device__ __forceinline__ int amr_locate(const AmrDevice& M, const int q[3], int v, int& lev)
+{
+    const int L = M.lmax;
     int l = 0;
     while (v < 0 && l < L) {
         ++l;
@@ -50,6 +57,11 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     constexpr bool SH = FORM == kFormShear;
     constexpr bool MA = FORM == kFormMethodA;
     constexpr bool GEN = FORM == kFormGeneric;
+    // AHEAD: advance to the next cell before integrating the current one and
+    // load its coarse link then, so that the load overlaps the segment's
+    // arithmetic (faster for the shear and Method A walks, whose segments
+    // carry more arithmetic; slower for the default and generic ones)
+    constexpr bool AHEAD = SH || MA;
     const long long rid = (long long)iy * A.nx + ix;
     const int NF = A.n0;   // finest cells per side
     RayRange rg;
@@ -91,9 +103,10 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
         const int flip = (W.sgn[0] < 0 ? 1 : 0) | (W.sgn[1] < 0 ? 2 : 0) | (W.sgn[2] < 0 ? 4 : 0);
         float sig = 0.f;                        // path from the sub-step start to the segment entry
         int iter = 0;
+        int link0 = AHEAD ? coarse_link(M, q) : 0;   // AHEAD: the current cell's coarse link
         while (true) {
             int lev;
-            const int leaf = amr_locate(M, q, lev);
+            const int leaf = amr_locate(M, q, AHEAD ? link0 : coarse_link(M, q), lev);
             if (leaf < 0) {
                 overflow = true;
                 break;
@@ -134,6 +147,39 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                             const int nq = q[a] + W.sgn[a] * m[a];
                             ends = nq < 0 || nq >= NF;
                         }
+                }
+            }
+
+            // leave through axis e; the other axes advance to their first
+            // crossing at or after the exit point (never past their own exit).
+            // Returns whether the exit leaves the box.
+            auto advance = [&]() -> bool {
+                bool out = false;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (a == e) {
+                        K[a] += mf[a];
+                        const int nq = q[a] + W.sgn[a] * m[a];
+                        out = nq < 0 || nq >= NF;
+                        q[a] = wrap_once(nq, NF);
+                    } else if (W.v[a] > 0.f) {
+                        // counters are exact integers in float: the first crossing at or after tend
+                        const float kmax = K[a] + (mf[a] - 1.f);
+                        float k = fminf(fmaxf(ceilf((tend - W.T0[a]) * W.v[a]), K[a]), kmax);
+                        while (k > K[a] && fmaf(k - 1.f, W.td[a], W.T0[a]) >= tend) k -= 1.f;
+                        while (k < kmax && fmaf(k, W.td[a], W.T0[a]) < tend) k += 1.f;
+                        q[a] = wrap_once(q[a] + W.sgn[a] * f2i_exact(k - K[a]), NF);
+                        K[a] = k;
+                    }
+                }
+                return out;
+            };
+            bool outside = false;
+            if constexpr (AHEAD) {
+                // nothing below reads q or K
+                if (!last) {
+                    outside = advance();
+                    link0 = coarse_link(M, q);
                 }
             }
 
@@ -233,27 +279,7 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
             }
             sig = tend;
             if (last) break;
-
-            // leave through axis e; the other axes advance to their first
-            // crossing at or after the exit point (never past their own exit)
-            bool outside = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (a == e) {
-                    K[a] += mf[a];
-                    const int nq = q[a] + W.sgn[a] * m[a];
-                    outside = nq < 0 || nq >= NF;
-                    q[a] = wrap_once(nq, NF);
-                } else if (W.v[a] > 0.f) {
-                    // counters are exact integers in float: the first crossing at or after tend
-                    const float kmax = K[a] + (mf[a] - 1.f);
-                    float k = fminf(fmaxf(ceilf((tend - W.T0[a]) * W.v[a]), K[a]), kmax);
-                    while (k > K[a] && fmaf(k - 1.f, W.td[a], W.T0[a]) >= tend) k -= 1.f;
-                    while (k < kmax && fmaf(k, W.td[a], W.T0[a]) < tend) k += 1.f;
-                    q[a] = wrap_once(q[a] + W.sgn[a] * f2i_exact(k - K[a]), NF);
-                    K[a] = k;
-                }
-            }
+            if constexpr (!AHEAD) outside = advance();
             if (!A.periodic && outside) break;
             if (++iter > W.max_iter) {
                 overflow = true;
