@@ -40,7 +40,10 @@ typedef enum {
     RR_ERR_STEP_LIMIT = -4, /* a ray exceeded its per-step iteration cap */
     RR_ERR_STATE = -5,      /* calls out of order (e.g. a gap between steps) */
     RR_ERR_NONFINITE = -6,  /* a per-ray sum became NaN or infinite */
-    RR_ERR_CAPACITY = -7    /* more rays than rr_trace_step_noalloc's fixed scratch holds */
+    RR_ERR_CAPACITY = -7,   /* more rays than rr_trace_step_noalloc's fixed scratch holds */
+    RR_ERR_RANGE = -8       /* internal check: a ray of a step traced with flat (no-wrap) record
+                               addressing would have left the index range it covers; that ray read
+                               nothing and its step contributes nothing */
 } rr_status;
 
 /* rr_bundle_desc.interp: how Q varies inside a cell (Sec. 2.6). */
@@ -131,6 +134,22 @@ const char* rr_status_string(rr_status s);
  * fit. Initialising the ray directions (Eq. txty, raypos) runs on the device.
  */
 rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out);
+
+/*
+ * A context for the rows [y0, y1) of `bundle` only: the rays of pixels
+ * (i_x, i_y) with y0 <= i_y < y1, directions from Eq. (txty) with the whole
+ * bundle's N_y, ids counted from row y0 (Eq. rayid restricted to the band).
+ * Rays are independent (Secs. 2.3-2.5: the paper exchanges rays between
+ * processes only because it splits the volume), so a bundle traced on several
+ * GPUs gives each one a band of rows: every call below then works on the
+ * band's (y1 - y0) x nx rays, rr_finalize writes rows y0 .. y1 - 1 of the
+ * whole map, and the whole map is the bands' maps concatenated in row order;
+ * the adjoint of the whole bundle is the sum over the bands of their
+ * rr_trace_backward results, each given its own rows of dL/dkappa. Footprint
+ * boxes (rr_footprint_bbox) of the whole bundle hold those of every band.
+ * Synchronous, as rr_create. RR_ERR_ARG unless 0 <= y0 < y1 <= ny.
+ */
+rr_status rr_create_band(const rr_bundle_desc* bundle, int32_t y0, int32_t y1, rr_ctx** out);
 
 /* Free the context and its device state (synchronises the device first). */
 rr_status rr_destroy(rr_ctx* ctx);
@@ -267,8 +286,8 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
  * Write the maps in rayid order (x fastest): kappa[ny*nx] and, if not NULL,
  * kappa_born[ny*nx], both device FP64. Also totals the per-ray segment
  * counters. Synchronises `stream` and returns the context's error word:
- * RR_ERR_STEP_LIMIT or RR_ERR_NONFINITE if a device-side check failed during
- * any step since create/reset, else RR_OK.
+ * RR_ERR_STEP_LIMIT, RR_ERR_NONFINITE or RR_ERR_RANGE if a device-side check
+ * failed during any step since create/reset, else RR_OK.
  */
 rr_status rr_finalize(rr_ctx* ctx, double* kappa, double* kappa_born, void* stream);
 
@@ -566,8 +585,10 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* mesh, const float* leaf_rec, do
  * It traces every ray of `bundle` from chi_a down to chi_b exactly as
  * rr_trace_step does (same kernels, same arguments and meaning) and writes
  * kappa and (if not NULL) kappa_born, device FP64 [ny*nx] in rayid order,
- * holding scale * the step's integrals; then it synchronises `stream` and
- * returns the device error word as rr_finalize does.
+ * holding scale * the step's integrals. Every call then copies the device
+ * error word to the host and waits for `stream` to finish
+ * (cudaStreamSynchronize) before it returns, so it blocks the calling thread
+ * until the step's work is done, and returns that word as rr_finalize does.
  *
  * Scratch: instead of memory the library allocates, the per-ray directions,
  * accumulators, segment counters and error word live in one fixed array in
@@ -580,13 +601,29 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* mesh, const float* leaf_rec, do
  * into at the start; calls whose work overlaps on the GPU (two streams, or
  * two host threads, at once) race on it and must be serialised by the caller.
  * Returns RR_ERR_CAPACITY if nx * ny > RR_NOALLOC_MAX_RAYS, RR_ERR_ARG for
- * the argument errors rr_trace_step rejects (no step-order check: each call
- * is independent).
+ * the argument errors rr_create and rr_trace_step reject (a field of view of
+ * pi or more, non-finite observer, distances, scale or grid sizes, ...; no
+ * step-order check: each call is independent) and for flags other than
+ * RR_PERIODIC and RR_FP64_DDA.
  */
 #define RR_NOALLOC_MAX_RAYS 65536
 rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const rr_grid_desc* grid, const float* rec,
                                 double chi_a, double chi_b, double scale, double a_step, double* kappa,
                                 double* kappa_born, void* stream);
+
+/*
+ * Measurement helper (the paper has no counterpart): launches an FP32 FMA
+ * throughput kernel on `stream`, `blocks` x `threads` threads, each running
+ * independent fused multiply-add chains for `iters` iterations (packed != 0:
+ * the packed two-lane FFMA2 form). *fmas receives the number of FMAs the
+ * launch performs (lane operations; an FFMA2 counts two). Time the launch
+ * with events on `stream`: FMAs / time is the FP32 FMA rate that the cell
+ * walk's arithmetic roofline is reported against. `out` (device, >= blocks
+ * floats) is never written for these arguments; it keeps the chains live.
+ * Asynchronous. RR_ERR_ARG for bad sizes or null pointers.
+ */
+rr_status rr_fp32_peak(int32_t packed, int32_t blocks, int32_t threads, int32_t iters, float* out,
+                       int64_t* fmas, void* stream);
 
 #ifdef __cplusplus
 }

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 from . import _rr
 from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, bundle_desc, grid_desc,
-                  rr_create, rr_destroy, rr_finalize, rr_footprint_bbox, rr_reset, rr_segment_count,
+                  rr_create, rr_create_band, rr_destroy, rr_finalize, rr_footprint_bbox, rr_reset, rr_segment_count,
                   rr_status_string, rr_step_count, rr_sync_status, rr_tidal_tensor, rr_tidal_tensor_adjoint,
                   rr_trace_backward, rr_trace_step, rr_trace_step_adjoint)
 
@@ -78,14 +78,16 @@ class Tracer:
     """
 
     def __init__(self, bundle, fp64_dda: bool = False, plain_sums: bool = False, moments: bool = False,
-                 shear: bool = False, method_a: bool = False, generic: bool = False):
+                 shear: bool = False, method_a: bool = False, generic: bool = False, rows=None):
         _rr.load()
         self.bundle = bundle
         self.method_a = bool(method_a)
         self.generic = bool(generic)
         self.desc = bundle_desc(bundle, fp64_dda=fp64_dda, plain_sums=plain_sums, moments=moments, shear=shear,
                                 method_a=method_a, generic=generic)
-        self.ctx = rr_create(self.desc)
+        # rows (y0, y1): this tracer's rays are that band of the bundle (rr_create_band)
+        self.rows = (0, int(bundle.ny)) if rows is None else (int(rows[0]), int(rows[1]))
+        self.ctx = rr_create(self.desc) if rows is None else rr_create_band(self.desc, *self.rows)
         self.where = RR_AT_VERTICES if int(self.desc.interp) == RR_TRILINEAR else RR_AT_CENTRES
 
     def close(self):
@@ -141,7 +143,7 @@ class Tracer:
     def finalize(self, kappa=None, kborn=None, stream=None):
         """FP64 maps [ny, nx] on the device (rayid order, x fastest)."""
         import torch
-        ny, nx = int(self.desc.ny), int(self.desc.nx)
+        ny, nx = self.rows[1] - self.rows[0], int(self.desc.nx)
         if kappa is None:
             kappa = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
         if kborn is None:
@@ -156,7 +158,7 @@ class Tracer:
         """Snapshot of the moments so far: FP64 [4, ny, nx] on the device, rows
         A_kappa, B_kappa, A_born, B_born (contexts created with moments=True)."""
         import torch
-        ny, nx = int(self.desc.ny), int(self.desc.nx)
+        ny, nx = self.rows[1] - self.rows[0], int(self.desc.nx)
         if out is None:
             out = torch.empty((4, ny, nx), dtype=torch.float64, device="cuda")
         _rr.rr_moments(self.ctx, out, stream)
@@ -166,7 +168,7 @@ class Tracer:
         """The shear maps so far: FP64 (gamma1, gamma2), each [ny, nx] on the
         device (contexts created with shear=True)."""
         import torch
-        ny, nx = int(self.desc.ny), int(self.desc.nx)
+        ny, nx = self.rows[1] - self.rows[0], int(self.desc.nx)
         if gamma1 is None:
             gamma1 = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
         if gamma2 is None:

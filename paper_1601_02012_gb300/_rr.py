@@ -26,6 +26,7 @@ RR_ERR_STEP_LIMIT = -4
 RR_ERR_STATE = -5
 RR_ERR_NONFINITE = -6
 RR_ERR_CAPACITY = -7
+RR_ERR_RANGE = -8
 RR_NOALLOC_MAX_RAYS = 65536
 
 RR_NGP = 0
@@ -74,6 +75,7 @@ def load() -> C.CDLL:
         sig = {
             "rr_status_string": ([C.c_int], C.c_char_p),
             "rr_create": ([P, C.POINTER(C.c_void_p)], C.c_int),
+            "rr_create_band": ([P, I32, I32, C.POINTER(C.c_void_p)], C.c_int),
             "rr_destroy": ([P], C.c_int),
             "rr_reset": ([P, P], C.c_int),
             "rr_tidal_tensor": ([P, P, P, P, I32, P, P], C.c_int),
@@ -116,6 +118,7 @@ def load() -> C.CDLL:
             "rr_amr_gradient": ([P, P, I32, P, P, P, P], C.c_int),
             "rr_amr_scalars": ([P, P, P, D, P, P, D, I32, P, P, P, P], C.c_int),
             "rr_amr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
+            "rr_fp32_peak": ([I32, I32, I32, I32, P, C.POINTER(C.c_int64), P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -196,6 +199,12 @@ def grid_desc(g) -> rr_grid_desc:
 def rr_create(bundle: rr_bundle_desc) -> C.c_void_p:
     h = C.c_void_p()
     _check(load().rr_create(C.byref(bundle), C.byref(h)), "rr_create")
+    return h
+
+
+def rr_create_band(bundle: rr_bundle_desc, y0: int, y1: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().rr_create_band(C.byref(bundle), int(y0), int(y1), C.byref(h)), "rr_create_band")
     return h
 
 
@@ -477,3 +486,13 @@ def rr_amr_trace_step(ctx, mesh, leaf_rec, chi_a: float, chi_b: float, scale: fl
                       stream=None) -> None:
     _check(load().rr_amr_trace_step(ctx, mesh, _ptr(leaf_rec), float(chi_a), float(chi_b), float(scale),
                                     float(a_step), _stream(stream)), "rr_amr_trace_step")
+
+
+# ---- measurement -----------------------------------------------------------
+
+def rr_fp32_peak(packed: bool, blocks: int, threads: int, iters: int, out, stream=None) -> int:
+    """Launch the FP32 FMA throughput kernel; returns the FMA count of the launch."""
+    n = C.c_int64()
+    _check(load().rr_fp32_peak(int(bool(packed)), int(blocks), int(threads), int(iters), _ptr(out), C.byref(n),
+                               _stream(stream)), "rr_fp32_peak")
+    return int(n.value)

@@ -16,6 +16,43 @@ bool is_finite(double x) { return std::isfinite(x); }
 
 bool is_aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+rr_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return RR_OK;
+    if (e == cudaErrorMemoryAllocation) return RR_ERR_OOM;
+    return RR_ERR_CUDA;
+}
+
+rr_status status_from_word(uint32_t w)
+{
+    if (w & kErrStepLimit) return RR_ERR_STEP_LIMIT;
+    if (w & kErrNonFinite) return RR_ERR_NONFINITE;
+    if (w & kErrRange) return RR_ERR_RANGE;
+    return RR_OK;
+}
+
+void free_state(RayState& s)
+{
+    cudaFree(s.dir);
+    cudaFree(s.dirh);
+    cudaFree(s.dirl);
+    cudaFree(s.kacc);
+    cudaFree(s.bacc);
+    cudaFree(s.kmom);
+    cudaFree(s.bmom);
+    cudaFree(s.g1acc);
+    cudaFree(s.g2acc);
+    cudaFree(s.nseg);
+    cudaFree(s.err);
+    cudaFree(s.total);
+    s = RayState{};
+}
+
+
+}  // namespace
+
+namespace rr {
+
 rr_status check_bundle(const rr_bundle_desc* b)
 {
     if (!b) return RR_ERR_ARG;
@@ -51,49 +88,13 @@ rr_status check_grid(const rr_grid_desc* g)
     return RR_OK;
 }
 
-rr_status from_cuda(cudaError_t e)
+// The step geometry and a bundle's per-ray state pointers, as the kernels take them.
+TraceArgs make_trace_args(const rr_bundle_desc& b, const RayState& st, const rr_grid_desc* grid, const float* rec,
+                          double chi_a, double chi_b, double scale, double a_step, const double* obs,
+                          const double* kq)
 {
-    if (e == cudaSuccess) return RR_OK;
-    if (e == cudaErrorMemoryAllocation) return RR_ERR_OOM;
-    return RR_ERR_CUDA;
-}
-
-rr_status status_from_word(uint32_t w)
-{
-    if (w & kErrStepLimit) return RR_ERR_STEP_LIMIT;
-    if (w & kErrNonFinite) return RR_ERR_NONFINITE;
-    return RR_OK;
-}
-
-void free_state(RayState& s)
-{
-    cudaFree(s.dir);
-    cudaFree(s.dirh);
-    cudaFree(s.dirl);
-    cudaFree(s.kacc);
-    cudaFree(s.bacc);
-    cudaFree(s.kmom);
-    cudaFree(s.bmom);
-    cudaFree(s.g1acc);
-    cudaFree(s.g2acc);
-    cudaFree(s.nseg);
-    cudaFree(s.err);
-    cudaFree(s.total);
-    s = RayState{};
-}
-
-
-}  // namespace
-
-namespace rr {
-
-// The step geometry and the context's state pointers, as the kernels take them.
-TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
-                          double scale, double a_step, const double* obs)
-{
-    const rr_bundle_desc& b = ctx->bundle;
     if (!obs) obs = b.obs;
-    TraceArgs a;
+    TraceArgs a{};
     a.rec = reinterpret_cast<const float4*>(rec);
     a.n0 = grid->n[0]; a.n1 = grid->n[1]; a.n2 = grid->n[2];
     a.h = grid->box / grid->n[0];
@@ -112,17 +113,17 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     a.inv_chi_s_f = (float)(1.0 / b.chi_s);
     a.sub_len = (float)(32.0 * a.h);
     a.periodic = (b.flags & RR_PERIODIC) ? 1 : 0;
-    a.dir = ctx->st.dir;
-    a.dirh = ctx->st.dirh;
-    a.dirl = ctx->st.dirl;
-    a.kacc = ctx->st.kacc;
-    a.bacc = ctx->st.bacc;
-    a.kmom = ctx->st.kmom;
-    a.bmom = ctx->st.bmom;
-    a.g1acc = ctx->st.g1acc;
-    a.g2acc = ctx->st.g2acc;
-    a.nseg = ctx->st.nseg;
-    a.err = ctx->st.err;
+    a.dir = st.dir;
+    a.dirh = st.dirh;
+    a.dirl = st.dirl;
+    a.kacc = st.kacc;
+    a.bacc = st.bacc;
+    a.kmom = st.kmom;
+    a.bmom = st.bmom;
+    a.g1acc = st.g1acc;
+    a.g2acc = st.g2acc;
+    a.nseg = st.nseg;
+    a.err = st.err;
     split_ff(scale, a.sch, a.scl);
     if (b.flags & RR_GENERIC) {
         // both channels are plain integrals times the step's scale
@@ -131,8 +132,18 @@ TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* re
     } else {
         split_ff(scale * 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step, a.bsh, a.bsl);
     }
-    for (int i = 0; i < 6; ++i) a.kq[i] = (float)ctx->kq[i];
+    // the generic form's kernels (default: the lensing kernel g = chi - chi^2 / chi_s on both channels)
+    const double kg[6] = {0.0, 1.0, -1.0 / b.chi_s, 0.0, 1.0, -1.0 / b.chi_s};
+    if (!kq) kq = kg;
+    for (int i = 0; i < 6; ++i) a.kq[i] = (float)kq[i];
     return a;
+}
+
+// The step geometry and the context's state pointers, as the kernels take them.
+TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
+                          double scale, double a_step, const double* obs)
+{
+    return make_trace_args(ctx->bundle, ctx->st, grid, rec, chi_a, chi_b, scale, a_step, obs, ctx->kq);
 }
 
 StepRecord make_step_record(const rr_ctx* ctx, const rr_grid_desc* grid, double chi_a, double chi_b, double scale,
@@ -165,6 +176,45 @@ rr_status status_of_cuda(cudaError_t e) { return from_cuda(e); }
 
 }  // namespace rr
 
+namespace rr {
+
+void footprint_box(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a,
+                   double chi_b, long long i0[3], long long i1[3])
+{
+    // Bounds of the direction over the bundle: n_x = theta_x sinc(theta) lies in
+    // [-sin(U_x/2), sin(U_x/2)] because sinc decreases on [0, pi); n_z = cos(theta)
+    // lies in [cos(theta_max), 1].
+    const double hx = b.nx > 1 ? 0.5 * b.fov_x : 0.0, hy = b.ny > 1 ? 0.5 * b.fov_y : 0.0;
+    const double thmax = sqrt(hx * hx + hy * hy);
+    const double nlo[3] = {-sin(hx), -sin(hy), cos(thmax)};
+    const double nhi[3] = {sin(hx), sin(hy), 1.0};
+    const double h = g.box / g.n[0];
+    for (int a = 0; a < 3; ++a) {
+        const double c1 = chi_a * nlo[a], c2 = chi_b * nlo[a], c3 = chi_a * nhi[a], c4 = chi_b * nhi[a];
+        const double lo = obs[a] + std::min(std::min(c1, c2), std::min(c3, c4));
+        const double hi = obs[a] + std::max(std::max(c1, c2), std::max(c3, c4));
+        const double f0 = floor(lo / h), f1 = floor(hi / h);
+        // (saturated far outside any grid; the callers compare against [0, n])
+        i0[a] = (f0 > -1e15 ? (long long)f0 : -1000000000000000LL) - 1;
+        i1[a] = (f1 < 1e15 ? (long long)f1 : 1000000000000000LL) + 3;
+    }
+}
+
+bool flat_ok(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a, double chi_b)
+{
+    if (!(b.flags & RR_PERIODIC) || b.interp != RR_TRILINEAR) return false;
+    if ((long long)g.n[0] * g.n[1] * g.n[2] >= (1LL << 31)) return false;
+    long long i0[3], i1[3];
+    footprint_box(b, obs, g, chi_a, chi_b, i0, i1);
+    // cells i0 + 1 .. i1 - 3 are reachable; with one more cell of margin on
+    // each side, every vertex plane the walk reads lies in [0, n - 1]
+    for (int a = 0; a < 3; ++a)
+        if (i0[a] < 1 || i1[a] > g.n[a] - 1) return false;
+    return true;
+}
+
+}  // namespace rr
+
 extern "C" {
 
 const char* rr_status_string(rr_status s)
@@ -178,19 +228,24 @@ const char* rr_status_string(rr_status s)
     case RR_ERR_STATE: return "RR_ERR_STATE: calls out of order";
     case RR_ERR_NONFINITE: return "RR_ERR_NONFINITE: a per-ray sum is not finite";
     case RR_ERR_CAPACITY: return "RR_ERR_CAPACITY: more rays than the fixed no-allocation scratch holds";
+    case RR_ERR_RANGE: return "RR_ERR_RANGE: a ray left the index range its step's record addressing covers";
     }
     return "unknown rr_status";
 }
 
-rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
+static rr_status create_context(const rr_bundle_desc* bundle, int32_t y0, int32_t y1, rr_ctx** out)
 {
     if (!out) return RR_ERR_ARG;
     *out = nullptr;
     rr_status st = check_bundle(bundle);
     if (st != RR_OK) return st;
+    if (y0 < 0 || y1 > bundle->ny || !(y0 < y1)) return RR_ERR_ARG;
     rr_ctx* ctx = new (std::nothrow) rr_ctx();
     if (!ctx) return RR_ERR_OOM;
     ctx->bundle = *bundle;
+    ctx->bundle.ny = y1 - y0;
+    ctx->row0 = y0;
+    ctx->ny_full = bundle->ny;
     // generic form: both kernels start as the lensing kernel g = chi - chi^2 / chi_s
     for (int c = 0; c < 2; ++c) {
         ctx->kq[3 * c] = 0.0;
@@ -198,7 +253,7 @@ rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
         ctx->kq[3 * c + 2] = -1.0 / bundle->chi_s;
     }
     cudaGetDevice(&ctx->device);
-    const size_t nr = (size_t)bundle->nx * bundle->ny;
+    const size_t nr = (size_t)bundle->nx * (size_t)(y1 - y0);
     cudaError_t e = cudaSuccess;
     RayState& s = ctx->st;
     if (e == cudaSuccess) e = cudaMalloc(&s.dir, 3 * nr * sizeof(double));
@@ -228,7 +283,7 @@ rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
     if (e == cudaSuccess) e = cudaMemset(s.nseg, 0, nr * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.err, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(s.total, 0, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = launch_init_directions(*bundle, s.dir, s.dirh, s.dirl, 0);
+    if (e == cudaSuccess) e = launch_init_directions(*bundle, s.dir, s.dirh, s.dirl, 0, y0, y1 - y0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_state(s);
@@ -239,6 +294,16 @@ rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
     }
     *out = ctx;
     return RR_OK;
+}
+
+rr_status rr_create(const rr_bundle_desc* bundle, rr_ctx** out)
+{
+    return create_context(bundle, 0, bundle ? bundle->ny : 0, out);
+}
+
+rr_status rr_create_band(const rr_bundle_desc* bundle, int32_t y0, int32_t y1, rr_ctx** out)
+{
+    return create_context(bundle, y0, y1, out);
 }
 
 rr_status rr_destroy(rr_ctx* ctx)
@@ -400,19 +465,10 @@ rr_status rr_footprint_bbox(const rr_bundle_desc* b, const rr_grid_desc* g, doub
     st = check_grid(g);
     if (st != RR_OK) return st;
     if (!bbox || !is_finite(chi_a) || !is_finite(chi_b) || !(chi_a >= chi_b) || chi_b < 0) return RR_ERR_ARG;
-    // Bounds of the direction over the bundle: n_x = theta_x sinc(theta) lies in
-    // [-sin(U_x/2), sin(U_x/2)] because sinc decreases on [0, pi); n_z = cos(theta)
-    // lies in [cos(theta_max), 1].
-    const double hx = b->nx > 1 ? 0.5 * b->fov_x : 0.0, hy = b->ny > 1 ? 0.5 * b->fov_y : 0.0;
-    const double thmax = sqrt(hx * hx + hy * hy);
-    const double nlo[3] = {-sin(hx), -sin(hy), cos(thmax)};
-    const double nhi[3] = {sin(hx), sin(hy), 1.0};
-    const double h = g->box / g->n[0];
+    long long b0[3], b1[3];
+    footprint_box(*b, b->obs, *g, chi_a, chi_b, b0, b1);
     for (int a = 0; a < 3; ++a) {
-        const double c1 = chi_a * nlo[a], c2 = chi_b * nlo[a], c3 = chi_a * nhi[a], c4 = chi_b * nhi[a];
-        const double lo = b->obs[a] + std::min(std::min(c1, c2), std::min(c3, c4));
-        const double hi = b->obs[a] + std::max(std::max(c1, c2), std::max(c3, c4));
-        long long i0 = (long long)floor(lo / h) - 1, i1 = (long long)floor(hi / h) + 3;
+        long long i0 = b0[a], i1 = b1[a];
         if (i1 - i0 >= g->n[a] || i0 < -(1 << 20) || i1 > (1 << 20)) {
             i0 = 0;
             i1 = g->n[a];
@@ -436,7 +492,12 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
                      : (b.flags & RR_METHOD_A)     ? kFormMethodA
                      : (b.flags & RR_GENERIC)      ? kFormGeneric
                                                    : kFormKahan;
-    cudaError_t e = launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{}, form);
+    // (the footprint of the whole bundle holds the footprint of a band of it)
+    rr_bundle_desc whole = b;
+    whole.ny = ctx->ny_full;
+    const bool flat = form == kFormKahan && !(b.flags & RR_FP64_DDA) && flat_ok(whole, b.obs, *grid, chi_a, chi_b);
+    cudaError_t e =
+        launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{}, form, flat);
     if (e != cudaSuccess) return from_cuda(e);
     ctx->log.push_back(make_step_record(ctx, grid, chi_a, chi_b, scale, a_step));
     ctx->relocated = false;

@@ -10,6 +10,7 @@
 // point uses a file-scope __device__ array (kNoAllocBytes, a few MB, held by
 // every GPU that loads the library until the process exits) for the per-ray
 // directions, accumulators, segment counters and error word.
+#include <cmath>
 #include <mutex>
 
 #include "rr_internal.h"
@@ -73,16 +74,17 @@ extern "C" rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const r
                                            const float* rec, double chi_a, double chi_b, double scale,
                                            double a_step, double* kappa, double* kappa_born, void* stream)
 {
-    if (!bundle || !grid || !rec || !kappa) return RR_ERR_ARG;
-    if (bundle->nx < 1 || bundle->ny < 1) return RR_ERR_ARG;
-    if ((size_t)bundle->nx * (size_t)bundle->ny > kMaxRays) return RR_ERR_CAPACITY;
-    if (((uintptr_t)rec & 15u) != 0) return RR_ERR_ARG;
-    if (bundle->interp != RR_NGP && bundle->interp != RR_TRILINEAR) return RR_ERR_ARG;
+    // the argument checks of rr_create and rr_trace_step, without the step-order check
+    if (!kappa) return RR_ERR_ARG;
+    rr_status st = check_bundle(bundle);
+    if (st == RR_OK) st = check_grid(grid);
+    if (st != RR_OK) return st;
     if (bundle->flags & ~(RR_PERIODIC | RR_FP64_DDA)) return RR_ERR_ARG;
-    if (!(bundle->chi_s > 0) || !(bundle->fov_x >= 0) || !(bundle->fov_y >= 0)) return RR_ERR_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (grid->n[a] < 2 || grid->n[a] > 4096) return RR_ERR_ARG;
-    if (!(grid->box > 0) || !(grid->omega_m > 0) || !(a_step > 0)) return RR_ERR_ARG;
+    if ((size_t)bundle->nx * (size_t)bundle->ny > kMaxRays) return RR_ERR_CAPACITY;
+    if (!rec || ((uintptr_t)rec & 15u) != 0) return RR_ERR_ARG;
+    if (!std::isfinite(chi_a) || !std::isfinite(chi_b) || !std::isfinite(scale) || !std::isfinite(a_step) ||
+        !(a_step > 0))
+        return RR_ERR_ARG;
     if (!(chi_a > chi_b) || !(chi_b >= 0) || chi_a > bundle->chi_s * (1.0 + 1e-12)) return RR_ERR_ARG;
 
     unsigned char* base = nullptr;
@@ -107,38 +109,16 @@ extern "C" rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const r
     if (e == cudaSuccess) e = launch_init_directions(*bundle, dir, dirh, dirl, s);
     if (e != cudaSuccess) return to_status(e);
 
-    TraceArgs a;
-    a.rec = reinterpret_cast<const float4*>(rec);
-    a.n0 = grid->n[0]; a.n1 = grid->n[1]; a.n2 = grid->n[2];
-    a.h = grid->box / grid->n[0];
-    a.inv_h = 1.0 / a.h;
-    a.inv_hf = (float)a.inv_h;
-    split_ff(a.inv_h, a.ihh, a.ihl);
-    a.nx = bundle->nx; a.ny = bundle->ny;
-    a.obs0 = bundle->obs[0]; a.obs1 = bundle->obs[1]; a.obs2 = bundle->obs[2];
-    for (int i = 0; i < 3; ++i) split_ff(bundle->obs[i], a.oh[i], a.ol[i]);
-    a.chi_s = bundle->chi_s;
-    a.chi_a = chi_a;
-    a.chi_b = chi_b;
-    split_ff(chi_a, a.cah, a.cal);
-    a.Lf = (float)(chi_a - chi_b);
-    a.D0f = (float)(bundle->chi_s - chi_a);
-    a.inv_chi_s_f = (float)(1.0 / bundle->chi_s);
-    a.sub_len = (float)(32.0 * a.h);
-    a.periodic = (bundle->flags & RR_PERIODIC) ? 1 : 0;
-    a.dir = dir;
-    a.dirh = dirh;
-    a.dirl = dirl;
-    a.kacc = kacc;
-    a.bacc = bacc;
-    a.kmom = nullptr;
-    a.bmom = nullptr;
-    a.g1acc = nullptr;
-    a.g2acc = nullptr;
-    a.nseg = nseg;
-    a.err = err;
-    split_ff(scale, a.sch, a.scl);
-    split_ff(scale * 1.5 * grid->omega_m * kH0OverC * kH0OverC / a_step, a.bsh, a.bsl);
+    RayState rs;
+    rs.dir = dir;
+    rs.dirh = dirh;
+    rs.dirl = dirl;
+    rs.kacc = kacc;
+    rs.bacc = bacc;
+    rs.nseg = nseg;
+    rs.err = err;
+    rs.total = total;
+    const TraceArgs a = make_trace_args(*bundle, rs, grid, rec, chi_a, chi_b, scale, a_step, nullptr, nullptr);
     e = launch_trace(a, bundle->interp, (bundle->flags & RR_FP64_DDA) != 0, s);
     if (e == cudaSuccess) e = launch_finalize((int)nr, kacc, bacc, nseg, kappa, kappa_born, total, s);
     if (e != cudaSuccess) return to_status(e);
@@ -149,5 +129,6 @@ extern "C" rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const r
     if (e != cudaSuccess) return to_status(e);
     if (word & kErrStepLimit) return RR_ERR_STEP_LIMIT;
     if (word & kErrNonFinite) return RR_ERR_NONFINITE;
+    if (word & kErrRange) return RR_ERR_RANGE;
     return RR_OK;
 }

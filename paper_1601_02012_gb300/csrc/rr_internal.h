@@ -13,7 +13,9 @@ namespace rr {
 constexpr double kH0OverC = 1.0 / 2997.92458;  // h/Mpc
 
 // Bits of the device error word.
-enum : uint32_t { kErrStepLimit = 1u, kErrNonFinite = 2u };
+// kErrRange: a ray of a step launched with flat (no-wrap) record addressing
+// would have left the index range that addressing covers; it read nothing.
+enum : uint32_t { kErrStepLimit = 1u, kErrNonFinite = 2u, kErrRange = 4u };
 
 // Per-ray state, structure of arrays, indexed by ray id (Eq. rayid).
 struct RayState {
@@ -111,15 +113,22 @@ struct BatchArgs {
 };
 
 // Launchers (one per translation unit).
-cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s);
+// Directions of the rows [row0, row0 + nrows) of bundle b (all rows: nrows < 0).
+cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s,
+                                   int row0 = 0, int nrows = -1);
 // kind 0: tidal records (2 float4 per point); kind 1: gradient records (1 float4)
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s, int kind = 0);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
 // Forms of the FP32 walk's sums.
 enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2, kFormShear = 3, kFormMethodA = 4, kFormGeneric = 5 };
+// Record addressing of the trilinear walk (see trace.cu).
+enum { kAddrIndex = 0, kAddrPlanes = 1, kAddrFlat = 2 };
+// flat: the caller has checked that no ray of the step comes within a cell of
+// the periodic seam and that the grid has fewer than 2^31 points (used by the
+// default FP32 trilinear periodic form only; ignored otherwise).
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
-                         int form = kFormKahan);
+                         int form = kFormKahan, bool flat = false);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
 int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
 dim3 tile_grid(const TileCfg& t, int nx, int ny);
@@ -148,6 +157,23 @@ cudaError_t launch_source_kappa(const double* m_end, const double* m_k, long lon
 // (obs: the observer to trace from; NULL: the context's current one)
 TraceArgs make_trace_args(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec, double chi_a, double chi_b,
                           double scale, double a_step, const double* obs = nullptr);
+// The same for a bundle and per-ray state held outside a context (kq: the
+// generic form's six kernel coefficients, or NULL for the lensing kernel g).
+TraceArgs make_trace_args(const rr_bundle_desc& b, const RayState& st, const rr_grid_desc* grid, const float* rec,
+                          double chi_a, double chi_b, double scale, double a_step, const double* obs,
+                          const double* kq);
+// Index box [i0, i1) per axis of the cells the rays of bundle b (observer
+// obs) can reach between chi_b and chi_a, widened by 1 cell below and 2
+// above, without any wrap or clamp (the values may lie outside [0, n)).
+void footprint_box(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a,
+                   double chi_b, long long i0[3], long long i1[3]);
+// Whether a step of bundle b (observer obs) on grid g can use flat record
+// addressing: periodic trilinear FP32 walk, fewer than 2^31 points, and a
+// footprint at least one cell clear of the periodic seam on every axis.
+bool flat_ok(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a, double chi_b);
+// Argument checks of a bundle and a grid description (RR_OK or RR_ERR_ARG).
+rr_status check_bundle(const rr_bundle_desc* b);
+rr_status check_grid(const rr_grid_desc* g);
 // The log entry of a step traced now from the context's current observer.
 StepRecord make_step_record(const rr_ctx* ctx, const rr_grid_desc* grid, double chi_a, double chi_b, double scale,
                             double a_step);
@@ -166,7 +192,12 @@ inline void split_ff(double x, float& hi, float& lo)
 }  // namespace rr
 
 struct rr_ctx {
+    // The context's own rays: rows [row0, row0 + bundle.ny) of a bundle of
+    // ny_full rows (rr_create_band; rr_create: row0 = 0, ny_full = bundle.ny).
+    // Sizes and kernels use bundle.ny; directions and footprints use ny_full.
     rr_bundle_desc bundle;
+    int row0 = 0;
+    int ny_full = 0;
     rr::RayState st;
     int device = 0;
     std::vector<rr::StepRecord> log;

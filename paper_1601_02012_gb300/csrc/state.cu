@@ -5,12 +5,13 @@
 namespace rr {
 namespace {
 
-__global__ void init_directions_kernel(int nx, int ny, double fov_x, double fov_y, double* dir, float4* dirh,
-                                       float4* dirl)
+// Rows [row0, row0 + nrows) of an nx x ny bundle; rid counts from row row0.
+__global__ void init_directions_kernel(int nx, int ny, int row0, int nrows, double fov_x, double fov_y,
+                                       double* dir, float4* dirh, float4* dirl)
 {
     const long long rid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (rid >= (long long)nx * ny) return;
-    const int ix = (int)(rid % nx), iy = (int)(rid / nx);
+    if (rid >= (long long)nx * nrows) return;
+    const int ix = (int)(rid % nx), iy = row0 + (int)(rid / nx);
     // Eq. (txty) with 0-based pixel indices, as (2i - (N-1)) U / (2(N-1)): the
     // central pixel of an odd row is at exactly 0; a single ray per side sits at 0
     const double tx = nx > 1 ? (double)(2 * ix - (nx - 1)) * (fov_x / (2.0 * (nx - 1))) : 0.0;
@@ -123,12 +124,14 @@ cudaError_t launch_source_kappa(const double* m_end, const double* m_k, long lon
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s)
+cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s,
+                                   int row0, int nrows)
 {
-    const long long nr = (long long)b.nx * b.ny;
+    if (nrows < 0) nrows = b.ny;
+    const long long nr = (long long)b.nx * nrows;
     const int nt = 256;
-    init_directions_kernel<<<(unsigned)((nr + nt - 1) / nt), nt, 0, s>>>(b.nx, b.ny, b.fov_x, b.fov_y, dir, dirh,
-                                                                                    dirl);
+    init_directions_kernel<<<(unsigned)((nr + nt - 1) / nt), nt, 0, s>>>(b.nx, b.ny, row0, nrows, b.fov_x, b.fov_y,
+                                                                          dir, dirh, dirl);
     return cudaGetLastError();
 }
 

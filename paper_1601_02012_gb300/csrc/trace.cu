@@ -83,17 +83,30 @@ __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], in
 // interval (Eq. 2nterm); the second is the Born term as in the other forms) or
 // kFormGeneric (two scalar fields from float2 records, each with its own
 // quadratic kernel K(chi): the generic integrals of Eqs. Ic, Icfinal).
-// PLANES: the trilinear walk keeps the 64-bit record offsets of the mirrored
-// cell's two vertex planes per axis (entry and exit side) instead of vertex
-// indices, so that a record's offset is two additions (6.5 % faster on the
-// production workload; 32-bit offsets measured slower, the walk then spills).
-// Only the default form uses them: the persistent batch kernel, which also
-// holds its staged arguments, and the forms with more per-segment state
-// (moments, shear, Method A, generic) measured 1.5-4 % slower with them.
-template <int INTERP, class R, int FORM = kFormKahan, bool PLANES = true>
+// ADDR: how the trilinear walk addresses its records.
+//  kAddrIndex:  vertex indices per axis, with periodic wrap (any grid).
+//  kAddrPlanes: the 64-bit record offsets of the mirrored cell's two vertex
+//               planes per axis (entry and exit side), with wrap, so that a
+//               record's offset is two additions (6.5 % faster than indices
+//               on the production workload). The persistent batch kernel,
+//               which also holds its staged arguments, and the forms with
+//               more per-segment state (moments, shear, Method A, generic)
+//               measured 1.5-4 % slower with them and keep indices.
+//  kAddrFlat:   no wrap: a 32-bit point index B of the mirrored cell's entry
+//               corner and a constant signed stride d_a per axis (the next
+//               vertex plane along the motion), so the 8 corners are B plus
+//               sums of the d_a and a crossing of face e is B += d_e. Valid
+//               when no ray of the step comes within a cell of the periodic
+//               seam and the grid has fewer than 2^31 points: the host checks
+//               the step's footprint box; each sub-step checks its own cell
+//               range first and, outside it, flags kErrRange and reads nothing.
+template <int INTERP, class R, int FORM = kFormKahan, int ADDR = kAddrPlanes>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 {
     using OT = unsigned long long;
+    constexpr bool PLANES = ADDR == kAddrPlanes;
+    constexpr bool FLAT = ADDR == kAddrFlat;
+    static_assert(!FLAT || (INTERP == RR_TRILINEAR && sizeof(R) == 4), "flat addressing: FP32 trilinear walk");
     constexpr bool F64 = sizeof(R) == 8;
     constexpr bool SH = !F64 && FORM == kFormShear;
     constexpr bool MA = !F64 && FORM == kFormMethodA;
@@ -133,6 +146,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     int iter = 0;
     bool overflow = false;
     int pc0 = -1, pc1 = -1, pc2 = -1;   // cell where the previous sub-step ended
+    int pB = -1;                        // FLAT: entry corner where the previous sub-step ended
     for (int j = 0; j < nsub && !overflow; ++j) {
     float bh, bl, Lj, D0j;
     sub_step(rg, j, nsub, dsub, bh, bl, Lj, D0j);
@@ -161,6 +175,32 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     const float* w = W.w;
     const R L = W.L, chiA0 = W.chiA0, D0 = W.D0;
     const int max_iter = W.max_iter;
+    // FLAT: entry corner B, strides d, crossing counts as floats
+    int fB = 0, fd[3] = {0, 0, 0};
+    float kf[3] = {0.f, 0.f, 0.f};
+    if constexpr (FLAT) {
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int sa = a == 0 ? A.n1 * A.n2 : (a == 1 ? A.n2 : 1);
+            fB += vlo[a] * sa;
+            fd[a] = sgn[a] * sa;
+            // crossings this sub-step can make on axis a (2 more than the path
+            // allows, for rounding); cells c .. c + sgn K, vertex planes one further
+            int K = 0;
+            if (T0[a] < L) {
+                const float x = (L - T0[a]) * v[a];
+                if (x < 4194304.f) K = f2i_exact(x) + 2;
+                else inside = false;
+            }
+            const int lo = sgn[a] > 0 ? c[a] : c[a] - K, hi = sgn[a] > 0 ? c[a] + K + 1 : c[a] + 1;
+            if (lo < 0 || hi > nn[a] - 1) inside = false;
+        }
+        if (!inside) {
+            atomicOr(A.err, kErrRange);
+            break;
+        }
+    }
     auto fetch = [&](long long i) -> PR {
         if constexpr (MA) return load_grad_rec(A.rec, i);
         else if constexpr (GEN) return __ldg(reinterpret_cast<const float2*>(A.rec) + i);
@@ -174,7 +214,9 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     };
     // a sub-step that resumes inside the previous one's last cell does not
     // start a new cell segment
-    bool resume = j > 0 && c[0] == pc0 && c[1] == pc1 && c[2] == pc2;
+    bool resume;
+    if constexpr (FLAT) resume = j > 0 && fB == pB;
+    else resume = j > 0 && c[0] == pc0 && c[1] == pc1 && c[2] == pc2;
     iter = 0;
 
     // Field cache: (projected kappa value, delta) at the 8 mirrored corners
@@ -186,7 +228,9 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             long long o;
-            if constexpr (PLANES) {
+            if constexpr (FLAT) {
+                o = (unsigned)(fB + ((m & 1) ? fd[0] : 0) + ((m & 2) ? fd[1] : 0) + ((m & 4) ? fd[2] : 0));
+            } else if constexpr (PLANES) {
                 o = (long long)(((m & 1) ? phi[0] : plo[0]) + ((m & 2) ? phi[1] : plo[1]) +
                                 ((m & 4) ? phi[2] : plo[2]));
             } else {
@@ -227,7 +271,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         // mirrored entry point of this segment
         R u[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u[a] = fmin(fmax(fma(sig - T[a], v[a], cu[a]), (R)0), (R)1);
+        for (int a = 0; a < 3; ++a) {
+            if constexpr (FLAT) u[a] = __saturatef(fmaf(sig - T[a], v[a], cu[a]));
+            else u[a] = fmin(fmax(fma(sig - T[a], v[a], cu[a]), (R)0), (R)1);
+        }
 
         // Prefetch the next cell's new records before this segment's arithmetic.
         // (register arrays are indexed only through unrolled loops, never by e)
@@ -235,7 +282,19 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         OT nph = 0;     // offset of the vertex plane beyond the exit face (PLANES)
         int nvhi = 0;   // its vertex index (otherwise)
         PR nr[4];
-        if (!last) {
+        // FLAT: the stride along the exit axis
+        const int fde = e == 0 ? fd[0] : (e == 1 ? fd[1] : fd[2]);
+        if (FLAT && !last) {
+            // the new exit-side corners: B + 2 d_e plus 0, d_A, d_B, d_A + d_B
+            // over the other two axes A < B
+            const int P = fB + 2 * fde;
+            const int dA = e == 0 ? fd[1] : fd[0];
+            const int dB = e == 2 ? fd[1] : fd[2];
+            nr[0] = fetch((unsigned)P);
+            nr[1] = fetch((unsigned)(P + dA));
+            nr[2] = fetch((unsigned)(P + dB));
+            nr[3] = fetch((unsigned)(P + dA + dB));
+        } else if (!last) {
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 if (a == e) {
@@ -375,6 +434,15 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 
         // cross the exit face e
         resume = false;
+        if constexpr (FLAT) {
+            fB += fde;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (a == e) {
+                    kf[a] += 1.f;
+                    T[a] = fmaf(kf[a], td[a], T0[a]);
+                }
+        } else {
         if (!A.periodic && (ncell < 0 || ncell >= ne)) break;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -391,6 +459,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                 if constexpr (F64) T[a] = fma((R)k[a], td[a], T0[a]);
                 else T[a] = fmaf(i2f_exact(k[a]), td[a], T0[a]);
             }
+        }
         if (INTERP == RR_TRILINEAR) {
             float2 p2[4];
 #pragma unroll
@@ -411,6 +480,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         }
     }
     pc0 = c[0]; pc1 = c[1]; pc2 = c[2];
+    pB = fB;
     }
 
     if constexpr (MA) {
@@ -455,12 +525,12 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 }
 
 
-template <int INTERP, class R, int FORM = kFormKahan>
+template <int INTERP, class R, int FORM = kFormKahan, int ADDR = (FORM == kFormKahan ? kAddrPlanes : kAddrIndex)>
 __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, const TileCfg t)
 {
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
-    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM, FORM == kFormKahan>(A, ix, iy);
+    if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM, ADDR>(A, ix, iy);
 }
 
 // Persistent work queue over the ray tiles of many bundles (lightcones): each
@@ -504,7 +574,7 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_batch_kernel(const BatchArgs 
             const int ntx = B.tiles_x[cone];
             int ix, iy;
             tile_ray(B.tile, local % ntx, local / ntx, ix, iy);
-            if (ix < sA.nx && iy < sA.ny) trace_ray<INTERP, R, kFormKahan, false>(sA, ix, iy);
+            if (ix < sA.nx && iy < sA.ny) trace_ray<INTERP, R, kFormKahan, kAddrIndex>(sA, ix, iy);
             __syncthreads();
         }
     }
@@ -543,11 +613,15 @@ cudaError_t launch_form(const TraceArgs& a, int interp, const dim3& grid, int nt
 }  // namespace
 
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
-                         int form)
+                         int form, bool flat)
 {
     if (!tile_ok(t)) return cudaErrorInvalidValue;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const int nt = 32 * t.bwx * t.bwy;
+    if (flat && !fp64_dda && form == kFormKahan && interp == RR_TRILINEAR && a.periodic) {
+        trace_kernel<RR_TRILINEAR, float, kFormKahan, kAddrFlat><<<grid, nt, 0, s>>>(a, t);
+        return cudaGetLastError();
+    }
     if (fp64_dda)
         return interp == RR_TRILINEAR ? launch_one<RR_TRILINEAR, double, kFormKahan>(a, grid, nt, s, t)
                                       : launch_one<RR_NGP, double, kFormKahan>(a, grid, nt, s, t);

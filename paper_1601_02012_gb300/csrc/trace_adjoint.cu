@@ -231,10 +231,11 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
                 ne = nn[a];
             }
         if (INTERP == RR_TRILINEAR) {
-            // the 4 corners on the entry face along e leave the ray's cell;
-            // their four atomics are issued before any returned value is used
-            // the previous crossing's compensations, whose atomics have had this
-            // segment's arithmetic to return
+            // The 4 corners on the entry face along e leave the ray's cell.
+            // First the previous crossing's compensations are finished: their
+            // atomics have had this segment's arithmetic to return. Then this
+            // crossing's four atomics are issued; the values they return are
+            // used at the next crossing, or after the loop.
 #pragma unroll
             for (int r = 0; r < 4; ++r)
                 if (pending[r]) finish_add(pend[r]);
