@@ -45,6 +45,21 @@ L2_FLUSH_BYTES = 256 << 20
 # (kernel source, workload): valid only for the source it was taken on (sha256
 # of csrc/trace.cu + csrc/walk.cuh) and for that workload.
 TRACE_TRAFFIC = {("bb4db20400ea0c5f", "prod_512"): 275_203_968}
+# warp instructions per cell segment of one trace launch from the same kind of
+# ncu capture (smsp__inst_executed.sum / segments of the launch), per (kernel
+# source, workload); null in the line when the source differs
+TRACE_WARP_INSTRUCTIONS = {}
+
+# FP32 lane operations the method needs per trilinear segment, counted from its
+# formulas as the walk evaluates them: exit face (2 compares) and segment length
+# (1); mirrored entry point, 3 axes x (subtract, fused multiply-add with clamp)
+# (6); projection Q = w.H of the 4 corner records the crossing brings in, 4 x 6
+# (24); the trilinear field on the line as a cubic, 33 per channel x 2 channels
+# (kappa, delta) (66); the lensing kernel about the entry point, G0 and G1 (6);
+# J_1..J_4 (22); sum_N e_(N-1) J_N on both channels (8); the compensated (Kahan)
+# sums of both channels (8); the crossing: the next face distance (2).
+ALU_OPS_PER_SEGMENT = 145
+MAX_SM_MHZ = 2070.0   # GB300 maximum SM clock (the issue peak when no clock was sampled)
 
 
 def _src_hash(*names):
@@ -54,12 +69,6 @@ def _src_hash(*names):
         with open(os.path.join(ROOT, "paper_1601_02012_gb300", "csrc", name), "rb") as f:
             hsh.update(f.read())
     return hsh.hexdigest()[:16]
-
-
-def rank_seed(base_seed, rank):
-    """Field seed of a rank: every rank traces its own lightcone (its own field
-    realisation), so the ranks share no data and need no collective."""
-    return base_seed + 1000 * rank
 
 
 def combine_over_ranks(dist, device, total_ms, segs, e2e_s):
@@ -206,7 +215,7 @@ def run_reference(args, w, steps):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(w, len(steps)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{sample} random rays of the 2048x2048 bundle per step, all {len(steps)} "
@@ -867,6 +876,92 @@ def _generic_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, kappa_pa
                     f"CUDA events per step, L2 flushed before each pass, mean of {reps}"}
 
 
+def _fp32_peak(rrp, torch, dev, stream):
+    """FP32 FMA rates of this GPU, measured now (rr_fp32_peak): lane FMAs per
+    second of the packed FFMA2 form and of scalar FFMA (one warp instruction
+    per scheduler and cycle: the issue rate), best of 5 launches each."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = torch.zeros(sms * 8, dtype=torch.float32, device=dev)
+    rates = {}
+    with torch.cuda.stream(stream):
+        for packed in (1, 0):
+            rrp._rr.rr_fp32_peak(packed, sms * 8, 256, 200, out, stream)
+            best = float("inf")
+            n = 0
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                n = rrp._rr.rr_fp32_peak(packed, sms * 8, 256, 2000, out, stream)
+                e1.record(stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            rates["packed" if packed else "scalar"] = n / best
+    return {"lane_fma_per_s": rates["packed"], "scalar_ffma_per_s": rates["scalar"], "sms": sms}
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def _sub_line(argv, timeout=900):
+    """Run this script with other arguments in a child process (one GPU, the
+    same environment) and return its JSON line, or an error record."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py")] + argv
+    try:
+        p = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout, cwd=ROOT)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout} s", "cmd": " ".join(argv)}
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    if p.returncode != 0 or not lines:
+        return {"error": f"exit {p.returncode}: {p.stderr.strip().splitlines()[-1:] or ''}", "cmd": " ".join(argv)}
+    return json.loads(lines[-1])
+
+
+def _compact(line, keys):
+    out = {}
+    for k in keys:
+        if k in line:
+            out[k] = line[k]
+    return out
+
+
+def _other_workloads(steps, warmup):
+    """The adaptive-mesh, batched and differentiation workloads, each in its own
+    child process with fewer timed passes, condensed for the main line."""
+    amr = _sub_line(["--workload", "amr_256", "--steps", str(steps), "--warmup", str(warmup)])
+    if "error" not in amr:
+        amr = _compact(amr, ["value", "unit", "ms_per_step", "rays_per_s", "segments_per_step",
+                             "kernels_ms_per_step", "roofline", "e2e", "error_vs_oracle", "cpu_baseline",
+                             "clocks", "config", "gpu_launches"])
+    bat = _sub_line(["--workload", "batch64", "--steps", str(steps), "--warmup", str(warmup)])
+    if "error" not in bat:
+        bat = _compact(bat, ["value", "unit", "ms_per_step", "rays_per_s", "segments_per_step",
+                             "plain_fp64_per_cone", "speedup_vs_plain", "error_vs_oracle", "tuning", "roofline",
+                             "clocks", "config", "gpu_launches"])
+    adj = _sub_line(["--workload", "adjoint_256", "--with-backward", "--compact", "--no-sub",
+                     "--steps", str(steps), "--warmup", str(warmup)])
+    if "error" not in adj:
+        adj = _compact(adj, ["value", "unit", "ms_per_step", "segments_per_step", "backward",
+                             "error_vs_oracle", "gradient_vs_oracle", "clocks", "config"])
+    return {"amr_256": amr, "batch64": bat, "adjoint_256": adj,
+            "note": f"each workload run by this script in a child process (--workload NAME --steps {steps} "
+                    f"--warmup {warmup}; the adjoint with --with-backward), condensed"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -878,6 +973,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--with-backward", action="store_true",
                     help="also time rr_trace_backward (dL/dPhi of a squared-distance loss) per pass")
+    ap.add_argument("--compact", action="store_true",
+                    help="skip the side measurements (other forms, map statistics) and use a small oracle sample")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="do not run the adaptive-mesh, batched and differentiation workloads after the main one")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -915,6 +1014,7 @@ def main():
     import torch
     import paper_1601_02012_gb300 as rrp
     from paper_1601_02012_gb300 import build as rrbuild
+    from paper_1601_02012_gb300 import shard
 
     rrbuild.build()
     torch.cuda.set_device(local)
@@ -924,21 +1024,34 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    # each rank traces its own lightcone (its own field realisation): no data-path collective
-    seed = rank_seed(w.seed, rank)
-    phi_host = synth.grf_phi_cached(w.grid.n[0], w.grid.box, seed)
+    # one bundle; with several ranks each traces a band of its rows (whole ray
+    # tiles) and the maps are gathered at the end of every pass
+    y0, y1 = shard.band_rows(w.bundle.ny, rank, world)
+    if y1 <= y0:
+        raise SystemExit(f"rank {rank}: no rows of the {w.bundle.ny}-row bundle left for this rank")
+    rows = None if world == 1 else (y0, y1)
+    phi_host = synth.grf_phi_cached(w.grid.n[0], w.grid.box, w.seed)
     stream = torch.cuda.Stream(device=dev)
     phi = torch.from_numpy(phi_host).to(dev)
     rec = rrp.record_buffer(w.grid, device=dev)
-    tr = rrp.Tracer(w.bundle, fp64_dda=args.fp64_dda)
+    tr = rrp.Tracer(w.bundle, fp64_dda=args.fp64_dda, rows=rows)
     gd = rrp.grid_desc(w.grid)
     bboxes = [tr.footprint(w.grid, st.chi_a, st.chi_b) for st in steps]
-    kappa = torch.empty((w.bundle.ny, w.bundle.nx), dtype=torch.float64, device=dev)
+    kappa = torch.empty((y1 - y0, w.bundle.nx), dtype=torch.float64, device=dev)
     kborn = torch.empty_like(kappa)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     nst = len(steps)
     ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
     ev_td = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+    whole = {}
+
+    def gather():
+        # the whole maps on every rank (one all-gather per map; nothing for one rank)
+        if world > 1:
+            whole["k"] = shard.gather_rows(kappa, w.bundle.ny, rank, world)
+            whole["kb"] = shard.gather_rows(kborn, w.bundle.ny, rank, world)
+        else:
+            whole["k"], whole["kb"] = kappa, kborn
 
     def one_pass(src=None, timed_kernels=False):
         rrp.rr_reset(tr.ctx, stream)
@@ -954,6 +1067,7 @@ def main():
             if timed_kernels:
                 ev_tr[i][1].record(stream)
         rrp.rr_finalize(tr.ctx, kappa, kborn, stream)   # synchronises the stream
+        gather()
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -995,6 +1109,7 @@ def main():
 
         # adjoint: dL/dPhi for L = ||kappa - 0.9 kappa||^2-like target, after a pass
         bwd = None
+        grad_check = None
         if args.with_backward:
             gradbuf = rrp.grad_buffer(w.grid, device=dev)
             dphi = torch.zeros_like(phi)
@@ -1010,19 +1125,50 @@ def main():
                 e1.synchronize()
                 bw_ms.append(e0.elapsed_time(e1))
             bw = sum(bw_ms[args.warmup:]) / args.steps
-            bwd = {"ms_per_step": bw, "segments_per_s": segs / (bw / 1e3),
+            fw = total_ms / args.steps
+            bwd = {"ms_per_step": bw, "segments_per_s": segs / (bw / 1e3), "backward_over_forward": bw / fw,
                    "note": "rr_trace_backward over all steps: zero the gradient records, the adjoint of "
-                           "every step (compensated atomics), the transposed stencils into dL/dPhi"}
+                           "every step (compensated atomics), the transposed stencils into dL/dPhi; "
+                           "backward_over_forward against the forward pass of this line"}
+            if world == 1 and not args.no_cpu_baseline:
+                # the gradient against the FP64 oracle's: dL/dkappa, dL/dkborn non-zero on sampled
+                # rays (the oracle's adjoint skips the others), dL/dPhi over the whole grid
+                import oracle
+                oracle.build()
+                rng = np.random.default_rng(11)
+                rids = rng.choice(w.bundle.nrays, 2000, replace=False)
+                yk = np.zeros(w.bundle.nrays)
+                yb = np.zeros(w.bundle.nrays)
+                yk[rids] = rng.standard_normal(len(rids))
+                yb[rids] = rng.standard_normal(len(rids))
+                dphi.zero_()
+                rrp.rr_trace_backward(tr.ctx, torch.from_numpy(yk).to(dev), torch.from_numpy(yb).to(dev),
+                                      gradbuf, dphi, None, stream)
+                stream.synchronize()
+                got = dphi.cpu().numpy().astype(np.float64).ravel()
+                t0 = time.perf_counter()
+                want, _ = oracle.trace_adjoint(w.bundle, w.grid, steps, yk, yb)
+                dto = time.perf_counter() - t0
+                want = want.ravel()
+                sup = want != 0.0
+                rmsg = math.sqrt(float(np.mean(want[sup] ** 2)))
+                grad_check = {"rays": len(rids), "l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                              "max_over_rms_support": float(np.abs(got - want).max() / rmsg),
+                              "support_fraction": float(sup.mean()), "oracle_s": dto,
+                              "note": "dL/dkappa and dL/dkborn standard normal on the sampled rays, zero "
+                                      "elsewhere; dL/dPhi on every cell, GPU (FP32, compensated atomics) "
+                                      "against the FP64 oracle's adjoint; max difference over the rms of the "
+                                      "gradient on the cells it reaches"}
             del gradbuf
 
         # end to end through the public API with host buffers: the potential
         # streamed from pinned host memory step by step (rr_upload_box of each
         # step's footprint on a copy stream, two device buffers, overlapped
-        # with the previous step), the pass, D2H of both maps
-        k_dev = kappa.clone()
-        kb_dev = kborn.clone()
+        # with the previous step), the pass, the maps gathered, D2H of both
+        k_dev = whole["k"].clone()
+        kb_dev = whole["kb"].clone()
         phi_pinned = torch.from_numpy(phi_host).pin_memory()
-        k_host = torch.empty(kappa.shape, dtype=torch.float64).pin_memory()
+        k_host = torch.empty(tuple(whole["k"].shape), dtype=torch.float64).pin_memory()
         kb_host = torch.empty_like(k_host).pin_memory()
         bufs = [torch.zeros_like(phi) for _ in range(2)]
         copy_stream = torch.cuda.Stream(device=dev)
@@ -1031,12 +1177,15 @@ def main():
         for it in range(args.warmup + args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
             t0 = time.perf_counter()
             rrp.rr_reset(tr.ctx, stream)
             h2d_bytes = tr.trace_streamed(w.grid, phi_pinned, steps, rec, bufs, stream, copy_stream, bboxes)
             rrp.rr_finalize(tr.ctx, kappa, kborn, stream)
-            k_host.copy_(kappa, non_blocking=True)
-            kb_host.copy_(kborn, non_blocking=True)
+            gather()
+            k_host.copy_(whole["k"], non_blocking=True)
+            kb_host.copy_(whole["kb"], non_blocking=True)
             stream.synchronize()
             if it >= args.warmup:
                 e2e_times.append(time.perf_counter() - t0)
@@ -1052,7 +1201,7 @@ def main():
         shear = None
         method_a = None
         generic = None
-        if world == 1:
+        if world == 1 and not args.compact:
             sources = _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush)
             # the shear in the same walk (Eqs. gamma1, gamma2)
             shear = _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush,
@@ -1067,6 +1216,7 @@ def main():
                                       total_ms / args.steps, kappa)
             # generic K.Q integrals (the ISW set-up of Sec. 6)
             generic = _generic_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, total_ms / args.steps)
+        peak = _fp32_peak(rrp, torch, dev, stream) if rank == 0 else None
 
     if rank != 0:
         dist.barrier()
@@ -1074,29 +1224,52 @@ def main():
         return
 
     peaks, peak_kind = _peaks()
-    per_pass_trace_s = trace_ms / args.steps / 1e3
-    achieved = segs * BYTES_PER_SEGMENT / per_pass_trace_s / 1e9
+    per_launch_s = trace_ms / args.steps / nst / 1e3
+    segs_per_launch = segs / nst
+    gather_gbs = segs_per_launch * BYTES_PER_SEGMENT / per_launch_s / 1e9
+    alu_gops = segs_per_launch * ALU_OPS_PER_SEGMENT / per_launch_s / 1e9
+    alu_peak = peak["lane_fma_per_s"] / 1e9
     tidal_points = sum((b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]) for b in bboxes)
     h = _src_hash("trace.cu", "walk.cuh")
     traffic = TRACE_TRAFFIC.get((h, w.name))
+    wi = TRACE_WARP_INSTRUCTIONS.get((h, w.name))
+    sm_mhz = (clocks or {}).get("sm_mhz") or MAX_SM_MHZ
+    issue_peak = 4.0 * peak["sms"] * sm_mhz * 1e6          # warp instructions per second
+    issue = None
+    if wi is not None:
+        issue = {"warp_instructions_per_segment": wi, "achieved_per_s": wi * segs_per_launch / per_launch_s,
+                 "peak_per_s": issue_peak, "frac": wi * segs_per_launch / per_launch_s / issue_peak}
     value = segs_all * args.steps / (total_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w, nst) | {"form": "fp64 walk" if args.fp64_dda else "fp32 walk, Kahan sums",
-                                      "parallelism": f"{world} independent lightcones, one per GPU"},
-        "rays_per_s": world * w.bundle.nrays * args.steps / (total_ms / 1e3),
+                                      "parallelism": f"one bundle, its rows split over {world} GPU(s) in "
+                                                     "whole ray tiles; maps all-gathered every pass"},
+        "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
         "segments_per_step": segs_all,
         "roofline": {
-            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": "trace_kernel<trilinear,float>",
-            "note": f"logical gather bytes: {BYTES_PER_SEGMENT} B per segment (8 vertex records) "
-                    f"x segments per launch / mean launch time; peak of {peak_kind} copy bandwidth; "
-                    "traffic: DRAM bytes read + written per launch (ncu, production workload), "
-                    "null when the kernel source differs from the captured one",
-            "algorithmic_bytes_per_launch": segs * BYTES_PER_SEGMENT / nst,
+            "bound": "alu", "achieved": alu_gops, "peak": alu_peak, "unit": "Gop/s", "frac": alu_gops / alu_peak,
+            "traffic": traffic, "kernel": "trace_kernel<trilinear,float>",
+            "algorithmic_ops_per_segment": ALU_OPS_PER_SEGMENT,
+            "algorithmic_ops_per_launch": segs_per_launch * ALU_OPS_PER_SEGMENT,
+            "mean_launch_ms": per_launch_s * 1e3,
+            "note": f"FP32 lane operations the method needs per trilinear segment ({ALU_OPS_PER_SEGMENT}: "
+                    "exit face, entry point, the projection of the 4 new corner records, the line cubic and "
+                    "the kernel integrals of both channels, the compensated sums, the crossing) x segments "
+                    "per launch / mean launch time (CUDA events, all launches of the timed passes); peak: "
+                    "the packed FFMA2 lane rate measured in this run (rr_fp32_peak); traffic: DRAM bytes "
+                    "read + written per launch (ncu), null when the kernel source differs from the captured one",
+            "fp32_peak": {"lane_fma_per_s": peak["lane_fma_per_s"], "scalar_ffma_per_s": peak["scalar_ffma_per_s"],
+                          "nominal_lane_fma_per_s": peak["sms"] * 128 * MAX_SM_MHZ * 1e6,
+                          "kind": "measured in this run"},
+            "issue": issue,
+            "gather": {"achieved": gather_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": gather_gbs / peaks["hbm_gbs"],
+                       "note": f"logical gather bytes ({BYTES_PER_SEGMENT} B per segment: 8 vertex records) / "
+                               f"launch time against the {peak_kind} HBM copy bandwidth; served by L1 and L2 "
+                               "(10^2-10^4 rays cross each cell), not by DRAM: above 1 by cache reuse"},
         },
         "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps,
                                 "tidal_points_per_step": tidal_points},
@@ -1109,13 +1282,15 @@ def main():
                            "note": "whole-grid launch, 36 B per point (4 B potential read, 32 B record written); "
                                    "the per-step footprint launches are small and latency-bound"},
         "backward": bwd,
+        "gradient_vs_oracle": grad_check,
         "e2e": {"value": segs_all * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d_bytes),
                 "d2h_bytes_per_step": int(k_host.numel() * 8 * 2),
                 "max_abs_diff_vs_device_maps": e2e_diff,
-                "note": "host potential (pinned, the whole 512^3 field) streamed per step: rr_upload_box of "
-                        "the step's footprint plus the stencil reach on a copy stream into one of two device "
-                        "buffers, overlapped with the previous step; both maps read back"},
+                "note": "host potential (pinned, the whole field) streamed per step: rr_upload_box of the "
+                        "step's footprint plus the stencil reach on a copy stream into one of two device "
+                        "buffers, overlapped with the previous step; both whole maps read back (rank 0's "
+                        "bytes; every rank streams its own footprints)"},
         "source_redshifts": sources,
         "shear": shear,
         "method_a": method_a,
@@ -1129,65 +1304,87 @@ def main():
         # the FP64 oracle on the host cores, on a bounded sample of the same
         # workload; the sampled rays also give the error of the GPU map
         threads = os.cpu_count() or 1
+        budget = 4.0 if args.compact else 12.0
         H, d = _oracle_fields(w.grid, phi_host)
         rng = np.random.default_rng(4321)
         rids = rng.choice(w.bundle.nrays, 256, replace=False)
         res, dt = _oracle_sample(w.bundle, w.grid, H, d, steps, rids, threads)
-        n2 = int(min(w.bundle.nrays, max(256, 256 * 12.0 / max(dt, 1e-3))))
+        n2 = int(min(w.bundle.nrays, max(256, 256 * budget / max(dt, 1e-3))))
         rids2 = rng.choice(w.bundle.nrays, n2, replace=False)
         res2, dt2 = _oracle_sample(w.bundle, w.grid, H, d, steps, rids2, threads)
+        # one thread, on a sample sized for ~budget / 3 s
+        n1 = int(min(w.bundle.nrays, max(16, 256 * (budget / 3.0) / max(dt * threads, 1e-3))))
+        rids1 = rng.choice(w.bundle.nrays, n1, replace=False)
+        res1, dt1 = _oracle_sample(w.bundle, w.grid, H, d, steps, rids1, 1)
         line["cpu_baseline"] = {
             "value": float(res2.nseg.sum()) / dt2, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n2} random rays of the bundle through all {nst} steps ({dt2:.1f} s); "
-                      "tidal centres of the full grid computed once outside the timing"}
-        kg = kappa.cpu().numpy().ravel()
-        kbg = kborn.cpu().numpy().ravel()
-        allr = np.concatenate([rids, rids2])
-        ko = np.concatenate([res.kappa, res2.kappa])
-        kbo = np.concatenate([res.kborn, res2.kborn])
+                      "tidal centres of the full grid computed once outside the timing",
+            "single_thread": {"value": float(res1.nseg.sum()) / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} random rays through all {nst} steps ({dt1:.1f} s)"},
+            "cpu_model": _cpu_model(), "host_threads": threads}
+        kg = whole["k"].cpu().numpy().ravel()
+        kbg = whole["kb"].cpu().numpy().ravel()
+        allr = np.concatenate([rids, rids2, rids1])
+        ko = np.concatenate([res.kappa, res2.kappa, res1.kappa])
+        kbo = np.concatenate([res.kborn, res2.kborn, res1.kborn])
         rms, rmsb = math.sqrt(float(np.mean(ko ** 2))), math.sqrt(float(np.mean(kbo ** 2)))
+        per_ray = torch.zeros(w.bundle.nrays, dtype=torch.int32, device=dev)
+        tr.segments(per_ray=per_ray)
+        torch.cuda.synchronize()
+        nseg_gpu = per_ray.cpu().numpy().view(np.uint32).astype(np.int64)
+        nseg_ora = np.concatenate([res.nseg, res2.nseg, res1.nseg])
         line["error_vs_oracle"] = {
             "rays": int(len(allr)),
             "kappa_max_over_rms": float(np.abs(kg[allr] - ko).max() / rms),
             "kborn_max_over_rms": float(np.abs(kbg[allr] - kbo).max() / rmsb),
             "segments_per_ray_gpu": segs / w.bundle.nrays,
-            "segments_per_ray_oracle": float(np.concatenate([res.nseg, res2.nseg]).mean()),
+            "segments_sampled_rays_gpu": int(nseg_gpu[allr].sum()),
+            "segments_sampled_rays_oracle": int(nseg_ora.sum()),
+            "segments_rel_diff": float(abs(int(nseg_gpu[allr].sum()) - int(nseg_ora.sum())) / nseg_ora.sum()),
         }
-        # map statistics: a contiguous patch of the map (its centre quarter per
-        # side) traced by the oracle through all steps, P(ell) and PDF vs the GPU's
-        from paper_1601_02012_gb300 import mapstats
-        px = min(512, w.bundle.nx)
-        py = min(512, w.bundle.ny)
-        x0, y0 = (w.bundle.nx - px) // 2, (w.bundle.ny - py) // 2
-        iy, ix = np.meshgrid(np.arange(y0, y0 + py), np.arange(x0, x0 + px), indexing="ij")
-        prids = (iy * w.bundle.nx + ix).ravel()
-        t0 = time.perf_counter()
-        pres, _ = _oracle_sample(w.bundle, w.grid, H, d, steps, prids, threads)
-        dtp = time.perf_counter() - t0
-        fx = w.bundle.fov_x * (px - 1) / max(w.bundle.nx - 1, 1)
-        fy = w.bundle.fov_y * (py - 1) / max(w.bundle.ny - 1, 1)
-        line["map_statistics"] = {
-            "patch": f"{px}x{py} rays at the map centre ({fx * 180 / math.pi:.3f} x {fy * 180 / math.pi:.3f} deg), "
-                     f"all {nst} steps, oracle {dtp:.1f} s",
-            "kappa": mapstats.compare(kg[prids].reshape(py, px), pres.kappa.reshape(py, px), fx, fy),
-            "kborn": mapstats.compare(kbg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
-            "definition": "P(ell): 20 log bins of ell = 2 pi m / Upsilon, largest relative bin difference; "
-                          "PDF: 100 bins over +-5 sigma of the oracle map, L1 distance",
-        }
-        # the same statistics for the FP32 walk without compensated sums (one pass)
-        trp = rrp.Tracer(w.bundle, plain_sums=True)
-        with torch.cuda.stream(stream):
-            for i, st in enumerate(steps):
-                rrp.rr_tidal_tensor(gd, phi, None, rec, trp.where, bboxes[i], stream)
-                rrp.rr_trace_step(trp.ctx, gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
-            kp, kbp = trp.finalize(stream=stream)
-        trp.close()
-        kpg, kbpg = kp.cpu().numpy().ravel(), kbp.cpu().numpy().ravel()
-        line["map_statistics"]["plain_fp32_sums"] = {
-            "kappa": mapstats.compare(kpg[prids].reshape(py, px), pres.kappa.reshape(py, px), fx, fy),
-            "kborn": mapstats.compare(kbpg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
-            "note": "the same pass with uncompensated FP32 sums within and across steps (RR_PLAIN_SUMS)",
-        }
+        if not args.compact:
+            # map statistics: a contiguous patch of the map (its centre quarter per
+            # side) traced by the oracle through all steps, P(ell) and PDF vs the GPU's
+            from paper_1601_02012_gb300 import mapstats
+            px = min(512, w.bundle.nx)
+            py = min(512, w.bundle.ny)
+            x0, yy0 = (w.bundle.nx - px) // 2, (w.bundle.ny - py) // 2
+            iy, ix = np.meshgrid(np.arange(yy0, yy0 + py), np.arange(x0, x0 + px), indexing="ij")
+            prids = (iy * w.bundle.nx + ix).ravel()
+            t0 = time.perf_counter()
+            pres, _ = _oracle_sample(w.bundle, w.grid, H, d, steps, prids, threads)
+            dtp = time.perf_counter() - t0
+            fx = w.bundle.fov_x * (px - 1) / max(w.bundle.nx - 1, 1)
+            fy = w.bundle.fov_y * (py - 1) / max(w.bundle.ny - 1, 1)
+            line["map_statistics"] = {
+                "patch": f"{px}x{py} rays at the map centre ({fx * 180 / math.pi:.3f} x "
+                         f"{fy * 180 / math.pi:.3f} deg), all {nst} steps, oracle {dtp:.1f} s",
+                "kappa": mapstats.compare(kg[prids].reshape(py, px), pres.kappa.reshape(py, px), fx, fy),
+                "kborn": mapstats.compare(kbg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
+                "definition": "P(ell): 20 log bins of ell = 2 pi m / Upsilon, largest relative bin difference; "
+                              "PDF: 100 bins over +-5 sigma of the oracle map, L1 distance",
+            }
+            # the same statistics for the FP32 walk without compensated sums (one pass)
+            trp = rrp.Tracer(w.bundle, plain_sums=True)
+            with torch.cuda.stream(stream):
+                for i, st in enumerate(steps):
+                    rrp.rr_tidal_tensor(gd, phi, None, rec, trp.where, bboxes[i], stream)
+                    rrp.rr_trace_step(trp.ctx, gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+                kp, kbp = trp.finalize(stream=stream)
+            trp.close()
+            kpg, kbpg = kp.cpu().numpy().ravel(), kbp.cpu().numpy().ravel()
+            line["map_statistics"]["plain_fp32_sums"] = {
+                "kappa": mapstats.compare(kpg[prids].reshape(py, px), pres.kappa.reshape(py, px), fx, fy),
+                "kborn": mapstats.compare(kbpg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
+                "note": "the same pass with uncompensated FP32 sums within and across steps (RR_PLAIN_SUMS)",
+            }
+    if world == 1 and not args.no_sub:
+        # free this workload's device memory before the child processes run
+        tr.close()
+        del rec, phi, kappa, kborn, flush, whole, k_dev, kb_dev
+        torch.cuda.empty_cache()
+        line["other_workloads"] = _other_workloads(3, 3)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

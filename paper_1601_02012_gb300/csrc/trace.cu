@@ -528,6 +528,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
 template <int INTERP, class R, int FORM = kFormKahan, int ADDR = (FORM == kFormKahan ? kAddrPlanes : kAddrIndex)>
 __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, const TileCfg t)
 {
+    prefetch_ahead(A, t);
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
     if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM, ADDR>(A, ix, iy);

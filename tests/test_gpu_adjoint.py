@@ -174,3 +174,38 @@ def test_differentiation_workload_fd(rrp):
         worst = max(worst, abs(fd - float(gmat[cell])) / rms)
     tr.close()
     assert worst <= 1e-4, worst
+
+
+def test_differentiation_workload_vs_oracle_gradient(rrp, oracle_lib):
+    """The differentiation workload at full size (256^3 potential, 1024^2 rays
+    over 5x5 deg to chi_s = 512, one step) against the FP64 oracle's gradient:
+    dL/dkappa and dL/dkborn non-zero on 3000 sampled rays of the bundle (the
+    oracle's adjoint skips the others), dL/dPhi on the whole grid from
+    rr_trace_backward and from the oracle: l2 within the tolerance above, and
+    the largest difference within 1e-4 of the gradient's rms over its support
+    (the cells it reaches: a gradient confined to sampled rays' footprints is
+    zero on most of the grid, where an rms over every cell would shrink the
+    scale the max is measured against)."""
+    import torch
+    w = synth.workload("adjoint_256")
+    g, b = w.grid, w.bundle
+    steps = [synth.Step(b.chi_s, 0.0, 1.0, 1.0)]
+    phi = torch.from_numpy(synth.grf_phi_cached(256, g.box, 5)).cuda()
+    rng = np.random.default_rng(11)
+    rids = rng.choice(b.nrays, 3000, replace=False)
+    yk = np.zeros(b.nrays)
+    yb = np.zeros(b.nrays)
+    yk[rids] = rng.standard_normal(len(rids))
+    yb[rids] = rng.standard_normal(len(rids))
+    tr, k, kb = _forward(rrp, phi, g, b, steps)
+    dphi = tr.backward(g, torch.from_numpy(yk.reshape(b.ny, b.nx)).cuda(),
+                       torch.from_numpy(yb.reshape(b.ny, b.nx)).cuda())
+    torch.cuda.synchronize()
+    got = dphi.cpu().numpy()
+    tr.close()
+    want, _ = oracle_lib.trace_adjoint(b, g, steps, yk, yb)
+    l2, _ = _rel(got, want)
+    support = want != 0.0
+    rms_support = math.sqrt(float(np.mean(want[support] ** 2)))
+    mx = float(np.abs(got.astype(np.float64) - want).max()) / rms_support
+    assert l2 <= 1e-5 and mx <= 1e-4, (l2, mx, float(support.mean()))
