@@ -357,20 +357,19 @@ rr_status rr_step_count(rr_ctx* ctx, int32_t* n);
  * of Eq. kappa2). The map is linear in the records, so this is its exact
  * transpose; it needs the geometry only, not the records.
  *   dL_dkappa, dL_dkborn  device FP64 [ny*nx] in rayid order (either may be NULL).
- *   grad_rec              device, n0*n1*n2 gradient records of 16 floats (64 B,
- *                         16-byte aligned): words 0-7 hold FP32 running sums of
- *                         the 8 record channels {Hxx,Hyy,Hzz,Hxy,Hxz,Hyz,delta,0},
- *                         words 8-15 the accumulated rounding errors of those
- *                         sums; the gradient of channel c is word c + word c+8.
- *                         Accumulated with compensated atomics (the order of
- *                         additions is not deterministic; the value is, to
- *                         rounding).
+ *   grad_rec              device, n0*n1*n2 gradient records of 64 B each
+ *                         (16-byte aligned; passed as float*, 16 floats per
+ *                         point): 8 FP64 sums, one per record channel
+ *                         {Hxx,Hyy,Hzz,Hxy,Hxz,Hyz,delta,0}, accumulated with
+ *                         FP64 atomic additions of warp-summed FP32
+ *                         contributions (the order of additions is not
+ *                         deterministic; the value is, to rounding).
  */
 rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkappa, const double* dL_dkborn,
                                 float* grad_rec, void* stream);
 
 /*
- * Transpose of rr_tidal_tensor: from gradient records (16 floats per point, as
+ * Transpose of rr_tidal_tensor: from gradient records (64 B per point, as
  * written by rr_trace_step_adjoint; at vertices or centres) to dL/dPhi at the
  * cell centres, accumulated (+=) into dL_dphi (device,
  * n0*n1*n2 floats). If dL_ddelta is NULL, delta is taken as derived from the
@@ -384,7 +383,7 @@ rr_status rr_tidal_tensor_adjoint(const rr_grid_desc* grid, const float* grad_re
  * dL/dPhi for maps traced from one potential: all logged steps must share one
  * grid and their records must come from the same phi (each step's field being
  * scale_k * that phi). Zeroes grad_rec (caller scratch, n0*n1*n2 gradient
- * records of 16 floats), adds the adjoint of every logged step, then applies
+ * records of 64 B), adds the adjoint of every logged step, then applies
  * rr_tidal_tensor_adjoint into dL_dphi (accumulated) / dL_ddelta (NULL: delta
  * derived from phi). RR_ERR_STATE if no step was traced or the grids differ.
  */

@@ -55,8 +55,8 @@ def record_buffer(grid, device="cuda"):
 
 
 def grad_buffer(grid, device="cuda"):
-    """Uninitialised device buffer for n0*n1*n2 gradient records of 16 floats
-    (hi and lo words of the 8 record channels)."""
+    """Uninitialised device buffer for n0*n1*n2 gradient records of 64 bytes
+    (16 floats' room: the 8 record channels as FP64 sums)."""
     import torch
     n = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
     return torch.empty((n, 16), dtype=torch.float32, device=device)

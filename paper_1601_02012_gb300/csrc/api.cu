@@ -178,22 +178,33 @@ rr_status status_of_cuda(cudaError_t e) { return from_cuda(e); }
 
 namespace rr {
 
-void footprint_box(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a,
-                   double chi_b, long long i0[3], long long i1[3])
+// Bounds [lo, hi] per axis of the positions obs + chi n of the bundle's rays
+// for chi in [chi_b, chi_a]. n_x = theta_x sinc(theta) lies in
+// [-sin(U_x/2), sin(U_x/2)] because sinc decreases on [0, pi); n_z = cos(theta)
+// lies in [cos(theta_max), 1]; a position is linear in chi, so its extremes
+// are at the ends of the interval.
+static void position_bounds(const rr_bundle_desc& b, const double obs[3], double chi_a, double chi_b,
+                            double lo[3], double hi[3])
 {
-    // Bounds of the direction over the bundle: n_x = theta_x sinc(theta) lies in
-    // [-sin(U_x/2), sin(U_x/2)] because sinc decreases on [0, pi); n_z = cos(theta)
-    // lies in [cos(theta_max), 1].
     const double hx = b.nx > 1 ? 0.5 * b.fov_x : 0.0, hy = b.ny > 1 ? 0.5 * b.fov_y : 0.0;
     const double thmax = sqrt(hx * hx + hy * hy);
     const double nlo[3] = {-sin(hx), -sin(hy), cos(thmax)};
     const double nhi[3] = {sin(hx), sin(hy), 1.0};
-    const double h = g.box / g.n[0];
     for (int a = 0; a < 3; ++a) {
         const double c1 = chi_a * nlo[a], c2 = chi_b * nlo[a], c3 = chi_a * nhi[a], c4 = chi_b * nhi[a];
-        const double lo = obs[a] + std::min(std::min(c1, c2), std::min(c3, c4));
-        const double hi = obs[a] + std::max(std::max(c1, c2), std::max(c3, c4));
-        const double f0 = floor(lo / h), f1 = floor(hi / h);
+        lo[a] = obs[a] + std::min(std::min(c1, c2), std::min(c3, c4));
+        hi[a] = obs[a] + std::max(std::max(c1, c2), std::max(c3, c4));
+    }
+}
+
+void footprint_box(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a,
+                   double chi_b, long long i0[3], long long i1[3])
+{
+    double lo[3], hi[3];
+    position_bounds(b, obs, chi_a, chi_b, lo, hi);
+    const double h = g.box / g.n[0];
+    for (int a = 0; a < 3; ++a) {
+        const double f0 = floor(lo[a] / h), f1 = floor(hi[a] / h);
         // (saturated far outside any grid; the callers compare against [0, n])
         i0[a] = (f0 > -1e15 ? (long long)f0 : -1000000000000000LL) - 1;
         i1[a] = (f1 < 1e15 ? (long long)f1 : 1000000000000000LL) + 3;
@@ -204,12 +215,15 @@ bool flat_ok(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g
 {
     if (!(b.flags & RR_PERIODIC) || b.interp != RR_TRILINEAR) return false;
     if ((long long)g.n[0] * g.n[1] * g.n[2] >= (1LL << 31)) return false;
-    long long i0[3], i1[3];
-    footprint_box(b, obs, g, chi_a, chi_b, i0, i1);
-    // cells i0 + 1 .. i1 - 3 are reachable; with one more cell of margin on
-    // each side, every vertex plane the walk reads lies in [0, n - 1]
+    // every position of the step inside [2 h, (n - 3) h) per axis: the walk's
+    // cells then lie in 2 .. n - 4, and each sub-step's own check (up to 2
+    // crossings more than its path allows, planes one further) stays in
+    // [0, n - 1]: no vertex plane across the periodic seam
+    double lo[3], hi[3];
+    position_bounds(b, obs, chi_a, chi_b, lo, hi);
+    const double h = g.box / g.n[0];
     for (int a = 0; a < 3; ++a)
-        if (i0[a] < 1 || i1[a] > g.n[a] - 1) return false;
+        if (!(lo[a] >= 2.0 * h) || !(hi[a] < (g.n[a] - 3) * h)) return false;
     return true;
 }
 
@@ -588,7 +602,7 @@ rr_status rr_trace_step_adjoint(rr_ctx* ctx, int32_t step, const double* dL_dkap
     AdjArgs g;
     g.dkappa = dL_dkappa;
     g.dkborn = dL_dkborn;
-    g.grad = reinterpret_cast<float4*>(grad_rec);
+    g.grad = reinterpret_cast<double*>(grad_rec);
     g.kscale = r.scale;
     g.bscale = r.scale * 1.5 * r.grid.omega_m * kH0OverC * kH0OverC / r.a_step;
     return from_cuda(launch_trace_adjoint(a, g, ctx->bundle.interp, (ctx->bundle.flags & RR_FP64_DDA) != 0,

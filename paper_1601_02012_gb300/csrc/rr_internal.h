@@ -87,11 +87,11 @@ struct TraceArgs {
 };
 
 // Adjoint of one step: per-ray derivatives of the loss and the gradient
-// records (2 float4 per point, same layout as the records).
+// records (8 FP64 sums per point, in the channel order of the records).
 struct AdjArgs {
     const double* dkappa;       // dL/dkappa per ray, or NULL
     const double* dkborn;       // dL/dkappa_born per ray, or NULL
-    float4* grad;
+    double* grad;
     double kscale;              // the step's scale
     double bscale;              // scale * 1.5 Omega_m (H0/c)^2 / a_step
 };
@@ -168,8 +168,10 @@ TraceArgs make_trace_args(const rr_bundle_desc& b, const RayState& st, const rr_
 void footprint_box(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a,
                    double chi_b, long long i0[3], long long i1[3]);
 // Whether a step of bundle b (observer obs) on grid g can use flat record
-// addressing: periodic trilinear FP32 walk, fewer than 2^31 points, and a
-// footprint at least one cell clear of the periodic seam on every axis.
+// addressing: periodic trilinear FP32 walk, fewer than 2^31 points, and every
+// position the rays take in the step at least 2 cells from the periodic seam
+// below and 3 above on every axis (no vertex plane the walk reads lies
+// across the seam).
 bool flat_ok(const rr_bundle_desc& b, const double obs[3], const rr_grid_desc& g, double chi_a, double chi_b);
 // Argument checks of a bundle and a grid description (RR_OK or RR_ERR_ARG).
 rr_status check_bundle(const rr_bundle_desc* b);

@@ -21,6 +21,7 @@
 // delta instead: one 16-byte record, 20 bytes per point.
 #include <algorithm>
 
+#include "fpbits.cuh"
 #include "rr_internal.h"
 
 namespace rr {
@@ -270,8 +271,8 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Transpose of the above: gradient records (16 floats per point: the hi and lo
-// words of 8 channels, at vertices or centres) -> dL/dPhi
+// Transpose of the above: gradient records (8 FP64 channel sums per point, at
+// vertices or centres) -> dL/dPhi
 // (and dL/ddelta when delta was an independent input).
 //   vertices: gH(c) = (1/8) sum of the gradient records of the 8 vertices of c
 //             (the transpose of the 8-cell mean);
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
 constexpr int AX = 4, AY = 4, AZ = 16;
 
 struct TidalAdjArgs {
-    const float4* grad;
+    const double2* grad;
     float* dphi;
     float* ddelta;
     int n0, n1, n2;
@@ -307,11 +308,11 @@ __global__ void __launch_bounds__(NT) tidal_adjoint_kernel(TidalAdjArgs a)
         const int z = i % GZ, y = (i / GZ) % GY, x = i / (GZ * GY);
         const int gx = wrapi(cx0 - 1 + x, a.n0), gy = wrapi(cy0 - 1 + y, a.n1), gz = wrapi(cz0 - 1 + z, a.n2);
         const size_t p = ((size_t)gx * a.n1 + gy) * a.n2 + gz;
-        // hi + lo of each channel (see the gradient record layout in rr.h)
-        const float4 h0 = __ldg(a.grad + 4 * p), h1 = __ldg(a.grad + 4 * p + 1);
-        const float4 l0 = __ldg(a.grad + 4 * p + 2), l1 = __ldg(a.grad + 4 * p + 3);
-        sg[0][i] = h0.x + l0.x; sg[1][i] = h0.y + l0.y; sg[2][i] = h0.z + l0.z; sg[3][i] = h0.w + l0.w;
-        sg[4][i] = h1.x + l1.x; sg[5][i] = h1.y + l1.y; sg[6][i] = h1.z + l1.z;
+        // the FP64 sums of the 8 channels (see the gradient record layout in rr.h)
+        const double2 g0 = __ldg(a.grad + 4 * p), g1 = __ldg(a.grad + 4 * p + 1);
+        const double2 g2 = __ldg(a.grad + 4 * p + 2), g3 = __ldg(a.grad + 4 * p + 3);
+        sg[0][i] = d2f_bits(g0.x); sg[1][i] = d2f_bits(g0.y); sg[2][i] = d2f_bits(g1.x); sg[3][i] = d2f_bits(g1.y);
+        sg[4][i] = d2f_bits(g2.x); sg[5][i] = d2f_bits(g2.y); sg[6][i] = d2f_bits(g3.x);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NH; i += NT) {
@@ -482,7 +483,7 @@ cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, i
                                  cudaStream_t s)
 {
     TidalAdjArgs a;
-    a.grad = reinterpret_cast<const float4*>(grad_rec);
+    a.grad = reinterpret_cast<const double2*>(grad_rec);
     a.dphi = dphi;
     a.ddelta = ddelta;
     a.n0 = g.n[0]; a.n1 = g.n[1]; a.n2 = g.n[2];

@@ -37,68 +37,54 @@ __device__ __forceinline__ void line_cubic_adjoint(const float J[4], float u0, f
     }
 }
 
-// Rounding error of the FP32 sum old + x (TwoSum), per component.
-__device__ __forceinline__ float4 sum_error(float4 o, float4 x)
-{
-    float4 e;
-    float s, t;
-    two_sum(o.x, x.x, s, t); e.x = t;
-    two_sum(o.y, x.y, s, t); e.y = t;
-    two_sum(o.z, x.z, s, t); e.z = t;
-    two_sum(o.w, x.w, s, t); e.w = t;
-    return e;
-}
-
-// Add S * (gk w, gb) to the gradient record of point idx. A gradient record
-// is 16 floats: the FP32 running sums of the 8 channels (hi) and the exact
-// rounding errors of those sums (lo): the atomic add returns the value it
-// added to, TwoSum of (old, x) gives the error of that addition, and the
-// error is itself accumulated. hi + lo is then accurate even where thousands
-// of contributions of both signs cancel.
+// Add S * (gk w, gb) to the gradient record of point idx: 8 FP64 sums, one
+// per record channel {Hxx, Hyy, Hzz, Hxy, Hxz, Hyz, delta, 0} (64 B).
 //
-// Neighbouring rays of a warp are far closer together than a cell, so they
-// usually cross the same faces in the same iteration and flush the same
-// point together. When all 32 lanes flush one point, their contributions are
-// summed across the warp first by a reduce-scatter butterfly (each of the
-// first three exchanges halves the channels a lane keeps: 4 + 2 + 1 + 1 + 1
-// shuffles instead of 5 per channel), after which lane 4c holds the total of
-// channel c and adds it with a compensated scalar atomic; otherwise every lane
-// adds its own. The 32-term warp sums are plain FP32 (a relative error of a
-// few ulp per flush); the compensation guards the long chains of additions
-// into one record, where thousands of contributions of both signs meet.
-// A flush whose compensation is still to be made: the atomic add of v into
-// *p returned old; the rounding error of old + v goes into p[8].
-struct PendingAdd {
-    float* p;
-    float old, v;
-};
-
-__device__ __forceinline__ void finish_add(const PendingAdd& d)
+// Neighbouring rays of a warp are far closer together than a cell, so the
+// lanes of a warp mostly flush the same point at the same crossing (on the
+// differentiation workload 80 % of a warp's flushes go to one point, 15 % to
+// two, 4 % to three). For each distinct point the warp sums the contributions
+// of the lanes flushing it in one reduce-scatter butterfly (every lane takes
+// part, lanes flushing another point with zeros; each of the first three
+// exchanges halves the channels a lane keeps: 4 + 2 + 1 + 1 + 1 shuffles
+// instead of 5 per channel), after which lane 4c holds the point's total of
+// channel c and adds it to the record with an FP64 atomic whose value is not
+// used: a reduction, with no round trip for the lane. FP64 sums keep their
+// accuracy where thousands of contributions of both signs meet; the 32-term
+// warp sums are plain FP32 (a relative error of a few ulp per flush). A warp
+// with inactive lanes adds every lane's channels on its own.
+__device__ __forceinline__ void flush_grad(double* __restrict__ grad, long long idx, float S, float gk, float gb,
+                                           const float* w)
 {
-    float sum, err;
-    two_sum(d.old, d.v, sum, err);
-    atomicAdd(d.p + 8, err);
-}
-
-// First half of a flush: returns true when it left a compensation pending in
-// `pend` (the warp-summed path), so that several flushes' atomics can be in
-// flight before their returned values are needed.
-__device__ __forceinline__ bool flush_grad_begin(float4* __restrict__ grad, long long idx, float S, float gk,
-                                                 float gb, const float* w, PendingAdd& pend)
-{
+    constexpr unsigned FULL = 0xffffffffu;
     const float a = gk * S;
+    const float x[8] = {a * w[0], a * w[1], a * w[2], a * w[3], a * w[4], a * w[5], gb * S, 0.f};
     const unsigned active = __activemask();
-    if (active == 0xffffffffu && __match_any_sync(active, idx) == active) {
-        constexpr unsigned FULL = 0xffffffffu;
-        const int lane = threadIdx.x & 31;
-        const float x[8] = {a * w[0], a * w[1], a * w[2], a * w[3], a * w[4], a * w[5], gb * S, 0.f};
+    if (active != FULL) {
+        if (S != 0.f) {
+            double* p = grad + 8 * idx;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) atomicAdd(p + c, (double)x[c]);
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    const int ch = lane >> 2;
+    unsigned todo = FULL;
+    while (todo) {   // one pass per distinct point (todo is the same in every lane)
+        const long long key = __shfl_sync(FULL, idx, __ffs(todo) - 1);
+        const bool mine = idx == key;
+        todo &= ~__ballot_sync(FULL, mine);
+        float y[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) y[i] = mine ? x[i] : 0.f;
         // xor 16: keep channels 4 b4 .. 4 b4 + 3
-        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
         float k4[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float sx = b4 ? x[i] : x[4 + i];
-            k4[i] = (b4 ? x[4 + i] : x[i]) + __shfl_xor_sync(FULL, sx, 16);
+            const float sx = b4 ? y[i] : y[4 + i];
+            k4[i] = (b4 ? y[4 + i] : y[i]) + __shfl_xor_sync(FULL, sx, 16);
         }
         // xor 8: keep 2 of the 4
         float k2[2];
@@ -107,36 +93,12 @@ __device__ __forceinline__ bool flush_grad_begin(float4* __restrict__ grad, long
             const float sx = b3 ? k4[i] : k4[2 + i];
             k2[i] = (b3 ? k4[2 + i] : k4[i]) + __shfl_xor_sync(FULL, sx, 8);
         }
-        // xor 4: keep 1 of the 2; xor 2, xor 1: the whole warp's total of channel (lane >> 2)
+        // xor 4: keep 1 of the 2; xor 2, xor 1: the warp's total of channel (lane >> 2)
         float v = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(FULL, b2 ? k2[0] : k2[1], 4);
         v += __shfl_xor_sync(FULL, v, 2);
         v += __shfl_xor_sync(FULL, v, 1);
-        const int ch = lane >> 2;
-        if ((lane & 3) == 0 && ch < 7 && v != 0.f) {
-            float* p = reinterpret_cast<float*>(grad + 4 * idx) + ch;
-            pend.p = p;
-            pend.v = v;
-            pend.old = atomicAdd(p, v);
-            return true;
-        }
-        return false;
+        if ((lane & 3) == 0 && ch < 7 && v != 0.f) atomicAdd(grad + 8 * key + ch, (double)v);
     }
-    if (S == 0.f) return false;
-    const float4 x0 = make_float4(a * w[0], a * w[1], a * w[2], a * w[3]);
-    const float4 x1 = make_float4(a * w[4], a * w[5], gb * S, 0.f);
-    float4* p = grad + 4 * idx;
-    const float4 o0 = atomicAdd(p, x0);
-    const float4 o1 = atomicAdd(p + 1, x1);
-    atomicAdd(p + 2, sum_error(o0, x0));
-    atomicAdd(p + 3, sum_error(o1, x1));
-    return false;
-}
-
-__device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long idx, float S, float gk, float gb,
-                                           const float* w)
-{
-    PendingAdd d;
-    if (flush_grad_begin(grad, idx, S, gk, gb, w, d)) finish_add(d);
 }
 
 // Adjoint of one step: replays the walk and, for every point the ray's
@@ -144,8 +106,8 @@ __device__ __forceinline__ void flush_grad(float4* __restrict__ grad, long long 
 // dI/dq of the segment integrals (the transpose of the forward map) while the
 // point stays in the ray's current cell; a point is flushed into the
 // gradient records once per residency, as gk * S * w (the six tidal channels
-// through Q_kappa = w . H) and gb * S (delta), with compensated 16-byte atomic
-// adds (flush_grad).
+// through Q_kappa = w . H) and gb * S (delta), summed over the warp and added
+// in FP64 (flush_grad).
 template <int INTERP, class R>
 __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A, const AdjArgs B, const TileCfg tc)
 {
@@ -185,8 +147,6 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
     R sig = 0;
     R T[3] = {W.T0[0], W.T0[1], W.T0[2]};
     int iter = 0;
-    PendingAdd pend[4];
-    bool pending[4] = {false, false, false, false};
     while (true) {
         R tend = T[0];
         int e = 0;
@@ -231,14 +191,7 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
                 ne = nn[a];
             }
         if (INTERP == RR_TRILINEAR) {
-            // The 4 corners on the entry face along e leave the ray's cell.
-            // First the previous crossing's compensations are finished: their
-            // atomics have had this segment's arithmetic to return. Then this
-            // crossing's four atomics are issued; the values they return are
-            // used at the next crossing, or after the loop.
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-                if (pending[r]) finish_add(pend[r]);
+            // the 4 corners on the entry face along e leave the ray's cell
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int pb = r & 1, qb2 = r >> 1;
@@ -250,7 +203,7 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
 #pragma unroll
                 for (int mm = 0; mm < 8; ++mm)
                     if (mm == m) Sm = S[mm];
-                pending[r] = flush_grad_begin(B.grad, gx * sx + gy * sy + gz, Sm, gk, gb, w, pend[r]);
+                flush_grad(B.grad, gx * sx + gy * sy + gz, Sm, gk, gb, w);
             }
             if (e == 0) {
                 S[0] = S[1]; S[2] = S[3]; S[4] = S[5]; S[6] = S[7];
@@ -283,9 +236,6 @@ __global__ void __launch_bounds__(NT_MAX) trace_adjoint_kernel(const TraceArgs A
             break;
         }
     }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-        if (pending[r]) finish_add(pend[r]);
     // flush everything still pending
     if (INTERP == RR_TRILINEAR) {
 #pragma unroll

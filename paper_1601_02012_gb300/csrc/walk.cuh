@@ -6,6 +6,7 @@
 
 #include <math_constants.h>
 
+#include "fpbits.cuh"
 #include "rr_internal.h"
 
 namespace rr {
