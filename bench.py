@@ -44,11 +44,11 @@ L2_FLUSH_BYTES = 256 << 20
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), per
 # (kernel source, workload): valid only for the source it was taken on (sha256
 # of csrc/trace.cu + csrc/walk.cuh) and for that workload.
-TRACE_TRAFFIC = {("bb4db20400ea0c5f", "prod_512"): 275_203_968}
+TRACE_TRAFFIC = {("ef59478465a00d8d", "prod_512"): 276_398_848}
 # warp instructions per cell segment of one trace launch from the same kind of
 # ncu capture (smsp__inst_executed.sum / segments of the launch), per (kernel
 # source, workload); null in the line when the source differs
-TRACE_WARP_INSTRUCTIONS = {}
+TRACE_WARP_INSTRUCTIONS = {("ef59478465a00d8d", "prod_512"): 9.0933}
 
 # FP32 lane operations the method needs per trilinear segment, counted from its
 # formulas as the walk evaluates them: exit face (2 compares) and segment length
@@ -1128,7 +1128,7 @@ def main():
             fw = total_ms / args.steps
             bwd = {"ms_per_step": bw, "segments_per_s": segs / (bw / 1e3), "backward_over_forward": bw / fw,
                    "note": "rr_trace_backward over all steps: zero the gradient records, the adjoint of "
-                           "every step (compensated atomics), the transposed stencils into dL/dPhi; "
+                           "every step (warp sums added with FP64 atomics), the transposed stencils into dL/dPhi; "
                            "backward_over_forward against the forward pass of this line"}
             if world == 1 and not args.no_cpu_baseline:
                 # the gradient against the FP64 oracle's: dL/dkappa, dL/dkborn non-zero on sampled
@@ -1156,7 +1156,7 @@ def main():
                               "max_over_rms_support": float(np.abs(got - want).max() / rmsg),
                               "support_fraction": float(sup.mean()), "oracle_s": dto,
                               "note": "dL/dkappa and dL/dkborn standard normal on the sampled rays, zero "
-                                      "elsewhere; dL/dPhi on every cell, GPU (FP32, compensated atomics) "
+                                      "elsewhere; dL/dPhi on every cell, GPU (FP32 walk, FP64 atomic sums) "
                                       "against the FP64 oracle's adjoint; max difference over the rms of the "
                                       "gradient on the cells it reaches"}
             del gradbuf
