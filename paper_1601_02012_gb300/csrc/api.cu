@@ -509,7 +509,7 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     // (the footprint of the whole bundle holds the footprint of a band of it)
     rr_bundle_desc whole = b;
     whole.ny = ctx->ny_full;
-    const bool flat = form == kFormKahan && !(b.flags & RR_FP64_DDA) && flat_ok(whole, b.obs, *grid, chi_a, chi_b);
+    const bool flat = !(b.flags & RR_FP64_DDA) && flat_ok(whole, b.obs, *grid, chi_a, chi_b);
     cudaError_t e =
         launch_trace(a, b.interp, (b.flags & RR_FP64_DDA) != 0, (cudaStream_t)stream, TileCfg{}, form, flat);
     if (e != cudaSuccess) return from_cuda(e);

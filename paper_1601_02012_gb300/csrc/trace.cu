@@ -619,8 +619,15 @@ cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStre
     if (!tile_ok(t)) return cudaErrorInvalidValue;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const int nt = 32 * t.bwx * t.bwy;
-    if (flat && !fp64_dda && form == kFormKahan && interp == RR_TRILINEAR && a.periodic) {
-        trace_kernel<RR_TRILINEAR, float, kFormKahan, kAddrFlat><<<grid, nt, 0, s>>>(a, t);
+    if (flat && !fp64_dda && interp == RR_TRILINEAR && a.periodic) {
+        switch (form) {
+        case kFormPlain: trace_kernel<RR_TRILINEAR, float, kFormPlain, kAddrFlat><<<grid, nt, 0, s>>>(a, t); break;
+        case kFormMoments: trace_kernel<RR_TRILINEAR, float, kFormMoments, kAddrFlat><<<grid, nt, 0, s>>>(a, t); break;
+        case kFormGeneric: trace_kernel<RR_TRILINEAR, float, kFormGeneric, kAddrFlat><<<grid, nt, 0, s>>>(a, t); break;
+        case kFormMethodA: trace_kernel<RR_TRILINEAR, float, kFormMethodA, kAddrFlat><<<grid, nt, 0, s>>>(a, t); break;
+        case kFormShear: trace_kernel<RR_TRILINEAR, float, kFormShear, kAddrFlat><<<grid, nt, 0, s>>>(a, t); break;
+        default: trace_kernel<RR_TRILINEAR, float, kFormKahan, kAddrFlat><<<grid, nt, 0, s>>>(a, t); break;
+        }
         return cudaGetLastError();
     }
     if (fp64_dda)

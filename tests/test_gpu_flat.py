@@ -100,3 +100,78 @@ def test_flat_matches_batch_bitwise_and_oracle(rrp, oracle_lib):
         e_inf, e_2 = _map_err(got, want)
         assert e_inf <= TOL and e_2 <= TOL, (e_inf, e_2)
     assert abs(segs1 - int(ora.nseg.sum())) <= 1e-4 * ora.nseg.sum()
+
+
+def _assert_maps(pairs):
+    for got, want, what in pairs:
+        e_inf, e_2 = _map_err(got, want)
+        assert e_inf <= TOL and e_2 <= TOL, (what, e_inf, e_2)
+
+
+def test_flat_shear_form_matches_oracle(rrp, oracle_lib):
+    """The shear form (kappa, Born kappa, gamma1, gamma2 in one walk) on flat steps."""
+    import torch
+    g, b, steps = _case()
+    phi = synth.grf_phi(64, 128.0, 37)
+    k, kb, g1, g2, _ = rrp.trace_shear(torch.from_numpy(phi).cuda(), g, b, steps)
+    torch.cuda.synchronize()
+    H, d = oracle_lib.fields(g, phi.astype(np.float64))
+    ora = oracle_lib.trace(b, g, H, d, steps)
+    o1, o2 = oracle_lib.trace_shear(b, g, H, steps)
+    _assert_maps([(k.cpu().numpy(), ora.kappa, "kappa"), (kb.cpu().numpy(), ora.kborn, "kborn"),
+                  (g1.cpu().numpy(), o1, "gamma1"), (g2.cpu().numpy(), o2, "gamma2")])
+
+
+def test_flat_method_a_matches_oracle(rrp, oracle_lib):
+    """Method A (gradient records, the surface terms) on flat steps."""
+    import torch
+    g, b, steps = _case()
+    phi = synth.grf_phi(64, 128.0, 38)
+    k, kb, _ = rrp.trace_method_a(torch.from_numpy(phi).cuda(), g, b, steps)
+    torch.cuda.synchronize()
+    p64 = phi.astype(np.float64)
+    _, d = oracle_lib.fields(g, p64)
+    kg, kbo = oracle_lib.trace_method_a(b, g, oracle_lib.fields_grad(g, p64), d, steps)
+    _assert_maps([(k.cpu().numpy(), kg + kbo, "kappa"), (kb.cpu().numpy(), kbo, "kborn")])
+
+
+def test_flat_generic_form_matches_oracle(rrp, oracle_lib):
+    """Two scalar channels with their own quadratic kernels on flat steps."""
+    import torch
+    g, b, steps = _case()
+    q1 = synth.grf_phi(64, 128.0, 39) * 1e4
+    q2 = synth.random_field(g.n, 40, np.float32)
+    ker = ((0.7, -0.011, 0.00004), (-1.3, 0.02, -0.0001))
+    tr = rrp.Tracer(b, generic=True)
+    tr.set_kernels(ker)
+    rec = tr.record_buffer(g)
+    for st in steps:
+        tr.scalars(g, torch.from_numpy(np.ascontiguousarray(q1, np.float32)).cuda(), rec, 0)
+        tr.scalars(g, torch.from_numpy(np.ascontiguousarray(q2, np.float32)).cuda(), rec, 1)
+        tr.step(g, rec, st.chi_a, st.chi_b, st.scale, st.a)
+    o1, o2 = tr.finalize()
+    torch.cuda.synchronize()
+    tr.close()
+    w1, w2 = oracle_lib.trace_kq(b, g, q1.astype(np.float32).astype(np.float64),
+                                 q2.astype(np.float32).astype(np.float64), ker, steps)
+    _assert_maps([(o1.cpu().numpy(), w1, "ch0"), (o2.cpu().numpy(), w2, "ch1")])
+
+
+def test_flat_moments_form_matches_direct_traces(rrp, oracle_lib):
+    """The source-redshift moments on flat steps: kappa for the context's own
+    chi_s from the moments against the oracle's direct trace."""
+    import torch
+    g, b, steps = _case()
+    phi = synth.grf_phi(64, 128.0, 41)
+    ph = torch.from_numpy(phi).cuda()
+    tr = rrp.Tracer(b, moments=True)
+    rec = rrp.record_buffer(g)
+    for st in steps:
+        tr.tidal(g, ph, rec)
+        tr.step(g, rec, st.chi_a, st.chi_b, st.scale, st.a)
+    k, kb = tr.finalize()
+    torch.cuda.synchronize()
+    tr.close()
+    H, d = oracle_lib.fields(g, phi.astype(np.float64))
+    ora = oracle_lib.trace(b, g, H, d, steps)
+    _assert_maps([(k.cpu().numpy(), ora.kappa, "kappa"), (kb.cpu().numpy(), ora.kborn, "kborn")])
