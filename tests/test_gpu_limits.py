@@ -1,6 +1,6 @@
 """The largest sizes the interface accepts, against the oracle: a grid of 4096
-cells along x (the per-axis maximum) and an adaptive mesh refined to the
-deepest level (lmax = 8)."""
+cells along z (the per-axis maximum), an adaptive mesh refined to the deepest
+level (lmax = 8), and a 4096-ray bundle through a mesh refined six levels."""
 import math
 
 import numpy as np
@@ -66,6 +66,37 @@ def test_amr_refined_to_level_8(rrp, oracle_lib):
     b = synth.Bundle(15, 13, synth.deg(6), synth.deg(5), (box / 2 + 0.013, box / 2 - 0.021, 0.0), 60.0,
                      periodic=False)
     steps = [synth.Step(60.0, 31.0, 1.0, 1.0), synth.Step(31.0, 0.0, 1.0, 1.0)]
+    tr = rrp.Tracer(b)
+    for st in steps:
+        tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a)
+    k, kb = tr.finalize()
+    nseg = tr.segments()
+    tr.close()
+    gm.close()
+    o = oracle_lib.amr_trace(b, mesh, steps)
+    assert _err(k.cpu().numpy().ravel(), o.kappa) <= TOL
+    assert _err(kb.cpu().numpy().ravel(), o.kborn) <= TOL
+    assert abs(nseg - int(o.nseg.sum())) <= max(2, 1e-4 * o.nseg.sum())
+
+
+def test_amr_deep_levels_wide_bundle(rrp, oracle_lib):
+    """A lognormal-cascade mesh refined to lmax = 6 below a 16^3 coarse grid
+    (3279 / 2260 / 673 / 243 / 56 / 2 octs per level, 49 687 leaves) and 4096
+    rays over 40 x 40 deg through it, two steps: every ray against the oracle.
+    The FP32 walk starts each sub-step from a float-float point, where the
+    production AMR configuration asks for FP64 set-up at deep levels; this
+    checks that reading on the deepest levels and on many rays."""
+    mesh = synth.amr_random(16, 32.0, 6, 77, threshold=1.05, child_sigma=0.9)
+    assert all(len(mesh.octs[l]) > 0 for l in range(1, 7))
+    f = synth.fourier_fn(32.0, 40, 2 * math.pi / 32.0 * 5, 87)
+    mesh.phi = [np.asarray(p, np.float32).astype(np.float64) for p in synth.amr_sample(mesh, f)]
+    b = synth.Bundle(64, 64, synth.deg(40), synth.deg(40), (16.3, 15.8, 0.3), 45.0)
+    steps = [synth.Step(45.0, 19.0, 1.1, 0.8), synth.Step(19.0, 0.0, 0.95, 1.0)]
+    import torch
+    gm = rrp.AmrMesh(mesh.n, mesh.lmax, mesh.box, mesh.octs, mesh.omega_m)
+    flat = np.concatenate([np.asarray(p).reshape(-1) for p in mesh.phi]).astype(np.float32)
+    rec = gm.record_buffer()
+    gm.tidal(torch.from_numpy(flat).cuda(), rec)
     tr = rrp.Tracer(b)
     for st in steps:
         tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a)
