@@ -163,13 +163,22 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                         out = nq < 0 || nq >= NF;
                         q[a] = wrap_once(nq, NF);
                     } else if (W.v[a] > 0.f) {
-                        // counters are exact integers in float: the first crossing at or after tend
+                        // counters are exact integers in float: the first crossing at or
+                        // after tend (those before sig are counted already; the axis's own
+                        // exit, kmax, is not before tend). Nearly always zero or one more
+                        // crossing: tested one at a time; beyond that the closed form.
                         const float kmax = K[a] + (mf[a] - 1.f);
-                        float k = fminf(fmaxf(ceilf((tend - W.T0[a]) * W.v[a]), K[a]), kmax);
-                        while (k > K[a] && fmaf(k - 1.f, W.td[a], W.T0[a]) >= tend) k -= 1.f;
-                        while (k < kmax && fmaf(k, W.td[a], W.T0[a]) < tend) k += 1.f;
-                        q[a] = wrap_once(q[a] + W.sgn[a] * f2i_exact(k - K[a]), NF);
-                        K[a] = k;
+                        float k = K[a];
+                        if (k < kmax && fmaf(k, W.td[a], W.T0[a]) < tend) {
+                            k += 1.f;
+                            if (k < kmax && fmaf(k, W.td[a], W.T0[a]) < tend) {
+                                k = fminf(fmaxf(ceilf((tend - W.T0[a]) * W.v[a]), k + 1.f), kmax);
+                                while (k > K[a] + 2.f && fmaf(k - 1.f, W.td[a], W.T0[a]) >= tend) k -= 1.f;
+                                while (k < kmax && fmaf(k, W.td[a], W.T0[a]) < tend) k += 1.f;
+                            }
+                            q[a] = wrap_once(q[a] + W.sgn[a] * f2i_exact(k - K[a]), NF);
+                            K[a] = k;
+                        }
                     }
                 }
                 return out;
