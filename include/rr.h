@@ -166,7 +166,8 @@ rr_status rr_reset(rr_ctx* ctx, void* stream);
  *   delta  device, n0*n1*n2 floats, or NULL: the density contrast. When NULL
  *          it is derived from the same stencils through the comoving Poisson
  *          equation at a = 1: delta = tr(H) / (1.5 Omega_m (H0/c)^2).
- *   rec    device, n0*n1*n2 records of 8 floats (32 bytes, 16-byte aligned):
+ *   rec    device, n0*n1*n2 records of 8 floats (32 bytes, 32-byte aligned:
+ *          each record is written and read with one 32-byte access):
  *          {Hxx, Hyy, Hzz, Hxy}, {Hxz, Hyz, delta, 0}, H in (h/Mpc)^2.
  *   where  RR_AT_VERTICES or RR_AT_CENTRES.
  *   bbox   NULL for the whole grid, else 6 ints {x0, x1, y0, y1, z0, z1}:
@@ -270,9 +271,11 @@ rr_status rr_footprint_bbox(const rr_bundle_desc* bundle, const rr_grid_desc* gr
  *   kappa_born += scale * sum_cells I_c with Q = 1.5 Omega_m (H0/c)^2 delta / a_step
  *                 (first term of Eq. kappa2, a held constant over the step).
  *   rec      records from rr_tidal_tensor (vertices for RR_TRILINEAR,
- *            centres for RR_NGP) covering every point the step reads; for
- *            an RR_METHOD_A context, records from rr_gradient_records (the
- *            kappa channel then follows Method A, see RR_METHOD_A).
+ *            centres for RR_NGP; 32-byte aligned) covering every point the
+ *            step reads; for an RR_METHOD_A context, records from
+ *            rr_gradient_records (the kappa channel then follows Method A,
+ *            see RR_METHOD_A; 16-byte aligned), for an RR_GENERIC one, from
+ *            rr_scalar_records (16-byte aligned).
  *   scale    multiplies every channel of the records (the field of this step
  *            is scale * stored field).
  * Requires chi_s >= chi_a > chi_b >= 0 and, after the first step since
@@ -514,7 +517,8 @@ rr_status rr_amr_sizes(rr_amr* mesh, int64_t* ncells, int64_t* nleaves, int64_t*
  *      RR_AT_CENTRES: the leaf's own cell value.
  *   phi         device float [ncells], Phi/c^2 at cell centres in cell order.
  *   where       RR_AT_VERTICES (for RR_TRILINEAR) or RR_AT_CENTRES (RR_NGP).
- *   leaf_rec    device, 16-byte aligned: RR_AT_VERTICES 64 floats per leaf
+ *   leaf_rec    device, 16-byte aligned (32-byte aligned for the tidal records
+ *               that rr_amr_trace_step reads): RR_AT_VERTICES 64 floats per leaf
  *               (8 corners, corner dx + 2 dy + 4 dz, 8 floats each as in
  *               rr_tidal_tensor's records); RR_AT_CENTRES 8 floats per leaf.
  *   cell_tidal  device float [ncells x 8] or NULL: also receives step 1's

@@ -15,6 +15,8 @@ namespace {
 bool is_finite(double x) { return std::isfinite(x); }
 
 bool is_aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+// tidal records (32 B per point) are read and written with 32-byte vector accesses
+bool is_aligned32(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 31u) == 0; }
 
 rr_status from_cuda(cudaError_t e)
 {
@@ -161,7 +163,9 @@ rr_status validate_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     if (!ctx) return RR_ERR_ARG;
     rr_status st = check_grid(grid);
     if (st != RR_OK) return st;
-    if (!rec || !is_aligned16(rec)) return RR_ERR_ARG;
+    // tidal records (every form but Method A's gradient and the generic scalar records): 32-byte aligned
+    const bool tidal = !(ctx->bundle.flags & (RR_METHOD_A | RR_GENERIC));
+    if (!rec || !is_aligned16(rec) || (tidal && !is_aligned32(rec))) return RR_ERR_ARG;
     if (!is_finite(chi_a) || !is_finite(chi_b) || !is_finite(scale) || !is_finite(a_step) || !(a_step > 0))
         return RR_ERR_ARG;
     if (!(chi_a > chi_b) || chi_b < 0 || chi_a > ctx->bundle.chi_s * (1.0 + 1e-12)) return RR_ERR_ARG;
@@ -354,7 +358,7 @@ static rr_status point_records(const rr_grid_desc* grid, const float* phi, const
 {
     rr_status st = check_grid(grid);
     if (st != RR_OK) return st;
-    if (!phi || !rec || !is_aligned16(rec)) return RR_ERR_ARG;
+    if (!phi || !rec || !is_aligned16(rec) || (kind == 0 && !is_aligned32(rec))) return RR_ERR_ARG;
     if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
     if (bbox) {
         for (int a = 0; a < 3; ++a) {

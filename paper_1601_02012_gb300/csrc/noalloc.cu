@@ -81,7 +81,7 @@ extern "C" rr_status rr_trace_step_noalloc(const rr_bundle_desc* bundle, const r
     if (st != RR_OK) return st;
     if (bundle->flags & ~(RR_PERIODIC | RR_FP64_DDA)) return RR_ERR_ARG;
     if ((size_t)bundle->nx * (size_t)bundle->ny > kMaxRays) return RR_ERR_CAPACITY;
-    if (!rec || ((uintptr_t)rec & 15u) != 0) return RR_ERR_ARG;
+    if (!rec || ((uintptr_t)rec & 31u) != 0) return RR_ERR_ARG;
     if (!std::isfinite(chi_a) || !std::isfinite(chi_b) || !std::isfinite(scale) || !std::isfinite(a_step) ||
         !(a_step > 0))
         return RR_ERR_ARG;

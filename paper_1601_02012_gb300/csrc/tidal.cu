@@ -19,7 +19,11 @@
 // record written once: 36 algorithmic bytes per point. The gradient records
 // (KIND 1) take the same march with the three central first differences and
 // delta instead: one 16-byte record, 20 bytes per point.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "fpbits.cuh"
 #include "rr_internal.h"
@@ -87,6 +91,60 @@ __device__ __forceinline__ void centre_channels(float p0, float x0m, float x0p, 
     }
 }
 
+// one 32-byte tidal record {c0..c3}, {c4, c5, c6, 0} in a single 256-bit store
+// (the record buffers are 32-byte aligned: the entry points check it)
+__device__ __forceinline__ void store_rec(float4* r, float c0, float c1, float c2, float c3, float c4, float c5,
+                                          float c6)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "l"(r), "f"(c0), "f"(c1), "f"(c2), "f"(c3), "f"(c4), "f"(c5), "f"(c6), "f"(0.f) : "memory");
+}
+
+// ---- the potential planes by TMA --------------------------------------------
+// A plane tile of the ring: PY rows of RP floats (the centres' 34 columns plus
+// the rounding of the first one down to a multiple of 4, which a tensor copy
+// needs to start on a 16-byte boundary), slots 128-byte aligned.
+constexpr int RP = TZ + 8;                          // 40 floats per row
+constexpr int PYR = TY + 2;                         // 18 rows
+constexpr int SLOT = ((PYR * RP * 4 + 127) / 128) * 128 / 4;   // floats per ring slot
+constexpr int NSLOT = 5;                            // planes c - 1 .. c + 1 in use, c + 2, c + 3 arriving
+constexpr unsigned kWaitTries = 1u << 22;           // bound of every wait on a copy
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count));
+}
+
+// one tile of plane x = gx, rows y0 .., columns z0 .. of the potential into dst,
+// completing on bar (the issuing thread also arms bar with the byte count)
+__device__ __forceinline__ void tma_plane(const CUtensorMap* map, float* dst, unsigned long long* bar, int gx,
+                                          int y0, int z0)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(bar)), "r"((unsigned)(PYR * RP * 4)) : "memory");
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(smem_u32(dst)), "l"(map), "r"(z0), "r"(y0), "r"(gx), "r"(smem_u32(bar)) : "memory");
+}
+
+// waits until phase `parity` of bar has completed; false after kWaitTries polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    for (unsigned i = 0; i < kWaitTries; ++i) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // MODE 0: records at vertices (15 x 31 per CTA and plane); MODE 1: records at
 // centres (16 x 32). KIND 0: tidal records, 7 channels {Hxx, Hyy, Hzz, Hxy,
 // Hxz, Hyz, delta} in 2 float4; KIND 1: gradient records, 4 channels
@@ -95,19 +153,27 @@ __device__ __forceinline__ void centre_channels(float p0, float x0m, float x0p, 
 // share their middle rows, so 28 shared-memory reads serve two centres (19 for
 // one alone), and the vertex between the two rows sums its y pair in
 // registers.
+// TMA: the potential planes arrive in the ring by tensor copies (one thread
+// issues them two planes ahead, each completing on the slot's mbarrier), for
+// blocks whose tile needs no periodic wrap in y and z; the other blocks (at
+// the seam) and grids whose rows are not a multiple of 16 bytes load them
+// through registers, a plane ahead. A copy that does not complete within
+// kWaitTries polls makes the block write NaN records (the trace then reports
+// a non-finite sum) after waiting, bounded again, for its copies in flight.
 // (4 resident CTAs per SM: 64 registers; uncapped, 69 registers left 3 and
 // measured 9 % slower on a 512^3 grid)
-template <int MODE, int KIND>
-__global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
+template <int MODE, int KIND, bool TMA>
+__global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const __grid_constant__ CUtensorMap map)
 {
     constexpr int V = (MODE == 0) ? 1 : 0;
     constexpr int NC = KIND == 0 ? 7 : 4;            // channels
     constexpr int OY = TY - V, OZ = TZ - V;          // output points per CTA and plane
-    constexpr int PY = TY + 2, PZ = TZ + 2;          // potential per plane (halo 1 around the centres)
-    constexpr int NP = PY * PZ;
-    constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane
+    constexpr int PZ = TZ + 2;                       // potential columns a block needs (halo 1)
+    constexpr int NP = PYR * PZ;
+    constexpr int LP = (NP + NT - 1) / NT;           // potential loads per thread and plane (register path)
     constexpr int NW = NT / 32;                      // warps
-    __shared__ float ring[4][NP];   // potential planes c - 1, c, c + 1 and the one arriving (c + 2)
+    __shared__ __align__(128) float ring[NSLOT * SLOT];
+    __shared__ __align__(8) unsigned long long mbar[NSLOT];
     __shared__ float sP[2][MODE == 0 ? NC : 1][MODE == 0 ? NT : 1];   // z-pair sums of each warp's second row
 
     const int w = threadIdx.x / 32, tz = threadIdx.x % 32;
@@ -116,8 +182,15 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
     const int xb = blockIdx.z * a.xchunk, xe = min(xb + a.xchunk, a.ex);   // output planes [xb, xe)
     const int cy0 = a.y0 + py0 - V, cz0 = a.z0 + pz0 - V;                 // centre (0, 0) of the block
     const int c_first = a.x0 + xb - V, c_last = a.x0 + xe - 1;            // centre planes (unwrapped)
+    const int p0 = c_first - 1;                                           // first plane in the ring
 
-    // potential plane gx into registers / into a ring slot
+    // tensor copies for this block: rows cy0 - 1 .. cy0 + 16 and columns
+    // zs .. zs + 39 (zs: cz0 - 1 rounded down to a multiple of 4) inside the grid
+    const int zs = (cz0 - 1) & ~3;
+    const bool tma = TMA && cy0 - 1 >= 0 && cy0 - 1 + PYR <= a.n1 && cz0 - 1 >= 0 && zs + RP <= a.n2;
+    const int dz = tma ? (cz0 - 1) - zs : 0;                              // column of the tile's first centre - 1
+
+    // register path: potential plane gx into registers / into a ring slot
     int poff[LP];
 #pragma unroll
     for (int k = 0; k < LP; ++k) {
@@ -130,24 +203,38 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
 #pragma unroll
         for (int k = 0; k < LP; ++k) r[k] = poff[k] >= 0 ? __ldg(a.phi + base + poff[k]) : 0.f;
     };
-    auto put = [&](int slot, const float r[LP]) {
+    auto slot = [&](int p) { return (p - p0) % NSLOT; };
+    auto put = [&](int sl, const float r[LP]) {
 #pragma unroll
         for (int k = 0; k < LP; ++k) {
             const int i = threadIdx.x + k * NT;
-            if (i < NP) ring[slot][i] = r[k];
+            if (i < NP) ring[sl * SLOT + (i / PZ) * RP + (i % PZ)] = r[k];
         }
     };
-    // ring slot of plane p
-    auto slot = [&](int p) { return (p - (c_first - 1)) & 3; };
-    float nxt[LP];   // the plane two ahead of the current one, on its way to the ring
-    {
+    // TMA path: plane p into its slot (thread 0), and the wait for it (all)
+    auto issue = [&](int p) {
+        tma_plane(&map, ring + slot(p) * SLOT, &mbar[slot(p)], wrapi(p, a.n0), cy0 - 1, zs);
+    };
+    auto arrived = [&](int p) { return mbar_wait(&mbar[slot(p)], (unsigned)(((p - p0) / NSLOT) & 1)); };
+    bool ok = true;   // every wait of this thread ended with its copy
+
+    float nxt[LP];   // register path: the plane two ahead of the current one, on its way to the ring
+    if (tma) {
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < NSLOT; ++k) mbar_init(&mbar[k], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            for (int p = p0; p <= p0 + 3 && p <= c_last + 1; ++p) issue(p);
+        }
+        __syncthreads();
+        ok = arrived(p0) && arrived(p0 + 1);
+    } else {
         float r[LP];
-        fetch(c_first - 1, r); put(0, r);
-        fetch(c_first, r); put(1, r);
-        fetch(c_first + 1, r); put(2, r);
-        fetch(c_first + 2, nxt);
+        fetch(p0, r); put(slot(p0), r);
+        fetch(p0 + 1, r); put(slot(p0 + 1), r);
+        fetch(p0 + 2, r); put(slot(p0 + 2), r);
+        fetch(p0 + 3, nxt);
+        __syncthreads();
     }
-    __syncthreads();
 
     // outputs: centre rows r0 and r0 + 1 (MODE 1), or the vertices on rows r0
     // and r0 + 1 (MODE 0: vertex row r is the upper corner of centre rows
@@ -163,7 +250,7 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
         out_ok[k] = oz_ok && (r0 + k) >= V && oy[k] < a.ey;
         out_off[k] = out_ok[k] ? (size_t)wrapi(a.y0 + oy[k], a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2) : 0;
     }
-    const int o = (r0 + 1) * PZ + (tz + 1);          // first centre in the ring
+    const int o = (r0 + 1) * RP + (tz + 1) + dz;     // first centre in a ring slot
     size_t d_yz[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) d_yz[k] = (size_t)wrapi(cy0 + r0 + k, a.n1) * a.n2 + wrapi(cz0 + tz, a.n2);
@@ -173,19 +260,28 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
 #pragma unroll
         for (int q = 0; q < NC; ++q) prev[k][q] = 0.f;
     for (int c = c_first; c <= c_last; ++c) {
-        const float* P0 = ring[slot(c - 1)];
-        const float* P1 = ring[slot(c)];
-        const float* P2 = ring[slot(c + 1)];
-        // plane c + 2 goes into the slot of plane c - 2 (read last iteration,
-        // before its barrier); plane c + 3 is fetched into registers, a whole
-        // plane of work ahead of its use
+        const float* P0 = ring + slot(c - 1) * SLOT;
+        const float* P1 = ring + slot(c) * SLOT;
+        const float* P2 = ring + slot(c + 1) * SLOT;
         float nxt2[LP];
-        if (c + 3 <= c_last + 1) fetch(c + 3, nxt2);
-        if (c + 2 <= c_last + 1) put(slot(c + 2), nxt);
+        if (tma) {
+            // plane c + 3 into the slot of plane c - 2, read before the last barrier
+            if (threadIdx.x == 0 && c + 3 <= c_last + 1) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(c + 3);
+            }
+            ok = arrived(c + 1) && ok;
+        } else {
+            // plane c + 2 goes into the slot of plane c - 3 (read before the last
+            // barrier); plane c + 3 is fetched into registers, a whole plane of
+            // work ahead of its use
+            if (c + 3 <= c_last + 1) fetch(c + 3, nxt2);
+            if (c + 2 <= c_last + 1) put(slot(c + 2), nxt);
+        }
 
         // the two stencils: rows r0 - 1 .. r0 + 2 of P1 at z - 1 .. z + 1, rows
         // r0 - 1 .. r0 + 2 of P0 and P2 at z, rows r0, r0 + 1 of P0 and P2 at z +- 1
-        const int om = o - PZ, o1 = o + PZ, op = o + 2 * PZ;
+        const int om = o - RP, o1 = o + RP, op = o + 2 * RP;
         const float a_m0 = P1[om - 1], a_m1 = P1[om], a_m2 = P1[om + 1];
         const float a_00 = P1[o - 1], a_01 = P1[o], a_02 = P1[o + 1];
         const float a_10 = P1[o1 - 1], a_11 = P1[o1], a_12 = P1[o1 + 1];
@@ -207,6 +303,12 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
         // centre (r0 + 1, z): y neighbours rows r0, r0 + 2
         centre_channels<KIND>(a_11, b_1, c_1, a_01, a_p1, a_10, a_12, c_p - c_0, b_0 - b_p, c_1p - c_1m, b_1m - b_1p,
                               a_p2 - a_p0, a_00 - a_02, dl[1], a.delta != nullptr, a, h[1]);
+        if (!ok) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int q = 0; q < NC; ++q) h[k][q] = __int_as_float(0x7fc00000);
+        }
 
         float pz[2][NC];
         if constexpr (MODE == 0) {
@@ -220,9 +322,9 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
                 for (int q = 0; q < NC; ++q) sP[(c - c_first) & 1][q][threadIdx.x] = pz[1][q];
             }
         }
-        // plane c + 2 is in the ring and the second-row z pairs of plane c are
-        // shared; the next iteration writes the other sP buffer and a ring slot
-        // not read here
+        // the plane that arrives next is in the ring and the second-row z pairs
+        // of plane c are shared; the next iteration writes the other sP buffer
+        // and a ring slot not read here
         __syncthreads();
         if constexpr (MODE == 0) {
             // vertex row r0 + 1: centre rows r0 and r0 + 1 (this thread); vertex
@@ -238,11 +340,10 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
                 if (c > c_first && out_ok[k]) {
                     const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_off[k];
                     if constexpr (KIND == 0) {
-                        float4* r = a.rec + 2 * pt;
-                        r[0] = make_float4((prev[k][0] + b[k][0]) * 0.125f, (prev[k][1] + b[k][1]) * 0.125f,
-                                           (prev[k][2] + b[k][2]) * 0.125f, (prev[k][3] + b[k][3]) * 0.125f);
-                        r[1] = make_float4((prev[k][4] + b[k][4]) * 0.125f, (prev[k][5] + b[k][5]) * 0.125f,
-                                           (prev[k][6] + b[k][6]) * 0.125f, 0.f);
+                        store_rec(a.rec + 2 * pt, (prev[k][0] + b[k][0]) * 0.125f, (prev[k][1] + b[k][1]) * 0.125f,
+                                  (prev[k][2] + b[k][2]) * 0.125f, (prev[k][3] + b[k][3]) * 0.125f,
+                                  (prev[k][4] + b[k][4]) * 0.125f, (prev[k][5] + b[k][5]) * 0.125f,
+                                  (prev[k][6] + b[k][6]) * 0.125f);
                     } else {
                         a.rec[pt] = make_float4((prev[k][0] + b[k][0]) * 0.125f, (prev[k][1] + b[k][1]) * 0.125f,
                                                 (prev[k][2] + b[k][2]) * 0.125f, (prev[k][3] + b[k][3]) * 0.125f);
@@ -257,16 +358,21 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a)
                 if (!out_ok[k]) continue;
                 const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_off[k];
                 if constexpr (KIND == 0) {
-                    float4* r = a.rec + 2 * pt;
-                    r[0] = make_float4(h[k][0], h[k][1], h[k][2], h[k][3]);
-                    r[1] = make_float4(h[k][4], h[k][5], h[k][6], 0.f);
+                    store_rec(a.rec + 2 * pt, h[k][0], h[k][1], h[k][2], h[k][3], h[k][4], h[k][5], h[k][6]);
                 } else {
                     a.rec[pt] = make_float4(h[k][0], h[k][1], h[k][2], h[k][3]);
                 }
             }
         }
+        if (!tma) {
 #pragma unroll
-        for (int k = 0; k < LP; ++k) nxt[k] = nxt2[k];
+            for (int k = 0; k < LP; ++k) nxt[k] = nxt2[k];
+        }
+    }
+    if (tma && __syncthreads_or(!ok) && threadIdx.x == 0) {
+        // a copy did not complete in time: wait (bounded) for every copy this
+        // block issued before its shared memory is released
+        for (int p = p0; p <= c_last + 1; ++p) mbar_wait(&mbar[slot(p)], (unsigned)(((p - p0) / NSLOT) & 1));
     }
 }
 
@@ -434,6 +540,44 @@ cudaError_t launch_scalar_records(const rr_grid_desc& g, const float* field, con
     return cudaGetLastError();
 }
 
+namespace {
+
+// The driver's tensor-map encoder, looked up once through the runtime (the
+// library links no driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of the potential (dims z, y, x; box RP x PYR x 1 floats) for the
+// tidal kernel's plane copies, when the rows are a multiple of 16 bytes, the
+// grid is at least one box wide and the encoder is available.
+bool phi_tensor_map(const rr_grid_desc& g, const float* phi, CUtensorMap* map)
+{
+    if (g.n[2] % 4 != 0 || g.n[2] < RP || g.n[1] < PYR || (reinterpret_cast<uintptr_t>(phi) & 15u)) return false;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.n[2], (cuuint64_t)g.n[1], (cuuint64_t)g.n[0]};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.n[2] * 4, (cuuint64_t)g.n[2] * g.n[1] * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)RP, (cuuint32_t)PYR, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(phi), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
                          const int32_t* bbox, cudaStream_t s, int kind)
 {
@@ -469,13 +613,22 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
     const long long want = (long long)a.ex * tiles_yz / (2LL * nsm);
     a.xchunk = (int)std::max(2LL, std::min((long long)XCHUNK_MAX, want));
     dim3 grid((a.ez + oz - 1) / oz, (a.ey + oy - 1) / oy, (a.ex + a.xchunk - 1) / a.xchunk);
+    CUtensorMap map;
+    const bool tma = phi_tensor_map(g, phi, &map);
+    if (!tma) memset(&map, 0, sizeof(map));
+#define RR_TIDAL_LAUNCH(M, K)                                                        \
+    do {                                                                              \
+        if (tma) tidal_kernel<M, K, true><<<grid, NT, 0, s>>>(a, map);                \
+        else tidal_kernel<M, K, false><<<grid, NT, 0, s>>>(a, map);                  \
+    } while (0)
     if (kind == 0) {
-        if (where == RR_AT_VERTICES) tidal_kernel<0, 0><<<grid, NT, 0, s>>>(a);
-        else tidal_kernel<1, 0><<<grid, NT, 0, s>>>(a);
+        if (where == RR_AT_VERTICES) RR_TIDAL_LAUNCH(0, 0);
+        else RR_TIDAL_LAUNCH(1, 0);
     } else {
-        if (where == RR_AT_VERTICES) tidal_kernel<0, 1><<<grid, NT, 0, s>>>(a);
-        else tidal_kernel<1, 1><<<grid, NT, 0, s>>>(a);
+        if (where == RR_AT_VERTICES) RR_TIDAL_LAUNCH(0, 1);
+        else RR_TIDAL_LAUNCH(1, 1);
     }
+#undef RR_TIDAL_LAUNCH
     return cudaGetLastError();
 }
 

@@ -204,6 +204,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     auto fetch = [&](long long i) -> PR {
         if constexpr (MA) return load_grad_rec(A.rec, i);
         else if constexpr (GEN) return __ldg(reinterpret_cast<const float2*>(A.rec) + i);
+        else if constexpr (FLAT) return load_rec32(A.rec, i);
         else return load_rec(A.rec, i);
     };
     // (the channel pair the walk integrates) of a record
@@ -405,25 +406,38 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                                 ? segment_trilinear(g2, u[0], u[1], u[2], v[0], v[1], v[2], t, G0, G1, G2)
                                 : segment_ngp(g2[0], t, G0, G1, G2));
             } else {
-                // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry point
-                const R chiA = chiA0 - sig;
-                const R G0 = (D0 + sig) * chiA * ichis;
-                const R G1 = (2 * chiA - chis) * ichis;
-                const R G2 = -ichis;
-                const R t2 = t * t;
-                const R J1 = t * (G0 + t * (G1 * (R)0.5 + t * G2 * (R)(1.0 / 3.0)));
+                // lensing kernel g(chi_A - s) = G0 + G1 s + G2 s^2 about the entry
+                // point; J_N and the sums rounded as written (the single-launch and
+                // the batch kernels must give the same values)
+                const double chiA = chiA0 - sig;
+                const double G0 = (D0 + sig) * chiA * ichis;
+                const double G1 = __dmul_rn(__fma_rn(2.0, chiA, -(double)chis), ichis);
+                const double G2 = -ichis;
+                const double t2 = __dmul_rn(t, t);
+                const double tn[4] = {t, t2, __dmul_rn(t2, t), __dmul_rn(t2, t2)};
+                const double ca[4] = {1.0, 0.5, 1.0 / 3.0, 0.25};
+                const double cb[4] = {0.5, 1.0 / 3.0, 0.25, 0.2};
+                const double cc[4] = {1.0 / 3.0, 0.25, 0.2, 1.0 / 6.0};
+                double J[4];
+#pragma unroll
+                for (int n = 0; n < 4; ++n)
+                    J[n] = __dmul_rn(tn[n], __fma_rn(t, __fma_rn(t, __dmul_rn(G2, cc[n]), __dmul_rn(G1, cb[n])),
+                                                   __dmul_rn(G0, ca[n])));
                 if (INTERP == RR_TRILINEAR) {
-                    const R J2 = t2 * (G0 * (R)0.5 + t * (G1 * (R)(1.0 / 3.0) + t * G2 * (R)0.25));
-                    const R J3 = t2 * t * (G0 * (R)(1.0 / 3.0) + t * (G1 * (R)0.25 + t * G2 * (R)0.2));
-                    const R J4 = t2 * t2 * (G0 * (R)0.25 + t * (G1 * (R)0.2 + t * G2 * (R)(1.0 / 6.0)));
                     float2 e2[4];
                     line_cubic2(q2, bc2((float)u[0]), bc2((float)u[1]), bc2((float)u[2]), bc2((float)v[0]),
                                 bc2((float)v[1]), bc2((float)v[2]), e2);
-                    sk.add((R)e2[0].x * J1 + (R)e2[1].x * J2 + (R)e2[2].x * J3 + (R)e2[3].x * J4);
-                    sb.add((R)e2[0].y * J1 + (R)e2[1].y * J2 + (R)e2[2].y * J3 + (R)e2[3].y * J4);
+                    double xk = __dmul_rn((double)e2[0].x, J[0]), xb = __dmul_rn((double)e2[0].y, J[0]);
+#pragma unroll
+                    for (int n = 1; n < 4; ++n) {
+                        xk = __fma_rn((double)e2[n].x, J[n], xk);
+                        xb = __fma_rn((double)e2[n].y, J[n], xb);
+                    }
+                    sk.add((R)xk);
+                    sb.add((R)xb);
                 } else {
-                    sk.add((R)q2[0].x * J1);
-                    sb.add((R)q2[0].y * J1);
+                    sk.add((R)__dmul_rn((double)q2[0].x, J[0]));
+                    sb.add((R)__dmul_rn((double)q2[0].y, J[0]));
                 }
             }
             if (resume) resume = false;

@@ -199,6 +199,7 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
                     const float4* r = A.rec + 16 * (long long)leaf;
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
+                        // (two 16-byte loads: one 32-byte load per corner measured 3 % slower here)
                         const int rc = c ^ flip;
                         Rec x;
                         x.a = __ldg(r + 2 * rc);

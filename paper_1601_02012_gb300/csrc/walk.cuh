@@ -68,6 +68,18 @@ __device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, long lon
     return r;
 }
 
+// one 32-byte tidal record in a single 256-bit load (the record buffers are
+// 32-byte aligned: the entry points check it); faster than two 16-byte loads
+// in the flat-addressed walk, slower in the others
+__device__ __forceinline__ Rec load_rec32(const float4* __restrict__ rec, long long idx)
+{
+    Rec r;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r.a.x), "=f"(r.a.y), "=f"(r.a.z), "=f"(r.a.w), "=f"(r.b.x), "=f"(r.b.y), "=f"(r.b.z), "=f"(r.b.w)
+        : "l"(rec + 2 * idx));
+    return r;
+}
+
 // A gradient record of Method A: one float4 {d_x Phi, d_y Phi, d_z Phi, delta}
 // per point.
 __device__ __forceinline__ float4 load_grad_rec(const float4* __restrict__ rec, long long idx)
@@ -211,23 +223,36 @@ __device__ __forceinline__ void kernel_coeffs(float t, float sig, float chiA0, f
 {
     const float chiA = chiA0 - sig;
     G0 = (D0 + sig) * chiA * ichis;
-    G1 = (2.f * chiA - chis) * ichis;
+    G1 = __fmul_rn(__fmaf_rn(2.f, chiA, -chis), ichis);
     G2 = -ichis;
+}
+
+// J_N = int_0^t (G0 + G1 s + G2 s^2) s^(N-1) ds = t^N (G0 / N + t (G1 / (N + 1)
+// + t G2 / (N + 2))) for N = 1..4, every operation rounded as written (no
+// contraction left to the compiler, so every kernel that inlines this gives
+// the same values)
+__device__ __forceinline__ void j_moments(float t, float G0, float G1, float G2, float J[4])
+{
+    const float t2 = __fmul_rn(t, t);
+    const float tG2 = __fmul_rn(t, G2);
+    J[0] = __fmul_rn(t, __fmaf_rn(t, __fmaf_rn(G1, 0.5f, __fmul_rn(tG2, 1.f / 3.f)), G0));
+    J[1] = __fmul_rn(t2, __fmaf_rn(t, __fmaf_rn(G1, 1.f / 3.f, __fmul_rn(tG2, 0.25f)), __fmul_rn(G0, 0.5f)));
+    J[2] = __fmul_rn(__fmul_rn(t2, t),
+                     __fmaf_rn(t, __fmaf_rn(G1, 0.25f, __fmul_rn(tG2, 0.2f)), __fmul_rn(G0, 1.f / 3.f)));
+    J[3] = __fmul_rn(__fmul_rn(t2, t2),
+                     __fmaf_rn(t, __fmaf_rn(G1, 0.2f, __fmul_rn(tG2, 1.f / 6.f)), __fmul_rn(G0, 0.25f)));
 }
 
 // sum_N e_{N-1} J_N for the cubic e (pair channels) and the quadratic kernel
 // G0 + G1 s + G2 s^2 over [0, t]
 __device__ __forceinline__ float2 dot_kernel(const float2 e2[4], float t, float G0, float G1, float G2)
 {
-    const float t2 = t * t;
-    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
-    const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
-    const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
-    const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
-    float2 x = __fmul2_rn(e2[0], bc2(J1));
-    x = __ffma2_rn(e2[1], bc2(J2), x);
-    x = __ffma2_rn(e2[2], bc2(J3), x);
-    return __ffma2_rn(e2[3], bc2(J4), x);
+    float J[4];
+    j_moments(t, G0, G1, G2, J);
+    float2 x = __fmul2_rn(e2[0], bc2(J[0]));
+    x = __ffma2_rn(e2[1], bc2(J[1]), x);
+    x = __ffma2_rn(e2[2], bc2(J[2]), x);
+    return __ffma2_rn(e2[3], bc2(J[3]), x);
 }
 
 __device__ __forceinline__ float2 segment_trilinear(const float2 q[8], float u0, float u1, float u2, float v0,
@@ -244,20 +269,13 @@ __device__ __forceinline__ float2 segment_trilinear(const float2 q[8], float u0,
 // int_0^t K s^(N-1) ds.
 __device__ __forceinline__ float2 dot_kernel_a(const float2 e2[4], float t, float G0, float G1, float G2)
 {
-    const float t2 = t * t;
-    const float K0 = -G1, K1 = -2.f * G2;
-    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
-    const float J2 = t2 * (G0 * 0.5f + t * (G1 * (1.f / 3.f) + t * G2 * 0.25f));
-    const float J3 = t2 * t * (G0 * (1.f / 3.f) + t * (G1 * 0.25f + t * G2 * 0.2f));
-    const float J4 = t2 * t2 * (G0 * 0.25f + t * (G1 * 0.2f + t * G2 * (1.f / 6.f)));
-    const float L1 = t * (K0 + t * K1 * 0.5f);
-    const float L2 = t2 * (K0 * 0.5f + t * K1 * (1.f / 3.f));
-    const float L3 = t2 * t * (K0 * (1.f / 3.f) + t * K1 * 0.25f);
-    const float L4 = t2 * t2 * (K0 * 0.25f + t * K1 * 0.2f);
-    float2 x = __fmul2_rn(e2[0], make_float2(L1, J1));
-    x = __ffma2_rn(e2[1], make_float2(L2, J2), x);
-    x = __ffma2_rn(e2[2], make_float2(L3, J3), x);
-    return __ffma2_rn(e2[3], make_float2(L4, J4), x);
+    float J[4], Lk[4];
+    j_moments(t, G0, G1, G2, J);
+    j_moments(t, -G1, -2.f * G2, 0.f, Lk);   // K = dg/dchi: K0 = -G1, K1 = -2 G2
+    float2 x = __fmul2_rn(e2[0], make_float2(Lk[0], J[0]));
+    x = __ffma2_rn(e2[1], make_float2(Lk[1], J[1]), x);
+    x = __ffma2_rn(e2[2], make_float2(Lk[2], J[2]), x);
+    return __ffma2_rn(e2[3], make_float2(Lk[3], J[3]), x);
 }
 
 __device__ __forceinline__ float2 segment_trilinear_a(const float2 q[8], float u0, float u1, float u2, float v0,
@@ -270,9 +288,10 @@ __device__ __forceinline__ float2 segment_trilinear_a(const float2 q[8], float u
 
 __device__ __forceinline__ float2 segment_ngp_a(float2 q, float t, float G0, float G1, float G2)
 {
-    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
-    const float L1 = t * (-G1 - t * G2);
-    return __fmul2_rn(q, make_float2(L1, J1));
+    float J[4], Lk[4];
+    j_moments(t, G0, G1, G2, J);
+    j_moments(t, -G1, -2.f * G2, 0.f, Lk);
+    return __fmul2_rn(q, make_float2(Lk[0], J[0]));
 }
 
 // Two channels with their own quadratic kernels, K_c(chi_A - s) = G0c + G1c s
@@ -306,8 +325,9 @@ __device__ __forceinline__ float trilinear_x(const float2 q[8], float u0, float 
 
 __device__ __forceinline__ float2 segment_ngp(float2 q, float t, float G0, float G1, float G2)
 {
-    const float J1 = t * (G0 + t * (G1 * 0.5f + t * G2 * (1.f / 3.f)));
-    return __fmul2_rn(q, bc2(J1));
+    float J[4];
+    j_moments(t, G0, G1, G2, J);
+    return __fmul2_rn(q, bc2(J[0]));
 }
 
 // Q weights of the shear (Eqs. gamma1, gamma2) for the direction n = (sin th
@@ -327,16 +347,17 @@ __device__ __forceinline__ void shear_weights(float4 n, float w1[6], float w2[6]
     }
     const float fx = -sp, fy = cp;                          // e_phi
     const float tx = n.z * cp, ty = n.z * sp, tz = -st;     // e_theta
-    w1[0] = fx * fx - tx * tx;
-    w1[1] = fy * fy - ty * ty;
+    // (every sum of products rounded as written: no contraction left to the compiler)
+    w1[0] = __fsub_rn(__fmul_rn(fx, fx), __fmul_rn(tx, tx));
+    w1[1] = __fsub_rn(__fmul_rn(fy, fy), __fmul_rn(ty, ty));
     w1[2] = -tz * tz;
-    w1[3] = 2.f * (fx * fy - tx * ty);
+    w1[3] = 2.f * __fsub_rn(__fmul_rn(fx, fy), __fmul_rn(tx, ty));
     w1[4] = -2.f * tx * tz;
     w1[5] = -2.f * ty * tz;
     w2[0] = 2.f * fx * tx;
     w2[1] = 2.f * fy * ty;
     w2[2] = 0.f;
-    w2[3] = 2.f * (fx * ty + fy * tx);
+    w2[3] = 2.f * __fadd_rn(__fmul_rn(fx, ty), __fmul_rn(fy, tx));
     w2[4] = 2.f * fx * tz;
     w2[5] = 2.f * fy * tz;
 }
@@ -567,9 +588,10 @@ __device__ __forceinline__ void walk_setup(const TraceArgs& A, long long rid, fl
         vhi[a] = sgn[a] > 0 ? up : c[a];
     }
     float* w = W.w;
-    w[0] = nh[1] * nh[1] + nh[2] * nh[2];
-    w[1] = nh[0] * nh[0] + nh[2] * nh[2];
-    w[2] = nh[0] * nh[0] + nh[1] * nh[1];
+    // (sums of products rounded as written: every kernel gets the same weights)
+    w[0] = __fadd_rn(__fmul_rn(nh[1], nh[1]), __fmul_rn(nh[2], nh[2]));
+    w[1] = __fadd_rn(__fmul_rn(nh[0], nh[0]), __fmul_rn(nh[2], nh[2]));
+    w[2] = __fadd_rn(__fmul_rn(nh[0], nh[0]), __fmul_rn(nh[1], nh[1]));
     w[3] = -2.f * nh[0] * nh[1];
     w[4] = -2.f * nh[0] * nh[2];
     w[5] = -2.f * nh[1] * nh[2];

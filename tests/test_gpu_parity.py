@@ -64,10 +64,12 @@ def run_oracle(oracle_lib, phi, grid, bundle, steps, delta=None, rids=None):
 
 @pytest.mark.parametrize("where", ["vertices", "centres"])
 @pytest.mark.parametrize("with_delta", [False, True])
-@pytest.mark.parametrize("shape", [(24, 20, 40), (2, 3, 5), (5, 2, 33)])
+@pytest.mark.parametrize("shape", [(24, 20, 40), (2, 3, 5), (5, 2, 33), (40, 52, 96)])
 def test_tidal_records(rrpkg, oracle_lib, where, with_delta, shape):
     """Every record of the grid against the oracle's stencils and vertex means;
-    also grids smaller than a CTA's 8 x 32 block (indices wrap several times)."""
+    also grids smaller than a CTA's 8 x 32 block (indices wrap several times),
+    and one whose inner blocks take their potential planes by tensor copies
+    (rows a multiple of 16 bytes, tiles clear of the periodic seam)."""
     import torch
     g = synth.Grid(shape, 2.0 * shape[0])
     phi = synth.random_field(g.n, 7, np.float32)
@@ -89,6 +91,26 @@ def test_tidal_records(rrpkg, oracle_lib, where, with_delta, shape):
         scale = np.abs(want[..., c]).max()
         err = np.abs(got[..., c] - want[..., c]).max()
         assert err <= 4e-6 * scale, (c, err / scale)
+
+
+def test_tidal_bbox_on_tensor_copy_blocks(rrpkg):
+    """Boxes away from the seam (all blocks take tensor copies) and across it:
+    the records in the box equal the whole grid's, bit for bit."""
+    import torch
+    g = synth.Grid((64, 64, 128), 128.0)
+    phi = torch.from_numpy(synth.random_field(g.n, 19, np.float32)).cuda()
+    full = rrpkg.record_buffer(g)
+    rrpkg.rr_tidal_tensor(rrpkg.grid_desc(g), phi, None, full, rrpkg.RR_AT_VERTICES)
+    f = full.cpu().numpy().reshape(64, 64, 128, 8)
+    for bbox in ((10, 30, 7, 45, 17, 99), (-5, 9, 50, 70, 100, 140)):
+        part = torch.full_like(full, float("nan"))
+        rrpkg.rr_tidal_tensor(rrpkg.grid_desc(g), phi, None, part, rrpkg.RR_AT_VERTICES, bbox)
+        p = part.cpu().numpy().reshape(64, 64, 128, 8)
+        mask = np.zeros((64, 64, 128), bool)
+        mask[np.ix_(np.arange(bbox[0], bbox[1]) % 64, np.arange(bbox[2], bbox[3]) % 64,
+                    np.arange(bbox[4], bbox[5]) % 128)] = True
+        assert np.array_equal(p[mask], f[mask])
+        assert np.all(np.isnan(p[~mask]))
 
 
 def test_tidal_bbox_writes_only_the_box(rrpkg):
