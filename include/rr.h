@@ -385,10 +385,16 @@ rr_status rr_tidal_tensor_adjoint(const rr_grid_desc* grid, const float* grad_re
 /*
  * dL/dPhi for maps traced from one potential: all logged steps must share one
  * grid and their records must come from the same phi (each step's field being
- * scale_k * that phi). Zeroes grad_rec (caller scratch, n0*n1*n2 gradient
- * records of 64 B), adds the adjoint of every logged step, then applies
- * rr_tidal_tensor_adjoint into dL_dphi (accumulated) / dL_ddelta (NULL: delta
- * derived from phi). RR_ERR_STATE if no step was traced or the grids differ.
+ * scale_k * that phi). grad_rec is caller scratch (n0*n1*n2 gradient records of
+ * 64 B, 16-byte aligned). The call zeroes the records of the points the logged
+ * steps can reach (the union of their footprint boxes, rr_footprint_bbox of the
+ * whole bundle, widened by the stencils' reach; the whole grid when that union
+ * spans it), adds the adjoint of every logged step, then applies
+ * rr_tidal_tensor_adjoint over the cells within the stencils' reach of that
+ * union (every other cell's gradient is zero) into dL_dphi (accumulated) /
+ * dL_ddelta (NULL: delta derived from phi). Records outside the zeroed box are
+ * neither read nor written. RR_ERR_STATE if no step was traced or the grids
+ * differ.
  */
 rr_status rr_trace_backward(rr_ctx* ctx, const double* dL_dkappa, const double* dL_dkborn, float* grad_rec,
                             float* dL_dphi, float* dL_ddelta, void* stream);

@@ -634,15 +634,43 @@ rr_status rr_trace_backward(rr_ctx* ctx, const double* dL_dkappa, const double* 
         if (r.amr || r.grid.n[0] != g.n[0] || r.grid.n[1] != g.n[1] || r.grid.n[2] != g.n[2] || r.grid.box != g.box ||
             r.grid.omega_m != g.omega_m)
             return RR_ERR_STATE;
-    const size_t npts = (size_t)g.n[0] * g.n[1] * g.n[2];
-    cudaError_t e = cudaMemsetAsync(grad_rec, 0, npts * 16 * sizeof(float), (cudaStream_t)stream);
+    if (!is_aligned16(grad_rec)) return RR_ERR_ARG;
+    // The adjoint of a step adds only to the points its rays' cells touch,
+    // which lie in the step's footprint box (the box the forward computes its
+    // records over), so only the union U of those boxes is non-zero and only
+    // the cells within the stencils' reach of U get a gradient. Vertices: a
+    // cell's dL/dPhi reads the records of the points m - 1 .. m + 2 per axis
+    // (the 8-vertex mean, then the +-1 central differences), so the output
+    // box is U widened by 2 below and 1 above, and the records it reads (all
+    // zeroed here) U widened by 3 on both sides; centres: 1 and 1, 2 and 2.
+    rr_bundle_desc whole = ctx->bundle;
+    whole.ny = ctx->ny_full;
+    long long u0[3], u1[3];
+    for (size_t k = 0; k < ctx->log.size(); ++k) {
+        const StepRecord& r = ctx->log[k];
+        long long b0[3], b1[3];
+        footprint_box(whole, r.obs, r.grid, r.chi_a, r.chi_b, b0, b1);
+        for (int a = 0; a < 3; ++a) {
+            u0[a] = k ? std::min(u0[a], b0[a]) : b0[a];
+            u1[a] = k ? std::max(u1[a], b1[a]) : b1[a];
+        }
+    }
+    const bool vert = ctx->bundle.interp == RR_TRILINEAR;
+    long long z0[3], z1[3], o0[3], o1[3];
+    for (int a = 0; a < 3; ++a) {
+        z0[a] = u0[a] - (vert ? 3 : 2);
+        z1[a] = u1[a] + (vert ? 3 : 2);
+        o0[a] = u0[a] - (vert ? 2 : 1);
+        o1[a] = u1[a] + 1;
+    }
+    cudaError_t e = zero_grad_records(g, grad_rec, z0, z1, (cudaStream_t)stream);
     if (e != cudaSuccess) return from_cuda(e);
     for (int32_t k = 0; k < (int32_t)ctx->log.size(); ++k) {
         rr_status st = rr_trace_step_adjoint(ctx, k, dL_dkappa, dL_dkborn, grad_rec, stream);
         if (st != RR_OK) return st;
     }
-    const int where = ctx->bundle.interp == RR_TRILINEAR ? RR_AT_VERTICES : RR_AT_CENTRES;
-    return rr_tidal_tensor_adjoint(&g, grad_rec, where, dL_dphi, dL_ddelta, stream);
+    return from_cuda(launch_tidal_adjoint(g, grad_rec, vert ? RR_AT_VERTICES : RR_AT_CENTRES, dL_dphi, dL_ddelta,
+                                          (cudaStream_t)stream, o0, o1));
 }
 
 }  // extern "C"

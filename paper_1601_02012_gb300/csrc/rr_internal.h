@@ -136,8 +136,15 @@ bool tile_ok(const TileCfg& t);
 // form: kFormKahan, kFormShear (also gamma1, gamma2 into g1acc, g2acc) or kFormMethodA
 cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, int form = 0);
 cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s);
+// The transposed stencils over the output box [box0, box1) per axis (point
+// indices, unwrapped; an axis whose extent reaches n, or no box, is whole):
+// dL/dPhi is accumulated only there.
 cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const long long* box0 = nullptr, const long long* box1 = nullptr);
+// Zero the gradient records (64 B per point) of the points in [box0, box1)
+// per axis (unwrapped point indices; an axis whose extent reaches n is whole).
+cudaError_t zero_grad_records(const rr_grid_desc& g, float* grad_rec, const long long* box0, const long long* box1,
+                              cudaStream_t s);
 cudaError_t launch_finalize(int nrays, const float2* kacc, const float2* bacc, const uint32_t* nseg,
                             double* out_kappa, double* out_kborn, unsigned long long* total, cudaStream_t s,
                             const float2* kmom = nullptr, const float2* bmom = nullptr, double chi_s = 0.0,

@@ -385,7 +385,9 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const _
 //   delta derived from tr(H): gH_aa += gdelta / (1.5 Omega_m (H0/c)^2);
 //   dL/dPhi(m) += sum_ab (D_ab^T gH_ab)(m), and the central differences are
 //             symmetric on the periodic grid, so D_ab^T = D_ab.
-// One CTA handles 4 x 4 x 16 cells; each output cell is written by one thread.
+// One CTA handles 4 x 4 x 16 cells of the output box (the whole grid, or the
+// cells within the stencils' reach of the points a trace can touch); each
+// output cell is written by one thread.
 // ---------------------------------------------------------------------------
 
 constexpr int AX = 4, AY = 4, AZ = 16;
@@ -395,6 +397,8 @@ struct TidalAdjArgs {
     float* dphi;
     float* ddelta;
     int n0, n1, n2;
+    int x0, y0, z0;             // output box origin, each in [0, n)
+    int ex, ey, ez;             // output box extents, each <= n
     float ih2, iq, dinv;
 };
 
@@ -409,7 +413,9 @@ __global__ void __launch_bounds__(NT) tidal_adjoint_kernel(TidalAdjArgs a)
     __shared__ float sg[7][NG];
     __shared__ float sh[6][NH];
 
-    const int cx0 = blockIdx.z * AX, cy0 = blockIdx.y * AY, cz0 = blockIdx.x * AZ;   // first output cell
+    // first output cell of the tile, relative to the box and unwrapped
+    const int bx0 = blockIdx.z * AX, by0 = blockIdx.y * AY, bz0 = blockIdx.x * AZ;
+    const int cx0 = a.x0 + bx0, cy0 = a.y0 + by0, cz0 = a.z0 + bz0;
     for (int i = threadIdx.x; i < NG; i += NT) {
         const int z = i % GZ, y = (i / GZ) % GY, x = i / (GZ * GY);
         const int gx = wrapi(cx0 - 1 + x, a.n0), gy = wrapi(cy0 - 1 + y, a.n1), gz = wrapi(cz0 - 1 + z, a.n2);
@@ -464,8 +470,8 @@ __global__ void __launch_bounds__(NT) tidal_adjoint_kernel(TidalAdjArgs a)
         d += ((xy[SX + SY] + xy[-SX - SY]) - (xy[SX - SY] + xy[-SX + SY])) * a.iq;
         d += ((xz[SX + 1] + xz[-SX - 1]) - (xz[SX - 1] + xz[-SX + 1])) * a.iq;
         d += ((yz[SY + 1] + yz[-SY - 1]) - (yz[SY - 1] + yz[-SY + 1])) * a.iq;
-        if (cx0 + x >= a.n0 || cy0 + y >= a.n1 || cz0 + z >= a.n2) continue;
-        const size_t p = ((size_t)(cx0 + x) * a.n1 + (cy0 + y)) * a.n2 + (cz0 + z);
+        if (bx0 + x >= a.ex || by0 + y >= a.ey || bz0 + z >= a.ez) continue;
+        const size_t p = ((size_t)wrapi(cx0 + x, a.n0) * a.n1 + wrapi(cy0 + y, a.n1)) * a.n2 + wrapi(cz0 + z, a.n2);
         a.dphi[p] += d;
         if (a.ddelta) {
             float gd;
@@ -485,6 +491,21 @@ __global__ void __launch_bounds__(NT) tidal_adjoint_kernel(TidalAdjArgs a)
             a.ddelta[p] += gd;
         }
     }
+}
+
+// Zero the 64-byte gradient records of the points of a box (periodic wrap):
+// four 16-byte stores per point, z fastest.
+__global__ void zero_records_box_kernel(float4* __restrict__ rec, int n0, int n1, int n2, int x0, int y0, int z0,
+                                        int ex, int ey, int ez)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4LL * ex * ey * ez) return;
+    const long long pt = i >> 2;
+    const int z = (int)(pt % ez);
+    const long long r = pt / ez;
+    const int y = (int)(r % ey), x = (int)(r / ey);
+    const size_t p = ((size_t)wrapi(x0 + x, n0) * n1 + wrapi(y0 + y, n1)) * n2 + wrapi(z0 + z, n2);
+    rec[4 * p + (i & 3)] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Scalar-pair records (generic form): channel ch of the float2 record of each
@@ -633,22 +654,59 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
 }
 
 cudaError_t launch_tidal_adjoint(const rr_grid_desc& g, const float* grad_rec, int where, float* dphi, float* ddelta,
-                                 cudaStream_t s)
+                                 cudaStream_t s, const long long* box0, const long long* box1)
 {
     TidalAdjArgs a;
     a.grad = reinterpret_cast<const double2*>(grad_rec);
     a.dphi = dphi;
     a.ddelta = ddelta;
     a.n0 = g.n[0]; a.n1 = g.n[1]; a.n2 = g.n[2];
+    int o[3], e[3];
+    for (int k = 0; k < 3; ++k) {
+        if (box0 && box1 && box1[k] - box0[k] < g.n[k]) {
+            o[k] = (int)(((box0[k] % g.n[k]) + g.n[k]) % g.n[k]);
+            e[k] = (int)std::max(0LL, box1[k] - box0[k]);
+        } else {
+            o[k] = 0;
+            e[k] = g.n[k];
+        }
+    }
+    a.x0 = o[0]; a.y0 = o[1]; a.z0 = o[2];
+    a.ex = e[0]; a.ey = e[1]; a.ez = e[2];
     const double h = g.box / g.n[0];
     a.ih2 = (float)(1.0 / (h * h));
     a.iq = (float)(0.25 / (h * h));
     a.dinv = (float)(1.0 / (1.5 * g.omega_m * kH0OverC * kH0OverC));
-    dim3 grid((a.n2 + AZ - 1) / AZ, (a.n1 + AY - 1) / AY, (a.n0 + AX - 1) / AX);
+    if (a.ex == 0 || a.ey == 0 || a.ez == 0) return cudaSuccess;
+    dim3 grid((a.ez + AZ - 1) / AZ, (a.ey + AY - 1) / AY, (a.ex + AX - 1) / AX);
     if (where == RR_AT_VERTICES)
         tidal_adjoint_kernel<0><<<grid, NT, 0, s>>>(a);
     else
         tidal_adjoint_kernel<1><<<grid, NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t zero_grad_records(const rr_grid_desc& g, float* grad_rec, const long long* box0, const long long* box1,
+                              cudaStream_t s)
+{
+    long long o[3], e[3];
+    bool whole = true;
+    for (int k = 0; k < 3; ++k) {
+        if (box1[k] - box0[k] < g.n[k]) {
+            o[k] = ((box0[k] % g.n[k]) + g.n[k]) % g.n[k];
+            e[k] = std::max(0LL, box1[k] - box0[k]);
+            whole = false;
+        } else {
+            o[k] = 0;
+            e[k] = g.n[k];
+        }
+    }
+    if (whole) return cudaMemsetAsync(grad_rec, 0, (size_t)g.n[0] * g.n[1] * g.n[2] * 64, s);
+    const long long n = 4 * e[0] * e[1] * e[2];
+    if (n == 0) return cudaSuccess;
+    zero_records_box_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<float4*>(grad_rec), g.n[0], g.n[1], g.n[2], (int)o[0], (int)o[1], (int)o[2], (int)e[0],
+        (int)e[1], (int)e[2]);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,60 @@ def test_adjoint_with_independent_delta(rrp, oracle_lib):
         assert l2 <= 1e-5 and mx <= 1e-4, (l2, mx)
 
 
+@pytest.mark.parametrize("interp,indep_delta", [(1, False), (0, False), (1, True)])
+def test_backward_over_footprint_only(rrp, oracle_lib, interp, indep_delta):
+    """rr_trace_backward zeroes and transposes only the cells within the
+    stencils' reach of the logged steps' footprints: with the scratch records
+    filled with NaN it gives the whole-grid result (every step's adjoint into
+    zeroed records, then the whole-grid transposed stencils) and the oracle's
+    gradient, on a bundle whose footprint is a small part of the grid and
+    crosses the periodic seam on two axes (x below 0, z above n)."""
+    import torch
+    g = synth.Grid((48, 40, 56), 96.0)
+    b = synth.Bundle(24, 20, synth.deg(6), synth.deg(5), (3.0, 61.0, 100.0), 40.0, interp=interp)
+    steps = [synth.Step(40.0, 22.0, 1.1, 0.8), synth.Step(22.0, 0.0, 0.9, 1.0)]
+    phi = synth.random_field(g.n, 71, np.float32)
+    delta = synth.random_field(g.n, 72, np.float32) if indep_delta else None
+    rng = np.random.default_rng(73)
+    yk = rng.standard_normal(b.nrays)
+    yb = rng.standard_normal(b.nrays)
+    dk, db = torch.from_numpy(yk).cuda(), torch.from_numpy(yb).cuda()
+    tr, k, kb = _forward(rrp, torch.from_numpy(phi).cuda(), g, b, steps,
+                         torch.from_numpy(delta).cuda() if indep_delta else None)
+    n = tuple(g.n)
+    scratch = rrp.grad_buffer(g)
+    scratch.fill_(float("nan"))
+    dd_a = torch.zeros(n, dtype=torch.float32, device="cuda") if indep_delta else None
+    dphi_a = tr.backward(g, dk, db, grad_rec=scratch, ddelta=dd_a)
+    whole = rrp.grad_buffer(g)
+    whole.zero_()
+    for i in range(len(steps)):
+        rrp.rr_trace_step_adjoint(tr.ctx, i, dk, db, whole)
+    dphi_b = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dd_b = torch.zeros(n, dtype=torch.float32, device="cuda") if indep_delta else None
+    where = rrp.RR_AT_VERTICES if interp == 1 else rrp.RR_AT_CENTRES
+    rrp.rr_tidal_tensor_adjoint(rrp.grid_desc(g), whole, where, dphi_b, dd_b)
+    torch.cuda.synchronize()
+    tr.close()
+    got_a, got_b = dphi_a.cpu().numpy(), dphi_b.cpu().numpy()
+    assert np.isfinite(got_a).all()
+    support = got_b != 0
+    assert 0 < support.mean() < 0.2, support.mean()   # a small part of the grid
+    assert not got_a[~support].any()
+    rms = math.sqrt(float(np.mean(got_b[support].astype(np.float64) ** 2)))
+    assert np.abs(got_a - got_b).max() <= 1e-6 * rms   # the atomics' order only
+    want, wd = oracle_lib.trace_adjoint(b, g, steps, yk, yb, delta_derived=not indep_delta)
+    l2, mx = _rel(got_a, want)
+    assert l2 <= 1e-5 and mx <= 1e-4, (l2, mx)
+    if indep_delta:
+        ga, gb_ = dd_a.cpu().numpy(), dd_b.cpu().numpy()
+        assert np.isfinite(ga).all()
+        rmsd = math.sqrt(float(np.mean(gb_[gb_ != 0].astype(np.float64) ** 2)))
+        assert np.abs(ga - gb_).max() <= 1e-6 * rmsd
+        l2, mx = _rel(ga, wd)
+        assert l2 <= 1e-5 and mx <= 1e-4, (l2, mx)
+
+
 def test_dot_product_gpu(rrp):
     """<J x, y> (GPU forward) = <x, J^T y> (GPU adjoint) for the whole chain."""
     import torch
