@@ -62,6 +62,20 @@ ALU_OPS_PER_SEGMENT = 145
 MAX_SM_MHZ = 2070.0   # GB300 maximum SM clock (the issue peak when no clock was sampled)
 
 
+_PIPELINE_NOTE = {
+    False: "each step's footprint records computed on a side stream while the previous step is traced "
+           "(two record buffers; events order each buffer's reuse)",
+    True: "records then trace of each step in order on one stream (one record buffer)",
+}
+
+
+_SPLIT_NOTE = {
+    False: "sums of the CUDA-event intervals of each step's records (side stream) and trace; the records of "
+           "step k + 1 run beside the trace of step k, so the intervals overlap and both stretch",
+    True: "sums of the CUDA-event intervals of each step's records and trace, in order on one stream",
+}
+
+
 def _src_hash(*names):
     """sha256 (16 hex digits) of the kernel sources, in the given order."""
     hsh = hashlib.sha256()
@@ -423,19 +437,17 @@ def run_amr(args, name):
     ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
     ev_td = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
 
+    # the records of step k + 1 on a side stream while step k is traced (two record buffers)
+    recs = [rec] if args.no_pipeline else [rec, gm.record_buffer(rrp.RR_AT_VERTICES, device=dev)]
+    side = None if args.no_pipeline else torch.cuda.Stream(device=dev, priority=-1)
+
     def one_pass(src=None, timed_kernels=False):
         rrp.rr_reset(tr.ctx, stream)
         field = phi if src is None else src
-        for i, st in enumerate(steps):
-            if timed_kernels:
-                ev_td[i][0].record(stream)
-            gm.tidal(field, rec, rrp.RR_AT_VERTICES, None, bboxes[i], stream)
-            if timed_kernels:
-                ev_td[i][1].record(stream)
-                ev_tr[i][0].record(stream)
-            tr.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
-            if timed_kernels:
-                ev_tr[i][1].record(stream)
+        rrp.pipeline_steps(
+            nst, lambda i, b, s: gm.tidal(field, recs[b], rrp.RR_AT_VERTICES, None, bboxes[i], s),
+            lambda i, b, s: tr.amr_step(gm, recs[b], steps[i].chi_a, steps[i].chi_b, steps[i].scale, steps[i].a, s),
+            stream, side, len(recs), (ev_td, ev_tr) if timed_kernels else None)
         rrp.rr_finalize(tr.ctx, kappa, kborn, stream)
 
     with torch.cuda.stream(stream):
@@ -575,11 +587,13 @@ def run_amr(args, name):
         "metric": METRIC, "value": segs * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _amr_config(w, mesh, nst) | {"form": "fp32 float-float walk on the finest lattice, Kahan sums"},
+        "config": _amr_config(w, mesh, nst) | {"form": "fp32 float-float walk on the finest lattice, Kahan sums",
+                                               "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)]},
         "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
         "segments_per_step": segs,
         "setup_s": {"mesh_and_potential": t_gen, "plan": t_plan},
-        "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps},
+        "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps,
+                                "note": _SPLIT_NOTE[bool(args.no_pipeline)]},
         "shear": {"trace_ms_per_pass": sum(sh_ms) / len(sh_ms),
                   "kappa_only_trace_ms_per_pass": trace_ms / args.steps,
                   "cost_vs_kappa_only": (sum(sh_ms) / len(sh_ms)) / (trace_ms / args.steps),
@@ -977,6 +991,8 @@ def main():
                     help="skip the side measurements (other forms, map statistics) and use a small oracle sample")
     ap.add_argument("--no-sub", action="store_true",
                     help="do not run the adaptive-mesh, batched and differentiation workloads after the main one")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="compute each step's records and trace it in order on one stream (one record buffer)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -1053,19 +1069,18 @@ def main():
         else:
             whole["k"], whole["kb"] = kappa, kborn
 
+    # the records of step k + 1 on a side stream while step k is traced (two record buffers)
+    recs = [rec] if args.no_pipeline else [rec, rrp.record_buffer(w.grid, device=dev)]
+    side = None if args.no_pipeline else torch.cuda.Stream(device=dev, priority=-1)
+
     def one_pass(src=None, timed_kernels=False):
         rrp.rr_reset(tr.ctx, stream)
         field = phi if src is None else src
-        for i, st in enumerate(steps):
-            if timed_kernels:
-                ev_td[i][0].record(stream)
-            rrp.rr_tidal_tensor(gd, field, None, rec, tr.where, bboxes[i], stream)
-            if timed_kernels:
-                ev_td[i][1].record(stream)
-                ev_tr[i][0].record(stream)
-            rrp.rr_trace_step(tr.ctx, gd, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
-            if timed_kernels:
-                ev_tr[i][1].record(stream)
+        rrp.pipeline_steps(
+            nst, lambda i, b, s: rrp.rr_tidal_tensor(gd, field, None, recs[b], tr.where, bboxes[i], s),
+            lambda i, b, s: rrp.rr_trace_step(tr.ctx, gd, recs[b], steps[i].chi_a, steps[i].chi_b, steps[i].scale,
+                                              steps[i].a, s),
+            stream, side, len(recs), (ev_td, ev_tr) if timed_kernels else None)
         rrp.rr_finalize(tr.ctx, kappa, kborn, stream)   # synchronises the stream
         gather()
 
@@ -1245,6 +1260,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w, nst) | {"form": "fp64 walk" if args.fp64_dda else "fp32 walk, Kahan sums",
+                                      "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)],
                                       "parallelism": f"one bundle, its rows split over {world} GPU(s) in "
                                                      "whole ray tiles; maps all-gathered every pass"},
         "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
@@ -1272,6 +1288,7 @@ def main():
                                "(10^2-10^4 rays cross each cell), not by DRAM: above 1 by cache reuse"},
         },
         "kernels_ms_per_step": {"trace": trace_ms / args.steps, "tidal": tidal_ms / args.steps,
+                                "note": _SPLIT_NOTE[bool(args.no_pipeline)],
                                 "tidal_points_per_step": tidal_points},
         "tidal_roofline": {"bound": "hbm",
                            "achieved": w.grid.ncells * 36 / (min(full_ms) / 1e3) / 1e9,

@@ -25,7 +25,7 @@ __all__ = [
     "rr_amr_trace_step", "RR_SHEAR", "rr_shear", "RR_METHOD_A", "rr_gradient_records", "trace_method_a",
     "gradient_buffer", "RR_GENERIC", "rr_scalar_records", "rr_set_kernels", "rr_set_observer", "scalar_buffer",
     "trace_tiles", "rr_upload_box",
-    "Tracer", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
+    "Tracer", "pipeline_steps", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
     "rr_trace_backward", "TraceKappa", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
@@ -319,6 +319,62 @@ class AmrMesh:
     def footprint(self, tracer, chi_a, chi_b):
         """Coarse-cell box of the leaves a step of ``tracer``'s bundle can read."""
         return rr_footprint_bbox(tracer.desc, self.coarse_grid(), chi_a, chi_b)
+
+
+def pipeline_steps(n, records, trace, stream, side=None, nbuf=1, timing=None):
+    """Issue the n steps of a pass: ``records(i, b, s)`` computes step i's
+    records into buffer b on stream s, ``trace(i, b, s)`` traces step i from
+    buffer b on s. With one buffer (or no side stream) both run in order on
+    ``stream``. With two buffers and a side stream the records of step i + 1
+    are computed on ``side`` while step i is traced on ``stream``: step i's
+    trace waits for its records, and the records written into a buffer wait
+    for the trace that last read it (each step reads only its own footprint,
+    which its records cover). The side stream starts after the work already
+    on ``stream``; everything ends on ``stream``. Give ``side`` a higher
+    priority than ``stream`` (torch.cuda.Stream(priority=-1)): the records'
+    few blocks are then placed as soon as trace blocks retire, and are ready
+    before the trace they feed. ``timing``: two lists of n
+    (start, end) CUDA event pairs, recorded around each step's records and
+    its trace."""
+    import torch
+    rec_ev, tr_ev = timing if timing is not None else (None, None)
+
+    def rec(i, b, s):
+        if rec_ev is not None:
+            rec_ev[i][0].record(s)
+        records(i, b, s)
+        if rec_ev is not None:
+            rec_ev[i][1].record(s)
+
+    def tra(i, b, s):
+        if tr_ev is not None:
+            tr_ev[i][0].record(s)
+        trace(i, b, s)
+        if tr_ev is not None:
+            tr_ev[i][1].record(s)
+
+    if side is None or nbuf < 2:
+        for i in range(n):
+            rec(i, 0, stream)
+            tra(i, 0, stream)
+        return
+    start = torch.cuda.Event()
+    start.record(stream)
+    side.wait_event(start)
+    ready = [torch.cuda.Event() for _ in range(n)]
+    used = [torch.cuda.Event() for _ in range(n)]
+    if n > 0:
+        rec(0, 0, side)
+        ready[0].record(side)
+    for i in range(n):
+        if i + 1 < n:
+            if i >= 1:
+                side.wait_event(used[i - 1])   # buffer (i + 1) % 2 was last read by step i - 1
+            rec(i + 1, (i + 1) % 2, side)
+            ready[i + 1].record(side)
+        stream.wait_event(ready[i])
+        tra(i, i % 2, stream)
+        used[i].record(stream)
 
 
 def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=True, stream=None):
