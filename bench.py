@@ -42,13 +42,13 @@ L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one trace launch from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches), per
-# (kernel source, workload): valid only for the source it was taken on (sha256
-# of csrc/trace.cu + csrc/walk.cuh) and for that workload.
-TRACE_TRAFFIC = {("77240c8f04eae276", "prod_512"): 275_386_624}
+# (kernel source, workload, steps per launch): valid only for the source it was
+# taken on (sha256 of csrc/trace.cu + csrc/walk.cuh) and for that workload.
+TRACE_TRAFFIC = {("77240c8f04eae276", "prod_512", 1): 275_386_624}
 # warp instructions per cell segment of one trace launch from the same kind of
 # ncu capture (smsp__inst_executed.sum / segments of the launch), per (kernel
 # source, workload); null in the line when the source differs
-TRACE_WARP_INSTRUCTIONS = {("77240c8f04eae276", "prod_512"): 9.3201}
+TRACE_WARP_INSTRUCTIONS = {("77240c8f04eae276", "prod_512", 1): 9.3201}
 
 # FP32 lane operations the method needs per trilinear segment, counted from its
 # formulas as the walk evaluates them: exit face (2 compares) and segment length
@@ -993,6 +993,9 @@ def main():
                     help="do not run the adaptive-mesh, batched and differentiation workloads after the main one")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="compute each step's records and trace it in order on one stream (one record buffer)")
+    ap.add_argument("--group", type=int, default=16,
+                    help="uniform grid: steps traced per launch (rr_trace_steps on box-local records of each "
+                         "step's footprint); 1: one rr_trace_step per step on whole-grid records")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -1069,18 +1072,43 @@ def main():
         else:
             whole["k"], whole["kb"] = kappa, kborn
 
-    # the records of step k + 1 on a side stream while step k is traced (two record buffers)
-    recs = [rec] if args.no_pipeline else [rec, rrp.record_buffer(w.grid, device=dev)]
     side = None if args.no_pipeline else torch.cuda.Stream(device=dev, priority=-1)
+    G = 1 if args.fp64_dda else max(1, min(args.group, 16))
+    if G > 1:
+        # every step's records over its footprint box (widened by a point) in
+        # a box-local buffer of its own; G steps per rr_trace_steps launch; the
+        # records of group j + 1 on the side stream while group j is traced
+        pboxes = [tr.footprint(w.grid, st.chi_a, st.chi_b, pad=1) for st in steps]
+        brecs = [rrp.box_record_buffer(bb, device=dev) for bb in pboxes]
+        groups = [list(range(i, min(i + G, nst))) for i in range(0, nst, G)]
+        ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
+        ev_td = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
+
+        def group_records(gi, b, s, field):
+            for k in groups[gi]:
+                tr.tidal_box(w.grid, field, brecs[k], pboxes[k], stream=s)
+
+        def group_trace(gi, b, s):
+            ks = groups[gi]
+            tr.steps(w.grid, [brecs[k] for k in ks], [steps[k] for k in ks], boxes=[pboxes[k] for k in ks],
+                     stream=s)
+    else:
+        # the records of step k + 1 on a side stream while step k is traced (two record buffers)
+        recs = [rec] if args.no_pipeline else [rec, rrp.record_buffer(w.grid, device=dev)]
 
     def one_pass(src=None, timed_kernels=False):
         rrp.rr_reset(tr.ctx, stream)
         field = phi if src is None else src
-        rrp.pipeline_steps(
-            nst, lambda i, b, s: rrp.rr_tidal_tensor(gd, field, None, recs[b], tr.where, bboxes[i], s),
-            lambda i, b, s: rrp.rr_trace_step(tr.ctx, gd, recs[b], steps[i].chi_a, steps[i].chi_b, steps[i].scale,
-                                              steps[i].a, s),
-            stream, side, len(recs), (ev_td, ev_tr) if timed_kernels else None)
+        if G > 1:
+            rrp.pipeline_steps(len(groups), lambda gi, b, s: group_records(gi, b, s, field), group_trace,
+                               stream, side, 1 if args.no_pipeline else 2,
+                               (ev_td, ev_tr) if timed_kernels else None)
+        else:
+            rrp.pipeline_steps(
+                nst, lambda i, b, s: rrp.rr_tidal_tensor(gd, field, None, recs[b], tr.where, bboxes[i], s),
+                lambda i, b, s: rrp.rr_trace_step(tr.ctx, gd, recs[b], steps[i].chi_a, steps[i].chi_b,
+                                                  steps[i].scale, steps[i].a, s),
+                stream, side, len(recs), (ev_td, ev_tr) if timed_kernels else None)
         rrp.rr_finalize(tr.ctx, kappa, kborn, stream)   # synchronises the stream
         gather()
 
@@ -1196,7 +1224,11 @@ def main():
                 dist.barrier()
             t0 = time.perf_counter()
             rrp.rr_reset(tr.ctx, stream)
-            h2d_bytes = tr.trace_streamed(w.grid, phi_pinned, steps, rec, bufs, stream, copy_stream, bboxes)
+            if G > 1:
+                h2d_bytes = tr.trace_streamed(w.grid, phi_pinned, steps, rec, bufs, stream, copy_stream, pboxes,
+                                              group=G, box_recs=brecs)
+            else:
+                h2d_bytes = tr.trace_streamed(w.grid, phi_pinned, steps, rec, bufs, stream, copy_stream, bboxes)
             rrp.rr_finalize(tr.ctx, kappa, kborn, stream)
             gather()
             k_host.copy_(whole["k"], non_blocking=True)
@@ -1239,15 +1271,16 @@ def main():
         return
 
     peaks, peak_kind = _peaks()
-    per_launch_s = trace_ms / args.steps / nst / 1e3
-    segs_per_launch = segs / nst
+    nlaunch = len(groups) if G > 1 else nst      # trace launches per pass
+    per_launch_s = trace_ms / args.steps / nlaunch / 1e3
+    segs_per_launch = segs / nlaunch
     gather_gbs = segs_per_launch * BYTES_PER_SEGMENT / per_launch_s / 1e9
     alu_gops = segs_per_launch * ALU_OPS_PER_SEGMENT / per_launch_s / 1e9
     alu_peak = peak["lane_fma_per_s"] / 1e9
     tidal_points = sum((b[1] - b[0]) * (b[3] - b[2]) * (b[5] - b[4]) for b in bboxes)
     h = _src_hash("trace.cu", "walk.cuh")
-    traffic = TRACE_TRAFFIC.get((h, w.name))
-    wi = TRACE_WARP_INSTRUCTIONS.get((h, w.name))
+    traffic = TRACE_TRAFFIC.get((h, w.name, G))
+    wi = TRACE_WARP_INSTRUCTIONS.get((h, w.name, G))
     sm_mhz = (clocks or {}).get("sm_mhz") or MAX_SM_MHZ
     issue_peak = 4.0 * peak["sms"] * sm_mhz * 1e6          # warp instructions per second
     issue = None
@@ -1261,13 +1294,16 @@ def main():
         "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w, nst) | {"form": "fp64 walk" if args.fp64_dda else "fp32 walk, Kahan sums",
                                       "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)],
+                                      "steps_per_launch": G,
+                                      "records": ("each step's footprint box (widened by a point), box-local"
+                                                  if G > 1 else "whole grid, each step's footprint rewritten"),
                                       "parallelism": f"one bundle, its rows split over {world} GPU(s) in "
                                                      "whole ray tiles; maps all-gathered every pass"},
         "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
         "segments_per_step": segs_all,
         "roofline": {
             "bound": "alu", "achieved": alu_gops, "peak": alu_peak, "unit": "Gop/s", "frac": alu_gops / alu_peak,
-            "traffic": traffic, "kernel": "trace_kernel<trilinear,float>",
+            "traffic": traffic, "kernel": "trace_steps_kernel<trilinear, flat>" if G > 1 else "trace_kernel<trilinear,float>",
             "algorithmic_ops_per_segment": ALU_OPS_PER_SEGMENT,
             "algorithmic_ops_per_launch": segs_per_launch * ALU_OPS_PER_SEGMENT,
             "mean_launch_ms": per_launch_s * 1e3,

@@ -179,6 +179,18 @@ rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const floa
                           int32_t where, const int32_t* bbox, void* stream);
 
 /*
+ * rr_tidal_tensor over the box bbox (required: 6 int32 {x0, x1, y0, y1, z0,
+ * z1}, each extent in [1, n], periodic) with the records stored box-local:
+ * point (x0 + i, y0 + j, z0 + k) (wrapped) at record (i ey + j) ez + k, ex ey ez
+ * records of 32 bytes in all (fewer than 2^31; rec 32-byte aligned). A box
+ * that holds a step's footprint (rr_footprint_bbox) widened by one point per
+ * side is all rr_trace_steps needs of that step's records. RR_ERR_ARG as rr_tidal_tensor, and for a NULL
+ * bbox.
+ */
+rr_status rr_tidal_tensor_box(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                              int32_t where, const int32_t* bbox, void* stream);
+
+/*
  * Gradient records of Method A (Eq. kappa2, Sec. 3.5): d_a Phi by central
  * differences (Phi_{+1} - Phi_{-1}) / (2h) at the cell centres (periodic),
  * then records at the vertices (mean of the 8 cells, Sec. 2.7) or at the
@@ -334,6 +346,36 @@ rr_status rr_source_kappa(const double* m_end, const double* m_k, int64_t nrays,
  * without RR_SHEAR.
  */
 rr_status rr_shear(rr_ctx* ctx, double* gamma1, double* gamma2, void* stream);
+
+/*
+ * Steps i = 0 .. nsteps - 1 in order, each as rr_trace_step(ctx, grid, rec[i],
+ * chi_a[i], chi_b[i], scale[i], a_step[i], stream) would trace it: the same
+ * checks (every step continues the previous one), the same step log and the
+ * same results bit for bit. rec, chi_a, chi_b, scale, a_step: host arrays of
+ * nsteps entries; rec[i] are device record buffers (the same buffer may serve
+ * several steps) that must all stay valid until the stream reaches the end of
+ * the call. boxes: NULL (every rec[i] holds the whole grid's records, as for
+ * rr_trace_step), or a host array of 6 int32 per step: rec[i] then holds only
+ * the records of box i, in the box-local layout of rr_tidal_tensor_box, and
+ * box i (periodically) must hold the step's footprint box (rr_footprint_bbox
+ * of the whole bundle) widened by one point on each side, since the walk
+ * checks one vertex plane beyond it; boxes need a periodic trilinear bundle in the
+ * default form (RR_ERR_ARG otherwise, or for a box that misses the footprint).
+ * A step's records then take its footprint's memory only, so that the
+ * records of many steps can be resident at once. In the default FP32 form (no RR_FP64_DDA, RR_PLAIN_SUMS,
+ * RR_SOURCE_MOMENTS, RR_SHEAR, RR_METHOD_A or RR_GENERIC) up to 16 consecutive
+ * steps are traced by one launch: each ray walks them in turn with its sums
+ * held on chip, instead of reading and writing its state at every step (Sec.
+ * 2.5.2 moves all rays to the end of one time step before the next; with the
+ * records of several steps resident, one ray is moved through them). Steps
+ * whose footprint reaches the periodic seam (trilinear), and the other forms,
+ * get one launch each. If a step fails its checks nothing is launched and
+ * the log is unchanged (RR_ERR_ARG / RR_ERR_STATE as rr_trace_step);
+ * asynchronous otherwise. nsteps == 0: no-op.
+ */
+rr_status rr_trace_steps(rr_ctx* ctx, const rr_grid_desc* grid, int32_t nsteps, const float* const* rec,
+                         const int32_t* boxes, const double* chi_a, const double* chi_b, const double* scale,
+                         const double* a_step, void* stream);
 
 /* Synchronise `stream` and return the error word (as rr_finalize does),
  * without writing maps. */

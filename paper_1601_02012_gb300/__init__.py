@@ -11,7 +11,7 @@ from . import _rr
 from ._rr import (RR_AT_CENTRES, RR_AT_VERTICES, RR_NGP, RR_TRILINEAR, RRError, bundle_desc, grid_desc,
                   rr_create, rr_create_band, rr_destroy, rr_finalize, rr_footprint_bbox, rr_reset, rr_segment_count,
                   rr_status_string, rr_step_count, rr_sync_status, rr_tidal_tensor, rr_tidal_tensor_adjoint,
-                  rr_trace_backward, rr_trace_step, rr_trace_step_adjoint)
+                  rr_trace_backward, rr_trace_step, rr_trace_step_adjoint, rr_trace_steps)
 
 from .batch import Batch  # noqa: E402
 from ._rr import rr_amr_create, rr_amr_destroy, rr_amr_sizes, rr_amr_tidal, rr_amr_trace_step  # noqa: E402
@@ -25,10 +25,10 @@ __all__ = [
     "rr_amr_trace_step", "RR_SHEAR", "rr_shear", "RR_METHOD_A", "rr_gradient_records", "trace_method_a",
     "gradient_buffer", "RR_GENERIC", "rr_scalar_records", "rr_set_kernels", "rr_set_observer", "scalar_buffer",
     "trace_tiles", "rr_upload_box",
-    "Tracer", "pipeline_steps", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
+    "Tracer", "pipeline_steps", "box_record_buffer", "trace_kappa", "trace_shear", "record_buffer", "grad_buffer", "RRError", "rr_create", "rr_destroy", "rr_reset",
     "rr_tidal_tensor", "rr_footprint_bbox", "rr_trace_step", "rr_finalize", "rr_sync_status",
     "rr_segment_count", "rr_status_string", "rr_step_count", "rr_trace_step_adjoint", "rr_tidal_tensor_adjoint",
-    "rr_trace_backward", "TraceKappa", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
+    "rr_trace_backward", "rr_trace_steps", "TraceKappa", "RR_NGP", "RR_TRILINEAR", "RR_AT_VERTICES", "RR_AT_CENTRES",
 ]
 
 
@@ -51,6 +51,14 @@ def record_buffer(grid, device="cuda"):
     """Uninitialised device buffer for n0*n1*n2 records of 8 floats."""
     import torch
     n = int(grid.n[0]) * int(grid.n[1]) * int(grid.n[2])
+    return torch.empty((n, 8), dtype=torch.float32, device=device)
+
+
+def box_record_buffer(bbox, device="cuda"):
+    """Uninitialised device buffer for the box-local records of a box
+    (rr_tidal_tensor_box): 8 floats per point of the box."""
+    import torch
+    n = (int(bbox[1]) - int(bbox[0])) * (int(bbox[3]) - int(bbox[2])) * (int(bbox[5]) - int(bbox[4]))
     return torch.empty((n, 8), dtype=torch.float32, device=device)
 
 
@@ -134,11 +142,37 @@ class Tracer:
         _rr.rr_set_observer(self.ctx, obs)
         self.desc.obs[0], self.desc.obs[1], self.desc.obs[2] = (float(x) for x in obs)
 
-    def footprint(self, grid, chi_a, chi_b):
-        return rr_footprint_bbox(self.desc, grid_desc(grid), chi_a, chi_b)
+    def footprint(self, grid, chi_a, chi_b, pad=0):
+        """rr_footprint_bbox of the step, widened by ``pad`` points per side
+        (an axis it would cover whole becomes [0, n)); pad=1 gives the boxes
+        rr_trace_steps takes with box-local records."""
+        bb = list(rr_footprint_bbox(self.desc, grid_desc(grid), chi_a, chi_b))
+        for a in range(3):
+            n = int(grid.n[a])
+            if bb[2 * a + 1] - bb[2 * a] + 2 * pad >= n:
+                bb[2 * a], bb[2 * a + 1] = 0, n
+            else:
+                bb[2 * a] -= pad
+                bb[2 * a + 1] += pad
+        return tuple(bb)
 
     def step(self, grid, rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):
         rr_trace_step(self.ctx, grid_desc(grid), rec, chi_a, chi_b, scale, a, stream)
+
+    def steps(self, grid, recs, steps, boxes=None, stream=None):
+        """rr_trace_steps: the given steps (objects with chi_a, chi_b, scale,
+        a) in order, step i reading recs[i] (whole-grid records, or, with
+        ``boxes``, the box-local records of box i); the default form traces up
+        to 16 of them per launch."""
+        _rr.rr_trace_steps(self.ctx, grid_desc(grid), list(recs), [st.chi_a for st in steps],
+                           [st.chi_b for st in steps], [st.scale for st in steps], [st.a for st in steps],
+                           boxes, stream)
+
+    def tidal_box(self, grid, phi, rec, bbox, delta=None, stream=None):
+        """rr_tidal_tensor_box: the records of the points of ``bbox`` only,
+        box-local, into ``rec`` (box_record_buffer)."""
+        _rr.rr_tidal_tensor_box(grid_desc(grid), phi, delta, rec, self.where, bbox, stream)
+        return rec
 
     def finalize(self, kappa=None, kborn=None, stream=None):
         """FP64 maps [ny, nx] on the device (rayid order, x fastest)."""
@@ -177,7 +211,7 @@ class Tracer:
         return gamma1, gamma2
 
     def trace_streamed(self, grid, phi_host, steps, rec, bufs, stream, copy_stream, bboxes=None, delta_host=None,
-                       delta_bufs=None):
+                       delta_bufs=None, group=1, box_recs=None):
         """The steps of a pass with the potential streamed from host memory.
 
         phi_host: page-locked host tensor of n0*n1*n2 floats; bufs: two device
@@ -190,10 +224,15 @@ class Tracer:
         step reads are moved, so the maps equal those of the same steps on the
         whole field. delta_host / delta_bufs: the same for a given density
         contrast. The host arrays must stay unchanged until ``stream`` has
-        passed the last step. Returns the bytes copied."""
+        passed the last step. group > 1: each step's records go into its own
+        box-local buffer box_recs[i] over bboxes[i] (footprints widened by one
+        point: footprint(pad=1)), and every ``group`` steps are traced by one
+        rr_trace_steps call. Returns the bytes copied."""
         import torch
         if self.generic:
             raise ValueError("trace_streamed: the generic form takes its fields through scalars()")
+        if group > 1 and (box_recs is None or bboxes is None):
+            raise ValueError("trace_streamed: group > 1 takes box_recs and their (padded) bboxes")
         g = grid_desc(grid)
         if bboxes is None:
             bboxes = [self.footprint(grid, st.chi_a, st.chi_b) for st in steps]
@@ -216,11 +255,18 @@ class Tracer:
             copied = torch.cuda.Event()
             copied.record(copy_stream)
             stream.wait_event(copied)
-            self.tidal(grid, bufs[slot], rec, delta=delta, bbox=bboxes[i], stream=stream)
+            if group > 1:
+                self.tidal_box(grid, bufs[slot], box_recs[i], bboxes[i], delta=delta, stream=stream)
+            else:
+                self.tidal(grid, bufs[slot], rec, delta=delta, bbox=bboxes[i], stream=stream)
             done = torch.cuda.Event()
             done.record(stream)
             released[slot] = done
-            self.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            if group <= 1:
+                self.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+            elif (i + 1) % group == 0 or i == len(steps) - 1:
+                k0 = i - i % group
+                self.steps(grid, box_recs[k0:i + 1], steps[k0:i + 1], boxes=bboxes[k0:i + 1], stream=stream)
         return total
 
     def amr_step(self, mesh, leaf_rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):

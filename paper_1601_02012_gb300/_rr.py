@@ -82,6 +82,8 @@ def load() -> C.CDLL:
             "rr_footprint_bbox": ([P, P, D, D, P], C.c_int),
             "rr_upload_box": ([P, P, P, P, C.POINTER(C.c_int64), P], C.c_int),
             "rr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
+            "rr_trace_steps": ([P, P, I32, P, P, P, P, P, P, P], C.c_int),
+            "rr_tidal_tensor_box": ([P, P, P, P, I32, P, P], C.c_int),
             "rr_finalize": ([P, P, P, P], C.c_int),
             "rr_sync_status": ([P, P], C.c_int),
             "rr_segment_count": ([P, C.POINTER(C.c_uint64), P, P], C.c_int),
@@ -251,6 +253,30 @@ def rr_trace_step(ctx, grid: rr_grid_desc, rec, chi_a: float, chi_b: float, scal
                   a_step: float = 1.0, stream=None) -> None:
     _check(load().rr_trace_step(ctx, C.byref(grid), _ptr(rec), float(chi_a), float(chi_b), float(scale),
                                 float(a_step), _stream(stream)), "rr_trace_step")
+
+
+def rr_trace_steps(ctx, grid: rr_grid_desc, recs, chi_a, chi_b, scale, a_step, boxes=None, stream=None) -> None:
+    """Consecutive steps in order (equal lengths): recs[i] the record buffer
+    of step i, the others per-step numbers; boxes: None (whole-grid records)
+    or one 6-int box per step (box-local records of rr_tidal_tensor_box)."""
+    n = len(recs)
+    if not (len(chi_a) == len(chi_b) == len(scale) == len(a_step) == n):
+        raise ValueError("rr_trace_steps: per-step sequences of different lengths")
+    ptrs = (C.c_void_p * max(n, 1))(*[_ptr(r) for r in recs])
+    arr = [(C.c_double * max(n, 1))(*[float(x) for x in v]) for v in (chi_a, chi_b, scale, a_step)]
+    bx = None
+    if boxes is not None:
+        if len(boxes) != n:
+            raise ValueError("rr_trace_steps: one box per step")
+        bx = (C.c_int32 * (6 * max(n, 1)))(*[int(v) for bb in boxes for v in bb])
+    _check(load().rr_trace_steps(ctx, C.byref(grid), int(n), ptrs, bx, arr[0], arr[1], arr[2], arr[3],
+                                 _stream(stream)), "rr_trace_steps")
+
+
+def rr_tidal_tensor_box(grid: rr_grid_desc, phi, delta, rec, where: int, bbox, stream=None) -> None:
+    bb = (C.c_int32 * 6)(*[int(v) for v in bbox])
+    _check(load().rr_tidal_tensor_box(C.byref(grid), _ptr(phi), _ptr(delta), _ptr(rec), int(where), bb,
+                                      _stream(stream)), "rr_tidal_tensor_box")
 
 
 def rr_finalize(ctx, kappa, kappa_born=None, stream=None) -> None:

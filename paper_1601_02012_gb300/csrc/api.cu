@@ -115,6 +115,13 @@ TraceArgs make_trace_args(const rr_bundle_desc& b, const RayState& st, const rr_
     a.inv_chi_s_f = (float)(1.0 / b.chi_s);
     a.sub_len = (float)(32.0 * a.h);
     a.periodic = (b.flags & RR_PERIODIC) ? 1 : 0;
+    // flat addressing over the whole grid's records
+    for (int i = 0; i < 3; ++i) {
+        a.fo[i] = 0;
+        a.fe[i] = grid->n[i];
+    }
+    a.fs0 = grid->n[1] * grid->n[2];
+    a.fs1 = grid->n[2];
     a.dir = st.dir;
     a.dirh = st.dirh;
     a.dirl = st.dirl;
@@ -376,6 +383,24 @@ rr_status rr_tidal_tensor(const rr_grid_desc* grid, const float* phi, const floa
     return point_records(grid, phi, delta, rec, where, bbox, stream, 0);
 }
 
+rr_status rr_tidal_tensor_box(const rr_grid_desc* grid, const float* phi, const float* delta, float* rec,
+                              int32_t where, const int32_t* bbox, void* stream)
+{
+    rr_status st = check_grid(grid);
+    if (st != RR_OK) return st;
+    if (!phi || !rec || !bbox || !is_aligned32(rec)) return RR_ERR_ARG;
+    if (where != RR_AT_VERTICES && where != RR_AT_CENTRES) return RR_ERR_ARG;
+    long long npts = 1;
+    for (int a = 0; a < 3; ++a) {
+        const long long ext = (long long)bbox[2 * a + 1] - bbox[2 * a];
+        if (ext < 1 || ext > grid->n[a]) return RR_ERR_ARG;
+        if (bbox[2 * a] < -(1 << 20) || bbox[2 * a + 1] > (1 << 20)) return RR_ERR_ARG;
+        npts *= ext;
+    }
+    if (npts >= (1LL << 31)) return RR_ERR_ARG;
+    return from_cuda(launch_tidal(*grid, phi, delta, rec, where, bbox, (cudaStream_t)stream, 0, true));
+}
+
 rr_status rr_scalar_records(const rr_grid_desc* grid, const float* field, const float* field_prev, double inv_dt,
                             int32_t channel, float* rec, int32_t where, const int32_t* bbox, void* stream)
 {
@@ -520,6 +545,129 @@ rr_status rr_trace_step(rr_ctx* ctx, const rr_grid_desc* grid, const float* rec,
     ctx->log.push_back(make_step_record(ctx, grid, chi_a, chi_b, scale, a_step));
     ctx->relocated = false;
     return RR_OK;
+}
+
+// Does the box [bb[2a], bb[2a + 1]) per axis (periodically) hold the points
+// [f0[a], f1[a])?
+static bool box_holds(const int32_t* bb, const long long f0[3], const long long f1[3], const rr_grid_desc& g)
+{
+    for (int a = 0; a < 3; ++a) {
+        const long long n = g.n[a], b0 = bb[2 * a], b1 = bb[2 * a + 1];
+        if (f1[a] - f0[a] > b1 - b0) return false;
+        // the box's periodic image that starts at or below f0, within a period
+        const long long d = f0[a] - b0;
+        const long long m = d >= 0 ? d / n : -((-d + n - 1) / n);
+        if (f1[a] > b1 + m * n) return false;
+    }
+    return true;
+}
+
+rr_status rr_trace_steps(rr_ctx* ctx, const rr_grid_desc* grid, int32_t nsteps, const float* const* rec,
+                         const int32_t* boxes, const double* chi_a, const double* chi_b, const double* scale,
+                         const double* a_step, void* stream)
+{
+    if (!ctx || nsteps < 0) return RR_ERR_ARG;
+    if (nsteps == 0) return RR_OK;
+    if (!rec || !chi_a || !chi_b || !scale || !a_step) return RR_ERR_ARG;
+    const rr_bundle_desc& b = ctx->bundle;
+    const bool fused = !(b.flags & (RR_FP64_DDA | RR_SOURCE_MOMENTS | RR_PLAIN_SUMS | RR_SHEAR | RR_METHOD_A |
+                                    RR_GENERIC));
+    rr_bundle_desc whole = b;
+    whole.ny = ctx->ny_full;
+    if (boxes) {
+        // records of each step's box only: the flat walk over them (trilinear,
+        // periodic, the default form); each box must hold the step's footprint
+        if (!fused || b.interp != RR_TRILINEAR || !(b.flags & RR_PERIODIC)) return RR_ERR_ARG;
+        rr_status st = check_grid(grid);
+        if (st != RR_OK) return st;
+        for (int32_t i = 0; i < nsteps; ++i) {
+            const int32_t* bb = boxes + 6 * (size_t)i;
+            long long npts = 1;
+            for (int a = 0; a < 3; ++a) {
+                const long long ext = (long long)bb[2 * a + 1] - bb[2 * a];
+                if (ext < 1 || ext > grid->n[a] || bb[2 * a] < -(1 << 20) || bb[2 * a + 1] > (1 << 20))
+                    return RR_ERR_ARG;
+                npts *= ext;
+            }
+            if (npts >= (1LL << 31) || !is_finite(chi_a[i]) || !is_finite(chi_b[i])) return RR_ERR_ARG;
+            // the footprint box widened by one point per side: the flat walk
+            // checks one vertex plane beyond the footprint's reach
+            long long f0[3], f1[3];
+            footprint_box(whole, b.obs, *grid, chi_a[i], chi_b[i], f0, f1);
+            for (int a = 0; a < 3; ++a) {
+                f0[a] -= 1;
+                f1[a] += 1;
+            }
+            if (!box_holds(bb, f0, f1, *grid)) return RR_ERR_ARG;
+        }
+    }
+    if (!fused) {
+        // other forms: one launch per step (the same results)
+        for (int32_t i = 0; i < nsteps; ++i) {
+            rr_status st = rr_trace_step(ctx, grid, rec[i], chi_a[i], chi_b[i], scale[i], a_step[i], stream);
+            if (st != RR_OK) return st;
+        }
+        return RR_OK;
+    }
+    // validate every step in order (each continuing the previous one) before
+    // anything is launched; the log takes them only if all pass
+    const size_t log0 = ctx->log.size();
+    const bool reloc0 = ctx->relocated;
+    for (int32_t i = 0; i < nsteps; ++i) {
+        rr_status st = validate_step(ctx, grid, rec[i], chi_a[i], chi_b[i], scale[i], a_step[i]);
+        if (st != RR_OK) {
+            ctx->log.resize(log0);
+            ctx->relocated = reloc0;
+            return st;
+        }
+        ctx->log.push_back(make_step_record(ctx, grid, chi_a[i], chi_b[i], scale[i], a_step[i]));
+        ctx->relocated = false;
+    }
+    const TraceArgs a0 = make_trace_args(ctx, grid, rec[0], chi_a[0], chi_b[0], scale[0], a_step[0]);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    // blocks of up to kMaxStepBlock steps that all take the flat addressing
+    // (trilinear) or any steps (NGP) go to one launch each; a trilinear step
+    // outside the flat range is launched on its own
+    int32_t i = 0;
+    while (i < nsteps && e == cudaSuccess) {
+        const bool tri = b.interp == RR_TRILINEAR;
+        auto flat_at = [&](int32_t k) { return boxes || flat_ok(whole, b.obs, *grid, chi_a[k], chi_b[k]); };
+        if (tri && !flat_at(i)) {
+            const TraceArgs a = make_trace_args(ctx, grid, rec[i], chi_a[i], chi_b[i], scale[i], a_step[i]);
+            e = launch_trace(a, b.interp, false, s, TileCfg{}, kFormKahan, false);
+            ++i;
+            continue;
+        }
+        StepBlock blk{};
+        blk.n = 0;
+        while (i < nsteps && blk.n < kMaxStepBlock && (!tri || flat_at(i))) {
+            const TraceArgs a = make_trace_args(ctx, grid, rec[i], chi_a[i], chi_b[i], scale[i], a_step[i]);
+            StepArgs& st = blk.s[blk.n++];
+            st.rec = a.rec;
+            st.chi_a = a.chi_a; st.chi_b = a.chi_b;
+            st.cah = a.cah; st.cal = a.cal; st.Lf = a.Lf; st.D0f = a.D0f;
+            st.sch = a.sch; st.scl = a.scl; st.bsh = a.bsh; st.bsl = a.bsl;
+            for (int q = 0; q < 3; ++q) {
+                st.fo[q] = a.fo[q];
+                st.fe[q] = a.fe[q];
+            }
+            st.fs0 = a.fs0;
+            st.fs1 = a.fs1;
+            if (boxes) {
+                const int32_t* bb = boxes + 6 * (size_t)i;
+                for (int q = 0; q < 3; ++q) {
+                    st.fo[q] = (int)(((bb[2 * q] % grid->n[q]) + grid->n[q]) % grid->n[q]);
+                    st.fe[q] = bb[2 * q + 1] - bb[2 * q];
+                }
+                st.fs0 = st.fe[1] * st.fe[2];
+                st.fs1 = st.fe[2];
+            }
+            ++i;
+        }
+        e = launch_trace_steps(a0, blk, b.interp, tri, s);
+    }
+    return from_cuda(e);
 }
 
 rr_status rr_sync_status(rr_ctx* ctx, void* stream)

@@ -84,6 +84,27 @@ struct TraceArgs {
     uint32_t* err;
     float sch, scl;             // scale (multiplies the kappa step sum), float-float
     float bsh, bsl;             // scale * 1.5 Omega_m (H0/c)^2 / a_step, float-float
+    // flat record addressing: the records cover the box of points fo .. fo +
+    // fe - 1 per axis (fo in [0, n), periodic), point (i, j, k) of the box at
+    // i fs0 + j fs1 + k; the whole grid: fo = 0, fe = n, fs0 = n1 n2, fs1 = n2
+    int fo[3], fe[3];
+    int fs0, fs1;
+};
+
+// The per-step fields of TraceArgs for a launch over several consecutive
+// steps (trace_steps_kernel); the other fields are shared.
+struct StepArgs {
+    const float4* rec;
+    double chi_a, chi_b;
+    float cah, cal, Lf, D0f;
+    float sch, scl, bsh, bsl;
+    int fo[3], fe[3];
+    int fs0, fs1;
+};
+constexpr int kMaxStepBlock = 16;
+struct StepBlock {
+    int n;
+    StepArgs s[kMaxStepBlock];
 };
 
 // Adjoint of one step: per-ray derivatives of the loss and the gradient
@@ -117,8 +138,10 @@ struct BatchArgs {
 cudaError_t launch_init_directions(const rr_bundle_desc& b, double* dir, float4* dirh, float4* dirl, cudaStream_t s,
                                    int row0 = 0, int nrows = -1);
 // kind 0: tidal records (2 float4 per point); kind 1: gradient records (1 float4)
+// compact (with a bbox): the records stored box-local, point (i, j, k) of the
+// box at (i ey + j) ez + k
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
-                         const int32_t* bbox, cudaStream_t s, int kind = 0);
+                         const int32_t* bbox, cudaStream_t s, int kind = 0, bool compact = false);
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s);
 // Forms of the FP32 walk's sums.
 enum { kFormKahan = 0, kFormPlain = 1, kFormMoments = 2, kFormShear = 3, kFormMethodA = 4, kFormGeneric = 5 };
@@ -130,6 +153,9 @@ enum { kAddrIndex = 0, kAddrPlanes = 1, kAddrFlat = 2 };
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
                          int form = kFormKahan, bool flat = false);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
+// Steps b.s[0 .. b.n) of the FP32 default form in one launch; a holds the
+// shared fields. flat: every step passed the flat-addressing check (trilinear).
+cudaError_t launch_trace_steps(const TraceArgs& a, const StepBlock& b, int interp, bool flat, cudaStream_t s);
 int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
 dim3 tile_grid(const TileCfg& t, int nx, int ny);
 bool tile_ok(const TileCfg& t);

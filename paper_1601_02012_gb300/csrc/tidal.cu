@@ -47,6 +47,7 @@ struct TidalArgs {
     float dinv;       // 1 / (1.5 Omega_m (H0/c)^2)
     float ih2h;       // 1/(2h), gradient records
     int xchunk;       // planes per CTA
+    int compact;      // records stored box-local (point (i, j, k) of the box at (i ey + j) ez + k)
 };
 
 // i mod n; the integer division only runs for indices outside [0, n) (halo
@@ -89,6 +90,12 @@ __device__ __forceinline__ void centre_channels(float p0, float x0m, float x0p, 
             h[3] = lap * a.dinv;
         }
     }
+}
+
+// first record of output plane c (unwrapped centre/vertex plane index)
+__device__ __forceinline__ size_t out_plane(const TidalArgs& a, int c)
+{
+    return a.compact ? (size_t)(c - a.x0) * a.ey * a.ez : (size_t)wrapi(c, a.n0) * a.n1 * a.n2;
 }
 
 // one 32-byte tidal record {c0..c3}, {c4, c5, c6, 0} in a single 256-bit store
@@ -248,7 +255,9 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const _
     for (int k = 0; k < 2; ++k) {
         oy[k] = py0 + r0 + k - V;
         out_ok[k] = oz_ok && (r0 + k) >= V && oy[k] < a.ey;
-        out_off[k] = out_ok[k] ? (size_t)wrapi(a.y0 + oy[k], a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2) : 0;
+        out_off[k] = !out_ok[k] ? 0
+                     : a.compact ? (size_t)oy[k] * a.ez + oz
+                                 : (size_t)wrapi(a.y0 + oy[k], a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2);
     }
     const int o = (r0 + 1) * RP + (tz + 1) + dz;     // first centre in a ring slot
     size_t d_yz[2];
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const _
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (c > c_first && out_ok[k]) {
-                    const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_off[k];
+                    const size_t pt = out_plane(a, c) + out_off[k];
                     if constexpr (KIND == 0) {
                         store_rec(a.rec + 2 * pt, (prev[k][0] + b[k][0]) * 0.125f, (prev[k][1] + b[k][1]) * 0.125f,
                                   (prev[k][2] + b[k][2]) * 0.125f, (prev[k][3] + b[k][3]) * 0.125f,
@@ -356,7 +365,7 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const _
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (!out_ok[k]) continue;
-                const size_t pt = (size_t)wrapi(c, a.n0) * a.n1 * a.n2 + out_off[k];
+                const size_t pt = out_plane(a, c) + out_off[k];
                 if constexpr (KIND == 0) {
                     store_rec(a.rec + 2 * pt, h[k][0], h[k][1], h[k][2], h[k][3], h[k][4], h[k][5], h[k][6]);
                 } else {
@@ -600,9 +609,10 @@ bool phi_tensor_map(const rr_grid_desc& g, const float* phi, CUtensorMap* map)
 }  // namespace
 
 cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* delta, float* rec, int where,
-                         const int32_t* bbox, cudaStream_t s, int kind)
+                         const int32_t* bbox, cudaStream_t s, int kind, bool compact)
 {
     TidalArgs a;
+    a.compact = compact && bbox ? 1 : 0;
     a.phi = phi;
     a.delta = delta;
     a.rec = reinterpret_cast<float4*>(rec);

@@ -100,9 +100,19 @@ __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], in
 //               seam and the grid has fewer than 2^31 points: the host checks
 //               the step's footprint box; each sub-step checks its own cell
 //               range first and, outside it, flags kErrRange and reads nothing.
-template <int INTERP, class R, int FORM = kFormKahan, int ADDR = kAddrPlanes>
-__device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
+// A ray's accumulators held in registers across the steps of one launch
+// (trace_steps_kernel): read from the ray state at the end of the first step,
+// written back after the last.
+struct RayAcc {
+    float2 k, b;
+    uint32_t n;
+    bool loaded;
+};
+
+template <int INTERP, class R, int FORM = kFormKahan, int ADDR = kAddrPlanes, bool REGACC = false>
+__device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy, RayAcc* acc = nullptr)
 {
+    static_assert(!REGACC || (FORM == kFormKahan && sizeof(R) == 4), "register accumulators: FP32 default form");
     using OT = unsigned long long;
     constexpr bool PLANES = ADDR == kAddrPlanes;
     constexpr bool FLAT = ADDR == kAddrFlat;
@@ -118,9 +128,11 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     const int nn[3] = {A.n0, A.n1, A.n2};
     RayRange rg;
     if (!ray_range(A, rid, rg)) return;
-    prefetch_l2(A.kacc + rid);
-    prefetch_l2(A.bacc + rid);
-    prefetch_l2(A.nseg + rid);
+    if (!REGACC || !acc->loaded) {
+        prefetch_l2(A.kacc + rid);
+        prefetch_l2(A.bacc + rid);
+        prefetch_l2(A.nseg + rid);
+    }
     if constexpr (SH) {
         prefetch_l2(A.g1acc + rid);
         prefetch_l2(A.g2acc + rid);
@@ -182,8 +194,14 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
         bool inside = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const int sa = a == 0 ? A.n1 * A.n2 : (a == 1 ? A.n2 : 1);
-            fB += vlo[a] * sa;
+            // box-local vertex and cell coordinates (the records' box starts
+            // at fo, periodically)
+            const int sa = a == 0 ? A.fs0 : (a == 1 ? A.fs1 : 1);
+            int vl = vlo[a] - A.fo[a];
+            if (vl < 0) vl += nn[a];
+            int cl = c[a] - A.fo[a];
+            if (cl < 0) cl += nn[a];
+            fB += vl * sa;
             fd[a] = sgn[a] * sa;
             // crossings this sub-step can make on axis a (2 more than the path
             // allows, for rounding); cells c .. c + sgn K, vertex planes one further
@@ -193,8 +211,8 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
                 if (x < 4194304.f) K = f2i_exact(x) + 2;
                 else inside = false;
             }
-            const int lo = sgn[a] > 0 ? c[a] : c[a] - K, hi = sgn[a] > 0 ? c[a] + K + 1 : c[a] + 1;
-            if (lo < 0 || hi > nn[a] - 1) inside = false;
+            const int lo = sgn[a] > 0 ? cl : cl - K, hi = sgn[a] > 0 ? cl + K + 1 : cl + 1;
+            if (lo < 0 || hi > A.fe[a] - 1) inside = false;
         }
         if (!inside) {
             atomicOr(A.err, kErrRange);
@@ -533,6 +551,18 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy)
     float kh, kl, bh, bl;
     sk.pair(kh, kl);
     sb.pair(bh, bl);
+    if constexpr (REGACC) {
+        if (!acc->loaded) {
+            acc->k = A.kacc[rid];
+            acc->b = A.bacc[rid];
+            acc->n = A.nseg[rid];
+            acc->loaded = true;
+        }
+        acc->k = ff_mul_add(acc->k, kh, kl, A.sch, A.scl);
+        acc->b = ff_mul_add(acc->b, bh, bl, A.bsh, A.bsl);
+        acc->n += cnt;
+        return;
+    }
     A.kacc[rid] = ff_mul_add(A.kacc[rid], kh, kl, A.sch, A.scl);
     A.bacc[rid] = ff_mul_add(A.bacc[rid], bh, bl, A.bsh, A.bsl);
     A.nseg[rid] += cnt;
@@ -546,6 +576,45 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, con
     int ix, iy;
     tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
     if (ix < A.nx && iy < A.ny) trace_ray<INTERP, R, FORM, ADDR>(A, ix, iy);
+}
+
+// Consecutive steps of one bundle in one launch (the default FP32 form): each
+// thread walks its ray through the steps in order, every step reading its own
+// records with its own interval and scales, the ray's accumulators kept in
+// registers in between. Per step the arithmetic is that of trace_kernel, so
+// the result equals one trace_kernel launch per step bit for bit; what goes
+// is the per-launch and per-step traffic of the ray state (directions,
+// accumulators) and all launches but one.
+template <int INTERP, int ADDR>
+__global__ void __launch_bounds__(NT_MAX, 2)
+    trace_steps_kernel(const TraceArgs A, const __grid_constant__ StepBlock S, const TileCfg t)
+{
+    prefetch_ahead(A, t);
+    int ix, iy;
+    tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
+    if (ix >= A.nx || iy >= A.ny) return;
+    RayAcc acc;
+    acc.loaded = false;
+    for (int g = 0; g < S.n; ++g) {
+        const StepArgs& st = S.s[g];
+        TraceArgs As = A;
+        As.rec = st.rec;
+        As.chi_a = st.chi_a; As.chi_b = st.chi_b;
+        As.cah = st.cah; As.cal = st.cal;
+        As.Lf = st.Lf; As.D0f = st.D0f;
+        As.sch = st.sch; As.scl = st.scl;
+        As.bsh = st.bsh; As.bsl = st.bsl;
+        As.fo[0] = st.fo[0]; As.fo[1] = st.fo[1]; As.fo[2] = st.fo[2];
+        As.fe[0] = st.fe[0]; As.fe[1] = st.fe[1]; As.fe[2] = st.fe[2];
+        As.fs0 = st.fs0; As.fs1 = st.fs1;
+        trace_ray<INTERP, float, kFormKahan, ADDR, true>(As, ix, iy, &acc);
+    }
+    if (acc.loaded) {
+        const long long rid = (long long)iy * A.nx + ix;
+        A.kacc[rid] = acc.k;
+        A.bacc[rid] = acc.b;
+        A.nseg[rid] = acc.n;
+    }
 }
 
 // Persistent work queue over the ray tiles of many bundles (lightcones): each
@@ -657,6 +726,21 @@ cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStre
     case kFormShear: return launch_form<kFormShear>(a, interp, grid, nt, s, t);
     default: return launch_form<kFormKahan>(a, interp, grid, nt, s, t);
     }
+}
+
+cudaError_t launch_trace_steps(const TraceArgs& a, const StepBlock& b, int interp, bool flat, cudaStream_t s)
+{
+    const TileCfg t{};
+    if (b.n < 1 || b.n > kMaxStepBlock) return cudaErrorInvalidValue;
+    const dim3 grid = tile_grid(t, a.nx, a.ny);
+    const int nt = 32 * t.bwx * t.bwy;
+    if (interp == RR_TRILINEAR) {
+        if (flat && a.periodic) trace_steps_kernel<RR_TRILINEAR, kAddrFlat><<<grid, nt, 0, s>>>(a, b, t);
+        else trace_steps_kernel<RR_TRILINEAR, kAddrPlanes><<<grid, nt, 0, s>>>(a, b, t);
+    } else {
+        trace_steps_kernel<RR_NGP, kAddrPlanes><<<grid, nt, 0, s>>>(a, b, t);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s)

@@ -65,6 +65,12 @@ def test_argument_validation_is_host_side(rr):
     assert lib.rr_tidal_tensor(C.byref(g), C.c_void_p(16), None, C.c_void_p(16), 0, C.cast(bb, C.c_void_p),
                                None) == rr.RR_ERR_ARG
     assert lib.rr_trace_step(None, C.byref(g), C.c_void_p(16), 1.0, 0.0, 1.0, 1.0, None) == rr.RR_ERR_ARG
+    one = (C.c_double * 1)(1.0)
+    recs = (C.c_void_p * 1)(16)
+    assert lib.rr_trace_steps(None, C.byref(g), 1, recs, None, one, one, one, one, None) == rr.RR_ERR_ARG
+    assert lib.rr_tidal_tensor_box(C.byref(g), C.c_void_p(32), None, C.c_void_p(32), 0, None, None) == rr.RR_ERR_ARG
+    assert lib.rr_tidal_tensor_box(C.byref(g), C.c_void_p(32), None, C.c_void_p(16), 0, C.cast(bb, C.c_void_p),
+                                   None) == rr.RR_ERR_ARG
     assert lib.rr_finalize(None, None, None, None) == rr.RR_ERR_ARG
     assert lib.rr_destroy(None) == rr.RR_ERR_ARG
     out = (C.c_int32 * 6)()
