@@ -437,17 +437,36 @@ def run_amr(args, name):
     ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
     ev_td = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
 
-    # the records of step k + 1 on a side stream while step k is traced (two record buffers)
-    recs = [rec] if args.no_pipeline else [rec, gm.record_buffer(rrp.RR_AT_VERTICES, device=dev)]
+    # G steps per rr_amr_trace_steps launch, each step's leaf records in a
+    # buffer of its own (whole mesh); the records of group j + 1 on a side
+    # stream while group j is traced (two sets of G buffers)
     side = None if args.no_pipeline else torch.cuda.Stream(device=dev, priority=-1)
+    G = max(1, min(args.amr_group, 16))
+    groups = [list(range(i, min(i + G, nst))) for i in range(0, nst, G)]
+    sets = [[rec] + [gm.record_buffer(rrp.RR_AT_VERTICES, device=dev) for _ in range(G - 1)]]
+    if not args.no_pipeline:
+        sets.append([gm.record_buffer(rrp.RR_AT_VERTICES, device=dev) for _ in range(G)])
+    ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
+    ev_td = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
 
     def one_pass(src=None, timed_kernels=False):
         rrp.rr_reset(tr.ctx, stream)
         field = phi if src is None else src
-        rrp.pipeline_steps(
-            nst, lambda i, b, s: gm.tidal(field, recs[b], rrp.RR_AT_VERTICES, None, bboxes[i], s),
-            lambda i, b, s: tr.amr_step(gm, recs[b], steps[i].chi_a, steps[i].chi_b, steps[i].scale, steps[i].a, s),
-            stream, side, len(recs), (ev_td, ev_tr) if timed_kernels else None)
+
+        def records(gi, b, s):
+            for j, k in enumerate(groups[gi]):
+                gm.tidal(field, sets[b][j], rrp.RR_AT_VERTICES, None, bboxes[k], s)
+
+        def trace(gi, b, s):
+            ks = groups[gi]
+            if G == 1:
+                st = steps[ks[0]]
+                tr.amr_step(gm, sets[b][0], st.chi_a, st.chi_b, st.scale, st.a, s)
+            else:
+                tr.amr_steps(gm, [sets[b][j] for j in range(len(ks))], [steps[k] for k in ks], s)
+
+        rrp.pipeline_steps(len(groups), records, trace, stream, side, len(sets),
+                           (ev_td, ev_tr) if timed_kernels else None)
         rrp.rr_finalize(tr.ctx, kappa, kborn, stream)
 
     with torch.cuda.stream(stream):
@@ -588,7 +607,8 @@ def run_amr(args, name):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _amr_config(w, mesh, nst) | {"form": "fp32 float-float walk on the finest lattice, Kahan sums",
-                                               "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)]},
+                                               "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)],
+                                               "steps_per_launch": G},
         "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
         "segments_per_step": segs,
         "setup_s": {"mesh_and_potential": t_gen, "plan": t_plan},
@@ -607,7 +627,7 @@ def run_amr(args, name):
                                 "generic AMR walk set up as the ISW integral, CUDA events per step, mean of 2"},
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "trace_amr_kernel<trilinear>",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "trace_amr_steps_kernel<trilinear>" if G > 1 else "trace_amr_kernel<trilinear>",
             "note": f"logical gather bytes: {BYTES_PER_SEGMENT} B per leaf segment (the leaf's 8 corner "
                     f"records) x leaf segments / trace time; peak of {peak_kind} copy bandwidth"},
         "tidal_per_pass": {"launches": nst * (w.lmax + 3), "ms": tidal_ms / args.steps,
@@ -621,7 +641,7 @@ def run_amr(args, name):
                                      "cell read + 256 B of records per leaf written (plan tables not counted)"},
         "e2e": {"value": segs * args.steps / sum(e2e), "unit": UNIT, "h2d_bytes_per_step": int(flat.nbytes),
                 "d2h_bytes_per_step": int(k_host.numel() * 8 * 2)},
-        "gpu_launches": args.steps * (nst * (w.lmax + 4) + 1),
+        "gpu_launches": args.steps * (nst * (w.lmax + 3) + len(groups) + 1),
         "clocks": clocks,
         "trace_src": _src_hash("trace_amr.cu", "walk.cuh"),
     }
@@ -993,6 +1013,9 @@ def main():
                     help="do not run the adaptive-mesh, batched and differentiation workloads after the main one")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="compute each step's records and trace it in order on one stream (one record buffer)")
+    ap.add_argument("--amr-group", type=int, default=4,
+                    help="adaptive mesh: steps traced per launch (rr_amr_trace_steps; a whole-mesh leaf-record "
+                         "buffer per step of a group, two sets); 1: one rr_amr_trace_step per step")
     ap.add_argument("--group", type=int, default=16,
                     help="uniform grid: steps traced per launch (rr_trace_steps on box-local records of each "
                          "step's footprint); 1: one rr_trace_step per step on whole-grid records")
@@ -1348,7 +1371,7 @@ def main():
         "shear": shear,
         "method_a": method_a,
         "generic_isw": generic,
-        "gpu_launches": args.steps * (2 * nst + 1),
+        "gpu_launches": args.steps * (nst + nlaunch + 1),
         "clocks": clocks,
         "trace_src": h,
     }

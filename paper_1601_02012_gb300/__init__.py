@@ -269,6 +269,13 @@ class Tracer:
                 self.steps(grid, box_recs[k0:i + 1], steps[k0:i + 1], boxes=bboxes[k0:i + 1], stream=stream)
         return total
 
+    def amr_steps(self, mesh, leaf_recs, steps, stream=None):
+        """rr_amr_trace_steps: the given steps over ``mesh`` in order, step i
+        reading leaf_recs[i]; the default form traces up to 16 per launch."""
+        _rr.rr_amr_trace_steps(self.ctx, mesh.handle, list(leaf_recs), [st.chi_a for st in steps],
+                               [st.chi_b for st in steps], [st.scale for st in steps], [st.a for st in steps],
+                               stream)
+
     def amr_step(self, mesh, leaf_rec, chi_a, chi_b, scale=1.0, a=1.0, stream=None):
         """One step over an adaptive mesh (``AmrMesh``) from its leaf records."""
         rr_amr_trace_step(self.ctx, mesh.handle, leaf_rec, chi_a, chi_b, scale, a, stream)

@@ -84,6 +84,7 @@ def load() -> C.CDLL:
             "rr_trace_step": ([P, P, P, D, D, D, D, P], C.c_int),
             "rr_trace_steps": ([P, P, I32, P, P, P, P, P, P, P], C.c_int),
             "rr_tidal_tensor_box": ([P, P, P, P, I32, P, P], C.c_int),
+            "rr_amr_trace_steps": ([P, P, I32, P, P, P, P, P, P], C.c_int),
             "rr_finalize": ([P, P, P, P], C.c_int),
             "rr_sync_status": ([P, P], C.c_int),
             "rr_segment_count": ([P, C.POINTER(C.c_uint64), P, P], C.c_int),
@@ -271,6 +272,18 @@ def rr_trace_steps(ctx, grid: rr_grid_desc, recs, chi_a, chi_b, scale, a_step, b
         bx = (C.c_int32 * (6 * max(n, 1)))(*[int(v) for bb in boxes for v in bb])
     _check(load().rr_trace_steps(ctx, C.byref(grid), int(n), ptrs, bx, arr[0], arr[1], arr[2], arr[3],
                                  _stream(stream)), "rr_trace_steps")
+
+
+def rr_amr_trace_steps(ctx, mesh, leaf_recs, chi_a, chi_b, scale, a_step, stream=None) -> None:
+    """Consecutive steps over an adaptive mesh (equal lengths): leaf_recs[i]
+    the leaf records of step i."""
+    n = len(leaf_recs)
+    if not (len(chi_a) == len(chi_b) == len(scale) == len(a_step) == n):
+        raise ValueError("rr_amr_trace_steps: per-step sequences of different lengths")
+    ptrs = (C.c_void_p * max(n, 1))(*[_ptr(r) for r in leaf_recs])
+    arr = [(C.c_double * max(n, 1))(*[float(x) for x in v]) for v in (chi_a, chi_b, scale, a_step)]
+    _check(load().rr_amr_trace_steps(ctx, mesh, int(n), ptrs, arr[0], arr[1], arr[2], arr[3], _stream(stream)),
+           "rr_amr_trace_steps")
 
 
 def rr_tidal_tensor_box(grid: rr_grid_desc, phi, delta, rec, where: int, bbox, stream=None) -> None:

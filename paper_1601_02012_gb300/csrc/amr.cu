@@ -918,6 +918,79 @@ rr_status rr_amr_scalars(rr_amr* A, const float* field0, const float* prev0, dou
     return amr_records(A, field0, where, leaf_rec, cell_buf, bbox, stream, 0, &sc);
 }
 
+static TraceArgs amr_trace_args(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, double chi_a, double chi_b,
+                                double scale, double a_step)
+{
+    // the walk runs on the finest lattice: n 2^lmax cells of h_0 / 2^lmax
+    rr_grid_desc fine;
+    fine.n[0] = fine.n[1] = fine.n[2] = A->h.n << A->h.lmax;
+    fine.box = A->h.box;
+    fine.omega_m = A->h.omega_m;
+    TraceArgs a = make_trace_args(ctx, &fine, leaf_rec, chi_a, chi_b, scale, a_step);
+    // FP32 path variable: sub-steps of at most 256 finest cells (and 32 coarse
+    // ones), so that an ulp of the path stays below 2e-5 of a finest cell; 64
+    // finest cells gave maps within 1.2e-6 of the map rms of these and a 14 %
+    // slower walk on the production mesh (the restarts' set-up and link descent)
+    a.sub_len = (float)(std::min(32.0, 256.0 / (double)(1 << A->h.lmax)) * (A->h.box / A->h.n));
+    return a;
+}
+
+rr_status rr_amr_trace_steps(rr_ctx* ctx, rr_amr* A, int32_t nsteps, const float* const* leaf_rec,
+                             const double* chi_a, const double* chi_b, const double* scale, const double* a_step,
+                             void* stream)
+{
+    if (!ctx || !A || nsteps < 0) return RR_ERR_ARG;
+    if (nsteps == 0) return RR_OK;
+    if (!leaf_rec || !chi_a || !chi_b || !scale || !a_step) return RR_ERR_ARG;
+    if (ctx->bundle.flags & (RR_SHEAR | RR_METHOD_A | RR_GENERIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS)) {
+        // the other forms (or the errors of rr_amr_trace_step): step by step
+        for (int32_t i = 0; i < nsteps; ++i) {
+            rr_status st = rr_amr_trace_step(ctx, A, leaf_rec[i], chi_a[i], chi_b[i], scale[i], a_step[i], stream);
+            if (st != RR_OK) return st;
+        }
+        return RR_OK;
+    }
+    rr_grid_desc g;   // the coarse grid: argument and step-order checks
+    g.n[0] = g.n[1] = g.n[2] = A->h.n;
+    g.box = A->h.box;
+    g.omega_m = A->h.omega_m;
+    const size_t log0 = ctx->log.size();
+    const bool reloc0 = ctx->relocated;
+    for (int32_t i = 0; i < nsteps; ++i) {
+        rr_status st = validate_step(ctx, &g, leaf_rec[i], chi_a[i], chi_b[i], scale[i], a_step[i]);
+        if (st != RR_OK) {
+            ctx->log.resize(log0);
+            ctx->relocated = reloc0;
+            return st;
+        }
+        StepRecord r = make_step_record(ctx, &g, chi_a[i], chi_b[i], scale[i], a_step[i]);
+        r.amr = 1;
+        ctx->log.push_back(r);
+        ctx->relocated = false;
+    }
+    AmrDevice m;
+    m.link = A->d_link;
+    m.n = A->h.n;
+    m.lmax = A->h.lmax;
+    const TraceArgs a0 = amr_trace_args(ctx, A, leaf_rec[0], chi_a[0], chi_b[0], scale[0], a_step[0]);
+    cudaError_t e = cudaSuccess;
+    for (int32_t i = 0; i < nsteps && e == cudaSuccess;) {
+        StepBlock blk{};
+        blk.n = 0;
+        while (i < nsteps && blk.n < kMaxStepBlock) {
+            const TraceArgs a = amr_trace_args(ctx, A, leaf_rec[i], chi_a[i], chi_b[i], scale[i], a_step[i]);
+            StepArgs& st = blk.s[blk.n++];
+            st.rec = a.rec;
+            st.chi_a = a.chi_a; st.chi_b = a.chi_b;
+            st.cah = a.cah; st.cal = a.cal; st.Lf = a.Lf; st.D0f = a.D0f;
+            st.sch = a.sch; st.scl = a.scl; st.bsh = a.bsh; st.bsl = a.bsl;
+            ++i;
+        }
+        e = launch_trace_amr_steps(a0, m, blk, ctx->bundle.interp, (cudaStream_t)stream);
+    }
+    return status_of_cuda(e);
+}
+
 rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, double chi_a, double chi_b,
                             double scale, double a_step, void* stream)
 {
@@ -929,15 +1002,7 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* A, const float* leaf_rec, doubl
     g.omega_m = A->h.omega_m;
     rr_status st = validate_step(ctx, &g, leaf_rec, chi_a, chi_b, scale, a_step);
     if (st != RR_OK) return st;
-    // the walk runs on the finest lattice: n 2^lmax cells of h_0 / 2^lmax
-    rr_grid_desc fine = g;
-    fine.n[0] = fine.n[1] = fine.n[2] = A->h.n << A->h.lmax;
-    TraceArgs a = make_trace_args(ctx, &fine, leaf_rec, chi_a, chi_b, scale, a_step);
-    // FP32 path variable: sub-steps of at most 256 finest cells (and 32 coarse
-    // ones), so that an ulp of the path stays below 2e-5 of a finest cell; 64
-    // finest cells gave maps within 1.2e-6 of the map rms of these and a 14 %
-    // slower walk on the production mesh (the restarts' set-up and link descent)
-    a.sub_len = (float)(std::min(32.0, 256.0 / (double)(1 << A->h.lmax)) * (A->h.box / A->h.n));
+    TraceArgs a = amr_trace_args(ctx, A, leaf_rec, chi_a, chi_b, scale, a_step);
     AmrDevice m;
     m.link = A->d_link;
     m.n = A->h.n;

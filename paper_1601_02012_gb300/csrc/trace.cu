@@ -100,15 +100,6 @@ __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], in
 //               seam and the grid has fewer than 2^31 points: the host checks
 //               the step's footprint box; each sub-step checks its own cell
 //               range first and, outside it, flags kErrRange and reads nothing.
-// A ray's accumulators held in registers across the steps of one launch
-// (trace_steps_kernel): read from the ray state at the end of the first step,
-// written back after the last.
-struct RayAcc {
-    float2 k, b;
-    uint32_t n;
-    bool loaded;
-};
-
 template <int INTERP, class R, int FORM = kFormKahan, int ADDR = kAddrPlanes, bool REGACC = false>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy, RayAcc* acc = nullptr)
 {

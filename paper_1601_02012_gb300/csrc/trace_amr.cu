@@ -51,9 +51,11 @@ __device__ __forceinline__ int amr_locate(const AmrDevice& M, const int q[3], in
     return v < 0 ? -1 : v;
 }
 
-template <int INTERP, int FORM>
-__device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevice& M, int ix, int iy)
+template <int INTERP, int FORM, bool REGACC = false>
+__device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevice& M, int ix, int iy,
+                                              RayAcc* acc = nullptr)
 {
+    static_assert(!REGACC || FORM == kFormKahan, "register accumulators: the default form");
     constexpr bool SH = FORM == kFormShear;
     constexpr bool MA = FORM == kFormMethodA;
     constexpr bool GEN = FORM == kFormGeneric;
@@ -66,9 +68,11 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     const int NF = A.n0;   // finest cells per side
     RayRange rg;
     if (!ray_range(A, rid, rg)) return;
-    prefetch_l2(A.kacc + rid);
-    prefetch_l2(A.bacc + rid);
-    prefetch_l2(A.nseg + rid);
+    if (!REGACC || !acc->loaded) {
+        prefetch_l2(A.kacc + rid);
+        prefetch_l2(A.bacc + rid);
+        prefetch_l2(A.nseg + rid);
+    }
     if constexpr (SH) {
         prefetch_l2(A.g1acc + rid);
         prefetch_l2(A.g2acc + rid);
@@ -307,6 +311,18 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
     float kh, kl, bh, bl;
     two_sum(s2.s.x, -s2.c.x, kh, kl);
     two_sum(s2.s.y, -s2.c.y, bh, bl);
+    if constexpr (REGACC) {
+        if (!acc->loaded) {
+            acc->k = A.kacc[rid];
+            acc->b = A.bacc[rid];
+            acc->n = A.nseg[rid];
+            acc->loaded = true;
+        }
+        acc->k = ff_mul_add(acc->k, kh, kl, A.sch, A.scl);
+        acc->b = ff_mul_add(acc->b, bh, bl, A.bsh, A.bsl);
+        acc->n += cnt;
+        return;
+    }
     A.kacc[rid] = ff_mul_add(A.kacc[rid], kh, kl, A.sch, A.scl);
     A.bacc[rid] = ff_mul_add(A.bacc[rid], bh, bl, A.bsh, A.bsl);
     A.nseg[rid] += cnt;
@@ -328,7 +344,51 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_amr_kernel(const TraceArgs A,
     if (ix < A.nx && iy < A.ny) trace_ray_amr<INTERP, FORM>(A, M, ix, iy);
 }
 
+// Consecutive steps over the adaptive mesh in one launch (the default form),
+// as trace_steps_kernel does on the uniform grid: every step its own leaf
+// records, interval and scales, the ray's sums in registers in between; per
+// step the arithmetic of trace_amr_kernel, so the same results bit for bit.
+template <int INTERP>
+__global__ void __launch_bounds__(NT_MAX, 2)
+    trace_amr_steps_kernel(const TraceArgs A, const AmrDevice M, const __grid_constant__ StepBlock S, const TileCfg t)
+{
+    int ix, iy;
+    tile_ray(t, blockIdx.x, blockIdx.y, ix, iy);
+    if (ix >= A.nx || iy >= A.ny) return;
+    RayAcc acc;
+    acc.loaded = false;
+    for (int g = 0; g < S.n; ++g) {
+        const StepArgs& st = S.s[g];
+        TraceArgs As = A;
+        As.rec = st.rec;
+        As.chi_a = st.chi_a; As.chi_b = st.chi_b;
+        As.cah = st.cah; As.cal = st.cal;
+        As.Lf = st.Lf; As.D0f = st.D0f;
+        As.sch = st.sch; As.scl = st.scl;
+        As.bsh = st.bsh; As.bsl = st.bsl;
+        trace_ray_amr<INTERP, kFormKahan, true>(As, M, ix, iy, &acc);
+    }
+    if (acc.loaded) {
+        const long long rid = (long long)iy * A.nx + ix;
+        A.kacc[rid] = acc.k;
+        A.bacc[rid] = acc.b;
+        A.nseg[rid] = acc.n;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_trace_amr_steps(const TraceArgs& a, const AmrDevice& m, const StepBlock& b, int interp,
+                                   cudaStream_t s)
+{
+    if (b.n < 1 || b.n > kMaxStepBlock) return cudaErrorInvalidValue;
+    const TileCfg t;
+    const dim3 grid = tile_grid(t, a.nx, a.ny);
+    const dim3 block(32 * t.bwx * t.bwy);
+    if (interp == RR_TRILINEAR) trace_amr_steps_kernel<RR_TRILINEAR><<<grid, block, 0, s>>>(a, m, b, t);
+    else trace_amr_steps_kernel<RR_NGP><<<grid, block, 0, s>>>(a, m, b, t);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, int form)
 {

@@ -56,6 +56,15 @@ __device__ __forceinline__ void prefetch_ahead(const TraceArgs& A, const TileCfg
 
 __device__ __forceinline__ int wrap_once(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
+// A ray's accumulators held in registers across the steps of one launch (the
+// multi-step kernels): read from the ray state at the end of the first step,
+// written back after the last.
+struct RayAcc {
+    float2 k, b;
+    uint32_t n;
+    bool loaded;
+};
+
 struct Rec {
     float4 a, b;
 };

@@ -200,3 +200,41 @@ def test_box_checks(rrp):
             t2.steps(g, recs, steps, boxes=boxes)
         t2.close()
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("interp", [1, 0])
+def test_amr_steps_match_single_launches(rrp, interp):
+    """rr_amr_trace_steps against one rr_amr_trace_step per step on a random
+    mesh: the same maps and segment counts bit for bit; the shear form goes
+    step by step with the same result."""
+    import torch
+    mesh = synth.amr_random(16, 64.0, 2, 7, threshold=1.5, child_sigma=0.8)
+    pots = synth.amr_potential(mesh, synth.amr_density(mesh, 7, child_sigma=0.8))
+    flat = np.concatenate([np.asarray(p, np.float64).reshape(-1) for p in pots]).astype(np.float32)
+    gm = rrp.AmrMesh(16, 2, 64.0, mesh.octs, mesh.omega_m)
+    where = rrp.RR_AT_VERTICES if interp == 1 else rrp.RR_AT_CENTRES
+    phi = torch.from_numpy(flat).cuda()
+    b = synth.Bundle(56, 48, synth.deg(9), synth.deg(7), (31.0, 33.0, 2.0), 60.0, interp=interp)
+    steps = synth.step_schedule(60.0, 19, rescale=True)
+    recs = [gm.tidal(phi, gm.record_buffer(where), where) for _ in range(2)]
+    per_step = [recs[i % 2] for i in range(len(steps))]
+    out = []
+    for kw, fused in (({}, False), ({}, True), ({"shear": True}, False), ({"shear": True}, True)):
+        if interp == 0 and kw:
+            continue
+        tr = rrp.Tracer(b, **kw)
+        if fused:
+            tr.amr_steps(gm, per_step, steps)
+        else:
+            for st, r in zip(steps, per_step):
+                tr.amr_step(gm, r, st.chi_a, st.chi_b, st.scale, st.a)
+        k, kb = tr.finalize()
+        n = tr.segments()
+        torch.cuda.synchronize()
+        out.append((k.cpu().numpy(), kb.cpu().numpy(), n, rrp.rr_step_count(tr.ctx)))
+        tr.close()
+    gm.close()
+    for i in range(0, len(out), 2):
+        one, fused = out[i], out[i + 1]
+        assert np.array_equal(one[0], fused[0]) and np.array_equal(one[1], fused[1])
+        assert one[2] == fused[2] and one[3] == fused[3] == len(steps)
