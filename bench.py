@@ -1098,10 +1098,15 @@ def main():
     side = None if args.no_pipeline else torch.cuda.Stream(device=dev, priority=-1)
     G = 1 if args.fp64_dda else max(1, min(args.group, 16))
     if G > 1:
+        # box-local records need every step's (widened) footprint to be smaller
+        # than the grid on every axis; otherwise whole-grid records, step by step
+        pboxes = [tr.footprint(w.grid, st.chi_a, st.chi_b, pad=1) for st in steps]
+        if any(bb[2 * a + 1] - bb[2 * a] >= int(w.grid.n[a]) for bb in pboxes for a in range(3)):
+            G = 1
+    if G > 1:
         # every step's records over its footprint box (widened by a point) in
         # a box-local buffer of its own; G steps per rr_trace_steps launch; the
         # records of group j + 1 on the side stream while group j is traced
-        pboxes = [tr.footprint(w.grid, st.chi_a, st.chi_b, pad=1) for st in steps]
         brecs = [rrp.box_record_buffer(bb, device=dev) for bb in pboxes]
         groups = [list(range(i, min(i + G, nst))) for i in range(0, nst, G)]
         ev_tr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]

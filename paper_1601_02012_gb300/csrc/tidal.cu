@@ -92,10 +92,12 @@ __device__ __forceinline__ void centre_channels(float p0, float x0m, float x0p, 
     }
 }
 
-// first record of output plane c (unwrapped centre/vertex plane index)
+// first record of output plane c (unwrapped centre/vertex plane index);
+// CMP: the box-local layout
+template <bool CMP>
 __device__ __forceinline__ size_t out_plane(const TidalArgs& a, int c)
 {
-    return a.compact ? (size_t)(c - a.x0) * a.ey * a.ez : (size_t)wrapi(c, a.n0) * a.n1 * a.n2;
+    return CMP ? (size_t)(c - a.x0) * a.ey * a.ez : (size_t)wrapi(c, a.n0) * a.n1 * a.n2;
 }
 
 // one 32-byte tidal record {c0..c3}, {c4, c5, c6, 0} in a single 256-bit store
@@ -169,7 +171,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // a non-finite sum) after waiting, bounded again, for its copies in flight.
 // (4 resident CTAs per SM: 64 registers; uncapped, 69 registers left 3 and
 // measured 9 % slower on a 512^3 grid)
-template <int MODE, int KIND, bool TMA>
+template <int MODE, int KIND, bool TMA, bool CMP = false>
 __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const __grid_constant__ CUtensorMap map)
 {
     constexpr int V = (MODE == 0) ? 1 : 0;
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const _
         oy[k] = py0 + r0 + k - V;
         out_ok[k] = oz_ok && (r0 + k) >= V && oy[k] < a.ey;
         out_off[k] = !out_ok[k] ? 0
-                     : a.compact ? (size_t)oy[k] * a.ez + oz
+                     : CMP ? (size_t)oy[k] * a.ez + oz
                                  : (size_t)wrapi(a.y0 + oy[k], a.n1) * a.n2 + wrapi(a.z0 + oz, a.n2);
     }
     const int o = (r0 + 1) * RP + (tz + 1) + dz;     // first centre in a ring slot
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const _
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (c > c_first && out_ok[k]) {
-                    const size_t pt = out_plane(a, c) + out_off[k];
+                    const size_t pt = out_plane<CMP>(a, c) + out_off[k];
                     if constexpr (KIND == 0) {
                         store_rec(a.rec + 2 * pt, (prev[k][0] + b[k][0]) * 0.125f, (prev[k][1] + b[k][1]) * 0.125f,
                                   (prev[k][2] + b[k][2]) * 0.125f, (prev[k][3] + b[k][3]) * 0.125f,
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const _
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (!out_ok[k]) continue;
-                const size_t pt = out_plane(a, c) + out_off[k];
+                const size_t pt = out_plane<CMP>(a, c) + out_off[k];
                 if constexpr (KIND == 0) {
                     store_rec(a.rec + 2 * pt, h[k][0], h[k][1], h[k][2], h[k][3], h[k][4], h[k][5], h[k][6]);
                 } else {
@@ -652,6 +654,17 @@ cudaError_t launch_tidal(const rr_grid_desc& g, const float* phi, const float* d
         if (tma) tidal_kernel<M, K, true><<<grid, NT, 0, s>>>(a, map);                \
         else tidal_kernel<M, K, false><<<grid, NT, 0, s>>>(a, map);                  \
     } while (0)
+    if (a.compact) {
+        // box-local tidal records (the other kinds are whole-grid only)
+        if (where == RR_AT_VERTICES) {
+            if (tma) tidal_kernel<0, 0, true, true><<<grid, NT, 0, s>>>(a, map);
+            else tidal_kernel<0, 0, false, true><<<grid, NT, 0, s>>>(a, map);
+        } else {
+            if (tma) tidal_kernel<1, 0, true, true><<<grid, NT, 0, s>>>(a, map);
+            else tidal_kernel<1, 0, false, true><<<grid, NT, 0, s>>>(a, map);
+        }
+        return cudaGetLastError();
+    }
     if (kind == 0) {
         if (where == RR_AT_VERTICES) RR_TIDAL_LAUNCH(0, 0);
         else RR_TIDAL_LAUNCH(1, 0);
