@@ -430,22 +430,40 @@ def pipeline_steps(n, records, trace, stream, side=None, nbuf=1, timing=None):
         used[i].record(stream)
 
 
-def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=True, stream=None):
+def trace_kappa(phi, grid, bundle, steps, delta=None, fp64_dda=False, footprint=True, stream=None, group=16):
     """Trace a bundle through a sequence of steps on one potential.
 
     phi: device float32 tensor n0 x n1 x n2 (Phi/c^2 at cell centres).
     steps: objects with chi_a, chi_b, scale, a (the step's field is scale * Phi).
     For each step the records are recomputed (restricted to the step's
     footprint when ``footprint``) and the bundle is advanced; returns the FP64
-    (kappa, kappa_born) maps and the number of cell segments.
+    (kappa, kappa_born) maps and the number of cell segments. For a periodic
+    trilinear bundle in the FP32 walk whose steps' footprints (widened by a
+    point) are smaller than the grid, each step's records are computed over
+    its footprint box only (box-local) and ``group`` steps are traced per
+    launch (rr_trace_steps; the same maps bit for bit); group=1: one
+    rr_trace_step per step on whole-grid records.
     """
     tr = Tracer(bundle, fp64_dda=fp64_dda)
     try:
-        rec = record_buffer(grid, device=phi.device)
-        for st in steps:
-            bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
-            tr.tidal(grid, phi, rec, delta=delta, bbox=bbox, stream=stream)
-            tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
+        boxes = None
+        if group > 1 and footprint and not fp64_dda and int(bundle.interp) == RR_TRILINEAR and \
+                (int(tr.desc.flags) & _rr.RR_PERIODIC):
+            boxes = [tr.footprint(grid, st.chi_a, st.chi_b, pad=1) for st in steps]
+            if any(bb[2 * a + 1] - bb[2 * a] >= int(grid.n[a]) for bb in boxes for a in range(3)):
+                boxes = None
+        if boxes is not None:
+            recs = [box_record_buffer(bb, device=phi.device) for bb in boxes]
+            for i in range(0, len(steps), group):
+                for k in range(i, min(i + group, len(steps))):
+                    tr.tidal_box(grid, phi, recs[k], boxes[k], delta=delta, stream=stream)
+                tr.steps(grid, recs[i:i + group], steps[i:i + group], boxes=boxes[i:i + group], stream=stream)
+        else:
+            rec = record_buffer(grid, device=phi.device)
+            for st in steps:
+                bbox = tr.footprint(grid, st.chi_a, st.chi_b) if footprint else None
+                tr.tidal(grid, phi, rec, delta=delta, bbox=bbox, stream=stream)
+                tr.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream=stream)
         k, kb = tr.finalize(stream=stream)
         return k, kb, tr.segments()
     finally:
