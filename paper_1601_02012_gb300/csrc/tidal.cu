@@ -169,10 +169,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // through registers, a plane ahead. A copy that does not complete within
 // kWaitTries polls makes the block write NaN records (the trace then reports
 // a non-finite sum) after waiting, bounded again, for its copies in flight.
-// (4 resident CTAs per SM: 64 registers; uncapped, 69 registers left 3 and
-// measured 9 % slower on a 512^3 grid)
+// (3 resident CTAs per SM: 80 registers, no spills. With the planes staged
+// through registers, 4 CTAs at 64 registers had been 9 % faster; with the
+// tensor copies, 3 CTAs measure 5 % faster than 4, whose cap spills)
 template <int MODE, int KIND, bool TMA, bool CMP = false>
-__global__ void __launch_bounds__(NT, 4) tidal_kernel(const TidalArgs a, const __grid_constant__ CUtensorMap map)
+__global__ void __launch_bounds__(NT, 3) tidal_kernel(const TidalArgs a, const __grid_constant__ CUtensorMap map)
 {
     constexpr int V = (MODE == 0) ? 1 : 0;
     constexpr int NC = KIND == 0 ? 7 : 4;            // channels
