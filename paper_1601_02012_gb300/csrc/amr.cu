@@ -868,6 +868,37 @@ static rr_status amr_records(rr_amr* A, const float* phi, int32_t where, float* 
         // vertices read leaves up to 3 coarse cells outside the box; an
         // interpolated cell reads the coarser level one coarse cell further out
         a.margin = 3 + h.lmax - l;
+        if (l == 0 && !grad && !sc && ((uintptr_t)H & 31u) == 0) {
+            // the domain level is the regular coarse grid in row-major cell
+            // order with every neighbour present: its second differences are
+            // those of the uniform tidal kernel (same formulas, same order of
+            // operations), which marches its planes by tensor copy; records at
+            // the cell centres, over the box widened by the margin
+            rr_grid_desc cg;
+            cg.n[0] = cg.n[1] = cg.n[2] = h.n;
+            cg.box = h.box;
+            cg.omega_m = h.omega_m;
+            int32_t cb[6];
+            const int32_t* cbp = nullptr;
+            if (!box.all) {
+                const int b0[3] = {box.x0, box.y0, box.z0}, bw[3] = {box.wx, box.wy, box.wz};
+                bool whole = true;
+                for (int q = 0; q < 3; ++q) {
+                    if (bw[q] + 2 * a.margin >= h.n) {
+                        cb[2 * q] = 0;
+                        cb[2 * q + 1] = h.n;
+                    } else {
+                        cb[2 * q] = b0[q] - a.margin;
+                        cb[2 * q + 1] = b0[q] + bw[q] + a.margin;
+                        whole = false;
+                    }
+                }
+                if (!whole) cbp = cb;
+            }
+            const cudaError_t e = launch_tidal(cg, phi, nullptr, H, RR_AT_CENTRES, cbp, s, 0);
+            if (e != cudaSuccess) return status_of_cuda(e);
+            continue;
+        }
         a.cells = level_cells(l, a.margin);
         const int64_t cnt = a.cells.pre[a.cells.n];
         if (cnt == 0) continue;
