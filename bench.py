@@ -686,10 +686,30 @@ def run_amr(args, name):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
-def _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, nck=8):
+def _group_trace(rrp, ctx, gd, phi, where, steps, idx, box, stream, cuts=()):
+    """Box-local records of steps idx (consecutive) then rr_trace_steps over
+    them, at most 16 per call and a new call at each step in ``cuts``."""
+    pboxes, brecs = box
+    for k in idx:
+        rrp._rr.rr_tidal_tensor_box(gd, phi, None, brecs[k], where, pboxes[k], stream)
+    run = []
+    for k in list(idx) + [None]:
+        if run and (k is None or k in cuts or len(run) == 16):
+            rrp.rr_trace_steps(ctx, gd, [brecs[q] for q in run], [steps[q].chi_a for q in run],
+                               [steps[q].chi_b for q in run], [steps[q].scale for q in run],
+                               [steps[q].a for q in run], [pboxes[q] for q in run], stream)
+            run = []
+        if k is not None:
+            run.append(k)
+
+
+def _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, nck=8, box=None):
     """Time kappa maps for nck source distances (the step boundaries nearest
     to chi_s j / nck): one moments pass with snapshots vs one ordinary pass per
-    source distance; the maps of the two agree to the stated difference."""
+    source distance; the maps of the two agree to the stated difference. box:
+    (footprint boxes, box-local record buffers) per step: both sides trace up
+    to 16 steps per launch (rr_trace_steps), the moments pass cutting its
+    launches at the snapshots."""
     nst = len(steps)
     picks = sorted({min(range(nst), key=lambda i: abs(steps[i].chi_a - w.bundle.chi_s * j / nck))
                     for j in range(1, nck + 1)})
@@ -700,6 +720,15 @@ def _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush,
 
     def moments_pass():
         rrp.rr_reset(trm.ctx, stream)
+        if box is not None:
+            cuts = sorted(snaps)
+            bounds = [0] + cuts + [nst]
+            for a, b in zip(bounds[:-1], bounds[1:]):
+                if a in snaps:
+                    trm.moments(snaps[a], stream)
+                _group_trace(rrp, trm.ctx, gd, phi, trm.where, steps, range(a, b), box, stream)
+            trm.moments(m_end, stream)
+            return
         for i, st in enumerate(steps):
             if i in snaps:
                 trm.moments(snaps[i], stream)
@@ -719,6 +748,10 @@ def _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush,
     def ordinary_passes():
         for i in picks:
             rrp.rr_reset(ctxs[i], stream)
+            if box is not None:
+                _group_trace(rrp, ctxs[i], gd, phi, where, steps, range(i, nst), box, stream)
+                rrp.rr_finalize(ctxs[i], maps[i], None, stream)
+                continue
             for j in range(i, nst):
                 st = steps[j]
                 rrp.rr_tidal_tensor(gd, phi, None, rec, where, bboxes[j], stream)
@@ -754,10 +787,12 @@ def _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush,
             "max_over_rms_vs_ordinary": worst,
             "note": "one pass in the moments form with a snapshot at each source distance, against one "
                     "ordinary pass per source distance (each from its chi_s down to 0, contexts created "
-                    "before the timing); CUDA events, L2 flushed before each"}
+                    "before the timing); CUDA events, L2 flushed before each"
+                    + ("; both with box-local records and up to 16 steps per launch (the moments pass "
+                       "cut at the snapshots)" if box is not None else "")}
 
 
-def _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, kappa_trace_ms, reps=3):
+def _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, kappa_trace_ms, reps=3, box=None):
     """Time the trace kernels of a pass in the shear form (kappa, Born kappa,
     gamma1 and gamma2 of Eqs. gamma1, gamma2 in one walk) against those of the
     default form (kappa_trace_ms, per pass); the shear form's kappa is checked
@@ -769,8 +804,25 @@ def _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, kappa
     k = torch.empty((ny, nx), dtype=torch.float64, device=phi.device)
     kb = torch.empty_like(k)
 
+    groups = [list(range(i, min(i + 16, nst))) for i in range(0, nst, 16)]
+    evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
+
     def shear_pass(timed_kernels):
         rrp.rr_reset(trs.ctx, stream)
+        if box is not None:
+            # box-local records, 16 steps per launch, as the default form's pass
+            pboxes, brecs = box
+            for i in range(nst):
+                trs.tidal_box(w.grid, phi, brecs[i], pboxes[i], stream=stream)
+            for (e0, e1), ks in zip(evg, groups):
+                if timed_kernels:
+                    e0.record(stream)
+                trs.steps(w.grid, [brecs[q] for q in ks], [steps[q] for q in ks], boxes=[pboxes[q] for q in ks],
+                          stream=stream)
+                if timed_kernels:
+                    e1.record(stream)
+            rrp.rr_finalize(trs.ctx, k, kb, stream)
+            return
         for i, st in enumerate(steps):
             rrp.rr_tidal_tensor(gd, phi, None, rec, trs.where, bboxes[i], stream)
             if timed_kernels:
@@ -786,7 +838,7 @@ def _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, kappa
         for _ in range(reps):
             flush.fill_(1.0)
             shear_pass(True)
-            ms.append(sum(a.elapsed_time(b) for a, b in ev))
+            ms.append(sum(a.elapsed_time(b) for a, b in (evg if box is not None else ev)))
         segs = trs.segments()
         g1, g2 = trs.shear(stream=stream)
         torch.cuda.synchronize()
@@ -799,7 +851,8 @@ def _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, kappa
             "rms_gamma1": rms_g[0], "rms_gamma2": rms_g[1], "kappa": k, "kborn": kb,
             "note": "trace kernels of one pass in the shear form (kappa, Born kappa, gamma1, gamma2 "
                     "in one walk), CUDA events per launch, L2 flushed before each pass, mean of "
-                    f"{reps} passes; the default form's per-pass trace time beside it"}
+                    f"{reps} passes; the default form's per-pass trace time beside it"
+                    + ("; box-local records, 16 steps per launch" if box is not None else "")}
 
 
 def _method_a_form(rrp, torch, w, steps, gd, phi, bboxes, stream, flush, kappa_pass_ms, kappa, reps=3):
@@ -1279,10 +1332,11 @@ def main():
         method_a = None
         generic = None
         if world == 1 and not args.compact:
-            sources = _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush)
+            box = (pboxes, brecs) if G > 1 else None
+            sources = _source_redshifts(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush, box=box)
             # the shear in the same walk (Eqs. gamma1, gamma2)
             shear = _shear_form(rrp, torch, w, steps, gd, phi, rec, bboxes, stream, flush,
-                                trace_ms / args.steps)
+                                trace_ms / args.steps, box=box)
             one_pass()
             ks, kbs = shear.pop("kappa"), shear.pop("kborn")
             rms = float(torch.sqrt(torch.mean(kappa * kappa)))

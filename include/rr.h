@@ -359,17 +359,19 @@ rr_status rr_shear(rr_ctx* ctx, double* gamma1, double* gamma2, void* stream);
  * the records of box i, in the box-local layout of rr_tidal_tensor_box, and
  * box i (periodically) must hold the step's footprint box (rr_footprint_bbox
  * of the whole bundle) widened by one point on each side, since the walk
- * checks one vertex plane beyond it; boxes need a periodic trilinear bundle in the
- * default form (RR_ERR_ARG otherwise, or for a box that misses the footprint).
- * A step's records then take its footprint's memory only, so that the
- * records of many steps can be resident at once. In the default FP32 form (no RR_FP64_DDA, RR_PLAIN_SUMS,
- * RR_SOURCE_MOMENTS, RR_SHEAR, RR_METHOD_A or RR_GENERIC) up to 16 consecutive
- * steps are traced by one launch: each ray walks them in turn with its sums
+ * checks one vertex plane beyond it; boxes need a periodic trilinear bundle
+ * whose form reads tidal records (not RR_METHOD_A or RR_GENERIC; RR_ERR_ARG
+ * otherwise, or for a box that misses the footprint). A step's records then
+ * take its footprint's memory only, so that the records of many steps can be
+ * resident at once. In the FP32 compensated forms (not RR_FP64_DDA or
+ * RR_PLAIN_SUMS) up to 16 consecutive steps are traced by one launch: each
+ * ray walks them in turn with its sums (and its shear pair or B moments)
  * held on chip, instead of reading and writing its state at every step (Sec.
  * 2.5.2 moves all rays to the end of one time step before the next; with the
  * records of several steps resident, one ray is moved through them). Steps
- * whose footprint reaches the periodic seam (trilinear), and the other forms,
- * get one launch each. If a step fails its checks nothing is launched and
+ * whose footprint reaches the periodic seam (trilinear, whole-grid records),
+ * and the other forms, get one launch each. A moments snapshot (rr_moments)
+ * between steps needs a call boundary there. If a step fails its checks nothing is launched and
  * the log is unchanged (RR_ERR_ARG / RR_ERR_STATE as rr_trace_step);
  * asynchronous otherwise. nsteps == 0: no-op.
  */

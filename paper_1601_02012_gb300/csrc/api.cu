@@ -570,14 +570,21 @@ rr_status rr_trace_steps(rr_ctx* ctx, const rr_grid_desc* grid, int32_t nsteps, 
     if (nsteps == 0) return RR_OK;
     if (!rec || !chi_a || !chi_b || !scale || !a_step) return RR_ERR_ARG;
     const rr_bundle_desc& b = ctx->bundle;
-    const bool fused = !(b.flags & (RR_FP64_DDA | RR_SOURCE_MOMENTS | RR_PLAIN_SUMS | RR_SHEAR | RR_METHOD_A |
-                                    RR_GENERIC));
+    const bool fused = !(b.flags & (RR_FP64_DDA | RR_PLAIN_SUMS));
+    const int form = (b.flags & RR_SOURCE_MOMENTS) ? kFormMoments
+                     : (b.flags & RR_SHEAR)        ? kFormShear
+                     : (b.flags & RR_METHOD_A)     ? kFormMethodA
+                     : (b.flags & RR_GENERIC)      ? kFormGeneric
+                                                   : kFormKahan;
     rr_bundle_desc whole = b;
     whole.ny = ctx->ny_full;
     if (boxes) {
         // records of each step's box only: the flat walk over them (trilinear,
-        // periodic, the default form); each box must hold the step's footprint
-        if (!fused || b.interp != RR_TRILINEAR || !(b.flags & RR_PERIODIC)) return RR_ERR_ARG;
+        // periodic, a form that reads tidal records); each box must hold the
+        // step's footprint
+        if (!fused || form == kFormMethodA || form == kFormGeneric || b.interp != RR_TRILINEAR ||
+            !(b.flags & RR_PERIODIC))
+            return RR_ERR_ARG;
         rr_status st = check_grid(grid);
         if (st != RR_OK) return st;
         for (int32_t i = 0; i < nsteps; ++i) {
@@ -635,7 +642,7 @@ rr_status rr_trace_steps(rr_ctx* ctx, const rr_grid_desc* grid, int32_t nsteps, 
         auto flat_at = [&](int32_t k) { return boxes || flat_ok(whole, b.obs, *grid, chi_a[k], chi_b[k]); };
         if (tri && !flat_at(i)) {
             const TraceArgs a = make_trace_args(ctx, grid, rec[i], chi_a[i], chi_b[i], scale[i], a_step[i]);
-            e = launch_trace(a, b.interp, false, s, TileCfg{}, kFormKahan, false);
+            e = launch_trace(a, b.interp, false, s, TileCfg{}, form, false);
             ++i;
             continue;
         }
@@ -665,7 +672,7 @@ rr_status rr_trace_steps(rr_ctx* ctx, const rr_grid_desc* grid, int32_t nsteps, 
             }
             ++i;
         }
-        e = launch_trace_steps(a0, blk, b.interp, tri, s);
+        e = launch_trace_steps(a0, blk, b.interp, tri, s, form);
     }
     return from_cuda(e);
 }

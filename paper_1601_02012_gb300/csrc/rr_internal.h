@@ -153,9 +153,11 @@ enum { kAddrIndex = 0, kAddrPlanes = 1, kAddrFlat = 2 };
 cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStream_t s, const TileCfg& t,
                          int form = kFormKahan, bool flat = false);
 cudaError_t launch_trace_batch(const BatchArgs& b, int interp, bool fp64_dda, int blocks, cudaStream_t s);
-// Steps b.s[0 .. b.n) of the FP32 default form in one launch; a holds the
-// shared fields. flat: every step passed the flat-addressing check (trilinear).
-cudaError_t launch_trace_steps(const TraceArgs& a, const StepBlock& b, int interp, bool flat, cudaStream_t s);
+// Steps b.s[0 .. b.n) of an FP32 compensated form (kFormKahan, kFormShear,
+// kFormMoments, kFormMethodA, kFormGeneric) in one launch; a holds the shared
+// fields. flat: every step passed the flat-addressing check (trilinear).
+cudaError_t launch_trace_steps(const TraceArgs& a, const StepBlock& b, int interp, bool flat, cudaStream_t s,
+                               int form = kFormKahan);
 int batch_blocks_per_sm(int interp, bool fp64_dda, const TileCfg& t);
 dim3 tile_grid(const TileCfg& t, int nx, int ny);
 bool tile_ok(const TileCfg& t);

@@ -103,7 +103,7 @@ __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], in
 template <int INTERP, class R, int FORM = kFormKahan, int ADDR = kAddrPlanes, bool REGACC = false>
 __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy, RayAcc* acc = nullptr)
 {
-    static_assert(!REGACC || (FORM == kFormKahan && sizeof(R) == 4), "register accumulators: FP32 default form");
+    static_assert(!REGACC || (FORM != kFormPlain && sizeof(R) == 4), "register accumulators: FP32 compensated forms");
     using OT = unsigned long long;
     constexpr bool PLANES = ADDR == kAddrPlanes;
     constexpr bool FLAT = ADDR == kAddrFlat;
@@ -123,10 +123,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy, Ra
         prefetch_l2(A.kacc + rid);
         prefetch_l2(A.bacc + rid);
         prefetch_l2(A.nseg + rid);
-    }
-    if constexpr (SH) {
-        prefetch_l2(A.g1acc + rid);
-        prefetch_l2(A.g2acc + rid);
+        if constexpr (SH) {
+            prefetch_l2(A.g1acc + rid);
+            prefetch_l2(A.g2acc + rid);
+        }
     }
     const R chis = (R)A.chi_s;
     const R ichis = F64 ? (R)(1.0 / A.chi_s) : (R)A.inv_chi_s_f;
@@ -516,21 +516,42 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy, Ra
     }
     if (overflow) atomicOr(A.err, kErrStepLimit);
     if (!sk.finite() || !sb.finite()) atomicOr(A.err, kErrNonFinite);
+    if constexpr (REGACC) {
+        // the first step of the launch: the ray's state from memory
+        if (!acc->loaded) {
+            acc->k = A.kacc[rid];
+            acc->b = A.bacc[rid];
+            acc->n = A.nseg[rid];
+            if constexpr (SH) {
+                acc->x1 = A.g1acc[rid];
+                acc->x2 = A.g2acc[rid];
+            }
+            if constexpr (FORM == kFormMoments) {
+                acc->x1 = A.kmom[rid];
+                acc->x2 = A.bmom[rid];
+            }
+            acc->loaded = true;
+        }
+    }
     if constexpr (SH) {
         float gh, gl;
         if (!s2m.finite()) atomicOr(A.err, kErrNonFinite);
         two_sum(s2m.s.x, -s2m.c.x, gh, gl);
-        A.g1acc[rid] = ff_mul_add(A.g1acc[rid], gh, gl, A.sch, A.scl);
+        if constexpr (REGACC) acc->x1 = ff_mul_add(acc->x1, gh, gl, A.sch, A.scl);
+        else A.g1acc[rid] = ff_mul_add(A.g1acc[rid], gh, gl, A.sch, A.scl);
         two_sum(s2m.s.y, -s2m.c.y, gh, gl);
-        A.g2acc[rid] = ff_mul_add(A.g2acc[rid], gh, gl, A.sch, A.scl);
+        if constexpr (REGACC) acc->x2 = ff_mul_add(acc->x2, gh, gl, A.sch, A.scl);
+        else A.g2acc[rid] = ff_mul_add(A.g2acc[rid], gh, gl, A.sch, A.scl);
     }
     if constexpr (FORM == kFormMoments) {
         float mh, ml;
         if (!s2m.finite()) atomicOr(A.err, kErrNonFinite);
         two_sum(s2m.s.x, -s2m.c.x, mh, ml);
-        A.kmom[rid] = ff_mul_add(A.kmom[rid], mh, ml, A.sch, A.scl);
+        if constexpr (REGACC) acc->x1 = ff_mul_add(acc->x1, mh, ml, A.sch, A.scl);
+        else A.kmom[rid] = ff_mul_add(A.kmom[rid], mh, ml, A.sch, A.scl);
         two_sum(s2m.s.y, -s2m.c.y, mh, ml);
-        A.bmom[rid] = ff_mul_add(A.bmom[rid], mh, ml, A.bsh, A.bsl);
+        if constexpr (REGACC) acc->x2 = ff_mul_add(acc->x2, mh, ml, A.bsh, A.bsl);
+        else A.bmom[rid] = ff_mul_add(A.bmom[rid], mh, ml, A.bsh, A.bsl);
     }
     if constexpr (FORM == kFormPlain) {
         // plain FP32 across steps too: the high word only
@@ -543,12 +564,6 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy, Ra
     sk.pair(kh, kl);
     sb.pair(bh, bl);
     if constexpr (REGACC) {
-        if (!acc->loaded) {
-            acc->k = A.kacc[rid];
-            acc->b = A.bacc[rid];
-            acc->n = A.nseg[rid];
-            acc->loaded = true;
-        }
         acc->k = ff_mul_add(acc->k, kh, kl, A.sch, A.scl);
         acc->b = ff_mul_add(acc->b, bh, bl, A.bsh, A.bsl);
         acc->n += cnt;
@@ -576,7 +591,7 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_kernel(const TraceArgs A, con
 // the result equals one trace_kernel launch per step bit for bit; what goes
 // is the per-launch and per-step traffic of the ray state (directions,
 // accumulators) and all launches but one.
-template <int INTERP, int ADDR>
+template <int INTERP, int ADDR, int FORM>
 __global__ void __launch_bounds__(NT_MAX, 2)
     trace_steps_kernel(const TraceArgs A, const __grid_constant__ StepBlock S, const TileCfg t)
 {
@@ -598,13 +613,21 @@ __global__ void __launch_bounds__(NT_MAX, 2)
         As.fo[0] = st.fo[0]; As.fo[1] = st.fo[1]; As.fo[2] = st.fo[2];
         As.fe[0] = st.fe[0]; As.fe[1] = st.fe[1]; As.fe[2] = st.fe[2];
         As.fs0 = st.fs0; As.fs1 = st.fs1;
-        trace_ray<INTERP, float, kFormKahan, ADDR, true>(As, ix, iy, &acc);
+        trace_ray<INTERP, float, FORM, ADDR, true>(As, ix, iy, &acc);
     }
     if (acc.loaded) {
         const long long rid = (long long)iy * A.nx + ix;
         A.kacc[rid] = acc.k;
         A.bacc[rid] = acc.b;
         A.nseg[rid] = acc.n;
+        if constexpr (FORM == kFormShear) {
+            A.g1acc[rid] = acc.x1;
+            A.g2acc[rid] = acc.x2;
+        }
+        if constexpr (FORM == kFormMoments) {
+            A.kmom[rid] = acc.x1;
+            A.bmom[rid] = acc.x2;
+        }
     }
 }
 
@@ -719,17 +742,36 @@ cudaError_t launch_trace(const TraceArgs& a, int interp, bool fp64_dda, cudaStre
     }
 }
 
-cudaError_t launch_trace_steps(const TraceArgs& a, const StepBlock& b, int interp, bool flat, cudaStream_t s)
+template <int FORM>
+static void launch_steps_form(const TraceArgs& a, const StepBlock& b, int interp, bool flat, dim3 grid, int nt,
+                              const TileCfg& t, cudaStream_t s)
+{
+    // the addressing of each form's single-step kernel: flat for trilinear
+    // steps clear of the seam (or box-local records); otherwise vertex-plane
+    // offsets for the default form and vertex indices for the others
+    constexpr int ADDR = FORM == kFormKahan ? kAddrPlanes : kAddrIndex;
+    if (interp == RR_TRILINEAR) {
+        if (flat && a.periodic) trace_steps_kernel<RR_TRILINEAR, kAddrFlat, FORM><<<grid, nt, 0, s>>>(a, b, t);
+        else trace_steps_kernel<RR_TRILINEAR, ADDR, FORM><<<grid, nt, 0, s>>>(a, b, t);
+    } else {
+        trace_steps_kernel<RR_NGP, ADDR, FORM><<<grid, nt, 0, s>>>(a, b, t);
+    }
+}
+
+cudaError_t launch_trace_steps(const TraceArgs& a, const StepBlock& b, int interp, bool flat, cudaStream_t s,
+                               int form)
 {
     const TileCfg t{};
     if (b.n < 1 || b.n > kMaxStepBlock) return cudaErrorInvalidValue;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const int nt = 32 * t.bwx * t.bwy;
-    if (interp == RR_TRILINEAR) {
-        if (flat && a.periodic) trace_steps_kernel<RR_TRILINEAR, kAddrFlat><<<grid, nt, 0, s>>>(a, b, t);
-        else trace_steps_kernel<RR_TRILINEAR, kAddrPlanes><<<grid, nt, 0, s>>>(a, b, t);
-    } else {
-        trace_steps_kernel<RR_NGP, kAddrPlanes><<<grid, nt, 0, s>>>(a, b, t);
+    switch (form) {
+    case kFormKahan: launch_steps_form<kFormKahan>(a, b, interp, flat, grid, nt, t, s); break;
+    case kFormShear: launch_steps_form<kFormShear>(a, b, interp, flat, grid, nt, t, s); break;
+    case kFormMoments: launch_steps_form<kFormMoments>(a, b, interp, flat, grid, nt, t, s); break;
+    case kFormMethodA: launch_steps_form<kFormMethodA>(a, b, interp, flat, grid, nt, t, s); break;
+    case kFormGeneric: launch_steps_form<kFormGeneric>(a, b, interp, flat, grid, nt, t, s); break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

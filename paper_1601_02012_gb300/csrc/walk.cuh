@@ -61,6 +61,7 @@ __device__ __forceinline__ int wrap_once(int c, int n) { return c < 0 ? c + n : 
 // written back after the last.
 struct RayAcc {
     float2 k, b;
+    float2 x1, x2;   // the shear pair (gamma1, gamma2), or the B moments of kappa and Born kappa
     uint32_t n;
     bool loaded;
 };

@@ -95,15 +95,69 @@ def test_steps_flat_only_and_per_step_buffers(rrp, oracle_lib):
     assert int(o.nseg.sum()) == fused[2]
 
 
-def test_steps_other_form_step_by_step(rrp):
-    """The shear form is traced one launch per step: the same maps."""
+@pytest.mark.parametrize("form", ["shear", "moments", "method_a", "generic"])
+def test_steps_other_forms_match_single_launches(rrp, form):
+    """The shear, moments, Method A and generic forms through rr_trace_steps
+    (their extra sums in registers too) against one rr_trace_step per step:
+    every output bit for bit; shear and moments also on box-local records."""
+    import torch
     g = synth.Grid((32, 32, 32), 64.0)
     b = synth.Bundle(40, 36, synth.deg(8), synth.deg(7), (31.0, 33.0, 5.0), 50.0)
-    steps = synth.step_schedule(50.0, 5, rescale=True)
-    recs = _records(rrp, b, g, [synth.grf_phi(32, 64.0, 94)]) * len(steps)
-    one = _trace(rrp, b, g, steps, recs, False, shear=True)
-    fused = _trace(rrp, b, g, steps, recs, True, shear=True)
-    assert np.array_equal(one[0], fused[0]) and np.array_equal(one[1], fused[1]) and one[2] == fused[2]
+    steps = synth.step_schedule(50.0, 7, rescale=True)
+    phi = torch.from_numpy(synth.grf_phi(32, 64.0, 94)).cuda()
+    prev = torch.from_numpy(synth.grf_phi(32, 64.0, 95)).cuda()
+    kw = {form: True}
+
+    def outputs(tr):
+        k, kb = tr.finalize()
+        out = [k.cpu().numpy(), kb.cpu().numpy(), tr.segments()]
+        if form == "shear":
+            g1, g2 = tr.shear()
+            out += [g1.cpu().numpy(), g2.cpu().numpy()]
+        if form == "moments":
+            out.append(tr.moments().cpu().numpy())
+        torch.cuda.synchronize()
+        return out
+
+    def records(tr):
+        rec = tr.record_buffer(g)
+        if form == "generic":
+            tr.scalars(g, phi, rec, channel=0, field_prev=prev, inv_dt=0.5)
+            tr.scalars(g, phi, rec, channel=1)
+        else:
+            tr.tidal(g, phi, rec)
+        return rec
+
+    res = []
+    for fused in (False, True):
+        tr = rrp.Tracer(b, **kw)
+        rec = records(tr)
+        if fused:
+            tr.steps(g, [rec] * len(steps), steps)
+        else:
+            for st in steps:
+                tr.step(g, rec, st.chi_a, st.chi_b, st.scale, st.a)
+        res.append(outputs(tr))
+        tr.close()
+    if form in ("shear", "moments"):
+        tr = rrp.Tracer(b, **kw)
+        boxes = [tr.footprint(g, st.chi_a, st.chi_b, pad=1) for st in steps]
+        recs = [tr.tidal_box(g, phi, rrp.box_record_buffer(bb), bb) for bb in boxes]
+        tr.steps(g, recs, steps, boxes=boxes)
+        res.append(outputs(tr))
+        tr.close()
+    else:
+        tr = rrp.Tracer(b, **kw)
+        bb = tr.footprint(g, steps[0].chi_a, steps[0].chi_b, pad=1)
+        with pytest.raises(rrp.RRError):   # box-local records are tidal records only
+            tr.steps(g, [rrp.box_record_buffer(bb)], steps[:1], boxes=[bb])
+        tr.close()
+    for other in res[1:]:
+        for x, y in zip(res[0], other):
+            if isinstance(x, np.ndarray):
+                assert np.array_equal(x, y)
+            else:
+                assert x == y
 
 
 def test_steps_checks_leave_the_log_unchanged(rrp):
@@ -194,7 +248,7 @@ def test_box_checks(rrp):
         tr.steps(g, recs, steps, boxes=small)
     assert rrp.rr_step_count(tr.ctx) == 0
     tr.close()
-    for kw in ({"shear": True}, {"fp64_dda": True}):
+    for kw in ({"method_a": True}, {"fp64_dda": True}, {"plain_sums": True}):
         t2 = rrp.Tracer(b, **kw)
         with pytest.raises(rrp.RRError):
             t2.steps(g, recs, steps, boxes=boxes)
