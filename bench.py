@@ -522,17 +522,28 @@ def run_amr(args, name):
         k_side = torch.empty_like(kappa)
         kb_side = torch.empty_like(kappa)
         trs = rrp.Tracer(w.bundle, shear=True)
-        ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+
+        # the side forms take the main pass's grouping: G steps per rr_amr_trace_steps
+        # launch, the group's records first into the first set of buffers
+        ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
+
+        def group_walk(tracer, ks, stp, s):
+            if G == 1:
+                st = stp[ks[0]]
+                tracer.amr_step(gm, sets[0][0], st.chi_a, st.chi_b, st.scale, st.a, s)
+            else:
+                tracer.amr_steps(gm, [sets[0][j] for j in range(len(ks))], [stp[k] for k in ks], s)
 
         def shear_pass(timed):
             rrp.rr_reset(trs.ctx, stream)
-            for i, st in enumerate(steps):
-                gm.tidal(phi, rec, rrp.RR_AT_VERTICES, None, bboxes[i], stream)
+            for gi, ks in enumerate(groups):
+                for j, k in enumerate(ks):
+                    gm.tidal(phi, sets[0][j], rrp.RR_AT_VERTICES, None, bboxes[k], stream)
                 if timed:
-                    ev_s[i][0].record(stream)
-                trs.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
+                    ev_s[gi][0].record(stream)
+                group_walk(trs, ks, steps, stream)
                 if timed:
-                    ev_s[i][1].record(stream)
+                    ev_s[gi][1].record(stream)
             rrp.rr_finalize(trs.ctx, k_side, kb_side, stream)
 
         shear_pass(False)
@@ -546,17 +557,19 @@ def run_amr(args, name):
 
         # Method A through the same mesh (rr_amr_gradient records, RR_METHOD_A walk)
         tra = rrp.Tracer(w.bundle, method_a=True)
-        ev_a = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+        ev_a = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
+        steps_a = [synth.Step(st.chi_a, st.chi_b, st.scale, 1.0) for st in steps]
 
         def method_a_pass(timed):
             rrp.rr_reset(tra.ctx, stream)
-            for i, st in enumerate(steps):
+            for gi, ks in enumerate(groups):
                 if timed:
-                    ev_a[i][0].record(stream)
-                gm.gradient(phi, rec, rrp.RR_AT_VERTICES, None, bboxes[i], stream)
-                tra.amr_step(gm, rec, st.chi_a, st.chi_b, st.scale, 1.0, stream)
+                    ev_a[gi][0].record(stream)
+                for j, k in enumerate(ks):
+                    gm.gradient(phi, sets[0][j], rrp.RR_AT_VERTICES, None, bboxes[k], stream)
+                group_walk(tra, ks, steps_a, stream)
                 if timed:
-                    ev_a[i][1].record(stream)
+                    ev_a[gi][1].record(stream)
             rrp.rr_finalize(tra.ctx, k_side, kb_side, stream)
 
         method_a_pass(False)
@@ -574,20 +587,22 @@ def run_amr(args, name):
         trg.set_kernels(((2.0, 0.0, 0.0), (0.0, 1.0, -1.0 / w.bundle.chi_s)))
         cur_g = torch.empty_like(phi)
         prev_g = torch.empty_like(phi)
-        ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+        ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in groups]
+        steps_g = [synth.Step(st.chi_a, st.chi_b, 1.0, st.a) for st in steps]
 
         def generic_pass(timed):
             rrp.rr_reset(trg.ctx, stream)
-            for i, st in enumerate(steps):
-                torch.mul(phi, steps[i - 1].scale if i > 0 else st.scale, out=prev_g)
-                torch.mul(phi, st.scale, out=cur_g)
+            for gi, ks in enumerate(groups):
                 if timed:
-                    ev_g[i][0].record(stream)
-                gm.scalars(cur_g, rec, rrp.RR_AT_VERTICES, prev0=prev_g, inv_dt0=100.0, field1=cur_g,
-                           bbox=bboxes[i], stream=stream)
-                trg.amr_step(gm, rec, st.chi_a, st.chi_b, 1.0, st.a, stream)
+                    ev_g[gi][0].record(stream)
+                for j, k in enumerate(ks):
+                    torch.mul(phi, steps[k - 1].scale if k > 0 else steps[k].scale, out=prev_g)
+                    torch.mul(phi, steps[k].scale, out=cur_g)
+                    gm.scalars(cur_g, sets[0][j], rrp.RR_AT_VERTICES, prev0=prev_g, inv_dt0=100.0, field1=cur_g,
+                               bbox=bboxes[k], stream=stream)
+                group_walk(trg, ks, steps_g, stream)
                 if timed:
-                    ev_g[i][1].record(stream)
+                    ev_g[gi][1].record(stream)
             rrp.rr_finalize(trg.ctx, k_side, kb_side, stream)
 
         generic_pass(False)
@@ -620,13 +635,16 @@ def run_amr(args, name):
                   "kappa_only_trace_ms_per_pass": trace_ms / args.steps,
                   "cost_vs_kappa_only": (sum(sh_ms) / len(sh_ms)) / (trace_ms / args.steps),
                   "note": "trace kernels of one pass in the shear form (kappa, Born kappa, gamma1, gamma2 in "
-                          "one AMR walk), CUDA events per launch, L2 flushed before each pass, mean of 2"},
+                          "one AMR walk), CUDA events per launch (the main pass's steps per launch), L2 flushed "
+                          "before each pass, mean of 2"},
         "method_a": {"ms_per_pass": sum(ma_ms) / len(ma_ms), "method_b_ms_per_pass": total_ms / args.steps,
                      "note": "records (rr_amr_gradient over each step's footprint) and the Method A AMR walk "
-                             "of one pass, CUDA events per step, L2 flushed before each pass, mean of 2"},
+                             "of one pass, CUDA events per group of steps (the main pass's steps per launch), L2 flushed before "
+                             "each pass, mean of 2"},
         "generic_isw": {"ms_per_pass": sum(gen_ms) / len(gen_ms), "method_b_ms_per_pass": total_ms / args.steps,
                         "note": "records (rr_amr_scalars, two channels, over each step's footprint) and the "
-                                "generic AMR walk set up as the ISW integral, CUDA events per step, mean of 2"},
+                                "generic AMR walk set up as the ISW integral, CUDA events per group of steps (the main pass's "
+                                "steps per launch), mean of 2"},
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "trace_amr_steps_kernel<trilinear>" if G > 1 else "trace_amr_kernel<trilinear>",

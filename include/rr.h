@@ -633,11 +633,11 @@ rr_status rr_amr_trace_step(rr_ctx* ctx, rr_amr* mesh, const float* leaf_rec, do
  * a_step[i], stream) would trace it (the same checks, step log and results bit
  * for bit); host arrays of nsteps entries, leaf_rec[i] device leaf-record
  * buffers (the same buffer may serve several steps) that must stay valid until
- * the stream reaches the end of the call. In the default form up to 16
- * consecutive steps are traced by one launch, each ray walking them in turn
- * with its sums held on chip (as rr_trace_steps); the other forms get one
- * launch per step. If a step fails its checks nothing is launched and the log
- * is unchanged. nsteps == 0: no-op.
+ * the stream reaches the end of the call. Up to 16 consecutive steps are
+ * traced by one launch, each ray walking them in turn with its sums (and its
+ * shear pair) held on chip, as rr_trace_steps does. If a step fails its checks
+ * nothing is launched and the log is unchanged (RR_ERR_ARG for the forms
+ * rr_amr_trace_step refuses). nsteps == 0: no-op.
  */
 rr_status rr_amr_trace_steps(rr_ctx* ctx, rr_amr* mesh, int32_t nsteps, const float* const* leaf_rec,
                              const double* chi_a, const double* chi_b, const double* scale, const double* a_step,

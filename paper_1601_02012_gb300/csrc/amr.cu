@@ -973,8 +973,8 @@ rr_status rr_amr_trace_steps(rr_ctx* ctx, rr_amr* A, int32_t nsteps, const float
     if (!ctx || !A || nsteps < 0) return RR_ERR_ARG;
     if (nsteps == 0) return RR_OK;
     if (!leaf_rec || !chi_a || !chi_b || !scale || !a_step) return RR_ERR_ARG;
-    if (ctx->bundle.flags & (RR_SHEAR | RR_METHOD_A | RR_GENERIC | RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS)) {
-        // the other forms (or the errors of rr_amr_trace_step): step by step
+    if (ctx->bundle.flags & (RR_FP64_DDA | RR_PLAIN_SUMS | RR_SOURCE_MOMENTS)) {
+        // the errors of rr_amr_trace_step, step by step
         for (int32_t i = 0; i < nsteps; ++i) {
             rr_status st = rr_amr_trace_step(ctx, A, leaf_rec[i], chi_a[i], chi_b[i], scale[i], a_step[i], stream);
             if (st != RR_OK) return st;
@@ -1017,7 +1017,11 @@ rr_status rr_amr_trace_steps(rr_ctx* ctx, rr_amr* A, int32_t nsteps, const float
             st.sch = a.sch; st.scl = a.scl; st.bsh = a.bsh; st.bsl = a.bsl;
             ++i;
         }
-        e = launch_trace_amr_steps(a0, m, blk, ctx->bundle.interp, (cudaStream_t)stream);
+        e = launch_trace_amr_steps(a0, m, blk, ctx->bundle.interp, (cudaStream_t)stream,
+                                   (ctx->bundle.flags & RR_SHEAR)      ? kFormShear
+                                   : (ctx->bundle.flags & RR_METHOD_A) ? kFormMethodA
+                                   : (ctx->bundle.flags & RR_GENERIC)  ? kFormGeneric
+                                                                       : kFormKahan);
     }
     return status_of_cuda(e);
 }

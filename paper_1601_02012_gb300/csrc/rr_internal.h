@@ -163,9 +163,10 @@ dim3 tile_grid(const TileCfg& t, int nx, int ny);
 bool tile_ok(const TileCfg& t);
 // form: kFormKahan, kFormShear (also gamma1, gamma2 into g1acc, g2acc) or kFormMethodA
 cudaError_t launch_trace_amr(const TraceArgs& a, const AmrDevice& m, int interp, cudaStream_t s, int form = 0);
-// Steps b.s[0 .. b.n) over the adaptive mesh in one launch (the default form)
+// Steps b.s[0 .. b.n) over the adaptive mesh in one launch (kFormKahan,
+// kFormShear, kFormMethodA, kFormGeneric)
 cudaError_t launch_trace_amr_steps(const TraceArgs& a, const AmrDevice& m, const StepBlock& b, int interp,
-                                   cudaStream_t s);
+                                   cudaStream_t s, int form = kFormKahan);
 cudaError_t launch_trace_adjoint(const TraceArgs& a, const AdjArgs& b, int interp, bool fp64_dda, cudaStream_t s);
 // The transposed stencils over the output box [box0, box1) per axis (point
 // indices, unwrapped; an axis whose extent reaches n, or no box, is whole):

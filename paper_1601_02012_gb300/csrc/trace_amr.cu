@@ -55,7 +55,9 @@ template <int INTERP, int FORM, bool REGACC = false>
 __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevice& M, int ix, int iy,
                                               RayAcc* acc = nullptr)
 {
-    static_assert(!REGACC || FORM == kFormKahan, "register accumulators: the default form");
+    static_assert(!REGACC || FORM == kFormKahan || FORM == kFormShear || FORM == kFormMethodA ||
+                      FORM == kFormGeneric,
+                  "register accumulators: the compensated forms of the adaptive-mesh walk");
     constexpr bool SH = FORM == kFormShear;
     constexpr bool MA = FORM == kFormMethodA;
     constexpr bool GEN = FORM == kFormGeneric;
@@ -72,10 +74,10 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
         prefetch_l2(A.kacc + rid);
         prefetch_l2(A.bacc + rid);
         prefetch_l2(A.nseg + rid);
-    }
-    if constexpr (SH) {
-        prefetch_l2(A.g1acc + rid);
-        prefetch_l2(A.g2acc + rid);
+        if constexpr (SH) {
+            prefetch_l2(A.g1acc + rid);
+            prefetch_l2(A.g2acc + rid);
+        }
     }
     const float chis = (float)A.chi_s;
     const float ichis = A.inv_chi_s_f;
@@ -316,11 +318,23 @@ __device__ __forceinline__ void trace_ray_amr(const TraceArgs& A, const AmrDevic
             acc->k = A.kacc[rid];
             acc->b = A.bacc[rid];
             acc->n = A.nseg[rid];
+            if constexpr (SH) {
+                acc->x1 = A.g1acc[rid];
+                acc->x2 = A.g2acc[rid];
+            }
             acc->loaded = true;
         }
         acc->k = ff_mul_add(acc->k, kh, kl, A.sch, A.scl);
         acc->b = ff_mul_add(acc->b, bh, bl, A.bsh, A.bsl);
         acc->n += cnt;
+        if constexpr (SH) {
+            if (!sg.finite()) atomicOr(A.err, kErrNonFinite);
+            float gh, gl;
+            two_sum(sg.s.x, -sg.c.x, gh, gl);
+            acc->x1 = ff_mul_add(acc->x1, gh, gl, A.sch, A.scl);
+            two_sum(sg.s.y, -sg.c.y, gh, gl);
+            acc->x2 = ff_mul_add(acc->x2, gh, gl, A.sch, A.scl);
+        }
         return;
     }
     A.kacc[rid] = ff_mul_add(A.kacc[rid], kh, kl, A.sch, A.scl);
@@ -344,11 +358,12 @@ __global__ void __launch_bounds__(NT_MAX, 2) trace_amr_kernel(const TraceArgs A,
     if (ix < A.nx && iy < A.ny) trace_ray_amr<INTERP, FORM>(A, M, ix, iy);
 }
 
-// Consecutive steps over the adaptive mesh in one launch (the default form),
-// as trace_steps_kernel does on the uniform grid: every step its own leaf
-// records, interval and scales, the ray's sums in registers in between; per
-// step the arithmetic of trace_amr_kernel, so the same results bit for bit.
-template <int INTERP>
+// Consecutive steps over the adaptive mesh in one launch, as
+// trace_steps_kernel does on the uniform grid: every step its own leaf
+// records, interval and scales, the ray's sums (and its shear pair) in
+// registers in between; per step the arithmetic of trace_amr_kernel, so the
+// same results bit for bit.
+template <int INTERP, int FORM>
 __global__ void __launch_bounds__(NT_MAX, 2)
     trace_amr_steps_kernel(const TraceArgs A, const AmrDevice M, const __grid_constant__ StepBlock S, const TileCfg t)
 {
@@ -366,27 +381,43 @@ __global__ void __launch_bounds__(NT_MAX, 2)
         As.Lf = st.Lf; As.D0f = st.D0f;
         As.sch = st.sch; As.scl = st.scl;
         As.bsh = st.bsh; As.bsl = st.bsl;
-        trace_ray_amr<INTERP, kFormKahan, true>(As, M, ix, iy, &acc);
+        trace_ray_amr<INTERP, FORM, true>(As, M, ix, iy, &acc);
     }
     if (acc.loaded) {
         const long long rid = (long long)iy * A.nx + ix;
         A.kacc[rid] = acc.k;
         A.bacc[rid] = acc.b;
         A.nseg[rid] = acc.n;
+        if constexpr (FORM == kFormShear) {
+            A.g1acc[rid] = acc.x1;
+            A.g2acc[rid] = acc.x2;
+        }
     }
 }
 
 }  // namespace
 
 cudaError_t launch_trace_amr_steps(const TraceArgs& a, const AmrDevice& m, const StepBlock& b, int interp,
-                                   cudaStream_t s)
+                                   cudaStream_t s, int form)
 {
     if (b.n < 1 || b.n > kMaxStepBlock) return cudaErrorInvalidValue;
     const TileCfg t;
     const dim3 grid = tile_grid(t, a.nx, a.ny);
     const dim3 block(32 * t.bwx * t.bwy);
-    if (interp == RR_TRILINEAR) trace_amr_steps_kernel<RR_TRILINEAR><<<grid, block, 0, s>>>(a, m, b, t);
-    else trace_amr_steps_kernel<RR_NGP><<<grid, block, 0, s>>>(a, m, b, t);
+    const bool tri = interp == RR_TRILINEAR;
+#define RR_AMR_STEPS(F)                                                                              \
+    do {                                                                                              \
+        if (tri) trace_amr_steps_kernel<RR_TRILINEAR, F><<<grid, block, 0, s>>>(a, m, b, t);          \
+        else trace_amr_steps_kernel<RR_NGP, F><<<grid, block, 0, s>>>(a, m, b, t);                   \
+    } while (0)
+    switch (form) {
+    case kFormKahan: RR_AMR_STEPS(kFormKahan); break;
+    case kFormShear: RR_AMR_STEPS(kFormShear); break;
+    case kFormMethodA: RR_AMR_STEPS(kFormMethodA); break;
+    case kFormGeneric: RR_AMR_STEPS(kFormGeneric); break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef RR_AMR_STEPS
     return cudaGetLastError();
 }
 

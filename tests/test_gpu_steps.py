@@ -257,10 +257,11 @@ def test_box_checks(rrp):
 
 
 @pytest.mark.parametrize("interp", [1, 0])
-def test_amr_steps_match_single_launches(rrp, interp):
+@pytest.mark.parametrize("form", ["default", "shear", "method_a", "generic"])
+def test_amr_steps_match_single_launches(rrp, interp, form):
     """rr_amr_trace_steps against one rr_amr_trace_step per step on a random
-    mesh: the same maps and segment counts bit for bit; the shear form goes
-    step by step with the same result."""
+    mesh, in every form of the adaptive-mesh walk: the same maps (and shear
+    maps) and segment counts bit for bit, 19 steps (two launches)."""
     import torch
     mesh = synth.amr_random(16, 64.0, 2, 7, threshold=1.5, child_sigma=0.8)
     pots = synth.amr_potential(mesh, synth.amr_density(mesh, 7, child_sigma=0.8))
@@ -270,12 +271,20 @@ def test_amr_steps_match_single_launches(rrp, interp):
     phi = torch.from_numpy(flat).cuda()
     b = synth.Bundle(56, 48, synth.deg(9), synth.deg(7), (31.0, 33.0, 2.0), 60.0, interp=interp)
     steps = synth.step_schedule(60.0, 19, rescale=True)
-    recs = [gm.tidal(phi, gm.record_buffer(where), where) for _ in range(2)]
+    kw = {} if form == "default" else {form: True}
+
+    def records():
+        rec = gm.record_buffer(where)
+        if form == "method_a":
+            return gm.gradient(phi, rec, where)
+        if form == "generic":
+            return gm.scalars(phi, rec, where, prev0=phi * 0.5, inv_dt0=2.0, field1=phi)
+        return gm.tidal(phi, rec, where)
+
+    recs = [records() for _ in range(2)]
     per_step = [recs[i % 2] for i in range(len(steps))]
     out = []
-    for kw, fused in (({}, False), ({}, True), ({"shear": True}, False), ({"shear": True}, True)):
-        if interp == 0 and kw:
-            continue
+    for fused in (False, True):
         tr = rrp.Tracer(b, **kw)
         if fused:
             tr.amr_steps(gm, per_step, steps)
@@ -283,12 +292,16 @@ def test_amr_steps_match_single_launches(rrp, interp):
             for st, r in zip(steps, per_step):
                 tr.amr_step(gm, r, st.chi_a, st.chi_b, st.scale, st.a)
         k, kb = tr.finalize()
+        maps = [k.cpu().numpy(), kb.cpu().numpy()]
+        if form == "shear":
+            maps += [x.cpu().numpy() for x in tr.shear()]
         n = tr.segments()
         torch.cuda.synchronize()
-        out.append((k.cpu().numpy(), kb.cpu().numpy(), n, rrp.rr_step_count(tr.ctx)))
+        out.append((maps, n, rrp.rr_step_count(tr.ctx)))
         tr.close()
     gm.close()
-    for i in range(0, len(out), 2):
-        one, fused = out[i], out[i + 1]
-        assert np.array_equal(one[0], fused[0]) and np.array_equal(one[1], fused[1])
-        assert one[2] == fused[2] and one[3] == fused[3] == len(steps)
+    one, fused = out
+    assert np.isfinite(one[0][0]).all()
+    for x, y in zip(one[0], fused[0]):
+        assert np.array_equal(x, y)
+    assert one[1] == fused[1] and one[2] == fused[2] == len(steps)
