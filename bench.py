@@ -45,12 +45,12 @@ L2_FLUSH_BYTES = 256 << 20
 # (kernel source, workload, steps per launch): valid only for the source it was
 # taken on (sha256 of csrc/trace.cu + csrc/walk.cuh) and for that workload.
 TRACE_TRAFFIC = {("77240c8f04eae276", "prod_512", 1): 275_386_624,
-                 ("c483806de75dff9e", "prod_512", 16): 293_591_552}
+                 ("8ac9a523f7f334dd", "prod_512", 16): 293_330_859}
 # warp instructions per cell segment of one trace launch from the same kind of
 # ncu capture (smsp__inst_executed.sum / segments of the launch), per (kernel
 # source, workload); null in the line when the source differs
 TRACE_WARP_INSTRUCTIONS = {("77240c8f04eae276", "prod_512", 1): 9.3201,
-                           ("c483806de75dff9e", "prod_512", 16): 9.3731}
+                           ("8ac9a523f7f334dd", "prod_512", 16): 8.8203}
 
 # FP32 lane operations the method needs per trilinear segment, counted from its
 # formulas as the walk evaluates them: exit face (2 compares) and segment length

@@ -38,9 +38,10 @@ namespace {
 // Crossing face e of the mirrored cell: the 4 corners on the exit side become
 // the entry side and the 4 new corner values p come in on the exit side.
 // SEL: the same moves as selects on e (no divergent branches), slot by slot
-// the value it takes for e = 0, 1, 2; measured faster in the shear and
-// Method A forms, slower in the default and moments forms.
-template <bool SEL = false>
+// the value it takes for e = 0, 1, 2. Selects are used everywhere: faster in
+// the shear and Method A forms and in the multi-step kernels (2 % on the
+// production pass), the same as the branches for one default step per launch.
+template <bool SEL = true>
 __device__ __forceinline__ void shift_corners(float2 q[8], const float2 p[4], int e)
 {
     if constexpr (SEL) {
@@ -487,7 +488,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs& A, int ix, int iy, Ra
             float2 p2[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) p2[r] = pair(nr[r]);
-            shift_corners<SH || MA>(q2, p2, e);
+            shift_corners(q2, p2, e);
             if constexpr (SH) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r) p2[r] = make_float2(project(w1, nr[r]), project(w2, nr[r]));
