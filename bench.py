@@ -1327,7 +1327,7 @@ def main():
             rrp.rr_reset(tr.ctx, stream)
             if G > 1:
                 h2d_bytes = tr.trace_streamed(w.grid, phi_pinned, steps, rec, bufs, stream, copy_stream, pboxes,
-                                              group=G, box_recs=brecs)
+                                              group=G, box_recs=brecs, rec_stream=side)
             else:
                 h2d_bytes = tr.trace_streamed(w.grid, phi_pinned, steps, rec, bufs, stream, copy_stream, bboxes)
             rrp.rr_finalize(tr.ctx, kappa, kborn, stream)

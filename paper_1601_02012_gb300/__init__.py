@@ -211,7 +211,7 @@ class Tracer:
         return gamma1, gamma2
 
     def trace_streamed(self, grid, phi_host, steps, rec, bufs, stream, copy_stream, bboxes=None, delta_host=None,
-                       delta_bufs=None, group=1, box_recs=None):
+                       delta_bufs=None, group=1, box_recs=None, rec_stream=None):
         """The steps of a pass with the potential streamed from host memory.
 
         phi_host: page-locked host tensor of n0*n1*n2 floats; bufs: two device
@@ -227,7 +227,9 @@ class Tracer:
         passed the last step. group > 1: each step's records go into its own
         box-local buffer box_recs[i] over bboxes[i] (footprints widened by one
         point: footprint(pad=1)), and every ``group`` steps are traced by one
-        rr_trace_steps call. Returns the bytes copied."""
+        rr_trace_steps call; with ``rec_stream`` (a higher-priority stream)
+        those records are computed there, beside the previous group's trace,
+        and each group's trace waits for its own. Returns the bytes copied."""
         import torch
         if self.generic:
             raise ValueError("trace_streamed: the generic form takes its fields through scalars()")
@@ -241,6 +243,9 @@ class Tracer:
         queued = torch.cuda.Event()
         queued.record(stream)
         copy_stream.wait_event(queued)
+        rs = rec_stream if (group > 1 and rec_stream is not None) else stream
+        if rs is not stream:
+            rs.wait_event(queued)
         released = [None, None]
         total = 0
         for i, st in enumerate(steps):
@@ -254,18 +259,20 @@ class Tracer:
                 delta = delta_bufs[slot]
             copied = torch.cuda.Event()
             copied.record(copy_stream)
-            stream.wait_event(copied)
+            rs.wait_event(copied)
             if group > 1:
-                self.tidal_box(grid, bufs[slot], box_recs[i], bboxes[i], delta=delta, stream=stream)
+                self.tidal_box(grid, bufs[slot], box_recs[i], bboxes[i], delta=delta, stream=rs)
             else:
-                self.tidal(grid, bufs[slot], rec, delta=delta, bbox=bboxes[i], stream=stream)
+                self.tidal(grid, bufs[slot], rec, delta=delta, bbox=bboxes[i], stream=rs)
             done = torch.cuda.Event()
-            done.record(stream)
+            done.record(rs)
             released[slot] = done
             if group <= 1:
                 self.step(grid, rec, st.chi_a, st.chi_b, st.scale, st.a, stream)
             elif (i + 1) % group == 0 or i == len(steps) - 1:
                 k0 = i - i % group
+                if rs is not stream:
+                    stream.wait_event(done)   # the group's records (rs runs them in order)
                 self.steps(grid, box_recs[k0:i + 1], steps[k0:i + 1], boxes=bboxes[k0:i + 1], stream=stream)
         return total
 

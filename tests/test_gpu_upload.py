@@ -195,3 +195,36 @@ def test_back_to_back_streamed_passes_share_buffers(rrpkg):
             tr.close()
     for (k1, kb1), (k2, kb2) in zip(ref, maps):
         assert torch.equal(k1, k2) and torch.equal(kb1, kb2)
+
+
+@pytest.mark.parametrize("with_side", [False, True])
+def test_streamed_grouped_pass_equals_resident_pass(rrpkg, with_side):
+    """Box-local records from the streamed buffers, 4 steps per rr_trace_steps
+    launch, the records on a high-priority side stream or in order; two
+    passes queued back to back through the same buffers: each equals the
+    resident pass bit for bit."""
+    import torch
+    rrp = rrpkg
+    grid, bundle, steps, phi = _pass_case(1)
+    k1, kb1, s1 = rrp.trace_kappa(torch.from_numpy(phi).cuda(), grid, bundle, steps, group=1)
+    tr = rrp.Tracer(bundle)
+    try:
+        stream, copy_stream = torch.cuda.Stream(), torch.cuda.Stream()
+        side = torch.cuda.Stream(priority=-1) if with_side else None
+        host = torch.from_numpy(phi).pin_memory()
+        bufs = [torch.full(phi.shape, float("nan"), dtype=torch.float32, device="cuda") for _ in range(2)]
+        pboxes = [tr.footprint(grid, st.chi_a, st.chi_b, pad=1) for st in steps]
+        brecs = [rrp.box_record_buffer(b) for b in pboxes]
+        out = []
+        for _ in range(2):
+            tr.reset(stream)
+            tr.trace_streamed(grid, host, steps, None, bufs, stream, copy_stream, pboxes, group=4, box_recs=brecs,
+                              rec_stream=side)
+            k2, kb2 = tr.finalize(stream=stream)
+            out.append((k2.clone(), kb2.clone(), tr.segments(stream=stream)))
+        torch.cuda.synchronize()
+    finally:
+        tr.close()
+    for k2, kb2, s2 in out:
+        assert s1 == s2
+        assert torch.equal(k1, k2) and torch.equal(kb1, kb2)
