@@ -695,6 +695,27 @@ def run_amr(args, name):
             "segments_per_ray_gpu": segs / w.bundle.nrays,
             "segments_per_ray_oracle": float(np.concatenate([res.nseg, res2.nseg]).mean()),
         }
+        if not args.compact:
+            # map statistics on a contiguous 64 x 64 patch at the map centre, traced
+            # by the (single-threaded) AMR oracle through all steps
+            from paper_1601_02012_gb300 import mapstats
+            px = py = min(64, w.bundle.nx, w.bundle.ny)
+            x0, yy0 = (w.bundle.nx - px) // 2, (w.bundle.ny - py) // 2
+            iy, ix = np.meshgrid(np.arange(yy0, yy0 + py), np.arange(x0, x0 + px), indexing="ij")
+            prids = (iy * w.bundle.nx + ix).ravel()
+            t0 = time.perf_counter()
+            pres = oracle.amr_trace(w.bundle, mesh, steps, rids=prids)
+            dtp = time.perf_counter() - t0
+            fx = w.bundle.fov_x * (px - 1) / max(w.bundle.nx - 1, 1)
+            fy = w.bundle.fov_y * (py - 1) / max(w.bundle.ny - 1, 1)
+            line["map_statistics"] = {
+                "patch": f"{px}x{py} rays at the map centre ({fx * 180 / math.pi:.4f} x "
+                         f"{fy * 180 / math.pi:.4f} deg), all {nst} steps, oracle {dtp:.1f} s",
+                "kappa": mapstats.compare(kg[prids].reshape(py, px), pres.kappa.reshape(py, px), fx, fy),
+                "kborn": mapstats.compare(kbg[prids].reshape(py, px), pres.kborn.reshape(py, px), fx, fy),
+                "definition": "P(ell): 20 log bins of ell = 2 pi m / Upsilon, largest relative bin difference; "
+                              "PDF: 100 bins over +-5 sigma of the oracle map, L1 distance",
+            }
     tr.close()
     gm.close()
     print(json.dumps(line), flush=True)
@@ -1052,7 +1073,8 @@ def _other_workloads(steps, warmup):
     amr = _sub_line(["--workload", "amr_256", "--steps", str(steps), "--warmup", str(warmup)])
     if "error" not in amr:
         amr = _compact(amr, ["value", "unit", "ms_per_step", "rays_per_s", "segments_per_step",
-                             "kernels_ms_per_step", "roofline", "e2e", "error_vs_oracle", "cpu_baseline",
+                             "kernels_ms_per_step", "roofline", "e2e", "error_vs_oracle", "map_statistics",
+                             "cpu_baseline",
                              "clocks", "config", "gpu_launches"])
     bat = _sub_line(["--workload", "batch64", "--steps", str(steps), "--warmup", str(warmup)])
     if "error" not in bat:
@@ -1063,7 +1085,7 @@ def _other_workloads(steps, warmup):
                      "--steps", str(steps), "--warmup", str(warmup)])
     if "error" not in adj:
         adj = _compact(adj, ["value", "unit", "ms_per_step", "segments_per_step", "backward",
-                             "error_vs_oracle", "gradient_vs_oracle", "clocks", "config"])
+                             "error_vs_oracle", "map_statistics", "gradient_vs_oracle", "clocks", "config"])
     return {"amr_256": amr, "batch64": bat, "adjoint_256": adj,
             "note": f"each workload run by this script in a child process (--workload NAME --steps {steps} "
                     f"--warmup {warmup}; the adjoint with --with-backward), condensed"}
@@ -1498,9 +1520,10 @@ def main():
             "segments_sampled_rays_oracle": int(nseg_ora.sum()),
             "segments_rel_diff": float(abs(int(nseg_gpu[allr].sum()) - int(nseg_ora.sum())) / nseg_ora.sum()),
         }
-        if not args.compact:
+        if not args.compact or w.name == "adjoint_256":
             # map statistics: a contiguous patch of the map (its centre quarter per
             # side) traced by the oracle through all steps, P(ell) and PDF vs the GPU's
+            # (the one-step differentiation workload's patch takes the oracle ~3 s)
             from paper_1601_02012_gb300 import mapstats
             px = min(512, w.bundle.nx)
             py = min(512, w.bundle.ny)
