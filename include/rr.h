@@ -665,8 +665,8 @@ rr_status rr_amr_trace_steps(rr_ctx* ctx, rr_amr* mesh, int32_t nsteps, const fl
  * 4.8 MB). Every GPU that loads the library holds that array until the
  * process exits. The caller still provides `rec` and the output maps. The
  * first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. Every call reuses the same array and clears what it accumulates
+ * device, with that device current). Every call reuses the same array and
+ * clears what it accumulates
  * into at the start; calls whose work overlaps on the GPU (two streams, or
  * two host threads, at once) race on it and must be serialised by the caller.
  * Returns RR_ERR_CAPACITY if nx * ny > RR_NOALLOC_MAX_RAYS, RR_ERR_ARG for
