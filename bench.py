@@ -1416,13 +1416,16 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config(w, nst) | {"form": "fp64 walk" if args.fp64_dda else "fp32 walk, Kahan sums",
-                                      "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)],
-                                      "steps_per_launch": G,
-                                      "records": ("each step's footprint box (widened by a point), box-local"
-                                                  if G > 1 else "whole grid, each step's footprint rewritten"),
-                                      "parallelism": f"one bundle, its rows split over {world} GPU(s) in "
-                                                     "whole ray tiles; maps all-gathered every pass"},
+        "config": _config(w, nst),
+        # how this arm runs the workload (the config above is the workload alone, the
+        # same in the reference arm's line)
+        "execution": {"form": "fp64 walk" if args.fp64_dda else "fp32 walk, Kahan sums",
+                      "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)],
+                      "steps_per_launch": G,
+                      "records": ("each step's footprint box (widened by a point), box-local"
+                                  if G > 1 else "whole grid, each step's footprint rewritten"),
+                      "parallelism": f"one bundle, its rows split over {world} GPU(s) in "
+                                     "whole ray tiles; maps all-gathered every pass"},
         "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
         "segments_per_step": segs_all,
         "roofline": {
