@@ -68,6 +68,10 @@ _PIPELINE_NOTE = {
     False: "each step's footprint records computed on a side stream while the previous step is traced "
            "(two record buffers; events order each buffer's reuse)",
     True: "records then trace of each step in order on one stream (one record buffer)",
+    "grouped": "the footprint records of a group of steps computed on a high-priority side stream while the "
+               "previous group is traced (a box-local record buffer per step); each group's launch waits "
+               "for its records",
+    "grouped_in_order": "the records of each group of steps, then its launch, in order on one stream",
 }
 
 
@@ -624,7 +628,9 @@ def run_amr(args, name):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _amr_config(w, mesh, nst) | {"form": "fp32 float-float walk on the finest lattice, Kahan sums",
-                                               "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)],
+                                               "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline) if G == 1 else
+                                                                          ("grouped_in_order" if args.no_pipeline
+                                                                           else "grouped")],
                                                "steps_per_launch": G},
         "rays_per_s": w.bundle.nrays * args.steps / (total_ms / 1e3),
         "segments_per_step": segs,
@@ -1420,7 +1426,8 @@ def main():
         # how this arm runs the workload (the config above is the workload alone, the
         # same in the reference arm's line)
         "execution": {"form": "fp64 walk" if args.fp64_dda else "fp32 walk, Kahan sums",
-                      "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline)],
+                      "pipeline": _PIPELINE_NOTE[bool(args.no_pipeline) if G == 1 else
+                                                 ("grouped_in_order" if args.no_pipeline else "grouped")],
                       "steps_per_launch": G,
                       "records": ("each step's footprint box (widened by a point), box-local"
                                   if G > 1 else "whole grid, each step's footprint rewritten"),
