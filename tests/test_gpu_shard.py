@@ -106,3 +106,32 @@ def test_sharded_autograd_on_one_rank_equals_trace_kappa(rrp):
     (k2.square().sum() + kb2.sum()).backward()
     assert torch.equal(k1, k2) and torch.equal(kb1, kb2)
     assert float((phi.grad - g1).norm()) <= 1e-5 * float(g1.norm())
+
+
+def test_bands_with_multi_step_launches_on_box_records(rrp):
+    """Bands traced by rr_trace_steps on box-local records (the footprints of
+    the whole bundle, widened by a point) concatenate to the whole bundle's
+    maps traced one rr_trace_step per step on whole-grid records."""
+    import torch
+    from paper_1601_02012_gb300 import shard
+    g = synth.Grid((48, 48, 48), 96.0)
+    b = synth.Bundle(48, 40, synth.deg(10), synth.deg(9), (46.0, 49.0, 3.0), 80.0)
+    steps = synth.step_schedule(80.0, 7, rescale=True)
+    ph = torch.from_numpy(synth.grf_phi(48, 96.0, 6)).cuda()
+    rec = rrp.record_buffer(g)
+    rrp.rr_tidal_tensor(rrp.grid_desc(g), ph, None, rec, rrp.RR_AT_VERTICES)
+    whole, k, kb = _trace(rrp, g, b, rec, steps)
+    whole.close()
+    parts_k, parts_kb = [], []
+    for y0, y1 in shard.bands(b.ny, 3):
+        tr = rrp.Tracer(b, rows=(y0, y1))
+        boxes = [tr.footprint(g, st.chi_a, st.chi_b, pad=1) for st in steps]
+        recs = [tr.tidal_box(g, ph, rrp.box_record_buffer(bb), bb) for bb in boxes]
+        tr.steps(g, recs, steps, boxes=boxes)
+        kk, kkb = tr.finalize()
+        torch.cuda.synchronize()
+        parts_k.append(kk.cpu().numpy())
+        parts_kb.append(kkb.cpu().numpy())
+        tr.close()
+    assert np.array_equal(np.concatenate(parts_k), k)
+    assert np.array_equal(np.concatenate(parts_kb), kb)
